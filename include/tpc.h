@@ -1,0 +1,322 @@
+/*
+ * tpc.h — C ABI of the B300 TPC timeframe reconstruction library.
+ *
+ * The library reconstructs one TPC timeframe on one GPU: zero-suppressed (ZS)
+ * digit decoding, the 3x3 peak / cluster finder per pad row, cellular-automaton
+ * (CA) seeding across pad rows, the in-sector segment merge and the Kalman helix
+ * fit.  The paper (Rohr, "The ALICE Run 3 Online / Offline Processing",
+ * section "Hardware and data flow") states that the EPN GPUs perform the full
+ * online TPC track reconstruction, that this is the most computing-intense part
+ * of the synchronous processing, and that zero suppression of the raw data runs
+ * upstream in the readout FPGA.  The paper does not define any of the
+ * algorithms; every operation below is therefore defined in this header (and
+ * restated, independently, by the CPU oracle shipped for testing).
+ *
+ * Conventions
+ *   - Every function returns tpc_status: 0 on success, a negative TPC_E_* code
+ *     otherwise.  tpc_last_error() returns a thread-local message for the most
+ *     recent failure on the calling thread.
+ *   - Pointers are host pointers unless stated otherwise.  "Borrowed" means the
+ *     caller keeps ownership and must keep the memory valid for the stated time.
+ *   - Units: x, y, z in cm.  A time bin is 200 ns = 0.5 cm of drift.  The common
+ *     integer unit u = 7.8125 um is used by CA and merge (see TPC coordinates).
+ *
+ * Geometry (sector-local frame)
+ *   n_sectors sectors (36: 0..17 on side A, z > 0; 18..35 on side C), each with
+ *   n_rows pad rows.  Row r has npads[r] pads of pitch 0.4 cm centred on the
+ *   sector axis: y(r, p) = (p - (npads[r]-1)/2) * 0.4 cm.  Row r sits at
+ *   x = row_x[r] * 0.05 cm.  Sector s has axis angle alpha_s = ((s mod 18) + 0.5)
+ *   * 20 degrees.
+ *
+ * ZS page format (one page per window = (sector, row, fragment); a fragment is
+ * 256 time bins, fragment f covers time bins [256 f, 256 f + 256)).  All
+ * integers little endian.  Pages start on 16-byte boundaries and their length is
+ * a multiple of 16.
+ *     off  0  u32 page_bytes      total length including this header
+ *     off  4  u16 n_tb            number of time-bin entries
+ *     off  6  u16 n_runs          number of pad runs
+ *     off  8  u16 n_digits        number of digits (= sum of run lengths)
+ *     off 10  u8  sector, u8 row
+ *     off 12  u16 fragment
+ *     off 14  u16 magic           TPC_ZS_MAGIC
+ *     off 16  u16 lo_tb, lo_runs, lo_digits   entries/runs/digits with t < 3
+ *     off 22  u16 hi_tb, hi_runs, hi_digits   first entry/run/digit with t >= 253
+ *     off 28  u32 reserved (0)
+ *     off 32  n_tb  x {u8 t_in_fragment, u8 n_runs}   strictly increasing t, n_runs >= 1
+ *             n_runs x {u8 pad_start, u8 len}          per entry: ascending, disjoint, len >= 1
+ *             (4-byte aligned) ceil(n_digits/3) x u32  ADCs, digit k in bits 10*(k%3)..+9 of word k/3
+ *             zero padding to a multiple of 16 bytes
+ *   Digit order is time-major, pad-ascending.  The lo_/hi_ fields let the two
+ *   neighbouring windows read only the 3-time-bin halo they need.
+ *
+ * Results
+ *   Clusters are returned in canonical order: ascending (sector, row, t_peak,
+ *   pad_peak); a cluster's index is its position in that order.  Tracks are
+ *   returned ordered by (sector, index of their lowest cluster).
+ */
+#ifndef TPC_H
+#define TPC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t tpc_status;
+
+#define TPC_OK            0
+#define TPC_E_INVAL      -1   /* bad argument (null pointer, size out of range, bad descriptor) */
+#define TPC_E_NOMEM      -2   /* request larger than the context's memory budget, or allocation failed */
+#define TPC_E_BUSY       -3   /* no free slot and TPC_TF_NOWAIT given */
+#define TPC_E_CUDA       -4   /* a CUDA runtime call failed; message in tpc_last_error() */
+#define TPC_E_CORRUPT    -5   /* a ZS page failed validation (header, ranges, counts) */
+#define TPC_E_NOTREADY   -6   /* results requested before the timeframe finished */
+#define TPC_E_TIMEOUT    -7   /* tpc_poll timed out, or a bounded device wait gave up */
+#define TPC_E_OVERFLOW   -8   /* a capacity (clusters, chains, tracks) was exceeded */
+#define TPC_E_DEVICE     -9   /* device error word set for another reason */
+#define TPC_E_NOTFOUND  -10   /* unknown or released ticket */
+
+#define TPC_ZS_MAGIC      0x5A53u
+#define TPC_FRAGMENT_BINS 256
+#define TPC_ZS_HALO       3
+#define TPC_MAX_PADS      255
+#define TPC_MAX_ROWS      255
+#define TPC_MAX_SECTORS   255
+
+/* Ticket states reported by tpc_poll (monotone). */
+#define TPC_STATE_QUEUED          0   /* admitted, waiting for a slot */
+#define TPC_STATE_RUNNING         1   /* work enqueued on the device */
+#define TPC_STATE_INPUT_RELEASED  2   /* input pages copied; caller may reuse them */
+#define TPC_STATE_DONE            3   /* results resident on the device */
+#define TPC_STATE_FAILED          4   /* finished with an error; tpc_poll returns it */
+
+/* Timeframe flags. */
+#define TPC_TF_DEVICE_INPUT  1u   /* pages / page_offsets are device pointers */
+#define TPC_TF_NOWAIT        2u   /* fail with TPC_E_BUSY instead of waiting for a slot */
+
+/* Context flags. */
+#define TPC_CTX_STAGE_TIMING 1u   /* record CUDA events around each stage (tpc_get_stage_times) */
+
+/* Pipeline stages, in launch order (indices into tpc_get_stage_times). */
+#define TPC_STAGE_FIND       0    /* ZS decode + peak finder + cluster moments + compaction */
+#define TPC_STAGE_CA         1    /* CA neighbours, links, chains */
+#define TPC_STAGE_MERGE      2    /* segment merge + track assembly */
+#define TPC_STAGE_FIT        3    /* Kalman fit + emit */
+#define TPC_N_STAGES         4
+
+typedef struct tpc_geometry tpc_geometry;
+typedef struct tpc_context  tpc_context;
+
+/* Geometry descriptor.  npads and row_x are borrowed for the call only. */
+typedef struct {
+  int32_t n_sectors;         /* 1..TPC_MAX_SECTORS */
+  int32_t n_rows;            /* 3..TPC_MAX_ROWS */
+  const int32_t* npads;      /* [n_rows], each 3..TPC_MAX_PADS */
+  const int32_t* row_x;      /* [n_rows], x of the row in units of 0.05 cm, strictly increasing */
+} tpc_geometry_desc;
+
+/* Reconstruction parameters.  tpc_params_default() fills the defaults listed. */
+typedef struct {
+  uint32_t version;          /* TPC_PARAMS_VERSION */
+  int32_t  q_peak_min;       /* 10   minimum peak ADC */
+  int32_t  ca_slope_y_num;   /* 1    |dY| <= (num/den) dX window, y */
+  int32_t  ca_slope_y_den;   /* 1 */
+  int32_t  ca_slope_z_num;   /* 11   |dZ| <= (num/den) dX window, z (1.1) */
+  int32_t  ca_slope_z_den;   /* 10 */
+  int32_t  ca_cut;           /* 256  straight-line deviation cut, u (0.2 cm) */
+  int32_t  min_chain;        /* 5    clusters per kept CA chain */
+  int32_t  merge_cut;        /* 384  merge extrapolation cut, u (0.3 cm) */
+  int32_t  merge_gap_min;    /* 2    row(b1) - row(a2) lower bound */
+  int32_t  merge_gap_max;    /* 4    row(b1) - row(a2) upper bound */
+  int32_t  merge_max_passes; /* 8 */
+  int32_t  min_track;        /* 10   clusters per output track */
+  int32_t  fit_passes;       /* 3    inward, outward, inward */
+  int32_t  reserved0;
+  double   bz;               /* 0.5  T */
+  double   sigma_y;          /* 0.02 cm */
+  double   sigma_z;          /* 0.03 cm */
+  double   c0[5];            /* 4, 4, 0.25, 1, 100 initial covariance diagonal */
+} tpc_params;
+
+#define TPC_PARAMS_VERSION 1u
+
+/* Timeframe descriptor.  pages / page_offsets are borrowed until tpc_poll
+ * reports a state >= TPC_STATE_INPUT_RELEASED. */
+typedef struct {
+  const void*     pages;         /* concatenated ZS pages (16-byte aligned) */
+  uint64_t        pages_bytes;   /* total bytes of pages */
+  const uint64_t* page_offsets;  /* [n_sectors*n_rows*n_fragments] byte offset of the page of
+                                    window (s, r, f) at index (s*n_rows + r)*n_fragments + f */
+  uint32_t        n_time_bins;   /* 1..65535; n_fragments = ceil(n_time_bins / 256) */
+  uint32_t        flags;         /* TPC_TF_* */
+} tpc_timeframe_desc;
+
+/* Cluster record (16 bytes).  See tpc_submit_timeframe for the definition of
+ * every field. */
+typedef struct {
+  uint16_t pad_fp;       /* 256 * pad of the charge centroid (8.8 fixed point) */
+  uint16_t time_fp;      /* 128 * (centroid time - 256*fragment + 4) (9.7 fixed point) */
+  uint16_t qmax;         /* ADC of the peak digit */
+  uint16_t qtot;         /* min(total charge of the cluster, 65535) */
+  uint8_t  sigma2_pad;   /* 16 * pad variance (4.4), saturating at 255 */
+  uint8_t  sigma2_time;  /* 16 * time variance (4.4), saturating at 255 */
+  uint8_t  flags;        /* TPC_CL_* */
+  uint8_t  row;
+  uint16_t t_peak;       /* time bin of the peak digit */
+  uint8_t  pad_peak;     /* pad of the peak digit */
+  uint8_t  sector;
+} tpc_cluster;
+
+#define TPC_CL_EDGE      1u   /* peak on the first/last pad of the row or first/last time bin */
+#define TPC_CL_EXCLUDED  2u   /* an outer-ring digit with charge was left out */
+#define TPC_CL_NEIGHBOUR 4u   /* another peak lies in the 5x5 window */
+
+/* Track record (112 bytes). */
+typedef struct {
+  float    par[5];       /* y, zeta, snp = sin(phi_local), tgl_zeta = dzeta/ds_T, q/pT (1/GeV) */
+  float    x;            /* cm, x of the innermost cluster: the point the parameters refer to */
+  float    alpha;        /* sector axis angle, rad */
+  float    chi2;         /* of the final pass */
+  float    cov[15];      /* lower triangle, row major: c00, c10, c11, c20, c21, c22, ... */
+  int32_t  ndf;          /* 2 * n_used - 5 */
+  int32_t  n_clusters;
+  int32_t  first_cluster;/* canonical index of the lowest-row cluster */
+  int16_t  sector;
+  uint16_t flags;        /* TPC_TRK_* */
+  int32_t  n_fp64;       /* covariance updates redone in FP64 after a failed PD check */
+  int32_t  reserved;
+} tpc_track;
+
+#define TPC_TRK_STOPPED  1u   /* a pass stopped early (|snp| would reach 0.999) */
+#define TPC_TRK_NOT_PD   2u   /* covariance not positive definite even after the FP64 redo */
+
+/* Fill *p with the defaults listed in tpc_params.  Never fails for p != NULL. */
+tpc_status tpc_params_default(tpc_params* p);
+
+/* Create a geometry object from desc (validated: sizes in range, row_x strictly
+ * increasing).  The caller owns *out and frees it with tpc_destroy_geometry.
+ * Defines the sector-local frame of the paper's TPC ("Hardware and data flow":
+ * the TPC data the EPNs reconstruct); the layout itself is this library's. */
+tpc_status tpc_create_geometry(const tpc_geometry_desc* desc, tpc_geometry** out);
+void       tpc_destroy_geometry(tpc_geometry* g);
+
+/* Create a reconstruction context on CUDA device `device`.
+ *   geom        borrowed for the lifetime of the context
+ *   params      copied (NULL: defaults)
+ *   mem_budget  device bytes the context may hold for timeframes in flight
+ *               (0: 8 GiB).  Work space is allocated once, here and on growth.
+ *   n_slots     timeframes that may be in flight at once (1..64)
+ *   stream      cudaStream_t (as void*) to run slot 0 on, or NULL for a
+ *               library-created stream.  Slots > 0 always get their own stream.
+ *   flags       TPC_CTX_*
+ * Errors: TPC_E_INVAL, TPC_E_CUDA, TPC_E_NOMEM. */
+tpc_status tpc_create_context(const tpc_geometry* geom, const tpc_params* params, int device,
+                              uint64_t mem_budget, int n_slots, void* stream, uint32_t flags,
+                              tpc_context** out);
+void       tpc_destroy_context(tpc_context* ctx);
+
+/* Submit one timeframe for reconstruction (non-blocking).
+ *
+ * Operation (the EPN GPU step of the paper's section "Hardware and data flow";
+ * the algorithm is this library's own definition, stated here):
+ *   1 decode   every page is validated and decoded to digits q(p, t).  Pixels
+ *              without a digit have q = 0, as do pads outside the row and times
+ *              outside [0, n_time_bins).
+ *   2 peaks    pixel c is a peak iff q(c) >= q_peak_min and its key
+ *              (q, -(t*npads + p)) is lexicographically greater than the key of
+ *              each of its 8 neighbours in the same row.
+ *   3 cluster  5x5 window around each peak: the inner 3x3 is always included; an
+ *              outer pixel (dp, dt) is included iff q(outer) <= q(inner) and
+ *              q(inner) > 0, inner = (sgn dp*min(|dp|,1), sgn dt*min(|dt|,1)).
+ *              With Q = sum q, Sp = sum q dp, St = sum q dt, Spp = sum q dp^2,
+ *              Stt = sum q dt^2 and R(a, b) = floor((2a + b) / (2b)):
+ *              pad_fp = 256 p + R(256 Sp, Q); time_fp = 128 (t - 256 f + 4) +
+ *              R(128 St, Q); sigma2_pad = min(255, R(16 (Spp Q - Sp^2), Q^2)),
+ *              likewise sigma2_time; qmax = q(peak); qtot = min(Q, 65535).
+ *   4 coords   Y = 2 (pad_fp - 128 (npads-1)), Z = 5 (32768 f + time_fp - 512),
+ *              X = 64 row_x, all in u = 7.8125 um.
+ *   5 CA       for a cluster c on rows 1..n_rows-2, over d on row-1 and u on row+1
+ *              with |Y_u-Y_c| <= sy (X_u-X_c), |Y_c-Y_d| <= sy (X_c-X_d) and the
+ *              same for Z with sz: dev_Y = (Y_u-Y_c)(X_c-X_d) - (Y_c-Y_d)(X_u-X_c),
+ *              dev_Z alike; accepted iff |dev_Y|, |dev_Z| <= ca_cut (X_u - X_d);
+ *              (up[c], down[c]) = argmin of dev_Y^2 + dev_Z^2, ties to the
+ *              smallest (d, u); none: -1.  Row 0: up[d] = argmin of c's score
+ *              over {c on row 1: down[c] = d}, ties to the smallest c; the last
+ *              row mirrors it.
+ *   6 chains   link (c, u) kept iff up[c] = u and down[u] = c.  Chains are the
+ *              maximal paths; chain id = index of the lowest cluster; chains with
+ *              fewer than min_chain clusters are dropped.
+ *   7 merge    for a chain top (a1 below a2) and a chain bottom (b1 below b2) in
+ *              the same sector with merge_gap_min <= row(b1)-row(a2) <=
+ *              merge_gap_max, the forward residuals trunc(((Y_b1-Y_a2)(X_a2-X_a1) -
+ *              (Y_a2-Y_a1)(X_b1-X_a2)) / (X_a2-X_a1)) (and Z), and the backward
+ *              ones from (b2, b1) to a2, must all be <= merge_cut in size; score =
+ *              sum of squares; mutual-best pairs merge (ties to the lower chain
+ *              id of the end's chain); repeated up to merge_max_passes times.
+ *              Merged chains with >= min_track clusters become tracks.
+ *   8 fit      Kalman helix fit of each track in FP32 (see tpc_track): exact
+ *              helix transport, (y, zeta) measurements with sigma_y, sigma_z,
+ *              initial state from the circle through the outermost, middle and
+ *              innermost clusters, C0 = diag(c0); passes inward, outward, inward
+ *              with the covariance reset at each pass start; update C' = C - K H C
+ *              then symmetrised; an update whose result fails the PD check is
+ *              redone in FP64.
+ * Ownership: tf->pages and tf->page_offsets are borrowed (see the descriptor).
+ * Results stay on the device until tpc_release.  *ticket identifies them.
+ * Errors: TPC_E_INVAL (descriptor), TPC_E_NOMEM (over budget), TPC_E_BUSY
+ * (TPC_TF_NOWAIT and no slot), TPC_E_CUDA.  Page corruption and capacity
+ * overflow are reported by tpc_poll (TPC_E_CORRUPT, TPC_E_OVERFLOW). */
+tpc_status tpc_submit_timeframe(tpc_context* ctx, const tpc_timeframe_desc* tf, uint64_t* ticket);
+
+/* Wait up to timeout_us (0: do not wait; UINT32_MAX: forever) for the ticket
+ * and report its state in *state.  Returns TPC_OK while running or done,
+ * TPC_E_TIMEOUT if the wait expired, or the timeframe's own error
+ * (TPC_E_CORRUPT, TPC_E_OVERFLOW, TPC_E_TIMEOUT, TPC_E_DEVICE, TPC_E_CUDA) once it
+ * has failed (state TPC_STATE_FAILED). */
+tpc_status tpc_poll(tpc_context* ctx, uint64_t ticket, uint32_t timeout_us, int32_t* state);
+
+/* Copy the clusters of a finished ticket into out (host memory, cap records).
+ * out == NULL: only *n is set (size query).  TPC_E_OVERFLOW if cap < n.
+ * TPC_E_NOTREADY before TPC_STATE_DONE. */
+tpc_status tpc_get_clusters(tpc_context* ctx, uint64_t ticket, tpc_cluster* out, uint64_t cap,
+                            uint64_t* n);
+
+/* Copy the tracks (cap records) and, if cluster_to_track != NULL, the track
+ * index of every cluster (-1: none; n_clusters entries) into host memory.
+ * out == NULL: only *n is set.  Errors as tpc_get_clusters. */
+tpc_status tpc_get_tracks(tpc_context* ctx, uint64_t ticket, tpc_track* out, uint64_t cap,
+                          uint64_t* n, int32_t* cluster_to_track);
+
+/* Copy the CA results of a finished ticket (n_clusters entries each; any
+ * pointer may be NULL): up[], down[] (step 5, cluster indices or -1) and
+ * chain_of[] (step 6: id of the kept chain holding the cluster, or -1). */
+tpc_status tpc_get_links(tpc_context* ctx, uint64_t ticket, int32_t* up, int32_t* down,
+                         int32_t* chain_of);
+
+/* Device pointers to a finished ticket's results (valid until tpc_release);
+ * any output pointer may be NULL.  Lets device-resident callers skip the copy. */
+tpc_status tpc_get_device_results(tpc_context* ctx, uint64_t ticket, const tpc_cluster** clusters,
+                                  uint64_t* n_clusters, const tpc_track** tracks,
+                                  uint64_t* n_tracks, const int32_t** cluster_to_track);
+
+/* Per-stage device times (ms) of a finished ticket, from CUDA events recorded on
+ * the slot's stream around each stage; requires TPC_CTX_STAGE_TIMING.
+ * ms[TPC_N_STAGES]. */
+tpc_status tpc_get_stage_times(tpc_context* ctx, uint64_t ticket, float* ms);
+
+/* Counters of a finished ticket: out[0] digits, [1] clusters, [2] kept chains,
+ * [3] tracks, [4] FP64 covariance redos, [5] merge passes that merged, [6]
+ * device error word, [7] ZS bytes read.  n: entries requested (<= 8). */
+tpc_status tpc_get_counters(tpc_context* ctx, uint64_t ticket, uint64_t* out, int n);
+
+/* Free the ticket's slot and results.  Unknown ticket: TPC_E_NOTFOUND. */
+tpc_status tpc_release(tpc_context* ctx, uint64_t ticket);
+
+/* Thread-local message describing the last error on this thread ("" if none). */
+const char* tpc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TPC_H */

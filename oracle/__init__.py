@@ -1,0 +1,333 @@
+"""CPU oracle of the TPC timeframe reconstruction — TEST INFRASTRUCTURE ONLY.
+
+Only the tests, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline /
+reference leg may import this package.  The library (``paper_2208_07412_b300``)
+never does, and shares no code with it.
+
+The arithmetic lives in ``oracle.c`` (plain C, exact integers, FP64 fit; built
+``-O2`` without fast-math).  This module only marshals arguments.  What each
+function computes, and the passage it follows, is stated in ``oracle.c``: the
+paper (section "Hardware and data flow") says that the EPN GPUs run the full
+online TPC reconstruction on zero-suppressed data but defines no algorithm, so
+the oracle writes out the library's documented definition in its plainest form.
+
+Parity status: decode, peaks, clusters, CA, merge and fit are pinned by the
+``-m "not gpu"`` tests (round trip, 3x3 maximum filter, closed forms,
+hand-worked examples, gap closure, exact-helix closure, finite differences,
+information-form update, pulls).  Tracking efficiency / fake rate against the
+generator truth: parity unpinned (the paper prints no figure).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+CLUSTER_DTYPE = np.dtype([("pad_fp", "<u2"), ("time_fp", "<u2"), ("qmax", "<u2"), ("qtot", "<u2"),
+                          ("sigma2_pad", "u1"), ("sigma2_time", "u1"), ("flags", "u1"),
+                          ("row", "u1"), ("t_peak", "<u2"), ("pad_peak", "u1"), ("sector", "u1")])
+assert CLUSTER_DTYPE.itemsize == 16
+
+FIT_DTYPE = np.dtype([("par", "<f8", (5,)), ("x", "<f8"), ("cov", "<f8", (15,)), ("chi2", "<f8"),
+                      ("ndf", "<i4"), ("n_used", "<i4"), ("flags", "<i4"), ("pad", "<i4")])
+assert FIT_DTYPE.itemsize == 8 * 22 + 16
+
+U_CM = 7.8125e-4
+
+
+def build(force: bool = False) -> str:
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-fno-fast-math", "-ffp-contract=off", "-shared",
+                               "-fPIC", "-std=c11", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Input(ctypes.Structure):
+    _fields_ = [("n_sectors", ctypes.c_int32), ("n_rows", ctypes.c_int32),
+                ("npads", ctypes.c_void_p), ("row_x", ctypes.c_void_p),
+                ("n_time_bins", ctypes.c_int32), ("pages", ctypes.c_void_p),
+                ("pages_bytes", ctypes.c_uint64), ("page_offsets", ctypes.c_void_p)]
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("q_peak_min", ctypes.c_int32), ("sy_num", ctypes.c_int32),
+                ("sy_den", ctypes.c_int32), ("sz_num", ctypes.c_int32),
+                ("sz_den", ctypes.c_int32), ("ca_cut", ctypes.c_int32),
+                ("min_chain", ctypes.c_int32), ("merge_cut", ctypes.c_int32),
+                ("gap_min", ctypes.c_int32), ("gap_max", ctypes.c_int32),
+                ("merge_passes", ctypes.c_int32), ("min_track", ctypes.c_int32),
+                ("fit_passes", ctypes.c_int32), ("bz", ctypes.c_double),
+                ("sigma_y", ctypes.c_double), ("sigma_z", ctypes.c_double),
+                ("c0", ctypes.c_double * 5)]
+
+
+@dataclass
+class OracleParams:
+    """The oracle's own copy of the reconstruction constants."""
+    q_peak_min: int = 10
+    sy_num: int = 1
+    sy_den: int = 1
+    sz_num: int = 11
+    sz_den: int = 10
+    ca_cut: int = 256          # 0.2 cm in u
+    min_chain: int = 5
+    merge_cut: int = 384       # 0.3 cm in u
+    gap_min: int = 1
+    gap_max: int = 6
+    merge_passes: int = 8
+    min_track: int = 10
+    fit_passes: int = 3
+    bz: float = 0.5
+    sigma_y: float = 0.02
+    sigma_z: float = 0.03
+    c0: tuple = (4.0, 4.0, 0.25, 1.0, 100.0)
+
+    def _c(self) -> _Params:
+        p = _Params()
+        for k in ("q_peak_min", "sy_num", "sy_den", "sz_num", "sz_den", "ca_cut", "min_chain",
+                  "merge_cut", "gap_min", "gap_max", "merge_passes", "min_track", "fit_passes"):
+            setattr(p, k, int(getattr(self, k)))
+        p.bz, p.sigma_y, p.sigma_z = self.bz, self.sigma_y, self.sigma_z
+        for i in range(5):
+            p.c0[i] = self.c0[i]
+        return p
+
+
+_lib = None
+_P = ctypes.c_void_p
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB)
+        L.orc_decode_row.argtypes = [_P, ctypes.c_int, ctypes.c_int, _P]
+        L.orc_decode_all.argtypes = [_P, _P, ctypes.c_int]
+        L.orc_find_clusters.argtypes = [_P, _P, _P, ctypes.c_int64]
+        L.orc_find_clusters.restype = ctypes.c_int64
+        L.orc_peaks_plane.argtypes = [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P]
+        L.orc_cluster_at.argtypes = [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                     ctypes.c_int, _P]
+        L.orc_ca.argtypes = [_P, _P, _P, ctypes.c_int64, _P, _P, _P]
+        L.orc_merge.argtypes = [_P, _P, _P, ctypes.c_int64, _P, _P, _P, _P, _P, _P, ctypes.c_int64, _P]
+        L.orc_merge.restype = ctypes.c_int64
+        L.orc_fit_all.argtypes = [_P, _P, _P, ctypes.c_int64, _P, ctypes.c_int64, _P]
+        L.orc_fit_points.argtypes = [_P, ctypes.c_int, _P, _P, _P, _P]
+        L.orc_fit_track.argtypes = [_P, ctypes.c_int, _P, _P, _P, _P]
+        L.orc_transport.argtypes = [_P, _P, ctypes.c_double, _P, _P]
+        L.orc_update.argtypes = [_P, _P, _P, ctypes.c_double, ctypes.c_double, _P]
+        L.orc_update.restype = ctypes.c_double
+        _lib = L
+    return _lib
+
+
+class _In:
+    """Keeps the numpy buffers of one oracle input alive."""
+
+    def __init__(self, pages, page_offsets, npads, row_x, n_sectors, n_time_bins):
+        self.pages = np.ascontiguousarray(pages, dtype=np.uint8)
+        self.offs = np.ascontiguousarray(page_offsets, dtype=np.uint64)
+        self.npads = np.ascontiguousarray(npads, dtype=np.int32)
+        self.row_x = np.ascontiguousarray(row_x, dtype=np.int32)
+        s = _Input()
+        s.n_sectors, s.n_rows = int(n_sectors), int(len(self.npads))
+        s.npads, s.row_x = self.npads.ctypes.data, self.row_x.ctypes.data
+        s.n_time_bins = int(n_time_bins)
+        s.pages = self.pages.ctypes.data if self.pages.size else None
+        s.pages_bytes = int(self.pages.size)
+        s.page_offsets = self.offs.ctypes.data
+        self.s = s
+
+    @classmethod
+    def from_tf(cls, tf):
+        return cls(tf.pages, tf.page_offsets, tf.npads, tf.row_x, tf.n_sectors, tf.n_time_bins)
+
+    @property
+    def ref(self):
+        return ctypes.byref(self.s)
+
+
+class CorruptPage(Exception):
+    pass
+
+
+def decode_all(tf) -> np.ndarray:
+    """Dense planes [sector, row, t, pad] (pads padded to the widest row)."""
+    L = _load()
+    inp = _In.from_tf(tf)
+    npmax = int(inp.npads.max())
+    out = np.zeros((tf.n_sectors, len(inp.npads), tf.n_time_bins, npmax), dtype=np.uint16)
+    if L.orc_decode_all(inp.ref, out.ctypes.data, npmax) != 0:
+        raise CorruptPage("corrupt ZS page")
+    return out
+
+
+def peaks_plane(plane: np.ndarray, q_peak_min: int = 10) -> np.ndarray:
+    """Peak flags of one dense plane q[t, pad]."""
+    L = _load()
+    plane = np.ascontiguousarray(plane, dtype=np.uint16)
+    T, np_ = plane.shape
+    fl = np.zeros((T, np_), dtype=np.uint8)
+    L.orc_peaks_plane(plane.ctypes.data, np_, T, q_peak_min, fl.ctypes.data)
+    return fl.astype(bool)
+
+
+def cluster_at(plane: np.ndarray, pad: int, t: int, q_peak_min: int = 10) -> np.void:
+    L = _load()
+    plane = np.ascontiguousarray(plane, dtype=np.uint16)
+    T, np_ = plane.shape
+    out = np.zeros(1, dtype=CLUSTER_DTYPE)
+    L.orc_cluster_at(plane.ctypes.data, np_, T, pad, t, q_peak_min, out.ctypes.data)
+    return out[0]
+
+
+def find_clusters(tf, params: OracleParams | None = None) -> np.ndarray:
+    L = _load()
+    p = (params or OracleParams())._c()
+    inp = _In.from_tf(tf)
+    n = L.orc_find_clusters(inp.ref, ctypes.byref(p), None, 0)
+    if n < 0:
+        raise CorruptPage("corrupt ZS page")
+    out = np.zeros(n, dtype=CLUSTER_DTYPE)
+    L.orc_find_clusters(inp.ref, ctypes.byref(p), out.ctypes.data if n else None, n)
+    return out
+
+
+def coords(tf, clusters: np.ndarray):
+    """Integer (X, Y, Z) in u = 7.8125 um (restated here from the same definition
+    for convenience of the tests; the C code is what the other functions use)."""
+    npads = np.asarray(tf.npads, dtype=np.int64)
+    row_x = np.asarray(tf.row_x, dtype=np.int64)
+    r = clusters["row"].astype(np.int64)
+    f = clusters["t_peak"].astype(np.int64) // 256
+    Y = 2 * (clusters["pad_fp"].astype(np.int64) - 128 * (npads[r] - 1))
+    Z = 5 * (128 * 256 * f + clusters["time_fp"].astype(np.int64) - 512)
+    X = 64 * row_x[r]
+    return X, Y, Z
+
+
+def ca(tf, clusters: np.ndarray, params: OracleParams | None = None):
+    L = _load()
+    p = (params or OracleParams())._c()
+    inp = _In.from_tf(tf)
+    cl = np.ascontiguousarray(clusters, dtype=CLUSTER_DTYPE)
+    n = len(cl)
+    up = np.full(n, -1, np.int32)
+    down = np.full(n, -1, np.int32)
+    chain = np.full(n, -1, np.int32)
+    L.orc_ca(inp.ref, ctypes.byref(p), cl.ctypes.data if n else None, n, up.ctypes.data,
+             down.ctypes.data, chain.ctypes.data)
+    return up, down, chain
+
+
+def merge(tf, clusters, up, down, chain_of, params: OracleParams | None = None):
+    L = _load()
+    p = (params or OracleParams())._c()
+    inp = _In.from_tf(tf)
+    cl = np.ascontiguousarray(clusters, dtype=CLUSTER_DTYPE)
+    n = len(cl)
+    cl2trk = np.full(n, -1, np.int32)
+    cap = max(1, n // 5 + 1)
+    first = np.zeros(cap, np.int64)
+    ncl = np.zeros(cap, np.int64)
+    passes = ctypes.c_int32(0)
+    up = np.ascontiguousarray(up, np.int32)
+    down = np.ascontiguousarray(down, np.int32)
+    chain_of = np.ascontiguousarray(chain_of, np.int32)
+    nt = L.orc_merge(inp.ref, ctypes.byref(p), cl.ctypes.data if n else None, n, up.ctypes.data,
+                     down.ctypes.data, chain_of.ctypes.data, cl2trk.ctypes.data, first.ctypes.data,
+                     ncl.ctypes.data, cap, ctypes.byref(passes))
+    return cl2trk, first[:nt].copy(), ncl[:nt].copy(), int(passes.value)
+
+
+def fit_all(tf, clusters, cl2trk, n_tracks, params: OracleParams | None = None) -> np.ndarray:
+    L = _load()
+    p = (params or OracleParams())._c()
+    inp = _In.from_tf(tf)
+    cl = np.ascontiguousarray(clusters, dtype=CLUSTER_DTYPE)
+    out = np.zeros(max(n_tracks, 1), dtype=FIT_DTYPE)
+    cl2trk = np.ascontiguousarray(cl2trk, np.int32)
+    L.orc_fit_all(inp.ref, ctypes.byref(p), cl.ctypes.data if len(cl) else None, len(cl),
+                  cl2trk.ctypes.data, n_tracks, out.ctypes.data)
+    return out[:n_tracks]
+
+
+def fit_points(x, y, z, params: OracleParams | None = None) -> np.void:
+    """FP64 fit of points (cm), ascending x."""
+    L = _load()
+    p = (params or OracleParams())._c()
+    x = np.ascontiguousarray(x, np.float64)
+    y = np.ascontiguousarray(y, np.float64)
+    z = np.ascontiguousarray(z, np.float64)
+    out = np.zeros(1, dtype=FIT_DTYPE)
+    L.orc_fit_points(ctypes.byref(p), len(x), x.ctypes.data, y.ctypes.data, z.ctypes.data,
+                     out.ctypes.data)
+    return out[0]
+
+
+def transport(state, dx, params: OracleParams | None = None):
+    """Exact helix transport; returns (new_state, F) or (None, None) if stopped."""
+    L = _load()
+    p = (params or OracleParams())._c()
+    s = np.ascontiguousarray(state, np.float64)
+    o = np.zeros(5)
+    F = np.zeros(25)
+    rc = L.orc_transport(ctypes.byref(p), s.ctypes.data, float(dx), o.ctypes.data, F.ctypes.data)
+    if rc:
+        return None, None
+    return o, F.reshape(5, 5)
+
+
+def update(state, C, my, mz, params: OracleParams | None = None):
+    """One Kalman update; returns (state', C', chi2, pd_ok)."""
+    L = _load()
+    p = (params or OracleParams())._c()
+    s = np.array(state, np.float64)
+    Cm = np.array(C, np.float64).reshape(25).copy()
+    ok = ctypes.c_int(0)
+    chi2 = L.orc_update(ctypes.byref(p), s.ctypes.data, Cm.ctypes.data, float(my), float(mz),
+                        ctypes.byref(ok))
+    return s, Cm.reshape(5, 5), chi2, bool(ok.value)
+
+
+@dataclass
+class OracleResult:
+    clusters: np.ndarray
+    up: np.ndarray
+    down: np.ndarray
+    chain_of: np.ndarray
+    cl2trk: np.ndarray
+    track_first: np.ndarray
+    track_ncl: np.ndarray
+    fits: np.ndarray
+    merge_passes: int = 0
+    times: dict = field(default_factory=dict)
+
+
+def reconstruct(tf, params: OracleParams | None = None) -> OracleResult:
+    """The whole pipeline, stage by stage."""
+    import time
+    times = {}
+    t = time.perf_counter()
+    cl = find_clusters(tf, params)
+    times["find"] = time.perf_counter() - t
+    t = time.perf_counter()
+    up, down, chain = ca(tf, cl, params)
+    times["ca"] = time.perf_counter() - t
+    t = time.perf_counter()
+    cl2trk, first, ncl, passes = merge(tf, cl, up, down, chain, params)
+    times["merge"] = time.perf_counter() - t
+    t = time.perf_counter()
+    fits = fit_all(tf, cl, cl2trk, len(first), params)
+    times["fit"] = time.perf_counter() - t
+    return OracleResult(cl, up, down, chain, cl2trk, first, ncl, fits, passes, times)

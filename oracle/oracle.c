@@ -1,0 +1,654 @@
+/*
+ * oracle.c — plain, slow CPU oracle of the TPC timeframe reconstruction.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the
+ * benchmark's CPU-baseline leg may load this code; the library never does.  It
+ * shares no code, header, table or constant with the CUDA path.
+ *
+ * The paper (section "Hardware and data flow") says only that the EPN GPUs run
+ * the full online TPC track reconstruction on zero-suppressed data; it defines
+ * none of the algorithms.  This file therefore writes out, step by step and in
+ * the plainest form, the definition the library documents: ZS decode, 3x3 peak
+ * test under a total order, 5x5 cluster moments, integer CA neighbour search by
+ * brute force over all candidate pairs, mutual links and chains, integer
+ * segment merge, and the FP64 Kalman helix fit.  Integers are exact; the fit is
+ * double precision.  No blocking, fusion or reordering beyond the definition.
+ *
+ * Pins (tests, not this file): ZS round trip, peak finder against a 3x3
+ * maximum filter, centroid closed forms, CA special cases and hand-worked
+ * examples, merge gap closure, fit closure on exact helices, Jacobian against
+ * finite differences, Kalman update against the information form, pulls.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------ data types */
+typedef struct {
+  int32_t n_sectors, n_rows;
+  const int32_t* npads;
+  const int32_t* row_x;       /* 0.05 cm units */
+  int32_t n_time_bins;
+  const uint8_t* pages;
+  uint64_t pages_bytes;
+  const uint64_t* page_offsets;
+} orc_input;
+
+typedef struct {
+  int32_t q_peak_min;
+  int32_t sy_num, sy_den, sz_num, sz_den;
+  int32_t ca_cut;
+  int32_t min_chain;
+  int32_t merge_cut, gap_min, gap_max, merge_passes;
+  int32_t min_track;
+  int32_t fit_passes;
+  double bz, sigma_y, sigma_z;
+  double c0[5];
+} orc_params;
+
+/* 16-byte cluster record, field for field as documented by the library. */
+typedef struct {
+  uint16_t pad_fp, time_fp, qmax, qtot;
+  uint8_t sigma2_pad, sigma2_time, flags, row;
+  uint16_t t_peak;
+  uint8_t pad_peak, sector;
+} orc_cluster;
+
+typedef struct {
+  double par[5];   /* y, zeta, snp, tgl_zeta, q/pT (absolute y, zeta) */
+  double x;
+  double cov[15];
+  double chi2;
+  int32_t ndf, n_used, flags, pad;
+} orc_fit;
+
+#define ORC_E_CORRUPT (-5)
+
+/* ------------------------------------------------------------ helpers */
+static uint32_t rd16(const uint8_t* p) { return (uint32_t)p[0] | ((uint32_t)p[1] << 8); }
+static uint32_t rd32(const uint8_t* p) {
+  return (uint32_t)p[0] | ((uint32_t)p[1] << 8) | ((uint32_t)p[2] << 16) | ((uint32_t)p[3] << 24);
+}
+/* R(a, b) = floor((2a + b) / (2b)) for b > 0: division rounding half up */
+static int64_t round_div(int64_t a, int64_t b) {
+  int64_t n = 2 * a + b, d = 2 * b;
+  int64_t q = n / d;
+  if ((n % d != 0) && ((n < 0) != (d < 0))) q -= 1;
+  return q;
+}
+static int64_t iabs64(int64_t v) { return v < 0 ? -v : v; }
+
+/* ------------------------------------------------------------ 1. decode */
+/* Decode every page of (sector s, row r) into the dense plane q[t * npads + p]
+ * (zero where there is no digit).  Returns 0 or ORC_E_CORRUPT. */
+int orc_decode_row(const orc_input* in, int s, int r, uint16_t* plane) {
+  int np = in->npads[r];
+  int T = in->n_time_bins;
+  int nf = (T + 255) / 256;
+  memset(plane, 0, sizeof(uint16_t) * (size_t)T * np);
+  for (int f = 0; f < nf; f++) {
+    uint64_t off = in->page_offsets[((int64_t)s * in->n_rows + r) * nf + f];
+    if (off % 16 != 0 || off + 32 > in->pages_bytes) return ORC_E_CORRUPT;
+    const uint8_t* pg = in->pages + off;
+    uint32_t len = rd32(pg);
+    uint32_t n_tb = rd16(pg + 4), n_runs = rd16(pg + 6), n_dig = rd16(pg + 8);
+    if (rd16(pg + 14) != 0x5A53u || pg[10] != s || pg[11] != r || rd16(pg + 12) != (uint32_t)f)
+      return ORC_E_CORRUPT;
+    uint64_t body = 32 + 2 * (uint64_t)n_tb + 2 * (uint64_t)n_runs;
+    body = (body + 3) & ~(uint64_t)3;
+    if (len % 16 != 0 || off + len > in->pages_bytes || body + 4 * (((uint64_t)n_dig + 2) / 3) > len)
+      return ORC_E_CORRUPT;
+    const uint8_t* ent = pg + 32;
+    const uint8_t* run = ent + 2 * n_tb;
+    const uint8_t* adcw = pg + body;
+    uint32_t ri = 0, di = 0;
+    int last_t = -1;
+    for (uint32_t e = 0; e < n_tb; e++) {
+      int t_in = ent[2 * e], nr = ent[2 * e + 1];
+      int t = 256 * f + t_in;
+      if (t_in <= last_t || nr < 1 || t >= T) return ORC_E_CORRUPT;
+      last_t = t_in;
+      int last_end = -1;
+      for (int k = 0; k < nr; k++, ri++) {
+        if (ri >= n_runs) return ORC_E_CORRUPT;
+        int ps = run[2 * ri], ln = run[2 * ri + 1];
+        if (ln < 1 || ps < last_end || ps + ln > np) return ORC_E_CORRUPT;
+        last_end = ps + ln;
+        for (int i = 0; i < ln; i++, di++) {
+          if (di >= n_dig) return ORC_E_CORRUPT;
+          uint32_t w = rd32(adcw + 4 * (di / 3));
+          plane[(size_t)t * np + ps + i] = (uint16_t)((w >> (10 * (di % 3))) & 1023u);
+        }
+      }
+    }
+    if (ri != n_runs || di != n_dig) return ORC_E_CORRUPT;
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------ 2-3. peaks, clusters */
+static int q_at(const uint16_t* plane, int np, int T, int p, int t) {
+  if (p < 0 || p >= np || t < 0 || t >= T) return 0;
+  return plane[(size_t)t * np + p];
+}
+
+/* key(c) > key(n) with key = (q, -(t*np + p)), lexicographic */
+static int key_greater(int qc, int64_t lc, int qn, int64_t ln) {
+  if (qc != qn) return qc > qn;
+  return lc < ln;
+}
+
+static int is_peak(const uint16_t* plane, int np, int T, int p, int t, int qmin) {
+  int q = q_at(plane, np, T, p, t);
+  if (q < qmin) return 0;
+  int64_t lc = (int64_t)t * np + p;
+  for (int dt = -1; dt <= 1; dt++)
+    for (int dp = -1; dp <= 1; dp++) {
+      if (dp == 0 && dt == 0) continue;
+      int pn = p + dp, tn = t + dt;
+      int qn = q_at(plane, np, T, pn, tn);
+      int64_t ln = (int64_t)tn * np + pn;
+      if (!key_greater(q, lc, qn, ln)) return 0;
+    }
+  return 1;
+}
+
+static int sgn(int v) { return (v > 0) - (v < 0); }
+static int imin(int a, int b) { return a < b ? a : b; }
+
+static orc_cluster make_cluster(const uint16_t* plane, int np, int T, int s, int r, int p, int t,
+                                int qmin) {
+  int64_t Q = 0, Sp = 0, St = 0, Spp = 0, Stt = 0;
+  int excluded = 0, other_peak = 0;
+  for (int dt = -2; dt <= 2; dt++)
+    for (int dp = -2; dp <= 2; dp++) {
+      int q = q_at(plane, np, T, p + dp, t + dt);
+      int inc;
+      if (abs(dp) <= 1 && abs(dt) <= 1) {
+        inc = 1;
+      } else {
+        int ip = sgn(dp) * imin(abs(dp), 1), it = sgn(dt) * imin(abs(dt), 1);
+        int qi = q_at(plane, np, T, p + ip, t + it);
+        inc = (qi > 0) && (q <= qi);
+        if (!inc && q > 0) excluded = 1;
+      }
+      if (inc) {
+        Q += q; Sp += (int64_t)q * dp; St += (int64_t)q * dt;
+        Spp += (int64_t)q * dp * dp; Stt += (int64_t)q * dt * dt;
+      }
+      if ((dp || dt) && p + dp >= 0 && p + dp < np && t + dt >= 0 && t + dt < T &&
+          is_peak(plane, np, T, p + dp, t + dt, qmin))
+        other_peak = 1;
+    }
+  int f = t / 256;
+  orc_cluster c;
+  c.pad_fp = (uint16_t)(256 * p + round_div(256 * Sp, Q));
+  c.time_fp = (uint16_t)(128 * (t - 256 * f + 4) + round_div(128 * St, Q));
+  int64_t vp = round_div(16 * (Spp * Q - Sp * Sp), Q * Q);
+  int64_t vt = round_div(16 * (Stt * Q - St * St), Q * Q);
+  c.sigma2_pad = (uint8_t)(vp > 255 ? 255 : vp);
+  c.sigma2_time = (uint8_t)(vt > 255 ? 255 : vt);
+  c.qmax = (uint16_t)q_at(plane, np, T, p, t);
+  c.qtot = (uint16_t)(Q > 65535 ? 65535 : Q);
+  c.flags = 0;
+  if (p == 0 || p == np - 1 || t == 0 || t == T - 1) c.flags |= 1;
+  if (excluded) c.flags |= 2;
+  if (other_peak) c.flags |= 4;
+  c.row = (uint8_t)r;
+  c.t_peak = (uint16_t)t;
+  c.pad_peak = (uint8_t)p;
+  c.sector = (uint8_t)s;
+  return c;
+}
+
+/* Clusters of the whole timeframe in canonical order (sector, row, t, p).
+ * out may be NULL (count only).  Returns the count, or ORC_E_CORRUPT. */
+int64_t orc_find_clusters(const orc_input* in, const orc_params* P, orc_cluster* out, int64_t cap) {
+  int npmax = 0;
+  for (int r = 0; r < in->n_rows; r++) if (in->npads[r] > npmax) npmax = in->npads[r];
+  uint16_t* plane = (uint16_t*)malloc(sizeof(uint16_t) * (size_t)in->n_time_bins * npmax + 2);
+  int64_t n = 0;
+  for (int s = 0; s < in->n_sectors; s++)
+    for (int r = 0; r < in->n_rows; r++) {
+      int np = in->npads[r], T = in->n_time_bins;
+      if (orc_decode_row(in, s, r, plane) != 0) { free(plane); return ORC_E_CORRUPT; }
+      for (int t = 0; t < T; t++)
+        for (int p = 0; p < np; p++)
+          if (is_peak(plane, np, T, p, t, P->q_peak_min)) {
+            if (out && n < cap) out[n] = make_cluster(plane, np, T, s, r, p, t, P->q_peak_min);
+            n++;
+          }
+    }
+  free(plane);
+  return n;
+}
+
+/* Dense decoded planes of a whole timeframe, [sector][row][t][pad] with pads
+ * padded to npmax; for tests. */
+int orc_decode_all(const orc_input* in, uint16_t* out, int npmax) {
+  uint16_t* plane = (uint16_t*)malloc(sizeof(uint16_t) * (size_t)in->n_time_bins * npmax + 2);
+  for (int s = 0; s < in->n_sectors; s++)
+    for (int r = 0; r < in->n_rows; r++) {
+      int np = in->npads[r];
+      if (orc_decode_row(in, s, r, plane) != 0) { free(plane); return ORC_E_CORRUPT; }
+      uint16_t* o = out + ((size_t)s * in->n_rows + r) * (size_t)in->n_time_bins * npmax;
+      memset(o, 0, sizeof(uint16_t) * (size_t)in->n_time_bins * npmax);
+      for (int t = 0; t < in->n_time_bins; t++)
+        memcpy(o + (size_t)t * npmax, plane + (size_t)t * np, sizeof(uint16_t) * np);
+    }
+  free(plane);
+  return 0;
+}
+
+/* Peak flags of one dense plane q[t * np + p] (tests). */
+void orc_peaks_plane(const uint16_t* plane, int np, int T, int qmin, uint8_t* flags) {
+  for (int t = 0; t < T; t++)
+    for (int p = 0; p < np; p++) flags[(size_t)t * np + p] = (uint8_t)is_peak(plane, np, T, p, t, qmin);
+}
+
+/* One cluster from a dense plane (tests). */
+void orc_cluster_at(const uint16_t* plane, int np, int T, int p, int t, int qmin, orc_cluster* out) {
+  *out = make_cluster(plane, np, T, 0, 0, p, t, qmin);
+}
+
+/* ------------------------------------------------------------ 4. coordinates */
+/* Integer coordinates in u = 7.8125 um. */
+void orc_coords(const orc_input* in, const orc_cluster* c, int64_t* X, int64_t* Y, int64_t* Z) {
+  int np = in->npads[c->row];
+  int f = c->t_peak / 256;
+  *Y = 2 * ((int64_t)c->pad_fp - 128 * (int64_t)(np - 1));
+  *Z = 5 * ((int64_t)128 * 256 * f + c->time_fp - 512);
+  *X = 64 * (int64_t)in->row_x[c->row];
+}
+
+/* ------------------------------------------------------------ 5-6. CA */
+/* up / down / best score for every cluster by brute force over all (d, u) pairs,
+ * then mutual links and chains.  chain_of[c] = index of the lowest cluster of
+ * the chain holding c if that chain has >= min_chain clusters, else -1. */
+int orc_ca(const orc_input* in, const orc_params* P, const orc_cluster* cl, int64_t n,
+           int32_t* up, int32_t* down, int32_t* chain_of) {
+  int64_t *X = (int64_t*)malloc(sizeof(int64_t) * (n + 1)), *Y = (int64_t*)malloc(sizeof(int64_t) * (n + 1)),
+          *Z = (int64_t*)malloc(sizeof(int64_t) * (n + 1)), *score = (int64_t*)malloc(sizeof(int64_t) * (n + 1));
+  for (int64_t i = 0; i < n; i++) { orc_coords(in, &cl[i], &X[i], &Y[i], &Z[i]); up[i] = down[i] = -1; score[i] = -1; }
+  /* row ranges: clusters are in canonical order, so each (sector, row) is contiguous */
+  int64_t nsr = (int64_t)in->n_sectors * in->n_rows;
+  int64_t* rs = (int64_t*)calloc((size_t)nsr + 1, sizeof(int64_t));
+  for (int64_t i = 0; i < n; i++) rs[(int64_t)cl[i].sector * in->n_rows + cl[i].row + 1]++;
+  for (int64_t b = 0; b < nsr; b++) rs[b + 1] += rs[b];
+  const int R = in->n_rows;
+  for (int s = 0; s < in->n_sectors; s++)
+    for (int r = 1; r <= R - 2; r++) {
+      int64_t bc = (int64_t)s * R + r;
+      for (int64_t c = rs[bc]; c < rs[bc + 1]; c++) {
+        int64_t best = -1, bd = -1, bu = -1;
+        for (int64_t d = rs[bc - 1]; d < rs[bc]; d++) {
+          int64_t dxd = X[c] - X[d];
+          if (iabs64(Y[c] - Y[d]) * P->sy_den > (int64_t)P->sy_num * dxd) continue;
+          if (iabs64(Z[c] - Z[d]) * P->sz_den > (int64_t)P->sz_num * dxd) continue;
+          for (int64_t u = rs[bc + 1]; u < rs[bc + 2]; u++) {
+            int64_t dxu = X[u] - X[c];
+            if (iabs64(Y[u] - Y[c]) * P->sy_den > (int64_t)P->sy_num * dxu) continue;
+            if (iabs64(Z[u] - Z[c]) * P->sz_den > (int64_t)P->sz_num * dxu) continue;
+            int64_t devy = (Y[u] - Y[c]) * dxd - (Y[c] - Y[d]) * dxu;
+            int64_t devz = (Z[u] - Z[c]) * dxd - (Z[c] - Z[d]) * dxu;
+            int64_t lim = (int64_t)P->ca_cut * (X[u] - X[d]);
+            if (iabs64(devy) > lim || iabs64(devz) > lim) continue;
+            int64_t sc = devy * devy + devz * devz;
+            /* d ascending, then u ascending: strict < keeps the smallest (d, u) on ties */
+            if (best < 0 || sc < best) { best = sc; bd = d; bu = u; }
+          }
+        }
+        if (best >= 0) { up[c] = (int32_t)bu; down[c] = (int32_t)bd; score[c] = best; }
+      }
+      (void)0;
+    }
+  /* edge rows */
+  for (int s = 0; s < in->n_sectors; s++) {
+    int64_t b0 = (int64_t)s * R, b1 = b0 + 1;
+    for (int64_t d = rs[b0]; d < rs[b0 + 1]; d++) {
+      int64_t best = -1, arg = -1;
+      for (int64_t c = rs[b1]; c < rs[b1 + 1]; c++)
+        if (down[c] == d && (best < 0 || score[c] < best)) { best = score[c]; arg = c; }
+      up[d] = (int32_t)arg;
+      down[d] = -1;
+    }
+    int64_t bl = (int64_t)s * R + R - 1, bm = bl - 1;
+    for (int64_t u = rs[bl]; u < rs[bl + 1]; u++) {
+      int64_t best = -1, arg = -1;
+      for (int64_t c = rs[bm]; c < rs[bm + 1]; c++)
+        if (up[c] == u && (best < 0 || score[c] < best)) { best = score[c]; arg = c; }
+      down[u] = (int32_t)arg;
+      up[u] = -1;
+    }
+  }
+  /* links and chains */
+  for (int64_t i = 0; i < n; i++) chain_of[i] = -1;
+  for (int64_t c = 0; c < n; c++) {
+    int has_down = down[c] >= 0 && up[down[c]] == c;
+    if (has_down) continue;
+    int64_t len = 1, cur = c;
+    while (up[cur] >= 0 && down[up[cur]] == cur) { cur = up[cur]; len++; }
+    if (len >= P->min_chain) {
+      cur = c;
+      chain_of[cur] = (int32_t)c;
+      while (up[cur] >= 0 && down[up[cur]] == cur) { cur = up[cur]; chain_of[cur] = (int32_t)c; }
+    }
+  }
+  free(X); free(Y); free(Z); free(score); free(rs);
+  return 0;
+}
+
+/* ------------------------------------------------------------ 7. merge */
+typedef struct {
+  int64_t root;       /* chain id */
+  int64_t* cl;        /* clusters bottom -> top */
+  int64_t len;
+  int64_t next, prev; /* merged neighbour chain (index into chain table) */
+} ochain;
+
+static int64_t trunc_div(int64_t a, int64_t b) { return a / b; /* C truncates toward zero */ }
+
+/* Residual of point (xb, yb) from the straight line through (x1, y1) -> (x2, y2),
+ * measured along y at xb: trunc(((yb-y2)(x2-x1) - (y2-y1)(xb-x2)) / (x2-x1)). */
+static int64_t extrap_res(int64_t x1, int64_t y1, int64_t x2, int64_t y2, int64_t xb, int64_t yb) {
+  return trunc_div((yb - y2) * (x2 - x1) - (y2 - y1) * (xb - x2), x2 - x1);
+}
+
+/* Merge kept chains into tracks.  cl2trk[c] = track index or -1; track_first[k]
+ * = index of the lowest cluster of track k; track_ncl[k].  Returns the track
+ * count; *passes_merged = passes that merged something. */
+int64_t orc_merge(const orc_input* in, const orc_params* P, const orc_cluster* cl, int64_t n,
+                  const int32_t* up, const int32_t* down, const int32_t* chain_of, int32_t* cl2trk,
+                  int64_t* track_first, int64_t* track_ncl, int64_t track_cap, int32_t* passes_merged) {
+  int64_t *X = (int64_t*)malloc(sizeof(int64_t) * (n + 1)), *Y = (int64_t*)malloc(sizeof(int64_t) * (n + 1)),
+          *Z = (int64_t*)malloc(sizeof(int64_t) * (n + 1));
+  for (int64_t i = 0; i < n; i++) orc_coords(in, &cl[i], &X[i], &Y[i], &Z[i]);
+  /* chain table in chain-id order */
+  int64_t nch = 0;
+  for (int64_t c = 0; c < n; c++) if (chain_of[c] == c) nch++;
+  ochain* ch = (ochain*)calloc((size_t)nch + 1, sizeof(ochain));
+  int64_t k = 0;
+  for (int64_t c = 0; c < n; c++)
+    if (chain_of[c] == c) {
+      int64_t len = 1, cur = c;
+      while (up[cur] >= 0 && down[up[cur]] == cur) { cur = up[cur]; len++; }
+      ch[k].root = c; ch[k].len = len; ch[k].next = ch[k].prev = -1;
+      ch[k].cl = (int64_t*)malloc(sizeof(int64_t) * len);
+      cur = c;
+      for (int64_t i = 0; i < len; i++) { ch[k].cl[i] = cur; if (i + 1 < len) cur = up[cur]; }
+      k++;
+    }
+  int64_t* sec_lo = (int64_t*)calloc((size_t)in->n_sectors + 2, sizeof(int64_t));
+  for (int64_t i = 0; i < nch; i++) sec_lo[cl[ch[i].root].sector + 1]++;
+  for (int s = 0; s < in->n_sectors; s++) sec_lo[s + 1] += sec_lo[s];
+  int64_t* bestB = (int64_t*)malloc(sizeof(int64_t) * (nch + 1));
+  int64_t* bestBs = (int64_t*)malloc(sizeof(int64_t) * (nch + 1));
+  int64_t* bestA = (int64_t*)malloc(sizeof(int64_t) * (nch + 1));
+  int64_t* bestAs = (int64_t*)malloc(sizeof(int64_t) * (nch + 1));
+  int merged_passes = 0;
+  for (int pass = 0; pass < P->merge_passes; pass++) {
+    for (int64_t i = 0; i < nch; i++) { bestB[i] = bestA[i] = -1; bestBs[i] = bestAs[i] = -1; }
+    for (int64_t a = 0; a < nch; a++) {
+      if (ch[a].next >= 0) continue;                 /* not a top end */
+      int64_t a2 = ch[a].cl[ch[a].len - 1], a1 = ch[a].cl[ch[a].len - 2];
+      /* chains are in id order, hence grouped by sector: scan only a2's sector */
+      for (int64_t b = sec_lo[cl[a2].sector]; b < sec_lo[cl[a2].sector + 1]; b++) {
+        if (ch[b].prev >= 0) continue;               /* not a bottom end */
+        int64_t b1 = ch[b].cl[0], b2 = ch[b].cl[1];
+        if (cl[b1].sector != cl[a2].sector) continue;
+        int gap = (int)cl[b1].row - (int)cl[a2].row;
+        if (gap < P->gap_min || gap > P->gap_max) continue;
+        int64_t ry = extrap_res(X[a1], Y[a1], X[a2], Y[a2], X[b1], Y[b1]);
+        int64_t rz = extrap_res(X[a1], Z[a1], X[a2], Z[a2], X[b1], Z[b1]);
+        int64_t sy = extrap_res(X[b2], Y[b2], X[b1], Y[b1], X[a2], Y[a2]);
+        int64_t sz = extrap_res(X[b2], Z[b2], X[b1], Z[b1], X[a2], Z[a2]);
+        if (iabs64(ry) > P->merge_cut || iabs64(rz) > P->merge_cut || iabs64(sy) > P->merge_cut ||
+            iabs64(sz) > P->merge_cut)
+          continue;
+        int64_t sc = ry * ry + rz * rz + sy * sy + sz * sz;
+        /* ties to the lower chain id: chains are visited in id order, strict < */
+        if (bestB[a] < 0 || sc < bestBs[a]) { bestB[a] = b; bestBs[a] = sc; }
+        if (bestA[b] < 0 || sc < bestAs[b]) { bestA[b] = a; bestAs[b] = sc; }
+      }
+    }
+    int any = 0;
+    for (int64_t a = 0; a < nch; a++) {
+      int64_t b = bestB[a];
+      if (b >= 0 && bestA[b] == a) { ch[a].next = b; ch[b].prev = a; any = 1; }
+    }
+    if (!any) break;
+    merged_passes++;
+  }
+  for (int64_t i = 0; i < n; i++) cl2trk[i] = -1;
+  int64_t ntr = 0;
+  for (int64_t a = 0; a < nch; a++) {
+    if (ch[a].prev >= 0) continue;
+    int64_t tot = 0;
+    for (int64_t g = a; g >= 0; g = ch[g].next) tot += ch[g].len;
+    if (tot < P->min_track) continue;
+    if (ntr < track_cap) { track_first[ntr] = ch[a].root; track_ncl[ntr] = tot; }
+    for (int64_t g = a; g >= 0; g = ch[g].next)
+      for (int64_t i = 0; i < ch[g].len; i++) cl2trk[ch[g].cl[i]] = (int32_t)ntr;
+    ntr++;
+  }
+  if (passes_merged) *passes_merged = merged_passes;
+  for (int64_t i = 0; i < nch; i++) free(ch[i].cl);
+  free(sec_lo); free(ch); free(bestB); free(bestBs); free(bestA); free(bestAs); free(X); free(Y); free(Z);
+  return ntr;
+}
+
+/* ------------------------------------------------------------ 8. Kalman fit */
+#define CLIGHT 0.299792458
+
+/* Curvature per unit q/pT: k = kfac * q/pT (1/cm), kfac = -bz * c * 1e-2. */
+static double kfac(const orc_params* P) { return -P->bz * CLIGHT * 1e-2; }
+
+/* Exact helix transport of state s (y, zeta, snp, tgl, qpt) by dx along x.
+ * Fills the 5x5 Jacobian F (row-major) if F != NULL.  Returns 0, or 1 if
+ * |snp| would reach 0.999. */
+int orc_transport(const orc_params* P, const double* s, double dx, double* out, double* F) {
+  double K = kfac(P);
+  double k = K * s[4];
+  double s1 = s[2], s2 = s1 + k * dx;
+  if (fabs(s1) >= 0.999 || fabs(s2) >= 0.999) return 1;
+  double c1 = sqrt(1.0 - s1 * s1), c2 = sqrt(1.0 - s2 * s2);
+  double f = (s1 + s2) / (c1 + c2);
+  double dy = dx * f;
+  double d = fabs(dx) * sqrt(1.0 + f * f);        /* chord length */
+  double kd = k * d;
+  double A;                                       /* unsigned arc length */
+  if (fabs(kd) < 1e-3) A = d * (1.0 + kd * kd / 24.0);
+  else {
+    double h = kd / 2.0;
+    if (h > 1.0) h = 1.0;
+    if (h < -1.0) h = -1.0;
+    A = 2.0 * asin(h) / k;
+  }
+  double sg = dx > 0 ? 1.0 : (dx < 0 ? -1.0 : 0.0);
+  out[0] = s[0] + dy;
+  out[1] = s[1] + s[3] * sg * A;
+  out[2] = s2;
+  out[3] = s[3];
+  out[4] = s[4];
+  if (F) {
+    for (int i = 0; i < 25; i++) F[i] = 0.0;
+    for (int i = 0; i < 5; i++) F[i * 5 + i] = 1.0;
+    /* f(s1, s2) partials */
+    double cc = c1 + c2;
+    double fs1 = 1.0 / cc + f * (s1 / c1) / cc;
+    double fs2 = 1.0 / cc + f * (s2 / c2) / cc;
+    double ds2dq = K * dx;
+    /* y */
+    F[0 * 5 + 2] = dx * (fs1 + fs2);
+    F[0 * 5 + 4] = dx * fs2 * ds2dq;
+    /* snp */
+    F[2 * 5 + 4] = ds2dq;
+    /* zeta: A(d, k), d(f) */
+    double x = kd / 2.0;
+    double Ad = 1.0 / sqrt(1.0 - x * x);
+    double Ak;
+    if (fabs(x) < 0.1) {
+      double x2 = x * x;
+      Ak = (k * d * d * d / 4.0) * (1.0 / 3.0 + x2 * (0.3 + x2 * (15.0 / 56.0 + x2 * (35.0 / 144.0))));
+    } else {
+      Ak = (2.0 / (k * k)) * (x / sqrt(1.0 - x * x) - asin(x));
+    }
+    double dd_df = fabs(dx) * f / sqrt(1.0 + f * f);
+    double dd_ds1 = dd_df * (fs1 + fs2);
+    double dd_dq = dd_df * fs2 * ds2dq;
+    F[1 * 5 + 2] = s[3] * sg * Ad * dd_ds1;
+    F[1 * 5 + 3] = sg * A;
+    F[1 * 5 + 4] = s[3] * sg * (Ad * dd_dq + Ak * K);
+  }
+  return 0;
+}
+
+/* One Kalman update with measurement (my, mz) of (y, zeta).  C is 5x5 full.
+ * Returns the chi2 increment; *pd_ok reports the PD check of the result. */
+double orc_update(const orc_params* P, double* s, double* C, double my, double mz, int* pd_ok) {
+  double S00 = C[0] + P->sigma_y * P->sigma_y, S01 = C[1], S11 = C[6] + P->sigma_z * P->sigma_z;
+  double det = S00 * S11 - S01 * S01;
+  double I00 = S11 / det, I01 = -S01 / det, I11 = S00 / det;
+  double r0 = my - s[0], r1 = mz - s[1];
+  double Kg[5][2];
+  for (int i = 0; i < 5; i++) {
+    Kg[i][0] = C[i * 5 + 0] * I00 + C[i * 5 + 1] * I01;
+    Kg[i][1] = C[i * 5 + 0] * I01 + C[i * 5 + 1] * I11;
+  }
+  for (int i = 0; i < 5; i++) s[i] += Kg[i][0] * r0 + Kg[i][1] * r1;
+  double Cn[25];
+  for (int i = 0; i < 5; i++)
+    for (int j = 0; j < 5; j++) Cn[i * 5 + j] = C[i * 5 + j] - (Kg[i][0] * C[0 * 5 + j] + Kg[i][1] * C[1 * 5 + j]);
+  for (int i = 0; i < 5; i++)
+    for (int j = 0; j < 5; j++) C[i * 5 + j] = 0.5 * (Cn[i * 5 + j] + Cn[j * 5 + i]);
+  int ok = 1;
+  for (int i = 0; i < 5; i++) if (!(C[i * 5 + i] > 0.0)) ok = 0;
+  for (int i = 0; i < 5 && ok; i++)
+    for (int j = i + 1; j < 5; j++)
+      if (!(C[i * 5 + j] * C[i * 5 + j] < C[i * 5 + i] * C[j * 5 + j])) ok = 0;
+  if (pd_ok) *pd_ok = ok;
+  return r0 * (I00 * r0 + I01 * r1) + r1 * (I01 * r0 + I11 * r1);
+}
+
+/* Initial state at the outermost point from the circle through the innermost
+ * (1), middle (2) and outermost (3) points. */
+static void fit_init(const orc_params* P, const double* x, const double* y, const double* z, int n,
+                     double* s) {
+  int i1 = 0, i2 = (n - 1) / 2, i3 = n - 1;
+  double ax = x[i2] - x[i1], ay = y[i2] - y[i1];
+  double bx = x[i3] - x[i2], by = y[i3] - y[i2];
+  double cx = x[i3] - x[i1], cy = y[i3] - y[i1];
+  double la = sqrt(ax * ax + ay * ay), lb = sqrt(bx * bx + by * by), lc = sqrt(cx * cx + cy * cy);
+  double k = 2.0 * (ax * cy - ay * cx) / (la * lb * lc);
+  double h = k * lc / 2.0;
+  if (h > 1.0) h = 1.0;
+  if (h < -1.0) h = -1.0;
+  double half = asin(h);
+  double phic = atan2(cy, cx);
+  double arc = fabs(k * lc) < 1e-3 ? lc * (1.0 + (k * lc) * (k * lc) / 24.0) : 2.0 * half / k;
+  s[0] = y[i3];
+  s[1] = z[i3];
+  s[2] = sin(phic + half);
+  s[3] = (z[i3] - z[i1]) / arc;
+  s[4] = k / kfac(P);
+}
+
+/* FP64 fit of measurement points (x, y, zeta in cm, ascending x, n >= 3).
+ * Three passes inward / outward / inward; output at the innermost point. */
+int orc_fit_points(const orc_params* P, int n, const double* x, const double* y, const double* z,
+                   orc_fit* out) {
+  double s[5], C[25];
+  fit_init(P, x, y, z, n, s);
+  double xcur = x[n - 1];
+  int flags = 0, n_used = 0;
+  double chi2 = 0.0;
+  for (int pass = 0; pass < P->fit_passes; pass++) {
+    for (int i = 0; i < 25; i++) C[i] = 0.0;
+    for (int i = 0; i < 5; i++) C[i * 5 + i] = P->c0[i];
+    chi2 = 0.0;
+    n_used = 0;
+    int inward = (pass % 2) == 0;
+    for (int j = 0; j < n; j++) {
+      int i = inward ? n - 1 - j : j;
+      double dx = x[i] - xcur;
+      if (dx != 0.0) {
+        double ns[5], F[25], T[25], Cn[25];
+        if (orc_transport(P, s, dx, ns, F)) { flags |= 1; break; }
+        /* C' = F C F^T */
+        for (int a = 0; a < 5; a++)
+          for (int b = 0; b < 5; b++) {
+            double acc = 0.0;
+            for (int l = 0; l < 5; l++) acc += F[a * 5 + l] * C[l * 5 + b];
+            T[a * 5 + b] = acc;
+          }
+        for (int a = 0; a < 5; a++)
+          for (int b = 0; b < 5; b++) {
+            double acc = 0.0;
+            for (int l = 0; l < 5; l++) acc += T[a * 5 + l] * F[b * 5 + l];
+            Cn[a * 5 + b] = acc;
+          }
+        memcpy(C, Cn, sizeof(Cn));
+        memcpy(s, ns, sizeof(ns));
+        xcur = x[i];
+      }
+      int ok = 1;
+      chi2 += orc_update(P, s, C, y[i], z[i], &ok);
+      if (!ok) flags |= 2;
+      n_used++;
+    }
+  }
+  for (int i = 0; i < 5; i++) out->par[i] = s[i];
+  out->x = xcur;
+  int m = 0;
+  for (int i = 0; i < 5; i++)
+    for (int j = 0; j <= i; j++) out->cov[m++] = C[i * 5 + j];
+  out->chi2 = chi2;
+  out->ndf = 2 * n_used - 5;
+  out->n_used = n_used;
+  out->flags = flags;
+  return 0;
+}
+
+/* Fit of one track given its clusters' integer coordinates (u units, ascending
+ * row).  Measurements are taken relative to the first cluster's exact integer
+ * coordinates, converted to cm, and the reference is added back at the end. */
+int orc_fit_track(const orc_params* P, int n, const int64_t* X, const int64_t* Y, const int64_t* Z,
+                  orc_fit* out) {
+  const double u = 7.8125e-4;
+  double* x = (double*)malloc(sizeof(double) * 3 * n);
+  double *y = x + n, *z = x + 2 * n;
+  for (int i = 0; i < n; i++) {
+    x[i] = (double)X[i] * u;
+    y[i] = (double)(Y[i] - Y[0]) * u;
+    z[i] = (double)(Z[i] - Z[0]) * u;
+  }
+  int rc = orc_fit_points(P, n, x, y, z, out);
+  out->par[0] += (double)Y[0] * u;
+  out->par[1] += (double)Z[0] * u;
+  free(x);
+  return rc;
+}
+
+/* Fit every track produced by orc_merge (cl2trk, n_tracks). */
+int orc_fit_all(const orc_input* in, const orc_params* P, const orc_cluster* cl, int64_t n,
+                const int32_t* cl2trk, int64_t n_tracks, orc_fit* out) {
+  int64_t* cnt = (int64_t*)calloc((size_t)n_tracks + 1, sizeof(int64_t));
+  for (int64_t i = 0; i < n; i++) if (cl2trk[i] >= 0) cnt[cl2trk[i] + 1]++;
+  for (int64_t t = 0; t < n_tracks; t++) cnt[t + 1] += cnt[t];
+  int64_t* lst = (int64_t*)malloc(sizeof(int64_t) * (cnt[n_tracks] + 1));
+  int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * (n_tracks + 1));
+  memcpy(fill, cnt, sizeof(int64_t) * n_tracks);
+  /* cluster indices ascend with row within a sector, so each list is in row order */
+  for (int64_t i = 0; i < n; i++) if (cl2trk[i] >= 0) lst[fill[cl2trk[i]]++] = i;
+  for (int64_t t = 0; t < n_tracks; t++) {
+    int m = (int)(cnt[t + 1] - cnt[t]);
+    int64_t* X = (int64_t*)malloc(sizeof(int64_t) * 3 * m);
+    int64_t *Y = X + m, *Z = X + 2 * m;
+    for (int i = 0; i < m; i++) orc_coords(in, &cl[lst[cnt[t] + i]], &X[i], &Y[i], &Z[i]);
+    orc_fit_track(P, m, X, Y, Z, &out[t]);
+    free(X);
+  }
+  free(cnt); free(lst); free(fill);
+  return 0;
+}
