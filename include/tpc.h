@@ -127,8 +127,8 @@ typedef struct {
   int32_t  ca_cut;           /* 256  straight-line deviation cut, u (0.2 cm) */
   int32_t  min_chain;        /* 5    clusters per kept CA chain */
   int32_t  merge_cut;        /* 384  merge extrapolation cut, u (0.3 cm) */
-  int32_t  merge_gap_min;    /* 2    row(b1) - row(a2) lower bound */
-  int32_t  merge_gap_max;    /* 4    row(b1) - row(a2) upper bound */
+  int32_t  merge_gap_min;    /* 1    row(b1) - row(a2) lower bound */
+  int32_t  merge_gap_max;    /* 6    row(b1) - row(a2) upper bound */
   int32_t  merge_max_passes; /* 8 */
   int32_t  min_track;        /* 10   clusters per output track */
   int32_t  fit_passes;       /* 3    inward, outward, inward */
@@ -185,7 +185,6 @@ typedef struct {
   int16_t  sector;
   uint16_t flags;        /* TPC_TRK_* */
   int32_t  n_fp64;       /* covariance updates redone in FP64 after a failed PD check */
-  int32_t  reserved;
 } tpc_track;
 
 #define TPC_TRK_STOPPED  1u   /* a pass stopped early (|snp| would reach 0.999) */
@@ -305,9 +304,11 @@ tpc_status tpc_get_device_results(tpc_context* ctx, uint64_t ticket, const tpc_c
  * ms[TPC_N_STAGES]. */
 tpc_status tpc_get_stage_times(tpc_context* ctx, uint64_t ticket, float* ms);
 
-/* Counters of a finished ticket: out[0] digits, [1] clusters, [2] kept chains,
- * [3] tracks, [4] FP64 covariance redos, [5] merge passes that merged, [6]
- * device error word, [7] ZS bytes read.  n: entries requested (<= 8). */
+/* Counters of a finished ticket: out[0] clusters, [1] kept chains, [2] tracks,
+ * [3] clusters on tracks, [4] FP64 covariance redos, [5] merge passes that
+ * merged, [6] device error word, [7] ZS bytes of the timeframe, [8] kernel
+ * launches of the last run, [9] runs (1, or 2 after a capacity regrowth).
+ * n: entries requested (<= 10). */
 tpc_status tpc_get_counters(tpc_context* ctx, uint64_t ticket, uint64_t* out, int n);
 
 /* Free the ticket's slot and results.  Unknown ticket: TPC_E_NOTFOUND. */

@@ -1,0 +1,197 @@
+// k_merge.cu — in-sector segment merge and track assembly (step 7 of the
+// library's definition; the paper's section "Hardware and data flow" names the
+// TPC tracking the EPN GPUs run, not its merge rule, which is this library's).
+//
+// A pass: every chain top end (a1 below a2) searches the rows gap_min..gap_max
+// above a2 for chain bottom ends b1 (b2 above) whose four integer straight-line
+// residuals pass the cut; the best bottom per top is kept locally and the best
+// top per bottom by a 64-bit atomicMin on (score << 32 | chain index).  Mutual
+// best pairs link.  Passes repeat until one links nothing; later passes exit at
+// once, so a fixed number of launches gives the fixpoint (graph friendly).
+#include "tpc_internal.cuh"
+
+namespace tpc {
+
+__device__ __forceinline__ unsigned long long n_chains_m(const DevWork& W) {
+  unsigned long long n = W.ctr[CTR_NCH];
+  return n < W.cap_ch ? n : W.cap_ch;
+}
+__device__ __forceinline__ long long floordiv_ll(long long a, long long b) {  // b > 0
+  long long q = a / b;
+  if ((a % b) != 0 && a < 0) q -= 1;
+  return q;
+}
+__device__ __forceinline__ long long absll(long long v) { return v < 0 ? -v : v; }
+// trunc(((yb - y2)(x2 - x1) - (y2 - y1)(xb - x2)) / (x2 - x1))
+__device__ __forceinline__ long long extrap_res(long long x1, long long y1, long long x2, long long y2,
+                                                long long xb, long long yb) {
+  return ((yb - y2) * (x2 - x1) - (y2 - y1) * (xb - x2)) / (x2 - x1);
+}
+__device__ __forceinline__ unsigned lower_bound_tm(const int32_t* __restrict__ t, unsigned lo, unsigned hi, long long v) {
+  while (lo < hi) {
+    unsigned mid = (lo + hi) >> 1;
+    if ((long long)__ldg(t + mid) < v) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void k_merge_best(DevGeom G, DevParams P, DevWork W, int pass) {
+  if (pass > 0 && W.ctr[CTR_MERGED0 + pass - 1] == 0) return;
+  const unsigned long long nch = n_chains_m(W);
+  unsigned long long* bestA = W.best_a + (size_t)(pass & 1) * W.cap_ch;
+  const int R = G.n_rows;
+  const long long MC = P.merge_cut;
+  for (unsigned long long k = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; k < nch;
+       k += (unsigned long long)gridDim.x * blockDim.x) {
+    unsigned long long bestkey = ~0ull;
+    if (W.ch_next[k] < 0) {
+      const int a2 = W.ch_top[k], a1 = W.ch_top2[k];
+      const uint4 rec = __ldg(reinterpret_cast<const uint4*>(W.clusters) + a2);
+      const int r2 = (rec.z >> 24) & 0xff, s = rec.w >> 24;
+      const long long Xa1 = W.cl_x[a1], Ya1 = W.cl_y[a1], Za1 = W.cl_z[a1];
+      const long long Xa2 = W.cl_x[a2], Ya2 = W.cl_y[a2], Za2 = W.cl_z[a2];
+      const long long dxa = Xa2 - Xa1;
+      for (int rb = r2 + P.gap_min; rb <= r2 + P.gap_max && rb < R; rb++) {
+        const long long Xb = G.xrow[rb];
+        const long long zp = Za2 + floordiv_ll((Za2 - Za1) * (Xb - Xa2), dxa);
+        const long long tlo = floordiv_ll(zp - MC - 2, 640) - 3;
+        const long long thi = floordiv_ll(zp + MC + 2, 640) + 3;
+        const unsigned lo = W.row_start[s * R + rb], hi = W.row_start[s * R + rb + 1];
+        for (unsigned b1 = lower_bound_tm(W.cl_t, lo, hi, tlo); b1 < hi; b1++) {
+          if ((long long)__ldg(W.cl_t + b1) > thi) break;
+          const int kb = W.cl_chain[b1];
+          if (kb < 0 || W.ch_root[kb] != (int)b1 || W.ch_prev[kb] >= 0) continue;
+          const int b2 = W.ch_b2[kb];
+          const long long Xb1 = W.cl_x[b1], Yb1 = W.cl_y[b1], Zb1 = W.cl_z[b1];
+          const long long Xb2 = W.cl_x[b2], Yb2 = W.cl_y[b2], Zb2 = W.cl_z[b2];
+          const long long ry = extrap_res(Xa1, Ya1, Xa2, Ya2, Xb1, Yb1);
+          const long long rz = extrap_res(Xa1, Za1, Xa2, Za2, Xb1, Zb1);
+          const long long sy = extrap_res(Xb2, Yb2, Xb1, Yb1, Xa2, Ya2);
+          const long long sz = extrap_res(Xb2, Zb2, Xb1, Zb1, Xa2, Za2);
+          if (absll(ry) > MC || absll(rz) > MC || absll(sy) > MC || absll(sz) > MC) continue;
+          const unsigned long long sc = (unsigned long long)(ry * ry + rz * rz + sy * sy + sz * sz);
+          const unsigned long long key = (sc << 32) | (unsigned)kb;
+          if (key < bestkey) bestkey = key;
+          atomicMin(&bestA[kb], (sc << 32) | (unsigned)k);
+        }
+      }
+    }
+    W.best_b[k] = bestkey;
+  }
+}
+
+__global__ void k_merge_link(DevWork W, int pass) {
+  if (pass > 0 && W.ctr[CTR_MERGED0 + pass - 1] == 0) return;
+  const unsigned long long nch = n_chains_m(W);
+  const unsigned long long* bestA = W.best_a + (size_t)(pass & 1) * W.cap_ch;
+  unsigned long long* nextA = W.best_a + (size_t)((pass + 1) & 1) * W.cap_ch;
+  unsigned int linked = 0;
+  for (unsigned long long k = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; k < nch;
+       k += (unsigned long long)gridDim.x * blockDim.x) {
+    nextA[k] = ~0ull;
+    const unsigned long long key = W.best_b[k];
+    if (key == ~0ull) continue;
+    const unsigned kb = (unsigned)key;
+    if ((unsigned)bestA[kb] == (unsigned)k) {
+      W.ch_next[k] = (int)kb;
+      W.ch_prev[kb] = (int)k;
+      linked++;
+    }
+  }
+  if (linked) atomicAdd(&W.ctr[CTR_MERGED0 + pass], (unsigned long long)linked);
+}
+
+// Group roots (chains with no lower neighbour) sum their group's clusters; a
+// group with >= min_track clusters becomes a track.  The scan value packs
+// (is_track << 32 | clusters) so one scan gives track indices and offsets.
+__global__ void k_groups(DevParams P, DevWork W) {
+  const unsigned long long nch = n_chains_m(W);
+  for (unsigned long long k = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; k < nch;
+       k += (unsigned long long)gridDim.x * blockDim.x) {
+    unsigned long long v = 0;
+    int tot = 0;
+    if (W.ch_prev[k] < 0) {
+      int g = (int)k;
+      for (int it = 0; g >= 0 && it < kMaxRowsDev; it++) { tot += W.ch_len[g]; g = W.ch_next[g]; }
+      if (tot >= P.min_track) v = (1ull << 32) | (unsigned)tot;
+    }
+    W.grp_total[k] = tot;
+    W.scan_val[k] = v;
+  }
+}
+
+__global__ void k_group_assign(DevParams P, DevWork W) {
+  const unsigned long long nch = n_chains_m(W);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const unsigned long long tot = W.ctr[CTR_NCLCL];
+    W.ctr[CTR_NTRK] = tot >> 32;
+  }
+  for (unsigned long long k = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; k < nch;
+       k += (unsigned long long)gridDim.x * blockDim.x) {
+    if (W.ch_prev[k] >= 0) continue;
+    const bool is_trk = W.grp_total[k] >= P.min_track;
+    const unsigned long long v = W.scan_val[k];
+    const int t = is_trk ? (int)(v >> 32) : -1;
+    if (is_trk) {
+      W.trk_first[t] = W.ch_root[k];
+      W.trk_ncl[t] = W.grp_total[k];
+      W.trk_off[t] = (int)(unsigned)v;
+    }
+    int g = (int)k, run = 0;
+    for (int it = 0; g >= 0 && it < kMaxRowsDev; it++) {
+      W.ch_track[g] = t;
+      W.ch_off[g] = run;
+      run += W.ch_len[g];
+      g = W.ch_next[g];
+    }
+  }
+}
+
+__global__ void k_cluster_assign(DevWork W) {
+  unsigned long long n = W.ctr[CTR_NCL];
+  if (n > W.cap_cl) n = W.cap_cl;
+  for (unsigned long long c = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; c < n;
+       c += (unsigned long long)gridDim.x * blockDim.x) {
+    const int k = W.cl_chain[c];
+    int t = -1;
+    if (k >= 0) {
+      t = W.ch_track[k];
+      if (t >= 0) {
+        const int pos = (int)(W.jump[c] >> 32);
+        W.track_cl[W.trk_off[t] + W.ch_off[k] + pos] = (int)c;
+      }
+    }
+    W.cl2trk[c] = t;
+  }
+}
+
+static inline unsigned grid_for_m(unsigned long long cap, int n_sm, int per_sm) {
+  unsigned long long g = (cap + 255) / 256;
+  unsigned long long m = (unsigned long long)n_sm * per_sm;
+  if (g > m) g = m;
+  return (unsigned)(g ? g : 1);
+}
+
+cudaError_t launch_scan(uint64_t* v, const unsigned long long* n_ptr, unsigned long long cap,
+                        unsigned long long* state, unsigned int* ticket, unsigned long long* total, uint32_t* err,
+                        int n_sm, cudaStream_t st);
+
+cudaError_t launch_merge(const DevGeom& G, const DevParams& P, const DevWork& W, int n_sm, cudaStream_t st,
+                         unsigned long long* scan_state_b, int* launches) {
+  const unsigned gc = grid_for_m(W.cap_ch, n_sm, 8);
+  for (int p = 0; p < P.merge_passes; p++) {
+    k_merge_best<<<gc, 256, 0, st>>>(G, P, W, p);
+    k_merge_link<<<gc, 256, 0, st>>>(W, p);
+  }
+  k_groups<<<gc, 256, 0, st>>>(P, W);
+  cudaError_t e = launch_scan(W.scan_val, W.ctr + CTR_NCH, W.cap_ch, scan_state_b, W.tickets + TK_SCAN_B,
+                              W.ctr + CTR_NCLCL, W.err, n_sm, st);
+  if (e != cudaSuccess) return e;
+  k_group_assign<<<gc, 256, 0, st>>>(P, W);
+  const unsigned g = grid_for_m(W.cap_cl, n_sm, 8);
+  k_cluster_assign<<<g, 256, 0, st>>>(W);
+  *launches += 2 * P.merge_passes + 4;
+  return cudaGetLastError();
+}
+
+}  // namespace tpc

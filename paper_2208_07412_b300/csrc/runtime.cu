@@ -1,0 +1,628 @@
+// runtime.cu — host side of the C ABI declared in include/tpc.h.
+//
+// A context owns n_slots slots.  Each slot has its own stream, its own device
+// work space (allocated once, regrown only when a timeframe needs more) and a
+// pinned block of counters that the pipeline copies back at its end, so
+// tpc_poll never needs an extra synchronising copy.  A timeframe's whole
+// pipeline (find -> CA -> merge -> fit) is enqueued on its slot's stream by
+// tpc_submit_timeframe; nothing on the host waits for the device until the
+// caller polls or fetches results.
+#include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "tpc_internal.cuh"
+
+namespace tpc {
+size_t find_smem_bytes(int npmax, int nw);
+cudaError_t launch_find(const DevGeom&, const DevParams&, const DevWork&, unsigned int, int, cudaStream_t);
+cudaError_t launch_ca(const DevGeom&, const DevParams&, const DevWork&, int, cudaStream_t, int*);
+cudaError_t launch_merge(const DevGeom&, const DevParams&, const DevWork&, int, cudaStream_t,
+                         unsigned long long*, int*);
+cudaError_t launch_fit(const DevGeom&, const DevParams&, const DevWork&, int, cudaStream_t, int*);
+size_t scan_tiles(unsigned long long cap);
+}  // namespace tpc
+
+using namespace tpc;
+
+static thread_local std::string g_err;
+static tpc_status fail(tpc_status st, const std::string& msg) {
+  g_err = msg;
+  return st;
+}
+#define CUDA_TRY(expr)                                                                          \
+  do {                                                                                          \
+    cudaError_t e_ = (expr);                                                                    \
+    if (e_ != cudaSuccess)                                                                      \
+      return fail(TPC_E_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_));              \
+  } while (0)
+
+struct tpc_geometry {
+  int n_sectors, n_rows, npmax;
+  std::vector<int> npads, row_x;
+};
+
+namespace {
+
+struct Buf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+struct Slot {
+  int index = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  cudaEvent_t ev_stage[TPC_N_STAGES + 1] = {};
+  cudaEvent_t ev_done = nullptr, ev_input = nullptr;
+  // device buffers
+  Buf pages, offsets, winstate, cl, clx, cly, clz, clt, rowstart, up, down, score, edge, jump, chlen, scanv,
+      scanst, chainof, clchain, ch_i32, besta, bestb, trk_i32, trackcl, cl2trk, tracks, ctrl;
+  unsigned long long* h_ctrl = nullptr;   // pinned copy of [ctr | err]
+  // capacities
+  uint64_t cap_pages = 0, cap_windows = 0, cap_cl = 0, cap_ch = 0;
+  // ticket
+  bool in_use = false;
+  uint64_t ticket = 0;
+  int state = TPC_STATE_QUEUED;
+  tpc_status status = TPC_OK;
+  int runs = 0, launches = 0;
+  // timeframe
+  const void* user_pages = nullptr;
+  const uint64_t* user_offsets = nullptr;
+  uint64_t pages_bytes = 0;
+  unsigned n_windows = 0;
+  uint32_t n_time_bins = 0, tf_flags = 0;
+  DevWork W{};
+};
+
+}  // namespace
+
+struct tpc_context {
+  tpc_geometry geom;
+  tpc_params params;
+  DevGeom G{};
+  DevParams P{};
+  int device = 0, n_sm = 148;
+  uint64_t budget = 0, used = 0;
+  uint32_t flags = 0;
+  std::vector<Slot> slots;
+  uint64_t next_ticket = 1;
+  std::mutex mu;
+};
+
+// ------------------------------------------------------------------ params / geometry
+extern "C" tpc_status tpc_params_default(tpc_params* p) {
+  if (!p) return fail(TPC_E_INVAL, "tpc_params_default: null");
+  std::memset(p, 0, sizeof(*p));
+  p->version = TPC_PARAMS_VERSION;
+  p->q_peak_min = 10;
+  p->ca_slope_y_num = 1; p->ca_slope_y_den = 1;
+  p->ca_slope_z_num = 11; p->ca_slope_z_den = 10;
+  p->ca_cut = 256;
+  p->min_chain = 5;
+  p->merge_cut = 384;
+  p->merge_gap_min = 1; p->merge_gap_max = 6;
+  p->merge_max_passes = 8;
+  p->min_track = 10;
+  p->fit_passes = 3;
+  p->bz = 0.5;
+  p->sigma_y = 0.02; p->sigma_z = 0.03;
+  p->c0[0] = 4.0; p->c0[1] = 4.0; p->c0[2] = 0.25; p->c0[3] = 1.0; p->c0[4] = 100.0;
+  return TPC_OK;
+}
+
+extern "C" tpc_status tpc_create_geometry(const tpc_geometry_desc* d, tpc_geometry** out) {
+  if (!d || !out || !d->npads || !d->row_x) return fail(TPC_E_INVAL, "tpc_create_geometry: null argument");
+  if (d->n_sectors < 1 || d->n_sectors > TPC_MAX_SECTORS) return fail(TPC_E_INVAL, "n_sectors out of range");
+  if (d->n_rows < 3 || d->n_rows > TPC_MAX_ROWS) return fail(TPC_E_INVAL, "n_rows out of range");
+  auto* g = new tpc_geometry;
+  g->n_sectors = d->n_sectors;
+  g->n_rows = d->n_rows;
+  g->npmax = 0;
+  for (int r = 0; r < d->n_rows; r++) {
+    if (d->npads[r] < 3 || d->npads[r] > TPC_MAX_PADS) { delete g; return fail(TPC_E_INVAL, "npads out of range"); }
+    if (d->row_x[r] <= 0 || d->row_x[r] > 1000000 || (r > 0 && d->row_x[r] <= d->row_x[r - 1])) {
+      delete g;
+      return fail(TPC_E_INVAL, "row_x must be positive and strictly increasing");
+    }
+    g->npads.push_back(d->npads[r]);
+    g->row_x.push_back(d->row_x[r]);
+    g->npmax = std::max(g->npmax, d->npads[r]);
+  }
+  *out = g;
+  return TPC_OK;
+}
+
+extern "C" void tpc_destroy_geometry(tpc_geometry* g) { delete g; }
+
+static tpc_status check_params(const tpc_params& p, const tpc_geometry& g) {
+  if (p.version != TPC_PARAMS_VERSION) return fail(TPC_E_INVAL, "params: version mismatch");
+  if (p.q_peak_min < 1 || p.q_peak_min > 1023) return fail(TPC_E_INVAL, "params: q_peak_min out of range");
+  if (p.ca_slope_y_num < 0 || p.ca_slope_y_den < 1 || p.ca_slope_z_num < 0 || p.ca_slope_z_den < 1 ||
+      p.ca_slope_y_num > 1000 || p.ca_slope_z_num > 1000 || p.ca_slope_y_den > 1000 || p.ca_slope_z_den > 1000)
+    return fail(TPC_E_INVAL, "params: CA slopes out of range");
+  if (p.ca_cut < 0 || p.min_chain < 2 || p.min_track < 3) return fail(TPC_E_INVAL, "params: cuts out of range");
+  if (p.merge_cut < 0 || p.merge_cut > 16383 || p.merge_gap_min < 1 || p.merge_gap_max < p.merge_gap_min ||
+      p.merge_max_passes < 0 || p.merge_max_passes > 16)
+    return fail(TPC_E_INVAL, "params: merge settings out of range");
+  if (p.fit_passes < 1 || p.fit_passes > 15 || !(p.sigma_y > 0) || !(p.sigma_z > 0))
+    return fail(TPC_E_INVAL, "params: fit settings out of range");
+  for (int i = 0; i < 5; i++)
+    if (!(p.c0[i] > 0)) return fail(TPC_E_INVAL, "params: c0 must be positive");
+  // CA scores must fit the 41-bit field of the edge-row keys
+  for (int r = 1; r + 1 < g.n_rows; r++) {
+    long double lim = (long double)p.ca_cut * 64.0L * (g.row_x[r + 1] - g.row_x[r - 1]);
+    if (2.0L * lim * lim >= 2199023255552.0L) return fail(TPC_E_INVAL, "params: ca_cut too large for the geometry");
+  }
+  return TPC_OK;
+}
+
+// ------------------------------------------------------------------ buffers
+static void free_buf(Buf& b) {
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+}
+static cudaError_t ensure(Buf& b, size_t bytes) {
+  if (b.bytes >= bytes && b.p) return cudaSuccess;
+  free_buf(b);
+  cudaError_t e = cudaMalloc(&b.p, std::max<size_t>(bytes, 256));
+  if (e == cudaSuccess) b.bytes = std::max<size_t>(bytes, 256);
+  return e;
+}
+
+static size_t slot_bytes(uint64_t pages, uint64_t windows, uint64_t cap_cl, uint64_t cap_ch, int nsr) {
+  size_t b = pages + 16 + windows * 16 + cap_cl * (16 + 16 + 8 + 8 + 8 + 8 + 4 + 8 + 4 + 4 + 4 + 4) +
+             (scan_tiles(cap_cl) + scan_tiles(cap_ch)) * 8 + cap_ch * (12 * 4 + 8 + 16 + sizeof(tpc_track)) +
+             (size_t)(nsr + 1) * 4 + 1024;
+  return b;
+}
+
+static tpc_status slot_reserve(tpc_context* ctx, Slot& s, uint64_t pages_bytes, uint64_t windows,
+                               uint64_t cap_cl, bool need_pages) {
+  const int nsr = ctx->geom.n_sectors * ctx->geom.n_rows;
+  uint64_t cap_ch = cap_cl / (uint64_t)ctx->params.min_chain + 16;
+  uint64_t want_pages = need_pages ? pages_bytes : 0;
+  size_t cur = slot_bytes(s.cap_pages, s.cap_windows, s.cap_cl, s.cap_ch, nsr);
+  size_t need = slot_bytes(std::max(s.cap_pages, want_pages), std::max(s.cap_windows, windows),
+                           std::max(s.cap_cl, cap_cl), std::max(s.cap_ch, cap_ch), nsr);
+  if (ctx->used - cur + need > ctx->budget)
+    return fail(TPC_E_NOMEM, "timeframe needs " + std::to_string(need) + " device bytes; budget left " +
+                                 std::to_string(ctx->budget - ctx->used + cur));
+  if (want_pages > s.cap_pages) { CUDA_TRY(ensure(s.pages, want_pages + 16)); s.cap_pages = want_pages; }
+  if (windows > s.cap_windows) {
+    CUDA_TRY(ensure(s.offsets, windows * 8));
+    CUDA_TRY(ensure(s.winstate, windows * 8));
+    s.cap_windows = windows;
+  }
+  if (cap_cl > s.cap_cl) {
+    CUDA_TRY(ensure(s.cl, cap_cl * 16));
+    CUDA_TRY(ensure(s.clx, cap_cl * 4)); CUDA_TRY(ensure(s.cly, cap_cl * 4));
+    CUDA_TRY(ensure(s.clz, cap_cl * 4)); CUDA_TRY(ensure(s.clt, cap_cl * 4));
+    CUDA_TRY(ensure(s.up, cap_cl * 4)); CUDA_TRY(ensure(s.down, cap_cl * 4));
+    CUDA_TRY(ensure(s.score, cap_cl * 8)); CUDA_TRY(ensure(s.edge, cap_cl * 8));
+    CUDA_TRY(ensure(s.jump, cap_cl * 8)); CUDA_TRY(ensure(s.chlen, cap_cl * 4));
+    CUDA_TRY(ensure(s.scanv, cap_cl * 8));
+    CUDA_TRY(ensure(s.chainof, cap_cl * 4)); CUDA_TRY(ensure(s.clchain, cap_cl * 4));
+    CUDA_TRY(ensure(s.trackcl, cap_cl * 4)); CUDA_TRY(ensure(s.cl2trk, cap_cl * 4));
+    s.cap_cl = cap_cl;
+  }
+  if (cap_ch > s.cap_ch) {
+    CUDA_TRY(ensure(s.ch_i32, cap_ch * 4 * 13));
+    CUDA_TRY(ensure(s.bestb, cap_ch * 8));
+    CUDA_TRY(ensure(s.besta, cap_ch * 16));
+    CUDA_TRY(ensure(s.tracks, cap_ch * sizeof(tpc_track)));
+    s.cap_ch = cap_ch;
+  }
+  CUDA_TRY(ensure(s.scanst, (scan_tiles(s.cap_cl) + scan_tiles(s.cap_ch)) * 8));
+  CUDA_TRY(ensure(s.rowstart, (size_t)(nsr + 1) * 4));
+  CUDA_TRY(ensure(s.ctrl, 256));
+  ctx->used = ctx->used - cur + slot_bytes(s.cap_pages, s.cap_windows, s.cap_cl, s.cap_ch, nsr);
+  // wire the work-space pointers
+  DevWork& W = s.W;
+  W.clusters = (tpc_cluster*)s.cl.p;
+  W.cl_x = (int32_t*)s.clx.p; W.cl_y = (int32_t*)s.cly.p; W.cl_z = (int32_t*)s.clz.p; W.cl_t = (int32_t*)s.clt.p;
+  W.row_start = (uint32_t*)s.rowstart.p;
+  W.win_state = (unsigned long long*)s.winstate.p;
+  W.up = (int32_t*)s.up.p; W.down = (int32_t*)s.down.p;
+  W.score = (int64_t*)s.score.p;
+  W.edge_key = (unsigned long long*)s.edge.p;
+  W.jump = (unsigned long long*)s.jump.p;
+  W.chain_len = (int32_t*)s.chlen.p;
+  W.scan_val = (uint64_t*)s.scanv.p;
+  W.scan_state = (unsigned long long*)s.scanst.p;
+  W.chain_of = (int32_t*)s.chainof.p;
+  W.cl_chain = (int32_t*)s.clchain.p;
+  int32_t* ci = (int32_t*)s.ch_i32.p;
+  const uint64_t C = s.cap_ch;
+  W.ch_root = ci; W.ch_len = ci + C; W.ch_b2 = ci + 2 * C; W.ch_top = ci + 3 * C; W.ch_top2 = ci + 4 * C;
+  W.ch_next = ci + 5 * C; W.ch_prev = ci + 6 * C; W.ch_track = ci + 7 * C; W.ch_off = ci + 8 * C;
+  W.grp_total = ci + 9 * C; W.trk_first = ci + 10 * C; W.trk_ncl = ci + 11 * C; W.trk_off = ci + 12 * C;
+  W.best_b = (unsigned long long*)s.bestb.p;
+  W.best_a = (unsigned long long*)s.besta.p;
+  W.track_cl = (int32_t*)s.trackcl.p;
+  W.cl2trk = (int32_t*)s.cl2trk.p;
+  W.tracks = (tpc_track*)s.tracks.p;
+  W.ctr = (unsigned long long*)s.ctrl.p;
+  W.err = (uint32_t*)((unsigned long long*)s.ctrl.p + CTR_COUNT);
+  W.tickets = (unsigned int*)((unsigned long long*)s.ctrl.p + CTR_COUNT + 1);
+  W.cap_cl = s.cap_cl;
+  W.cap_ch = s.cap_ch;
+  return TPC_OK;
+}
+
+static void slot_free(tpc_context* ctx, Slot& s) {
+  Buf* all[] = {&s.pages, &s.offsets, &s.winstate, &s.cl, &s.clx, &s.cly, &s.clz, &s.clt, &s.rowstart, &s.up,
+                &s.down, &s.score, &s.edge, &s.jump, &s.chlen, &s.scanv, &s.scanst, &s.chainof, &s.clchain,
+                &s.ch_i32, &s.besta, &s.bestb, &s.trk_i32, &s.trackcl, &s.cl2trk, &s.tracks, &s.ctrl};
+  for (Buf* b : all) free_buf(*b);
+  for (auto& e : s.ev_stage) if (e) cudaEventDestroy(e);
+  if (s.ev_done) cudaEventDestroy(s.ev_done);
+  if (s.ev_input) cudaEventDestroy(s.ev_input);
+  if (s.own_stream && s.stream) cudaStreamDestroy(s.stream);
+  if (s.h_ctrl) cudaFreeHost(s.h_ctrl);
+  (void)ctx;
+}
+
+// ------------------------------------------------------------------ context
+extern "C" tpc_status tpc_create_context(const tpc_geometry* geom, const tpc_params* params, int device,
+                                         uint64_t mem_budget, int n_slots, void* stream, uint32_t flags,
+                                         tpc_context** out) {
+  if (!geom || !out) return fail(TPC_E_INVAL, "tpc_create_context: null argument");
+  if (n_slots < 1 || n_slots > 64) return fail(TPC_E_INVAL, "n_slots must be 1..64");
+  tpc_params p;
+  if (params) p = *params; else tpc_params_default(&p);
+  tpc_status st = check_params(p, *geom);
+  if (st) return st;
+  int ndev = 0;
+  CUDA_TRY(cudaGetDeviceCount(&ndev));
+  if (device < 0 || device >= ndev) return fail(TPC_E_INVAL, "no such CUDA device");
+  CUDA_TRY(cudaSetDevice(device));
+  auto* ctx = new tpc_context;
+  ctx->geom = *geom;
+  ctx->params = p;
+  ctx->device = device;
+  ctx->budget = mem_budget ? mem_budget : (8ull << 30);
+  ctx->flags = flags;
+  cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, device);
+  DevGeom& G = ctx->G;
+  G.n_sectors = geom->n_sectors;
+  G.n_rows = geom->n_rows;
+  G.npmax = geom->npmax;
+  G.nw = (geom->npmax + 31) / 32;
+  for (int r = 0; r < geom->n_rows; r++) { G.npads[r] = geom->npads[r]; G.xrow[r] = 64 * geom->row_x[r]; }
+  DevParams& P = ctx->P;
+  P.q_peak_min = p.q_peak_min;
+  P.sy_num = p.ca_slope_y_num; P.sy_den = p.ca_slope_y_den;
+  P.sz_num = p.ca_slope_z_num; P.sz_den = p.ca_slope_z_den;
+  P.ca_cut = p.ca_cut; P.min_chain = p.min_chain;
+  P.merge_cut = p.merge_cut; P.gap_min = p.merge_gap_min; P.gap_max = p.merge_gap_max;
+  P.merge_passes = p.merge_max_passes; P.min_track = p.min_track; P.fit_passes = p.fit_passes;
+  P.kfac_d = -p.bz * 0.299792458 * 1e-2;
+  P.kfac = (float)P.kfac_d;
+  P.sy2_d = p.sigma_y * p.sigma_y; P.sz2_d = p.sigma_z * p.sigma_z;
+  P.sy2 = (float)P.sy2_d; P.sz2 = (float)P.sz2_d;
+  for (int i = 0; i < 5; i++) P.c0[i] = (float)p.c0[i];
+  if (find_smem_bytes(G.npmax, G.nw) > 227 * 1024) { delete ctx; return fail(TPC_E_INVAL, "rows too wide"); }
+  ctx->slots.resize(n_slots);
+  for (int i = 0; i < n_slots; i++) {
+    Slot& s = ctx->slots[i];
+    s.index = i;
+    cudaError_t e = cudaSuccess;
+    if (i == 0 && stream) { s.stream = (cudaStream_t)stream; s.own_stream = false; }
+    else { e = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking); s.own_stream = true; }
+    for (auto& ev : s.ev_stage) if (e == cudaSuccess) e = cudaEventCreate(&ev);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.ev_done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.ev_input, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&s.h_ctrl, 256);
+    if (e != cudaSuccess) {
+      for (auto& s2 : ctx->slots) slot_free(ctx, s2);
+      delete ctx;
+      return fail(TPC_E_CUDA, std::string("context setup: ") + cudaGetErrorString(e));
+    }
+  }
+  *out = ctx;
+  return TPC_OK;
+}
+
+extern "C" void tpc_destroy_context(tpc_context* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  for (auto& s : ctx->slots) {
+    if (s.stream) cudaStreamSynchronize(s.stream);
+    slot_free(ctx, s);
+  }
+  delete ctx;
+}
+
+// ------------------------------------------------------------------ pipeline
+static tpc_status enqueue(tpc_context* ctx, Slot& s) {
+  cudaStream_t st = s.stream;
+  DevWork& W = s.W;
+  DevGeom G = ctx->G;
+  G.n_time_bins = (int)s.n_time_bins;
+  G.n_frag = (int)((s.n_time_bins + kFrag - 1) / kFrag);
+  const bool timing = ctx->flags & TPC_CTX_STAGE_TIMING;
+  s.launches = 0;
+  CUDA_TRY(cudaMemsetAsync(s.ctrl.p, 0, 256, st));
+  CUDA_TRY(cudaMemsetAsync(W.win_state, 0, (size_t)s.n_windows * 8, st));
+  const size_t tiles_a = scan_tiles(s.cap_cl);
+  CUDA_TRY(cudaMemsetAsync(W.scan_state, 0, (tiles_a + scan_tiles(s.cap_ch)) * 8, st));
+  if (timing) CUDA_TRY(cudaEventRecord(s.ev_stage[0], st));
+  CUDA_TRY(launch_find(G, ctx->P, W, s.n_windows, ctx->n_sm, st));
+  s.launches += 1;
+  if (timing) CUDA_TRY(cudaEventRecord(s.ev_stage[1], st));
+  CUDA_TRY(launch_ca(G, ctx->P, W, ctx->n_sm, st, &s.launches));
+  if (timing) CUDA_TRY(cudaEventRecord(s.ev_stage[2], st));
+  CUDA_TRY(launch_merge(G, ctx->P, W, ctx->n_sm, st, (unsigned long long*)W.scan_state + tiles_a, &s.launches));
+  if (timing) CUDA_TRY(cudaEventRecord(s.ev_stage[3], st));
+  CUDA_TRY(launch_fit(G, ctx->P, W, ctx->n_sm, st, &s.launches));
+  if (timing) CUDA_TRY(cudaEventRecord(s.ev_stage[4], st));
+  CUDA_TRY(cudaMemcpyAsync(s.h_ctrl, s.ctrl.p, 256, cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaEventRecord(s.ev_done, st));
+  s.runs++;
+  return TPC_OK;
+}
+
+static Slot* find_ticket(tpc_context* ctx, uint64_t ticket) {
+  for (auto& s : ctx->slots)
+    if (s.in_use && s.ticket == ticket) return &s;
+  return nullptr;
+}
+
+static uint64_t guaranteed_cap_cl(uint64_t pages_bytes) {
+  // a cluster needs a peak digit with its own run (2 B) and 10-bit ADC: > 3 B each
+  return pages_bytes / 3 + 1024;
+}
+
+extern "C" tpc_status tpc_submit_timeframe(tpc_context* ctx, const tpc_timeframe_desc* tf, uint64_t* ticket) {
+  if (!ctx || !tf || !ticket) return fail(TPC_E_INVAL, "tpc_submit_timeframe: null argument");
+  if (tf->n_time_bins < 1 || tf->n_time_bins > 65535) return fail(TPC_E_INVAL, "n_time_bins out of range");
+  if (!tf->pages || !tf->page_offsets || tf->pages_bytes < 32)
+    return fail(TPC_E_INVAL, "pages / page_offsets missing");
+  const bool dev_in = tf->flags & TPC_TF_DEVICE_INPUT;
+  if (dev_in && ((uintptr_t)tf->pages & 15)) return fail(TPC_E_INVAL, "device pages must be 16-byte aligned");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  Slot* s = nullptr;
+  for (auto& c : ctx->slots)
+    if (!c.in_use) { s = &c; break; }
+  if (!s) return fail(TPC_E_BUSY, "no free slot: release a finished ticket first");
+  const unsigned nfrag = (tf->n_time_bins + kFrag - 1) / kFrag;
+  const uint64_t nwin = (uint64_t)ctx->geom.n_sectors * ctx->geom.n_rows * nfrag;
+  if (nwin > 0xffffffffull) return fail(TPC_E_INVAL, "too many windows");
+  uint64_t cap_cl = std::max<uint64_t>(65536, tf->pages_bytes / 12);
+  cap_cl = std::min(cap_cl, guaranteed_cap_cl(tf->pages_bytes));
+  cap_cl = std::max(cap_cl, s->cap_cl);
+  tpc_status st = slot_reserve(ctx, *s, tf->pages_bytes, nwin, cap_cl, !dev_in);
+  if (st) return st;
+  s->pages_bytes = tf->pages_bytes;
+  s->n_windows = (unsigned)nwin;
+  s->n_time_bins = tf->n_time_bins;
+  s->tf_flags = tf->flags;
+  s->runs = 0;
+  if (dev_in) {
+    s->W.pages = (const uint8_t*)tf->pages;
+    s->W.page_offsets = tf->page_offsets;
+  } else {
+    CUDA_TRY(cudaMemcpyAsync(s->pages.p, tf->pages, tf->pages_bytes, cudaMemcpyHostToDevice, s->stream));
+    CUDA_TRY(cudaMemcpyAsync(s->offsets.p, tf->page_offsets, nwin * 8, cudaMemcpyHostToDevice, s->stream));
+    s->W.pages = (const uint8_t*)s->pages.p;
+    s->W.page_offsets = (const uint64_t*)s->offsets.p;
+  }
+  s->W.pages_bytes = tf->pages_bytes;
+  CUDA_TRY(cudaEventRecord(s->ev_input, s->stream));
+  st = enqueue(ctx, *s);
+  if (st) return st;
+  s->in_use = true;
+  s->ticket = ctx->next_ticket++;
+  s->state = TPC_STATE_RUNNING;
+  s->status = TPC_OK;
+  *ticket = s->ticket;
+  return TPC_OK;
+}
+
+static tpc_status status_from_err(uint32_t e) {
+  if (e & kErrCorrupt) return TPC_E_CORRUPT;
+  if (e & kErrTimeout) return TPC_E_TIMEOUT;
+  if (e & (kErrOverflowCl | kErrOverflowCh | kErrRowCount)) return TPC_E_OVERFLOW;
+  return e ? TPC_E_DEVICE : TPC_OK;
+}
+
+// Called with the lock held once ev_done has completed.
+static tpc_status finish(tpc_context* ctx, Slot& s) {
+  const uint32_t e = *(const uint32_t*)(s.h_ctrl + CTR_COUNT);
+  if ((e & (kErrOverflowCl | kErrOverflowCh)) && !(e & (kErrCorrupt | kErrTimeout)) && s.runs == 1) {
+    // regrow to the guaranteed bound and run again (input still resident)
+    uint64_t cap = guaranteed_cap_cl(s.pages_bytes);
+    tpc_status st = slot_reserve(ctx, s, s.pages_bytes, s.n_windows, cap, !(s.tf_flags & TPC_TF_DEVICE_INPUT));
+    if (st) { s.state = TPC_STATE_FAILED; s.status = st; return st; }
+    st = enqueue(ctx, s);
+    if (st) { s.state = TPC_STATE_FAILED; s.status = st; return st; }
+    return TPC_E_NOTREADY;   // still running
+  }
+  tpc_status st = status_from_err(e);
+  if (st) {
+    s.state = TPC_STATE_FAILED;
+    s.status = st;
+    char buf[96];
+    std::snprintf(buf, sizeof buf, "timeframe failed on the device (error word 0x%x)", e);
+    return fail(st, buf);
+  }
+  s.state = TPC_STATE_DONE;
+  return TPC_OK;
+}
+
+extern "C" tpc_status tpc_poll(tpc_context* ctx, uint64_t ticket, uint32_t timeout_us, int32_t* state) {
+  if (!ctx || !state) return fail(TPC_E_INVAL, "tpc_poll: null argument");
+  auto t0 = std::chrono::steady_clock::now();
+  while (true) {
+    {
+      std::lock_guard<std::mutex> lk(ctx->mu);
+      Slot* s = find_ticket(ctx, ticket);
+      if (!s) return fail(TPC_E_NOTFOUND, "unknown ticket");
+      if (s->state == TPC_STATE_DONE || s->state == TPC_STATE_FAILED) {
+        *state = s->state;
+        return s->status ? fail(s->status, "timeframe failed") : TPC_OK;
+      }
+      cudaSetDevice(ctx->device);
+      cudaError_t q = cudaEventQuery(s->ev_done);
+      if (q == cudaSuccess) {
+        tpc_status st = finish(ctx, *s);
+        if (st != TPC_E_NOTREADY) {
+          *state = s->state;
+          return st;
+        }
+      } else if (q != cudaErrorNotReady) {
+        s->state = TPC_STATE_FAILED;
+        s->status = TPC_E_CUDA;
+        *state = s->state;
+        return fail(TPC_E_CUDA, std::string("device error: ") + cudaGetErrorString(q));
+      } else if (s->state == TPC_STATE_RUNNING && cudaEventQuery(s->ev_input) == cudaSuccess) {
+        s->state = TPC_STATE_INPUT_RELEASED;
+      }
+      *state = s->state;
+    }
+    if (timeout_us == 0) return TPC_OK;
+    auto el = std::chrono::duration_cast<std::chrono::microseconds>(std::chrono::steady_clock::now() - t0).count();
+    if (timeout_us != UINT32_MAX && (uint64_t)el >= timeout_us) return fail(TPC_E_TIMEOUT, "tpc_poll timed out");
+    std::this_thread::sleep_for(std::chrono::microseconds(el < 2000 ? 5 : 50));
+  }
+}
+
+static tpc_status done_slot(tpc_context* ctx, uint64_t ticket, Slot** out) {
+  Slot* s = find_ticket(ctx, ticket);
+  if (!s) return fail(TPC_E_NOTFOUND, "unknown ticket");
+  if (s->state == TPC_STATE_FAILED) return fail(s->status, "timeframe failed");
+  if (s->state != TPC_STATE_DONE) return fail(TPC_E_NOTREADY, "timeframe not finished (poll it first)");
+  *out = s;
+  return TPC_OK;
+}
+
+static uint64_t ctr(const Slot& s, int i) { return s.h_ctrl[i]; }
+static uint64_t n_cl_of(const Slot& s) { return std::min<uint64_t>(ctr(s, CTR_NCL), s.cap_cl); }
+static uint64_t n_trk_of(const Slot& s) { return std::min<uint64_t>(ctr(s, CTR_NTRK), s.cap_ch); }
+
+extern "C" tpc_status tpc_get_clusters(tpc_context* ctx, uint64_t ticket, tpc_cluster* out, uint64_t cap,
+                                       uint64_t* n) {
+  if (!ctx || !n) return fail(TPC_E_INVAL, "tpc_get_clusters: null argument");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  Slot* s;
+  tpc_status st = done_slot(ctx, ticket, &s);
+  if (st) return st;
+  *n = n_cl_of(*s);
+  if (!out) return TPC_OK;
+  if (cap < *n) return fail(TPC_E_OVERFLOW, "output buffer too small");
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  if (*n) CUDA_TRY(cudaMemcpyAsync(out, s->W.clusters, *n * sizeof(tpc_cluster), cudaMemcpyDeviceToHost, s->stream));
+  CUDA_TRY(cudaStreamSynchronize(s->stream));
+  return TPC_OK;
+}
+
+extern "C" tpc_status tpc_get_tracks(tpc_context* ctx, uint64_t ticket, tpc_track* out, uint64_t cap, uint64_t* n,
+                                     int32_t* cluster_to_track) {
+  if (!ctx || !n) return fail(TPC_E_INVAL, "tpc_get_tracks: null argument");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  Slot* s;
+  tpc_status st = done_slot(ctx, ticket, &s);
+  if (st) return st;
+  *n = n_trk_of(*s);
+  if (!out && !cluster_to_track) return TPC_OK;
+  if (out && cap < *n) return fail(TPC_E_OVERFLOW, "output buffer too small");
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  if (out && *n) CUDA_TRY(cudaMemcpyAsync(out, s->W.tracks, *n * sizeof(tpc_track), cudaMemcpyDeviceToHost, s->stream));
+  const uint64_t ncl = n_cl_of(*s);
+  if (cluster_to_track && ncl)
+    CUDA_TRY(cudaMemcpyAsync(cluster_to_track, s->W.cl2trk, ncl * 4, cudaMemcpyDeviceToHost, s->stream));
+  CUDA_TRY(cudaStreamSynchronize(s->stream));
+  return TPC_OK;
+}
+
+extern "C" tpc_status tpc_get_links(tpc_context* ctx, uint64_t ticket, int32_t* up, int32_t* down,
+                                    int32_t* chain_of) {
+  if (!ctx) return fail(TPC_E_INVAL, "tpc_get_links: null argument");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  Slot* s;
+  tpc_status st = done_slot(ctx, ticket, &s);
+  if (st) return st;
+  const uint64_t ncl = n_cl_of(*s);
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  if (ncl) {
+    if (up) CUDA_TRY(cudaMemcpyAsync(up, s->W.up, ncl * 4, cudaMemcpyDeviceToHost, s->stream));
+    if (down) CUDA_TRY(cudaMemcpyAsync(down, s->W.down, ncl * 4, cudaMemcpyDeviceToHost, s->stream));
+    if (chain_of) CUDA_TRY(cudaMemcpyAsync(chain_of, s->W.chain_of, ncl * 4, cudaMemcpyDeviceToHost, s->stream));
+  }
+  CUDA_TRY(cudaStreamSynchronize(s->stream));
+  return TPC_OK;
+}
+
+extern "C" tpc_status tpc_get_device_results(tpc_context* ctx, uint64_t ticket, const tpc_cluster** clusters,
+                                             uint64_t* n_clusters, const tpc_track** tracks, uint64_t* n_tracks,
+                                             const int32_t** cluster_to_track) {
+  if (!ctx) return fail(TPC_E_INVAL, "tpc_get_device_results: null argument");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  Slot* s;
+  tpc_status st = done_slot(ctx, ticket, &s);
+  if (st) return st;
+  if (clusters) *clusters = s->W.clusters;
+  if (n_clusters) *n_clusters = n_cl_of(*s);
+  if (tracks) *tracks = s->W.tracks;
+  if (n_tracks) *n_tracks = n_trk_of(*s);
+  if (cluster_to_track) *cluster_to_track = s->W.cl2trk;
+  return TPC_OK;
+}
+
+extern "C" tpc_status tpc_get_stage_times(tpc_context* ctx, uint64_t ticket, float* ms) {
+  if (!ctx || !ms) return fail(TPC_E_INVAL, "tpc_get_stage_times: null argument");
+  if (!(ctx->flags & TPC_CTX_STAGE_TIMING)) return fail(TPC_E_INVAL, "context created without TPC_CTX_STAGE_TIMING");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  Slot* s;
+  tpc_status st = done_slot(ctx, ticket, &s);
+  if (st) return st;
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  for (int i = 0; i < TPC_N_STAGES; i++) CUDA_TRY(cudaEventElapsedTime(&ms[i], s->ev_stage[i], s->ev_stage[i + 1]));
+  return TPC_OK;
+}
+
+extern "C" tpc_status tpc_get_counters(tpc_context* ctx, uint64_t ticket, uint64_t* out, int n) {
+  if (!ctx || !out || n < 0 || n > 10) return fail(TPC_E_INVAL, "tpc_get_counters: bad argument");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  Slot* s = find_ticket(ctx, ticket);
+  if (!s) return fail(TPC_E_NOTFOUND, "unknown ticket");
+  if (s->state != TPC_STATE_DONE && s->state != TPC_STATE_FAILED)
+    return fail(TPC_E_NOTREADY, "timeframe not finished (poll it first)");
+  uint64_t passes = 0;
+  for (int p = 0; p < 16; p++) passes += ctr(*s, CTR_MERGED0 + p) ? 1 : 0;
+  uint64_t v[10] = {ctr(*s, CTR_NCL),
+                    ctr(*s, CTR_NCH),
+                    ctr(*s, CTR_NTRK),
+                    ctr(*s, CTR_NCLCL) & 0xffffffffull,
+                    ctr(*s, CTR_NFP64),
+                    passes,
+                    (uint64_t) * (const uint32_t*)(s->h_ctrl + CTR_COUNT),
+                    s->pages_bytes,
+                    (uint64_t)s->launches,
+                    (uint64_t)s->runs};
+  for (int i = 0; i < n; i++) out[i] = v[i];
+  return TPC_OK;
+}
+
+extern "C" tpc_status tpc_release(tpc_context* ctx, uint64_t ticket) {
+  if (!ctx) return fail(TPC_E_INVAL, "tpc_release: null argument");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  Slot* s = find_ticket(ctx, ticket);
+  if (!s) return fail(TPC_E_NOTFOUND, "unknown ticket");
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(s->stream);
+  s->in_use = false;
+  s->state = TPC_STATE_QUEUED;
+  return TPC_OK;
+}
+
+extern "C" const char* tpc_last_error(void) { return g_err.c_str(); }

@@ -1,0 +1,194 @@
+// tpc_internal.cuh — shared device-side definitions of the B300 TPC library.
+//
+// Everything here belongs to the CUDA path.  The CPU oracle used by the tests
+// is separate code and shares nothing with these files.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/tpc.h"
+
+namespace tpc {
+
+constexpr int kFrag = TPC_FRAGMENT_BINS;     // 256 time bins per window
+constexpr int kHalo = TPC_ZS_HALO;           // 3 time bins of halo each side
+constexpr int kWinT = kFrag + 2 * kHalo;     // 262 plane rows per window
+constexpr int kMaxRowsDev = 256;
+
+// device error word bits
+constexpr uint32_t kErrCorrupt = 1u;         // a ZS page failed validation
+constexpr uint32_t kErrOverflowCl = 2u;      // cluster capacity exceeded
+constexpr uint32_t kErrOverflowCh = 4u;      // chain / track capacity exceeded
+constexpr uint32_t kErrTimeout = 8u;         // a bounded wait gave up
+constexpr uint32_t kErrRowCount = 16u;       // a row holds >= 2^23 clusters (edge keys)
+
+// bounded spin for look-back waits: 4e6 polls of L2 is a few seconds at most
+constexpr long long kSpinLimit = 4000000LL;
+
+// Geometry + parameters, passed by value to every kernel (fits in the 32 KB
+// kernel parameter space).
+struct DevGeom {
+  int n_sectors, n_rows, n_time_bins, n_frag;
+  int npmax, nw;                 // widest row, 32-pad words per plane row
+  int npads[kMaxRowsDev];
+  int xrow[kMaxRowsDev];         // X of each row in u (= 64 * row_x)
+};
+
+struct DevParams {
+  int q_peak_min;
+  int sy_num, sy_den, sz_num, sz_den;
+  int ca_cut, min_chain;
+  int merge_cut, gap_min, gap_max, merge_passes;
+  int min_track, fit_passes;
+  float kfac;                    // curvature per unit q/pT: -bz * c * 1e-2 (1/cm per 1/GeV)
+  float sy2, sz2;                // sigma_y^2, sigma_z^2 (cm^2)
+  float c0[5];
+  double kfac_d, sy2_d, sz2_d;   // FP64 copies for the covariance redo
+};
+
+// Per-slot device work space.  All pointers are device memory owned by the
+// runtime; capacities are in elements.
+struct DevWork {
+  // input
+  const uint8_t* pages;
+  const uint64_t* page_offsets;
+  uint64_t pages_bytes;
+  // finder
+  tpc_cluster* clusters;
+  int32_t* cl_x; int32_t* cl_y; int32_t* cl_z; int32_t* cl_t;
+  uint32_t* row_start;           // [n_sectors * n_rows + 1]
+  unsigned long long* win_state;  // look-back states of the finder windows
+  // CA
+  int32_t* up; int32_t* down;
+  int64_t* score;
+  unsigned long long* edge_key;
+  unsigned long long* jump;      // (dist << 32) | ptr
+  int32_t* chain_len;            // indexed by root cluster
+  uint64_t* scan_val;            // scan inputs / outputs (clusters or chains)
+  unsigned long long* scan_state;
+  int32_t* chain_of;
+  int32_t* cl_chain;
+  // chain table
+  int32_t* ch_root; int32_t* ch_len; int32_t* ch_b2; int32_t* ch_top; int32_t* ch_top2;
+  int32_t* ch_next; int32_t* ch_prev;
+  unsigned long long* best_b;
+  unsigned long long* best_a;    // [2 * cap_chains]
+  int32_t* ch_track; int32_t* ch_off;
+  int32_t* grp_total;
+  // tracks
+  int32_t* trk_first; int32_t* trk_ncl; int32_t* trk_off;
+  int32_t* track_cl;
+  int32_t* cl2trk;
+  tpc_track* tracks;
+  // counters (device scalars, one 64-byte block)
+  unsigned long long* ctr;       // see CTR_* below
+  uint32_t* err;
+  unsigned int* tickets;         // [kNumTickets] atomic ticket counters
+  // capacities
+  uint64_t cap_cl, cap_ch;
+};
+
+enum {
+  CTR_NCL = 0,        // clusters found (may exceed cap_cl on overflow)
+  CTR_NCH = 1,        // kept chains
+  CTR_NTRK = 2,       // tracks
+  CTR_NFP64 = 3,      // FP64 covariance redos
+  CTR_MERGED0 = 4,    // merges in pass p at CTR_MERGED0 + p (up to 16 passes)
+  CTR_NCLCL = 20,     // clusters assigned to tracks
+  CTR_COUNT = 24
+};
+enum { TK_FIND = 0, TK_SCAN_A = 1, TK_SCAN_B = 2, kNumTickets = 4 };
+
+// ------------------------------------------------------------------ helpers
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Inclusive warp scan of a 64-bit value.
+__device__ __forceinline__ unsigned long long warp_incl_scan(unsigned long long v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    unsigned long long n = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += n;
+  }
+  return v;
+}
+
+// Exclusive block scan of one 64-bit value per thread (blockDim.x <= 1024,
+// multiple of 32).  Returns the exclusive prefix; *total gets the block sum.
+// sm: >= 33 entries of shared scratch.
+__device__ __forceinline__ unsigned long long block_excl_scan(unsigned long long v, unsigned long long* sm,
+                                                              unsigned long long* total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  unsigned long long inc = warp_incl_scan(v);
+  if (lane == 31) sm[wid] = inc;
+  __syncthreads();
+  if (wid == 0) {
+    unsigned long long w = lane < nw ? sm[lane] : 0ull;
+    unsigned long long wi = warp_incl_scan(w);
+    if (lane < nw) sm[lane] = wi - w;
+    if (lane == nw - 1) sm[32] = wi;
+  }
+  __syncthreads();
+  unsigned long long r = sm[wid] + inc - v;
+  *total = sm[32];
+  __syncthreads();
+  return r;
+}
+
+// Decoupled look-back (single pass chained scan).  Called by warp 0 of the
+// block owning tile `tile` after it knows its aggregate.  States: bits 63:62 =
+// 0 empty, 1 aggregate, 2 inclusive prefix; bits 61:0 the value.  Tiles are
+// handed out by an atomic ticket, so every predecessor is running or done and
+// publishes its aggregate without waiting: the spin ends.  It is bounded all
+// the same; on expiry the error word gets kErrTimeout and 0 is returned.
+constexpr unsigned long long kStFlagAgg = 1ull << 62, kStFlagPre = 2ull << 62,
+                             kStMask = (1ull << 62) - 1;
+__device__ __forceinline__ unsigned long long lookback_warp0(unsigned long long* state, long long tile,
+                                                             unsigned long long aggregate, uint32_t* err) {
+  const int lane = threadIdx.x & 31;
+  if (tile == 0) {
+    if (lane == 0) st_release_u64(&state[0], kStFlagPre | aggregate);
+    return 0;
+  }
+  if (lane == 0) st_release_u64(&state[tile], kStFlagAgg | aggregate);
+  unsigned long long excl = 0;
+  long long base = tile - 1;
+  long long spins = 0;
+  while (true) {
+    long long j = base - lane;
+    unsigned long long s = j >= 0 ? ld_acquire_u64(&state[j]) : kStFlagPre;
+    unsigned flag = (unsigned)(s >> 62);
+    unsigned empty = __ballot_sync(0xffffffffu, flag == 0);
+    if (empty) {
+      if (++spins > kSpinLimit) {
+        if (lane == 0) atomicOr(err, kErrTimeout);
+        excl = 0;
+        break;
+      }
+      continue;
+    }
+    unsigned pre = __ballot_sync(0xffffffffu, flag == 2);
+    // lanes up to and including the first lane holding a prefix contribute
+    int stop = pre ? __ffs(pre) - 1 : 31;
+    unsigned long long v = lane <= stop ? (s & kStMask) : 0ull;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    excl += v;
+    if (pre) break;
+    base -= 32;
+  }
+  if (lane == 0) st_release_u64(&state[tile], kStFlagPre | (excl + aggregate));
+  return excl;
+}
+
+__device__ __forceinline__ int sector_row_of(const tpc_cluster& c) { return c.sector; }
+
+}  // namespace tpc

@@ -1,0 +1,65 @@
+"""Comparison of the CUDA path's results with the oracle's.
+
+Integers (clusters, CA links, chains, cluster-to-track map, track membership)
+must be bit-exact.  Track parameters must agree within 1e-4 relative with
+floors (y, zeta: 1 cm; snp, tgl: 0.1; q/pT: 0.1 1/GeV) and covariances within
+1e-3 * sqrt(C_ii C_jj) of the FP64 oracle."""
+from __future__ import annotations
+
+import numpy as np
+
+PAR_FLOORS = np.array([1.0, 1.0, 0.1, 0.1, 0.1])
+PAR_RTOL = 1e-4
+COV_RTOL = 1e-3
+TRI = [(i, j) for i in range(5) for j in range(i + 1)]
+
+
+def cluster_bytes(a):
+    return np.ascontiguousarray(a).view(np.uint8).reshape(len(a), 16)
+
+
+def compare_integer(gpu: dict, orc) -> None:
+    gcl, ocl = gpu["clusters"], orc.clusters
+    assert len(gcl) == len(ocl), f"cluster count {len(gcl)} != oracle {len(ocl)}"
+    gb, ob = cluster_bytes(gcl), cluster_bytes(ocl)
+    bad = np.nonzero(np.any(gb != ob, axis=1))[0]
+    assert len(bad) == 0, f"{len(bad)} clusters differ, first {bad[:5]}: gpu {gcl[bad[:2]]} oracle {ocl[bad[:2]]}"
+    for k in ("up", "down", "chain_of", "cl2trk"):
+        g, o = gpu[k], getattr(orc, k)
+        bad = np.nonzero(g != o)[0]
+        assert len(bad) == 0, f"{k}: {len(bad)} differ, first {bad[:5]} gpu {g[bad[:5]]} oracle {o[bad[:5]]}"
+    tr = gpu["tracks"]
+    assert len(tr) == len(orc.track_first)
+    assert np.array_equal(tr["first_cluster"], orc.track_first)
+    assert np.array_equal(tr["n_clusters"], orc.track_ncl)
+
+
+def fit_errors(gpu_tracks, fits):
+    """Per-parameter max |diff| / max(|p|, floor) and max cov deviation in units
+    of sqrt(C_ii C_jj); tracks flagged by either side are excluded."""
+    ok = (gpu_tracks["flags"] == 0) & (fits["flags"] == 0)
+    gp = gpu_tracks["par"][ok].astype(np.float64)
+    op = fits["par"][ok]
+    rel = np.abs(gp - op) / np.maximum(np.abs(op), PAR_FLOORS)
+    gc = gpu_tracks["cov"][ok].astype(np.float64)
+    oc = fits["cov"][ok]
+    diag = [0, 2, 5, 9, 14]
+    cov_dev = np.zeros((ok.sum(), 15))
+    for m, (i, j) in enumerate(TRI):
+        cov_dev[:, m] = np.abs(gc[:, m] - oc[:, m]) / np.sqrt(oc[:, diag[i]] * oc[:, diag[j]])
+    return rel, cov_dev, ok
+
+
+def compare_fit(gpu: dict, orc, min_ok_fraction: float = 0.99) -> dict:
+    tr, fits = gpu["tracks"], orc.fits
+    assert np.array_equal(tr["ndf"][(tr["flags"] == 0) & (fits["flags"] == 0)],
+                          fits["ndf"][(tr["flags"] == 0) & (fits["flags"] == 0)])
+    rel, cov_dev, ok = fit_errors(tr, fits)
+    assert ok.mean() >= min_ok_fraction if len(ok) else True, f"flagged fraction {1 - ok.mean()}"
+    assert np.allclose(tr["x"], fits["x"], rtol=1e-6)
+    report = {"max_rel_par": rel.max(0).tolist() if len(rel) else [0] * 5,
+              "max_cov_dev": float(cov_dev.max()) if cov_dev.size else 0.0,
+              "n_tracks": int(len(tr)), "n_compared": int(ok.sum())}
+    assert np.all(rel <= PAR_RTOL), f"params beyond 1e-4: {report}"
+    assert np.all(cov_dev <= COV_RTOL), f"cov beyond 1e-3: {report}"
+    return report

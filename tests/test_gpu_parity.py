@@ -1,0 +1,144 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle, element by
+element on the same seeded inputs, plus the edge cases of the method."""
+import copy
+
+import numpy as np
+import pytest
+
+import oracle
+import tpcgen
+from parity import compare_fit, compare_integer
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2208_07412_b300 import tpc
+    tpc.load()
+    return tpc
+
+
+def run_gpu(tpc, tf, **kw):
+    with tpc.Reconstructor.for_timeframe(tf, **kw) as R:
+        return R.run(tf)
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3, 4])
+def test_single_sector_parity(lib, seed):
+    tf = tpcgen.generate(tpcgen.single_sector(seed))
+    orc = oracle.reconstruct(tf)
+    gpu = run_gpu(lib, tf)
+    compare_integer(gpu, orc)
+    compare_fit(gpu, orc)
+    assert gpu["counters"]["error_word"] == 0
+
+
+def test_full_tpc_parity(lib):
+    """36 sectors, 1000 time bins, 10,000 tracks: the benchmark workload."""
+    tf = tpcgen.generate(tpcgen.full_tpc(1))
+    orc = oracle.reconstruct(tf)
+    gpu = run_gpu(lib, tf)
+    compare_integer(gpu, orc)
+    rep = compare_fit(gpu, orc)
+    assert rep["n_tracks"] > 10000
+    assert gpu["counters"]["merge_passes"] == orc.merge_passes
+
+
+@pytest.mark.parametrize("n_time_bins", [1, 3, 255, 256, 257, 511, 700])
+def test_ragged_time_ranges(lib, n_time_bins):
+    """Partial last fragment, fragments shorter than the halo, a single bin."""
+    tf = tpcgen.generate(tpcgen.single_sector(5, n_tracks=60, n_time_bins=n_time_bins,
+                                              coll_t0=[n_time_bins - 500.0]))
+    orc = oracle.reconstruct(tf)
+    gpu = run_gpu(lib, tf)
+    compare_integer(gpu, orc)
+    compare_fit(gpu, orc, min_ok_fraction=0.0)
+
+
+def test_empty_and_noise_only(lib):
+    tf = tpcgen.generate(tpcgen.single_sector(6, n_tracks=0))
+    orc = oracle.reconstruct(tf)
+    gpu = run_gpu(lib, tf)
+    compare_integer(gpu, orc)
+    assert len(gpu["tracks"]) == 0
+    # no digits at all: zero threshold above every ADC
+    tf2 = tpcgen.generate(tpcgen.single_sector(6, n_tracks=0, zs_threshold=1024))
+    gpu2 = run_gpu(lib, tf2)
+    assert len(gpu2["clusters"]) == 0 and len(gpu2["tracks"]) == 0
+
+
+def test_dense_occupancy(lib):
+    """Heavy pile-up in one sector: many neighbouring peaks, excluded pixels."""
+    tf = tpcgen.generate(tpcgen.single_sector(8, n_tracks=3000))
+    orc = oracle.reconstruct(tf)
+    gpu = run_gpu(lib, tf)
+    compare_integer(gpu, orc)
+    compare_fit(gpu, orc, min_ok_fraction=0.95)
+
+
+def test_corrupt_page_reported(lib):
+    tf = tpcgen.generate(tpcgen.single_sector(1))
+    bad = copy.copy(tf)
+    bad.pages = tf.pages.copy()
+    o = int(tf.page_offsets[40 * 2 + 1])
+    bad.pages[o + 14] ^= 0xFF  # magic
+    with lib.Reconstructor.for_timeframe(bad) as R:
+        t = R.submit(bad.pages, bad.page_offsets, bad.n_time_bins)
+        with pytest.raises(lib.TpcError) as ei:
+            R.wait(t)
+        assert ei.value.code == -5
+        lib.tpc_release(R.ctx, t)
+        # the context stays usable
+        good = R.run(tf)
+    orc = oracle.reconstruct(tf)
+    compare_integer(good, orc)
+
+
+def test_device_input_matches_host(lib):
+    import torch
+    tf = tpcgen.generate(tpcgen.single_sector(2))
+    host = run_gpu(lib, tf)
+    pages = torch.from_numpy(tf.pages).cuda()
+    offs = torch.from_numpy(tf.page_offsets.view(np.int64)).cuda()
+    with lib.Reconstructor.for_timeframe(tf) as R:
+        t = R.submit(pages, offs, tf.n_time_bins)
+        R.wait(t)
+        cl = lib.tpc_get_clusters(R.ctx, t)
+        tr, m = lib.tpc_get_tracks(R.ctx, t, len(cl))
+        lib.tpc_release(R.ctx, t)
+    assert cl.tobytes() == host["clusters"].tobytes()
+    assert tr.tobytes() == host["tracks"].tobytes()
+    assert np.array_equal(m, host["cl2trk"])
+
+
+def test_slots_in_flight_give_identical_results(lib):
+    """Several timeframes in flight on different slots/streams at once: each
+    result equals the same timeframe run alone (bitwise, the kernels are
+    deterministic)."""
+    tfs = [tpcgen.generate(tpcgen.single_sector(s)) for s in (11, 12, 13)]
+    alone = [run_gpu(lib, tf) for tf in tfs]
+    with lib.Reconstructor.for_timeframe(tfs[0], n_slots=3) as R:
+        tickets = [R.submit(tf.pages, tf.page_offsets, tf.n_time_bins) for tf in tfs]
+        for tf, t, a in zip(tfs, tickets, alone):
+            R.wait(t)
+            cl = lib.tpc_get_clusters(R.ctx, t)
+            tr, m = lib.tpc_get_tracks(R.ctx, t, len(cl))
+            assert cl.tobytes() == a["clusters"].tobytes()
+            assert tr.tobytes() == a["tracks"].tobytes()
+            lib.tpc_release(R.ctx, t)
+
+
+def test_stage_times_and_counters(lib):
+    tf = tpcgen.generate(tpcgen.single_sector(3))
+    with lib.Reconstructor.for_timeframe(tf, flags=lib.TPC_CTX_STAGE_TIMING) as R:
+        t = R.submit(tf.pages, tf.page_offsets, tf.n_time_bins)
+        R.wait(t)
+        ms = lib.tpc_get_stage_times(R.ctx, t)
+        ctr = lib.tpc_get_counters(R.ctx, t)
+        lib.tpc_release(R.ctx, t)
+    assert set(ms) == {"find", "ca", "merge", "fit"} and all(v >= 0 for v in ms.values())
+    assert ctr["kernel_launches"] > 10 and ctr["runs"] == 1 and ctr["error_word"] == 0
