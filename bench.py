@@ -193,7 +193,11 @@ def run_ours(args, world, rank, local):
     torch.cuda.set_device(local)
     make, desc = WORKLOADS[args.workload]
     tf = tpcgen.generate(make(args.seed + rank))
-    stream = torch.cuda.current_stream()
+    # a dedicated stream: the library runs slot 0 on it and the CUDA events
+    # below are recorded on it (the legacy default stream has handle 0, which
+    # the library would replace by a stream of its own)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     R = tpc.Reconstructor.for_timeframe(tf, device=local, stream=stream.cuda_stream,
                                         flags=tpc.TPC_CTX_STAGE_TIMING, mem_budget=16 << 30)
     pages_d = torch.from_numpy(tf.pages).to("cuda")

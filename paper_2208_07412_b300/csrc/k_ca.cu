@@ -40,7 +40,7 @@ __global__ void k_ca_neighbours(DevGeom G, DevParams P, DevWork W) {
     const uint4 rec = __ldg(reinterpret_cast<const uint4*>(W.clusters) + c);
     const int r = (rec.z >> 24) & 0xff, s = rec.w >> 24;
     W.edge_key[c] = ~0ull;
-    if (r == 0 || r == R - 1) {
+    if (r == 0 || r >= R - 1 || s >= G.n_sectors) {
       W.up[c] = -1; W.down[c] = -1; W.score[c] = -1;
       continue;
     }
@@ -91,7 +91,7 @@ __global__ void k_ca_edge_min(DevGeom G, DevWork W) {
        c += (unsigned long long)gridDim.x * blockDim.x) {
     const uint4 rec = __ldg(reinterpret_cast<const uint4*>(W.clusters) + c);
     const int r = (rec.z >> 24) & 0xff, s = rec.w >> 24;
-    if (r != 1 && r != R - 2) continue;
+    if ((r != 1 && r != R - 2) || s >= G.n_sectors) continue;
     const long long sc = W.score[c];
     if (sc < 0) continue;
     const unsigned local = (unsigned)(c - W.row_start[s * R + r]);
@@ -109,7 +109,7 @@ __global__ void k_ca_edge_apply(DevGeom G, DevWork W) {
        c += (unsigned long long)gridDim.x * blockDim.x) {
     const uint4 rec = __ldg(reinterpret_cast<const uint4*>(W.clusters) + c);
     const int r = (rec.z >> 24) & 0xff, s = rec.w >> 24;
-    if (r != 0 && r != R - 1) continue;
+    if ((r != 0 && r != R - 1) || s >= G.n_sectors) continue;
     const unsigned long long key = W.edge_key[c];
     int tgt = -1;
     if (key != ~0ull) {

@@ -46,10 +46,16 @@ __device__ __forceinline__ bool read_header(const DevWork& W, uint64_t off, Page
   return true;
 }
 
+constexpr int kStage = 256;   // clusters staged in shared memory before the look-back
+
 struct FindSmem {
   uint16_t* plane;     // [kWinT][npmax]
   uint32_t* occ;       // [kWinT][nw]
   uint32_t* pk;        // [kWinT][nw]
+  uint16_t* wpre;      // digit rank prefix over the words of plane rows 1..260, [(kWinT-2)*nw + 1]
+  uint16_t* ppre;      // own-peak rank prefix over the words of rows 3..258, [kFrag*nw + 1]
+  uint4* st_rec;       // [kStage] staged cluster records
+  int4* st_xyz;        // [kStage] staged (X, Y, Z, t_peak)
   uint8_t* ent_t;      // [256]
   int32_t* ent_rs;     // [257]
   unsigned long long* scan;  // [34]
@@ -166,10 +172,64 @@ __device__ __forceinline__ bool peak_test(const FindSmem& S, int stride, int nw,
          q >= qat(S, stride, nw, np, tt + 1, p) && q >= qat(S, stride, nw, np, tt + 1, p + 1);
 }
 
+// Index of the last prefix entry <= r in pre[0..n] (pre ascending, pre[0] = 0).
+__device__ __forceinline__ int rank_search(const uint16_t* pre, int n, int r) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if ((int)pre[mid] <= r) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Cluster of the peak at (tt, p): 5x5 window with the inner/outer rule.
+__device__ __forceinline__ void make_cluster(const FindSmem& S, int stride, int nw, int np, int T, int s, int r,
+                                             int f, int tt, int p, int xrow, uint4& rec, int4& xyz) {
+  int Q = 0, Sp = 0, St = 0, Spp = 0, Stt = 0;
+  bool excl = false, other = false;
+#pragma unroll
+  for (int dt = -2; dt <= 2; dt++) {
+#pragma unroll
+    for (int dp = -2; dp <= 2; dp++) {
+      const int q = qat(S, stride, nw, np, tt + dt, p + dp);
+      bool inc;
+      if (dp >= -1 && dp <= 1 && dt >= -1 && dt <= 1) {
+        inc = true;
+      } else {
+        const int ip = dp > 0 ? 1 : (dp < 0 ? -1 : 0), it = dt > 0 ? 1 : (dt < 0 ? -1 : 0);
+        const int qi = qat(S, stride, nw, np, tt + it, p + ip);
+        inc = qi > 0 && q <= qi;
+        if (!inc && q > 0) excl = true;
+      }
+      if (inc) {
+        Q += q; Sp += q * dp; St += q * dt; Spp += q * dp * dp; Stt += q * dt * dt;
+      }
+      if ((dp || dt) && pkat(S, nw, np, tt + dt, p + dp)) other = true;
+    }
+  }
+  const int t_in = tt - kHalo;
+  const int t = kFrag * f + t_in;
+  const long long QQ = Q;
+  const int pad_fp = 256 * p + (int)round_half_up(256LL * Sp, QQ);
+  const int time_fp = 128 * (t_in + 4) + (int)round_half_up(128LL * St, QQ);
+  const long long vp = round_half_up(16LL * ((long long)Spp * QQ - (long long)Sp * Sp), QQ * QQ);
+  const long long vt = round_half_up(16LL * ((long long)Stt * QQ - (long long)St * St), QQ * QQ);
+  const int flags = ((p == 0 || p == np - 1 || t == 0 || t == T - 1) ? TPC_CL_EDGE : 0) |
+                    (excl ? TPC_CL_EXCLUDED : 0) | (other ? TPC_CL_NEIGHBOUR : 0);
+  rec.x = (uint32_t)(pad_fp & 0xffff) | ((uint32_t)(time_fp & 0xffff) << 16);
+  rec.y = (uint32_t)S.plane[tt * stride + p] | ((uint32_t)min(Q, 65535) << 16);
+  rec.z = (uint32_t)min(vp, 255LL) | ((uint32_t)min(vt, 255LL) << 8) | ((uint32_t)flags << 16) |
+          ((uint32_t)r << 24);
+  rec.w = (uint32_t)t | ((uint32_t)p << 16) | ((uint32_t)s << 24);
+  xyz = make_int4(xrow, 2 * (pad_fp - 128 * (np - 1)), 5 * (32768 * f + time_fp - 512), t);
+}
+
 __global__ void __launch_bounds__(kFindThreads, 2)
 k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int stride = G.npmax, nw = G.nw;
+  const int nrow_words = (kWinT - 2) * nw;   // plane rows 1 .. 260
+  const int nown_words = kFrag * nw;         // plane rows 3 .. 258
   FindSmem S;
   {
     size_t o = 0;
@@ -180,17 +240,25 @@ k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
     S.pk = reinterpret_cast<uint32_t*>(smem_raw + o);
     o += (size_t)kWinT * nw * 4;
     o = (o + 15) & ~(size_t)15;
+    S.st_rec = reinterpret_cast<uint4*>(smem_raw + o);
+    o += kStage * 16;
+    S.st_xyz = reinterpret_cast<int4*>(smem_raw + o);
+    o += kStage * 16;
     S.scan = reinterpret_cast<unsigned long long*>(smem_raw + o);
     o += 34 * 8;
     S.ent_rs = reinterpret_cast<int32_t*>(smem_raw + o);
     o += 260 * 4;
     S.misc = reinterpret_cast<int32_t*>(smem_raw + o);
     o += 16 * 4;
+    S.wpre = reinterpret_cast<uint16_t*>(smem_raw + o);
+    o += ((size_t)nrow_words + 1) * 2;
+    S.ppre = reinterpret_cast<uint16_t*>(smem_raw + o);
+    o += ((size_t)nown_words + 1) * 2;
     S.ent_t = reinterpret_cast<uint8_t*>(smem_raw + o);
   }
   const int tid = threadIdx.x;
-  const int nrow_words = (kWinT - 2) * nw;                 // plane rows 1 .. 260
   const int wpt = (nrow_words + blockDim.x - 1) / blockDim.x;
+  const int opt = (nown_words + blockDim.x - 1) / blockDim.x;
 
   while (true) {
     if (tid == 0) S.misc[0] = (int)atomicAdd(&W.tickets[TK_FIND], 1u);
@@ -205,7 +273,7 @@ k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
     const int np = G.npads[r];
     const int T = G.n_time_bins;
 
-    // ---- decode own page and the neighbours' halos
+    // ---- 1. decode own page and the neighbours' halos
     PageHdr h;
     uint64_t off = W.page_offsets[w];
     bool ok = read_header(W, off, h) && h.sector == s && h.row == r && h.frag == f;
@@ -229,102 +297,101 @@ k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
                        T, false, S);
     }
     if (!ok && tid == 0) atomicOr(W.err, kErrCorrupt);
+
+    // ---- 2. rank the digits of rows 1..260 (popcount prefix over the bitmap words)
+    int ndig = 0;
+    {
+      const int w0 = tid * wpt, w1 = min(w0 + wpt, nrow_words);
+      int c = 0;
+      for (int i = w0; i < w1; i++) c += __popc(S.occ[nw + i]);
+      unsigned long long tot;
+      unsigned long long pre = block_excl_scan((unsigned long long)c, S.scan, &tot);
+      int run = (int)pre;
+      for (int i = w0; i < w1; i++) { S.wpre[i] = (uint16_t)run; run += __popc(S.occ[nw + i]); }
+      if (tid == 0) S.wpre[nrow_words] = (uint16_t)tot;
+      // the pk words of rows 1..260 are rebuilt by atomicOr below
+      for (int i = w0; i < w1; i++) S.pk[nw + i] = 0u;
+      ndig = ok ? (int)tot : 0;
+    }
     __syncthreads();
 
-    // ---- peak test over plane rows 1..260 (own rows are 3..258)
-    int cnt = 0;
-    const int w0 = tid * wpt, w1 = min(w0 + wpt, nrow_words);
-    if (ok) {
-      for (int wi_ = w0; wi_ < w1; wi_++) {
-        const int tt = 1 + wi_ / nw, wi = wi_ % nw;
-        uint32_t bits = S.occ[tt * nw + wi];
-        uint32_t pkw = 0;
-        while (bits) {
-          const int b = __ffs(bits) - 1;
-          bits &= bits - 1;
-          const int p = wi * 32 + b;
-          const int q = S.plane[tt * stride + p];
-          if (q >= P.q_peak_min && peak_test(S, stride, nw, np, tt, p, q)) {
-            pkw |= 1u << b;
-            if (tt >= kHalo && tt < kHalo + kFrag) cnt++;
-          }
-        }
-        S.pk[tt * nw + wi] = pkw;
-      }
+    // ---- 3. peak test, one digit per thread (balanced)
+    for (int rk = tid; rk < ndig; rk += blockDim.x) {
+      const int wi_ = rank_search(S.wpre, nrow_words + 1, rk);
+      const uint32_t word = S.occ[nw + wi_];
+      const int bit = __fns(word, 0, rk - (int)S.wpre[wi_] + 1);
+      const int tt = 1 + wi_ / nw, p = (wi_ % nw) * 32 + bit;
+      const int q = S.plane[tt * stride + p];
+      if (q >= P.q_peak_min && peak_test(S, stride, nw, np, tt, p, q)) atomicOr(&S.pk[tt * nw + (p >> 5)], 1u << bit);
     }
-    unsigned long long tot;
-    const unsigned long long mine = block_excl_scan((unsigned long long)cnt, S.scan, &tot);
-    // ---- global offset of this window
+    __syncthreads();
+
+    // ---- 4. rank the own peaks (rows 3..258) and publish the window's count
+    int npk;
+    {
+      const int w0 = tid * opt, w1 = min(w0 + opt, nown_words);
+      int c = 0;
+      for (int i = w0; i < w1; i++) c += __popc(S.pk[kHalo * nw + i]);
+      unsigned long long tot;
+      unsigned long long pre = block_excl_scan((unsigned long long)c, S.scan, &tot);
+      int run = (int)pre;
+      for (int i = w0; i < w1; i++) { S.ppre[i] = (uint16_t)run; run += __popc(S.pk[kHalo * nw + i]); }
+      if (tid == 0) {
+        S.ppre[nown_words] = (uint16_t)tot;
+        lookback_publish(W.win_state, (long long)w, tot);
+      }
+      npk = (int)tot;
+    }
+    __syncthreads();
+
+    // ---- 5. clusters of the first kStage peaks, staged in shared memory
+    const int nst = min(npk, kStage);
+    for (int k = tid; k < nst; k += blockDim.x) {
+      const int wi_ = rank_search(S.ppre, nown_words + 1, k);
+      const uint32_t word = S.pk[kHalo * nw + wi_];
+      const int bit = __fns(word, 0, k - (int)S.ppre[wi_] + 1);
+      const int tt = kHalo + wi_ / nw, p = (wi_ % nw) * 32 + bit;
+      make_cluster(S, stride, nw, np, T, s, r, f, tt, p, G.xrow[r], S.st_rec[k], S.st_xyz[k]);
+    }
+
+    // ---- 6. global offset of this window (decoupled look-back)
     if (tid < 32) {
-      unsigned long long base = lookback_warp0(W.win_state, (long long)w, tot, W.err);
+      const unsigned long long base = lookback_wait(W.win_state, (long long)w, (unsigned long long)npk, W.err);
       if (tid == 0) {
         S.scan[33] = base;
-        if (f == 0) W.row_start[sr] = (uint32_t)min(base, (unsigned long long)0xffffffffu);
+        // row starts are clamped to the capacity so that, after an overflow,
+        // every later kernel still indexes inside the cluster arrays
+        if (f == 0) W.row_start[sr] = (uint32_t)min(base, (unsigned long long)W.cap_cl);
         if (w == n_windows - 1) {
-          W.row_start[G.n_sectors * G.n_rows] = (uint32_t)min(base + tot, (unsigned long long)0xffffffffu);
-          W.ctr[CTR_NCL] = base + tot;
+          W.row_start[G.n_sectors * G.n_rows] = (uint32_t)min(base + npk, (unsigned long long)W.cap_cl);
+          W.ctr[CTR_NCL] = base + npk;
         }
-        if (base + tot > W.cap_cl) atomicOr(W.err, kErrOverflowCl);
+        if (base + npk > W.cap_cl) atomicOr(W.err, kErrOverflowCl);
       }
     }
     __syncthreads();
     const unsigned long long base = S.scan[33];
-    // ---- clusters, written in canonical order at their final index
-    if (ok && cnt && base + tot <= W.cap_cl) {
-      unsigned long long idx = base + mine;
-      for (int wi_ = w0; wi_ < w1; wi_++) {
-        const int tt = 1 + wi_ / nw, wi = wi_ % nw;
-        if (tt < kHalo || tt >= kHalo + kFrag) continue;
-        uint32_t bits = S.pk[tt * nw + wi];
-        while (bits) {
-          const int b = __ffs(bits) - 1;
-          bits &= bits - 1;
-          const int p = wi * 32 + b;
-          int Q = 0, Sp = 0, St = 0, Spp = 0, Stt = 0;
-          bool excl = false, other = false;
-#pragma unroll
-          for (int dt = -2; dt <= 2; dt++) {
-#pragma unroll
-            for (int dp = -2; dp <= 2; dp++) {
-              const int q = qat(S, stride, nw, np, tt + dt, p + dp);
-              bool inc;
-              if (dp >= -1 && dp <= 1 && dt >= -1 && dt <= 1) {
-                inc = true;
-              } else {
-                const int ip = dp > 0 ? 1 : (dp < 0 ? -1 : 0), it = dt > 0 ? 1 : (dt < 0 ? -1 : 0);
-                const int qi = qat(S, stride, nw, np, tt + it, p + ip);
-                inc = qi > 0 && q <= qi;
-                if (!inc && q > 0) excl = true;
-              }
-              if (inc) {
-                Q += q; Sp += q * dp; St += q * dt; Spp += q * dp * dp; Stt += q * dt * dt;
-              }
-              if ((dp || dt) && pkat(S, nw, np, tt + dt, p + dp)) other = true;
-            }
-          }
-          const int t_in = tt - kHalo;
-          const int t = kFrag * f + t_in;
-          const long long QQ = Q;
-          const int pad_fp = 256 * p + (int)round_half_up(256LL * Sp, QQ);
-          const int time_fp = 128 * (t_in + 4) + (int)round_half_up(128LL * St, QQ);
-          long long vp = round_half_up(16LL * ((long long)Spp * QQ - (long long)Sp * Sp), QQ * QQ);
-          long long vt = round_half_up(16LL * ((long long)Stt * QQ - (long long)St * St), QQ * QQ);
-          const int flags = ((p == 0 || p == np - 1 || t == 0 || t == T - 1) ? TPC_CL_EDGE : 0) |
-                            (excl ? TPC_CL_EXCLUDED : 0) | (other ? TPC_CL_NEIGHBOUR : 0);
-          uint4 rec;
-          rec.x = (uint32_t)(pad_fp & 0xffff) | ((uint32_t)(time_fp & 0xffff) << 16);
-          rec.y = (uint32_t)S.plane[tt * stride + p] | ((uint32_t)min(Q, 65535) << 16);
-          rec.z = (uint32_t)min(vp, 255LL) | ((uint32_t)min(vt, 255LL) << 8) | ((uint32_t)flags << 16) |
-                  ((uint32_t)r << 24);
-          rec.w = (uint32_t)t | ((uint32_t)p << 16) | ((uint32_t)s << 24);
-          reinterpret_cast<uint4*>(W.clusters)[idx] = rec;
-          W.cl_x[idx] = G.xrow[r];
-          W.cl_y[idx] = 2 * (pad_fp - 128 * (np - 1));
-          W.cl_z[idx] = 5 * (32768 * f + time_fp - 512);
-          W.cl_t[idx] = t;
-          idx++;
-        }
+
+    // ---- 7. write out (coalesced), then any peaks beyond the staging buffer
+    for (int k = tid; k < npk; k += blockDim.x) {
+      const unsigned long long idx = base + k;
+      if (idx >= W.cap_cl) break;   // overflow: keep [0, cap) free of gaps, drop the rest
+      uint4 rec;
+      int4 xyz;
+      if (k < kStage) {
+        rec = S.st_rec[k];
+        xyz = S.st_xyz[k];
+      } else {
+        const int wi_ = rank_search(S.ppre, nown_words + 1, k);
+        const uint32_t word = S.pk[kHalo * nw + wi_];
+        const int bit = __fns(word, 0, k - (int)S.ppre[wi_] + 1);
+        make_cluster(S, stride, nw, np, T, s, r, f, kHalo + wi_ / nw, (wi_ % nw) * 32 + bit, G.xrow[r], rec, xyz);
       }
+      reinterpret_cast<uint4*>(W.clusters)[idx] = rec;
+      W.cl_x[idx] = xyz.x;
+      W.cl_y[idx] = xyz.y;
+      W.cl_z[idx] = xyz.z;
+      W.cl_t[idx] = xyz.w;
     }
     __syncthreads();
   }
@@ -334,7 +401,9 @@ size_t find_smem_bytes(int npmax, int nw) {
   size_t o = ((size_t)kWinT * npmax * 2 + 15) & ~(size_t)15;
   o += 2 * (size_t)kWinT * nw * 4;
   o = (o + 15) & ~(size_t)15;
-  o += 34 * 8 + 260 * 4 + 16 * 4 + 256;
+  o += 2 * kStage * 16 + 34 * 8 + 260 * 4 + 16 * 4;
+  o += ((size_t)(kWinT - 2) * nw + 1) * 2 + ((size_t)kFrag * nw + 1) * 2;
+  o += 256;
   return o;
 }
 

@@ -4,9 +4,11 @@
 //
 // One thread per track, the 5-parameter state and its covariance in FP32
 // registers.  Exact helix transport (chord form), analytic Jacobian, (y, zeta)
-// measurement updates C' = C - K H C then symmetrised.  An update whose result
-// fails the positive-definiteness check is recomputed in FP64 from the
-// pre-update state and counted; FP64 is used nowhere else.  Measurements are
+// measurement updates.  The covariance is kept as U D U^T factors (below): the
+// same Kalman filter in exact arithmetic, far less rounding loss in FP32.  An
+// update whose result fails the positive-definiteness check (a D entry not
+// positive) is recomputed in FP64 from the pre-update state and counted; FP64
+// is used nowhere else.  Measurements are
 // integer coordinates relative to the track's first cluster, so they reach
 // FP32 exactly before the single scaling to cm.
 #include "tpc_internal.cuh"
@@ -68,62 +70,86 @@ __device__ __forceinline__ bool transport(float kfac, float* s, float dx, Jac<fl
   return true;
 }
 
-// C <- F C F^T for the sparse helix Jacobian (full symmetric 5x5 storage).
+// The covariance is carried in factored form C = U D U^T (U unit upper
+// triangular, D diagonal).  Exact arithmetic gives the same C as the plain
+// update C' = C - K H C; in FP32 the factored form keeps the information that
+// the plain form loses to cancellation once C is highly correlated (the
+// classical argument for square-root filters).  With the state ordered (y,
+// zeta, snp, tgl, q/pT) the helix Jacobian F is unit upper triangular, so the
+// time update C' = F C F^T is U' = F U with D unchanged: no re-factorisation.
 template <typename T>
-__device__ __forceinline__ void propagate_cov(T C[5][5], const Jac<T>& J) {
-  T Tm[5][5];
-#pragma unroll
-  for (int j = 0; j < 5; j++) {
-    Tm[0][j] = C[0][j] + J.a * C[2][j] + J.b * C[4][j];
-    Tm[1][j] = C[1][j] + J.e * C[2][j] + J.g * C[3][j] + J.h * C[4][j];
-    Tm[2][j] = C[2][j] + J.m * C[4][j];
-    Tm[3][j] = C[3][j];
-    Tm[4][j] = C[4][j];
-  }
+struct UD {
+  T u[5][5];   // only i < j used (unit diagonal implied)
+  T d[5];
+};
+
+template <typename T>
+__device__ __forceinline__ void ud_reset(UD<T>& M, const float* c0) {
 #pragma unroll
   for (int i = 0; i < 5; i++) {
-    C[i][0] = Tm[i][0] + J.a * Tm[i][2] + J.b * Tm[i][4];
-    C[i][1] = Tm[i][1] + J.e * Tm[i][2] + J.g * Tm[i][3] + J.h * Tm[i][4];
-    C[i][2] = Tm[i][2] + J.m * Tm[i][4];
-    C[i][3] = Tm[i][3];
-    C[i][4] = Tm[i][4];
+    M.d[i] = T(c0[i]);
+#pragma unroll
+    for (int j = 0; j < 5; j++) M.u[i][j] = T(0);
   }
 }
 
-// Kalman update with measurement (my, mz); returns the chi2 increment and
-// whether the result passed the PD check.
+// U <- F U for the sparse unit upper triangular Jacobian.
 template <typename T>
-__device__ __forceinline__ T kf_update(T s[5], T C[5][5], T my, T mz, T sy2, T sz2, bool& pd) {
-  const T S00 = C[0][0] + sy2, S01 = C[1][0], S11 = C[1][1] + sz2;
-  const T det = S00 * S11 - S01 * S01;
-  const T I00 = S11 / det, I01 = -S01 / det, I11 = S00 / det;
-  const T r0 = my - s[0], r1 = mz - s[1];
-  T K[5][2];
+__device__ __forceinline__ void ud_propagate(UD<T>& M, const Jac<T>& J) {
+  T(&u)[5][5] = M.u;
+  // row 0: + a * row2 + b * row4  (row4 of U = e4, row2 = (0,0,1,u23,u24))
+  u[0][2] += J.a;
+  u[0][3] += J.a * u[2][3];
+  u[0][4] += J.a * u[2][4] + J.b;
+  // row 1: + e * row2 + g * row3 + h * row4
+  u[1][2] += J.e;
+  u[1][3] += J.e * u[2][3] + J.g;
+  u[1][4] += J.e * u[2][4] + J.g * u[3][4] + J.h;
+  // row 2: + m * row4
+  u[2][4] += J.m;
+}
+
+// Bierman's scalar measurement update of component `row` (0: y, 1: zeta) with
+// variance r.  Updates the state and the factors; returns innovation^2 / its
+// variance (the chi2 increment).
+template <typename T, int ROW>
+__device__ __forceinline__ T ud_update(T s[5], UD<T>& M, T z, T r) {
+  T f[5], v[5], b[5];
 #pragma unroll
-  for (int i = 0; i < 5; i++) {
-    K[i][0] = C[i][0] * I00 + C[i][1] * I01;
-    K[i][1] = C[i][0] * I01 + C[i][1] * I11;
+  for (int j = 0; j < 5; j++) {
+    f[j] = (j < ROW) ? T(0) : (j == ROW ? T(1) : M.u[ROW][j]);
+    v[j] = M.d[j] * f[j];
   }
+  T alpha = r + v[0] * f[0];
+  M.d[0] = M.d[0] * r / alpha;
+  b[0] = v[0];
 #pragma unroll
-  for (int i = 0; i < 5; i++) s[i] += K[i][0] * r0 + K[i][1] * r1;
-  T N[5][5];
+  for (int j = 1; j < 5; j++) {
+    const T beta = alpha;
+    alpha = alpha + v[j] * f[j];
+    const T lam = -f[j] / beta;
+    M.d[j] = M.d[j] * beta / alpha;
 #pragma unroll
-  for (int i = 0; i < 5; i++)
+    for (int i = 0; i < j; i++) {
+      const T uo = M.u[i][j];
+      M.u[i][j] = uo + lam * b[i];
+      b[i] = b[i] + v[j] * uo;
+    }
+    b[j] = v[j];
+  }
+  const T innov = z - s[ROW];
+  const T ia = T(1) / alpha;
 #pragma unroll
-    for (int j = 0; j < 5; j++) N[i][j] = C[i][j] - (K[i][0] * C[0][j] + K[i][1] * C[1][j]);
+  for (int i = 0; i < 5; i++) s[i] += b[i] * ia * innov;
+  return innov * innov * ia;
+}
+
+template <typename T>
+__device__ __forceinline__ bool ud_pd(const UD<T>& M) {
   bool ok = true;
 #pragma unroll
-  for (int i = 0; i < 5; i++)
-#pragma unroll
-    for (int j = 0; j < 5; j++) C[i][j] = T(0.5) * (N[i][j] + N[j][i]);
-#pragma unroll
-  for (int i = 0; i < 5; i++) ok = ok && (C[i][i] > T(0));
-#pragma unroll
-  for (int i = 0; i < 5; i++)
-#pragma unroll
-    for (int j = i + 1; j < 5; j++) ok = ok && (C[i][j] * C[i][j] < C[i][i] * C[j][j]);
-  pd = ok;
-  return r0 * (I00 * r0 + I01 * r1) + r1 * (I01 * r0 + I11 * r1);
+  for (int i = 0; i < 5; i++) ok = ok && (M.d[i] > T(0)) && (M.d[i] < T(1e30));
+  return ok;
 }
 
 __global__ void __launch_bounds__(128)
@@ -151,15 +177,12 @@ k_fit(DevGeom G, DevParams P, DevWork W) {
     const float arc = fabsf(klc) < 1e-3f ? lc * (1.f + klc * klc * (1.f / 24.f)) : 2.f * half / kc;
     const float zo = (float)(W.cl_z[co] - Z0) * kU;
     float s[5] = {cy, zo, sinf(phic + half), zo / arc, kc / P.kfac};
-    float C[5][5];
+    UD<float> M;
     int xcur = W.cl_x[co];
     int flags = 0, n_used = 0, nfp64 = 0;
     float chi2 = 0.f;
     for (int pass = 0; pass < P.fit_passes; pass++) {
-#pragma unroll
-      for (int i = 0; i < 5; i++)
-#pragma unroll
-        for (int j = 0; j < 5; j++) C[i][j] = (i == j) ? P.c0[i] : 0.f;
+      ud_reset(M, P.c0);
       chi2 = 0.f;
       n_used = 0;
       const bool inward = (pass & 1) == 0;
@@ -170,46 +193,45 @@ k_fit(DevGeom G, DevParams P, DevWork W) {
         if (Xi != xcur) {
           Jac<float> J;
           if (!transport(P.kfac, s, (float)(Xi - xcur) * kU, J)) { flags |= TPC_TRK_STOPPED; break; }
-          propagate_cov(C, J);
+          ud_propagate(M, J);
           xcur = Xi;
         }
-        const float my = (float)(W.cl_y[c] - Y0) * kU, mz = (float)(W.cl_z[c] - Z0) * kU;
-        float s0[5], C0[5][5];
+        const int dY = W.cl_y[c] - Y0, dZ = W.cl_z[c] - Z0;
+        float s0[5];
+        UD<float> M0 = M;
 #pragma unroll
-        for (int a = 0; a < 5; a++) {
-          s0[a] = s[a];
-#pragma unroll
-          for (int b = 0; b < 5; b++) C0[a][b] = C[a][b];
-        }
-        bool pd;
-        float dchi = kf_update<float>(s, C, my, mz, P.sy2, P.sz2, pd);
-        if (!pd) {
+        for (int a = 0; a < 5; a++) s0[a] = s[a];
+        float dchi = ud_update<float, 0>(s, M, (float)dY * kU, P.sy2);
+        dchi += ud_update<float, 1>(s, M, (float)dZ * kU, P.sz2);
+        if (!ud_pd(M)) {
           // redo this update in FP64 from the pre-update state
-          double sd[5], Cd[5][5];
+          double sd[5];
+          UD<double> Md;
 #pragma unroll
           for (int a = 0; a < 5; a++) {
             sd[a] = s0[a];
+            Md.d[a] = M0.d[a];
 #pragma unroll
-            for (int b = 0; b < 5; b++) Cd[a][b] = C0[a][b];
+            for (int b = 0; b < 5; b++) Md.u[a][b] = M0.u[a][b];
           }
-          bool pdd;
-          double dd = kf_update<double>(sd, Cd, (double)(W.cl_y[c] - Y0) * kUd, (double)(W.cl_z[c] - Z0) * kUd,
-                                        P.sy2_d, P.sz2_d, pdd);
+          double dd = ud_update<double, 0>(sd, Md, (double)dY * kUd, P.sy2_d);
+          dd += ud_update<double, 1>(sd, Md, (double)dZ * kUd, P.sz2_d);
+          if (!ud_pd(Md)) flags |= TPC_TRK_NOT_PD;
 #pragma unroll
           for (int a = 0; a < 5; a++) {
             s[a] = (float)sd[a];
+            M.d[a] = (float)Md.d[a];
 #pragma unroll
-            for (int b = 0; b < 5; b++) C[a][b] = (float)Cd[a][b];
+            for (int b = 0; b < 5; b++) M.u[a][b] = (float)Md.u[a][b];
           }
           dchi = (float)dd;
-          if (!pdd) flags |= TPC_TRK_NOT_PD;
           nfp64++;
         }
         chi2 += dchi;
         n_used++;
       }
     }
-    // ---- emit
+    // ---- emit: C = U D U^T
     tpc_track out;
     out.par[0] = s[0] + (float)Y0 * kU;
     out.par[1] = s[1] + (float)Z0 * kU;
@@ -224,7 +246,12 @@ k_fit(DevGeom G, DevParams P, DevWork W) {
 #pragma unroll
     for (int i = 0; i < 5; i++)
 #pragma unroll
-      for (int j = 0; j <= i; j++) out.cov[m++] = C[i][j];
+      for (int j = 0; j <= i; j++) {
+        float acc = M.d[i] * (j == i ? 1.f : M.u[j][i]);
+#pragma unroll
+        for (int k = i + 1; k < 5; k++) acc += M.u[i][k] * M.d[k] * M.u[j][k];
+        out.cov[m++] = acc;
+      }
     out.ndf = 2 * n_used - 5;
     out.n_clusters = n;
     out.first_cluster = W.trk_first[t];

@@ -47,11 +47,11 @@ __global__ void k_merge_best(DevGeom G, DevParams P, DevWork W, int pass) {
     if (W.ch_next[k] < 0) {
       const int a2 = W.ch_top[k], a1 = W.ch_top2[k];
       const uint4 rec = __ldg(reinterpret_cast<const uint4*>(W.clusters) + a2);
-      const int r2 = (rec.z >> 24) & 0xff, s = rec.w >> 24;
+      const int r2 = (rec.z >> 24) & 0xff, s = min((int)(rec.w >> 24), G.n_sectors - 1);
       const long long Xa1 = W.cl_x[a1], Ya1 = W.cl_y[a1], Za1 = W.cl_z[a1];
       const long long Xa2 = W.cl_x[a2], Ya2 = W.cl_y[a2], Za2 = W.cl_z[a2];
       const long long dxa = Xa2 - Xa1;
-      for (int rb = r2 + P.gap_min; rb <= r2 + P.gap_max && rb < R; rb++) {
+      for (int rb = r2 + P.gap_min; rb <= r2 + P.gap_max && rb < R && r2 < R; rb++) {
         const long long Xb = G.xrow[rb];
         const long long zp = Za2 + floordiv_ll((Za2 - Za1) * (Xb - Xa2), dxa);
         const long long tlo = floordiv_ll(zp - MC - 2, 640) - 3;

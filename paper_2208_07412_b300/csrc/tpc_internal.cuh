@@ -23,7 +23,7 @@ constexpr uint32_t kErrOverflowCh = 4u;      // chain / track capacity exceeded
 constexpr uint32_t kErrTimeout = 8u;         // a bounded wait gave up
 constexpr uint32_t kErrRowCount = 16u;       // a row holds >= 2^23 clusters (edge keys)
 
-// bounded spin for look-back waits: 4e6 polls of L2 is a few seconds at most
+// bounded spin for look-back waits: 4e6 polls with back-off is about a second
 constexpr long long kSpinLimit = 4000000LL;
 
 // Geometry + parameters, passed by value to every kernel (fits in the 32 KB
@@ -106,6 +106,11 @@ __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long
   asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
 }
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
 __device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
   asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
@@ -151,20 +156,31 @@ __device__ __forceinline__ unsigned long long block_excl_scan(unsigned long long
 // the same; on expiry the error word gets kErrTimeout and 0 is returned.
 constexpr unsigned long long kStFlagAgg = 1ull << 62, kStFlagPre = 2ull << 62,
                              kStMask = (1ull << 62) - 1;
+// Publish a tile's aggregate (tile 0 publishes its inclusive prefix at once).
+__device__ __forceinline__ void lookback_publish(unsigned long long* state, long long tile,
+                                                 unsigned long long aggregate) {
+  st_release_u64(&state[tile], (tile == 0 ? kStFlagPre : kStFlagAgg) | aggregate);
+}
+// Wait for the exclusive prefix of `tile` (warp 0 of the block; the aggregate
+// must already be published) and publish the tile's inclusive prefix.
+__device__ __forceinline__ unsigned long long lookback_wait(unsigned long long* state, long long tile,
+                                                            unsigned long long aggregate, uint32_t* err);
 __device__ __forceinline__ unsigned long long lookback_warp0(unsigned long long* state, long long tile,
                                                              unsigned long long aggregate, uint32_t* err) {
+  if ((threadIdx.x & 31) == 0) lookback_publish(state, tile, aggregate);
+  return lookback_wait(state, tile, aggregate, err);
+}
+__device__ __forceinline__ unsigned long long lookback_wait(unsigned long long* state, long long tile,
+                                                            unsigned long long aggregate, uint32_t* err) {
   const int lane = threadIdx.x & 31;
-  if (tile == 0) {
-    if (lane == 0) st_release_u64(&state[0], kStFlagPre | aggregate);
-    return 0;
-  }
-  if (lane == 0) st_release_u64(&state[tile], kStFlagAgg | aggregate);
+  if (tile == 0) return 0;
   unsigned long long excl = 0;
   long long base = tile - 1;
   long long spins = 0;
   while (true) {
     long long j = base - lane;
-    unsigned long long s = j >= 0 ? ld_acquire_u64(&state[j]) : kStFlagPre;
+    // the state word carries the whole value, so a relaxed poll suffices
+    unsigned long long s = j >= 0 ? ld_relaxed_u64(&state[j]) : kStFlagPre;
     unsigned flag = (unsigned)(s >> 62);
     unsigned empty = __ballot_sync(0xffffffffu, flag == 0);
     if (empty) {
@@ -173,6 +189,7 @@ __device__ __forceinline__ unsigned long long lookback_warp0(unsigned long long*
         excl = 0;
         break;
       }
+      __nanosleep(spins < 8 ? 32 : 256);
       continue;
     }
     unsigned pre = __ballot_sync(0xffffffffu, flag == 2);

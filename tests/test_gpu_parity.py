@@ -44,6 +44,7 @@ def test_full_tpc_parity(lib):
     gpu = run_gpu(lib, tf)
     compare_integer(gpu, orc)
     rep = compare_fit(gpu, orc)
+    print("full_tpc fit precision vs FP64 oracle:", rep)
     assert rep["n_tracks"] > 10000
     assert gpu["counters"]["merge_passes"] == orc.merge_passes
 
