@@ -4,15 +4,19 @@
 // step of the TPC reconstruction on the EPN GPUs, after FPGA zero suppression).
 //
 // One CTA iteration processes one window = (sector, row, 256-bin fragment).
-// Memory round trips are the cost to avoid: the next window's ticket is taken
-// a window ahead, the page is staged in shared memory by one coalesced copy
-// (issued together with the neighbours' headers), and the neighbours' 3-bin
-// halo byte ranges by a second one; everything after that reads shared memory.
-// Digits are decoded into a plane guarded by an occupancy bitmap: only the
-// bitmap (5 KB) is cleared, never the 72 KB plane, so the work scales with the
-// digits, not with the pixels.  Digits, then peaks, are ranked by popcount
-// prefixes over the bitmap words, which follow the canonical (t, pad) order,
-// so every thread gets an equal share of the peak tests and of the clusters.
+// Memory round trips are the cost to avoid: the page is staged in shared
+// memory by one coalesced copy (issued together with the neighbours' headers),
+// and the neighbours' 3-bin halo byte ranges by a second one; everything after
+// that reads shared memory.  The small halo segments are decoded by one warp
+// each, without block barriers.
+// Digits are decoded into a zero-padded plane (two empty pads on each side of
+// the row) that is cleared lazily: at the end of a window only the cells its
+// digits wrote are reset, never the 74 KB plane, so the work scales with the
+// digits and every pixel lookup is a single shared load.  The decoder lists
+// the digits as it writes them; one thread per listed digit runs the peak
+// test; own peaks are ranked in canonical (t, pad) order by popcount prefixes
+// over the peak bitmap, and one thread per peak builds its cluster from the
+// 5x5 neighbourhood held in registers.
 // A decoupled look-back over the windows (handed out in index order by the
 // ticket) gives each window's global offset; its aggregate is published before
 // the clusters are built, so the wait overlaps that work, and the clusters are
@@ -56,12 +60,15 @@ constexpr int kStage = 256;                  // clusters staged in shared memory
 constexpr int kOwnStage = 2 * kStage * 16;   // bytes; the page is staged in the same buffer first
 constexpr int kHaloStage = 2048;             // bytes per neighbouring page's halo ranges
 constexpr int kHaloRunOff = 16, kHaloAdcOff = 800;
+constexpr int kList = 4096;                  // digits listed by the decoder (beyond: bitmap walk)
+constexpr int kPad = 2;                      // empty pads on each side of a plane row
 
 struct FindSmem {
-  uint16_t* plane;     // [kWinT][npmax]
-  uint32_t* occ;       // [kWinT][nw]
-  uint32_t* pk;        // [kWinT][nw]
-  uint16_t* wpre;      // digit rank prefix over the words of plane rows 1..260
+  uint16_t* plane;     // [kWinT][ps], pixel (tt, p) at tt * ps + p + kPad; zero where no digit
+  uint32_t* occ;       // [kWinT][nw] occupancy bitmap
+  uint32_t* pk;        // [kWinT][nw] peak bitmap
+  uint16_t* list;      // [kList] plane index of every decoded digit
+  uint16_t* plist;     // [kStage] plane index of the first own peaks in canonical order
   uint16_t* ppre;      // own-peak rank prefix over the words of rows 3..258
   uint4* st_rec;       // [kStage] staged cluster records (first: the staged page)
   int4* st_xyz;        // [kStage] staged (X, Y, Z, t_peak)
@@ -81,23 +88,58 @@ __device__ __forceinline__ long long round_half_up(long long a, long long b) {
   if ((n % d) != 0 && (n < 0)) q -= 1;
   return q;
 }
+__device__ __forceinline__ int floordiv32(int n, int d) {   // d > 0
+  int q = n / d;
+  if ((n % d) != 0 && n < 0) q -= 1;
+  return q;
+}
+// min(255, R(num, den)) for 0 <= num, 0 < den < 2^31: a float quotient,
+// corrected exactly in integers (the quotient is at most 256 here).
+__device__ __forceinline__ int round_half_up_sat255(long long num, long long den) {
+  if (num >= 255LL * den + den / 2 + den) return 255;
+  const long long n2 = 2 * num + den, d2 = 2 * den;
+  long long q = (long long)floorf((float)n2 / (float)d2);
+  while (q * d2 > n2) q--;
+  while ((q + 1) * d2 <= n2) q++;
+  return (int)min(q, 255LL);
+}
 
 // Entries of one page to decode: entries (t_in | n_runs << 8), the runs they
 // own (pad_start | len << 8) and their ADC words; digit k of the segment is
-// field (dfirst + k) % 3 of word (dfirst + k) / 3.  Pointers may address shared
-// or global memory.
+// field (dfirst + k) % 3 of word (dfirst + k) / 3.  Digit k is listed at
+// list[lbase + k] if that is below kList.  Pointers may be shared or global.
 struct Seg {
   const uint16_t* ent; int ne;
   const uint16_t* run; int nrun;
   const uint32_t* adc; int dfirst; int ndig;
-  int tt_base, t_base_abs;
+  int tt_base, t_base_abs, lbase;
   bool strict;                    // the window's own page: ordering and exact counts
 };
 
-// Decode a segment into plane rows tt = t_in + tt_base.  All reads are bounds-
-// checked against the segment's counts and all writes against the plane.
-// Returns true (block-uniform) if every check passed.
-__device__ bool decode_seg(const Seg& g, int np, int stride, int nw, int T, const FindSmem& S) {
+__device__ __forceinline__ void put_run(const Seg& g, const FindSmem& S, int ps_stride, int nw, int tt, int ps,
+                                        int len, int di) {
+  uint16_t* prow = S.plane + tt * ps_stride + kPad;
+  for (int k = 0; k < len; k++) {
+    const int d = g.dfirst + di + k;
+    prow[ps + k] = (uint16_t)((g.adc[d / 3] >> (10 * (d % 3))) & 1023u);
+    const int li = g.lbase + di + k;
+    if (li < kList) S.list[li] = (uint16_t)(tt * ps_stride + kPad + ps + k);
+  }
+  int p = ps;
+  const int pe = ps + len;
+  while (p < pe) {
+    const int wi = p >> 5, b0 = p & 31;
+    const int n = min(32 - b0, pe - p);
+    const uint32_t m = (n == 32) ? 0xffffffffu : (((1u << n) - 1u) << b0);
+    atomicOr(&S.occ[tt * nw + wi], m);
+    p += n;
+  }
+}
+
+// Block-wide decode of a segment into plane rows tt = t_in + tt_base.  All
+// reads are bounds-checked against the segment's counts and all writes
+// against the plane.  Returns true (block-uniform) if every check passed.
+__device__ bool decode_seg(const Seg& g, int np, int ps_stride, int nw, int T, const FindSmem& S) {
   const int tid = threadIdx.x;
   const int ne = g.ne;
   bool bad = ne < 0 || ne > kFrag;
@@ -141,27 +183,48 @@ __device__ bool decode_seg(const Seg& g, int np, int stride, int nw, int T, cons
     const unsigned long long doff = block_excl_scan((unsigned long long)len, S.scan, &ctot);
     const long long di = (long long)dcarry + (long long)doff;
     if (mine && di + len > g.ndig) { bad = true; mine = false; }
-    if (mine) {
-      uint16_t* prow = S.plane + tt * stride;
-      for (int k = 0; k < len; k++) {
-        const int d = g.dfirst + (int)di + k;
-        prow[ps + k] = (uint16_t)((g.adc[d / 3] >> (10 * (d % 3))) & 1023u);
-      }
-      // occupancy bits for pads [ps, ps + len)
-      int p = ps;
-      const int pe = ps + len;
-      while (p < pe) {
-        const int wi = p >> 5, b0 = p & 31;
-        const int n = min(32 - b0, pe - p);
-        const uint32_t m = (n == 32) ? 0xffffffffu : (((1u << n) - 1u) << b0);
-        atomicOr(&S.occ[tt * nw + wi], m);
-        p += n;
-      }
-    }
+    if (mine) put_run(g, S, ps_stride, nw, tt, ps, len, (int)di);
     dcarry += ctot;
   }
   if (g.strict && (nrun != g.nrun || (long long)dcarry != g.ndig)) bad = true;
   return !__syncthreads_or(bad);
+}
+
+// Warp-level decode of a small segment (the 3-bin halos): the same checks, no
+// block barrier.  A violated bound stops it; the page's own window reports it.
+__device__ bool decode_seg_warp(const Seg& g, int np, int ps_stride, int nw, int T, const FindSmem& S) {
+  const int lane = threadIdx.x & 31;
+  bool bad = g.ne < 0 || g.ne > kFrag;
+  int run0 = 0, dig0 = 0;   // runs / digits consumed by earlier entries
+  for (int e = 0; e < g.ne && !bad; e++) {
+    const uint32_t v = g.ent[e];
+    const int t_in = v & 0xff, nr = v >> 8;
+    const int tt = t_in + g.tt_base;
+    if (nr < 1 || tt < 0 || tt >= kWinT || g.t_base_abs + t_in >= T || run0 + nr > g.nrun) { bad = true; break; }
+    for (int jb = 0; jb < nr; jb += 32) {
+      const int j = jb + lane;
+      int ps = 0, len = 0;
+      if (j < nr) {
+        const uint32_t rv = g.run[run0 + j];
+        ps = rv & 0xff;
+        len = rv >> 8;
+        if (len < 1 || ps + len > np) { len = 0; bad = true; }
+      }
+      int incl = len;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int n = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += n;
+      }
+      const int di = dig0 + incl - len;
+      if (len && di + len > g.ndig) { len = 0; bad = true; }
+      if (len) put_run(g, S, ps_stride, nw, tt, ps, len, di);
+      dig0 += __shfl_sync(0xffffffffu, incl, 31);
+      bad = __any_sync(0xffffffffu, bad);
+    }
+    run0 += nr;
+  }
+  return !bad;
 }
 
 // Copy the byte range [a, b) of a page (2-byte aligned, both in bounds) to dst
@@ -171,22 +234,16 @@ __device__ __forceinline__ void copy_u16(uint16_t* dst, const uint8_t* pg, uint3
   for (uint32_t i = threadIdx.x; i < (b - a) / 2; i += blockDim.x) dst[i] = __ldg(src + i);
 }
 
-__device__ __forceinline__ int qat(const FindSmem& S, int stride, int nw, int np, int tt, int p) {
-  if (p < 0 || p >= np) return 0;
-  return ((S.occ[tt * nw + (p >> 5)] >> (p & 31)) & 1u) ? (int)S.plane[tt * stride + p] : 0;
-}
-__device__ __forceinline__ bool pkat(const FindSmem& S, int nw, int np, int tt, int p) {
-  if (p < 0 || p >= np) return false;
-  return (S.pk[tt * nw + (p >> 5)] >> (p & 31)) & 1u;
-}
-
-__device__ __forceinline__ bool peak_test(const FindSmem& S, int stride, int nw, int np, int tt, int p, int q) {
-  // neighbours with a lower linear index must be strictly lower in charge,
-  // those with a higher index lower or equal: key = (q, -(t * npads + p))
-  return q > qat(S, stride, nw, np, tt - 1, p - 1) && q > qat(S, stride, nw, np, tt - 1, p) &&
-         q > qat(S, stride, nw, np, tt - 1, p + 1) && q > qat(S, stride, nw, np, tt, p - 1) &&
-         q >= qat(S, stride, nw, np, tt, p + 1) && q >= qat(S, stride, nw, np, tt + 1, p - 1) &&
-         q >= qat(S, stride, nw, np, tt + 1, p) && q >= qat(S, stride, nw, np, tt + 1, p + 1);
+// Peak test of the digit at plane index L (row tt, pad p): neighbours with a
+// lower linear index (t * npads + p) must be strictly lower in charge, those
+// with a higher index lower or equal; padding pads and empty pixels read 0.
+__device__ __forceinline__ bool peak_at(const uint16_t* pl, int L, int ps_stride, int qmin) {
+  const int q = pl[L];
+  if (q < qmin) return false;
+  const uint16_t* u = pl + L - ps_stride;
+  const uint16_t* d = pl + L + ps_stride;
+  return q > u[-1] && q > u[0] && q > u[1] && q > pl[L - 1] && q >= pl[L + 1] && q >= d[-1] && q >= d[0] &&
+         q >= d[1];
 }
 
 // Index of the last prefix entry <= r in pre[0..n] (pre ascending, pre[0] = 0).
@@ -199,44 +256,62 @@ __device__ __forceinline__ int rank_search(const uint16_t* pre, int n, int r) {
   return lo;
 }
 
-// Cluster of the peak at (tt, p): 5x5 window with the inner/outer rule.
-__device__ __forceinline__ void make_cluster(const FindSmem& S, int stride, int nw, int np, int T, int s, int r,
+// Five bits of a bitmap row around pad p: bit k <-> pad p - 2 + k (0 outside).
+__device__ __forceinline__ uint32_t bits5(const uint32_t* row, int nw, int p) {
+  const int lo = p - 2;                       // >= -2
+  const int w0 = (lo + 32) / 32 - 1;          // floor(lo / 32)
+  const uint32_t a = (w0 >= 0 && w0 < nw) ? row[w0] : 0u;
+  const uint32_t b = (w0 + 1 >= 0 && w0 + 1 < nw) ? row[w0 + 1] : 0u;
+  const unsigned long long v = ((unsigned long long)b << 32) | a;
+  return (uint32_t)(v >> (lo - 32 * w0)) & 31u;
+}
+
+// Cluster of the peak at (tt, p): 5x5 window with the inner/outer rule, the
+// neighbourhood held in registers.
+__device__ __forceinline__ void make_cluster(const FindSmem& S, int ps_stride, int nw, int np, int T, int s, int r,
                                              int f, int tt, int p, int xrow, uint4& rec, int4& xyz) {
+  const uint16_t* c = S.plane + tt * ps_stride + kPad + p;
+  int q[5][5];
+#pragma unroll
+  for (int dt = 0; dt < 5; dt++)
+#pragma unroll
+    for (int dp = 0; dp < 5; dp++) q[dt][dp] = c[(dt - 2) * ps_stride + dp - 2];
   int Q = 0, Sp = 0, St = 0, Spp = 0, Stt = 0;
-  bool excl = false, other = false;
+  bool excl = false;
 #pragma unroll
   for (int dt = -2; dt <= 2; dt++) {
 #pragma unroll
     for (int dp = -2; dp <= 2; dp++) {
-      const int q = qat(S, stride, nw, np, tt + dt, p + dp);
-      bool inc;
-      if (dp >= -1 && dp <= 1 && dt >= -1 && dt <= 1) {
-        inc = true;
-      } else {
+      const int v = q[dt + 2][dp + 2];
+      bool inc = true;
+      if (dp < -1 || dp > 1 || dt < -1 || dt > 1) {
         const int ip = dp > 0 ? 1 : (dp < 0 ? -1 : 0), it = dt > 0 ? 1 : (dt < 0 ? -1 : 0);
-        const int qi = qat(S, stride, nw, np, tt + it, p + ip);
-        inc = qi > 0 && q <= qi;
-        if (!inc && q > 0) excl = true;
+        const int qi = q[it + 2][ip + 2];
+        inc = qi > 0 && v <= qi;
+        excl |= (!inc && v > 0);
       }
-      if (inc) {
-        Q += q; Sp += q * dp; St += q * dt; Spp += q * dp * dp; Stt += q * dt * dt;
-      }
-      if ((dp || dt) && pkat(S, nw, np, tt + dt, p + dp)) other = true;
+      if (inc) { Q += v; Sp += v * dp; St += v * dt; Spp += v * dp * dp; Stt += v * dt * dt; }
     }
+  }
+  uint32_t other = 0;
+#pragma unroll
+  for (int dt = -2; dt <= 2; dt++) {
+    uint32_t b = bits5(S.pk + (tt + dt) * nw, nw, p);
+    if (dt == 0) b &= ~4u;
+    other |= b;
   }
   const int t_in = tt - kHalo;
   const int t = kFrag * f + t_in;
-  const long long QQ = Q;
-  const int pad_fp = 256 * p + (int)round_half_up(256LL * Sp, QQ);
-  const int time_fp = 128 * (t_in + 4) + (int)round_half_up(128LL * St, QQ);
-  const long long vp = round_half_up(16LL * ((long long)Spp * QQ - (long long)Sp * Sp), QQ * QQ);
-  const long long vt = round_half_up(16LL * ((long long)Stt * QQ - (long long)St * St), QQ * QQ);
+  const int pad_fp = 256 * p + floordiv32(512 * Sp + Q, 2 * Q);
+  const int time_fp = 128 * (t_in + 4) + floordiv32(256 * St + Q, 2 * Q);
+  const long long QQ = (long long)Q * Q;
+  const int vp = round_half_up_sat255(16LL * ((long long)Spp * Q - (long long)Sp * Sp), QQ);
+  const int vt = round_half_up_sat255(16LL * ((long long)Stt * Q - (long long)St * St), QQ);
   const int flags = ((p == 0 || p == np - 1 || t == 0 || t == T - 1) ? TPC_CL_EDGE : 0) |
                     (excl ? TPC_CL_EXCLUDED : 0) | (other ? TPC_CL_NEIGHBOUR : 0);
   rec.x = (uint32_t)(pad_fp & 0xffff) | ((uint32_t)(time_fp & 0xffff) << 16);
-  rec.y = (uint32_t)S.plane[tt * stride + p] | ((uint32_t)min(Q, 65535) << 16);
-  rec.z = (uint32_t)min(vp, 255LL) | ((uint32_t)min(vt, 255LL) << 8) | ((uint32_t)flags << 16) |
-          ((uint32_t)r << 24);
+  rec.y = (uint32_t)q[2][2] | ((uint32_t)min(Q, 65535) << 16);
+  rec.z = (uint32_t)vp | ((uint32_t)vt << 8) | ((uint32_t)flags << 16) | ((uint32_t)r << 24);
   rec.w = (uint32_t)t | ((uint32_t)p << 16) | ((uint32_t)s << 24);
   xyz = make_int4(xrow, 2 * (pad_fp - 128 * (np - 1)), 5 * (32768 * f + time_fp - 512), t);
 }
@@ -244,14 +319,16 @@ __device__ __forceinline__ void make_cluster(const FindSmem& S, int stride, int 
 __global__ void __launch_bounds__(kFindThreads, 2)
 k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int stride = G.npmax, nw = G.nw;
-  const int nrow_words = (kWinT - 2) * nw;   // plane rows 1 .. 260
+  const int ps_stride = G.npmax + 2 * kPad, nw = G.nw;
   const int nown_words = kFrag * nw;         // plane rows 3 .. 258
+  const int nplane = kWinT * ps_stride;
+  const bool use_list = nplane <= 65536;     // plane indices fit the 16-bit lists
+  const uint32_t magic = (uint32_t)((0x100000000ull + ps_stride - 1) / ps_stride);  // row = umulhi(L, magic)
   FindSmem S;
   {
     size_t o = 0;
     S.plane = reinterpret_cast<uint16_t*>(smem_raw + o);
-    o += ((size_t)kWinT * stride * 2 + 15) & ~(size_t)15;
+    o += ((size_t)nplane * 2 + 15) & ~(size_t)15;
     S.occ = reinterpret_cast<uint32_t*>(smem_raw + o);
     o += (size_t)kWinT * nw * 4;
     S.pk = reinterpret_cast<uint32_t*>(smem_raw + o);
@@ -273,20 +350,26 @@ k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
     o += 260 * 4;
     S.misc = reinterpret_cast<int32_t*>(smem_raw + o);
     o += 16 * 4;
-    S.wpre = reinterpret_cast<uint16_t*>(smem_raw + o);
-    o += ((size_t)nrow_words + 1) * 2;
+    S.list = reinterpret_cast<uint16_t*>(smem_raw + o);
+    o += kList * 2;
+    S.plist = reinterpret_cast<uint16_t*>(smem_raw + o);
+    o += kStage * 2;
     S.ppre = reinterpret_cast<uint16_t*>(smem_raw + o);
     o += ((size_t)nown_words + 1) * 2;
     S.ent_t = reinterpret_cast<uint8_t*>(smem_raw + o);
   }
   const int tid = threadIdx.x;
-  const int wpt = (nrow_words + blockDim.x - 1) / blockDim.x;
   const int opt = (nown_words + blockDim.x - 1) / blockDim.x;
   uint8_t* own_stage = reinterpret_cast<uint8_t*>(S.st_rec);
 
-  if (tid == 0) S.misc[1] = (int)atomicAdd(&W.tickets[TK_FIND], 1u);
+  // the plane starts empty and is kept empty between windows
+  for (int i = tid; i < nplane / 2; i += blockDim.x) reinterpret_cast<uint32_t*>(S.plane)[i] = 0u;
+  if (tid == 0 && (nplane & 1)) S.plane[nplane - 1] = 0;
+
   while (true) {
-    // ---- 0. window w; take the next ticket now, one window ahead
+    // ---- 0. window w.  The ticket is taken only now: a CTA that held a later
+    // window while still busy would stall every successor's look-back.
+    if (tid == 0) S.misc[1] = (int)atomicAdd(&W.tickets[TK_FIND], 1u);
     __syncthreads();
     const unsigned int w = (unsigned int)S.misc[1];
     if (w >= n_windows) break;
@@ -294,10 +377,8 @@ k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
       const long long j = (long long)w - 1 + tid;
       S.offs[tid] = (j >= 0 && j < (long long)n_windows) ? W.page_offsets[j] : ~0ull;
     }
-    for (int i = tid; i < kWinT * nw; i += blockDim.x) S.occ[i] = 0u;
+    for (int i = tid; i < kWinT * nw; i += blockDim.x) { S.occ[i] = 0u; S.pk[i] = 0u; }
     __syncthreads();
-    // every thread has read w: the slot may now receive the next ticket
-    if (tid == 0) S.misc[1] = (int)atomicAdd(&W.tickets[TK_FIND], 1u);
     const int f = (int)(w % G.n_frag);
     const int sr = (int)(w / G.n_frag);
     const int r = sr % G.n_rows, s = sr / G.n_rows;
@@ -328,8 +409,7 @@ k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
     const uint8_t* own = copied >= 32 ? own_stage : W.pages + off;
     bool ok = parse_header(reinterpret_cast<const uint4*>(own), off, W.pages_bytes, h) && h.sector == s &&
               h.row == r && h.frag == f;
-    const bool own_in_smem = ok && h.len <= copied;
-    if (ok && !own_in_smem) own = W.pages + off;   // page larger than the stage: decode from global
+    if (ok && h.len > copied) own = W.pages + off;   // page larger than the stage: decode from global
     const bool okp = f > 0 && parse_header(S.hdr, S.offs[0], W.pages_bytes, hp) &&
                      2 * (hp.n_tb - hp.hi_tb) <= kHaloRunOff && 2 * (hp.n_runs - hp.hi_runs) <= kHaloAdcOff - kHaloRunOff &&
                      4 * ((hp.n_dig + 2) / 3 - hp.hi_dig / 3) <= kHaloStage - kHaloAdcOff;
@@ -354,57 +434,68 @@ k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
     }
     __syncthreads();
 
-    // ---- 3. decode own page and the two halos into the plane
+    // ---- 3. decode the two halos (warps 0 and 1) and the own page (block);
+    // digits listed as own | previous halo | next halo
+    const int n_own = ok ? h.n_dig : 0;
+    const int n_prev = okp ? hp.n_dig - hp.hi_dig : 0;
+    const int n_next = okn ? hn.lo_dig : 0;
+    const int ndig = n_own + n_prev + n_next;
+    const bool listed = use_list && ndig <= kList;
+    if (okp && (tid >> 5) == 0) {
+      Seg g{reinterpret_cast<const uint16_t*>(hprev), hp.n_tb - hp.hi_tb,
+            reinterpret_cast<const uint16_t*>(hprev + kHaloRunOff), hp.n_runs - hp.hi_runs,
+            reinterpret_cast<const uint32_t*>(hprev + kHaloAdcOff), hp.hi_dig % 3, n_prev,
+            kHalo - kFrag, kFrag * (f - 1), listed ? n_own : kList, false};
+      decode_seg_warp(g, np, ps_stride, nw, T, S);
+    }
+    if (okn && (tid >> 5) == 1) {
+      Seg g{reinterpret_cast<const uint16_t*>(hnext), hn.lo_tb,
+            reinterpret_cast<const uint16_t*>(hnext + kHaloRunOff), hn.lo_runs,
+            reinterpret_cast<const uint32_t*>(hnext + kHaloAdcOff), 0, n_next, kHalo + kFrag, kFrag * (f + 1),
+            listed ? n_own + n_prev : kList, false};
+      decode_seg_warp(g, np, ps_stride, nw, T, S);
+    }
     if (ok) {
       Seg g{reinterpret_cast<const uint16_t*>(own + 32), h.n_tb,
             reinterpret_cast<const uint16_t*>(own + 32 + 2 * h.n_tb), h.n_runs,
-            reinterpret_cast<const uint32_t*>(own + h.body), 0, h.n_dig, kHalo, kFrag * f, true};
-      ok = decode_seg(g, np, stride, nw, T, S);
-    }
-    if (okp) {
-      Seg g{reinterpret_cast<const uint16_t*>(hprev), hp.n_tb - hp.hi_tb,
-            reinterpret_cast<const uint16_t*>(hprev + kHaloRunOff), hp.n_runs - hp.hi_runs,
-            reinterpret_cast<const uint32_t*>(hprev + kHaloAdcOff), hp.hi_dig % 3, hp.n_dig - hp.hi_dig,
-            kHalo - kFrag, kFrag * (f - 1), false};
-      decode_seg(g, np, stride, nw, T, S);
-    }
-    if (okn) {
-      Seg g{reinterpret_cast<const uint16_t*>(hnext), hn.lo_tb,
-            reinterpret_cast<const uint16_t*>(hnext + kHaloRunOff), hn.lo_runs,
-            reinterpret_cast<const uint32_t*>(hnext + kHaloAdcOff), 0, hn.lo_dig, kHalo + kFrag, kFrag * (f + 1),
-            false};
-      decode_seg(g, np, stride, nw, T, S);
+            reinterpret_cast<const uint32_t*>(own + h.body), 0, h.n_dig, kHalo, kFrag * f, listed ? 0 : kList, true};
+      ok = decode_seg(g, np, ps_stride, nw, T, S);
     }
     if (!ok && tid == 0) atomicOr(W.err, kErrCorrupt);
+    __syncthreads();
 
-    // ---- 4. rank the digits of rows 1..260 (popcount prefix over the bitmap words)
-    int ndig = 0;
-    {
-      const int w0 = tid * wpt, w1 = min(w0 + wpt, nrow_words);
-      int c = 0;
-      for (int i = w0; i < w1; i++) c += __popc(S.occ[nw + i]);
-      unsigned long long tot;
-      const unsigned long long pre = block_excl_scan((unsigned long long)c, S.scan, &tot);
-      int run = (int)pre;
-      for (int i = w0; i < w1; i++) { S.wpre[i] = (uint16_t)run; run += __popc(S.occ[nw + i]); }
-      if (tid == 0) S.wpre[nrow_words] = (uint16_t)tot;
-      for (int i = w0; i < w1; i++) S.pk[nw + i] = 0u;   // rebuilt by atomicOr below
-      ndig = ok ? (int)tot : 0;
+    // ---- 4. peak test, one digit per thread (rows 1..260; rows 0 and 261 only
+    // serve as neighbours)
+    if (ok) {
+      if (listed) {
+        for (int i = tid; i < ndig; i += blockDim.x) {
+          const int L = S.list[i];
+          if (L >= nplane) continue;
+          const int tt = (int)__umulhi((uint32_t)L, magic);
+          if (tt < 1 || tt > kWinT - 2) continue;
+          if (peak_at(S.plane, L, ps_stride, P.q_peak_min)) {
+            const int p = L - tt * ps_stride - kPad;
+            atomicOr(&S.pk[tt * nw + (p >> 5)], 1u << (p & 31));
+          }
+        }
+      } else {
+        // too many digits to list: walk the occupancy bitmap
+        for (int wi_ = nw + tid; wi_ < (kWinT - 1) * nw; wi_ += blockDim.x) {
+          uint32_t word = S.occ[wi_];
+          const int tt = wi_ / nw, p0 = (wi_ % nw) * 32;
+          while (word) {
+            const int b = __ffs(word) - 1;
+            word &= word - 1;
+            if (peak_at(S.plane, tt * ps_stride + kPad + p0 + b, ps_stride, P.q_peak_min))
+              atomicOr(&S.pk[wi_], 1u << b);
+          }
+        }
+      }
     }
     __syncthreads();
 
-    // ---- 5. peak test, one digit per thread (balanced)
-    for (int rk = tid; rk < ndig; rk += blockDim.x) {
-      const int wi_ = rank_search(S.wpre, nrow_words + 1, rk);
-      const uint32_t word = S.occ[nw + wi_];
-      const int bit = __fns(word, 0, rk - (int)S.wpre[wi_] + 1);
-      const int tt = 1 + wi_ / nw, p = (wi_ % nw) * 32 + bit;
-      const int q = S.plane[tt * stride + p];
-      if (q >= P.q_peak_min && peak_test(S, stride, nw, np, tt, p, q)) atomicOr(&S.pk[tt * nw + (p >> 5)], 1u << bit);
-    }
-    __syncthreads();
-
-    // ---- 6. rank the own peaks (rows 3..258) and publish the window's count
+    // ---- 5. rank the own peaks (rows 3..258) in canonical order, list the
+    // first kStage, publish the window's count
     int npk;
     {
       const int w0 = tid * opt, w1 = min(w0 + opt, nown_words);
@@ -413,7 +504,19 @@ k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
       unsigned long long tot;
       const unsigned long long pre = block_excl_scan((unsigned long long)c, S.scan, &tot);
       int run = (int)pre;
-      for (int i = w0; i < w1; i++) { S.ppre[i] = (uint16_t)run; run += __popc(S.pk[kHalo * nw + i]); }
+      for (int i = w0; i < w1; i++) {
+        uint32_t word = S.pk[kHalo * nw + i];
+        S.ppre[i] = (uint16_t)run;
+        while (word) {
+          const int b = __ffs(word) - 1;
+          word &= word - 1;
+          if (run < kStage && use_list) {
+            const int wi_ = i + kHalo * nw;
+            S.plist[run] = (uint16_t)((wi_ / nw) * ps_stride + kPad + (wi_ % nw) * 32 + b);
+          }
+          run++;
+        }
+      }
       if (tid == 0) {
         S.ppre[nown_words] = (uint16_t)tot;
         lookback_publish(W.win_state, (long long)w, tot);
@@ -422,17 +525,23 @@ k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
     }
     __syncthreads();
 
-    // ---- 7. clusters of the first kStage peaks, staged in shared memory
+    // ---- 6. clusters of the first kStage peaks, one thread each, staged
     const int nst = min(npk, kStage);
     for (int k = tid; k < nst; k += blockDim.x) {
-      const int wi_ = rank_search(S.ppre, nown_words + 1, k);
-      const uint32_t word = S.pk[kHalo * nw + wi_];
-      const int bit = __fns(word, 0, k - (int)S.ppre[wi_] + 1);
-      const int tt = kHalo + wi_ / nw, p = (wi_ % nw) * 32 + bit;
-      make_cluster(S, stride, nw, np, T, s, r, f, tt, p, G.xrow[r], S.st_rec[k], S.st_xyz[k]);
+      int tt, p;
+      if (use_list) {
+        const int L = S.plist[k];
+        tt = (int)__umulhi((uint32_t)L, magic);
+        p = L - tt * ps_stride - kPad;
+      } else {   // rows too wide for 16-bit plane indices
+        const int wo = rank_search(S.ppre, nown_words + 1, k);
+        tt = kHalo + wo / nw;
+        p = (wo % nw) * 32 + __fns(S.pk[kHalo * nw + wo], 0, k - (int)S.ppre[wo] + 1);
+      }
+      make_cluster(S, ps_stride, nw, np, T, s, r, f, tt, p, G.xrow[r], S.st_rec[k], S.st_xyz[k]);
     }
 
-    // ---- 8. global offset of this window (decoupled look-back)
+    // ---- 7. global offset of this window (decoupled look-back)
     if (tid < 32) {
       const unsigned long long base = lookback_wait(W.win_state, (long long)w, (unsigned long long)npk, W.err);
       if (tid == 0) {
@@ -450,7 +559,7 @@ k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
     __syncthreads();
     const unsigned long long base = S.scan[33];
 
-    // ---- 9. write out (coalesced), then any peaks beyond the staging buffer
+    // ---- 8. write out: staged clusters coalesced, any beyond one thread each
     for (int k = tid; k < npk; k += blockDim.x) {
       const unsigned long long idx = base + k;
       if (idx >= W.cap_cl) break;   // overflow: keep [0, cap) free of gaps, drop the rest
@@ -460,10 +569,9 @@ k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
         rec = S.st_rec[k];
         xyz = S.st_xyz[k];
       } else {
-        const int wi_ = rank_search(S.ppre, nown_words + 1, k);
-        const uint32_t word = S.pk[kHalo * nw + wi_];
-        const int bit = __fns(word, 0, k - (int)S.ppre[wi_] + 1);
-        make_cluster(S, stride, nw, np, T, s, r, f, kHalo + wi_ / nw, (wi_ % nw) * 32 + bit, G.xrow[r], rec, xyz);
+        const int wo = rank_search(S.ppre, nown_words + 1, k);
+        const int bit = __fns(S.pk[kHalo * nw + wo], 0, k - (int)S.ppre[wo] + 1);
+        make_cluster(S, ps_stride, nw, np, T, s, r, f, kHalo + wo / nw, (wo % nw) * 32 + bit, G.xrow[r], rec, xyz);
       }
       reinterpret_cast<uint4*>(W.clusters)[idx] = rec;
       W.cl_x[idx] = xyz.x;
@@ -471,15 +579,34 @@ k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
       W.cl_z[idx] = xyz.z;
       W.cl_t[idx] = xyz.w;
     }
+    __syncthreads();
+
+    // ---- 9. leave the plane empty for the next window
+    if (listed) {
+      for (int i = tid; i < ndig; i += blockDim.x) {
+        const int L = S.list[i];
+        if (L < nplane) S.plane[L] = 0;
+      }
+    } else {
+      for (int wi_ = tid; wi_ < kWinT * nw; wi_ += blockDim.x) {
+        uint32_t word = S.occ[wi_];
+        const int tt = wi_ / nw, p0 = (wi_ % nw) * 32;
+        while (word) {
+          const int b = __ffs(word) - 1;
+          word &= word - 1;
+          S.plane[tt * ps_stride + kPad + p0 + b] = 0;
+        }
+      }
+    }
   }
 }
 
 size_t find_smem_bytes(int npmax, int nw) {
-  size_t o = ((size_t)kWinT * npmax * 2 + 15) & ~(size_t)15;
+  size_t o = ((size_t)kWinT * (npmax + 2 * kPad) * 2 + 15) & ~(size_t)15;
   o += 2 * (size_t)kWinT * nw * 4;
   o = (o + 15) & ~(size_t)15;
   o += 2 * kStage * 16 + 2 * kHaloStage + 4 * 16 + 4 * 8 + 34 * 8 + 260 * 4 + 16 * 4;
-  o += ((size_t)(kWinT - 2) * nw + 1) * 2 + ((size_t)kFrag * nw + 1) * 2;
+  o += kList * 2 + kStage * 2 + ((size_t)kFrag * nw + 1) * 2;
   o += 256;
   return o;
 }
