@@ -314,6 +314,37 @@ tpc_status tpc_get_counters(tpc_context* ctx, uint64_t ticket, uint64_t* out, in
 /* Free the ticket's slot and results.  Unknown ticket: TPC_E_NOTFOUND. */
 tpc_status tpc_release(tpc_context* ctx, uint64_t ticket);
 
+/* Allocation-free cluster finder (steps 1-4 only).  The paper has no
+ * counterpart to this entry point; it exists for callers that cannot allocate
+ * device memory: code that runs inside a device-memory budget owned by another
+ * framework, or in a loop that must never reach cudaMalloc / cudaFree, whose
+ * implicit device-wide synchronisation and unbounded latency such a loop
+ * cannot afford.  It computes exactly the clusters tpc_submit_timeframe
+ * computes, with no context and no allocation of any kind.
+ *   geom          host geometry object
+ *   params        NULL for defaults; only q_peak_min is used
+ *   device        CUDA device the pointers live on
+ *   pages, page_offsets, pages_bytes, n_time_bins   as in tpc_timeframe_desc,
+ *                 device memory, borrowed for the call; pages 16-byte aligned
+ *   clusters      device memory for cap records (16-byte aligned), written in
+ *                 canonical order
+ *   n_clusters    host out: clusters found (may exceed cap: TPC_E_OVERFLOW)
+ *   stream        cudaStream_t (as void*) to run on, NULL for the default stream
+ * Scratch: a file-scope device array of 65,536 windows' look-back states plus
+ * 256 bytes of control words (about 513 KB, held on every GPU that loads the
+ * library until the process exits).  A timeframe with more windows (sectors x
+ * rows x 256-bin fragments) is rejected with TPC_E_INVAL.  The first call on a
+ * device looks up the array's device address and sets the kernel's shared-
+ * memory limit; make that first call before any stream capture.  Every call
+ * shares the one array, and clears it on its stream before use: calls that
+ * overlap on the GPU (other streams, other host threads) race and corrupt
+ * each other's results.  The call waits for its stream before returning.
+ * Errors: TPC_E_INVAL, TPC_E_CUDA, TPC_E_CORRUPT, TPC_E_OVERFLOW, TPC_E_TIMEOUT. */
+tpc_status tpc_find_clusters_noalloc(const tpc_geometry* geom, const tpc_params* params, int device,
+                                     const void* pages, uint64_t pages_bytes, const uint64_t* page_offsets,
+                                     uint32_t n_time_bins, tpc_cluster* clusters, uint64_t cap,
+                                     uint64_t* n_clusters, void* stream);
+
 /* Thread-local message describing the last error on this thread ("" if none). */
 const char* tpc_last_error(void);
 

@@ -21,6 +21,9 @@
 // ticket) gives each window's global offset; its aggregate is published before
 // the clusters are built, so the wait overlaps that work, and the clusters are
 // written once, coalesced, at their final place.
+#include <algorithm>
+#include <mutex>
+
 #include "tpc_internal.cuh"
 
 namespace tpc {
@@ -316,6 +319,9 @@ __device__ __forceinline__ void make_cluster(const FindSmem& S, int ps_stride, i
   xyz = make_int4(xrow, 2 * (pad_fp - 128 * (np - 1)), 5 * (32768 * f + time_fp - 512), t);
 }
 
+// kAux: also write the row starts and the per-cluster (X, Y, Z, t_peak)
+// arrays the later stages read (false only for the allocation-free variant).
+template <bool kAux>
 __global__ void __launch_bounds__(kFindThreads, 2)
 k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -548,9 +554,9 @@ k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
         S.scan[33] = base;
         // row starts are clamped to the capacity so that, after an overflow,
         // every later kernel still indexes inside the cluster arrays
-        if (f == 0) W.row_start[sr] = (uint32_t)min(base, (unsigned long long)W.cap_cl);
+        if (kAux && f == 0) W.row_start[sr] = (uint32_t)min(base, (unsigned long long)W.cap_cl);
         if (w == n_windows - 1) {
-          W.row_start[G.n_sectors * G.n_rows] = (uint32_t)min(base + npk, (unsigned long long)W.cap_cl);
+          if (kAux) W.row_start[G.n_sectors * G.n_rows] = (uint32_t)min(base + npk, (unsigned long long)W.cap_cl);
           W.ctr[CTR_NCL] = base + npk;
         }
         if (base + npk > W.cap_cl) atomicOr(W.err, kErrOverflowCl);
@@ -574,10 +580,12 @@ k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
         make_cluster(S, ps_stride, nw, np, T, s, r, f, kHalo + wo / nw, (wo % nw) * 32 + bit, G.xrow[r], rec, xyz);
       }
       reinterpret_cast<uint4*>(W.clusters)[idx] = rec;
-      W.cl_x[idx] = xyz.x;
-      W.cl_y[idx] = xyz.y;
-      W.cl_z[idx] = xyz.z;
-      W.cl_t[idx] = xyz.w;
+      if (kAux) {
+        W.cl_x[idx] = xyz.x;
+        W.cl_y[idx] = xyz.y;
+        W.cl_z[idx] = xyz.z;
+        W.cl_t[idx] = xyz.w;
+      }
     }
     __syncthreads();
 
@@ -616,14 +624,122 @@ cudaError_t launch_find(const DevGeom& G, const DevParams& P, const DevWork& W, 
   size_t sm = find_smem_bytes(G.npmax, G.nw);
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_find_clusters, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = cudaFuncSetAttribute(k_find_clusters<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
   unsigned int grid = (unsigned int)min((long long)n_windows, (long long)n_sm * 2);
   if (grid == 0) grid = 1;
-  k_find_clusters<<<grid, kFindThreads, sm, st>>>(G, P, W, n_windows);
+  k_find_clusters<true><<<grid, kFindThreads, sm, st>>>(G, P, W, n_windows);
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the finder.  The look-back states and the control
+// words (counters, error word, ticket) live in this file-scope array instead
+// of memory from cudaMalloc; every GPU that loads the library holds it until
+// the process exits.
+constexpr unsigned kNoAllocMaxWindows = 65536;
+constexpr unsigned kNoAllocCtrlWords = 32;   // CTR_COUNT counters + error word + tickets
+static __device__ __align__(256) unsigned long long g_noalloc_scratch[kNoAllocMaxWindows + kNoAllocCtrlWords];
+
+namespace {
+std::mutex g_noalloc_mu;
+unsigned long long* g_noalloc_addr[64];      // device address of the array, per device
+bool g_noalloc_ready[64];
+}  // namespace
+
 }  // namespace tpc
+
+extern "C" tpc_status tpc_find_clusters_noalloc(const tpc_geometry* geom, const tpc_params* params, int device,
+                                                const void* pages, uint64_t pages_bytes,
+                                                const uint64_t* page_offsets, uint32_t n_time_bins,
+                                                tpc_cluster* clusters, uint64_t cap, uint64_t* n_clusters,
+                                                void* stream) {
+  using namespace tpc;
+  auto fail = [](tpc_status st, const char* msg) { set_last_error(msg); return st; };
+  if (!geom || !pages || !page_offsets || !clusters || !n_clusters)
+    return fail(TPC_E_INVAL, "tpc_find_clusters_noalloc: null argument");
+  if (((uintptr_t)pages & 15) || ((uintptr_t)clusters & 15))
+    return fail(TPC_E_INVAL, "tpc_find_clusters_noalloc: pages and clusters must be 16-byte aligned");
+  if (n_time_bins < 1 || n_time_bins > 65535 || pages_bytes < 32)
+    return fail(TPC_E_INVAL, "tpc_find_clusters_noalloc: n_time_bins or pages_bytes out of range");
+  const int q_peak_min = params ? params->q_peak_min : 10;
+  if (params && params->version != TPC_PARAMS_VERSION)
+    return fail(TPC_E_INVAL, "tpc_find_clusters_noalloc: params version mismatch");
+  if (q_peak_min < 1 || q_peak_min > 1023) return fail(TPC_E_INVAL, "tpc_find_clusters_noalloc: bad q_peak_min");
+  const unsigned long long nfrag = (n_time_bins + kFrag - 1) / kFrag;
+  const unsigned long long nwin = (unsigned long long)geom->n_sectors * geom->n_rows * nfrag;
+  if (nwin > kNoAllocMaxWindows)
+    return fail(TPC_E_INVAL,
+                "tpc_find_clusters_noalloc: the timeframe has more windows (sector x row x 256-bin fragment) "
+                "than the 65536 its fixed scratch holds");
+  if (device < 0 || device >= 64) return fail(TPC_E_INVAL, "tpc_find_clusters_noalloc: bad device");
+  int prev_dev = -1;
+  if (cudaGetDevice(&prev_dev) != cudaSuccess) return fail(TPC_E_CUDA, "cudaGetDevice failed");
+  if (prev_dev != device && cudaSetDevice(device) != cudaSuccess) return fail(TPC_E_CUDA, "cudaSetDevice failed");
+  struct Restore {
+    int d, p;
+    ~Restore() { if (p >= 0 && p != d) cudaSetDevice(p); }
+  } restore{device, prev_dev};
+  // one-time set-up on this device (with the device current): the array's
+  // device address and the kernel's shared-memory limit
+  const size_t smem = find_smem_bytes(geom->npmax, (geom->npmax + 31) / 32);
+  {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ready[device]) {
+      void* ptr = nullptr;
+      if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr)
+        return fail(TPC_E_CUDA, "tpc_find_clusters_noalloc: cudaGetSymbolAddress failed");
+      if (cudaFuncSetAttribute(k_find_clusters<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) !=
+          cudaSuccess)
+        return fail(TPC_E_CUDA, "tpc_find_clusters_noalloc: cudaFuncSetAttribute failed");
+      g_noalloc_addr[device] = static_cast<unsigned long long*>(ptr);
+      g_noalloc_ready[device] = true;
+    }
+  }
+  if (smem > 227 * 1024) return fail(TPC_E_INVAL, "tpc_find_clusters_noalloc: rows too wide");
+  unsigned long long* scratch = g_noalloc_addr[device];
+  DevGeom G{};
+  G.n_sectors = geom->n_sectors;
+  G.n_rows = geom->n_rows;
+  G.npmax = geom->npmax;
+  G.nw = (geom->npmax + 31) / 32;
+  G.n_time_bins = (int)n_time_bins;
+  G.n_frag = (int)nfrag;
+  for (int r = 0; r < geom->n_rows; r++) { G.npads[r] = geom->npads[r]; G.xrow[r] = 64 * geom->row_x[r]; }
+  DevParams P{};
+  P.q_peak_min = q_peak_min;
+  DevWork W{};
+  W.pages = static_cast<const uint8_t*>(pages);
+  W.page_offsets = page_offsets;
+  W.pages_bytes = pages_bytes;
+  W.clusters = clusters;
+  W.cap_cl = cap;
+  W.win_state = scratch;
+  W.ctr = scratch + kNoAllocMaxWindows;
+  W.err = reinterpret_cast<uint32_t*>(W.ctr + CTR_COUNT);
+  W.tickets = reinterpret_cast<unsigned int*>(W.ctr + CTR_COUNT + 1);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // the array keeps the previous call's contents: clear what must start at zero
+  if (cudaMemsetAsync(W.ctr, 0, kNoAllocCtrlWords * 8, st) != cudaSuccess ||
+      cudaMemsetAsync(W.win_state, 0, nwin * 8, st) != cudaSuccess)
+    return fail(TPC_E_CUDA, "tpc_find_clusters_noalloc: cudaMemsetAsync failed");
+  int n_sm = 148;
+  cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, device);
+  unsigned grid = (unsigned)std::min<unsigned long long>(nwin, (unsigned long long)n_sm * 2);
+  k_find_clusters<false><<<grid ? grid : 1, kFindThreads, smem, st>>>(G, P, W, (unsigned)nwin);
+  if (cudaGetLastError() != cudaSuccess) return fail(TPC_E_CUDA, "tpc_find_clusters_noalloc: launch failed");
+  unsigned long long ctrl[CTR_COUNT + 1];
+  if (cudaMemcpyAsync(ctrl, W.ctr, sizeof ctrl, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return fail(TPC_E_CUDA, "tpc_find_clusters_noalloc: device error");
+  const uint32_t err = static_cast<uint32_t>(ctrl[CTR_COUNT] & 0xffffffffu);
+  *n_clusters = ctrl[CTR_NCL];
+  if (err & kErrCorrupt) return fail(TPC_E_CORRUPT, "tpc_find_clusters_noalloc: corrupt ZS page");
+  if (err & kErrTimeout) return fail(TPC_E_TIMEOUT, "tpc_find_clusters_noalloc: look-back wait gave up");
+  if (err & kErrOverflowCl) return fail(TPC_E_OVERFLOW, "tpc_find_clusters_noalloc: more clusters than cap");
+  if (err) return fail(TPC_E_DEVICE, "tpc_find_clusters_noalloc: device error word set");
+  return TPC_OK;
+}
+

@@ -35,17 +35,15 @@ static tpc_status fail(tpc_status st, const std::string& msg) {
   g_err = msg;
   return st;
 }
+namespace tpc {
+void set_last_error(const char* msg) { g_err = msg; }
+}  // namespace tpc
 #define CUDA_TRY(expr)                                                                          \
   do {                                                                                          \
     cudaError_t e_ = (expr);                                                                    \
     if (e_ != cudaSuccess)                                                                      \
       return fail(TPC_E_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_));              \
   } while (0)
-
-struct tpc_geometry {
-  int n_sectors, n_rows, npmax;
-  std::vector<int> npads, row_x;
-};
 
 namespace {
 

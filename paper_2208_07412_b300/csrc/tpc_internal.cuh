@@ -5,11 +5,21 @@
 #pragma once
 
 #include <cstdint>
+#include <vector>
 #include <cuda_runtime.h>
 
 #include "../../include/tpc.h"
 
+// Host-side geometry object behind the opaque tpc_geometry handle.
+struct tpc_geometry {
+  int n_sectors, n_rows, npmax;
+  std::vector<int> npads, row_x;
+};
+
 namespace tpc {
+
+// Sets the thread-local message returned by tpc_last_error().
+void set_last_error(const char* msg);
 
 constexpr int kFrag = TPC_FRAGMENT_BINS;     // 256 time bins per window
 constexpr int kHalo = TPC_ZS_HALO;           // 3 time bins of halo each side

@@ -69,7 +69,7 @@ class tpc_timeframe_desc(ctypes.Structure):
 EXPORTS = ("tpc_params_default", "tpc_create_geometry", "tpc_destroy_geometry", "tpc_create_context",
            "tpc_destroy_context", "tpc_submit_timeframe", "tpc_poll", "tpc_get_clusters",
            "tpc_get_tracks", "tpc_get_links", "tpc_get_device_results", "tpc_get_stage_times",
-           "tpc_get_counters", "tpc_release", "tpc_last_error")
+           "tpc_get_counters", "tpc_release", "tpc_last_error", "tpc_find_clusters_noalloc")
 
 _lib = None
 
@@ -107,6 +107,8 @@ def load(build_if_missing: bool = True):
     L.tpc_get_stage_times.argtypes = [_P, _u64, _P]
     L.tpc_get_counters.argtypes = [_P, _u64, _P, ctypes.c_int]
     L.tpc_release.argtypes = [_P, _u64]
+    L.tpc_find_clusters_noalloc.argtypes = [_P, ctypes.POINTER(tpc_params), ctypes.c_int, _P, _u64, _P,
+                                            ctypes.c_uint32, _P, _u64, ctypes.POINTER(_u64), _P]
     L.tpc_last_error.argtypes = []
     L.tpc_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -245,6 +247,20 @@ def tpc_get_counters(ctx, ticket: int) -> dict:
 
 def tpc_release(ctx, ticket: int):
     _check(load().tpc_release(ctx, ticket))
+
+
+def tpc_find_clusters_noalloc(geom, pages, page_offsets, n_time_bins: int, clusters, device: int = 0,
+                              params: tpc_params | None = None, stream: int | None = None) -> int:
+    """Allocation-free finder: pages, page_offsets and clusters are torch CUDA
+    tensors owned by the caller (clusters: uint8 tensor of 16 * cap bytes).
+    Returns the number of clusters written."""
+    n = _u64()
+    cap = clusters.numel() * clusters.element_size() // 16
+    _check(load().tpc_find_clusters_noalloc(geom, ctypes.byref(params) if params is not None else None, device,
+                                            pages.data_ptr(), pages.numel() * pages.element_size(),
+                                            page_offsets.data_ptr(), int(n_time_bins), clusters.data_ptr(),
+                                            cap, ctypes.byref(n), stream))
+    return int(n.value)
 
 
 def tpc_last_error() -> str:
