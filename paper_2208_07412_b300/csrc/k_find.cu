@@ -319,9 +319,14 @@ __device__ __forceinline__ void make_cluster(const FindSmem& S, int ps_stride, i
   xyz = make_int4(xrow, 2 * (pad_fp - 128 * (np - 1)), 5 * (32768 * f + time_fp - 512), t);
 }
 
-// kAux: also write the row starts and the per-cluster (X, Y, Z, t_peak)
-// arrays the later stages read (false only for the allocation-free variant).
-template <bool kAux>
+// Output modes.  kScratch (the pipeline): each window reserves a span of the
+// scratch buffer with one atomic and writes its records there; a scan over the
+// window counts and k_compact_clusters then place them in canonical order and
+// derive the per-cluster (X, Y, Z, t_peak) arrays.  No window waits for
+// another.  Otherwise (the allocation-free entry point, which has no scratch
+// buffer for records): a decoupled look-back over the windows gives each its
+// canonical offset and the records are written in place; only the records.
+template <bool kScratch>
 __global__ void __launch_bounds__(kFindThreads, 2)
 k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -368,6 +373,7 @@ k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
   const int opt = (nown_words + blockDim.x - 1) / blockDim.x;
   uint8_t* own_stage = reinterpret_cast<uint8_t*>(S.st_rec);
 
+  if (kScratch && blockIdx.x == 0 && tid == 0) W.ctr[CTR_NWIN] = n_windows;
   // the plane starts empty and is kept empty between windows
   for (int i = tid; i < nplane / 2; i += blockDim.x) reinterpret_cast<uint32_t*>(S.plane)[i] = 0u;
   if (tid == 0 && (nplane & 1)) S.plane[nplane - 1] = 0;
@@ -525,7 +531,7 @@ k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
       }
       if (tid == 0) {
         S.ppre[nown_words] = (uint16_t)tot;
-        lookback_publish(W.win_state, (long long)w, tot);
+        if (!kScratch) lookback_publish(W.win_state, (long long)w, tot);
       }
       npk = (int)tot;
     }
@@ -547,25 +553,29 @@ k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
       make_cluster(S, ps_stride, nw, np, T, s, r, f, tt, p, G.xrow[r], S.st_rec[k], S.st_xyz[k]);
     }
 
-    // ---- 7. global offset of this window (decoupled look-back)
-    if (tid < 32) {
+    // ---- 7. where the records go: a scratch span (one atomic) or, without
+    // scratch, the canonical offset from the decoupled look-back
+    if (kScratch) {
+      if (tid == 0) {
+        const unsigned long long so = atomicAdd(&W.ctr[CTR_SCURSOR], (unsigned long long)npk);
+        if (so + npk > W.cap_cl) atomicOr(W.err, kErrOverflowCl);
+        W.win_cnt[w] = (unsigned long long)npk;
+        W.win_soff[w] = (uint32_t)min(so, (unsigned long long)W.cap_cl);
+        S.scan[33] = so;
+      }
+    } else if (tid < 32) {
       const unsigned long long base = lookback_wait(W.win_state, (long long)w, (unsigned long long)npk, W.err);
       if (tid == 0) {
         S.scan[33] = base;
-        // row starts are clamped to the capacity so that, after an overflow,
-        // every later kernel still indexes inside the cluster arrays
-        if (kAux && f == 0) W.row_start[sr] = (uint32_t)min(base, (unsigned long long)W.cap_cl);
-        if (w == n_windows - 1) {
-          if (kAux) W.row_start[G.n_sectors * G.n_rows] = (uint32_t)min(base + npk, (unsigned long long)W.cap_cl);
-          W.ctr[CTR_NCL] = base + npk;
-        }
+        if (w == n_windows - 1) W.ctr[CTR_NCL] = base + npk;
         if (base + npk > W.cap_cl) atomicOr(W.err, kErrOverflowCl);
       }
     }
     __syncthreads();
     const unsigned long long base = S.scan[33];
+    tpc_cluster* const dst = kScratch ? W.scratch_cl : W.clusters;
 
-    // ---- 8. write out: staged clusters coalesced, any beyond one thread each
+    // ---- 8. write out: staged records coalesced, any beyond one thread each
     for (int k = tid; k < npk; k += blockDim.x) {
       const unsigned long long idx = base + k;
       if (idx >= W.cap_cl) break;   // overflow: keep [0, cap) free of gaps, drop the rest
@@ -573,19 +583,12 @@ k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
       int4 xyz;
       if (k < kStage) {
         rec = S.st_rec[k];
-        xyz = S.st_xyz[k];
       } else {
         const int wo = rank_search(S.ppre, nown_words + 1, k);
         const int bit = __fns(S.pk[kHalo * nw + wo], 0, k - (int)S.ppre[wo] + 1);
         make_cluster(S, ps_stride, nw, np, T, s, r, f, kHalo + wo / nw, (wo % nw) * 32 + bit, G.xrow[r], rec, xyz);
       }
-      reinterpret_cast<uint4*>(W.clusters)[idx] = rec;
-      if (kAux) {
-        W.cl_x[idx] = xyz.x;
-        W.cl_y[idx] = xyz.y;
-        W.cl_z[idx] = xyz.z;
-        W.cl_t[idx] = xyz.w;
-      }
+      reinterpret_cast<uint4*>(dst)[idx] = rec;
     }
     __syncthreads();
 
@@ -609,6 +612,37 @@ k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
   }
 }
 
+// Places every window's scratch span at its canonical offset (win_cnt holds the
+// exclusive scan of the window counts; the total is in ctr[CTR_NCL]) and
+// derives the (X, Y, Z, t_peak) arrays and the row starts.  One warp per window.
+__global__ void __launch_bounds__(256)
+k_compact_clusters(DevGeom G, DevWork W, unsigned int n_windows) {
+  const int lane = threadIdx.x & 31;
+  const unsigned long long total = W.ctr[CTR_NCL];
+  const unsigned long long cap = W.cap_cl;
+  for (unsigned long long w = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5; w < n_windows;
+       w += ((unsigned long long)gridDim.x * blockDim.x) >> 5) {
+    const unsigned long long b = W.win_cnt[w];
+    const unsigned long long e = (w + 1 < n_windows) ? W.win_cnt[w + 1] : total;
+    const unsigned long long so = W.win_soff[w];
+    if (lane == 0 && w % G.n_frag == 0) W.row_start[w / G.n_frag] = (uint32_t)min(b, cap);
+    if (lane == 0 && w == n_windows - 1) W.row_start[G.n_sectors * G.n_rows] = (uint32_t)min(total, cap);
+    for (unsigned long long k = lane; b + k < e; k += 32) {
+      if (b + k >= cap || so + k >= cap) break;
+      const uint4 rec = __ldg(reinterpret_cast<const uint4*>(W.scratch_cl) + so + k);
+      const unsigned long long idx = b + k;
+      reinterpret_cast<uint4*>(W.clusters)[idx] = rec;
+      const int r = (rec.z >> 24) & 0xff;
+      const int pad_fp = rec.x & 0xffff, time_fp = rec.x >> 16, t = rec.w & 0xffff;
+      const int rr = r < G.n_rows ? r : 0;
+      W.cl_x[idx] = G.xrow[rr];
+      W.cl_y[idx] = 2 * (pad_fp - 128 * (G.npads[rr] - 1));
+      W.cl_z[idx] = 5 * (32768 * (t / kFrag) + time_fp - 512);
+      W.cl_t[idx] = t;
+    }
+  }
+}
+
 size_t find_smem_bytes(int npmax, int nw) {
   size_t o = ((size_t)kWinT * (npmax + 2 * kPad) * 2 + 15) & ~(size_t)15;
   o += 2 * (size_t)kWinT * nw * 4;
@@ -619,8 +653,12 @@ size_t find_smem_bytes(int npmax, int nw) {
   return o;
 }
 
+cudaError_t launch_scan(uint64_t* v, const unsigned long long* n_ptr, unsigned long long cap,
+                        unsigned long long* state, unsigned int* ticket, unsigned long long* total, uint32_t* err,
+                        int n_sm, cudaStream_t st);
+
 cudaError_t launch_find(const DevGeom& G, const DevParams& P, const DevWork& W, unsigned int n_windows,
-                        int n_sm, cudaStream_t st) {
+                        int n_sm, cudaStream_t st, unsigned long long* win_scan_state, int* launches) {
   size_t sm = find_smem_bytes(G.npmax, G.nw);
   static bool attr_set = false;
   if (!attr_set) {
@@ -631,6 +669,13 @@ cudaError_t launch_find(const DevGeom& G, const DevParams& P, const DevWork& W, 
   unsigned int grid = (unsigned int)min((long long)n_windows, (long long)n_sm * 2);
   if (grid == 0) grid = 1;
   k_find_clusters<true><<<grid, kFindThreads, sm, st>>>(G, P, W, n_windows);
+  cudaError_t e = launch_scan(reinterpret_cast<uint64_t*>(W.win_cnt), W.ctr + CTR_NWIN, n_windows, win_scan_state,
+                              W.tickets + TK_SCAN_W, W.ctr + CTR_NCL, W.err, n_sm, st);
+  if (e != cudaSuccess) return e;
+  unsigned long long gc = ((unsigned long long)n_windows * 32 + 255) / 256;
+  if (gc > (unsigned long long)n_sm * 8) gc = (unsigned long long)n_sm * 8;
+  k_compact_clusters<<<(unsigned)(gc ? gc : 1), 256, 0, st>>>(G, W, n_windows);
+  *launches += 3;
   return cudaGetLastError();
 }
 

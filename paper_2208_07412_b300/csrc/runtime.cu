@@ -20,7 +20,8 @@
 
 namespace tpc {
 size_t find_smem_bytes(int npmax, int nw);
-cudaError_t launch_find(const DevGeom&, const DevParams&, const DevWork&, unsigned int, int, cudaStream_t);
+cudaError_t launch_find(const DevGeom&, const DevParams&, const DevWork&, unsigned int, int, cudaStream_t,
+                        unsigned long long*, int*);
 cudaError_t launch_ca(const DevGeom&, const DevParams&, const DevWork&, int, cudaStream_t, int*);
 cudaError_t launch_merge(const DevGeom&, const DevParams&, const DevWork&, int, cudaStream_t,
                          unsigned long long*, int*);
@@ -60,7 +61,7 @@ struct Slot {
   cudaEvent_t ev_done = nullptr, ev_input = nullptr;
   // device buffers
   Buf pages, offsets, winstate, cl, clx, cly, clz, clt, rowstart, up, down, score, edge, jump, chlen, scanv,
-      scanst, chainof, clchain, ch_i32, besta, bestb, trk_i32, trackcl, cl2trk, tracks, ctrl;
+      scanst, chainof, clchain, ch_i32, besta, bestb, trk_i32, trackcl, cl2trk, tracks, ctrl, scratch, wincnt, winsoff;
   unsigned long long* h_ctrl = nullptr;   // pinned copy of [ctr | err]
   // capacities
   uint64_t cap_pages = 0, cap_windows = 0, cap_cl = 0, cap_ch = 0;
@@ -176,8 +177,9 @@ static cudaError_t ensure(Buf& b, size_t bytes) {
 }
 
 static size_t slot_bytes(uint64_t pages, uint64_t windows, uint64_t cap_cl, uint64_t cap_ch, int nsr) {
-  size_t b = pages + 16 + windows * 16 + cap_cl * (16 + 16 + 8 + 8 + 8 + 8 + 4 + 8 + 4 + 4 + 4 + 4) +
-             (scan_tiles(cap_cl) + scan_tiles(cap_ch)) * 8 + cap_ch * (12 * 4 + 8 + 16 + sizeof(tpc_track)) +
+  size_t b = pages + 16 + windows * 28 + cap_cl * (16 + 16 + 16 + 8 + 8 + 8 + 8 + 4 + 8 + 4 + 4 + 4 + 4) +
+             (scan_tiles(cap_cl) + scan_tiles(cap_ch) + scan_tiles(windows)) * 8 +
+             cap_ch * (12 * 4 + 8 + 16 + sizeof(tpc_track)) +
              (size_t)(nsr + 1) * 4 + 1024;
   return b;
 }
@@ -197,10 +199,13 @@ static tpc_status slot_reserve(tpc_context* ctx, Slot& s, uint64_t pages_bytes, 
   if (windows > s.cap_windows) {
     CUDA_TRY(ensure(s.offsets, windows * 8));
     CUDA_TRY(ensure(s.winstate, windows * 8));
+    CUDA_TRY(ensure(s.wincnt, windows * 8));
+    CUDA_TRY(ensure(s.winsoff, windows * 4));
     s.cap_windows = windows;
   }
   if (cap_cl > s.cap_cl) {
     CUDA_TRY(ensure(s.cl, cap_cl * 16));
+    CUDA_TRY(ensure(s.scratch, cap_cl * 16));
     CUDA_TRY(ensure(s.clx, cap_cl * 4)); CUDA_TRY(ensure(s.cly, cap_cl * 4));
     CUDA_TRY(ensure(s.clz, cap_cl * 4)); CUDA_TRY(ensure(s.clt, cap_cl * 4));
     CUDA_TRY(ensure(s.up, cap_cl * 4)); CUDA_TRY(ensure(s.down, cap_cl * 4));
@@ -218,7 +223,7 @@ static tpc_status slot_reserve(tpc_context* ctx, Slot& s, uint64_t pages_bytes, 
     CUDA_TRY(ensure(s.tracks, cap_ch * sizeof(tpc_track)));
     s.cap_ch = cap_ch;
   }
-  CUDA_TRY(ensure(s.scanst, (scan_tiles(s.cap_cl) + scan_tiles(s.cap_ch)) * 8));
+  CUDA_TRY(ensure(s.scanst, (scan_tiles(s.cap_cl) + scan_tiles(s.cap_ch) + scan_tiles(s.cap_windows)) * 8));
   CUDA_TRY(ensure(s.rowstart, (size_t)(nsr + 1) * 4));
   CUDA_TRY(ensure(s.ctrl, 256));
   ctx->used = ctx->used - cur + slot_bytes(s.cap_pages, s.cap_windows, s.cap_cl, s.cap_ch, nsr);
@@ -228,6 +233,9 @@ static tpc_status slot_reserve(tpc_context* ctx, Slot& s, uint64_t pages_bytes, 
   W.cl_x = (int32_t*)s.clx.p; W.cl_y = (int32_t*)s.cly.p; W.cl_z = (int32_t*)s.clz.p; W.cl_t = (int32_t*)s.clt.p;
   W.row_start = (uint32_t*)s.rowstart.p;
   W.win_state = (unsigned long long*)s.winstate.p;
+  W.scratch_cl = (tpc_cluster*)s.scratch.p;
+  W.win_cnt = (unsigned long long*)s.wincnt.p;
+  W.win_soff = (uint32_t*)s.winsoff.p;
   W.up = (int32_t*)s.up.p; W.down = (int32_t*)s.down.p;
   W.score = (int64_t*)s.score.p;
   W.edge_key = (unsigned long long*)s.edge.p;
@@ -258,7 +266,8 @@ static tpc_status slot_reserve(tpc_context* ctx, Slot& s, uint64_t pages_bytes, 
 static void slot_free(tpc_context* ctx, Slot& s) {
   Buf* all[] = {&s.pages, &s.offsets, &s.winstate, &s.cl, &s.clx, &s.cly, &s.clz, &s.clt, &s.rowstart, &s.up,
                 &s.down, &s.score, &s.edge, &s.jump, &s.chlen, &s.scanv, &s.scanst, &s.chainof, &s.clchain,
-                &s.ch_i32, &s.besta, &s.bestb, &s.trk_i32, &s.trackcl, &s.cl2trk, &s.tracks, &s.ctrl};
+                &s.ch_i32, &s.besta, &s.bestb, &s.trk_i32, &s.trackcl, &s.cl2trk, &s.tracks, &s.ctrl,
+                &s.scratch, &s.wincnt, &s.winsoff};
   for (Buf* b : all) free_buf(*b);
   for (auto& e : s.ev_stage) if (e) cudaEventDestroy(e);
   if (s.ev_done) cudaEventDestroy(s.ev_done);
@@ -349,12 +358,10 @@ static tpc_status enqueue(tpc_context* ctx, Slot& s) {
   const bool timing = ctx->flags & TPC_CTX_STAGE_TIMING;
   s.launches = 0;
   CUDA_TRY(cudaMemsetAsync(s.ctrl.p, 0, 256, st));
-  CUDA_TRY(cudaMemsetAsync(W.win_state, 0, (size_t)s.n_windows * 8, st));
-  const size_t tiles_a = scan_tiles(s.cap_cl);
-  CUDA_TRY(cudaMemsetAsync(W.scan_state, 0, (tiles_a + scan_tiles(s.cap_ch)) * 8, st));
+  const size_t tiles_a = scan_tiles(s.cap_cl), tiles_b = scan_tiles(s.cap_ch);
+  CUDA_TRY(cudaMemsetAsync(W.scan_state, 0, (tiles_a + tiles_b + scan_tiles(s.n_windows)) * 8, st));
   if (timing) CUDA_TRY(cudaEventRecord(s.ev_stage[0], st));
-  CUDA_TRY(launch_find(G, ctx->P, W, s.n_windows, ctx->n_sm, st));
-  s.launches += 1;
+  CUDA_TRY(launch_find(G, ctx->P, W, s.n_windows, ctx->n_sm, st, W.scan_state + tiles_a + tiles_b, &s.launches));
   if (timing) CUDA_TRY(cudaEventRecord(s.ev_stage[1], st));
   CUDA_TRY(launch_ca(G, ctx->P, W, ctx->n_sm, st, &s.launches));
   if (timing) CUDA_TRY(cudaEventRecord(s.ev_stage[2], st));

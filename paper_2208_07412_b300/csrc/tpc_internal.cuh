@@ -68,7 +68,10 @@ struct DevWork {
   tpc_cluster* clusters;
   int32_t* cl_x; int32_t* cl_y; int32_t* cl_z; int32_t* cl_t;
   uint32_t* row_start;           // [n_sectors * n_rows + 1]
-  unsigned long long* win_state;  // look-back states of the finder windows
+  unsigned long long* win_state;  // look-back states of the finder windows (allocation-free mode)
+  tpc_cluster* scratch_cl;       // finder output, window spans in completion order
+  unsigned long long* win_cnt;   // clusters per window, scanned in place to canonical bases
+  uint32_t* win_soff;            // start of each window's span in scratch_cl
   // CA
   int32_t* up; int32_t* down;
   int64_t* score;
@@ -106,9 +109,11 @@ enum {
   CTR_NFP64 = 3,      // FP64 covariance redos
   CTR_MERGED0 = 4,    // merges in pass p at CTR_MERGED0 + p (up to 16 passes)
   CTR_NCLCL = 20,     // clusters assigned to tracks
+  CTR_SCURSOR = 21,   // next free scratch record of the finder
+  CTR_NWIN = 22,      // windows of the timeframe
   CTR_COUNT = 24
 };
-enum { TK_FIND = 0, TK_SCAN_A = 1, TK_SCAN_B = 2, kNumTickets = 4 };
+enum { TK_FIND = 0, TK_SCAN_A = 1, TK_SCAN_B = 2, TK_SCAN_W = 3, kNumTickets = 4 };
 
 // ------------------------------------------------------------------ helpers
 __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
