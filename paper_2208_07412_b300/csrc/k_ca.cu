@@ -32,51 +32,144 @@ __device__ __forceinline__ unsigned lower_bound_t(const int32_t* __restrict__ t,
 __device__ __forceinline__ long long llabs_(long long v) { return v < 0 ? -v : v; }
 
 // ---------------------------------------------------------------- neighbours
-__global__ void k_ca_neighbours(DevGeom G, DevParams P, DevWork W) {
+// One block per pad row (grid-stride over the sector x row list), in chunks of
+// kCaChunk clusters: the slices of rows r-1 and r+1 that can hold a partner of
+// the chunk (time-sorted, so two binary searches bound them) are staged in
+// shared memory as (t, Y, Z); every search and candidate loop then runs there.
+// A slice larger than the stage is read from global memory instead.  The
+// iteration order (d ascending, then u ascending, strict <) is the definition's
+// tie rule.
+constexpr int kCaThreads = 256, kCaChunk = 256, kCaStage = 1536;
+
+struct Slice {
+  const int32_t* t; const int32_t* y; const int32_t* z;
+  unsigned base, n;   // cluster index of element 0, element count
+};
+
+__device__ __forceinline__ unsigned lb_slice(const int32_t* t, unsigned n, int v) {
+  unsigned lo = 0, hi = n;
+  while (lo < hi) {
+    const unsigned mid = (lo + hi) >> 1;
+    if (t[mid] < v) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(kCaThreads)
+k_ca_neighbours(DevGeom G, DevParams P, DevWork W) {
+  __shared__ int32_t sm_t[2][kCaStage], sm_y[2][kCaStage], sm_z[2][kCaStage];
+  __shared__ unsigned sm_rng[4];
   const unsigned long long n = n_clusters(W);
-  const int R = G.n_rows;
-  for (unsigned long long c = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; c < n;
-       c += (unsigned long long)gridDim.x * blockDim.x) {
-    const uint4 rec = __ldg(reinterpret_cast<const uint4*>(W.clusters) + c);
-    const int r = (rec.z >> 24) & 0xff, s = rec.w >> 24;
+  const int R = G.n_rows, nsr = G.n_sectors * R;
+  const int tid = threadIdx.x;
+  // edge keys start empty everywhere; the first and last rows get no pair
+  for (unsigned long long c = blockIdx.x * (unsigned long long)blockDim.x + tid; c < n;
+       c += (unsigned long long)gridDim.x * blockDim.x)
     W.edge_key[c] = ~0ull;
-    if (r == 0 || r >= R - 1 || s >= G.n_sectors) {
-      W.up[c] = -1; W.down[c] = -1; W.score[c] = -1;
+  for (int sr = blockIdx.x; sr < nsr; sr += gridDim.x) {
+    const int r = sr % R;
+    const unsigned lo = min((unsigned long long)W.row_start[sr], n), hi = min((unsigned long long)W.row_start[sr + 1], n);
+    if (r == 0 || r == R - 1) {
+      for (unsigned c = lo + tid; c < hi; c += blockDim.x) { W.up[c] = -1; W.down[c] = -1; W.score[c] = -1; }
       continue;
     }
-    const int sr = s * R + r;
     const long long Xc = G.xrow[r], Xd = G.xrow[r - 1], Xu = G.xrow[r + 1];
-    const long long Yc = __ldg(W.cl_y + c), Zc = __ldg(W.cl_z + c);
-    const int tc = __ldg(W.cl_t + c);
     const long long dxd = Xc - Xd, dxu = Xu - Xc;
-    const unsigned dlo = W.row_start[sr - 1], dhi = W.row_start[sr];
-    const unsigned ulo = W.row_start[sr + 1], uhi = W.row_start[sr + 2];
     const int wd = (int)((P.sz_num * dxd) / (P.sz_den * 640LL)) + 5;
     const int wu = (int)((P.sz_num * dxu) / (P.sz_den * 640LL)) + 5;
-    const unsigned d0 = lower_bound_t(W.cl_t, dlo, dhi, tc - wd);
-    const unsigned u0 = lower_bound_t(W.cl_t, ulo, uhi, tc - wu);
     const long long lim = (long long)P.ca_cut * (Xu - Xd);
-    long long best = -1;
-    int bd = -1, bu = -1;
-    for (unsigned d = d0; d < dhi; d++) {
-      if (__ldg(W.cl_t + d) > tc + wd) break;
-      const long long Yd = __ldg(W.cl_y + d), Zd = __ldg(W.cl_z + d);
-      if (llabs_(Yc - Yd) * P.sy_den > P.sy_num * dxd) continue;
-      if (llabs_(Zc - Zd) * P.sz_den > P.sz_num * dxd) continue;
-      for (unsigned u = u0; u < uhi; u++) {
-        if (__ldg(W.cl_t + u) > tc + wu) break;
-        const long long Yu = __ldg(W.cl_y + u), Zu = __ldg(W.cl_z + u);
-        if (llabs_(Yu - Yc) * P.sy_den > P.sy_num * dxu) continue;
-        if (llabs_(Zu - Zc) * P.sz_den > P.sz_num * dxu) continue;
-        const long long devy = (Yu - Yc) * dxd - (Yc - Yd) * dxu;
-        const long long devz = (Zu - Zc) * dxd - (Zc - Zd) * dxu;
-        if (llabs_(devy) > lim || llabs_(devz) > lim) continue;
-        const long long sc = devy * devy + devz * devz;
-        // d ascending, then u ascending; strict < keeps the smallest (d, u)
-        if (best < 0 || sc < best) { best = sc; bd = (int)d; bu = (int)u; }
+    const unsigned dlo = W.row_start[sr - 1], dhi = min((unsigned long long)W.row_start[sr], n);
+    const unsigned ulo = min((unsigned long long)W.row_start[sr + 1], n), uhi = min((unsigned long long)W.row_start[sr + 2], n);
+    for (unsigned cs = lo; cs < hi; cs += kCaChunk) {
+      const unsigned ce = min(cs + kCaChunk, hi);
+      if (tid < 2) {
+        // slice of the neighbour row that can pair with clusters [cs, ce)
+        const int tmin = W.cl_t[cs], tmax = W.cl_t[ce - 1];
+        const unsigned a = tid == 0 ? dlo : ulo, b = tid == 0 ? dhi : uhi;
+        const int w = tid == 0 ? wd : wu;
+        sm_rng[2 * tid] = lower_bound_t(W.cl_t, a, b, tmin - w);
+        sm_rng[2 * tid + 1] = lower_bound_t(W.cl_t, a, b, tmax + w + 1);
       }
+      __syncthreads();
+      Slice sl[2];
+#pragma unroll
+      for (int k = 0; k < 2; k++) {
+        const unsigned a = sm_rng[2 * k], b = sm_rng[2 * k + 1];
+        sl[k].base = a;
+        sl[k].n = b > a ? b - a : 0;
+        if (sl[k].n <= (unsigned)kCaStage) {
+          for (unsigned i = tid; i < sl[k].n; i += blockDim.x) {
+            sm_t[k][i] = W.cl_t[a + i];
+            sm_y[k][i] = W.cl_y[a + i];
+            sm_z[k][i] = W.cl_z[a + i];
+          }
+          sl[k].t = sm_t[k]; sl[k].y = sm_y[k]; sl[k].z = sm_z[k];
+        } else {
+          sl[k].t = W.cl_t + a; sl[k].y = W.cl_y + a; sl[k].z = W.cl_z + a;
+        }
+      }
+      __syncthreads();
+      const unsigned c = cs + tid;
+      if (c < ce) {
+        const long long Yc = W.cl_y[c], Zc = W.cl_z[c];
+        const int tc = W.cl_t[c];
+        const unsigned d0 = lb_slice(sl[0].t, sl[0].n, tc - wd);
+        const unsigned u0 = lb_slice(sl[1].t, sl[1].n, tc - wu);
+        // candidates passing the window cuts, in ascending index order
+        constexpr int kMaxCand = 8;
+        unsigned di[kMaxCand], ui[kMaxCand];
+        int nd = 0, nu = 0;
+        bool spill = false;
+        for (unsigned i = d0; i < sl[0].n && sl[0].t[i] <= tc + wd; i++) {
+          if (llabs_(Yc - sl[0].y[i]) * P.sy_den > P.sy_num * dxd) continue;
+          if (llabs_(Zc - sl[0].z[i]) * P.sz_den > P.sz_num * dxd) continue;
+          if (nd < kMaxCand) di[nd] = i; else spill = true;
+          nd++;
+        }
+        for (unsigned j = u0; nd > 0 && j < sl[1].n && sl[1].t[j] <= tc + wu; j++) {
+          if (llabs_(sl[1].y[j] - Yc) * P.sy_den > P.sy_num * dxu) continue;
+          if (llabs_(sl[1].z[j] - Zc) * P.sz_den > P.sz_num * dxu) continue;
+          if (nu < kMaxCand) ui[nu] = j; else spill = true;
+          nu++;
+        }
+        long long best = -1;
+        int bd = -1, bu = -1;
+        if (!spill) {
+          for (int a = 0; a < nd; a++) {
+            const long long Yd = sl[0].y[di[a]], Zd = sl[0].z[di[a]];
+            for (int b = 0; b < nu; b++) {
+              const long long Yu = sl[1].y[ui[b]], Zu = sl[1].z[ui[b]];
+              const long long devy = (Yu - Yc) * dxd - (Yc - Yd) * dxu;
+              const long long devz = (Zu - Zc) * dxd - (Zc - Zd) * dxu;
+              if (llabs_(devy) > lim || llabs_(devz) > lim) continue;
+              const long long sc = devy * devy + devz * devz;
+              if (best < 0 || sc < best) { best = sc; bd = (int)(sl[0].base + di[a]); bu = (int)(sl[1].base + ui[b]); }
+            }
+          }
+        } else {
+          // more candidates than the lists hold: the plain double loop
+          for (unsigned i = d0; i < sl[0].n; i++) {
+            if (sl[0].t[i] > tc + wd) break;
+            const long long Yd = sl[0].y[i], Zd = sl[0].z[i];
+            if (llabs_(Yc - Yd) * P.sy_den > P.sy_num * dxd) continue;
+            if (llabs_(Zc - Zd) * P.sz_den > P.sz_num * dxd) continue;
+            for (unsigned j = u0; j < sl[1].n; j++) {
+              if (sl[1].t[j] > tc + wu) break;
+              const long long Yu = sl[1].y[j], Zu = sl[1].z[j];
+              if (llabs_(Yu - Yc) * P.sy_den > P.sy_num * dxu) continue;
+              if (llabs_(Zu - Zc) * P.sz_den > P.sz_num * dxu) continue;
+              const long long devy = (Yu - Yc) * dxd - (Yc - Yd) * dxu;
+              const long long devz = (Zu - Zc) * dxd - (Zc - Zd) * dxu;
+              if (llabs_(devy) > lim || llabs_(devz) > lim) continue;
+              const long long sc = devy * devy + devz * devz;
+              if (best < 0 || sc < best) { best = sc; bd = (int)(sl[0].base + i); bu = (int)(sl[1].base + j); }
+            }
+          }
+        }
+        W.up[c] = bu; W.down[c] = bd; W.score[c] = best;
+      }
+      __syncthreads();
     }
-    W.up[c] = bu; W.down[c] = bd; W.score[c] = best;
   }
 }
 
@@ -180,6 +273,7 @@ __global__ void k_chain_table(DevParams P, DevWork W) {
       if (pos == 0) {
         W.ch_root[k] = (int)c; W.ch_len[k] = L; W.ch_next[k] = -1; W.ch_prev[k] = -1;
         W.best_a[k] = ~0ull;
+        W.best_b[k] = ~0ull;
       }
       if (pos == 1) W.ch_b2[k] = (int)c;
       if (pos == L - 1) W.ch_top[k] = (int)c;
@@ -253,7 +347,7 @@ static inline unsigned grid_for(unsigned long long cap, int n_sm, int per_sm) {
 cudaError_t launch_ca(const DevGeom& G, const DevParams& P, const DevWork& W, int n_sm, cudaStream_t st,
                       int* launches) {
   const unsigned g = grid_for(W.cap_cl, n_sm, 8);
-  k_ca_neighbours<<<g, 256, 0, st>>>(G, P, W);
+  k_ca_neighbours<<<(unsigned)min(G.n_sectors * G.n_rows, n_sm * 8), kCaThreads, 0, st>>>(G, P, W);
   k_ca_edge_min<<<g, 256, 0, st>>>(G, W);
   k_ca_edge_apply<<<g, 256, 0, st>>>(G, W);
   k_links<<<g, 256, 0, st>>>(W);

@@ -152,21 +152,22 @@ __device__ __forceinline__ bool ud_pd(const UD<T>& M) {
   return ok;
 }
 
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(64)
 k_fit(DevGeom G, DevParams P, DevWork W) {
   const unsigned long long ntrk = W.ctr[CTR_NTRK];
   const unsigned long long nmax = ntrk < W.cap_ch ? ntrk : W.cap_ch;
   unsigned int fp64_count = 0;
-  for (unsigned long long t = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; t < nmax;
-       t += (unsigned long long)gridDim.x * blockDim.x) {
+  for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < nmax;
+       i += (unsigned long long)gridDim.x * blockDim.x) {
+    const unsigned long long t = (unsigned long long)W.fit_order[i];   // longest tracks first
     const int n = W.trk_ncl[t];
-    const int* lst = W.track_cl + W.trk_off[t];
-    const int c0 = lst[0];
-    const int X0 = W.cl_x[c0], Y0 = W.cl_y[c0], Z0 = W.cl_z[c0];
+    const int4* pts = W.trk_xyz + W.trk_off[t];   // (X, Y, Z, cluster), innermost first
+    const int4 p0 = pts[0], pm = pts[(n - 1) / 2], po = pts[n - 1];
+    const int c0 = p0.w;
+    const int X0 = p0.x, Y0 = p0.y, Z0 = p0.z;
     // ---- initial state: circle through innermost, middle and outermost clusters
-    const int cm = lst[(n - 1) / 2], co = lst[n - 1];
-    const float ax = (float)(W.cl_x[cm] - X0) * kU, ay = (float)(W.cl_y[cm] - Y0) * kU;
-    const float cx = (float)(W.cl_x[co] - X0) * kU, cy = (float)(W.cl_y[co] - Y0) * kU;
+    const float ax = (float)(pm.x - X0) * kU, ay = (float)(pm.y - Y0) * kU;
+    const float cx = (float)(po.x - X0) * kU, cy = (float)(po.y - Y0) * kU;
     const float bx = cx - ax, by = cy - ay;
     const float la = sqrtf(ax * ax + ay * ay), lb = sqrtf(bx * bx + by * by), lc = sqrtf(cx * cx + cy * cy);
     const float kc = 2.f * (ax * cy - ay * cx) / (la * lb * lc);
@@ -175,10 +176,10 @@ k_fit(DevGeom G, DevParams P, DevWork W) {
     const float phic = atan2f(cy, cx);
     const float klc = kc * lc;
     const float arc = fabsf(klc) < 1e-3f ? lc * (1.f + klc * klc * (1.f / 24.f)) : 2.f * half / kc;
-    const float zo = (float)(W.cl_z[co] - Z0) * kU;
+    const float zo = (float)(po.z - Z0) * kU;
     float s[5] = {cy, zo, sinf(phic + half), zo / arc, kc / P.kfac};
     UD<float> M;
-    int xcur = W.cl_x[co];
+    int xcur = po.x;
     int flags = 0, n_used = 0, nfp64 = 0;
     float chi2 = 0.f;
     for (int pass = 0; pass < P.fit_passes; pass++) {
@@ -186,17 +187,18 @@ k_fit(DevGeom G, DevParams P, DevWork W) {
       chi2 = 0.f;
       n_used = 0;
       const bool inward = (pass & 1) == 0;
+      int4 nxt = pts[inward ? n - 1 : 0];
       for (int jj = 0; jj < n; jj++) {
-        const int i = inward ? n - 1 - jj : jj;
-        const int c = lst[i];
-        const int Xi = W.cl_x[c];
+        const int4 cur = nxt;
+        if (jj + 1 < n) nxt = pts[inward ? n - 2 - jj : jj + 1];   // one cluster ahead
+        const int Xi = cur.x;
         if (Xi != xcur) {
           Jac<float> J;
           if (!transport(P.kfac, s, (float)(Xi - xcur) * kU, J)) { flags |= TPC_TRK_STOPPED; break; }
           ud_propagate(M, J);
           xcur = Xi;
         }
-        const int dY = W.cl_y[c] - Y0, dZ = W.cl_z[c] - Z0;
+        const int dY = cur.y - Y0, dZ = cur.z - Z0;
         float s0[5];
         UD<float> M0 = M;
 #pragma unroll
@@ -269,10 +271,10 @@ k_fit(DevGeom G, DevParams P, DevWork W) {
 
 cudaError_t launch_fit(const DevGeom& G, const DevParams& P, const DevWork& W, int n_sm, cudaStream_t st,
                        int* launches) {
-  unsigned long long g = (W.cap_ch + 127) / 128;
-  unsigned long long m = (unsigned long long)n_sm * 16;
+  unsigned long long g = (W.cap_ch + 63) / 64;
+  unsigned long long m = (unsigned long long)n_sm * 32;
   if (g > m) g = m;
-  k_fit<<<(unsigned)(g ? g : 1), 128, 0, st>>>(G, P, W);
+  k_fit<<<(unsigned)(g ? g : 1), 64, 0, st>>>(G, P, W);
   *launches += 1;
   return cudaGetLastError();
 }

@@ -2,12 +2,15 @@
 // library's definition; the paper's section "Hardware and data flow" names the
 // TPC tracking the EPN GPUs run, not its merge rule, which is this library's).
 //
-// A pass: every chain top end (a1 below a2) searches the rows gap_min..gap_max
-// above a2 for chain bottom ends b1 (b2 above) whose four integer straight-line
-// residuals pass the cut; the best bottom per top is kept locally and the best
-// top per bottom by a 64-bit atomicMin on (score << 32 | chain index).  Mutual
-// best pairs link.  Passes repeat until one links nothing; later passes exit at
-// once, so a fixed number of launches gives the fixpoint (graph friendly).
+// The ends of merged groups are always ends of the original chains, so the
+// candidate pairs (top end a1 below a2, bottom end b1 below b2, four integer
+// straight-line residuals within the cut) do not change between passes: they
+// are searched once, one thread per (top chain, gap row), and stored.  A pass
+// then takes, among the stored pairs whose top is still a group top and whose
+// bottom is still a group bottom, the best bottom per top and the best top per
+// bottom by 64-bit atomicMin on (score << 32 | chain index), and links the
+// mutual-best pairs.  Passes repeat until one links nothing; later passes exit
+// at once, so a fixed number of launches gives the fixpoint (graph friendly).
 #include "tpc_internal.cuh"
 
 namespace tpc {
@@ -35,48 +38,69 @@ __device__ __forceinline__ unsigned lower_bound_tm(const int32_t* __restrict__ t
   return lo;
 }
 
-__global__ void k_merge_best(DevGeom G, DevParams P, DevWork W, int pass) {
-  if (pass > 0 && W.ctr[CTR_MERGED0 + pass - 1] == 0) return;
+__global__ void k_merge_cand(DevGeom G, DevParams P, DevWork W) {
   const unsigned long long nch = n_chains_m(W);
-  unsigned long long* bestA = W.best_a + (size_t)(pass & 1) * W.cap_ch;
+  const int ngap = P.gap_max - P.gap_min + 1;
+  unsigned long long* bestA = W.best_a;   // pass 0 buffer
   const int R = G.n_rows;
   const long long MC = P.merge_cut;
-  for (unsigned long long k = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; k < nch;
-       k += (unsigned long long)gridDim.x * blockDim.x) {
-    unsigned long long bestkey = ~0ull;
-    if (W.ch_next[k] < 0) {
-      const int a2 = W.ch_top[k], a1 = W.ch_top2[k];
-      const uint4 rec = __ldg(reinterpret_cast<const uint4*>(W.clusters) + a2);
-      const int r2 = (rec.z >> 24) & 0xff, s = min((int)(rec.w >> 24), G.n_sectors - 1);
-      const long long Xa1 = W.cl_x[a1], Ya1 = W.cl_y[a1], Za1 = W.cl_z[a1];
-      const long long Xa2 = W.cl_x[a2], Ya2 = W.cl_y[a2], Za2 = W.cl_z[a2];
-      const long long dxa = Xa2 - Xa1;
-      for (int rb = r2 + P.gap_min; rb <= r2 + P.gap_max && rb < R && r2 < R; rb++) {
-        const long long Xb = G.xrow[rb];
-        const long long zp = Za2 + floordiv_ll((Za2 - Za1) * (Xb - Xa2), dxa);
-        const long long tlo = floordiv_ll(zp - MC - 2, 640) - 3;
-        const long long thi = floordiv_ll(zp + MC + 2, 640) + 3;
-        const unsigned lo = W.row_start[s * R + rb], hi = W.row_start[s * R + rb + 1];
-        for (unsigned b1 = lower_bound_tm(W.cl_t, lo, hi, tlo); b1 < hi; b1++) {
-          if ((long long)__ldg(W.cl_t + b1) > thi) break;
-          const int kb = W.cl_chain[b1];
-          if (kb < 0 || W.ch_root[kb] != (int)b1 || W.ch_prev[kb] >= 0) continue;
-          const int b2 = W.ch_b2[kb];
-          const long long Xb1 = W.cl_x[b1], Yb1 = W.cl_y[b1], Zb1 = W.cl_z[b1];
-          const long long Xb2 = W.cl_x[b2], Yb2 = W.cl_y[b2], Zb2 = W.cl_z[b2];
-          const long long ry = extrap_res(Xa1, Ya1, Xa2, Ya2, Xb1, Yb1);
-          const long long rz = extrap_res(Xa1, Za1, Xa2, Za2, Xb1, Zb1);
-          const long long sy = extrap_res(Xb2, Yb2, Xb1, Yb1, Xa2, Ya2);
-          const long long sz = extrap_res(Xb2, Zb2, Xb1, Zb1, Xa2, Za2);
-          if (absll(ry) > MC || absll(rz) > MC || absll(sy) > MC || absll(sz) > MC) continue;
-          const unsigned long long sc = (unsigned long long)(ry * ry + rz * rz + sy * sy + sz * sz);
-          const unsigned long long key = (sc << 32) | (unsigned)kb;
-          if (key < bestkey) bestkey = key;
-          atomicMin(&bestA[kb], (sc << 32) | (unsigned)k);
-        }
+  for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < nch * ngap;
+       i += (unsigned long long)gridDim.x * blockDim.x) {
+    const unsigned long long k = i / ngap;
+    const int a2 = W.ch_top[k], a1 = W.ch_top2[k];
+    const uint4 rec = __ldg(reinterpret_cast<const uint4*>(W.clusters) + a2);
+    const int r2 = (rec.z >> 24) & 0xff, s = min((int)(rec.w >> 24), G.n_sectors - 1);
+    const int rb = r2 + P.gap_min + (int)(i % ngap);
+    if (r2 >= R || rb >= R) continue;
+    const long long Xa1 = W.cl_x[a1], Ya1 = W.cl_y[a1], Za1 = W.cl_z[a1];
+    const long long Xa2 = W.cl_x[a2], Ya2 = W.cl_y[a2], Za2 = W.cl_z[a2];
+    const long long dxa = Xa2 - Xa1;
+    const long long Xb = G.xrow[rb];
+    const long long zp = Za2 + floordiv_ll((Za2 - Za1) * (Xb - Xa2), dxa);
+    const long long tlo = floordiv_ll(zp - MC - 2, 640) - 3;
+    const long long thi = floordiv_ll(zp + MC + 2, 640) + 3;
+    const unsigned lo = W.row_start[s * R + rb], hi = W.row_start[s * R + rb + 1];
+    for (unsigned b1 = lower_bound_tm(W.cl_t, lo, hi, tlo); b1 < hi; b1++) {
+      if ((long long)__ldg(W.cl_t + b1) > thi) break;
+      const int kb = W.cl_chain[b1];
+      if (kb < 0 || W.ch_root[kb] != (int)b1) continue;
+      const int b2 = W.ch_b2[kb];
+      const long long Xb1 = W.cl_x[b1], Yb1 = W.cl_y[b1], Zb1 = W.cl_z[b1];
+      const long long Xb2 = W.cl_x[b2], Yb2 = W.cl_y[b2], Zb2 = W.cl_z[b2];
+      const long long ry = extrap_res(Xa1, Ya1, Xa2, Ya2, Xb1, Yb1);
+      const long long rz = extrap_res(Xa1, Za1, Xa2, Za2, Xb1, Zb1);
+      const long long sy = extrap_res(Xb2, Yb2, Xb1, Yb1, Xa2, Ya2);
+      const long long sz = extrap_res(Xb2, Zb2, Xb1, Zb1, Xa2, Za2);
+      if (absll(ry) > MC || absll(rz) > MC || absll(sy) > MC || absll(sz) > MC) continue;
+      const unsigned long long sc = (unsigned long long)(ry * ry + rz * rz + sy * sy + sz * sz);
+      // pass 0: every chain is both a group top and a group bottom
+      atomicMin(&W.best_b[k], (sc << 32) | (unsigned)kb);
+      atomicMin(&bestA[kb], (sc << 32) | (unsigned)k);
+      const unsigned long long slot = atomicAdd(&W.ctr[CTR_NCAND], 1ull);
+      if (slot < W.cap_cand) {
+        W.cand_ab[slot] = (k << 32) | (unsigned)kb;
+        W.cand_sc[slot] = (uint32_t)sc;
+      } else {
+        atomicOr(W.err, kErrOverflowCh);
       }
     }
-    W.best_b[k] = bestkey;
+  }
+}
+
+// Passes after the first: the stored pairs whose ends are still group ends.
+__global__ void k_merge_best(DevWork W, int pass) {
+  if (W.ctr[CTR_MERGED0 + pass - 1] == 0) return;
+  unsigned long long n = W.ctr[CTR_NCAND];
+  if (n > W.cap_cand) n = W.cap_cand;
+  unsigned long long* bestA = W.best_a + (size_t)(pass & 1) * W.cap_ch;
+  for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
+       i += (unsigned long long)gridDim.x * blockDim.x) {
+    const unsigned long long ab = W.cand_ab[i];
+    const unsigned k = (unsigned)(ab >> 32), kb = (unsigned)ab;
+    if (W.ch_next[k] >= 0 || W.ch_prev[kb] >= 0) continue;
+    const unsigned long long sc = W.cand_sc[i];
+    atomicMin(&W.best_b[k], (sc << 32) | kb);
+    atomicMin(&bestA[kb], (sc << 32) | k);
   }
 }
 
@@ -90,6 +114,7 @@ __global__ void k_merge_link(DevWork W, int pass) {
        k += (unsigned long long)gridDim.x * blockDim.x) {
     nextA[k] = ~0ull;
     const unsigned long long key = W.best_b[k];
+    W.best_b[k] = ~0ull;   // ready for the next pass
     if (key == ~0ull) continue;
     const unsigned kb = (unsigned)key;
     if ((unsigned)bestA[kb] == (unsigned)k) {
@@ -136,6 +161,7 @@ __global__ void k_group_assign(DevParams P, DevWork W) {
       W.trk_first[t] = W.ch_root[k];
       W.trk_ncl[t] = W.grp_total[k];
       W.trk_off[t] = (int)(unsigned)v;
+      atomicAdd(&W.len_hist[255 - min(W.grp_total[k], 255)], 1u);
     }
     int g = (int)k, run = 0;
     for (int it = 0; g >= 0 && it < kMaxRowsDev; it++) {
@@ -158,10 +184,34 @@ __global__ void k_cluster_assign(DevWork W) {
       t = W.ch_track[k];
       if (t >= 0) {
         const int pos = (int)(W.jump[c] >> 32);
-        W.track_cl[W.trk_off[t] + W.ch_off[k] + pos] = (int)c;
+        const int idx = W.trk_off[t] + W.ch_off[k] + pos;
+        W.track_cl[idx] = (int)c;
+        // the fit reads the coordinates in track order, without indirection
+        W.trk_xyz[idx] = make_int4(W.cl_x[c], W.cl_y[c], W.cl_z[c], (int)c);
       }
     }
     W.cl2trk[c] = t;
+  }
+}
+
+// Fit order: tracks sorted by length, longest first (a counting sort over
+// 256 length bins), so that a warp holds tracks of similar length and the
+// longest serial chains start first.  Order within a bin is arbitrary; each
+// track's fit does not depend on it.
+__global__ void k_fit_order(DevWork W) {
+  __shared__ unsigned long long pre[256];
+  __shared__ unsigned long long sm[34];
+  const unsigned long long ntrk = min(W.ctr[CTR_NTRK], (unsigned long long)W.cap_ch);
+  unsigned long long tot;
+  const unsigned long long v = threadIdx.x < 256 ? W.len_hist[threadIdx.x] : 0ull;
+  const unsigned long long ex = block_excl_scan(v, sm, &tot);
+  if (threadIdx.x < 256) pre[threadIdx.x] = ex;
+  __syncthreads();
+  for (unsigned long long t = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; t < ntrk;
+       t += (unsigned long long)gridDim.x * blockDim.x) {
+    const int bin = 255 - min(W.trk_ncl[t], 255);
+    const unsigned rank = atomicAdd(&W.len_hist[256 + bin], 1u);
+    W.fit_order[pre[bin] + rank] = (int)t;
   }
 }
 
@@ -180,7 +230,12 @@ cudaError_t launch_merge(const DevGeom& G, const DevParams& P, const DevWork& W,
                          unsigned long long* scan_state_b, int* launches) {
   const unsigned gc = grid_for_m(W.cap_ch, n_sm, 8);
   for (int p = 0; p < P.merge_passes; p++) {
-    k_merge_best<<<gc, 256, 0, st>>>(G, P, W, p);
+    if (p == 0) {
+      const int ngap = P.gap_max - P.gap_min + 1;
+      k_merge_cand<<<grid_for_m(W.cap_ch * ngap, n_sm, 8), 256, 0, st>>>(G, P, W);
+    } else {
+      k_merge_best<<<grid_for_m(W.cap_cand, n_sm, 8), 256, 0, st>>>(W, p);
+    }
     k_merge_link<<<gc, 256, 0, st>>>(W, p);
   }
   k_groups<<<gc, 256, 0, st>>>(P, W);
@@ -190,7 +245,8 @@ cudaError_t launch_merge(const DevGeom& G, const DevParams& P, const DevWork& W,
   k_group_assign<<<gc, 256, 0, st>>>(P, W);
   const unsigned g = grid_for_m(W.cap_cl, n_sm, 8);
   k_cluster_assign<<<g, 256, 0, st>>>(W);
-  *launches += 2 * P.merge_passes + 4;
+  k_fit_order<<<grid_for_m(W.cap_ch, n_sm, 4), 256, 0, st>>>(W);
+  *launches += 2 * P.merge_passes + 5;
   return cudaGetLastError();
 }
 

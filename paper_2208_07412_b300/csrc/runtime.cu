@@ -61,7 +61,8 @@ struct Slot {
   cudaEvent_t ev_done = nullptr, ev_input = nullptr;
   // device buffers
   Buf pages, offsets, winstate, cl, clx, cly, clz, clt, rowstart, up, down, score, edge, jump, chlen, scanv,
-      scanst, chainof, clchain, ch_i32, besta, bestb, trk_i32, trackcl, cl2trk, tracks, ctrl, scratch, wincnt, winsoff;
+      scanst, chainof, clchain, ch_i32, besta, bestb, trk_i32, trackcl, cl2trk, tracks, ctrl, scratch, wincnt, winsoff,
+      candab, candsc, lenhist;
   unsigned long long* h_ctrl = nullptr;   // pinned copy of [ctr | err]
   // capacities
   uint64_t cap_pages = 0, cap_windows = 0, cap_cl = 0, cap_ch = 0;
@@ -179,7 +180,7 @@ static cudaError_t ensure(Buf& b, size_t bytes) {
 static size_t slot_bytes(uint64_t pages, uint64_t windows, uint64_t cap_cl, uint64_t cap_ch, int nsr) {
   size_t b = pages + 16 + windows * 28 + cap_cl * (16 + 16 + 16 + 8 + 8 + 8 + 8 + 4 + 8 + 4 + 4 + 4 + 4) +
              (scan_tiles(cap_cl) + scan_tiles(cap_ch) + scan_tiles(windows)) * 8 +
-             cap_ch * (12 * 4 + 8 + 16 + sizeof(tpc_track)) +
+             cap_ch * (12 * 4 + 8 + 16 + sizeof(tpc_track) + 4 * 12) +
              (size_t)(nsr + 1) * 4 + 1024;
   return b;
 }
@@ -221,11 +222,14 @@ static tpc_status slot_reserve(tpc_context* ctx, Slot& s, uint64_t pages_bytes, 
     CUDA_TRY(ensure(s.bestb, cap_ch * 8));
     CUDA_TRY(ensure(s.besta, cap_ch * 16));
     CUDA_TRY(ensure(s.tracks, cap_ch * sizeof(tpc_track)));
+    CUDA_TRY(ensure(s.candab, cap_ch * 4 * 8));
+    CUDA_TRY(ensure(s.candsc, cap_ch * 4 * 4));
     s.cap_ch = cap_ch;
   }
   CUDA_TRY(ensure(s.scanst, (scan_tiles(s.cap_cl) + scan_tiles(s.cap_ch) + scan_tiles(s.cap_windows)) * 8));
   CUDA_TRY(ensure(s.rowstart, (size_t)(nsr + 1) * 4));
   CUDA_TRY(ensure(s.ctrl, 256));
+  CUDA_TRY(ensure(s.lenhist, 512 * 4));
   ctx->used = ctx->used - cur + slot_bytes(s.cap_pages, s.cap_windows, s.cap_cl, s.cap_ch, nsr);
   // wire the work-space pointers
   DevWork& W = s.W;
@@ -250,9 +254,15 @@ static tpc_status slot_reserve(tpc_context* ctx, Slot& s, uint64_t pages_bytes, 
   W.ch_root = ci; W.ch_len = ci + C; W.ch_b2 = ci + 2 * C; W.ch_top = ci + 3 * C; W.ch_top2 = ci + 4 * C;
   W.ch_next = ci + 5 * C; W.ch_prev = ci + 6 * C; W.ch_track = ci + 7 * C; W.ch_off = ci + 8 * C;
   W.grp_total = ci + 9 * C; W.trk_first = ci + 10 * C; W.trk_ncl = ci + 11 * C; W.trk_off = ci + 12 * C;
+  W.fit_order = W.ch_off;   // free once the clusters are assigned to tracks
+  W.len_hist = (uint32_t*)s.lenhist.p;
   W.best_b = (unsigned long long*)s.bestb.p;
   W.best_a = (unsigned long long*)s.besta.p;
+  W.cand_ab = (unsigned long long*)s.candab.p;
+  W.cand_sc = (uint32_t*)s.candsc.p;
+  W.cap_cand = s.cap_ch * 4;
   W.track_cl = (int32_t*)s.trackcl.p;
+  W.trk_xyz = (int4*)s.scratch.p;   // the finder's scratch is free once the clusters are compacted
   W.cl2trk = (int32_t*)s.cl2trk.p;
   W.tracks = (tpc_track*)s.tracks.p;
   W.ctr = (unsigned long long*)s.ctrl.p;
@@ -267,7 +277,7 @@ static void slot_free(tpc_context* ctx, Slot& s) {
   Buf* all[] = {&s.pages, &s.offsets, &s.winstate, &s.cl, &s.clx, &s.cly, &s.clz, &s.clt, &s.rowstart, &s.up,
                 &s.down, &s.score, &s.edge, &s.jump, &s.chlen, &s.scanv, &s.scanst, &s.chainof, &s.clchain,
                 &s.ch_i32, &s.besta, &s.bestb, &s.trk_i32, &s.trackcl, &s.cl2trk, &s.tracks, &s.ctrl,
-                &s.scratch, &s.wincnt, &s.winsoff};
+                &s.scratch, &s.wincnt, &s.winsoff, &s.candab, &s.candsc, &s.lenhist};
   for (Buf* b : all) free_buf(*b);
   for (auto& e : s.ev_stage) if (e) cudaEventDestroy(e);
   if (s.ev_done) cudaEventDestroy(s.ev_done);
@@ -358,6 +368,7 @@ static tpc_status enqueue(tpc_context* ctx, Slot& s) {
   const bool timing = ctx->flags & TPC_CTX_STAGE_TIMING;
   s.launches = 0;
   CUDA_TRY(cudaMemsetAsync(s.ctrl.p, 0, 256, st));
+  CUDA_TRY(cudaMemsetAsync(W.len_hist, 0, 512 * 4, st));
   const size_t tiles_a = scan_tiles(s.cap_cl), tiles_b = scan_tiles(s.cap_ch);
   CUDA_TRY(cudaMemsetAsync(W.scan_state, 0, (tiles_a + tiles_b + scan_tiles(s.n_windows)) * 8, st));
   if (timing) CUDA_TRY(cudaEventRecord(s.ev_stage[0], st));

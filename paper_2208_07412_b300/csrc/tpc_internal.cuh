@@ -87,11 +87,17 @@ struct DevWork {
   int32_t* ch_next; int32_t* ch_prev;
   unsigned long long* best_b;
   unsigned long long* best_a;    // [2 * cap_chains]
+  unsigned long long* cand_ab;   // merge candidate pairs (top chain << 32 | bottom chain)
+  uint32_t* cand_sc;             // their scores
+  uint64_t cap_cand;
   int32_t* ch_track; int32_t* ch_off;
   int32_t* grp_total;
   // tracks
   int32_t* trk_first; int32_t* trk_ncl; int32_t* trk_off;
+  uint32_t* len_hist;            // [512]: tracks per length bin (longest first), then ranks
+  int32_t* fit_order;            // tracks, longest first (reuses ch_off once assignment is done)
   int32_t* track_cl;
+  int4* trk_xyz;                 // (X, Y, Z, cluster) in track order, aligned with track_cl (reuses scratch_cl)
   int32_t* cl2trk;
   tpc_track* tracks;
   // counters (device scalars, one 64-byte block)
@@ -111,6 +117,7 @@ enum {
   CTR_NCLCL = 20,     // clusters assigned to tracks
   CTR_SCURSOR = 21,   // next free scratch record of the finder
   CTR_NWIN = 22,      // windows of the timeframe
+  CTR_NCAND = 23,     // merge candidate pairs found
   CTR_COUNT = 24
 };
 enum { TK_FIND = 0, TK_SCAN_A = 1, TK_SCAN_B = 2, TK_SCAN_W = 3, kNumTickets = 4 };
