@@ -243,9 +243,10 @@ def run_ours(args, world, rank, local):
     # ---- end to end through the C ABI with host (pinned) buffers
     pages_h = torch.from_numpy(tf.pages).pin_memory()
     offs_h = torch.from_numpy(tf.page_offsets.view(np.int64)).pin_memory()
-    cl_out = np.zeros(n_cl, tpc.CLUSTER_DTYPE)
-    tr_out = np.zeros(max(n_tr, 1), tpc.TRACK_DTYPE)
-    map_out = np.zeros(max(n_cl, 1), np.int32)
+    # results land in pinned host memory, like the inputs
+    cl_buf = torch.empty(max(n_cl, 1) * 16, dtype=torch.uint8).pin_memory()
+    tr_buf = torch.empty(max(n_tr, 1) * 112, dtype=torch.uint8).pin_memory()
+    map_buf = torch.empty(max(n_cl, 1), dtype=torch.int32).pin_memory()
     import ctypes
     L = tpc.load()
     n = ctypes.c_uint64()
@@ -253,8 +254,8 @@ def run_ours(args, world, rank, local):
     def e2e_step():
         t = R.submit(pages_h, offs_h, tf.n_time_bins)
         R.wait(t)
-        L.tpc_get_clusters(R.ctx, t, cl_out.ctypes.data, n_cl, ctypes.byref(n))
-        L.tpc_get_tracks(R.ctx, t, tr_out.ctypes.data, len(tr_out), ctypes.byref(n), map_out.ctypes.data)
+        L.tpc_get_clusters(R.ctx, t, cl_buf.data_ptr(), max(n_cl, 1), ctypes.byref(n))
+        L.tpc_get_tracks(R.ctx, t, tr_buf.data_ptr(), max(n_tr, 1), ctypes.byref(n), map_buf.data_ptr())
         tpc.tpc_release(R.ctx, t)
 
     for _ in range(max(1, args.warmup)):

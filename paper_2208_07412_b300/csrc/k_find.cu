@@ -139,57 +139,56 @@ __device__ __forceinline__ void put_run(const Seg& g, const FindSmem& S, int ps_
   }
 }
 
-// Block-wide decode of a segment into plane rows tt = t_in + tt_base.  All
-// reads are bounds-checked against the segment's counts and all writes
-// against the plane.  Returns true (block-uniform) if every check passed.
+// Block-wide decode of a segment into plane rows tt = t_in + tt_base, one
+// thread per time-bin entry (a page has at most 256): a block scan of the run
+// counts gives each entry its first run, a second of the digit counts its first
+// digit, and the thread then writes its own runs.  All reads are bounds-checked
+// against the segment's counts and all writes against the plane.  Returns true
+// (block-uniform) if every check passed.
 __device__ bool decode_seg(const Seg& g, int np, int ps_stride, int nw, int T, const FindSmem& S) {
   const int tid = threadIdx.x;
   const int ne = g.ne;
-  bool bad = ne < 0 || ne > kFrag;
-  int t_in = 0, nr = 0;
-  if (!bad && tid < ne) {
+  bool bad = ne < 0 || ne > kFrag || ne > (int)blockDim.x;
+  const bool mine = !bad && tid < ne;
+  int t_in = 0, nr = 0, tt = 0;
+  if (mine) {
     const uint32_t v = g.ent[tid];
     t_in = v & 0xff;
     nr = v >> 8;
-    const int tt = t_in + g.tt_base;
-    if (nr < 1 || tt < 0 || tt >= kWinT || g.t_base_abs + t_in >= T) bad = true;
+    tt = t_in + g.tt_base;
+    if (nr < 1 || tt < 0 || tt >= kWinT || g.t_base_abs + t_in >= T) { bad = true; nr = 0; }
     if (g.strict && tid > 0 && (int)(g.ent[tid - 1] & 0xff) >= t_in) bad = true;
   }
   unsigned long long tot;
-  const unsigned long long rs = block_excl_scan((unsigned long long)nr, S.scan, &tot);
-  if (tid < ne) { S.ent_t[tid] = (uint8_t)t_in; S.ent_rs[tid] = (int32_t)rs; }
+  const int r0 = (int)block_excl_scan((unsigned long long)nr, S.scan, &tot);
   const int nrun = (int)tot;
-  if (nrun > g.nrun) bad = true;
-  __syncthreads();
-  unsigned long long dcarry = 0;
-  for (int base = 0; base < nrun; base += blockDim.x) {
-    const int j = base + tid;
-    int ps = 0, len = 0, tt = 0;
-    bool mine = j < nrun && j < g.nrun;
-    if (mine) {
-      const uint32_t v = g.run[j];
-      ps = v & 0xff;
-      len = v >> 8;
-      int lo = 0, hi = ne - 1;
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (S.ent_rs[mid] <= j) lo = mid; else hi = mid - 1;
-      }
-      tt = (int)S.ent_t[lo] + g.tt_base;
-      if (len < 1 || ps + len > np || tt < 0 || tt >= kWinT) { bad = true; mine = false; len = 0; }
-      if (g.strict && j > S.ent_rs[lo]) {
-        const uint32_t pv = g.run[j - 1];
-        if ((int)ps < (int)(pv & 0xff) + (int)(pv >> 8)) bad = true;
-      }
+  if (nrun > g.nrun || (g.strict && nrun != g.nrun)) bad = true;
+  // digits of this entry's runs, with the run checks
+  int nd = 0;
+  if (mine && r0 + nr <= g.nrun) {
+    int last_end = -1;
+    for (int k = 0; k < nr; k++) {
+      const uint32_t rv = g.run[r0 + k];
+      const int ps = rv & 0xff, len = rv >> 8;
+      if (len < 1 || ps + len > np) { bad = true; nd = 0; break; }
+      if (g.strict && ps < last_end) bad = true;
+      last_end = ps + len;
+      nd += len;
     }
-    unsigned long long ctot;
-    const unsigned long long doff = block_excl_scan((unsigned long long)len, S.scan, &ctot);
-    const long long di = (long long)dcarry + (long long)doff;
-    if (mine && di + len > g.ndig) { bad = true; mine = false; }
-    if (mine) put_run(g, S, ps_stride, nw, tt, ps, len, (int)di);
-    dcarry += ctot;
+  } else if (mine) {
+    bad = true;
   }
-  if (g.strict && (nrun != g.nrun || (long long)dcarry != g.ndig)) bad = true;
+  const long long d0 = (long long)block_excl_scan((unsigned long long)nd, S.scan, &tot);
+  if ((long long)tot > g.ndig || (g.strict && (long long)tot != g.ndig)) bad = true;
+  if (mine && nd > 0 && d0 + nd <= g.ndig) {
+    int di = (int)d0;
+    for (int k = 0; k < nr; k++) {
+      const uint32_t rv = g.run[r0 + k];
+      const int ps = rv & 0xff, len = rv >> 8;
+      put_run(g, S, ps_stride, nw, tt, ps, len, di);
+      di += len;
+    }
+  }
   return !__syncthreads_or(bad);
 }
 
