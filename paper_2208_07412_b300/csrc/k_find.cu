@@ -28,7 +28,7 @@
 
 namespace tpc {
 
-constexpr int kFindThreads = 256;
+constexpr int kFindThreads = 384;
 
 struct PageHdr {
   uint32_t len;
@@ -121,12 +121,19 @@ struct Seg {
 
 __device__ __forceinline__ void put_run(const Seg& g, const FindSmem& S, int ps_stride, int nw, int tt, int ps,
                                         int len, int di) {
-  uint16_t* prow = S.plane + tt * ps_stride + kPad;
+  uint16_t* prow = S.plane + tt * ps_stride + kPad + ps;
+  const int d0 = g.dfirst + di;
+  int wd = d0 / 3, sh = 10 * (d0 - 3 * (d0 / 3));
+  uint32_t word = g.adc[wd];
+  const int li0 = g.lbase + di;
+  const uint16_t L0 = (uint16_t)(tt * ps_stride + kPad + ps);
+  const bool list_all = li0 + len <= kList;
   for (int k = 0; k < len; k++) {
-    const int d = g.dfirst + di + k;
-    prow[ps + k] = (uint16_t)((g.adc[d / 3] >> (10 * (d % 3))) & 1023u);
-    const int li = g.lbase + di + k;
-    if (li < kList) S.list[li] = (uint16_t)(tt * ps_stride + kPad + ps + k);
+    prow[k] = (uint16_t)((word >> sh) & 1023u);
+    if (list_all) S.list[li0 + k] = (uint16_t)(L0 + k);
+    else if (li0 + k < kList) S.list[li0 + k] = (uint16_t)(L0 + k);
+    sh += 10;
+    if (sh == 30 && k + 1 < len) { sh = 0; word = g.adc[++wd]; }
   }
   int p = ps;
   const int pe = ps + len;
@@ -241,11 +248,11 @@ __device__ __forceinline__ void copy_u16(uint16_t* dst, const uint8_t* pg, uint3
 // with a higher index lower or equal; padding pads and empty pixels read 0.
 __device__ __forceinline__ bool peak_at(const uint16_t* pl, int L, int ps_stride, int qmin) {
   const int q = pl[L];
-  if (q < qmin) return false;
   const uint16_t* u = pl + L - ps_stride;
   const uint16_t* d = pl + L + ps_stride;
-  return q > u[-1] && q > u[0] && q > u[1] && q > pl[L - 1] && q >= pl[L + 1] && q >= d[-1] && q >= d[0] &&
-         q >= d[1];
+  const int lo = max(max((int)u[-1], (int)u[0]), max((int)u[1], (int)pl[L - 1]));
+  const int hi = max(max((int)pl[L + 1], (int)d[-1]), max((int)d[0], (int)d[1]));
+  return (q >= qmin) & (q > lo) & (q >= hi);
 }
 
 // Index of the last prefix entry <= r in pre[0..n] (pre ascending, pre[0] = 0).
@@ -377,18 +384,39 @@ k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
   for (int i = tid; i < nplane / 2; i += blockDim.x) reinterpret_cast<uint32_t*>(S.plane)[i] = 0u;
   if (tid == 0 && (nplane & 1)) S.plane[nplane - 1] = 0;
 
+  // With scratch output no window waits for another, so the next window is
+  // taken early: its ticket at the top of the current one, its page offsets
+  // after the decode, and its three-page byte range is prefetched into L2
+  // after the peak test.  In look-back mode a held window would stall every
+  // successor's look-back: there the ticket is taken only at the top.
+  if (kScratch && tid == 0) {
+    const unsigned w0 = atomicAdd(&W.tickets[TK_FIND], 1u);
+    S.misc[1] = (int)w0;
+    for (int k = 0; k < 4; k++) {
+      const long long j = (long long)w0 - 1 + k;
+      S.offs[k] = (j >= 0 && j < (long long)n_windows && w0 < n_windows) ? W.page_offsets[j] : ~0ull;
+    }
+  }
+  unsigned int nt = 0;                  // next window (thread 0, scratch mode)
+  unsigned long long noffs[4] = {~0ull, ~0ull, ~0ull, ~0ull};
   while (true) {
-    // ---- 0. window w.  The ticket is taken only now: a CTA that held a later
-    // window while still busy would stall every successor's look-back.
-    if (tid == 0) S.misc[1] = (int)atomicAdd(&W.tickets[TK_FIND], 1u);
+    // ---- 0. window w
+    if (!kScratch && tid == 0) S.misc[1] = (int)atomicAdd(&W.tickets[TK_FIND], 1u);
     __syncthreads();
     const unsigned int w = (unsigned int)S.misc[1];
     if (w >= n_windows) break;
-    if (tid < 4) {
+    if (kScratch && tid == 0) nt = atomicAdd(&W.tickets[TK_FIND], 1u);
+    if (!kScratch && tid < 4) {
       const long long j = (long long)w - 1 + tid;
       S.offs[tid] = (j >= 0 && j < (long long)n_windows) ? W.page_offsets[j] : ~0ull;
     }
-    for (int i = tid; i < kWinT * nw; i += blockDim.x) { S.occ[i] = 0u; S.pk[i] = 0u; }
+    {
+      // occ and pk are adjacent: clear both as 16-byte words (the tail word by word)
+      const int nwords = 2 * kWinT * nw;
+      uint4* o4 = reinterpret_cast<uint4*>(S.occ);
+      for (int i = tid; i < nwords / 4; i += blockDim.x) o4[i] = make_uint4(0u, 0u, 0u, 0u);
+      for (int i = (nwords & ~3) + tid; i < nwords; i += blockDim.x) S.occ[i] = 0u;
+    }
     __syncthreads();
     const int f = (int)(w % G.n_frag);
     const int sr = (int)(w / G.n_frag);
@@ -475,6 +503,13 @@ k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
     if (!ok && tid == 0) atomicOr(W.err, kErrCorrupt);
     __syncthreads();
 
+    if (kScratch && tid == 0 && nt < n_windows) {
+      for (int k = 0; k < 4; k++) {
+        const long long j = (long long)nt - 1 + k;
+        noffs[k] = (j >= 0 && j < (long long)n_windows) ? W.page_offsets[j] : ~0ull;
+      }
+    }
+
     // ---- 4. peak test, one digit per thread (rows 1..260; rows 0 and 261 only
     // serve as neighbours)
     if (ok) {
@@ -504,6 +539,21 @@ k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
       }
     }
     __syncthreads();
+
+    if (kScratch && tid == 0 && nt < n_windows) {
+      // next window: its page and both neighbours are contiguous in the usual
+      // layout; prefetch that byte range (at most 64 KB) into L2
+      const unsigned long long lo = noffs[0] != ~0ull ? noffs[0] : noffs[1];
+      unsigned long long hi = noffs[3] != ~0ull ? noffs[3] : W.pages_bytes;
+      if (lo < hi && lo < W.pages_bytes && (lo & 15) == 0) {
+        hi = min(hi, (unsigned long long)W.pages_bytes);
+        const unsigned long long n = min(hi - lo, 65536ull) & ~15ull;
+        if (n) {
+          const size_t ga = __cvta_generic_to_global(W.pages + lo);
+          asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(ga), "r"((unsigned)n) : "memory");
+        }
+      }
+    }
 
     // ---- 5. rank the own peaks (rows 3..258) in canonical order, list the
     // first kStage, publish the window's count
@@ -590,6 +640,11 @@ k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
       reinterpret_cast<uint4*>(dst)[idx] = rec;
     }
     __syncthreads();
+
+    if (kScratch && tid == 0) {
+      S.misc[1] = (int)nt;
+      for (int k = 0; k < 4; k++) S.offs[k] = noffs[k];
+    }
 
     // ---- 9. leave the plane empty for the next window
     if (listed) {
