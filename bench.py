@@ -40,8 +40,12 @@ WORKLOADS = {
                  "(5% loopers) from one vertex, Bz 0.5 T, Landau(60) Gaussian clouds, noise 1 ADC, ZS >= 3"),
     "single_sector": (lambda seed: tpcgen.single_sector(seed),
                       "single_sector: 1 sector x 152 rows, 500 time bins, 150 tracks"),
+    "continuous_50khz": (lambda seed: tpcgen.continuous_tf(seed),
+                         "continuous_50khz: 36 sectors x 152 rows, 55,000 time bins (11 ms at 5 MHz), "
+                         "Poisson(550) Pb-Pb-like collisions at uniform start times, multiplicity "
+                         "floor(15000 U^7.82) (mean ~1,700), 5% loopers, same charge/noise/ZS model"),
 }
-REF_SAMPLE_SECTORS = 9
+REF_SAMPLE_BYTES = 20 << 20
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -69,10 +73,15 @@ class ClockSampler:
                 ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,"
                  "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
                  "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-                 "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "100"],
+                 "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=self.f, stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
+            return self
+        # the timed region starts once the sampler is producing samples
+        t0 = time.time()
+        while time.time() - t0 < 5.0 and os.path.getsize(self.path) == 0:
+            time.sleep(0.02)
         return self
 
     def __exit__(self, *a):
@@ -141,21 +150,16 @@ def sum_over_ranks(world, v: float) -> float:
     return float(t.item())
 
 
-def sample_tf(tf, n_sectors):
-    """The first n_sectors sectors of a timeframe (their pages are a prefix)."""
-    import copy
-    s = copy.copy(tf)
-    nwin = n_sectors * tf.n_rows * tf.n_fragments
-    s.page_offsets = tf.page_offsets[:nwin].copy()
-    end = int(tf.page_offsets[nwin]) if nwin < len(tf.page_offsets) else len(tf.pages)
-    s.pages = tf.pages[:end]
-    s.n_sectors = n_sectors
-    return s
+def ref_sample_sectors(tf, sample_bytes: float = REF_SAMPLE_BYTES) -> int:
+    """Sectors in the oracle's sample: about sample_bytes of ZS pages (20 MB: a
+    few seconds of single-core CPU work), at least one sector."""
+    per_sector = tf.pages.nbytes / max(tf.n_sectors, 1)
+    return int(max(1, min(tf.n_sectors, sample_bytes // max(per_sector, 1))))
 
 
-def cpu_baseline(tf, steps=1):
+def cpu_baseline(tf, steps=1, sample_bytes: float = REF_SAMPLE_BYTES):
     import oracle
-    sub = sample_tf(tf, min(REF_SAMPLE_SECTORS, tf.n_sectors))
+    sub = tpcgen.sector_prefix(tf, ref_sample_sectors(tf, sample_bytes))
     times, ncl, ntr = [], 0, 0
     for _ in range(steps):
         t0 = time.perf_counter()
@@ -170,11 +174,18 @@ def cpu_baseline(tf, steps=1):
 def run_reference(args, world, rank):
     if rank != 0:
         return
-    make, desc = WORKLOADS[args.workload]
+    if args.workload == "serve":   # one Pb-Pb-like timeframe of the serving pool
+        make, desc = (lambda seed: tpcgen.continuous_tf(7, n_time_bins=args.serve_bins),
+                      f"serve pool: Pb-Pb-like continuous timeframe of {args.serve_bins} time bins")
+    else:
+        make, desc = WORKLOADS[args.workload]
     tf = tpcgen.generate(make(args.seed))
+    # each step a bounded sample, smaller when many steps are asked for, so the
+    # whole run stays around a minute of CPU time
+    per_step = REF_SAMPLE_BYTES * min(1.0, 20.0 / max(args.steps + args.warmup, 1))
     for _ in range(args.warmup):
-        cpu_baseline(tf, 1)
-    cb = cpu_baseline(tf, args.steps)
+        cpu_baseline(tf, 1, per_step)
+    cb = cpu_baseline(tf, args.steps, per_step)
     t = sum(cb["times"])
     v = cb["clusters"] * args.steps / t
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "clusters/s", "n_gpus": args.gpus,
@@ -184,6 +195,182 @@ def run_reference(args, world, rank):
             "tracks_per_s": cb["tracks"] * args.steps / t,
             "cpu_baseline": {"value": v, "unit": "clusters/s", "cores": 1, "kind": "oracle", "sample": cb["sample"]},
             "e2e": {"value": v, "unit": "clusters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def pct(v, q):
+    return float(np.percentile(np.asarray(v, dtype=np.float64), q)) if len(v) else None
+
+
+def batched_vs_plain(tpc, torch, local, n_events=64, seed=1000, reps=3):
+    """Uneven events on the full geometry (multiplicity log-uniform in
+    [200, 20000], 1000 time bins each), device-resident: the whole set as ONE
+    batched pipeline run, against one plain run per event (one slot, events in
+    sequence) and against the served path (4 slots, every event submitted at
+    once, admitted as slots free up).  Host wall time from the first submit to
+    the last result resident on the device."""
+    mult = tpcgen.batch_multiplicities(seed, n_events=n_events)
+    tfs = [tpcgen.generate(tpcgen.full_tpc(seed + i, n_tracks=int(m), want_labels=False))
+           for i, m in enumerate(mult)]
+    dev = [(torch.from_numpy(tf.pages).cuda(), torch.from_numpy(tf.page_offsets.view(np.int64)).cuda())
+           for tf in tfs]
+    torch.cuda.synchronize()   # the uploads ran on torch's stream, the library uses its own
+    T = tfs[0].n_time_bins
+    tot = sum(tf.pages.nbytes for tf in tfs)
+    free_b, _ = torch.cuda.mem_get_info()
+    budget = int(min(free_b * 0.8, 16 * tot + (8 << 30)))
+
+    def timed(fn):
+        fn()                                   # warm-up (captures the graphs)
+        torch.cuda.synchronize()
+        best = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            out = fn()
+            best.append(time.perf_counter() - t0)
+        return statistics.median(best), out
+
+    # one batched run
+    with tpc.Reconstructor.for_timeframe(tfs[0], device=local, mem_budget=budget) as R:
+        def batch():
+            t, keep = tpc.tpc_submit_batch(R.ctx, dev, T)
+            R.wait(t)
+            c = tpc.tpc_get_counters(R.ctx, t)
+            tpc.tpc_release(R.ctx, t)
+            return c
+        batch_s, ctr = timed(batch)
+    n_cl, n_tr = ctr["clusters"], ctr["tracks"]
+
+    # plain: one event after the other on one slot
+    with tpc.Reconstructor.for_timeframe(tfs[0], device=local, mem_budget=budget) as R:
+        def plain():
+            lat, ncl = [], 0
+            for p, o in dev:
+                a = time.perf_counter()
+                t = R.submit(p, o, T)
+                R.wait(t)
+                ncl += tpc.tpc_get_counters(R.ctx, t)["clusters"]
+                tpc.tpc_release(R.ctx, t)
+                lat.append(time.perf_counter() - a)
+            return lat, ncl
+        plain_s, (lat, ncl_plain) = timed(plain)
+
+    # served: all submitted at once to 4 slots; each release admits the next
+    with tpc.Reconstructor.for_timeframe(tfs[0], device=local, mem_budget=budget, n_slots=4) as R:
+        def served():
+            t0 = time.perf_counter()
+            tickets = [R.submit(p, o, T) for p, o in dev]
+            done, ncl = [], 0
+            pending = list(tickets)
+            while pending:
+                for t in list(pending):
+                    if tpc.tpc_poll(R.ctx, t, 0) == tpc.TPC_STATE_DONE:
+                        ncl += tpc.tpc_get_counters(R.ctx, t)["clusters"]
+                        tpc.tpc_release(R.ctx, t)
+                        pending.remove(t)
+                        done.append(time.perf_counter() - t0)
+                time.sleep(20e-6)
+            return done, ncl
+        served_s, (done, ncl_served) = timed(served)
+    assert ncl_plain == n_cl == ncl_served, (ncl_plain, n_cl, ncl_served)
+    return {
+        "workload": f"{n_events} events, full 36-sector geometry, 1000 time bins, multiplicity log-uniform "
+                    f"[200, 20000] (seed {seed}: {int(mult.sum())} tracks, {tot / 1e9:.2f} GB ZS, "
+                    f"{n_cl} clusters, {n_tr} tracks), device-resident inputs",
+        "clusters_per_s": {"batched": n_cl / batch_s, "plain": n_cl / plain_s, "served_4_slots": n_cl / served_s},
+        "tracks_per_s": {"batched": n_tr / batch_s, "plain": n_tr / plain_s, "served_4_slots": n_tr / served_s},
+        "speedup_vs_plain": {"batched": plain_s / batch_s, "served_4_slots": plain_s / served_s},
+        "latency_ms": {"plain_event_p50": 1e3 * pct(lat, 50), "plain_event_p99": 1e3 * pct(lat, 99),
+                       "batched_whole_batch": 1e3 * batch_s,
+                       "served_completion_p50": 1e3 * pct(done, 50), "served_completion_p99": 1e3 * pct(done, 99)},
+        "timing": f"host wall clock, median of {reps} passes after one warm-up pass",
+    }
+
+
+def serve_pass(tpc, R, pool, arrivals):
+    """Feed requests (pool index per arrival time, seconds from the start) to a
+    context: each is submitted when due; finished ones are released, which
+    admits queued ones.  Returns per-request latency (s) and the makespan."""
+    t0 = time.perf_counter()
+    nxt, inflight, lat, ncl = 0, {}, [], 0
+    while nxt < len(arrivals) or inflight:
+        now = time.perf_counter() - t0
+        while nxt < len(arrivals) and arrivals[nxt][0] <= now:
+            tf, pages, offs = pool[arrivals[nxt][1]]
+            inflight[R.submit(pages, offs, tf.n_time_bins)] = arrivals[nxt][0]
+            nxt += 1
+        for t in list(inflight):
+            if tpc.tpc_poll(R.ctx, t, 0) == tpc.TPC_STATE_DONE:
+                ncl += tpc.tpc_get_counters(R.ctx, t)["clusters"]
+                tpc.tpc_release(R.ctx, t)
+                lat.append(time.perf_counter() - t0 - inflight.pop(t))
+        time.sleep(20e-6)
+    return lat, time.perf_counter() - t0, ncl
+
+
+def run_serve(args, world, rank, local):
+    """Served vs plain sequential path under Poisson arrivals of timeframes
+    mixing pp-like and Pb-Pb-like occupancy, inputs in pinned host memory
+    (each request is copied in when it is admitted)."""
+    import torch
+    from paper_2208_07412_b300 import tpc
+    torch.cuda.set_device(local)
+    bins = args.serve_bins
+    cfgs = [tpcgen.pp_tf(7 + i, n_time_bins=bins) for i in range(8)] + \
+           [tpcgen.continuous_tf(7 + i, n_time_bins=bins) for i in range(8)]
+    pool = []
+    for c in cfgs:
+        tf = tpcgen.generate(c)
+        pool.append((tf, torch.from_numpy(tf.pages).pin_memory(),
+                     torch.from_numpy(tf.page_offsets.view(np.int64)).pin_memory()))
+    n_req = 3 * len(pool)
+    rng = np.random.default_rng(7)
+    order = rng.integers(0, len(pool), size=n_req)
+    free_b, _ = torch.cuda.mem_get_info()
+    biggest = max(tf.pages.nbytes for tf, _, _ in pool)
+    budget = int(min(free_b * 0.8, 4 * 16 * biggest + (8 << 30)))
+    points = []
+    with tpc.Reconstructor.for_timeframe(pool[0][0], device=local, mem_budget=budget, n_slots=1) as Rp, \
+            tpc.Reconstructor.for_timeframe(pool[0][0], device=local, mem_budget=budget, n_slots=4) as Rs:
+        burst = [(0.0, int(i)) for i in order]
+        serve_pass(tpc, Rp, pool, burst[:len(pool)])        # warm-up: grow slots, capture graphs
+        serve_pass(tpc, Rs, pool, burst[:len(pool)])
+        lat, span, ncl = serve_pass(tpc, Rp, pool, burst)
+        rate_plain = n_req / span                            # saturation throughput, plain
+        for f in args.serve_load:
+            lam = f * rate_plain
+            gaps = rng.exponential(1.0 / lam, size=n_req)
+            arr = [(float(a), int(i)) for a, i in zip(np.cumsum(gaps) - gaps[0], order)]
+            row = {"offered_tf_per_s": lam, "load_vs_plain_saturation": f}
+            for name, R in (("plain", Rp), ("served", Rs)):
+                lat, span, ncl = serve_pass(tpc, R, pool, arr)
+                row[name] = {"tf_per_s": n_req / span, "clusters_per_s": ncl / span,
+                             "latency_ms_p50": 1e3 * pct(lat, 50), "latency_ms_p99": 1e3 * pct(lat, 99)}
+            points.append(row)
+        lat_p, span_p, ncl_p = serve_pass(tpc, Rp, pool, burst)
+        lat_s, span_s, ncl_s = serve_pass(tpc, Rs, pool, burst)
+    sizes = sorted(tf.pages.nbytes for tf, _, _ in pool)
+    line = {
+        "metric": METRIC, "value": ncl_s / span_s, "unit": "clusters/s", "n_gpus": 1, "steps": n_req,
+        "warmup": len(pool), "ms_per_step": 1e3 * span_s / n_req, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "i64+f32", "data": "synthetic",
+        "config": {"workload": f"serve: pool of 8 pp-like (1 MHz, Poisson(30) tracks) + 8 Pb-Pb-like (50 kHz, "
+                               f"floor(15000 U^7.82)) continuous timeframes of {bins} time bins, "
+                               f"{sizes[0] / 1e9:.2f}-{sizes[-1] / 1e9:.2f} GB ZS each, {n_req} requests drawn "
+                               f"from the pool, pinned host inputs",
+                   "served": "4 slots, queued requests admitted as slots and memory free up",
+                   "plain": "1 slot, one timeframe at a time in arrival order"},
+        "saturation": {"served_tf_per_s": n_req / span_s, "plain_tf_per_s": n_req / span_p,
+                       "served_clusters_per_s": ncl_s / span_s, "plain_clusters_per_s": ncl_p / span_p,
+                       "speedup": span_p / span_s,
+                       "served_latency_ms_p50": 1e3 * pct(lat_s, 50), "served_latency_ms_p99": 1e3 * pct(lat_s, 99),
+                       "plain_latency_ms_p50": 1e3 * pct(lat_p, 50), "plain_latency_ms_p99": 1e3 * pct(lat_p, 99)},
+        "poisson_sweep": points,
+        "e2e": {"value": ncl_s / span_s, "unit": "clusters/s",
+                "h2d_bytes_per_step": int(np.mean([pool[i][0].pages.nbytes + pool[i][0].page_offsets.nbytes
+                                                   for i in order])),
+                "d2h_bytes_per_step": 256},
+    }
     print(json.dumps(line), flush=True)
 
 
@@ -198,8 +385,13 @@ def run_ours(args, world, rank, local):
     # the library would replace by a stream of its own)
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
+    flags = tpc.TPC_CTX_STAGE_TIMING | (tpc.TPC_CTX_NO_GRAPHS if args.no_graphs else 0)
+    # device memory for one slot: the pages, ~150 B per cluster of capacity
+    # (pages/12 clusters) and the rest; the budget is what the GPU has free
+    free_b, _ = torch.cuda.mem_get_info()
+    budget = int(min(free_b * 0.85, max(16 << 30, 40 * tf.pages.nbytes)))
     R = tpc.Reconstructor.for_timeframe(tf, device=local, stream=stream.cuda_stream,
-                                        flags=tpc.TPC_CTX_STAGE_TIMING, mem_budget=16 << 30)
+                                        flags=flags, mem_budget=budget)
     pages_d = torch.from_numpy(tf.pages).to("cuda")
     offs_d = torch.from_numpy(tf.page_offsets.view(np.int64)).to("cuda")
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
@@ -285,7 +477,8 @@ def run_ours(args, world, rank, local):
             "config": {"workload": desc, "seed": args.seed, "zs_bytes": int(tf.pages.nbytes),
                        "digits": int(tf.n_digits), "clusters_per_tf": n_cl, "tracks_per_tf": n_tr,
                        "l2": "flushed before every step (256 MB write)", "parallelism": f"replicas x{world}",
-                       "path": "plain per-timeframe launches"},
+                       "path": ("plain per-timeframe kernel launches" if args.no_graphs
+                                else "per-timeframe pipeline replayed from a captured CUDA graph")},
             "tracks_per_s": tr_all / dev_s_max,
             "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
             "stages_ms": stages,
@@ -299,6 +492,8 @@ def run_ours(args, world, rank, local):
             "clocks": clk.summary(),
             "gpu_launches": int(launches),
         }
+        if world == 1 and not args.no_batched and args.workload == "full_tpc":
+            line["batched"] = batched_vs_plain(tpc, torch, local)
         if world == 1 and not args.no_cpu_baseline:
             cb = cpu_baseline(tf, 1)
             line["cpu_baseline"] = {"value": cb["clusters"] / cb["times"][0], "unit": "clusters/s", "cores": 1,
@@ -310,17 +505,25 @@ def run_ours(args, world, rank, local):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="full_tpc")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["serve"], default="full_tpc")
+    ap.add_argument("--serve-bins", type=int, default=5500, help="time bins per served timeframe (1.1 ms)")
+    ap.add_argument("--serve-load", type=float, nargs="*", default=[0.5, 0.8, 1.0, 1.3],
+                    help="offered load as fractions of the plain path's saturation rate")
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-graphs", action="store_true", help="enqueue every kernel instead of graph replay")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain comparison")
     args = ap.parse_args()
     world, rank, local = dist_setup(args.gpus)
     try:
         if args.impl == "reference":
             run_reference(args, world, rank)
+        elif args.workload == "serve":
+            if rank == 0:
+                run_serve(args, world, rank, local)
         else:
             run_ours(args, world, rank, local)
     finally:

@@ -83,6 +83,7 @@ typedef int32_t tpc_status;
 #define TPC_MAX_PADS      255
 #define TPC_MAX_ROWS      255
 #define TPC_MAX_SECTORS   255
+#define TPC_MAX_BATCH     4096   /* events in one tpc_submit_batch */
 
 /* Ticket states reported by tpc_poll (monotone). */
 #define TPC_STATE_QUEUED          0   /* admitted, waiting for a slot */
@@ -97,6 +98,7 @@ typedef int32_t tpc_status;
 
 /* Context flags. */
 #define TPC_CTX_STAGE_TIMING 1u   /* record CUDA events around each stage (tpc_get_stage_times) */
+#define TPC_CTX_NO_GRAPHS    2u   /* enqueue every kernel instead of replaying the slot's captured CUDA graph */
 
 /* Pipeline stages, in launch order (indices into tpc_get_stage_times). */
 #define TPC_STAGE_FIND       0    /* ZS decode + peak finder + cluster moments + compaction */
@@ -261,12 +263,48 @@ void       tpc_destroy_context(tpc_context* ctx);
  *              with the covariance reset at each pass start; update C' = C - K H C
  *              then symmetrised; an update whose result fails the PD check is
  *              redone in FP64.
- * Ownership: tf->pages and tf->page_offsets are borrowed (see the descriptor).
- * Results stay on the device until tpc_release.  *ticket identifies them.
- * Errors: TPC_E_INVAL (descriptor), TPC_E_NOMEM (over budget), TPC_E_BUSY
- * (TPC_TF_NOWAIT and no slot), TPC_E_CUDA.  Page corruption and capacity
- * overflow are reported by tpc_poll (TPC_E_CORRUPT, TPC_E_OVERFLOW). */
+ * Admission: a timeframe starts at once on a free slot when the memory budget
+ * allows (the device buffers of idle slots are given back first if it is
+ * short).  Otherwise, and whenever earlier requests are still queued, it is
+ * queued (state TPC_STATE_QUEUED) and started in arrival order by the
+ * tpc_release that frees a slot and enough memory, so requests that arrive
+ * while others run are admitted as slots and memory free up and overlap with
+ * them on the device (each slot has its own stream).  A queued request that
+ * cannot fit even with every other slot idle fails with TPC_E_NOMEM (reported
+ * by tpc_poll).
+ * Ownership: tf->pages and tf->page_offsets are borrowed (see the descriptor),
+ * for a queued request until it has started and reached
+ * TPC_STATE_INPUT_RELEASED.  Results stay on the device until tpc_release.
+ * *ticket identifies them.
+ * Errors: TPC_E_INVAL (descriptor), TPC_E_NOMEM (over budget with nothing else
+ * running), TPC_E_BUSY (TPC_TF_NOWAIT and no slot or memory), TPC_E_CUDA.
+ * Page corruption and capacity overflow are reported by tpc_poll
+ * (TPC_E_CORRUPT, TPC_E_OVERFLOW). */
 tpc_status tpc_submit_timeframe(tpc_context* ctx, const tpc_timeframe_desc* tf, uint64_t* ticket);
+
+/* Submit a batch of n_events independent events (timeframes of the same
+ * geometry and the same n_time_bins, e.g. triggered collisions of uneven
+ * multiplicity) as ONE pipeline run: every stage is one set of launches over
+ * all events' windows, chains and tracks, so small events share the GPU
+ * instead of each leaving it mostly idle.  The paper processes each timeframe
+ * on its own; batching is this library's way to fill the GPU with small ones
+ * ("Real-time reconstruction": the EPNs reconstruct complete collisions).
+ * Internally the sector axis becomes (event, sector); every step of the
+ * method stays inside a sector, so each event's results equal those of a
+ * tpc_submit_timeframe of that event alone, bit for bit.
+ *   tfs       n_events descriptors (host or device pointers, told apart by
+ *             address; TPC_TF_DEVICE_INPUT is not needed); borrowed until
+ *             tpc_poll reports TPC_STATE_INPUT_RELEASED
+ *   n_events  1..TPC_MAX_BATCH
+ * The events' pages are gathered into the slot's own buffer (one copy per
+ * event) and their page tables rebased onto it; a page offset outside its
+ * event's own pages is treated as corrupt.  Results: tpc_get_batch_info and
+ * the tpc_get_event_* calls; the plain getters return the concatenation
+ * (events in order, indices global to the batch).
+ * Errors: as tpc_submit_timeframe; TPC_E_INVAL if the events' n_time_bins
+ * differ. */
+tpc_status tpc_submit_batch(tpc_context* ctx, const tpc_timeframe_desc* tfs, uint32_t n_events,
+                            uint64_t* ticket);
 
 /* Wait up to timeout_us (0: do not wait; UINT32_MAX: forever) for the ticket
  * and report its state in *state.  Returns TPC_OK while running or done,
@@ -286,6 +324,24 @@ tpc_status tpc_get_clusters(tpc_context* ctx, uint64_t ticket, tpc_cluster* out,
  * out == NULL: only *n is set.  Errors as tpc_get_clusters. */
 tpc_status tpc_get_tracks(tpc_context* ctx, uint64_t ticket, tpc_track* out, uint64_t cap,
                           uint64_t* n, int32_t* cluster_to_track);
+
+/* Layout of a finished ticket's results by event: *n_events (1 for a plain
+ * timeframe) and, if not NULL, cluster_start[n_events + 1] and
+ * track_start[n_events + 1], each event's first cluster / track in the
+ * concatenated results (last entry: the totals). */
+tpc_status tpc_get_batch_info(tpc_context* ctx, uint64_t ticket, uint32_t* n_events, uint64_t* cluster_start,
+                              uint64_t* track_start);
+
+/* One event's clusters of a finished ticket, as tpc_get_clusters gives them for
+ * that event submitted alone.  TPC_E_INVAL if event >= n_events. */
+tpc_status tpc_get_event_clusters(tpc_context* ctx, uint64_t ticket, uint32_t event, tpc_cluster* out,
+                                  uint64_t cap, uint64_t* n);
+
+/* One event's tracks and cluster-to-track map, indices relative to the event
+ * (first_cluster, map values), as tpc_get_tracks gives them for that event
+ * submitted alone. */
+tpc_status tpc_get_event_tracks(tpc_context* ctx, uint64_t ticket, uint32_t event, tpc_track* out,
+                                uint64_t cap, uint64_t* n, int32_t* cluster_to_track);
 
 /* Copy the CA results of a finished ticket (n_clusters entries each; any
  * pointer may be NULL): up[], down[] (step 5, cluster indices or -1) and
@@ -307,11 +363,12 @@ tpc_status tpc_get_stage_times(tpc_context* ctx, uint64_t ticket, float* ms);
 /* Counters of a finished ticket: out[0] clusters, [1] kept chains, [2] tracks,
  * [3] clusters on tracks, [4] FP64 covariance redos, [5] merge passes that
  * merged, [6] device error word, [7] ZS bytes of the timeframe, [8] kernel
- * launches of the last run, [9] runs (1, or 2 after a capacity regrowth).
+ * launches of the last run, [9] runs (1; 2 or 3 after capacity regrowths).
  * n: entries requested (<= 10). */
 tpc_status tpc_get_counters(tpc_context* ctx, uint64_t ticket, uint64_t* out, int n);
 
-/* Free the ticket's slot and results.  Unknown ticket: TPC_E_NOTFOUND. */
+/* Free the ticket's slot and results, then start the oldest queued requests
+ * that now fit.  A queued ticket is cancelled.  Unknown ticket: TPC_E_NOTFOUND. */
 tpc_status tpc_release(tpc_context* ctx, uint64_t ticket);
 
 /* Allocation-free cluster finder (steps 1-4 only).  The paper has no

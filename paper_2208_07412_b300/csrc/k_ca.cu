@@ -183,8 +183,10 @@ __global__ void k_ca_edge_min(DevGeom G, DevWork W) {
   for (unsigned long long c = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; c < n;
        c += (unsigned long long)gridDim.x * blockDim.x) {
     const uint4 rec = __ldg(reinterpret_cast<const uint4*>(W.clusters) + c);
-    const int r = (rec.z >> 24) & 0xff, s = rec.w >> 24;
-    if ((r != 1 && r != R - 2) || s >= G.n_sectors) continue;
+    const int r = (rec.z >> 24) & 0xff;
+    if (r != 1 && r != R - 2) continue;
+    const int s = vsector_of(G, W, c, (int)(rec.w >> 24));
+    if (s >= G.n_sectors) continue;
     const long long sc = W.score[c];
     if (sc < 0) continue;
     const unsigned local = (unsigned)(c - W.row_start[s * R + r]);
@@ -201,8 +203,10 @@ __global__ void k_ca_edge_apply(DevGeom G, DevWork W) {
   for (unsigned long long c = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; c < n;
        c += (unsigned long long)gridDim.x * blockDim.x) {
     const uint4 rec = __ldg(reinterpret_cast<const uint4*>(W.clusters) + c);
-    const int r = (rec.z >> 24) & 0xff, s = rec.w >> 24;
-    if ((r != 0 && r != R - 1) || s >= G.n_sectors) continue;
+    const int r = (rec.z >> 24) & 0xff;
+    if (r != 0 && r != R - 1) continue;
+    const int s = vsector_of(G, W, c, (int)(rec.w >> 24));
+    if (s >= G.n_sectors) continue;
     const unsigned long long key = W.edge_key[c];
     int tgt = -1;
     if (key != ~0ull) {

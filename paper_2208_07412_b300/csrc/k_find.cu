@@ -40,7 +40,7 @@ struct PageHdr {
 // Parse and validate a 32-byte page header (from shared or global memory) of
 // the page at byte offset `off` of a `pages_bytes` buffer.
 __device__ __forceinline__ bool parse_header(const uint4* p, uint64_t off, uint64_t pages_bytes, PageHdr& h) {
-  if ((off & 15) || off + 32 > pages_bytes) return false;
+  if ((off & 15) || off > pages_bytes || pages_bytes - off < 32) return false;
   const uint4 a = p[0], b = p[1];
   h.len = a.x;
   h.n_tb = a.y & 0xffff; h.n_runs = a.y >> 16;
@@ -50,7 +50,7 @@ __device__ __forceinline__ bool parse_header(const uint4* p, uint64_t off, uint6
   h.hi_tb = b.y >> 16; h.hi_runs = b.z & 0xffff; h.hi_dig = b.z >> 16;
   const uint64_t body = (32ull + 2ull * h.n_tb + 2ull * h.n_runs + 3ull) & ~3ull;
   h.body = (uint32_t)body;
-  if (h.magic != (int)TPC_ZS_MAGIC || (h.len & 15) || off + h.len > pages_bytes ||
+  if (h.magic != (int)TPC_ZS_MAGIC || (h.len & 15) || h.len > pages_bytes - off ||
       body + 4ull * ((h.n_dig + 2) / 3) > h.len)
     return false;
   if (h.n_tb > kFrag || h.lo_tb > h.n_tb || h.hi_tb > h.n_tb || h.lo_runs > h.n_runs ||
@@ -420,7 +420,7 @@ k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
     __syncthreads();
     const int f = (int)(w % G.n_frag);
     const int sr = (int)(w / G.n_frag);
-    const int r = sr % G.n_rows, s = sr / G.n_rows;
+    const int r = sr % G.n_rows, s = (sr / G.n_rows) % G.n_phys;   // physical sector
     const int np = G.npads[r];
     const int T = G.n_time_bins;
     const uint64_t off = S.offs[1];
@@ -428,7 +428,7 @@ k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
     // ---- 1. one round trip: stage the page (length guessed from the next
     // page's offset) and load both neighbours' headers
     uint32_t copied = 0;
-    if (off + 32 <= W.pages_bytes && (off & 15) == 0) {
+    if (off <= W.pages_bytes && W.pages_bytes - off >= 32 && (off & 15) == 0) {
       uint64_t guess = (S.offs[2] != ~0ull && S.offs[2] > off) ? S.offs[2] - off : W.pages_bytes - off;
       guess = min(guess, (uint64_t)kOwnStage);
       guess = min(guess, W.pages_bytes - off);
@@ -438,7 +438,8 @@ k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
     }
     if (tid < 4) {
       const uint64_t o2 = S.offs[tid < 2 ? 0 : 2];
-      const bool want = (tid < 2 ? f > 0 : f + 1 < G.n_frag) && o2 != ~0ull && (o2 & 15) == 0 && o2 + 32 <= W.pages_bytes;
+      const bool want = (tid < 2 ? f > 0 : f + 1 < G.n_frag) && o2 != ~0ull && (o2 & 15) == 0 && o2 <= W.pages_bytes &&
+                        W.pages_bytes - o2 >= 32;
       S.hdr[tid] = want ? __ldg(reinterpret_cast<const uint4*>(W.pages + o2) + (tid & 1)) : make_uint4(0, 0, 0, 0);
     }
     __syncthreads();
@@ -711,15 +712,15 @@ cudaError_t launch_scan(uint64_t* v, const unsigned long long* n_ptr, unsigned l
                         unsigned long long* state, unsigned int* ticket, unsigned long long* total, uint32_t* err,
                         int n_sm, cudaStream_t st);
 
+// Raise the finder's dynamic shared-memory limit on the current device (once
+// per context, outside any stream capture).
+cudaError_t prepare_find() {
+  return cudaFuncSetAttribute(k_find_clusters<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+}
+
 cudaError_t launch_find(const DevGeom& G, const DevParams& P, const DevWork& W, unsigned int n_windows,
                         int n_sm, cudaStream_t st, unsigned long long* win_scan_state, int* launches) {
-  size_t sm = find_smem_bytes(G.npmax, G.nw);
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_find_clusters<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  const size_t sm = find_smem_bytes(G.npmax, G.nw);
   unsigned int grid = (unsigned int)min((long long)n_windows, (long long)n_sm * 2);
   if (grid == 0) grid = 1;
   k_find_clusters<true><<<grid, kFindThreads, sm, st>>>(G, P, W, n_windows);
@@ -801,6 +802,8 @@ extern "C" tpc_status tpc_find_clusters_noalloc(const tpc_geometry* geom, const 
   unsigned long long* scratch = g_noalloc_addr[device];
   DevGeom G{};
   G.n_sectors = geom->n_sectors;
+  G.n_phys = geom->n_sectors;
+  G.n_events = 1;
   G.n_rows = geom->n_rows;
   G.npmax = geom->npmax;
   G.nw = (geom->npmax + 31) / 32;

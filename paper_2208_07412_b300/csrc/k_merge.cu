@@ -49,7 +49,7 @@ __global__ void k_merge_cand(DevGeom G, DevParams P, DevWork W) {
     const unsigned long long k = i / ngap;
     const int a2 = W.ch_top[k], a1 = W.ch_top2[k];
     const uint4 rec = __ldg(reinterpret_cast<const uint4*>(W.clusters) + a2);
-    const int r2 = (rec.z >> 24) & 0xff, s = min((int)(rec.w >> 24), G.n_sectors - 1);
+    const int r2 = (rec.z >> 24) & 0xff, s = min(vsector_of(G, W, a2, (int)(rec.w >> 24)), G.n_sectors - 1);
     const int rb = r2 + P.gap_min + (int)(i % ngap);
     if (r2 >= R || rb >= R) continue;
     const long long Xa1 = W.cl_x[a1], Ya1 = W.cl_y[a1], Za1 = W.cl_z[a1];

@@ -11,6 +11,7 @@
 #include <chrono>
 #include <cstdio>
 #include <cstring>
+#include <deque>
 #include <mutex>
 #include <string>
 #include <thread>
@@ -27,6 +28,7 @@ cudaError_t launch_merge(const DevGeom&, const DevParams&, const DevWork&, int, 
                          unsigned long long*, int*);
 cudaError_t launch_fit(const DevGeom&, const DevParams&, const DevWork&, int, cudaStream_t, int*);
 size_t scan_tiles(unsigned long long cap);
+cudaError_t prepare_find();
 }  // namespace tpc
 
 using namespace tpc;
@@ -62,8 +64,13 @@ struct Slot {
   // device buffers
   Buf pages, offsets, winstate, cl, clx, cly, clz, clt, rowstart, up, down, score, edge, jump, chlen, scanv,
       scanst, chainof, clchain, ch_i32, besta, bestb, trk_i32, trackcl, cl2trk, tracks, ctrl, scratch, wincnt, winsoff,
-      candab, candsc, lenhist;
+      candab, candsc, lenhist, evinfo;
   unsigned long long* h_ctrl = nullptr;   // pinned copy of [ctr | err]
+  // batch tables, device (evinfo) and pinned host copy, same layout:
+  // u64 base[kMaxBatch], u64 bytes[kMaxBatch], u32 cl_start[kMaxBatch + 1],
+  // u32 trk_start[kMaxBatch + 1]
+  uint64_t* h_ev = nullptr;
+  uint32_t n_events = 1;
   // capacities
   uint64_t cap_pages = 0, cap_windows = 0, cap_cl = 0, cap_ch = 0;
   // ticket
@@ -72,6 +79,11 @@ struct Slot {
   int state = TPC_STATE_QUEUED;
   tpc_status status = TPC_OK;
   int runs = 0, launches = 0;
+  // the captured pipeline of this slot, valid for one input shape
+  cudaGraphExec_t gexec = nullptr;
+  bool graph_broken = false;
+  DevWork gk_W{};        // the work-space wiring and input shape the graph was captured with
+  uint32_t gk_T = 0, gk_nwin = 0;
   // timeframe
   const void* user_pages = nullptr;
   const uint64_t* user_offsets = nullptr;
@@ -79,6 +91,13 @@ struct Slot {
   unsigned n_windows = 0;
   uint32_t n_time_bins = 0, tf_flags = 0;
   DevWork W{};
+};
+
+// A submitted request that waits for a slot and memory.
+struct Pending {
+  uint64_t ticket = 0;
+  bool batch = false;
+  std::vector<tpc_timeframe_desc> descs;
 };
 
 }  // namespace
@@ -92,6 +111,8 @@ struct tpc_context {
   uint64_t budget = 0, used = 0;
   uint32_t flags = 0;
   std::vector<Slot> slots;
+  std::deque<Pending> pending;                               // arrival order
+  std::vector<std::pair<uint64_t, tpc_status>> failed;       // queued requests that could not start
   uint64_t next_ticket = 1;
   std::mutex mu;
 };
@@ -187,7 +208,7 @@ static size_t slot_bytes(uint64_t pages, uint64_t windows, uint64_t cap_cl, uint
 
 static tpc_status slot_reserve(tpc_context* ctx, Slot& s, uint64_t pages_bytes, uint64_t windows,
                                uint64_t cap_cl, bool need_pages) {
-  const int nsr = ctx->geom.n_sectors * ctx->geom.n_rows;
+  const int nsr = ctx->geom.n_sectors * ctx->geom.n_rows * (int)s.n_events;
   uint64_t cap_ch = cap_cl / (uint64_t)ctx->params.min_chain + 16;
   uint64_t want_pages = need_pages ? pages_bytes : 0;
   size_t cur = slot_bytes(s.cap_pages, s.cap_windows, s.cap_cl, s.cap_ch, nsr);
@@ -277,13 +298,15 @@ static void slot_free(tpc_context* ctx, Slot& s) {
   Buf* all[] = {&s.pages, &s.offsets, &s.winstate, &s.cl, &s.clx, &s.cly, &s.clz, &s.clt, &s.rowstart, &s.up,
                 &s.down, &s.score, &s.edge, &s.jump, &s.chlen, &s.scanv, &s.scanst, &s.chainof, &s.clchain,
                 &s.ch_i32, &s.besta, &s.bestb, &s.trk_i32, &s.trackcl, &s.cl2trk, &s.tracks, &s.ctrl,
-                &s.scratch, &s.wincnt, &s.winsoff, &s.candab, &s.candsc, &s.lenhist};
+                &s.scratch, &s.wincnt, &s.winsoff, &s.candab, &s.candsc, &s.lenhist, &s.evinfo};
   for (Buf* b : all) free_buf(*b);
   for (auto& e : s.ev_stage) if (e) cudaEventDestroy(e);
   if (s.ev_done) cudaEventDestroy(s.ev_done);
   if (s.ev_input) cudaEventDestroy(s.ev_input);
+  if (s.gexec) cudaGraphExecDestroy(s.gexec);
   if (s.own_stream && s.stream) cudaStreamDestroy(s.stream);
   if (s.h_ctrl) cudaFreeHost(s.h_ctrl);
+  if (s.h_ev) cudaFreeHost(s.h_ev);
   (void)ctx;
 }
 
@@ -310,6 +333,8 @@ extern "C" tpc_status tpc_create_context(const tpc_geometry* geom, const tpc_par
   cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, device);
   DevGeom& G = ctx->G;
   G.n_sectors = geom->n_sectors;
+  G.n_phys = geom->n_sectors;
+  G.n_events = 1;
   G.n_rows = geom->n_rows;
   G.npmax = geom->npmax;
   G.nw = (geom->npmax + 31) / 32;
@@ -327,6 +352,7 @@ extern "C" tpc_status tpc_create_context(const tpc_geometry* geom, const tpc_par
   P.sy2 = (float)P.sy2_d; P.sz2 = (float)P.sz2_d;
   for (int i = 0; i < 5; i++) P.c0[i] = (float)p.c0[i];
   if (find_smem_bytes(G.npmax, G.nw) > 227 * 1024) { delete ctx; return fail(TPC_E_INVAL, "rows too wide"); }
+  if (prepare_find() != cudaSuccess) { delete ctx; return fail(TPC_E_CUDA, "cudaFuncSetAttribute failed"); }
   ctx->slots.resize(n_slots);
   for (int i = 0; i < n_slots; i++) {
     Slot& s = ctx->slots[i];
@@ -359,29 +385,126 @@ extern "C" void tpc_destroy_context(tpc_context* ctx) {
 }
 
 // ------------------------------------------------------------------ pipeline
-static tpc_status enqueue(tpc_context* ctx, Slot& s) {
+constexpr uint32_t kMaxBatch = TPC_MAX_BATCH;
+constexpr size_t kEvBytes = (size_t)kMaxBatch * 16 + 2 * ((size_t)kMaxBatch + 1) * 4;
+constexpr uint64_t kBadOffset = 1ull << 62;   // fails every page-range check
+
+// Offsets of a batch: event e's page offsets (copied in place) rebased onto its
+// position in the concatenated page buffer; an offset outside the event's own
+// pages becomes invalid, so a corrupt page table stays corrupt.
+__global__ void k_rebase_offsets(uint64_t* offs, unsigned long long nwin_e, int n_events, const uint64_t* ev) {
+  const unsigned long long n = nwin_e * (unsigned long long)n_events;
+  for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
+       i += (unsigned long long)gridDim.x * blockDim.x) {
+    const unsigned long long e = i / nwin_e;
+    const uint64_t o = offs[i];
+    offs[i] = o < ev[kMaxBatch + e] ? o + ev[e] : kBadOffset;
+  }
+}
+
+// First cluster and first track of every event of a batch (entry n_events:
+// the totals).  Tracks are ordered by their lowest cluster, so an event's
+// first track is the first whose lowest cluster is at or past its first cluster.
+__global__ void k_event_starts(DevWork W, int n_events, unsigned stride, uint32_t* cl_start, uint32_t* trk_start) {
+  const unsigned long long ntrk = min(W.ctr[CTR_NTRK], (unsigned long long)W.cap_ch);
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e <= n_events; e += gridDim.x * blockDim.x) {
+    const uint32_t c = W.row_start[(unsigned long long)e * stride];
+    unsigned long long lo = 0, hi = ntrk;
+    while (lo < hi) {
+      const unsigned long long mid = (lo + hi) >> 1;
+      if ((uint32_t)W.trk_first[mid] < c) lo = mid + 1; else hi = mid;
+    }
+    cl_start[e] = c;
+    trk_start[e] = (uint32_t)lo;
+  }
+}
+
+static tpc_status enqueue_body(tpc_context* ctx, Slot& s, bool capturing) {
   cudaStream_t st = s.stream;
+  // inside a capture an event record must become an external event node
+  const unsigned evf = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
   DevWork& W = s.W;
   DevGeom G = ctx->G;
   G.n_time_bins = (int)s.n_time_bins;
   G.n_frag = (int)((s.n_time_bins + kFrag - 1) / kFrag);
+  G.n_events = (int)s.n_events;
+  G.n_sectors = ctx->geom.n_sectors * (int)s.n_events;
   const bool timing = ctx->flags & TPC_CTX_STAGE_TIMING;
   s.launches = 0;
   CUDA_TRY(cudaMemsetAsync(s.ctrl.p, 0, 256, st));
   CUDA_TRY(cudaMemsetAsync(W.len_hist, 0, 512 * 4, st));
   const size_t tiles_a = scan_tiles(s.cap_cl), tiles_b = scan_tiles(s.cap_ch);
   CUDA_TRY(cudaMemsetAsync(W.scan_state, 0, (tiles_a + tiles_b + scan_tiles(s.n_windows)) * 8, st));
-  if (timing) CUDA_TRY(cudaEventRecord(s.ev_stage[0], st));
+  if (timing) CUDA_TRY(cudaEventRecordWithFlags(s.ev_stage[0], st, evf));
   CUDA_TRY(launch_find(G, ctx->P, W, s.n_windows, ctx->n_sm, st, W.scan_state + tiles_a + tiles_b, &s.launches));
-  if (timing) CUDA_TRY(cudaEventRecord(s.ev_stage[1], st));
+  if (timing) CUDA_TRY(cudaEventRecordWithFlags(s.ev_stage[1], st, evf));
   CUDA_TRY(launch_ca(G, ctx->P, W, ctx->n_sm, st, &s.launches));
-  if (timing) CUDA_TRY(cudaEventRecord(s.ev_stage[2], st));
+  if (timing) CUDA_TRY(cudaEventRecordWithFlags(s.ev_stage[2], st, evf));
   CUDA_TRY(launch_merge(G, ctx->P, W, ctx->n_sm, st, (unsigned long long*)W.scan_state + tiles_a, &s.launches));
-  if (timing) CUDA_TRY(cudaEventRecord(s.ev_stage[3], st));
+  if (timing) CUDA_TRY(cudaEventRecordWithFlags(s.ev_stage[3], st, evf));
   CUDA_TRY(launch_fit(G, ctx->P, W, ctx->n_sm, st, &s.launches));
-  if (timing) CUDA_TRY(cudaEventRecord(s.ev_stage[4], st));
+  if (timing) CUDA_TRY(cudaEventRecordWithFlags(s.ev_stage[4], st, evf));
+  if (s.n_events > 1) {
+    uint32_t* d_st = (uint32_t*)((uint64_t*)s.evinfo.p + 2 * kMaxBatch);
+    k_event_starts<<<(s.n_events + 256) / 256, 256, 0, st>>>(W, (int)s.n_events,
+                                                             (unsigned)(ctx->geom.n_sectors * ctx->geom.n_rows),
+                                                             d_st, d_st + kMaxBatch + 1);
+    CUDA_TRY(cudaGetLastError());
+    s.launches++;
+    uint32_t* h_st = (uint32_t*)(s.h_ev + 2 * kMaxBatch);
+    CUDA_TRY(cudaMemcpyAsync(h_st, d_st, (s.n_events + 1) * 4, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(h_st + kMaxBatch + 1, d_st + kMaxBatch + 1, (s.n_events + 1) * 4,
+                             cudaMemcpyDeviceToHost, st));
+  }
   CUDA_TRY(cudaMemcpyAsync(s.h_ctrl, s.ctrl.p, 256, cudaMemcpyDeviceToHost, st));
-  CUDA_TRY(cudaEventRecord(s.ev_done, st));
+  CUDA_TRY(cudaEventRecordWithFlags(s.ev_done, st, evf));
+  return TPC_OK;
+}
+
+// The whole pipeline of a timeframe, replayed from a CUDA graph captured once
+// per slot and input shape (pointers, sizes, capacities): one launch instead of
+// ~40 enqueues.  A capture that fails falls back to plain launches for good.
+static tpc_status enqueue(tpc_context* ctx, Slot& s) {
+  const bool use_graph = !(ctx->flags & TPC_CTX_NO_GRAPHS) && !s.graph_broken;
+  if (!use_graph) {
+    tpc_status st = enqueue_body(ctx, s, false);
+    if (st == TPC_OK) s.runs++;
+    return st;
+  }
+  const bool same = s.gexec && s.gk_T == s.n_time_bins && s.gk_nwin == s.n_windows &&
+                    std::memcmp(&s.gk_W, &s.W, sizeof(DevWork)) == 0;
+  if (!same) {
+    // capture the pipeline; a graph of the same topology (new input pointers,
+    // regrown buffers) updates the instantiated one in place
+    cudaGraph_t g = nullptr;
+    CUDA_TRY(cudaStreamBeginCapture(s.stream, cudaStreamCaptureModeThreadLocal));
+    tpc_status st = enqueue_body(ctx, s, true);
+    cudaError_t e = cudaStreamEndCapture(s.stream, &g);
+    bool ok = st == TPC_OK && e == cudaSuccess && g;
+    if (ok && s.gexec) {
+      cudaGraphExecUpdateResultInfo info;
+      if (cudaGraphExecUpdate(s.gexec, g, &info) != cudaSuccess) {
+        cudaGetLastError();
+        cudaGraphExecDestroy(s.gexec);
+        s.gexec = nullptr;
+      }
+    }
+    if (ok && !s.gexec) ok = cudaGraphInstantiate(&s.gexec, g, 0) == cudaSuccess;
+    if (g) cudaGraphDestroy(g);
+    if (!ok) {
+      if (s.gexec) cudaGraphExecDestroy(s.gexec);
+      s.gexec = nullptr;
+      s.graph_broken = true;
+      cudaGetLastError();
+      st = enqueue_body(ctx, s, false);
+      if (st == TPC_OK) s.runs++;
+      return st;
+    }
+    s.gk_W = s.W;
+    s.gk_T = s.n_time_bins;
+    s.gk_nwin = s.n_windows;
+  }
+  CUDA_TRY(cudaGraphLaunch(s.gexec, s.stream));
   s.runs++;
   return TPC_OK;
 }
@@ -397,19 +520,20 @@ static uint64_t guaranteed_cap_cl(uint64_t pages_bytes) {
   return pages_bytes / 3 + 1024;
 }
 
-extern "C" tpc_status tpc_submit_timeframe(tpc_context* ctx, const tpc_timeframe_desc* tf, uint64_t* ticket) {
-  if (!ctx || !tf || !ticket) return fail(TPC_E_INVAL, "tpc_submit_timeframe: null argument");
+// Validation of one descriptor (before any slot is touched).
+static tpc_status check_desc(const tpc_timeframe_desc* tf) {
   if (tf->n_time_bins < 1 || tf->n_time_bins > 65535) return fail(TPC_E_INVAL, "n_time_bins out of range");
   if (!tf->pages || !tf->page_offsets || tf->pages_bytes < 32)
     return fail(TPC_E_INVAL, "pages / page_offsets missing");
+  if ((tf->flags & TPC_TF_DEVICE_INPUT) && ((uintptr_t)tf->pages & 15))
+    return fail(TPC_E_INVAL, "device pages must be 16-byte aligned");
+  return TPC_OK;
+}
+
+// Start one timeframe on free slot s (lock held).
+static tpc_status start_timeframe(tpc_context* ctx, Slot* s, const tpc_timeframe_desc* tf) {
   const bool dev_in = tf->flags & TPC_TF_DEVICE_INPUT;
-  if (dev_in && ((uintptr_t)tf->pages & 15)) return fail(TPC_E_INVAL, "device pages must be 16-byte aligned");
-  std::lock_guard<std::mutex> lk(ctx->mu);
-  CUDA_TRY(cudaSetDevice(ctx->device));
-  Slot* s = nullptr;
-  for (auto& c : ctx->slots)
-    if (!c.in_use) { s = &c; break; }
-  if (!s) return fail(TPC_E_BUSY, "no free slot: release a finished ticket first");
+  s->n_events = 1;
   const unsigned nfrag = (tf->n_time_bins + kFrag - 1) / kFrag;
   const uint64_t nwin = (uint64_t)ctx->geom.n_sectors * ctx->geom.n_rows * nfrag;
   if (nwin > 0xffffffffull) return fail(TPC_E_INVAL, "too many windows");
@@ -434,14 +558,171 @@ extern "C" tpc_status tpc_submit_timeframe(tpc_context* ctx, const tpc_timeframe
   }
   s->W.pages_bytes = tf->pages_bytes;
   CUDA_TRY(cudaEventRecord(s->ev_input, s->stream));
-  st = enqueue(ctx, *s);
+  return enqueue(ctx, *s);
+}
+
+// Start a batch of events on free slot s (lock held); descriptors validated.
+static tpc_status start_batch(tpc_context* ctx, Slot* s, const tpc_timeframe_desc* tfs, uint32_t n_events) {
+  const uint32_t T = tfs[0].n_time_bins;
+  std::vector<uint64_t> base(n_events), bytes(n_events);
+  uint64_t total = 0;
+  for (uint32_t e = 0; e < n_events; e++) {
+    base[e] = total;
+    bytes[e] = tfs[e].pages_bytes;
+    total += (tfs[e].pages_bytes + 15) & ~15ull;
+  }
+  const unsigned nfrag = (T + kFrag - 1) / kFrag;
+  const uint64_t nwin_e = (uint64_t)ctx->geom.n_sectors * ctx->geom.n_rows * nfrag;
+  const uint64_t nwin = nwin_e * n_events;
+  if (nwin > 0xffffffffull) return fail(TPC_E_INVAL, "too many windows");
+  if (!s->h_ev) CUDA_TRY(cudaMallocHost((void**)&s->h_ev, kEvBytes));
+  CUDA_TRY(ensure(s->evinfo, kEvBytes));
+  uint64_t cap_cl = std::max<uint64_t>(65536, total / 12);
+  cap_cl = std::min(cap_cl, guaranteed_cap_cl(total));
+  cap_cl = std::max(cap_cl, s->cap_cl);
+  s->n_events = n_events;
+  tpc_status st = slot_reserve(ctx, *s, total, nwin, cap_cl, true);
+  if (st) { s->n_events = 1; return st; }
+  s->pages_bytes = total;
+  s->n_windows = (unsigned)nwin;
+  s->n_time_bins = T;
+  s->tf_flags = 0;   // the pages now live in the slot's own buffer
+  s->runs = 0;
+  // gather the events' pages and page tables, then rebase the offsets
+  uint8_t* pages = (uint8_t*)s->pages.p;
+  uint64_t* offs = (uint64_t*)s->offsets.p;
+  for (uint32_t e = 0; e < n_events; e++) {
+    CUDA_TRY(cudaMemcpyAsync(pages + base[e], tfs[e].pages, bytes[e], cudaMemcpyDefault, s->stream));
+    CUDA_TRY(cudaMemcpyAsync(offs + e * nwin_e, tfs[e].page_offsets, nwin_e * 8, cudaMemcpyDefault, s->stream));
+  }
+  // the slot is free, so nothing in flight still reads its pinned table
+  std::memcpy(s->h_ev, base.data(), n_events * 8);
+  std::memcpy(s->h_ev + kMaxBatch, bytes.data(), n_events * 8);
+  uint64_t* d_ev = (uint64_t*)s->evinfo.p;
+  CUDA_TRY(cudaMemcpyAsync(d_ev, s->h_ev, 2 * (size_t)kMaxBatch * 8, cudaMemcpyHostToDevice, s->stream));
+  const unsigned g = (unsigned)std::min<uint64_t>((nwin + 255) / 256, (uint64_t)ctx->n_sm * 8);
+  k_rebase_offsets<<<g, 256, 0, s->stream>>>(offs, nwin_e, (int)n_events, d_ev);
+  CUDA_TRY(cudaGetLastError());
+  s->W.pages = pages;
+  s->W.page_offsets = offs;
+  s->W.pages_bytes = total;
+  CUDA_TRY(cudaEventRecord(s->ev_input, s->stream));
+  return enqueue(ctx, *s);
+}
+
+static Slot* free_slot(tpc_context* ctx) {
+  for (auto& c : ctx->slots)
+    if (!c.in_use) return &c;
+  return nullptr;
+}
+
+static bool any_in_use(const tpc_context* ctx) {
+  for (auto& c : ctx->slots)
+    if (c.in_use) return true;
+  return false;
+}
+
+// Give the device memory of idle slots other than keep back to the budget.
+static void reclaim_idle(tpc_context* ctx, const Slot* keep) {
+  const int nsr1 = ctx->geom.n_sectors * ctx->geom.n_rows;
+  for (auto& c : ctx->slots) {
+    if (c.in_use || &c == keep || !c.cap_pages && !c.cap_cl) continue;
+    cudaStreamSynchronize(c.stream);
+    ctx->used -= slot_bytes(c.cap_pages, c.cap_windows, c.cap_cl, c.cap_ch, nsr1 * (int)c.n_events);
+    Buf* big[] = {&c.pages, &c.offsets, &c.winstate, &c.cl, &c.clx, &c.cly, &c.clz, &c.clt, &c.up, &c.down,
+                  &c.score, &c.edge, &c.jump, &c.chlen, &c.scanv, &c.scanst, &c.chainof, &c.clchain, &c.ch_i32,
+                  &c.besta, &c.bestb, &c.trk_i32, &c.trackcl, &c.cl2trk, &c.tracks, &c.scratch, &c.wincnt,
+                  &c.winsoff, &c.candab, &c.candsc};
+    for (Buf* b : big) free_buf(*b);
+    c.cap_pages = c.cap_windows = c.cap_cl = c.cap_ch = 0;
+  }
+}
+
+// Start a request on a free slot, reclaiming idle slots' memory if the budget
+// is short.  Returns TPC_E_NOMEM if it still does not fit.
+static tpc_status start_request(tpc_context* ctx, Slot* s, const Pending& rq) {
+  auto go = [&]() {
+    return rq.descs.size() == 1 && !rq.batch ? start_timeframe(ctx, s, rq.descs.data())
+                                             : start_batch(ctx, s, rq.descs.data(), (uint32_t)rq.descs.size());
+  };
+  tpc_status st = go();
+  if (st == TPC_E_NOMEM) {
+    reclaim_idle(ctx, s);
+    st = go();
+  }
   if (st) return st;
   s->in_use = true;
-  s->ticket = ctx->next_ticket++;
+  s->ticket = rq.ticket;
   s->state = TPC_STATE_RUNNING;
   s->status = TPC_OK;
-  *ticket = s->ticket;
   return TPC_OK;
+}
+
+// Admit queued requests in arrival order while slots and memory allow (lock
+// held).  A request that cannot fit even with every other slot idle fails.
+static void admit(tpc_context* ctx) {
+  while (!ctx->pending.empty()) {
+    Slot* s = free_slot(ctx);
+    if (!s) return;
+    Pending& rq = ctx->pending.front();
+    tpc_status st = start_request(ctx, s, rq);
+    if (st == TPC_E_NOMEM && any_in_use(ctx)) return;   // wait for memory
+    if (st) ctx->failed.emplace_back(rq.ticket, st);
+    ctx->pending.pop_front();
+  }
+}
+
+// Submit or queue one request (lock not held).
+static tpc_status submit(tpc_context* ctx, Pending&& rq, bool nowait, uint64_t* ticket) {
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  rq.ticket = ctx->next_ticket;
+  Slot* s = ctx->pending.empty() ? free_slot(ctx) : nullptr;
+  if (s) {
+    tpc_status st = start_request(ctx, s, rq);
+    if (st == TPC_OK) {
+      ctx->next_ticket++;
+      *ticket = rq.ticket;
+      return TPC_OK;
+    }
+    if (st != TPC_E_NOMEM || !any_in_use(ctx)) return st;
+    if (nowait) return fail(TPC_E_BUSY, "not enough of the memory budget free while other timeframes run");
+  } else if (nowait) {
+    return fail(TPC_E_BUSY, "no free slot: release a finished ticket first");
+  }
+  // queued: admitted when a slot and memory free up (tpc_release)
+  ctx->next_ticket++;
+  *ticket = rq.ticket;
+  ctx->pending.push_back(std::move(rq));
+  return TPC_OK;
+}
+
+extern "C" tpc_status tpc_submit_timeframe(tpc_context* ctx, const tpc_timeframe_desc* tf, uint64_t* ticket) {
+  if (!ctx || !tf || !ticket) return fail(TPC_E_INVAL, "tpc_submit_timeframe: null argument");
+  tpc_status st = check_desc(tf);
+  if (st) return st;
+  Pending rq;
+  rq.descs.assign(tf, tf + 1);
+  return submit(ctx, std::move(rq), tf->flags & TPC_TF_NOWAIT, ticket);
+}
+
+extern "C" tpc_status tpc_submit_batch(tpc_context* ctx, const tpc_timeframe_desc* tfs, uint32_t n_events,
+                                       uint64_t* ticket) {
+  if (!ctx || !tfs || !ticket) return fail(TPC_E_INVAL, "tpc_submit_batch: null argument");
+  if (n_events < 1 || n_events > kMaxBatch) return fail(TPC_E_INVAL, "n_events out of range");
+  for (uint32_t e = 0; e < n_events; e++) {
+    tpc_status st = check_desc(&tfs[e]);
+    if (st) return st;
+    if (tfs[e].n_time_bins != tfs[0].n_time_bins)
+      return fail(TPC_E_INVAL, "every event of a batch needs the same n_time_bins");
+  }
+  const uint64_t nfrag = (tfs[0].n_time_bins + kFrag - 1) / kFrag;
+  if ((uint64_t)ctx->geom.n_sectors * ctx->geom.n_rows * nfrag * n_events > 0xffffffffull)
+    return fail(TPC_E_INVAL, "too many windows");
+  Pending rq;
+  rq.batch = true;
+  rq.descs.assign(tfs, tfs + n_events);
+  return submit(ctx, std::move(rq), tfs[0].flags & TPC_TF_NOWAIT, ticket);
 }
 
 static tpc_status status_from_err(uint32_t e) {
@@ -454,10 +735,18 @@ static tpc_status status_from_err(uint32_t e) {
 // Called with the lock held once ev_done has completed.
 static tpc_status finish(tpc_context* ctx, Slot& s) {
   const uint32_t e = *(const uint32_t*)(s.h_ctrl + CTR_COUNT);
-  if ((e & (kErrOverflowCl | kErrOverflowCh)) && !(e & (kErrCorrupt | kErrTimeout)) && s.runs == 1) {
-    // regrow to the guaranteed bound and run again (input still resident)
-    uint64_t cap = guaranteed_cap_cl(s.pages_bytes);
+  if ((e & (kErrOverflowCl | kErrOverflowCh)) && !(e & (kErrCorrupt | kErrTimeout)) && s.runs <= 2) {
+    // regrow and run again (input still resident): to 1.25x the cluster count
+    // the finder reported (exact even past the capacity) or twice the old
+    // capacity, and on a second overflow to the bound no timeframe can exceed
+    const uint64_t ncl = s.h_ctrl[CTR_NCL];
+    uint64_t cap = s.runs == 1 ? std::max<uint64_t>(2 * s.cap_cl, ncl + ncl / 4 + 1024) : ~0ull;
+    cap = std::min(cap, guaranteed_cap_cl(s.pages_bytes));
     tpc_status st = slot_reserve(ctx, s, s.pages_bytes, s.n_windows, cap, !(s.tf_flags & TPC_TF_DEVICE_INPUT));
+    if (st == TPC_E_NOMEM) {
+      reclaim_idle(ctx, &s);
+      st = slot_reserve(ctx, s, s.pages_bytes, s.n_windows, cap, !(s.tf_flags & TPC_TF_DEVICE_INPUT));
+    }
     if (st) { s.state = TPC_STATE_FAILED; s.status = st; return st; }
     st = enqueue(ctx, s);
     if (st) { s.state = TPC_STATE_FAILED; s.status = st; return st; }
@@ -482,28 +771,43 @@ extern "C" tpc_status tpc_poll(tpc_context* ctx, uint64_t ticket, uint32_t timeo
     {
       std::lock_guard<std::mutex> lk(ctx->mu);
       Slot* s = find_ticket(ctx, ticket);
-      if (!s) return fail(TPC_E_NOTFOUND, "unknown ticket");
-      if (s->state == TPC_STATE_DONE || s->state == TPC_STATE_FAILED) {
+      if (!s) {
+        cudaSetDevice(ctx->device);
+        admit(ctx);
+        s = find_ticket(ctx, ticket);
+      }
+      if (!s) {
+        for (auto& f : ctx->failed)
+          if (f.first == ticket) {
+            *state = TPC_STATE_FAILED;
+            return fail(f.second, "queued timeframe could not start");
+          }
+        bool queued = false;
+        for (auto& rq : ctx->pending) queued |= rq.ticket == ticket;
+        if (!queued) return fail(TPC_E_NOTFOUND, "unknown ticket");
+        *state = TPC_STATE_QUEUED;
+      } else if (s->state == TPC_STATE_DONE || s->state == TPC_STATE_FAILED) {
         *state = s->state;
         return s->status ? fail(s->status, "timeframe failed") : TPC_OK;
-      }
-      cudaSetDevice(ctx->device);
-      cudaError_t q = cudaEventQuery(s->ev_done);
-      if (q == cudaSuccess) {
-        tpc_status st = finish(ctx, *s);
-        if (st != TPC_E_NOTREADY) {
+      } else {
+        cudaSetDevice(ctx->device);
+        cudaError_t q = cudaEventQuery(s->ev_done);
+        if (q == cudaSuccess) {
+          tpc_status st = finish(ctx, *s);
+          if (st != TPC_E_NOTREADY) {
+            *state = s->state;
+            return st;
+          }
+        } else if (q != cudaErrorNotReady) {
+          s->state = TPC_STATE_FAILED;
+          s->status = TPC_E_CUDA;
           *state = s->state;
-          return st;
+          return fail(TPC_E_CUDA, std::string("device error: ") + cudaGetErrorString(q));
+        } else if (s->state == TPC_STATE_RUNNING && cudaEventQuery(s->ev_input) == cudaSuccess) {
+          s->state = TPC_STATE_INPUT_RELEASED;
         }
-      } else if (q != cudaErrorNotReady) {
-        s->state = TPC_STATE_FAILED;
-        s->status = TPC_E_CUDA;
         *state = s->state;
-        return fail(TPC_E_CUDA, std::string("device error: ") + cudaGetErrorString(q));
-      } else if (s->state == TPC_STATE_RUNNING && cudaEventQuery(s->ev_input) == cudaSuccess) {
-        s->state = TPC_STATE_INPUT_RELEASED;
       }
-      *state = s->state;
     }
     if (timeout_us == 0) return TPC_OK;
     auto el = std::chrono::duration_cast<std::chrono::microseconds>(std::chrono::steady_clock::now() - t0).count();
@@ -557,6 +861,82 @@ extern "C" tpc_status tpc_get_tracks(tpc_context* ctx, uint64_t ticket, tpc_trac
   if (cluster_to_track && ncl)
     CUDA_TRY(cudaMemcpyAsync(cluster_to_track, s->W.cl2trk, ncl * 4, cudaMemcpyDeviceToHost, s->stream));
   CUDA_TRY(cudaStreamSynchronize(s->stream));
+  return TPC_OK;
+}
+
+extern "C" tpc_status tpc_get_batch_info(tpc_context* ctx, uint64_t ticket, uint32_t* n_events,
+                                         uint64_t* cluster_start, uint64_t* track_start) {
+  if (!ctx || !n_events) return fail(TPC_E_INVAL, "tpc_get_batch_info: null argument");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  Slot* s;
+  tpc_status st = done_slot(ctx, ticket, &s);
+  if (st) return st;
+  *n_events = s->n_events;
+  const uint32_t* h = (const uint32_t*)(s->h_ev + 2 * kMaxBatch);
+  for (uint32_t e = 0; e <= s->n_events; e++) {
+    const bool one = s->n_events == 1;
+    if (cluster_start) cluster_start[e] = one ? (e ? n_cl_of(*s) : 0) : h[e];
+    if (track_start) track_start[e] = one ? (e ? n_trk_of(*s) : 0) : h[kMaxBatch + 1 + e];
+  }
+  return TPC_OK;
+}
+
+static tpc_status event_range(const Slot& s, uint32_t event, uint64_t* c0, uint64_t* c1, uint64_t* t0,
+                              uint64_t* t1) {
+  if (event >= s.n_events) return fail(TPC_E_INVAL, "event index out of range");
+  if (s.n_events == 1) {
+    *c0 = 0; *c1 = n_cl_of(s); *t0 = 0; *t1 = n_trk_of(s);
+    return TPC_OK;
+  }
+  const uint32_t* h = (const uint32_t*)(s.h_ev + 2 * kMaxBatch);
+  *c0 = h[event]; *c1 = h[event + 1];
+  *t0 = h[kMaxBatch + 1 + event]; *t1 = h[kMaxBatch + 2 + event];
+  return TPC_OK;
+}
+
+extern "C" tpc_status tpc_get_event_clusters(tpc_context* ctx, uint64_t ticket, uint32_t event, tpc_cluster* out,
+                                             uint64_t cap, uint64_t* n) {
+  if (!ctx || !n) return fail(TPC_E_INVAL, "tpc_get_event_clusters: null argument");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  Slot* s;
+  tpc_status st = done_slot(ctx, ticket, &s);
+  if (st) return st;
+  uint64_t c0, c1, t0, t1;
+  if ((st = event_range(*s, event, &c0, &c1, &t0, &t1))) return st;
+  *n = c1 - c0;
+  if (!out) return TPC_OK;
+  if (cap < *n) return fail(TPC_E_OVERFLOW, "output buffer too small");
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  if (*n)
+    CUDA_TRY(cudaMemcpyAsync(out, s->W.clusters + c0, *n * sizeof(tpc_cluster), cudaMemcpyDeviceToHost, s->stream));
+  CUDA_TRY(cudaStreamSynchronize(s->stream));
+  return TPC_OK;
+}
+
+extern "C" tpc_status tpc_get_event_tracks(tpc_context* ctx, uint64_t ticket, uint32_t event, tpc_track* out,
+                                           uint64_t cap, uint64_t* n, int32_t* cluster_to_track) {
+  if (!ctx || !n) return fail(TPC_E_INVAL, "tpc_get_event_tracks: null argument");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  Slot* s;
+  tpc_status st = done_slot(ctx, ticket, &s);
+  if (st) return st;
+  uint64_t c0, c1, t0, t1;
+  if ((st = event_range(*s, event, &c0, &c1, &t0, &t1))) return st;
+  *n = t1 - t0;
+  if (!out && !cluster_to_track) return TPC_OK;
+  if (out && cap < *n) return fail(TPC_E_OVERFLOW, "output buffer too small");
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  if (out && *n)
+    CUDA_TRY(cudaMemcpyAsync(out, s->W.tracks + t0, *n * sizeof(tpc_track), cudaMemcpyDeviceToHost, s->stream));
+  if (cluster_to_track && c1 > c0)
+    CUDA_TRY(cudaMemcpyAsync(cluster_to_track, s->W.cl2trk + c0, (c1 - c0) * 4, cudaMemcpyDeviceToHost, s->stream));
+  CUDA_TRY(cudaStreamSynchronize(s->stream));
+  // indices relative to the event, as a run of the event alone gives them
+  if (out)
+    for (uint64_t i = 0; i < *n; i++) out[i].first_cluster -= (int32_t)c0;
+  if (cluster_to_track)
+    for (uint64_t i = 0; i < c1 - c0; i++)
+      if (cluster_to_track[i] >= 0) cluster_to_track[i] -= (int32_t)t0;
   return TPC_OK;
 }
 
@@ -632,12 +1012,20 @@ extern "C" tpc_status tpc_get_counters(tpc_context* ctx, uint64_t ticket, uint64
 extern "C" tpc_status tpc_release(tpc_context* ctx, uint64_t ticket) {
   if (!ctx) return fail(TPC_E_INVAL, "tpc_release: null argument");
   std::lock_guard<std::mutex> lk(ctx->mu);
-  Slot* s = find_ticket(ctx, ticket);
-  if (!s) return fail(TPC_E_NOTFOUND, "unknown ticket");
   cudaSetDevice(ctx->device);
+  Slot* s = find_ticket(ctx, ticket);
+  if (!s) {
+    // a queued request is cancelled, a failed one forgotten
+    for (auto it = ctx->pending.begin(); it != ctx->pending.end(); ++it)
+      if (it->ticket == ticket) { ctx->pending.erase(it); admit(ctx); return TPC_OK; }
+    for (auto it = ctx->failed.begin(); it != ctx->failed.end(); ++it)
+      if (it->first == ticket) { ctx->failed.erase(it); return TPC_OK; }
+    return fail(TPC_E_NOTFOUND, "unknown ticket");
+  }
   cudaStreamSynchronize(s->stream);
   s->in_use = false;
   s->state = TPC_STATE_QUEUED;
+  admit(ctx);   // the freed slot and memory go to the oldest queued request
   return TPC_OK;
 }
 

@@ -39,7 +39,11 @@ constexpr long long kSpinLimit = 4000000LL;
 // Geometry + parameters, passed by value to every kernel (fits in the 32 KB
 // kernel parameter space).
 struct DevGeom {
+  // A batch of events runs as one timeframe whose sector axis is
+  // (event, sector): n_sectors = n_events * n_phys "virtual" sectors, window and
+  // row tables indexed by virtual sector, records carrying the physical one.
   int n_sectors, n_rows, n_time_bins, n_frag;
+  int n_phys, n_events;          // sectors of the detector, events in the batch
   int npmax, nw;                 // widest row, 32-pad words per plane row
   int npads[kMaxRowsDev];
   int xrow[kMaxRowsDev];         // X of each row in u (= 64 * row_x)
@@ -228,6 +232,20 @@ __device__ __forceinline__ unsigned long long lookback_wait(unsigned long long* 
   return excl;
 }
 
-__device__ __forceinline__ int sector_row_of(const tpc_cluster& c) { return c.sector; }
+// Event of cluster c in a batch: the last e with row_start[e * n_phys * R] <= c.
+__device__ __forceinline__ int event_of(const DevGeom& G, const DevWork& W, unsigned long long c) {
+  int lo = 0, hi = G.n_events - 1;
+  const unsigned stride = (unsigned)(G.n_phys * G.n_rows);
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if ((unsigned long long)W.row_start[(unsigned)mid * stride] <= c) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Virtual sector of cluster c whose record holds physical sector s.
+__device__ __forceinline__ int vsector_of(const DevGeom& G, const DevWork& W, unsigned long long c, int s) {
+  return G.n_events > 1 ? s + G.n_phys * event_of(G, W, c) : s;
+}
 
 }  // namespace tpc

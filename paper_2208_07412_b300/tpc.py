@@ -25,6 +25,7 @@ TPC_STATE_QUEUED, TPC_STATE_RUNNING, TPC_STATE_INPUT_RELEASED, TPC_STATE_DONE, T
 TPC_TF_DEVICE_INPUT = 1
 TPC_TF_NOWAIT = 2
 TPC_CTX_STAGE_TIMING = 1
+TPC_CTX_NO_GRAPHS = 2
 STAGES = ("find", "ca", "merge", "fit")
 
 CLUSTER_DTYPE = np.dtype([("pad_fp", "<u2"), ("time_fp", "<u2"), ("qmax", "<u2"), ("qtot", "<u2"),
@@ -69,7 +70,8 @@ class tpc_timeframe_desc(ctypes.Structure):
 EXPORTS = ("tpc_params_default", "tpc_create_geometry", "tpc_destroy_geometry", "tpc_create_context",
            "tpc_destroy_context", "tpc_submit_timeframe", "tpc_poll", "tpc_get_clusters",
            "tpc_get_tracks", "tpc_get_links", "tpc_get_device_results", "tpc_get_stage_times",
-           "tpc_get_counters", "tpc_release", "tpc_last_error", "tpc_find_clusters_noalloc")
+           "tpc_get_counters", "tpc_release", "tpc_last_error", "tpc_find_clusters_noalloc",
+           "tpc_submit_batch", "tpc_get_batch_info", "tpc_get_event_clusters", "tpc_get_event_tracks")
 
 _lib = None
 
@@ -109,6 +111,10 @@ def load(build_if_missing: bool = True):
     L.tpc_release.argtypes = [_P, _u64]
     L.tpc_find_clusters_noalloc.argtypes = [_P, ctypes.POINTER(tpc_params), ctypes.c_int, _P, _u64, _P,
                                             ctypes.c_uint32, _P, _u64, ctypes.POINTER(_u64), _P]
+    L.tpc_submit_batch.argtypes = [_P, ctypes.POINTER(tpc_timeframe_desc), ctypes.c_uint32, ctypes.POINTER(_u64)]
+    L.tpc_get_batch_info.argtypes = [_P, _u64, ctypes.POINTER(ctypes.c_uint32), _P, _P]
+    L.tpc_get_event_clusters.argtypes = [_P, _u64, ctypes.c_uint32, _P, _u64, ctypes.POINTER(_u64)]
+    L.tpc_get_event_tracks.argtypes = [_P, _u64, ctypes.c_uint32, _P, _u64, ctypes.POINTER(_u64), _P]
     L.tpc_last_error.argtypes = []
     L.tpc_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -166,8 +172,16 @@ def tpc_submit_timeframe(ctx, pages, page_offsets, n_time_bins: int, flags: int 
     """pages / page_offsets: numpy arrays (host) or torch CUDA tensors (device,
     TPC_TF_DEVICE_INPUT is then set).  The caller keeps them alive until the
     ticket reaches TPC_STATE_INPUT_RELEASED."""
-    is_torch = hasattr(pages, "data_ptr")
-    if is_torch:
+    d, _keep = _desc(pages, page_offsets, n_time_bins, flags)
+    t = _u64()
+    _check(load().tpc_submit_timeframe(ctx, ctypes.byref(d), ctypes.byref(t)))
+    return int(t.value)
+
+
+def _desc(pages, page_offsets, n_time_bins: int, flags: int = 0):
+    """Descriptor of one timeframe; also returns the arrays it points into
+    (keep them alive while the descriptor is in use)."""
+    if hasattr(pages, "data_ptr"):
         if pages.is_cuda:
             flags |= TPC_TF_DEVICE_INPUT
         nbytes = pages.numel() * pages.element_size()
@@ -175,10 +189,57 @@ def tpc_submit_timeframe(ctx, pages, page_offsets, n_time_bins: int, flags: int 
         pages = np.ascontiguousarray(pages, np.uint8)
         page_offsets = np.ascontiguousarray(page_offsets, np.uint64)
         nbytes = pages.nbytes
-    d = tpc_timeframe_desc(_ptr(pages), nbytes, _ptr(page_offsets), int(n_time_bins), flags)
+    return tpc_timeframe_desc(_ptr(pages), nbytes, _ptr(page_offsets), int(n_time_bins), flags), (pages, page_offsets)
+
+
+def tpc_submit_batch(ctx, events, n_time_bins: int) -> tuple[int, list]:
+    """events: [(pages, page_offsets[, n_time_bins]), ...] as for
+    tpc_submit_timeframe (n_time_bins: the argument unless given per event).
+    Returns (ticket, keep): keep holds the arrays the descriptors point into;
+    keep it alive until TPC_STATE_INPUT_RELEASED."""
+    descs, keep = [], []
+    for ev in events:
+        pages, offs, *rest = ev
+        d, k = _desc(pages, offs, rest[0] if rest else n_time_bins)
+        descs.append(d)
+        keep.append(k)
+    arr = (tpc_timeframe_desc * len(descs))(*descs)
     t = _u64()
-    _check(load().tpc_submit_timeframe(ctx, ctypes.byref(d), ctypes.byref(t)))
-    return int(t.value)
+    _check(load().tpc_submit_batch(ctx, arr, len(descs), ctypes.byref(t)))
+    return int(t.value), keep
+
+
+def tpc_get_batch_info(ctx, ticket: int):
+    """Returns (cluster_start, track_start), each n_events + 1 long."""
+    L = load()
+    n = ctypes.c_uint32()
+    _check(L.tpc_get_batch_info(ctx, ticket, ctypes.byref(n), None, None))
+    cs = np.zeros(n.value + 1, np.uint64)
+    ts = np.zeros(n.value + 1, np.uint64)
+    _check(L.tpc_get_batch_info(ctx, ticket, ctypes.byref(n), cs.ctypes.data, ts.ctypes.data))
+    return cs, ts
+
+
+def tpc_get_event_clusters(ctx, ticket: int, event: int) -> np.ndarray:
+    L = load()
+    n = _u64()
+    _check(L.tpc_get_event_clusters(ctx, ticket, event, None, 0, ctypes.byref(n)))
+    out = np.zeros(n.value, CLUSTER_DTYPE)
+    if n.value:
+        _check(L.tpc_get_event_clusters(ctx, ticket, event, out.ctypes.data, n.value, ctypes.byref(n)))
+    return out
+
+
+def tpc_get_event_tracks(ctx, ticket: int, event: int, n_clusters: int):
+    """Returns (tracks, cluster_to_track) of one event, indices relative to it."""
+    L = load()
+    n = _u64()
+    _check(L.tpc_get_event_tracks(ctx, ticket, event, None, 0, ctypes.byref(n), None))
+    out = np.zeros(n.value, TRACK_DTYPE)
+    m = np.zeros(n_clusters, np.int32)
+    _check(L.tpc_get_event_tracks(ctx, ticket, event, out.ctypes.data if n.value else None, n.value,
+                                  ctypes.byref(n), m.ctypes.data if n_clusters else None))
+    return out, m
 
 
 def tpc_poll(ctx, ticket: int, timeout_us: int = 0xFFFFFFFF) -> int:
@@ -298,6 +359,25 @@ class Reconstructor:
         finally:
             tpc_release(self.ctx, t)
         return dict(clusters=cl, up=up, down=down, chain_of=chain, tracks=tracks, cl2trk=m, counters=ctr)
+
+    def run_batch(self, tfs):
+        """Submit generated timeframes (same n_time_bins) as one batch, wait,
+        fetch each event's results (indices relative to the event), release."""
+        t, keep = tpc_submit_batch(self.ctx, [(tf.pages, tf.page_offsets) for tf in tfs], tfs[0].n_time_bins)
+        try:
+            self.wait(t)
+            out = []
+            for e in range(len(tfs)):
+                cl = tpc_get_event_clusters(self.ctx, t, e)
+                tracks, m = tpc_get_event_tracks(self.ctx, t, e, len(cl))
+                out.append(dict(clusters=cl, tracks=tracks, cl2trk=m))
+            ctr = tpc_get_counters(self.ctx, t)
+            for o in out:
+                o["counters"] = ctr
+        finally:
+            tpc_release(self.ctx, t)
+            del keep
+        return out
 
     def close(self):
         if self.ctx:

@@ -1,0 +1,87 @@
+"""Continuous-readout timeframes at a 50 kHz Pb-Pb-like interaction rate:
+collisions with uniform start times whose drift windows overlap.
+
+A short continuous timeframe is compared with the oracle in full.  The
+full-size one (55,000 time bins, ~2.7e9 digits, ~5.7 GB of ZS pages) runs
+through the CUDA path as the benchmark runs it; the oracle checks its first
+sector element by element (every stage of the method stays inside a sector, so
+sector 0 of the whole timeframe equals sector 0 reconstructed alone) and
+properties that hold at any size check the rest."""
+import numpy as np
+import pytest
+
+import oracle
+import tpcgen
+from parity import compare_fit, compare_integer
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2208_07412_b300 import tpc
+    tpc.load()
+    return tpc
+
+
+def test_short_continuous_parity(lib):
+    """2000 bins (~20 overlapping collisions), 2 sectors: full parity."""
+    tf = tpcgen.generate(tpcgen.continuous_tf(2, n_time_bins=2000, n_sectors=2))
+    orc = oracle.reconstruct(tf)
+    with lib.Reconstructor.for_timeframe(tf) as R:
+        gpu = R.run(tf)
+    compare_integer(gpu, orc)
+    compare_fit(gpu, orc)
+    assert gpu["counters"]["error_word"] == 0
+
+
+def head_of(gpu: dict, n_cl: int, n_tr: int) -> dict:
+    return {"clusters": gpu["clusters"][:n_cl], "up": gpu["up"][:n_cl], "down": gpu["down"][:n_cl],
+            "chain_of": gpu["chain_of"][:n_cl], "cl2trk": gpu["cl2trk"][:n_cl],
+            "tracks": gpu["tracks"][:n_tr], "counters": gpu["counters"]}
+
+
+def check_properties(gpu: dict, tf) -> None:
+    cl, tr, m = gpu["clusters"], gpu["tracks"], gpu["cl2trk"]
+    assert gpu["counters"]["error_word"] == 0
+    # canonical cluster order: (sector, row, t_peak, pad_peak) strictly ascending
+    key = (cl["sector"].astype(np.int64) << 40) | (cl["row"].astype(np.int64) << 32) | \
+          (cl["t_peak"].astype(np.int64) << 8) | cl["pad_peak"].astype(np.int64)
+    assert np.all(np.diff(key) > 0)
+    assert int(cl["sector"].max()) < tf.n_sectors and int(cl["t_peak"].max()) < tf.n_time_bins
+    # links stay within the neighbouring rows of the same sector and are mutual on chains
+    up, down = gpu["up"], gpu["down"]
+    has_up = np.nonzero(up >= 0)[0]
+    assert np.all(cl["row"][up[has_up]] == cl["row"][has_up] + 1)
+    assert np.all(cl["sector"][up[has_up]] == cl["sector"][has_up])
+    # tracks: ordered by (sector, lowest cluster), membership agrees with the map
+    assert np.all(np.diff(tr["sector"].astype(np.int64) * (1 << 32) + tr["first_cluster"]) > 0)
+    on = m >= 0
+    assert np.array_equal(np.bincount(m[on], minlength=len(tr)), tr["n_clusters"])
+    assert np.all(m[tr["first_cluster"]] == np.arange(len(tr)))
+    assert np.all(tr["ndf"][tr["flags"] == 0] > 0)
+    assert np.all(np.isfinite(tr["par"]))
+
+
+def test_continuous_50khz_full_size(lib):
+    tf = tpcgen.generate(tpcgen.continuous_tf(1))
+    assert tf.n_time_bins == 55000 and tf.pages.nbytes > 3 << 30
+    with lib.Reconstructor.for_timeframe(tf, mem_budget=200 << 30) as R:
+        gpu = R.run(tf)
+    check_properties(gpu, tf)
+    n_cl, n_tr = len(gpu["clusters"]), len(gpu["tracks"])
+    assert n_cl > 5e7 and n_tr > 2e5, (n_cl, n_tr)
+    # sector 0 element by element against the oracle
+    sub = tpcgen.sector_prefix(tf, 1)
+    orc = oracle.reconstruct(sub)
+    n0 = len(orc.clusters)
+    t0 = len(orc.track_first)
+    assert np.all(gpu["clusters"]["sector"][:n0] == 0) and (n0 == n_cl or gpu["clusters"]["sector"][n0] == 1)
+    assert np.all(gpu["tracks"]["sector"][:t0] == 0) and (t0 == n_tr or gpu["tracks"]["sector"][t0] == 1)
+    head = head_of(gpu, n0, t0)
+    compare_integer(head, orc)
+    rep = compare_fit(head, orc)
+    print("continuous 50 kHz, sector 0 fit precision vs FP64 oracle:", rep)

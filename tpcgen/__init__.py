@@ -217,7 +217,9 @@ def generate(cfg: GenConfig) -> Timeframe:
         tracks = np.empty(int(r.n_tracks), dtype=TRACK_DTYPE)
         if tracks.size:
             ctypes.memmove(tracks.ctypes.data, r.tracks, tracks.nbytes)
-        hits = np.empty(int(r.n_hits), dtype=HIT_DTYPE)
+        # per-hit truth only where digit labels are asked for (a continuous
+        # timeframe has ~1.4e8 hits)
+        hits = np.empty(int(r.n_hits) if cfg.want_labels else 0, dtype=HIT_DTYPE)
         if hits.size:
             ctypes.memmove(hits.ctypes.data, r.hits, hits.nbytes)
         return Timeframe(pages=pages, page_offsets=offs, n_time_bins=cfg.n_time_bins,
@@ -261,6 +263,20 @@ def batch_multiplicities(seed: int, n_events: int = 64, lo: int = 200, hi: int =
     return np.floor(np.exp(rng.uniform(math.log(lo), math.log(hi), size=n_events))).astype(int)
 
 
+def pp_tf(seed: int = 1, n_time_bins: int = 55000, rate_per_bin: float = 0.2, mean_tracks: float = 30.0,
+          **kw) -> GenConfig:
+    """pp-like continuous timeframe: 1 MHz interaction rate (0.2 collisions per
+    200 ns time bin, Poisson), multiplicity per collision Poisson(mean_tracks)."""
+    rng = np.random.default_rng(seed + 0x99)
+    n = rng.poisson(rate_per_bin * n_time_bins)
+    t0 = np.sort(rng.uniform(0.0, n_time_bins, size=n))
+    m = rng.poisson(mean_tracks, size=n).astype(int)
+    d = dict(seed=seed, n_sectors=36, n_time_bins=n_time_bins, coll_t0=list(t0),
+             coll_ntracks=list(m), looper_frac=0.05, want_labels=False, name="pp_tf")
+    d.update(kw)
+    return GenConfig(**d)
+
+
 def continuous_tf(seed: int = 1, n_time_bins: int = 55000, rate_per_bin: float = 0.01,
                   **kw) -> GenConfig:
     """50 kHz continuous timeframe: Poisson(rate * bins) collisions with uniform
@@ -273,3 +289,19 @@ def continuous_tf(seed: int = 1, n_time_bins: int = 55000, rate_per_bin: float =
              coll_ntracks=list(m), looper_frac=0.05, want_labels=False, name="continuous_tf")
     d.update(kw)
     return GenConfig(**d)
+
+
+def sector_prefix(tf: Timeframe, n_sectors: int) -> Timeframe:
+    """The first n_sectors sectors of a timeframe as a timeframe of their own.
+    Pages are laid out window by window with the sector outermost, so these
+    sectors' pages are a prefix of the page array and keep their offsets."""
+    import copy
+    n_sectors = min(n_sectors, tf.n_sectors)
+    s = copy.copy(tf)
+    nwin = n_sectors * tf.n_rows * tf.n_fragments
+    s.page_offsets = tf.page_offsets[:nwin].copy()
+    end = int(tf.page_offsets[nwin]) if nwin < len(tf.page_offsets) else len(tf.pages)
+    s.pages = tf.pages[:end]
+    s.n_sectors = n_sectors
+    s.digit_labels = None
+    return s
