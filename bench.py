@@ -202,7 +202,7 @@ def pct(v, q):
     return float(np.percentile(np.asarray(v, dtype=np.float64), q)) if len(v) else None
 
 
-def batched_vs_plain(tpc, torch, local, n_events=64, seed=1000, reps=3):
+def batched_vs_plain(tpc, torch, local, n_events=64, seed=1000, reps=3, tuning=None):
     """Uneven events on the full geometry (multiplicity log-uniform in
     [200, 20000], 1000 time bins each), device-resident: the whole set as ONE
     batched pipeline run, against one plain run per event (one slot, events in
@@ -232,6 +232,8 @@ def batched_vs_plain(tpc, torch, local, n_events=64, seed=1000, reps=3):
 
     # one batched run
     with tpc.Reconstructor.for_timeframe(tfs[0], device=local, mem_budget=budget) as R:
+        if tuning:
+            tpc.tpc_set_tuning(R.ctx, **tuning)
         def batch():
             t, keep = tpc.tpc_submit_batch(R.ctx, dev, T)
             R.wait(t)
@@ -243,6 +245,8 @@ def batched_vs_plain(tpc, torch, local, n_events=64, seed=1000, reps=3):
 
     # plain: one event after the other on one slot
     with tpc.Reconstructor.for_timeframe(tfs[0], device=local, mem_budget=budget) as R:
+        if tuning:
+            tpc.tpc_set_tuning(R.ctx, **tuning)
         def plain():
             lat, ncl = [], 0
             for p, o in dev:
@@ -257,6 +261,8 @@ def batched_vs_plain(tpc, torch, local, n_events=64, seed=1000, reps=3):
 
     # served: all submitted at once to 4 slots; each release admits the next
     with tpc.Reconstructor.for_timeframe(tfs[0], device=local, mem_budget=budget, n_slots=4) as R:
+        if tuning:
+            tpc.tpc_set_tuning(R.ctx, **tuning)
         def served():
             t0 = time.perf_counter()
             tickets = [R.submit(p, o, T) for p, o in dev]
@@ -395,6 +401,10 @@ def run_ours(args, world, rank, local):
     pages_d = torch.from_numpy(tf.pages).to("cuda")
     offs_d = torch.from_numpy(tf.page_offsets.view(np.int64)).to("cuda")
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+    # launch configuration: the autotuner's pick on this workload (untimed setup)
+    tuning = (tpc.tpc_get_tuning(R.ctx) if args.no_autotune
+              else tpc.tpc_autotune(R.ctx, pages_d, offs_d, tf.n_time_bins, reps=3))
 
     def dev_step():
         flush.fill_(1)  # evict the pages from L2 before the timed region of the step
@@ -477,6 +487,7 @@ def run_ours(args, world, rank, local):
             "config": {"workload": desc, "seed": args.seed, "zs_bytes": int(tf.pages.nbytes),
                        "digits": int(tf.n_digits), "clusters_per_tf": n_cl, "tracks_per_tf": n_tr,
                        "l2": "flushed before every step (256 MB write)", "parallelism": f"replicas x{world}",
+                       "tuning": {"autotuned": not args.no_autotune, **tuning},
                        "path": ("plain per-timeframe kernel launches" if args.no_graphs
                                 else "per-timeframe pipeline replayed from a captured CUDA graph")},
             "tracks_per_s": tr_all / dev_s_max,
@@ -493,7 +504,7 @@ def run_ours(args, world, rank, local):
             "gpu_launches": int(launches),
         }
         if world == 1 and not args.no_batched and args.workload == "full_tpc":
-            line["batched"] = batched_vs_plain(tpc, torch, local)
+            line["batched"] = batched_vs_plain(tpc, torch, local, tuning=tuning)
         if world == 1 and not args.no_cpu_baseline:
             cb = cpu_baseline(tf, 1)
             line["cpu_baseline"] = {"value": cb["clusters"] / cb["times"][0], "unit": "clusters/s", "cores": 1,
@@ -516,6 +527,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graphs", action="store_true", help="enqueue every kernel instead of graph replay")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain comparison")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default launch configuration")
     args = ap.parse_args()
     world, rank, local = dist_setup(args.gpus)
     try:

@@ -371,6 +371,36 @@ tpc_status tpc_get_counters(tpc_context* ctx, uint64_t ticket, uint64_t* out, in
  * that now fit.  A queued ticket is cancelled.  Unknown ticket: TPC_E_NOTFOUND. */
 tpc_status tpc_release(tpc_context* ctx, uint64_t ticket);
 
+/* Launch configuration of the pipeline's kernels (per context).  Every choice
+ * gives the same results, bit for bit; only the speed differs.  Defaults:
+ * 384, 2, 8, 8, 64, 32. */
+typedef struct {
+  int32_t find_threads;        /* 256 | 384 | 512 threads per persistent finder CTA */
+  int32_t find_ctas_per_sm;    /* 1 | 2 finder CTAs per SM */
+  int32_t ca_blocks_per_sm;    /* 4 | 8 | 16 CA-neighbour blocks per SM */
+  int32_t elem_blocks_per_sm;  /* 4 | 8 | 16 blocks per SM of the grid-stride CA / merge kernels */
+  int32_t fit_threads;         /* 32 | 64 | 128 tracks per fit block */
+  int32_t fit_blocks_per_sm;   /* 16 | 32 | 64 fit blocks per SM (grid cap) */
+} tpc_tuning;
+
+/* The context's current launch configuration. */
+tpc_status tpc_get_tuning(tpc_context* ctx, tpc_tuning* out);
+
+/* Set the launch configuration (e.g. one saved from an earlier tpc_autotune)
+ * for the following submits.  TPC_E_INVAL if a value is outside its set. */
+tpc_status tpc_set_tuning(tpc_context* ctx, const tpc_tuning* t);
+
+/* Autotuner: run the sample timeframe (host or device input, as for
+ * tpc_submit_timeframe) reps times under each of 9 joint candidate
+ * configurations, time every stage with CUDA events, and keep per stage the
+ * fastest choice (finder: threads x CTAs per SM; CA and merge: grid sizes; fit:
+ * block and grid size); the result is set on the context and copied to *out
+ * (may be NULL).  The paper describes no tuner; this picks launch parameters
+ * per context and workload on the GPU at hand.  Needs an idle context (no ticket
+ * in flight or queued, else TPC_E_BUSY); blocks until done; errors of a
+ * sample run are returned (the configuration is then left unchanged). */
+tpc_status tpc_autotune(tpc_context* ctx, const tpc_timeframe_desc* sample, int reps, tpc_tuning* out);
+
 /* Allocation-free cluster finder (steps 1-4 only).  The paper has no
  * counterpart to this entry point; it exists for callers that cannot allocate
  * device memory: code that runs inside a device-memory budget owned by another

@@ -348,10 +348,10 @@ static inline unsigned grid_for(unsigned long long cap, int n_sm, int per_sm) {
   return (unsigned)(g ? g : 1);
 }
 
-cudaError_t launch_ca(const DevGeom& G, const DevParams& P, const DevWork& W, int n_sm, cudaStream_t st,
-                      int* launches) {
-  const unsigned g = grid_for(W.cap_cl, n_sm, 8);
-  k_ca_neighbours<<<(unsigned)min(G.n_sectors * G.n_rows, n_sm * 8), kCaThreads, 0, st>>>(G, P, W);
+cudaError_t launch_ca(const DevGeom& G, const DevParams& P, const DevWork& W, int n_sm, const LaunchCfg& L,
+                      cudaStream_t st, int* launches) {
+  const unsigned g = grid_for(W.cap_cl, n_sm, L.elem_blocks_per_sm);
+  k_ca_neighbours<<<(unsigned)min(G.n_sectors * G.n_rows, n_sm * L.ca_blocks_per_sm), kCaThreads, 0, st>>>(G, P, W);
   k_ca_edge_min<<<g, 256, 0, st>>>(G, W);
   k_ca_edge_apply<<<g, 256, 0, st>>>(G, W);
   k_links<<<g, 256, 0, st>>>(W);

@@ -28,7 +28,7 @@
 
 namespace tpc {
 
-constexpr int kFindThreads = 384;
+constexpr int kFindThreads = 384;   // default block size (the allocation-free entry point's)
 
 struct PageHdr {
   uint32_t len;
@@ -60,7 +60,9 @@ __device__ __forceinline__ bool parse_header(const uint4* p, uint64_t off, uint6
 }
 
 constexpr int kStage = 256;                  // clusters staged in shared memory before the look-back
-constexpr int kOwnStage = 2 * kStage * 16;   // bytes; the page is staged in the same buffer first
+// The own page is staged in [st_rec | st_xyz | plist | ppre], contiguous and
+// unused until the decode is over: 2 * kStage * 16 + kStage * 2 bytes plus
+// the rank prefix (own_stage_bytes).
 constexpr int kHaloStage = 2048;             // bytes per neighbouring page's halo ranges
 constexpr int kHaloRunOff = 16, kHaloAdcOff = 800;
 constexpr int kList = 4096;                  // digits listed by the decoder (beyond: bitmap walk)
@@ -78,10 +80,9 @@ struct FindSmem {
   uint8_t* halo;       // [2][kHaloStage] halo ranges of the previous / next page
   uint4* hdr;          // [4] headers of the previous (0,1) and next (2,3) page
   unsigned long long* offs;  // [4] page offsets of windows w-1 .. w+2
-  uint8_t* ent_t;      // [256]
-  int32_t* ent_rs;     // [257]
   unsigned long long* scan;  // [34]
   int32_t* misc;       // [16]
+  PageHdr* ph;         // [3] parsed headers: own, previous, next page
 };
 
 // R(a, b) = floor((2a + b) / (2b)), b > 0
@@ -119,6 +120,19 @@ struct Seg {
   bool strict;                    // the window's own page: ordering and exact counts
 };
 
+// Occupancy bits of pads [ps, ps + len) of plane row tt.
+__device__ __forceinline__ void set_occ(const FindSmem& S, int nw, int tt, int ps, int len) {
+  int p = ps;
+  const int pe = ps + len;
+  while (p < pe) {
+    const int wi = p >> 5, b0 = p & 31;
+    const int n = min(32 - b0, pe - p);
+    const uint32_t m = (n == 32) ? 0xffffffffu : (((1u << n) - 1u) << b0);
+    atomicOr(&S.occ[tt * nw + wi], m);
+    p += n;
+  }
+}
+
 __device__ __forceinline__ void put_run(const Seg& g, const FindSmem& S, int ps_stride, int nw, int tt, int ps,
                                         int len, int di) {
   uint16_t* prow = S.plane + tt * ps_stride + kPad + ps;
@@ -135,27 +149,51 @@ __device__ __forceinline__ void put_run(const Seg& g, const FindSmem& S, int ps_
     sh += 10;
     if (sh == 30 && k + 1 < len) { sh = 0; word = g.adc[++wd]; }
   }
-  int p = ps;
-  const int pe = ps + len;
-  while (p < pe) {
-    const int wi = p >> 5, b0 = p & 31;
-    const int n = min(32 - b0, pe - p);
-    const uint32_t m = (n == 32) ? 0xffffffffu : (((1u << n) - 1u) << b0);
-    atomicOr(&S.occ[tt * nw + wi], m);
-    p += n;
-  }
+  set_occ(S, nw, tt, ps, len);
 }
 
-// Block-wide decode of a segment into plane rows tt = t_in + tt_base, one
+// Exclusive block scan of 32-bit counts with one barrier: every warp scans the
+// (at most 16) warp totals itself.  sm holds 16 words; two scans with no barrier
+// between them must use different sm.
+__device__ __forceinline__ uint32_t block_excl_scan32(uint32_t v, uint32_t* sm, uint32_t* total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  uint32_t inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t n = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += n;
+  }
+  if (lane == 31) sm[wid] = inc;
+  __syncthreads();
+  const uint32_t wv = lane < nw ? sm[lane] : 0u;
+  uint32_t wi = wv;
+#pragma unroll
+  for (int o = 1; o < 16; o <<= 1) {
+    const uint32_t n = __shfl_up_sync(0xffffffffu, wi, o);
+    if (lane >= o) wi += n;
+  }
+  const uint32_t before = __shfl_sync(0xffffffffu, wi - wv, wid);
+  *total = __shfl_sync(0xffffffffu, wi, nw - 1);
+  return before + inc - v;
+}
+
+__device__ bool decode_seg_warp(const Seg& g, int np, int ps_stride, int nw, int T, const FindSmem& S);
+
+// Block-wide decode of the own page into plane rows tt = t_in + tt_base, one
 // thread per time-bin entry (a page has at most 256): a block scan of the run
 // counts gives each entry its first run, a second of the digit counts its first
-// digit, and the thread then writes its own runs.  All reads are bounds-checked
-// against the segment's counts and all writes against the plane.  Returns true
-// (block-uniform) if every check passed.
-__device__ bool decode_seg(const Seg& g, int np, int ps_stride, int nw, int T, const FindSmem& S) {
+// digit.  When the digits are listed, each entry thread then only writes the
+// plane index of its digits into the list, and the block writes the ADC values
+// digit-parallel (an entry can hold ten times the mean number of digits);
+// otherwise each entry thread writes its digits.  The halo segments (hprev,
+// hnext; may be null) are decoded meanwhile by the last two warps.  All reads
+// are bounds-checked against the segment's counts and all writes against the
+// plane.  Returns true (block-uniform) if valid (own_ok and every check passed).
+__device__ bool decode_seg(const Seg& g, bool own_ok, int np, int ps_stride, int nw, int T, const FindSmem& S,
+                           const Seg* hprev, const Seg* hnext) {
   const int tid = threadIdx.x;
-  const int ne = g.ne;
-  bool bad = ne < 0 || ne > kFrag || ne > (int)blockDim.x;
+  const int ne = own_ok ? g.ne : 0;
+  bool bad = !own_ok || ne < 0 || ne > kFrag || ne > (int)blockDim.x;
   const bool mine = !bad && tid < ne;
   int t_in = 0, nr = 0, tt = 0;
   if (mine) {
@@ -166,10 +204,10 @@ __device__ bool decode_seg(const Seg& g, int np, int ps_stride, int nw, int T, c
     if (nr < 1 || tt < 0 || tt >= kWinT || g.t_base_abs + t_in >= T) { bad = true; nr = 0; }
     if (g.strict && tid > 0 && (int)(g.ent[tid - 1] & 0xff) >= t_in) bad = true;
   }
-  unsigned long long tot;
-  const int r0 = (int)block_excl_scan((unsigned long long)nr, S.scan, &tot);
+  uint32_t tot;
+  const int r0 = (int)block_excl_scan32((uint32_t)nr, reinterpret_cast<uint32_t*>(S.scan), &tot);
   const int nrun = (int)tot;
-  if (nrun > g.nrun || (g.strict && nrun != g.nrun)) bad = true;
+  if (own_ok && (nrun > g.nrun || (g.strict && nrun != g.nrun))) bad = true;
   // digits of this entry's runs, with the run checks
   int nd = 0;
   if (mine && r0 + nr <= g.nrun) {
@@ -185,18 +223,38 @@ __device__ bool decode_seg(const Seg& g, int np, int ps_stride, int nw, int T, c
   } else if (mine) {
     bad = true;
   }
-  const long long d0 = (long long)block_excl_scan((unsigned long long)nd, S.scan, &tot);
-  if ((long long)tot > g.ndig || (g.strict && (long long)tot != g.ndig)) bad = true;
+  const long long d0 = (long long)block_excl_scan32((uint32_t)nd, reinterpret_cast<uint32_t*>(S.scan) + 20, &tot);
+  if (own_ok && ((long long)tot > g.ndig || (g.strict && (long long)tot != g.ndig))) bad = true;
+  const bool list_fill = g.lbase == 0 && g.dfirst == 0 && g.ndig <= kList;
   if (mine && nd > 0 && d0 + nd <= g.ndig) {
     int di = (int)d0;
     for (int k = 0; k < nr; k++) {
       const uint32_t rv = g.run[r0 + k];
       const int ps = rv & 0xff, len = rv >> 8;
-      put_run(g, S, ps_stride, nw, tt, ps, len, di);
+      if (list_fill) {
+        const uint16_t L0 = (uint16_t)(tt * ps_stride + kPad + ps);
+        for (int q = 0; q < len; q++) S.list[di + q] = (uint16_t)(L0 + q);
+        set_occ(S, nw, tt, ps, len);
+      } else {
+        put_run(g, S, ps_stride, nw, tt, ps, len, di);
+      }
       di += len;
     }
   }
-  return !__syncthreads_or(bad);
+  const int wid = tid >> 5, nwarp = (int)(blockDim.x >> 5);
+  if (hprev && wid == nwarp - 2) decode_seg_warp(*hprev, np, ps_stride, nw, T, S);
+  if (hnext && wid == nwarp - 1) decode_seg_warp(*hnext, np, ps_stride, nw, T, S);
+  const bool valid = !__syncthreads_or(bad);
+  if (valid && list_fill) {
+    // every own digit d has its plane index in list[d]: write the ADC values
+    const int nplane = kWinT * ps_stride;
+    for (uint32_t d = tid; d < (uint32_t)g.ndig; d += blockDim.x) {
+      const int L = S.list[d];
+      const uint32_t word = g.adc[d / 3u];
+      if (L < nplane) S.plane[L] = (uint16_t)((word >> (10u * (d % 3u))) & 1023u);
+    }
+  }
+  return valid;
 }
 
 // Warp-level decode of a small segment (the 3-bin halos): the same checks, no
@@ -236,11 +294,21 @@ __device__ bool decode_seg_warp(const Seg& g, int np, int ps_stride, int nw, int
   return !bad;
 }
 
+// Window w -> (fragment, row, physical sector) packed f | r << 16 | s << 24,
+// computed by one thread and shared (integer divisions by runtime values are
+// not worth repeating in every thread).
+__device__ __forceinline__ int window_frs(const DevGeom& G, unsigned int w) {
+  const int f = (int)(w % (unsigned)G.n_frag);
+  const int sr = (int)(w / (unsigned)G.n_frag);
+  const int r = sr % G.n_rows, s = (sr / G.n_rows) % G.n_phys;
+  return f | (r << 16) | (s << 24);
+}
+
 // Copy the byte range [a, b) of a page (2-byte aligned, both in bounds) to dst
-// as 16-bit words.
-__device__ __forceinline__ void copy_u16(uint16_t* dst, const uint8_t* pg, uint32_t a, uint32_t b) {
+// as 16-bit words, by one warp.
+__device__ __forceinline__ void copy_u16_warp(uint16_t* dst, const uint8_t* pg, uint32_t a, uint32_t b) {
   const uint16_t* src = reinterpret_cast<const uint16_t*>(pg + a);
-  for (uint32_t i = threadIdx.x; i < (b - a) / 2; i += blockDim.x) dst[i] = __ldg(src + i);
+  for (uint32_t i = threadIdx.x & 31; i < (b - a) / 2; i += 32) dst[i] = __ldg(src + i);
 }
 
 // Peak test of the digit at plane index L (row tt, pad p): neighbours with a
@@ -332,8 +400,8 @@ __device__ __forceinline__ void make_cluster(const FindSmem& S, int ps_stride, i
 // another.  Otherwise (the allocation-free entry point, which has no scratch
 // buffer for records): a decoupled look-back over the windows gives each its
 // canonical offset and the records are written in place; only the records.
-template <bool kScratch>
-__global__ void __launch_bounds__(kFindThreads, 2)
+template <bool kScratch, int kThreads>
+__global__ void __launch_bounds__(kThreads, 2)
 k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int ps_stride = G.npmax + 2 * kPad, nw = G.nw;
@@ -355,6 +423,11 @@ k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
     o += kStage * 16;
     S.st_xyz = reinterpret_cast<int4*>(smem_raw + o);
     o += kStage * 16;
+    S.plist = reinterpret_cast<uint16_t*>(smem_raw + o);
+    o += kStage * 2;
+    S.ppre = reinterpret_cast<uint16_t*>(smem_raw + o);
+    o += ((size_t)nown_words + 1) * 2;
+    o = (o + 15) & ~(size_t)15;
     S.halo = smem_raw + o;
     o += 2 * kHaloStage;
     S.hdr = reinterpret_cast<uint4*>(smem_raw + o);
@@ -363,21 +436,18 @@ k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
     o += 4 * 8;
     S.scan = reinterpret_cast<unsigned long long*>(smem_raw + o);
     o += 34 * 8;
-    S.ent_rs = reinterpret_cast<int32_t*>(smem_raw + o);
-    o += 260 * 4;
     S.misc = reinterpret_cast<int32_t*>(smem_raw + o);
     o += 16 * 4;
+    S.ph = reinterpret_cast<PageHdr*>(smem_raw + o);
+    o += 3 * sizeof(PageHdr);
+    o = (o + 15) & ~(size_t)15;
     S.list = reinterpret_cast<uint16_t*>(smem_raw + o);
     o += kList * 2;
-    S.plist = reinterpret_cast<uint16_t*>(smem_raw + o);
-    o += kStage * 2;
-    S.ppre = reinterpret_cast<uint16_t*>(smem_raw + o);
-    o += ((size_t)nown_words + 1) * 2;
-    S.ent_t = reinterpret_cast<uint8_t*>(smem_raw + o);
   }
   const int tid = threadIdx.x;
   const int opt = (nown_words + blockDim.x - 1) / blockDim.x;
   uint8_t* own_stage = reinterpret_cast<uint8_t*>(S.st_rec);
+  const uint32_t own_stage_bytes = (uint32_t)(((size_t)2 * kStage * 16 + kStage * 2 + ((size_t)nown_words + 1) * 2) & ~(size_t)15);
 
   if (kScratch && blockIdx.x == 0 && tid == 0) W.ctr[CTR_NWIN] = n_windows;
   // the plane starts empty and is kept empty between windows
@@ -392,6 +462,7 @@ k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
   if (kScratch && tid == 0) {
     const unsigned w0 = atomicAdd(&W.tickets[TK_FIND], 1u);
     S.misc[1] = (int)w0;
+    S.misc[2] = w0 < n_windows ? window_frs(G, w0) : 0;
     for (int k = 0; k < 4; k++) {
       const long long j = (long long)w0 - 1 + k;
       S.offs[k] = (j >= 0 && j < (long long)n_windows && w0 < n_windows) ? W.page_offsets[j] : ~0ull;
@@ -401,7 +472,11 @@ k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
   unsigned long long noffs[4] = {~0ull, ~0ull, ~0ull, ~0ull};
   while (true) {
     // ---- 0. window w
-    if (!kScratch && tid == 0) S.misc[1] = (int)atomicAdd(&W.tickets[TK_FIND], 1u);
+    if (!kScratch && tid == 0) {
+      const unsigned wt = atomicAdd(&W.tickets[TK_FIND], 1u);
+      S.misc[1] = (int)wt;
+      S.misc[2] = wt < n_windows ? window_frs(G, wt) : 0;
+    }
     __syncthreads();
     const unsigned int w = (unsigned int)S.misc[1];
     if (w >= n_windows) break;
@@ -418,9 +493,8 @@ k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
       for (int i = (nwords & ~3) + tid; i < nwords; i += blockDim.x) S.occ[i] = 0u;
     }
     __syncthreads();
-    const int f = (int)(w % G.n_frag);
-    const int sr = (int)(w / G.n_frag);
-    const int r = sr % G.n_rows, s = (sr / G.n_rows) % G.n_phys;   // physical sector
+    const int frs = S.misc[2];
+    const int f = frs & 0xffff, r = (frs >> 16) & 0xff, s = (frs >> 24) & 0xff;   // s: physical sector
     const int np = G.npads[r];
     const int T = G.n_time_bins;
     const uint64_t off = S.offs[1];
@@ -430,7 +504,7 @@ k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
     uint32_t copied = 0;
     if (off <= W.pages_bytes && W.pages_bytes - off >= 32 && (off & 15) == 0) {
       uint64_t guess = (S.offs[2] != ~0ull && S.offs[2] > off) ? S.offs[2] - off : W.pages_bytes - off;
-      guess = min(guess, (uint64_t)kOwnStage);
+      guess = min(guess, (uint64_t)own_stage_bytes);
       guess = min(guess, W.pages_bytes - off);
       copied = (uint32_t)(guess & ~15ull);
       const uint4* src = reinterpret_cast<const uint4*>(W.pages + off);
@@ -444,62 +518,96 @@ k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
     }
     __syncthreads();
 
-    // ---- 2. own header; neighbours' halo byte ranges in a second round trip
-    PageHdr h, hp, hn;
-    const uint8_t* own = copied >= 32 ? own_stage : W.pages + off;
-    bool ok = parse_header(reinterpret_cast<const uint4*>(own), off, W.pages_bytes, h) && h.sector == s &&
-              h.row == r && h.frag == f;
-    if (ok && h.len > copied) own = W.pages + off;   // page larger than the stage: decode from global
-    const bool okp = f > 0 && parse_header(S.hdr, S.offs[0], W.pages_bytes, hp) &&
-                     2 * (hp.n_tb - hp.hi_tb) <= kHaloRunOff && 2 * (hp.n_runs - hp.hi_runs) <= kHaloAdcOff - kHaloRunOff &&
-                     4 * ((hp.n_dig + 2) / 3 - hp.hi_dig / 3) <= kHaloStage - kHaloAdcOff;
-    const bool okn = f + 1 < G.n_frag && parse_header(S.hdr + 2, S.offs[2], W.pages_bytes, hn) &&
-                     2 * hn.lo_tb <= kHaloRunOff && 2 * hn.lo_runs <= kHaloAdcOff - kHaloRunOff &&
-                     4 * ((hn.lo_dig + 2) / 3) <= kHaloStage - kHaloAdcOff;
-    uint8_t* hprev = S.halo;
-    uint8_t* hnext = S.halo + kHaloStage;
-    if (okp) {
-      const uint8_t* pg = W.pages + S.offs[0];
-      copy_u16(reinterpret_cast<uint16_t*>(hprev), pg, 32 + 2 * hp.hi_tb, 32 + 2 * hp.n_tb);
-      copy_u16(reinterpret_cast<uint16_t*>(hprev + kHaloRunOff), pg, 32 + 2 * hp.n_tb + 2 * hp.hi_runs,
-               32 + 2 * hp.n_tb + 2 * hp.n_runs);
-      copy_u16(reinterpret_cast<uint16_t*>(hprev + kHaloAdcOff), pg, hp.body + 4 * (hp.hi_dig / 3),
-               hp.body + 4 * ((hp.n_dig + 2) / 3));
-    }
-    if (okn) {
-      const uint8_t* pg = W.pages + S.offs[2];
-      copy_u16(reinterpret_cast<uint16_t*>(hnext), pg, 32, 32 + 2 * hn.lo_tb);
-      copy_u16(reinterpret_cast<uint16_t*>(hnext + kHaloRunOff), pg, 32 + 2 * hn.n_tb, 32 + 2 * hn.n_tb + 2 * hn.lo_runs);
-      copy_u16(reinterpret_cast<uint16_t*>(hnext + kHaloAdcOff), pg, hn.body, hn.body + 4 * ((hn.lo_dig + 2) / 3));
+    // ---- 2. the three headers and the neighbours' halo byte ranges: warps 0-2
+    // copy the previous page's entries / runs / ADC words of its last 3 bins,
+    // warps 3-5 the next page's of its first 3 bins, each warp parsing the
+    // header it needs (one round trip, all six copies in flight); warp 6 parses
+    // the own header
+    const bool own_global = copied < 32;
+    {
+      const int wid = tid >> 5, lane = tid & 31;
+      if (wid < 6) {
+        const int nb = wid < 3 ? 0 : 1;   // 0: previous page, 1: next page
+        PageHdr hh;
+        uint32_t a = 0, b = 0;
+        int okk = 0;
+        if (lane == 0) {
+          const bool want = nb == 0 ? f > 0 : f + 1 < G.n_frag;
+          okk = want && parse_header(S.hdr + 2 * nb, S.offs[2 * nb], W.pages_bytes, hh);
+          if (nb == 0)
+            okk = okk && 2 * (hh.n_tb - hh.hi_tb) <= kHaloRunOff &&
+                  2 * (hh.n_runs - hh.hi_runs) <= kHaloAdcOff - kHaloRunOff &&
+                  4 * ((hh.n_dig + 2) / 3 - hh.hi_dig / 3) <= kHaloStage - kHaloAdcOff;
+          else
+            okk = okk && 2 * hh.lo_tb <= kHaloRunOff && 2 * hh.lo_runs <= kHaloAdcOff - kHaloRunOff &&
+                  4 * ((hh.lo_dig + 2) / 3) <= kHaloStage - kHaloAdcOff;
+          if (okk) {
+            const int part = wid % 3;
+            if (nb == 0) {
+              if (part == 0) { a = 32 + 2 * hh.hi_tb; b = 32 + 2 * hh.n_tb; }
+              else if (part == 1) { a = 32 + 2 * hh.n_tb + 2 * hh.hi_runs; b = 32 + 2 * hh.n_tb + 2 * hh.n_runs; }
+              else { a = hh.body + 4 * (hh.hi_dig / 3); b = hh.body + 4 * ((hh.n_dig + 2) / 3); }
+            } else {
+              if (part == 0) { a = 32; b = 32 + 2 * hh.lo_tb; }
+              else if (part == 1) { a = 32 + 2 * hh.n_tb; b = 32 + 2 * hh.n_tb + 2 * hh.lo_runs; }
+              else { a = hh.body; b = hh.body + 4 * ((hh.lo_dig + 2) / 3); }
+            }
+          }
+          if (wid == 0 || wid == 3) {
+            S.ph[1 + nb] = hh;
+            S.misc[5 + nb] = okk;
+          }
+        }
+        okk = __shfl_sync(0xffffffffu, okk, 0);
+        a = __shfl_sync(0xffffffffu, a, 0);
+        b = __shfl_sync(0xffffffffu, b, 0);
+        if (okk) {
+          const int part = wid % 3;
+          const int doff = part == 0 ? 0 : (part == 1 ? kHaloRunOff : kHaloAdcOff);
+          copy_u16_warp(reinterpret_cast<uint16_t*>(S.halo + nb * kHaloStage + doff),
+                        W.pages + S.offs[2 * nb], a, b);
+        }
+      } else if (wid == 6 && lane == 0) {
+        PageHdr hh;
+        const bool okk = parse_header(reinterpret_cast<const uint4*>(own_global ? W.pages + off : own_stage), off,
+                                      W.pages_bytes, hh) &&
+                         hh.sector == s && hh.row == r && hh.frag == f;
+        S.ph[0] = hh;
+        S.misc[4] = okk;
+      }
     }
     __syncthreads();
+    bool ok = S.misc[4];
+    const bool okp = S.misc[5], okn = S.misc[6];
+    const PageHdr& h = S.ph[0];
+    const PageHdr& hp = S.ph[1];
+    const PageHdr& hn = S.ph[2];
+    const uint8_t* own = (own_global || h.len > copied) ? W.pages + off : own_stage;
+    uint8_t* hprev = S.halo;
+    uint8_t* hnext = S.halo + kHaloStage;
 
-    // ---- 3. decode the two halos (warps 0 and 1) and the own page (block);
-    // digits listed as own | previous halo | next halo
+    // ---- 3. decode the own page (block) and the two halos (the last two warps,
+    // while the others write the own digits); digits listed as own | previous
+    // halo | next halo
     const int n_own = ok ? h.n_dig : 0;
     const int n_prev = okp ? hp.n_dig - hp.hi_dig : 0;
     const int n_next = okn ? hn.lo_dig : 0;
     const int ndig = n_own + n_prev + n_next;
     const bool listed = use_list && ndig <= kList;
-    if (okp && (tid >> 5) == 0) {
-      Seg g{reinterpret_cast<const uint16_t*>(hprev), hp.n_tb - hp.hi_tb,
-            reinterpret_cast<const uint16_t*>(hprev + kHaloRunOff), hp.n_runs - hp.hi_runs,
-            reinterpret_cast<const uint32_t*>(hprev + kHaloAdcOff), hp.hi_dig % 3, n_prev,
-            kHalo - kFrag, kFrag * (f - 1), listed ? n_own : kList, false};
-      decode_seg_warp(g, np, ps_stride, nw, T, S);
-    }
-    if (okn && (tid >> 5) == 1) {
-      Seg g{reinterpret_cast<const uint16_t*>(hnext), hn.lo_tb,
-            reinterpret_cast<const uint16_t*>(hnext + kHaloRunOff), hn.lo_runs,
-            reinterpret_cast<const uint32_t*>(hnext + kHaloAdcOff), 0, n_next, kHalo + kFrag, kFrag * (f + 1),
-            listed ? n_own + n_prev : kList, false};
-      decode_seg_warp(g, np, ps_stride, nw, T, S);
-    }
-    if (ok) {
-      Seg g{reinterpret_cast<const uint16_t*>(own + 32), h.n_tb,
-            reinterpret_cast<const uint16_t*>(own + 32 + 2 * h.n_tb), h.n_runs,
-            reinterpret_cast<const uint32_t*>(own + h.body), 0, h.n_dig, kHalo, kFrag * f, listed ? 0 : kList, true};
-      ok = decode_seg(g, np, ps_stride, nw, T, S);
+    {
+      const Seg gp{reinterpret_cast<const uint16_t*>(hprev), hp.n_tb - hp.hi_tb,
+                   reinterpret_cast<const uint16_t*>(hprev + kHaloRunOff), hp.n_runs - hp.hi_runs,
+                   reinterpret_cast<const uint32_t*>(hprev + kHaloAdcOff), hp.hi_dig % 3, n_prev,
+                   kHalo - kFrag, kFrag * (f - 1), listed ? n_own : kList, false};
+      const Seg gn{reinterpret_cast<const uint16_t*>(hnext), hn.lo_tb,
+                   reinterpret_cast<const uint16_t*>(hnext + kHaloRunOff), hn.lo_runs,
+                   reinterpret_cast<const uint32_t*>(hnext + kHaloAdcOff), 0, n_next, kHalo + kFrag, kFrag * (f + 1),
+                   listed ? n_own + n_prev : kList, false};
+      const Seg go{reinterpret_cast<const uint16_t*>(own + 32), h.n_tb,
+                   reinterpret_cast<const uint16_t*>(own + 32 + 2 * h.n_tb), h.n_runs,
+                   reinterpret_cast<const uint32_t*>(own + h.body), 0, h.n_dig, kHalo, kFrag * f,
+                   listed ? 0 : kList, true};
+      ok = decode_seg(go, ok, np, ps_stride, nw, T, S, okp ? &gp : nullptr, okn ? &gn : nullptr);
     }
     if (!ok && tid == 0) atomicOr(W.err, kErrCorrupt);
     __syncthreads();
@@ -563,8 +671,8 @@ k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
       const int w0 = tid * opt, w1 = min(w0 + opt, nown_words);
       int c = 0;
       for (int i = w0; i < w1; i++) c += __popc(S.pk[kHalo * nw + i]);
-      unsigned long long tot;
-      const unsigned long long pre = block_excl_scan((unsigned long long)c, S.scan, &tot);
+      uint32_t tot;
+      const uint32_t pre = block_excl_scan32((uint32_t)c, reinterpret_cast<uint32_t*>(S.scan), &tot);
       int run = (int)pre;
       for (int i = w0; i < w1; i++) {
         uint32_t word = S.pk[kHalo * nw + i];
@@ -644,6 +752,7 @@ k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
 
     if (kScratch && tid == 0) {
       S.misc[1] = (int)nt;
+      S.misc[2] = nt < n_windows ? window_frs(G, nt) : 0;
       for (int k = 0; k < 4; k++) S.offs[k] = noffs[k];
     }
 
@@ -702,9 +811,9 @@ size_t find_smem_bytes(int npmax, int nw) {
   size_t o = ((size_t)kWinT * (npmax + 2 * kPad) * 2 + 15) & ~(size_t)15;
   o += 2 * (size_t)kWinT * nw * 4;
   o = (o + 15) & ~(size_t)15;
-  o += 2 * kStage * 16 + 2 * kHaloStage + 4 * 16 + 4 * 8 + 34 * 8 + 260 * 4 + 16 * 4;
-  o += kList * 2 + kStage * 2 + ((size_t)kFrag * nw + 1) * 2;
-  o += 256;
+  o += 2 * kStage * 16 + 2 * kHaloStage + 4 * 16 + 4 * 8 + 34 * 8 + 16 * 4;
+  o += (3 * sizeof(PageHdr) + 15) & ~(size_t)15;
+  o += kList * 2 + kStage * 2 + ((size_t)kFrag * nw + 1) * 2 + 16;
   return o;
 }
 
@@ -715,15 +824,27 @@ cudaError_t launch_scan(uint64_t* v, const unsigned long long* n_ptr, unsigned l
 // Raise the finder's dynamic shared-memory limit on the current device (once
 // per context, outside any stream capture).
 cudaError_t prepare_find() {
-  return cudaFuncSetAttribute(k_find_clusters<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  cudaError_t e = cudaFuncSetAttribute(k_find_clusters<true, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_find_clusters<true, 384>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_find_clusters<true, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  return e;
 }
 
 cudaError_t launch_find(const DevGeom& G, const DevParams& P, const DevWork& W, unsigned int n_windows,
-                        int n_sm, cudaStream_t st, unsigned long long* win_scan_state, int* launches) {
+                        int n_sm, const LaunchCfg& L, cudaStream_t st, unsigned long long* win_scan_state,
+                        int* launches) {
   const size_t sm = find_smem_bytes(G.npmax, G.nw);
-  unsigned int grid = (unsigned int)min((long long)n_windows, (long long)n_sm * 2);
+  // persistent CTAs: find_ctas_per_sm per SM (at most 2 fit the shared memory)
+  unsigned int grid = (unsigned int)min((long long)n_windows, (long long)n_sm * L.find_ctas_per_sm);
   if (grid == 0) grid = 1;
-  k_find_clusters<true><<<grid, kFindThreads, sm, st>>>(G, P, W, n_windows);
+  if (L.find_threads == 256)
+    k_find_clusters<true, 256><<<grid, 256, sm, st>>>(G, P, W, n_windows);
+  else if (L.find_threads == 512)
+    k_find_clusters<true, 512><<<grid, 512, sm, st>>>(G, P, W, n_windows);
+  else
+    k_find_clusters<true, 384><<<grid, 384, sm, st>>>(G, P, W, n_windows);
   cudaError_t e = launch_scan(reinterpret_cast<uint64_t*>(W.win_cnt), W.ctr + CTR_NWIN, n_windows, win_scan_state,
                               W.tickets + TK_SCAN_W, W.ctr + CTR_NCL, W.err, n_sm, st);
   if (e != cudaSuccess) return e;
@@ -791,7 +912,7 @@ extern "C" tpc_status tpc_find_clusters_noalloc(const tpc_geometry* geom, const 
       void* ptr = nullptr;
       if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr)
         return fail(TPC_E_CUDA, "tpc_find_clusters_noalloc: cudaGetSymbolAddress failed");
-      if (cudaFuncSetAttribute(k_find_clusters<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) !=
+      if (cudaFuncSetAttribute(k_find_clusters<false, kFindThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) !=
           cudaSuccess)
         return fail(TPC_E_CUDA, "tpc_find_clusters_noalloc: cudaFuncSetAttribute failed");
       g_noalloc_addr[device] = static_cast<unsigned long long*>(ptr);
@@ -830,7 +951,7 @@ extern "C" tpc_status tpc_find_clusters_noalloc(const tpc_geometry* geom, const 
   int n_sm = 148;
   cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, device);
   unsigned grid = (unsigned)std::min<unsigned long long>(nwin, (unsigned long long)n_sm * 2);
-  k_find_clusters<false><<<grid ? grid : 1, kFindThreads, smem, st>>>(G, P, W, (unsigned)nwin);
+  k_find_clusters<false, kFindThreads><<<grid ? grid : 1, kFindThreads, smem, st>>>(G, P, W, (unsigned)nwin);
   if (cudaGetLastError() != cudaSuccess) return fail(TPC_E_CUDA, "tpc_find_clusters_noalloc: launch failed");
   unsigned long long ctrl[CTR_COUNT + 1];
   if (cudaMemcpyAsync(ctrl, W.ctr, sizeof ctrl, cudaMemcpyDeviceToHost, st) != cudaSuccess ||

@@ -163,7 +163,8 @@ __device__ __forceinline__ bool ud_pd(const UD<T>& M) {
   return ok;
 }
 
-__global__ void __launch_bounds__(64)
+template <int kThreads>
+__global__ void __launch_bounds__(kThreads)
 k_fit(DevGeom G, DevParams P, DevWork W) {
   const unsigned long long ntrk = W.ctr[CTR_NTRK];
   const unsigned long long nmax = ntrk < W.cap_ch ? ntrk : W.cap_ch;
@@ -280,12 +281,19 @@ k_fit(DevGeom G, DevParams P, DevWork W) {
   if (fp64_count) atomicAdd(&W.ctr[CTR_NFP64], (unsigned long long)fp64_count);
 }
 
-cudaError_t launch_fit(const DevGeom& G, const DevParams& P, const DevWork& W, int n_sm, cudaStream_t st,
-                       int* launches) {
-  unsigned long long g = (W.cap_ch + 63) / 64;
-  unsigned long long m = (unsigned long long)n_sm * 32;
+cudaError_t launch_fit(const DevGeom& G, const DevParams& P, const DevWork& W, int n_sm, const LaunchCfg& L,
+                       cudaStream_t st, int* launches) {
+  const int nt = L.fit_threads;
+  unsigned long long g = (W.cap_ch + nt - 1) / nt;
+  unsigned long long m = (unsigned long long)n_sm * L.fit_blocks_per_sm;
   if (g > m) g = m;
-  k_fit<<<(unsigned)(g ? g : 1), 64, 0, st>>>(G, P, W);
+  const unsigned grid = (unsigned)(g ? g : 1);
+  if (nt == 32)
+    k_fit<32><<<grid, 32, 0, st>>>(G, P, W);
+  else if (nt == 128)
+    k_fit<128><<<grid, 128, 0, st>>>(G, P, W);
+  else
+    k_fit<64><<<grid, 64, 0, st>>>(G, P, W);
   *launches += 1;
   return cudaGetLastError();
 }

@@ -76,7 +76,7 @@ __global__ void k_merge_cand(DevGeom G, DevParams P, DevWork W) {
       // pass 0: every chain is both a group top and a group bottom
       atomicMin(&W.best_b[k], (sc << 32) | (unsigned)kb);
       atomicMin(&bestA[kb], (sc << 32) | (unsigned)k);
-      const unsigned long long slot = atomicAdd(&W.ctr[CTR_NCAND], 1ull);
+      const unsigned long long slot = aggregated_inc(&W.ctr[CTR_NCAND]);
       if (slot < W.cap_cand) {
         W.cand_ab[slot] = (k << 32) | (unsigned)kb;
         W.cand_sc[slot] = (uint32_t)sc;
@@ -123,7 +123,8 @@ __global__ void k_merge_link(DevWork W, int pass) {
       linked++;
     }
   }
-  if (linked) atomicAdd(&W.ctr[CTR_MERGED0 + pass], (unsigned long long)linked);
+  linked = __reduce_add_sync(0xffffffffu, linked);
+  if ((threadIdx.x & 31) == 0 && linked) atomicAdd(&W.ctr[CTR_MERGED0 + pass], (unsigned long long)linked);
 }
 
 // Group roots (chains with no lower neighbour) sum their group's clusters; a
@@ -161,7 +162,7 @@ __global__ void k_group_assign(DevParams P, DevWork W) {
       W.trk_first[t] = W.ch_root[k];
       W.trk_ncl[t] = W.grp_total[k];
       W.trk_off[t] = (int)(unsigned)v;
-      atomicAdd(&W.len_hist[255 - min(W.grp_total[k], 255)], 1u);
+      aggregated_inc_keyed(W.len_hist, 255 - min(W.grp_total[k], 255));
     }
     int g = (int)k, run = 0;
     for (int it = 0; g >= 0 && it < kMaxRowsDev; it++) {
@@ -210,7 +211,7 @@ __global__ void k_fit_order(DevWork W) {
   for (unsigned long long t = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; t < ntrk;
        t += (unsigned long long)gridDim.x * blockDim.x) {
     const int bin = 255 - min(W.trk_ncl[t], 255);
-    const unsigned rank = atomicAdd(&W.len_hist[256 + bin], 1u);
+    const unsigned rank = aggregated_inc_keyed(W.len_hist + 256, bin);
     W.fit_order[pre[bin] + rank] = (int)t;
   }
 }
@@ -226,15 +227,16 @@ cudaError_t launch_scan(uint64_t* v, const unsigned long long* n_ptr, unsigned l
                         unsigned long long* state, unsigned int* ticket, unsigned long long* total, uint32_t* err,
                         int n_sm, cudaStream_t st);
 
-cudaError_t launch_merge(const DevGeom& G, const DevParams& P, const DevWork& W, int n_sm, cudaStream_t st,
-                         unsigned long long* scan_state_b, int* launches) {
-  const unsigned gc = grid_for_m(W.cap_ch, n_sm, 8);
+cudaError_t launch_merge(const DevGeom& G, const DevParams& P, const DevWork& W, int n_sm, const LaunchCfg& L,
+                         cudaStream_t st, unsigned long long* scan_state_b, int* launches) {
+  const int per_sm = L.elem_blocks_per_sm;
+  const unsigned gc = grid_for_m(W.cap_ch, n_sm, per_sm);
   for (int p = 0; p < P.merge_passes; p++) {
     if (p == 0) {
       const int ngap = P.gap_max - P.gap_min + 1;
-      k_merge_cand<<<grid_for_m(W.cap_ch * ngap, n_sm, 8), 256, 0, st>>>(G, P, W);
+      k_merge_cand<<<grid_for_m(W.cap_ch * ngap, n_sm, per_sm), 256, 0, st>>>(G, P, W);
     } else {
-      k_merge_best<<<grid_for_m(W.cap_cand, n_sm, 8), 256, 0, st>>>(W, p);
+      k_merge_best<<<grid_for_m(W.cap_cand, n_sm, per_sm), 256, 0, st>>>(W, p);
     }
     k_merge_link<<<gc, 256, 0, st>>>(W, p);
   }
@@ -243,7 +245,7 @@ cudaError_t launch_merge(const DevGeom& G, const DevParams& P, const DevWork& W,
                               W.ctr + CTR_NCLCL, W.err, n_sm, st);
   if (e != cudaSuccess) return e;
   k_group_assign<<<gc, 256, 0, st>>>(P, W);
-  const unsigned g = grid_for_m(W.cap_cl, n_sm, 8);
+  const unsigned g = grid_for_m(W.cap_cl, n_sm, per_sm);
   k_cluster_assign<<<g, 256, 0, st>>>(W);
   k_fit_order<<<grid_for_m(W.cap_ch, n_sm, 4), 256, 0, st>>>(W);
   *launches += 2 * P.merge_passes + 5;

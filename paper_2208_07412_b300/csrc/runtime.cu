@@ -21,12 +21,12 @@
 
 namespace tpc {
 size_t find_smem_bytes(int npmax, int nw);
-cudaError_t launch_find(const DevGeom&, const DevParams&, const DevWork&, unsigned int, int, cudaStream_t,
-                        unsigned long long*, int*);
-cudaError_t launch_ca(const DevGeom&, const DevParams&, const DevWork&, int, cudaStream_t, int*);
-cudaError_t launch_merge(const DevGeom&, const DevParams&, const DevWork&, int, cudaStream_t,
+cudaError_t launch_find(const DevGeom&, const DevParams&, const DevWork&, unsigned int, int, const LaunchCfg&,
+                        cudaStream_t, unsigned long long*, int*);
+cudaError_t launch_ca(const DevGeom&, const DevParams&, const DevWork&, int, const LaunchCfg&, cudaStream_t, int*);
+cudaError_t launch_merge(const DevGeom&, const DevParams&, const DevWork&, int, const LaunchCfg&, cudaStream_t,
                          unsigned long long*, int*);
-cudaError_t launch_fit(const DevGeom&, const DevParams&, const DevWork&, int, cudaStream_t, int*);
+cudaError_t launch_fit(const DevGeom&, const DevParams&, const DevWork&, int, const LaunchCfg&, cudaStream_t, int*);
 size_t scan_tiles(unsigned long long cap);
 cudaError_t prepare_find();
 }  // namespace tpc
@@ -83,7 +83,7 @@ struct Slot {
   cudaGraphExec_t gexec = nullptr;
   bool graph_broken = false;
   DevWork gk_W{};        // the work-space wiring and input shape the graph was captured with
-  uint32_t gk_T = 0, gk_nwin = 0;
+  uint32_t gk_T = 0, gk_nwin = 0, gk_tune = 0;
   // timeframe
   const void* user_pages = nullptr;
   const uint64_t* user_offsets = nullptr;
@@ -107,6 +107,8 @@ struct tpc_context {
   tpc_params params;
   DevGeom G{};
   DevParams P{};
+  LaunchCfg L{};
+  uint32_t tune_gen = 0;    // bumped when L changes (captured graphs are re-made)
   int device = 0, n_sm = 148;
   uint64_t budget = 0, used = 0;
   uint32_t flags = 0;
@@ -436,13 +438,14 @@ static tpc_status enqueue_body(tpc_context* ctx, Slot& s, bool capturing) {
   const size_t tiles_a = scan_tiles(s.cap_cl), tiles_b = scan_tiles(s.cap_ch);
   CUDA_TRY(cudaMemsetAsync(W.scan_state, 0, (tiles_a + tiles_b + scan_tiles(s.n_windows)) * 8, st));
   if (timing) CUDA_TRY(cudaEventRecordWithFlags(s.ev_stage[0], st, evf));
-  CUDA_TRY(launch_find(G, ctx->P, W, s.n_windows, ctx->n_sm, st, W.scan_state + tiles_a + tiles_b, &s.launches));
+  const LaunchCfg& L = ctx->L;
+  CUDA_TRY(launch_find(G, ctx->P, W, s.n_windows, ctx->n_sm, L, st, W.scan_state + tiles_a + tiles_b, &s.launches));
   if (timing) CUDA_TRY(cudaEventRecordWithFlags(s.ev_stage[1], st, evf));
-  CUDA_TRY(launch_ca(G, ctx->P, W, ctx->n_sm, st, &s.launches));
+  CUDA_TRY(launch_ca(G, ctx->P, W, ctx->n_sm, L, st, &s.launches));
   if (timing) CUDA_TRY(cudaEventRecordWithFlags(s.ev_stage[2], st, evf));
-  CUDA_TRY(launch_merge(G, ctx->P, W, ctx->n_sm, st, (unsigned long long*)W.scan_state + tiles_a, &s.launches));
+  CUDA_TRY(launch_merge(G, ctx->P, W, ctx->n_sm, L, st, (unsigned long long*)W.scan_state + tiles_a, &s.launches));
   if (timing) CUDA_TRY(cudaEventRecordWithFlags(s.ev_stage[3], st, evf));
-  CUDA_TRY(launch_fit(G, ctx->P, W, ctx->n_sm, st, &s.launches));
+  CUDA_TRY(launch_fit(G, ctx->P, W, ctx->n_sm, L, st, &s.launches));
   if (timing) CUDA_TRY(cudaEventRecordWithFlags(s.ev_stage[4], st, evf));
   if (s.n_events > 1) {
     uint32_t* d_st = (uint32_t*)((uint64_t*)s.evinfo.p + 2 * kMaxBatch);
@@ -471,7 +474,7 @@ static tpc_status enqueue(tpc_context* ctx, Slot& s) {
     if (st == TPC_OK) s.runs++;
     return st;
   }
-  const bool same = s.gexec && s.gk_T == s.n_time_bins && s.gk_nwin == s.n_windows &&
+  const bool same = s.gexec && s.gk_T == s.n_time_bins && s.gk_nwin == s.n_windows && s.gk_tune == ctx->tune_gen &&
                     std::memcmp(&s.gk_W, &s.W, sizeof(DevWork)) == 0;
   if (!same) {
     // capture the pipeline; a graph of the same topology (new input pointers,
@@ -501,6 +504,7 @@ static tpc_status enqueue(tpc_context* ctx, Slot& s) {
       return st;
     }
     s.gk_W = s.W;
+    s.gk_tune = ctx->tune_gen;
     s.gk_T = s.n_time_bins;
     s.gk_nwin = s.n_windows;
   }
@@ -1026,6 +1030,136 @@ extern "C" tpc_status tpc_release(tpc_context* ctx, uint64_t ticket) {
   s->in_use = false;
   s->state = TPC_STATE_QUEUED;
   admit(ctx);   // the freed slot and memory go to the oldest queued request
+  return TPC_OK;
+}
+
+// ------------------------------------------------------------------ tuning
+static const int kFindThreadsC[] = {256, 384, 512};
+static const int kFindCtasC[] = {1, 2};
+static const int kPerSmC[] = {4, 8, 16};
+static const int kFitThreadsC[] = {32, 64, 128};
+static const int kFitBlocksC[] = {16, 32, 64};
+
+template <size_t N>
+static bool one_of(int v, const int (&set)[N]) {
+  for (int x : set)
+    if (x == v) return true;
+  return false;
+}
+
+static void to_public(const LaunchCfg& L, tpc_tuning* t) {
+  t->find_threads = L.find_threads;
+  t->find_ctas_per_sm = L.find_ctas_per_sm;
+  t->ca_blocks_per_sm = L.ca_blocks_per_sm;
+  t->elem_blocks_per_sm = L.elem_blocks_per_sm;
+  t->fit_threads = L.fit_threads;
+  t->fit_blocks_per_sm = L.fit_blocks_per_sm;
+}
+
+extern "C" tpc_status tpc_get_tuning(tpc_context* ctx, tpc_tuning* out) {
+  if (!ctx || !out) return fail(TPC_E_INVAL, "tpc_get_tuning: null argument");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  to_public(ctx->L, out);
+  return TPC_OK;
+}
+
+extern "C" tpc_status tpc_set_tuning(tpc_context* ctx, const tpc_tuning* t) {
+  if (!ctx || !t) return fail(TPC_E_INVAL, "tpc_set_tuning: null argument");
+  if (!one_of(t->find_threads, kFindThreadsC) || !one_of(t->find_ctas_per_sm, kFindCtasC) ||
+      !one_of(t->ca_blocks_per_sm, kPerSmC) || !one_of(t->elem_blocks_per_sm, kPerSmC) ||
+      !one_of(t->fit_threads, kFitThreadsC) || !one_of(t->fit_blocks_per_sm, kFitBlocksC))
+    return fail(TPC_E_INVAL, "tpc_set_tuning: a value outside its candidate set");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  LaunchCfg L;
+  L.find_threads = t->find_threads;
+  L.find_ctas_per_sm = t->find_ctas_per_sm;
+  L.ca_blocks_per_sm = t->ca_blocks_per_sm;
+  L.elem_blocks_per_sm = t->elem_blocks_per_sm;
+  L.fit_threads = t->fit_threads;
+  L.fit_blocks_per_sm = t->fit_blocks_per_sm;
+  ctx->L = L;
+  ctx->tune_gen++;
+  return TPC_OK;
+}
+
+// Run one timeframe synchronously on slot s (lock held, slot free) with the
+// current launch configuration; stage times in ms[4].
+static tpc_status run_sync(tpc_context* ctx, Slot& s, const tpc_timeframe_desc* tf, float* ms) {
+  tpc_status st = start_timeframe(ctx, &s, tf);
+  if (st) return st;
+  while (true) {
+    CUDA_TRY(cudaEventSynchronize(s.ev_done));
+    st = finish(ctx, s);
+    if (st != TPC_E_NOTREADY) break;   // TPC_E_NOTREADY: regrown and re-enqueued
+  }
+  s.state = TPC_STATE_QUEUED;
+  if (st) return st;
+  for (int i = 0; i < TPC_N_STAGES; i++) CUDA_TRY(cudaEventElapsedTime(&ms[i], s.ev_stage[i], s.ev_stage[i + 1]));
+  return TPC_OK;
+}
+
+extern "C" tpc_status tpc_autotune(tpc_context* ctx, const tpc_timeframe_desc* sample, int reps, tpc_tuning* out) {
+  if (!ctx || !sample) return fail(TPC_E_INVAL, "tpc_autotune: null argument");
+  if (reps < 1 || reps > 100) return fail(TPC_E_INVAL, "tpc_autotune: reps out of range");
+  tpc_status st = check_desc(sample);
+  if (st) return st;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  if (any_in_use(ctx) || !ctx->pending.empty()) return fail(TPC_E_BUSY, "tpc_autotune needs an idle context");
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  Slot& s = ctx->slots[0];
+  const uint32_t flags0 = ctx->flags;
+  const LaunchCfg L0 = ctx->L;
+  ctx->flags = (flags0 | TPC_CTX_STAGE_TIMING | TPC_CTX_NO_GRAPHS);
+  // joint trials: trial i uses finder choice i % 6, CA/merge choice i % 9 and
+  // fit choice i % 9; a stage's time depends only on its own kernels' choice
+  const int n_find = 6, n_mid = 9, n_fit = 9, n_trials = 9;
+  std::vector<float> t_find(n_find, 1e30f), t_mid(n_mid, 1e30f), t_fit(n_fit, 1e30f);
+  float ms[TPC_N_STAGES];
+  st = run_sync(ctx, s, sample, ms);   // warm-up, grows the slot to the sample
+  for (int i = 0; i < n_trials && st == TPC_OK; i++) {
+    const int fi = i % n_find, mi = i % n_mid, ti = i % n_fit;
+    LaunchCfg L;
+    L.find_threads = kFindThreadsC[fi % 3];
+    L.find_ctas_per_sm = kFindCtasC[fi / 3];
+    L.ca_blocks_per_sm = kPerSmC[mi % 3];
+    L.elem_blocks_per_sm = kPerSmC[mi / 3];
+    L.fit_threads = kFitThreadsC[ti % 3];
+    L.fit_blocks_per_sm = kFitBlocksC[ti / 3];
+    ctx->L = L;
+    std::vector<float> a, b, c;
+    for (int r = 0; r < reps && st == TPC_OK; r++) {
+      st = run_sync(ctx, s, sample, ms);
+      a.push_back(ms[0]);
+      b.push_back(ms[1] + ms[2]);
+      c.push_back(ms[3]);
+    }
+    if (st) break;
+    auto med = [](std::vector<float>& v) {
+      std::sort(v.begin(), v.end());
+      return v[v.size() / 2];
+    };
+    t_find[fi] = std::min(t_find[fi], med(a));
+    t_mid[mi] = std::min(t_mid[mi], med(b));
+    t_fit[ti] = std::min(t_fit[ti], med(c));
+  }
+  ctx->flags = flags0;
+  if (st) {
+    ctx->L = L0;
+    return st;
+  }
+  const int fi = (int)(std::min_element(t_find.begin(), t_find.end()) - t_find.begin());
+  const int mi = (int)(std::min_element(t_mid.begin(), t_mid.end()) - t_mid.begin());
+  const int ti = (int)(std::min_element(t_fit.begin(), t_fit.end()) - t_fit.begin());
+  LaunchCfg L;
+  L.find_threads = kFindThreadsC[fi % 3];
+  L.find_ctas_per_sm = kFindCtasC[fi / 3];
+  L.ca_blocks_per_sm = kPerSmC[mi % 3];
+  L.elem_blocks_per_sm = kPerSmC[mi / 3];
+  L.fit_threads = kFitThreadsC[ti % 3];
+  L.fit_blocks_per_sm = kFitBlocksC[ti / 3];
+  ctx->L = L;
+  ctx->tune_gen++;
+  if (out) to_public(L, out);
   return TPC_OK;
 }
 

@@ -49,6 +49,18 @@ struct DevGeom {
   int xrow[kMaxRowsDev];         // X of each row in u (= 64 * row_x)
 };
 
+// Launch configuration of the pipeline's kernels.  Every choice computes the
+// same results (all kernels are deterministic in their outputs); the
+// autotuner picks the fastest per stage on a sample timeframe.
+struct LaunchCfg {
+  int find_threads = 384;        // 256 | 384 | 512 threads per finder CTA
+  int find_ctas_per_sm = 2;      // 1 | 2 persistent finder CTAs per SM
+  int ca_blocks_per_sm = 8;      // 4 | 8 | 16: CA neighbour blocks (one (sector, row) each at a time)
+  int elem_blocks_per_sm = 8;    // 4 | 8 | 16: grid-stride kernels of the CA and merge stages
+  int fit_threads = 64;          // 32 | 64 | 128 threads (tracks) per fit block
+  int fit_blocks_per_sm = 32;    // 16 | 32 | 64: fit grid cap
+};
+
 struct DevParams {
   int q_peak_min;
   int sy_num, sy_den, sz_num, sz_den;
@@ -230,6 +242,32 @@ __device__ __forceinline__ unsigned long long lookback_wait(unsigned long long* 
   }
   if (lane == 0) st_release_u64(&state[tile], kStFlagPre | (excl + aggregate));
   return excl;
+}
+
+// Warp-aggregated atomicAdd of 1 on one counter: the lanes that call it
+// together take consecutive values with a single atomic (correct under
+// independent thread scheduling: the group is whoever is converged here).
+__device__ __forceinline__ unsigned long long aggregated_inc(unsigned long long* ctr) {
+  const unsigned mask = __activemask();
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(mask) - 1;
+  unsigned long long base = 0;
+  if (lane == leader) base = atomicAdd(ctr, (unsigned long long)__popc(mask));
+  base = __shfl_sync(mask, base, leader);
+  return base + __popc(mask & ((1u << lane) - 1u));
+}
+
+// Warp-aggregated atomicAdd of 1 on counters indexed by key: lanes with equal
+// keys share one atomic and take consecutive values.
+__device__ __forceinline__ unsigned aggregated_inc_keyed(unsigned* base_ptr, int key) {
+  const unsigned mask = __activemask();
+  const unsigned peers = __match_any_sync(mask, key);
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(peers) - 1;
+  unsigned base = 0;
+  if (lane == leader) base = atomicAdd(base_ptr + key, (unsigned)__popc(peers));
+  base = __shfl_sync(peers, base, leader);
+  return base + __popc(peers & ((1u << lane) - 1u));
 }
 
 // Event of cluster c in a batch: the last e with row_start[e * n_phys * R] <= c.

@@ -62,6 +62,15 @@ class tpc_params(ctypes.Structure):
                 ("c0", ctypes.c_double * 5)]
 
 
+class tpc_tuning(ctypes.Structure):
+    _fields_ = [("find_threads", ctypes.c_int32), ("find_ctas_per_sm", ctypes.c_int32),
+                ("ca_blocks_per_sm", ctypes.c_int32), ("elem_blocks_per_sm", ctypes.c_int32),
+                ("fit_threads", ctypes.c_int32), ("fit_blocks_per_sm", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
 class tpc_timeframe_desc(ctypes.Structure):
     _fields_ = [("pages", _P), ("pages_bytes", _u64), ("page_offsets", _P),
                 ("n_time_bins", ctypes.c_uint32), ("flags", ctypes.c_uint32)]
@@ -71,7 +80,8 @@ EXPORTS = ("tpc_params_default", "tpc_create_geometry", "tpc_destroy_geometry", 
            "tpc_destroy_context", "tpc_submit_timeframe", "tpc_poll", "tpc_get_clusters",
            "tpc_get_tracks", "tpc_get_links", "tpc_get_device_results", "tpc_get_stage_times",
            "tpc_get_counters", "tpc_release", "tpc_last_error", "tpc_find_clusters_noalloc",
-           "tpc_submit_batch", "tpc_get_batch_info", "tpc_get_event_clusters", "tpc_get_event_tracks")
+           "tpc_submit_batch", "tpc_get_batch_info", "tpc_get_event_clusters", "tpc_get_event_tracks",
+           "tpc_get_tuning", "tpc_set_tuning", "tpc_autotune")
 
 _lib = None
 
@@ -115,6 +125,9 @@ def load(build_if_missing: bool = True):
     L.tpc_get_batch_info.argtypes = [_P, _u64, ctypes.POINTER(ctypes.c_uint32), _P, _P]
     L.tpc_get_event_clusters.argtypes = [_P, _u64, ctypes.c_uint32, _P, _u64, ctypes.POINTER(_u64)]
     L.tpc_get_event_tracks.argtypes = [_P, _u64, ctypes.c_uint32, _P, _u64, ctypes.POINTER(_u64), _P]
+    L.tpc_get_tuning.argtypes = [_P, ctypes.POINTER(tpc_tuning)]
+    L.tpc_set_tuning.argtypes = [_P, ctypes.POINTER(tpc_tuning)]
+    L.tpc_autotune.argtypes = [_P, ctypes.POINTER(tpc_timeframe_desc), ctypes.c_int, ctypes.POINTER(tpc_tuning)]
     L.tpc_last_error.argtypes = []
     L.tpc_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -240,6 +253,29 @@ def tpc_get_event_tracks(ctx, ticket: int, event: int, n_clusters: int):
     _check(L.tpc_get_event_tracks(ctx, ticket, event, out.ctypes.data if n.value else None, n.value,
                                   ctypes.byref(n), m.ctypes.data if n_clusters else None))
     return out, m
+
+
+def tpc_get_tuning(ctx) -> dict:
+    t = tpc_tuning()
+    _check(load().tpc_get_tuning(ctx, ctypes.byref(t)))
+    return t.as_dict()
+
+
+def tpc_set_tuning(ctx, **kw) -> None:
+    """Set launch-configuration fields (the others keep their current values)."""
+    t = tpc_tuning()
+    _check(load().tpc_get_tuning(ctx, ctypes.byref(t)))
+    for k, v in kw.items():
+        setattr(t, k, int(v))
+    _check(load().tpc_set_tuning(ctx, ctypes.byref(t)))
+
+
+def tpc_autotune(ctx, pages, page_offsets, n_time_bins: int, reps: int = 3) -> dict:
+    """Tune the context's launch configuration on a sample timeframe; returns it."""
+    d, _keep = _desc(pages, page_offsets, n_time_bins)
+    t = tpc_tuning()
+    _check(load().tpc_autotune(ctx, ctypes.byref(d), int(reps), ctypes.byref(t)))
+    return t.as_dict()
 
 
 def tpc_poll(ctx, ticket: int, timeout_us: int = 0xFFFFFFFF) -> int:
