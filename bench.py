@@ -40,7 +40,7 @@ WORKLOADS = {
                  "(5% loopers) from one vertex, Bz 0.5 T, Landau(60) Gaussian clouds, noise 1 ADC, ZS >= 3"),
     "single_sector": (lambda seed: tpcgen.single_sector(seed),
                       "single_sector: 1 sector x 152 rows, 500 time bins, 150 tracks"),
-    "continuous_50khz": (lambda seed: tpcgen.continuous_tf(seed),
+    "continuous_50khz": (lambda seed, bins=55000: tpcgen.continuous_tf(seed, n_time_bins=bins),
                          "continuous_50khz: 36 sectors x 152 rows, 55,000 time bins (11 ms at 5 MHz), "
                          "Poisson(550) Pb-Pb-like collisions at uniform start times, multiplicity "
                          "floor(15000 U^7.82) (mean ~1,700), 5% loopers, same charge/noise/ZS model"),
@@ -321,9 +321,11 @@ def run_serve(args, world, rank, local):
     import torch
     from paper_2208_07412_b300 import tpc
     torch.cuda.set_device(local)
-    bins = args.serve_bins
-    cfgs = [tpcgen.pp_tf(7 + i, n_time_bins=bins) for i in range(8)] + \
-           [tpcgen.continuous_tf(7 + i, n_time_bins=bins) for i in range(8)]
+    # timeframe lengths uniform in [serve_bins / 5.5, serve_bins] (2-11 ms scaled by serve_bins / 55,000)
+    rng_len = np.random.default_rng(77)
+    bins = [int(b) for b in rng_len.integers(args.serve_bins * 2 // 11, args.serve_bins + 1, size=16)]
+    cfgs = [tpcgen.pp_tf(7 + i, n_time_bins=bins[i]) for i in range(8)] + \
+           [tpcgen.continuous_tf(7 + i, n_time_bins=bins[8 + i]) for i in range(8)]
     pool = []
     for c in cfgs:
         tf = tpcgen.generate(c)
@@ -361,7 +363,7 @@ def run_serve(args, world, rank, local):
         "warmup": len(pool), "ms_per_step": 1e3 * span_s / n_req, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "i64+f32", "data": "synthetic",
         "config": {"workload": f"serve: pool of 8 pp-like (1 MHz, Poisson(30) tracks) + 8 Pb-Pb-like (50 kHz, "
-                               f"floor(15000 U^7.82)) continuous timeframes of {bins} time bins, "
+                               f"floor(15000 U^7.82)) continuous timeframes of {min(bins)}-{max(bins)} time bins, "
                                f"{sizes[0] / 1e9:.2f}-{sizes[-1] / 1e9:.2f} GB ZS each, {n_req} requests drawn "
                                f"from the pool, pinned host inputs",
                    "served": "4 slots, queued requests admitted as slots and memory free up",
@@ -385,7 +387,12 @@ def run_ours(args, world, rank, local):
     from paper_2208_07412_b300 import tpc
     torch.cuda.set_device(local)
     make, desc = WORKLOADS[args.workload]
-    tf = tpcgen.generate(make(args.seed + rank))
+    if args.workload == "continuous_50khz" and args.time_bins:
+        desc = desc.replace("55,000 time bins (11 ms at 5 MHz)", f"{args.time_bins} time bins") + \
+            ", Poisson(0.01 x bins) collisions"
+        tf = tpcgen.generate(make(args.seed + rank, args.time_bins))
+    else:
+        tf = tpcgen.generate(make(args.seed + rank))
     # a dedicated stream: the library runs slot 0 on it and the CUDA events
     # below are recorded on it (the legacy default stream has handle 0, which
     # the library would replace by a stream of its own)
@@ -403,8 +410,13 @@ def run_ours(args, world, rank, local):
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     torch.cuda.synchronize()
     # launch configuration: the autotuner's pick on this workload (untimed setup)
-    tuning = (tpc.tpc_get_tuning(R.ctx) if args.no_autotune
-              else tpc.tpc_autotune(R.ctx, pages_d, offs_d, tf.n_time_bins, reps=3))
+    if args.tuning:   # a fixed configuration, e.g. one the autotuner picked earlier
+        tpc.tpc_set_tuning(R.ctx, **{k: int(v) for k, v in (kv.split("=") for kv in args.tuning.split(","))})
+        tuning = tpc.tpc_get_tuning(R.ctx)
+    elif args.no_autotune:
+        tuning = tpc.tpc_get_tuning(R.ctx)
+    else:
+        tuning = tpc.tpc_autotune(R.ctx, pages_d, offs_d, tf.n_time_bins, reps=3)
 
     def dev_step():
         flush.fill_(1)  # evict the pages from L2 before the timed region of the step
@@ -487,7 +499,7 @@ def run_ours(args, world, rank, local):
             "config": {"workload": desc, "seed": args.seed, "zs_bytes": int(tf.pages.nbytes),
                        "digits": int(tf.n_digits), "clusters_per_tf": n_cl, "tracks_per_tf": n_tr,
                        "l2": "flushed before every step (256 MB write)", "parallelism": f"replicas x{world}",
-                       "tuning": {"autotuned": not args.no_autotune, **tuning},
+                       "tuning": {"autotuned": not (args.no_autotune or args.tuning), **tuning},
                        "path": ("plain per-timeframe kernel launches" if args.no_graphs
                                 else "per-timeframe pipeline replayed from a captured CUDA graph")},
             "tracks_per_s": tr_all / dev_s_max,
@@ -520,7 +532,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["serve"], default="full_tpc")
-    ap.add_argument("--serve-bins", type=int, default=5500, help="time bins per served timeframe (1.1 ms)")
+    ap.add_argument("--serve-bins", type=int, default=5500,
+                    help="longest served timeframe in time bins (1.1 ms; lengths uniform down to 2/11 of it)")
+    ap.add_argument("--time-bins", type=int, default=0, help="continuous_50khz: time bins (default 55,000)")
     ap.add_argument("--serve-load", type=float, nargs="*", default=[0.5, 0.8, 1.0, 1.3],
                     help="offered load as fractions of the plain path's saturation rate")
     ap.add_argument("--seed", type=int, default=1)
@@ -528,6 +542,7 @@ def main():
     ap.add_argument("--no-graphs", action="store_true", help="enqueue every kernel instead of graph replay")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain comparison")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch configuration")
+    ap.add_argument("--tuning", default="", help="fixed launch configuration, e.g. find_threads=384,fit_threads=32")
     args = ap.parse_args()
     world, rank, local = dist_setup(args.gpus)
     try:

@@ -20,14 +20,6 @@ __device__ __forceinline__ unsigned long long n_chains(const DevWork& W) {
   return n < W.cap_ch ? n : W.cap_ch;
 }
 
-// first index in [lo, hi) with t[i] >= v (t ascending within a row)
-__device__ __forceinline__ unsigned lower_bound_t(const int32_t* __restrict__ t, unsigned lo, unsigned hi, int v) {
-  while (lo < hi) {
-    unsigned mid = (lo + hi) >> 1;
-    if (__ldg(t + mid) < v) lo = mid + 1; else hi = mid;
-  }
-  return lo;
-}
 
 __device__ __forceinline__ long long llabs_(long long v) { return v < 0 ? -v : v; }
 
@@ -45,6 +37,33 @@ struct Slice {
   const int32_t* t; const int32_t* y; const int32_t* z;
   unsigned base, n;   // cluster index of element 0, element count
 };
+
+// First index in [lo, hi) with t[i] >= v (hi if none), by a whole warp: each
+// round the 32 lanes probe 32 evenly spaced elements and the range shrinks
+// 32-fold, so a row of 10^4-10^5 clusters takes 3-4 dependent loads instead of
+// 14-17.  Every lane returns the result.
+__device__ __forceinline__ unsigned warp_lower_bound(const int32_t* __restrict__ t, unsigned lo, unsigned hi, int v) {
+  const unsigned lane = threadIdx.x & 31;
+  while (hi - lo > 32) {
+    const unsigned step = (hi - lo + 31) / 32;
+    const unsigned idx = lo + lane * step;
+    const bool ge = idx >= hi || __ldg(t + idx) >= v;
+    const unsigned m = __ballot_sync(0xffffffffu, ge);
+    if (m == 0) {
+      lo = lo + 31 * step + 1;
+    } else {
+      const unsigned f = (unsigned)(__ffs(m) - 1);
+      if (f == 0) return lo;
+      const unsigned nlo = lo + (f - 1) * step + 1, nhi = min(lo + f * step, hi);
+      lo = nlo;
+      hi = nhi;
+    }
+  }
+  const unsigned idx = lo + lane;
+  const bool ge = idx >= hi || __ldg(t + idx) >= v;
+  const unsigned m = __ballot_sync(0xffffffffu, ge);
+  return m ? min(lo + (unsigned)(__ffs(m) - 1), hi) : hi;
+}
 
 __device__ __forceinline__ unsigned lb_slice(const int32_t* t, unsigned n, int v) {
   unsigned lo = 0, hi = n;
@@ -82,13 +101,15 @@ k_ca_neighbours(DevGeom G, DevParams P, DevWork W) {
     const unsigned ulo = min((unsigned long long)W.row_start[sr + 1], n), uhi = min((unsigned long long)W.row_start[sr + 2], n);
     for (unsigned cs = lo; cs < hi; cs += kCaChunk) {
       const unsigned ce = min(cs + kCaChunk, hi);
-      if (tid < 2) {
-        // slice of the neighbour row that can pair with clusters [cs, ce)
+      if (tid < 128) {
+        // slices of the neighbour rows that can pair with clusters [cs, ce):
+        // warp q computes bound q (row below: 0, 1; row above: 2, 3)
+        const int q = tid >> 5, side = q >> 1;
         const int tmin = W.cl_t[cs], tmax = W.cl_t[ce - 1];
-        const unsigned a = tid == 0 ? dlo : ulo, b = tid == 0 ? dhi : uhi;
-        const int w = tid == 0 ? wd : wu;
-        sm_rng[2 * tid] = lower_bound_t(W.cl_t, a, b, tmin - w);
-        sm_rng[2 * tid + 1] = lower_bound_t(W.cl_t, a, b, tmax + w + 1);
+        const unsigned a = side == 0 ? dlo : ulo, b = side == 0 ? dhi : uhi;
+        const int w = side == 0 ? wd : wu;
+        const unsigned bound = warp_lower_bound(W.cl_t, a, b, (q & 1) ? tmax + w + 1 : tmin - w);
+        if ((tid & 31) == 0) sm_rng[q] = bound;
       }
       __syncthreads();
       Slice sl[2];
@@ -276,6 +297,7 @@ __global__ void k_chain_table(DevParams P, DevWork W) {
       W.chain_of[c] = (int)root;
       if (pos == 0) {
         W.ch_root[k] = (int)c; W.ch_len[k] = L; W.ch_next[k] = -1; W.ch_prev[k] = -1;
+        W.ch_t[k] = W.cl_t[c];
         W.best_a[k] = ~0ull;
         W.best_b[k] = ~0ull;
       }
@@ -286,6 +308,33 @@ __global__ void k_chain_table(DevParams P, DevWork W) {
       W.cl_chain[c] = -1;
       W.chain_of[c] = -1;
     }
+  }
+}
+
+// Per (sector, row): the first chain whose root (bottom cluster) lies in it.
+// Chain ids follow their roots' canonical order, so the chains rooted in a row
+// are a contiguous id range, ordered by the root's time bin.
+__global__ void k_chain_rows(DevGeom G, DevWork W) {
+  const unsigned long long nch = min(W.ctr[CTR_NCH], (unsigned long long)W.cap_ch);
+  const int R = G.n_rows;
+  const long long nsr = (long long)G.n_sectors * R;
+  if (nch == 0) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i <= nsr; i += (long long)gridDim.x * blockDim.x)
+      W.ch_row_start[i] = 0;
+    return;
+  }
+  for (unsigned long long k = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; k < nch;
+       k += (unsigned long long)gridDim.x * blockDim.x) {
+    auto sr_of = [&](unsigned long long kk) {
+      const unsigned c = (unsigned)W.ch_root[kk];
+      const uint4 rec = __ldg(reinterpret_cast<const uint4*>(W.clusters) + c);
+      return (long long)vsector_of(G, W, c, (int)(rec.w >> 24)) * R + ((rec.z >> 24) & 0xff);
+    };
+    const long long sr = sr_of(k);
+    const long long prev = k > 0 ? sr_of(k - 1) : -1;
+    for (long long i = prev + 1; i <= sr && i <= nsr; i++) W.ch_row_start[i] = (uint32_t)k;
+    if (k == nch - 1)
+      for (long long i = sr + 1; i <= nsr; i++) W.ch_row_start[i] = (uint32_t)nch;
   }
 }
 
@@ -361,7 +410,8 @@ cudaError_t launch_ca(const DevGeom& G, const DevParams& P, const DevWork& W, in
   k_scan<<<gs, kScanThreads, 0, st>>>(W.scan_val, W.ctr + CTR_NCL, W.cap_cl, W.scan_state,
                                       W.tickets + TK_SCAN_A, W.ctr + CTR_NCH, W.err);
   k_chain_table<<<g, 256, 0, st>>>(P, W);
-  *launches += 8;
+  k_chain_rows<<<grid_for(W.cap_ch, n_sm, L.elem_blocks_per_sm), 256, 0, st>>>(G, W);
+  *launches += 9;
   return cudaGetLastError();
 }
 

@@ -67,11 +67,15 @@ constexpr int kHaloStage = 2048;             // bytes per neighbouring page's ha
 constexpr int kHaloRunOff = 16, kHaloAdcOff = 800;
 constexpr int kList = 4096;                  // digits listed by the decoder (beyond: bitmap walk)
 constexpr int kPad = 2;                      // empty pads on each side of a plane row
+constexpr int kMaxRuns = 2048;               // runs of a window decoded run-parallel (beyond: per entry)
+constexpr int kRunMapWords = kList / 32;     // run-start bitmap over the listed digits
 
 struct FindSmem {
   uint16_t* plane;     // [kWinT][ps], pixel (tt, p) at tt * ps + p + kPad; zero where no digit
   uint32_t* occ;       // [kWinT][nw] occupancy bitmap
   uint32_t* pk;        // [kWinT][nw] peak bitmap
+  uint32_t* dbm;       // [kRunMapWords] bit d set: listed digit d starts a run (follows pk)
+  uint8_t* run_t;      // [kMaxRuns] time bin (within its page) of each run of the window
   uint16_t* list;      // [kList] plane index of every decoded digit
   uint16_t* plist;     // [kStage] plane index of the first own peaks in canonical order
   uint16_t* ppre;      // own-peak rank prefix over the words of rows 3..258
@@ -177,7 +181,7 @@ __device__ __forceinline__ uint32_t block_excl_scan32(uint32_t v, uint32_t* sm, 
   return before + inc - v;
 }
 
-__device__ bool decode_seg_warp(const Seg& g, int np, int ps_stride, int nw, int T, const FindSmem& S);
+__device__ __forceinline__ bool decode_seg_warp(const Seg& g, int np, int ps_stride, int nw, int T, const FindSmem& S);
 
 // Block-wide decode of the own page into plane rows tt = t_in + tt_base, one
 // thread per time-bin entry (a page has at most 256): a block scan of the run
@@ -189,7 +193,7 @@ __device__ bool decode_seg_warp(const Seg& g, int np, int ps_stride, int nw, int
 // hnext; may be null) are decoded meanwhile by the last two warps.  All reads
 // are bounds-checked against the segment's counts and all writes against the
 // plane.  Returns true (block-uniform) if valid (own_ok and every check passed).
-__device__ bool decode_seg(const Seg& g, bool own_ok, int np, int ps_stride, int nw, int T, const FindSmem& S,
+__device__ __forceinline__ bool decode_seg(const Seg& g, bool own_ok, int np, int ps_stride, int nw, int T, const FindSmem& S,
                            const Seg* hprev, const Seg* hnext) {
   const int tid = threadIdx.x;
   const int ne = own_ok ? g.ne : 0;
@@ -259,7 +263,7 @@ __device__ bool decode_seg(const Seg& g, bool own_ok, int np, int ps_stride, int
 
 // Warp-level decode of a small segment (the 3-bin halos): the same checks, no
 // block barrier.  A violated bound stops it; the page's own window reports it.
-__device__ bool decode_seg_warp(const Seg& g, int np, int ps_stride, int nw, int T, const FindSmem& S) {
+__device__ __forceinline__ bool decode_seg_warp(const Seg& g, int np, int ps_stride, int nw, int T, const FindSmem& S) {
   const int lane = threadIdx.x & 31;
   bool bad = g.ne < 0 || g.ne > kFrag;
   int run0 = 0, dig0 = 0;   // runs / digits consumed by earlier entries
@@ -302,6 +306,134 @@ __device__ __forceinline__ int window_frs(const DevGeom& G, unsigned int w) {
   const int sr = (int)(w / (unsigned)G.n_frag);
   const int r = sr % G.n_rows, s = (sr / G.n_rows) % G.n_phys;
   return f | (r << 16) | (s << 24);
+}
+
+// Balanced decode of a whole window: the previous page's last 3 bins, the own
+// page and the next page's first 3 bins as one sequence of entries, runs and
+// digits (segments 0, 1, 2; listed in that order).  Three parallel phases, so
+// that no thread holds a whole time bin (an entry can hold ten times the mean
+// number of digits per thread):
+//   entries (two per thread at most): checks, run counts -> block scan -> run
+//     offsets; each entry tags its runs with its time bin;
+//   runs (a contiguous block per thread): checks, digit counts -> block scan ->
+//     digit offsets; each run lists the plane index of its first digit, marks
+//     the run start in a bitmap and sets its occupancy bits;
+//   digits (strided): the run start below the digit from the bitmap, the
+//     digit's plane index from it, its ADC value into the plane.
+// Every read is bounds-checked against the segment counts from the headers and
+// every write against the plane and the list.  Segment k may be empty.  Returns
+// true (block-uniform) if every check passed.
+struct WinSeg {
+  const uint16_t* ent; const uint16_t* run; const uint32_t* adc;
+  int ne, nrun, ndig, dfirst, tt_base, t_base_abs;
+};
+
+template <typename V>
+__device__ __forceinline__ V sel3(int k, V a, V b, V c) { return k == 0 ? a : (k == 1 ? b : c); }
+
+// (The three segments are separate by-value parameters: indexing an array of
+// them with a runtime segment number would place it in local memory.)
+__device__ __forceinline__ bool decode_window(const WinSeg s0, const WinSeg s1, const WinSeg s2, int np, int ps_stride,
+                                              int nw, int T, const FindSmem& S) {
+  const int tid = threadIdx.x, nt = (int)blockDim.x;
+  const int ebase1 = s0.ne, ebase2 = s0.ne + s1.ne, ne = ebase2 + s2.ne;
+  const int rbase1 = s0.nrun, rbase2 = s0.nrun + s1.nrun, nrun = rbase2 + s2.nrun;
+  const int dbase1 = s0.ndig, dbase2 = s0.ndig + s1.ndig, ndig = dbase2 + s2.ndig;
+  bool bad = ne > 2 * nt;
+  // ---- entries
+  int e_t[2] = {0, 0}, e_nr[2] = {0, 0}, my_nr = 0;
+#pragma unroll
+  for (int j = 0; j < 2; j++) {
+    const int e = 2 * tid + j;
+    if (e >= ne || bad) continue;
+    const int k = e < ebase1 ? 0 : (e < ebase2 ? 1 : 2);
+    const int el = e - (k == 0 ? 0 : (k == 1 ? ebase1 : ebase2));
+    const uint16_t* ent = sel3(k, s0.ent, s1.ent, s2.ent);
+    const uint32_t v = ent[el];
+    const int t_in = v & 0xff, nr = v >> 8, tt = t_in + sel3(k, s0.tt_base, s1.tt_base, s2.tt_base);
+    if (nr < 1 || tt < 0 || tt >= kWinT || sel3(k, s0.t_base_abs, s1.t_base_abs, s2.t_base_abs) + t_in >= T) {
+      bad = true;
+      continue;
+    }
+    if (el > 0 && (int)(ent[el - 1] & 0xff) >= t_in) bad = true;   // strictly increasing t
+    e_t[j] = t_in;
+    e_nr[j] = nr;
+    my_nr += nr;
+  }
+  uint32_t tot;
+  const int r_first = (int)block_excl_scan32((uint32_t)my_nr, reinterpret_cast<uint32_t*>(S.scan), &tot);
+  if ((int)tot != nrun) bad = true;
+  {
+    int r = r_first;
+#pragma unroll
+    for (int j = 0; j < 2; j++) {
+      const int e = 2 * tid + j;
+      if (e >= ne) continue;
+      // a segment's first entry must start at the segment's first run
+      if ((e == ebase1 && s1.ne > 0 && r != rbase1) || (e == ebase2 && s2.ne > 0 && r != rbase2)) bad = true;
+      for (int q = 0; q < e_nr[j]; q++)
+        if (r + q < kMaxRuns) S.run_t[r + q] = (uint8_t)e_t[j];
+      r += e_nr[j];
+    }
+  }
+  __syncthreads();
+  // ---- runs
+  const int per = (nrun + nt - 1) / nt;
+  const int ra = min(tid * per, nrun), rb = min(ra + per, nrun);
+  int my_nd = 0;
+  for (int r = ra; r < rb; r++) {
+    const int k = r < rbase1 ? 0 : (r < rbase2 ? 1 : 2);
+    const int rl = r - (k == 0 ? 0 : (k == 1 ? rbase1 : rbase2));
+    const uint16_t* run = sel3(k, s0.run, s1.run, s2.run);
+    const uint32_t rv = run[rl];
+    const int ps = rv & 0xff, len = rv >> 8;
+    if (len < 1 || ps + len > np) { bad = true; continue; }
+    if (rl > 0 && S.run_t[r - 1] == S.run_t[r]) {   // same time bin: ascending, disjoint
+      const uint32_t pv = run[rl - 1];
+      if (ps < (int)(pv & 0xff) + (int)(pv >> 8)) bad = true;
+    }
+    my_nd += len;
+  }
+  const int d_first = (int)block_excl_scan32((uint32_t)my_nd, reinterpret_cast<uint32_t*>(S.scan) + 20, &tot);
+  if ((int)tot != ndig) bad = true;
+  {
+    int d = d_first;
+    for (int r = ra; r < rb; r++) {
+      const int k = r < rbase1 ? 0 : (r < rbase2 ? 1 : 2);
+      const int rl = r - (k == 0 ? 0 : (k == 1 ? rbase1 : rbase2));
+      const uint32_t rv = sel3(k, s0.run, s1.run, s2.run)[rl];
+      const int ps = rv & 0xff, len = rv >> 8;
+      if (len < 1 || ps + len > np) continue;
+      // a segment's first run must start at the segment's first digit
+      if ((r == rbase1 && s1.nrun > 0 && d != dbase1) || (r == rbase2 && s2.nrun > 0 && d != dbase2)) bad = true;
+      const int tt = S.run_t[r] + sel3(k, s0.tt_base, s1.tt_base, s2.tt_base);   // stale if its entry failed: checked
+      if (d + len <= ndig && d + len <= kList && tt >= 0 && tt < kWinT) {
+        S.list[d] = (uint16_t)(tt * ps_stride + kPad + ps);
+        atomicOr(&S.dbm[d >> 5], 1u << (d & 31));
+        set_occ(S, nw, tt, ps, len);
+      } else {
+        bad = true;
+      }
+      d += len;
+    }
+  }
+  const bool valid = !__syncthreads_or(bad);
+  if (!valid) return false;
+  // ---- digits
+  const int nplane = kWinT * ps_stride;
+  for (int d = tid; d < ndig; d += nt) {
+    int w = d >> 5;
+    uint32_t m = S.dbm[w] & (0xffffffffu >> (31 - (d & 31)));
+    while (m == 0 && w > 0) m = S.dbm[--w];   // digit 0 always starts a run
+    const int st = 32 * w + 31 - __clz(m);
+    const int L = (int)S.list[st] + (d - st);
+    if (d != st) S.list[d] = (uint16_t)L;
+    const int k = d < dbase1 ? 0 : (d < dbase2 ? 1 : 2);
+    const int idx = sel3(k, s0.dfirst, s1.dfirst, s2.dfirst) + d - (k == 0 ? 0 : (k == 1 ? dbase1 : dbase2));
+    const uint32_t word = sel3(k, s0.adc, s1.adc, s2.adc)[idx / 3];
+    if (L < nplane) S.plane[L] = (uint16_t)((word >> (10 * (idx % 3))) & 1023u);
+  }
+  return true;
 }
 
 // Copy the byte range [a, b) of a page (2-byte aligned, both in bounds) to dst
@@ -418,6 +550,8 @@ k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
     o += (size_t)kWinT * nw * 4;
     S.pk = reinterpret_cast<uint32_t*>(smem_raw + o);
     o += (size_t)kWinT * nw * 4;
+    S.dbm = reinterpret_cast<uint32_t*>(smem_raw + o);
+    o += (size_t)kRunMapWords * 4;
     o = (o + 15) & ~(size_t)15;
     S.st_rec = reinterpret_cast<uint4*>(smem_raw + o);
     o += kStage * 16;
@@ -443,6 +577,8 @@ k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
     o = (o + 15) & ~(size_t)15;
     S.list = reinterpret_cast<uint16_t*>(smem_raw + o);
     o += kList * 2;
+    S.run_t = reinterpret_cast<uint8_t*>(smem_raw + o);
+    o += kMaxRuns;
   }
   const int tid = threadIdx.x;
   const int opt = (nown_words + blockDim.x - 1) / blockDim.x;
@@ -486,8 +622,8 @@ k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
       S.offs[tid] = (j >= 0 && j < (long long)n_windows) ? W.page_offsets[j] : ~0ull;
     }
     {
-      // occ and pk are adjacent: clear both as 16-byte words (the tail word by word)
-      const int nwords = 2 * kWinT * nw;
+      // occ, pk and dbm are adjacent: clear them as 16-byte words (the tail word by word)
+      const int nwords = 2 * kWinT * nw + kRunMapWords;
       uint4* o4 = reinterpret_cast<uint4*>(S.occ);
       for (int i = tid; i < nwords / 4; i += blockDim.x) o4[i] = make_uint4(0u, 0u, 0u, 0u);
       for (int i = (nwords & ~3) + tid; i < nwords; i += blockDim.x) S.occ[i] = 0u;
@@ -607,7 +743,17 @@ k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
                    reinterpret_cast<const uint16_t*>(own + 32 + 2 * h.n_tb), h.n_runs,
                    reinterpret_cast<const uint32_t*>(own + h.body), 0, h.n_dig, kHalo, kFrag * f,
                    listed ? 0 : kList, true};
-      ok = decode_seg(go, ok, np, ps_stride, nw, T, S, okp ? &gp : nullptr, okn ? &gn : nullptr);
+      const int nrun_all = (okp ? hp.n_runs - hp.hi_runs : 0) + (ok ? h.n_runs : 0) + (okn ? hn.lo_runs : 0);
+      if (ok && listed && nrun_all <= kMaxRuns) {
+        const WinSeg s0{gp.ent, gp.run, gp.adc, okp ? gp.ne : 0, okp ? gp.nrun : 0, n_prev, gp.dfirst, gp.tt_base,
+                        gp.t_base_abs};
+        const WinSeg s1{go.ent, go.run, go.adc, go.ne, go.nrun, n_own, 0, go.tt_base, go.t_base_abs};
+        const WinSeg s2{gn.ent, gn.run, gn.adc, okn ? gn.ne : 0, okn ? gn.nrun : 0, n_next, 0, gn.tt_base,
+                        gn.t_base_abs};
+        ok = decode_window(s0, s1, s2, np, ps_stride, nw, T, S);
+      } else {
+        ok = decode_seg(go, ok, np, ps_stride, nw, T, S, okp ? &gp : nullptr, okn ? &gn : nullptr);
+      }
     }
     if (!ok && tid == 0) atomicOr(W.err, kErrCorrupt);
     __syncthreads();
@@ -809,11 +955,12 @@ k_compact_clusters(DevGeom G, DevWork W, unsigned int n_windows) {
 
 size_t find_smem_bytes(int npmax, int nw) {
   size_t o = ((size_t)kWinT * (npmax + 2 * kPad) * 2 + 15) & ~(size_t)15;
-  o += 2 * (size_t)kWinT * nw * 4;
+  o += 2 * (size_t)kWinT * nw * 4 + (size_t)kRunMapWords * 4;
   o = (o + 15) & ~(size_t)15;
   o += 2 * kStage * 16 + 2 * kHaloStage + 4 * 16 + 4 * 8 + 34 * 8 + 16 * 4;
   o += (3 * sizeof(PageHdr) + 15) & ~(size_t)15;
   o += kList * 2 + kStage * 2 + ((size_t)kFrag * nw + 1) * 2 + 16;
+  o += kMaxRuns;
   return o;
 }
 

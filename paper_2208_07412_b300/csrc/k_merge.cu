@@ -59,11 +59,11 @@ __global__ void k_merge_cand(DevGeom G, DevParams P, DevWork W) {
     const long long zp = Za2 + floordiv_ll((Za2 - Za1) * (Xb - Xa2), dxa);
     const long long tlo = floordiv_ll(zp - MC - 2, 640) - 3;
     const long long thi = floordiv_ll(zp + MC + 2, 640) + 3;
-    const unsigned lo = W.row_start[s * R + rb], hi = W.row_start[s * R + rb + 1];
-    for (unsigned b1 = lower_bound_tm(W.cl_t, lo, hi, tlo); b1 < hi; b1++) {
-      if ((long long)__ldg(W.cl_t + b1) > thi) break;
-      const int kb = W.cl_chain[b1];
-      if (kb < 0 || W.ch_root[kb] != (int)b1) continue;
+    // the chains whose bottom (root) cluster lies in row rb, by root time bin
+    const unsigned lo = W.ch_row_start[s * R + rb], hi = W.ch_row_start[s * R + rb + 1];
+    for (unsigned kb = lower_bound_tm(W.ch_t, lo, hi, tlo); kb < hi; kb++) {
+      if ((long long)__ldg(W.ch_t + kb) > thi) break;
+      const int b1 = W.ch_root[kb];
       const int b2 = W.ch_b2[kb];
       const long long Xb1 = W.cl_x[b1], Yb1 = W.cl_y[b1], Zb1 = W.cl_z[b1];
       const long long Xb2 = W.cl_x[b2], Yb2 = W.cl_y[b2], Zb2 = W.cl_z[b2];

@@ -62,7 +62,7 @@ struct Slot {
   cudaEvent_t ev_stage[TPC_N_STAGES + 1] = {};
   cudaEvent_t ev_done = nullptr, ev_input = nullptr;
   // device buffers
-  Buf pages, offsets, winstate, cl, clx, cly, clz, clt, rowstart, up, down, score, edge, jump, chlen, scanv,
+  Buf pages, offsets, winstate, cl, clx, cly, clz, clt, rowstart, chrow, up, down, score, edge, jump, chlen, scanv,
       scanst, chainof, clchain, ch_i32, besta, bestb, trk_i32, trackcl, cl2trk, tracks, ctrl, scratch, wincnt, winsoff,
       candab, candsc, lenhist, evinfo;
   unsigned long long* h_ctrl = nullptr;   // pinned copy of [ctr | err]
@@ -203,8 +203,8 @@ static cudaError_t ensure(Buf& b, size_t bytes) {
 static size_t slot_bytes(uint64_t pages, uint64_t windows, uint64_t cap_cl, uint64_t cap_ch, int nsr) {
   size_t b = pages + 16 + windows * 28 + cap_cl * (16 + 16 + 16 + 8 + 8 + 8 + 8 + 4 + 8 + 4 + 4 + 4 + 4) +
              (scan_tiles(cap_cl) + scan_tiles(cap_ch) + scan_tiles(windows)) * 8 +
-             cap_ch * (12 * 4 + 8 + 16 + sizeof(tpc_track) + 4 * 12) +
-             (size_t)(nsr + 1) * 4 + 1024;
+             cap_ch * (14 * 4 + 8 + 16 + sizeof(tpc_track) + 4 * 12) +
+             (size_t)(nsr + 1) * 8 + 1024;
   return b;
 }
 
@@ -241,7 +241,7 @@ static tpc_status slot_reserve(tpc_context* ctx, Slot& s, uint64_t pages_bytes, 
     s.cap_cl = cap_cl;
   }
   if (cap_ch > s.cap_ch) {
-    CUDA_TRY(ensure(s.ch_i32, cap_ch * 4 * 13));
+    CUDA_TRY(ensure(s.ch_i32, cap_ch * 4 * 14));
     CUDA_TRY(ensure(s.bestb, cap_ch * 8));
     CUDA_TRY(ensure(s.besta, cap_ch * 16));
     CUDA_TRY(ensure(s.tracks, cap_ch * sizeof(tpc_track)));
@@ -251,6 +251,7 @@ static tpc_status slot_reserve(tpc_context* ctx, Slot& s, uint64_t pages_bytes, 
   }
   CUDA_TRY(ensure(s.scanst, (scan_tiles(s.cap_cl) + scan_tiles(s.cap_ch) + scan_tiles(s.cap_windows)) * 8));
   CUDA_TRY(ensure(s.rowstart, (size_t)(nsr + 1) * 4));
+  CUDA_TRY(ensure(s.chrow, (size_t)(nsr + 1) * 4));
   CUDA_TRY(ensure(s.ctrl, 256));
   CUDA_TRY(ensure(s.lenhist, 512 * 4));
   ctx->used = ctx->used - cur + slot_bytes(s.cap_pages, s.cap_windows, s.cap_cl, s.cap_ch, nsr);
@@ -259,6 +260,7 @@ static tpc_status slot_reserve(tpc_context* ctx, Slot& s, uint64_t pages_bytes, 
   W.clusters = (tpc_cluster*)s.cl.p;
   W.cl_x = (int32_t*)s.clx.p; W.cl_y = (int32_t*)s.cly.p; W.cl_z = (int32_t*)s.clz.p; W.cl_t = (int32_t*)s.clt.p;
   W.row_start = (uint32_t*)s.rowstart.p;
+  W.ch_row_start = (uint32_t*)s.chrow.p;
   W.win_state = (unsigned long long*)s.winstate.p;
   W.scratch_cl = (tpc_cluster*)s.scratch.p;
   W.win_cnt = (unsigned long long*)s.wincnt.p;
@@ -277,6 +279,7 @@ static tpc_status slot_reserve(tpc_context* ctx, Slot& s, uint64_t pages_bytes, 
   W.ch_root = ci; W.ch_len = ci + C; W.ch_b2 = ci + 2 * C; W.ch_top = ci + 3 * C; W.ch_top2 = ci + 4 * C;
   W.ch_next = ci + 5 * C; W.ch_prev = ci + 6 * C; W.ch_track = ci + 7 * C; W.ch_off = ci + 8 * C;
   W.grp_total = ci + 9 * C; W.trk_first = ci + 10 * C; W.trk_ncl = ci + 11 * C; W.trk_off = ci + 12 * C;
+  W.ch_t = ci + 13 * C;
   W.fit_order = W.ch_off;   // free once the clusters are assigned to tracks
   W.len_hist = (uint32_t*)s.lenhist.p;
   W.best_b = (unsigned long long*)s.bestb.p;
@@ -297,7 +300,7 @@ static tpc_status slot_reserve(tpc_context* ctx, Slot& s, uint64_t pages_bytes, 
 }
 
 static void slot_free(tpc_context* ctx, Slot& s) {
-  Buf* all[] = {&s.pages, &s.offsets, &s.winstate, &s.cl, &s.clx, &s.cly, &s.clz, &s.clt, &s.rowstart, &s.up,
+  Buf* all[] = {&s.pages, &s.offsets, &s.winstate, &s.cl, &s.clx, &s.cly, &s.clz, &s.clt, &s.rowstart, &s.chrow, &s.up,
                 &s.down, &s.score, &s.edge, &s.jump, &s.chlen, &s.scanv, &s.scanst, &s.chainof, &s.clchain,
                 &s.ch_i32, &s.besta, &s.bestb, &s.trk_i32, &s.trackcl, &s.cl2trk, &s.tracks, &s.ctrl,
                 &s.scratch, &s.wincnt, &s.winsoff, &s.candab, &s.candsc, &s.lenhist, &s.evinfo};
