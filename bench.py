@@ -46,6 +46,10 @@ WORKLOADS = {
                          "floor(15000 U^7.82) (mean ~1,700), 5% loopers, same charge/noise/ZS model"),
 }
 REF_SAMPLE_BYTES = 20 << 20
+# DRAM bytes (read + write) of one k_find_clusters launch, from an ncu capture of
+# the current kernel on the workload (seed 1); None where no capture exists.
+# Must be reset to None whenever the finder kernel changes.
+FINDER_DRAM_BYTES = {"full_tpc": 70_607_872 + 6_649_088}
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -507,7 +511,9 @@ def run_ours(args, world, rank, local):
             "stages_ms": stages,
             "wall_ms_per_step": 1e3 * wall / args.steps,
             "roofline": {"kernel": "k_find_clusters", "bound": "hbm", "achieved": achieved, "peak": hbm,
-                         "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                         "unit": "GB/s", "frac": achieved / hbm,
+                         "traffic": (FINDER_DRAM_BYTES.get(args.workload) if args.seed == 1 and not args.time_bins
+                                     else None),
                          "peak_kind": f"{peak_kind} hbm_gbs (copy)",
                          "algorithmic_bytes_per_launch": int(alg_bytes)},
             "e2e": {"value": cl_all / e2e_s_max, "unit": "clusters/s", "h2d_bytes_per_step": int(h2d),
