@@ -386,6 +386,23 @@ def run_serve(args, world, rank, local):
     print(json.dumps(line), flush=True)
 
 
+def cross_sector_timing(tpc, torch, R, pages_d, offs_d, tf, reps=5):
+    """The optional step 9 (tpc_merge_sectors) on a finished timeframe: host
+    wall time of the call (it runs on the slot's stream and waits for it)."""
+    t = R.submit(pages_d, offs_d, tf.n_time_bins)
+    R.wait(t)
+    n_in = tpc.tpc_get_counters(R.ctx, t)["tracks"]
+    tpc.tpc_merge_sectors(R.ctx, t)   # warm-up (allocates its work space)
+    times = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        n_out = tpc.tpc_merge_sectors(R.ctx, t)
+        times.append(time.perf_counter() - t0)
+    tpc.tpc_release(R.ctx, t)
+    return {"ms": 1e3 * statistics.median(times), "tracks_in": n_in, "tracks_out": n_out,
+            "links": n_in - n_out, "timing": f"host wall clock of the call, median of {reps}"}
+
+
 def run_ours(args, world, rank, local):
     import torch
     from paper_2208_07412_b300 import tpc
@@ -521,6 +538,8 @@ def run_ours(args, world, rank, local):
             "clocks": clk.summary(),
             "gpu_launches": int(launches),
         }
+        if world == 1 and args.workload == "full_tpc":
+            line["cross_sector"] = cross_sector_timing(tpc, torch, R, pages_d, offs_d, tf)
         if world == 1 and not args.no_batched and args.workload == "full_tpc":
             line["batched"] = batched_vs_plain(tpc, torch, local, tuning=tuning)
         if world == 1 and not args.no_cpu_baseline:

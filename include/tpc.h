@@ -191,6 +191,7 @@ typedef struct {
 
 #define TPC_TRK_STOPPED  1u   /* a pass stopped early (|snp| would reach 0.999) */
 #define TPC_TRK_NOT_PD   2u   /* covariance not positive definite even after the FP64 redo */
+#define TPC_TRK_XSECTOR  4u   /* refitted over pieces in several sectors (tpc_merge_sectors) */
 
 /* Fill *p with the defaults listed in tpc_params.  Never fails for p != NULL. */
 tpc_status tpc_params_default(tpc_params* p);
@@ -324,6 +325,54 @@ tpc_status tpc_get_clusters(tpc_context* ctx, uint64_t ticket, tpc_cluster* out,
  * out == NULL: only *n is set.  Errors as tpc_get_clusters. */
 tpc_status tpc_get_tracks(tpc_context* ctx, uint64_t ticket, tpc_track* out, uint64_t cap,
                           uint64_t* n, int32_t* cluster_to_track);
+
+/* Cross-sector merge parameters (step 9). */
+typedef struct {
+  double chi2_cut;   /* 100  matching chi2 (5 parameters) for a link */
+  double edge_cm;    /* 6    a piece's end counts as at a sector edge within this distance
+                              of the pad plane's edge (rounded to u = 7.8125 um) */
+} tpc_xs_params;
+
+/* Step 9, optional: join the pieces of tracks that cross a sector border, on
+ * a finished ticket's device-resident results, and refit each joined track
+ * over all its clusters.  The paper names the full TPC tracking on the EPN
+ * GPUs ("Hardware and data flow"); this is the library's definition of its
+ * last step:
+ *   - a track's end is at the +y (-y) edge of its sector when its outermost
+ *     (for the exit) or innermost (for the entry) cluster has
+ *     Y >= 256 (npads - 1) - E (Y <= -(256 (npads - 1) - E)), Y in u, E = edge_cm / u;
+ *   - candidates: A exiting through +y (-y) of sector s, B entering through -y
+ *     (+y) of the neighbouring sector s+1 (s-1) of the same side (sectors
+ *     0..17 and 18..35, cyclic), A's outermost row below B's innermost row,
+ *     neither fit flagged;
+ *   - B's state is rotated into A's frame and transported to A's reference x:
+ *     chi2 = d^T (C_A + J C_B J^T)^-1 d over the 5 parameters; with the
+ *     rotation by delta = alpha_B - alpha_A of a state at x: (x, y) ->
+ *     (x cos d - y sin d, x sin d + y cos d), snp -> sin(phi + d), and the
+ *     first-order Jacobian dy' = (cos d + tan(phi') sin d) dy, dzeta' = dzeta +
+ *     (tgl / cos(phi')) sin d dy, dsnp' = (cos d - sin d tan(phi)) dsnp +
+ *     k sin d dy;
+ *   - mutual best pairs with chi2 <= chi2_cut link (ties: lower track index);
+ *   - each chain of linked pieces is one track, ordered by its innermost
+ *     piece; refitted as in step 8 over all its clusters (initial circle in
+ *     the outermost piece's frame; state and covariance rotated into a piece's
+ *     frame before its first cluster); flagged TPC_TRK_XSECTOR; its parameters
+ *     refer to the innermost cluster in the innermost piece's frame.
+ *   Unlinked tracks keep their step-8 records.
+ * xp: NULL for the defaults.  *n_tracks (may be NULL): tracks after the merge.
+ * Runs on the ticket's stream and waits for it; results until tpc_release.
+ * The candidate search compares every exiting piece with every track of the
+ * neighbouring sector: cheap at full-TPC occupancy (~800 tracks per sector),
+ * quadratic on much larger timeframes.
+ * Errors: TPC_E_NOTREADY (ticket not done), TPC_E_NOTFOUND, TPC_E_CUDA, TPC_E_NOMEM. */
+tpc_status tpc_merge_sectors(tpc_context* ctx, uint64_t ticket, const tpc_xs_params* xp, uint64_t* n_tracks);
+
+/* The tracks after tpc_merge_sectors (cap records), the cluster-to-track map
+ * (n_clusters entries, may be NULL) and, per step-8 track (may be NULL), the
+ * index of its outer linked piece or -1.  out == NULL: only *n is set.
+ * TPC_E_NOTREADY if tpc_merge_sectors has not run on the ticket. */
+tpc_status tpc_get_merged_tracks(tpc_context* ctx, uint64_t ticket, tpc_track* out, uint64_t cap, uint64_t* n,
+                                 int32_t* cluster_to_track, int32_t* link);
 
 /* Layout of a finished ticket's results by event: *n_events (1 for a plain
  * timeframe) and, if not NULL, cluster_start[n_events + 1] and

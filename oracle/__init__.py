@@ -127,6 +127,13 @@ def _load():
         L.orc_transport.argtypes = [_P, _P, ctypes.c_double, _P, _P]
         L.orc_update.argtypes = [_P, _P, _P, ctypes.c_double, ctypes.c_double, _P]
         L.orc_update.restype = ctypes.c_double
+        L.orc_rotate.argtypes = [_P, _P, _P, ctypes.c_double, _P]
+        L.orc_xs_chi2.argtypes = [_P, _P, ctypes.c_double, _P, ctypes.c_double]
+        L.orc_xs_chi2.restype = ctypes.c_double
+        L.orc_fit_points_xs.argtypes = [_P, ctypes.c_int, _P, _P, _P, _P, _P]
+        L.orc_merge_sectors.argtypes = [_P, _P, _P, _P, ctypes.c_int64, _P, ctypes.c_int64, _P, _P, _P, _P,
+                                        _P, _P, _P, _P]
+        L.orc_merge_sectors.restype = ctypes.c_int64
         _lib = L
     return _lib
 
@@ -298,6 +305,93 @@ def update(state, C, my, mz, params: OracleParams | None = None):
     chi2 = L.orc_update(ctypes.byref(p), s.ctypes.data, Cm.ctypes.data, float(my), float(mz),
                         ctypes.byref(ok))
     return s, Cm.reshape(5, 5), chi2, bool(ok.value)
+
+
+class _XsParams(ctypes.Structure):
+    _fields_ = [("chi2_cut", ctypes.c_double), ("edge_cm", ctypes.c_double)]
+
+
+@dataclass
+class XsParams:
+    """Cross-sector merge constants."""
+    chi2_cut: float = 100.0
+    edge_cm: float = 6.0
+
+    def _c(self) -> _XsParams:
+        return _XsParams(float(self.chi2_cut), float(self.edge_cm))
+
+
+def sector_alpha(s: int) -> float:
+    return ((s % 18) + 0.5) * np.deg2rad(20.0)
+
+
+def rotate(state, x, delta, params: OracleParams | None = None):
+    """Express a state at x in a frame rotated by -delta (delta = alpha_old -
+    alpha_new); returns (state', x', R) or (None, None, None)."""
+    L = _load()
+    p = (params or OracleParams())._c()
+    s = np.array(state, np.float64)
+    xx = ctypes.c_double(float(x))
+    R = np.zeros(25)
+    if L.orc_rotate(ctypes.byref(p), s.ctypes.data, ctypes.byref(xx), float(delta), R.ctypes.data):
+        return None, None, None
+    return s, xx.value, R.reshape(5, 5)
+
+
+def xs_chi2(fa, alpha_a, fb, alpha_b, params: OracleParams | None = None) -> float:
+    L = _load()
+    p = (params or OracleParams())._c()
+    a = np.ascontiguousarray(np.array([fa], dtype=FIT_DTYPE))
+    b = np.ascontiguousarray(np.array([fb], dtype=FIT_DTYPE))
+    return L.orc_xs_chi2(ctypes.byref(p), a.ctypes.data, float(alpha_a), b.ctypes.data, float(alpha_b))
+
+
+def fit_points_xs(x, y, z, alpha, params: OracleParams | None = None) -> np.void:
+    """FP64 fit of points (cm) in several sector frames (alpha per point)."""
+    L = _load()
+    p = (params or OracleParams())._c()
+    arrs = [np.ascontiguousarray(a, np.float64) for a in (x, y, z, alpha)]
+    out = np.zeros(1, dtype=FIT_DTYPE)
+    L.orc_fit_points_xs(ctypes.byref(p), len(arrs[0]), *(a.ctypes.data for a in arrs), out.ctypes.data)
+    return out[0]
+
+
+@dataclass
+class XsResult:
+    link: np.ndarray        # [n_tracks] outer piece or -1
+    best_chi2: np.ndarray   # [n_tracks] best candidate chi2 as the inner piece, or -1
+    group_of: np.ndarray    # [n_tracks] merged track of every piece
+    fits: np.ndarray        # [n_merged]
+    first: np.ndarray       # [n_merged] lowest-row cluster of the innermost piece
+    ncl: np.ndarray         # [n_merged]
+    npieces: np.ndarray     # [n_merged]
+    cl2trk: np.ndarray      # [n_clusters] merged track or -1
+
+
+def merge_sectors(tf, res, params: OracleParams | None = None, xs: XsParams | None = None) -> XsResult:
+    """Cross-sector merge of an OracleResult's tracks (step 9)."""
+    L = _load()
+    p = (params or OracleParams())._c()
+    xp = (xs or XsParams())._c()
+    inp = _In.from_tf(tf)
+    cl = np.ascontiguousarray(res.clusters)
+    c2t = np.ascontiguousarray(res.cl2trk, np.int32)
+    fits = np.ascontiguousarray(res.fits)
+    nt = len(fits)
+    link = np.zeros(max(nt, 1), np.int32)
+    best = np.zeros(max(nt, 1), np.float64)
+    grp = np.zeros(max(nt, 1), np.int32)
+    gfit = np.zeros(max(nt, 1), FIT_DTYPE)
+    gf = np.zeros(max(nt, 1), np.int32)
+    gn = np.zeros(max(nt, 1), np.int32)
+    gp = np.zeros(max(nt, 1), np.int32)
+    ng = L.orc_merge_sectors(inp.ref, ctypes.byref(p), ctypes.byref(xp), cl.ctypes.data if len(cl) else None,
+                             len(cl), c2t.ctypes.data if len(c2t) else None, nt,
+                             fits.ctypes.data if nt else None, link.ctypes.data, best.ctypes.data,
+                             grp.ctypes.data, gfit.ctypes.data, gf.ctypes.data, gn.ctypes.data, gp.ctypes.data)
+    new_c2t = np.where(c2t >= 0, grp[np.maximum(c2t, 0)], -1).astype(np.int32)
+    return XsResult(link[:nt].copy(), best[:nt].copy(), grp[:nt].copy(), gfit[:ng].copy(), gf[:ng].copy(),
+                    gn[:ng].copy(), gp[:ng].copy(), new_c2t)
 
 
 @dataclass

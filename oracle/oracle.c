@@ -652,3 +652,297 @@ int orc_fit_all(const orc_input* in, const orc_params* P, const orc_cluster* cl,
   free(cnt); free(lst); free(fill);
   return 0;
 }
+
+/* ------------------------------------------------------------ 9. cross-sector merge
+ * Follows the library's definition of the optional cross-sector merge (the
+ * paper, section "Hardware and data flow", names the full TPC tracking on the
+ * EPN GPUs; matching track pieces across sector borders is this library's
+ * definition of that tracking's last step):
+ *   - a track piece A exits through the +y (-y) edge of its sector when its
+ *     outermost cluster lies within edge_cm of that edge of the pad plane; a
+ *     piece B enters through an edge when its innermost cluster does;
+ *   - a candidate pair is A exiting through +y (-y) of sector s and B entering
+ *     through -y (+y) of the neighbouring sector s+1 (s-1) of the same side,
+ *     with A's outermost row below B's innermost row;
+ *   - B's fitted state is expressed in A's frame (rotation about the beam axis)
+ *     and transported to A's reference x; chi2 = d^T (C_A + J C_B J^T)^-1 d;
+ *   - mutual best pairs under chi2 <= chi2_cut link (ties: lower index);
+ *   - chained pieces form one track, refitted over all their clusters with the
+ *     frame switched at each sector change.
+ * Rotation of a state (y, zeta, snp, tgl, q/pT) at x from a frame at angle
+ * alpha_old to one at alpha_new (delta = alpha_old - alpha_new): the point
+ * (x, y) maps to (x cos d - y sin d, x sin d + y cos d), the direction angle
+ * gains d.  Its Jacobian at the rotated reference x' (first order: the point
+ * moves with y by dx' = -sin d dy, and the state is carried back along the
+ * helix to the fixed x'): dy' = (cos d + tan(phi') sin d) dy;
+ * dzeta' = dzeta + (tgl / cos(phi')) sin d dy; dsnp' = (cos d - sin d snp /
+ * cos(phi)) dsnp + k sin d dy. */
+typedef struct {
+  double chi2_cut;   /* 100 */
+  double edge_cm;    /* 6 */
+} orc_xs_params;
+
+static double sector_alpha(int s) { return ((double)(s % 18) + 0.5) * (20.0 * 3.14159265358979323846 / 180.0); }
+
+int orc_rotate(const orc_params* P, double* s, double* x, double delta, double* R) {
+  double cd = cos(delta), sd = sin(delta);
+  double sn = s[2];
+  if (fabs(sn) >= 0.999) return 1;
+  double cs = sqrt(1.0 - sn * sn);
+  double sn2 = sn * cd + cs * sd;
+  if (fabs(sn2) >= 0.999) return 1;
+  double cs2 = sqrt(1.0 - sn2 * sn2);
+  if (R) {
+    for (int i = 0; i < 25; i++) R[i] = 0.0;
+    for (int i = 0; i < 5; i++) R[i * 5 + i] = 1.0;
+    R[0 * 5 + 0] = cd + (sn2 / cs2) * sd;
+    R[1 * 5 + 0] = (s[3] / cs2) * sd;
+    R[2 * 5 + 0] = kfac(P) * s[4] * sd;
+    R[2 * 5 + 2] = cd - sd * sn / cs;
+  }
+  double xn = *x * cd - s[0] * sd;
+  double yn = *x * sd + s[0] * cd;
+  s[0] = yn;
+  s[2] = sn2;
+  *x = xn;
+  return 0;
+}
+
+static void mat_abt(const double* A, const double* B, double* C) {   /* C = A B^T (5x5) */
+  for (int i = 0; i < 5; i++)
+    for (int j = 0; j < 5; j++) {
+      double acc = 0.0;
+      for (int l = 0; l < 5; l++) acc += A[i * 5 + l] * B[j * 5 + l];
+      C[i * 5 + j] = acc;
+    }
+}
+static void mat_ab(const double* A, const double* B, double* C) {    /* C = A B (5x5) */
+  for (int i = 0; i < 5; i++)
+    for (int j = 0; j < 5; j++) {
+      double acc = 0.0;
+      for (int l = 0; l < 5; l++) acc += A[i * 5 + l] * B[l * 5 + j];
+      C[i * 5 + j] = acc;
+    }
+}
+/* C <- J C J^T */
+static void sandwich(const double* J, double* C) {
+  double T[25], Jt[25];
+  mat_ab(J, C, T);
+  for (int i = 0; i < 5; i++)
+    for (int j = 0; j < 5; j++) Jt[i * 5 + j] = J[j * 5 + i];
+  mat_ab(T, Jt, C);
+}
+
+static void unpack_cov(const double* tri, double* C) {
+  int m = 0;
+  for (int i = 0; i < 5; i++)
+    for (int j = 0; j <= i; j++) { C[i * 5 + j] = tri[m]; C[j * 5 + i] = tri[m]; m++; }
+}
+
+/* chi2 of d^T M^-1 d for symmetric positive definite M (Cholesky); -1 if not PD. */
+static double chi2_spd(const double* M, const double* d) {
+  double L[25] = {0};
+  for (int j = 0; j < 5; j++) {
+    double acc = M[j * 5 + j];
+    for (int k = 0; k < j; k++) acc -= L[j * 5 + k] * L[j * 5 + k];
+    if (!(acc > 0.0)) return -1.0;
+    L[j * 5 + j] = sqrt(acc);
+    for (int i = j + 1; i < 5; i++) {
+      double a = M[i * 5 + j];
+      for (int k = 0; k < j; k++) a -= L[i * 5 + k] * L[j * 5 + k];
+      L[i * 5 + j] = a / L[j * 5 + j];
+    }
+  }
+  double w[5], c2 = 0.0;   /* solve L w = d */
+  for (int i = 0; i < 5; i++) {
+    double a = d[i];
+    for (int k = 0; k < i; k++) a -= L[i * 5 + k] * w[k];
+    w[i] = a / L[i * 5 + i];
+    c2 += w[i] * w[i];
+  }
+  return c2;
+}
+
+/* Matching chi2 of pieces A (state at xa in frame aa) and B (at xb in frame ab);
+ * -1 if B cannot be carried to A's reference. */
+double orc_xs_chi2(const orc_params* P, const orc_fit* A, double aa, const orc_fit* B, double ab) {
+  double s[5], x = B->x, R[25], F[25], J[25], CA[25], CB[25], out[5], d[5];
+  for (int i = 0; i < 5; i++) s[i] = B->par[i];
+  if (orc_rotate(P, s, &x, ab - aa, R)) return -1.0;
+  if (orc_transport(P, s, A->x - x, out, F)) return -1.0;
+  mat_ab(F, R, J);
+  unpack_cov(A->cov, CA);
+  unpack_cov(B->cov, CB);
+  sandwich(J, CB);
+  for (int i = 0; i < 25; i++) CA[i] += CB[i];
+  for (int i = 0; i < 5; i++) d[i] = A->par[i] - out[i];
+  return chi2_spd(CA, d);
+}
+
+/* FP64 fit over points in several sector frames: (x, y) in the frame of
+ * alpha[i], zeta common; points ordered innermost first, frames changing only
+ * between pieces.  Initial state from the circle through the innermost, middle
+ * and outermost points expressed in the outermost point's frame; passes as in
+ * orc_fit_points, the state and covariance rotated into a point's frame before
+ * it is reached. */
+int orc_fit_points_xs(const orc_params* P, int n, const double* x, const double* y, const double* z,
+                      const double* alpha, orc_fit* out) {
+  double s[5], C[25];
+  {
+    /* the three points in the outermost point's frame */
+    int idx[3] = {0, (n - 1) / 2, n - 1};
+    double px[3], py[3], pz[3];
+    for (int q = 0; q < 3; q++) {
+      double dd = alpha[idx[q]] - alpha[n - 1], cd = cos(dd), sd = sin(dd);
+      px[q] = x[idx[q]] * cd - y[idx[q]] * sd;
+      py[q] = x[idx[q]] * sd + y[idx[q]] * cd;
+      pz[q] = z[idx[q]];
+    }
+    fit_init(P, px, py, pz, 3, s);
+  }
+  double xcur = x[n - 1], acur = alpha[n - 1];
+  int flags = 0, n_used = 0;
+  double chi2 = 0.0;
+  for (int pass = 0; pass < P->fit_passes; pass++) {
+    for (int i = 0; i < 25; i++) C[i] = 0.0;
+    for (int i = 0; i < 5; i++) C[i * 5 + i] = P->c0[i];
+    chi2 = 0.0;
+    n_used = 0;
+    int inward = (pass % 2) == 0;
+    for (int j = 0; j < n; j++) {
+      int i = inward ? n - 1 - j : j;
+      if (alpha[i] != acur) {
+        double R[25];
+        if (orc_rotate(P, s, &xcur, acur - alpha[i], R)) { flags |= 1; break; }
+        sandwich(R, C);
+        acur = alpha[i];
+      }
+      double dx = x[i] - xcur;
+      if (dx != 0.0) {
+        double ns[5], F[25];
+        if (orc_transport(P, s, dx, ns, F)) { flags |= 1; break; }
+        sandwich(F, C);
+        memcpy(s, ns, sizeof(ns));
+        xcur = x[i];
+      }
+      int ok = 1;
+      chi2 += orc_update(P, s, C, y[i], z[i], &ok);
+      if (!ok) flags |= 2;
+      n_used++;
+    }
+  }
+  for (int i = 0; i < 5; i++) out->par[i] = s[i];
+  out->x = xcur;
+  int m = 0;
+  for (int i = 0; i < 5; i++)
+    for (int j = 0; j <= i; j++) out->cov[m++] = C[i * 5 + j];
+  out->chi2 = chi2;
+  out->ndf = 2 * n_used - 5;
+  out->n_used = n_used;
+  out->flags = flags;
+  return 0;
+}
+
+/* Edge test in integer u (7.8125 um): the pad plane of a row spans
+ * |Y| <= 256 (npads - 1); a cluster within E = edge_cm / u of an edge. */
+static int side_of(int64_t Y, int np, int64_t E) {
+  const int64_t hw = 256 * (int64_t)(np - 1);
+  if (Y >= hw - E) return 1;
+  if (Y <= -(hw - E)) return -1;
+  return 0;
+}
+static int neighbour_sector(int s, int side) {
+  int base = s < 18 ? 0 : 18, k = s - base;
+  return base + (k + (side > 0 ? 1 : 17)) % 18;
+}
+
+/* Cross-sector merge of the tracks of orc_merge / orc_fit_all.  Outputs:
+ * link[n_tracks] (outer piece or -1), best_chi2[n_tracks] (A's best candidate
+ * chi2 or -1), group_of[n_tracks] (merged track index of every piece),
+ * gfit / g_first / g_ncl / g_npieces per merged track (track order: by the
+ * innermost piece's index).  Returns the number of merged tracks. */
+int64_t orc_merge_sectors(const orc_input* in, const orc_params* P, const orc_xs_params* XP,
+                          const orc_cluster* cl, int64_t n, const int32_t* cl2trk, int64_t nt,
+                          const orc_fit* fits, int32_t* link, double* best_chi2, int32_t* group_of,
+                          orc_fit* gfit, int32_t* g_first, int32_t* g_ncl, int32_t* g_npieces) {
+  const double u = 7.8125e-4;
+  /* per-track cluster lists in row order */
+  int64_t* cnt = (int64_t*)calloc((size_t)nt + 1, sizeof(int64_t));
+  for (int64_t i = 0; i < n; i++) if (cl2trk[i] >= 0) cnt[cl2trk[i] + 1]++;
+  for (int64_t t = 0; t < nt; t++) cnt[t + 1] += cnt[t];
+  int64_t* lst = (int64_t*)malloc(sizeof(int64_t) * (cnt[nt] + 1));
+  int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * (nt + 1));
+  memcpy(fill, cnt, sizeof(int64_t) * nt);
+  for (int64_t i = 0; i < n; i++) if (cl2trk[i] >= 0) lst[fill[cl2trk[i]]++] = i;
+  /* ends */
+  int* sec = (int*)malloc(sizeof(int) * (nt + 1));
+  int* exit_side = (int*)malloc(sizeof(int) * (nt + 1));
+  int* entry_side = (int*)malloc(sizeof(int) * (nt + 1));
+  int* row_in = (int*)malloc(sizeof(int) * (nt + 1));
+  int* row_out = (int*)malloc(sizeof(int) * (nt + 1));
+  for (int64_t t = 0; t < nt; t++) {
+    const orc_cluster* ci = &cl[lst[cnt[t]]];
+    const orc_cluster* co = &cl[lst[cnt[t + 1] - 1]];
+    int64_t X, Y, Z;
+    sec[t] = ci->sector;
+    row_in[t] = ci->row;
+    row_out[t] = co->row;
+    const int64_t E = (int64_t)floor(XP->edge_cm / u + 0.5);
+    orc_coords(in, ci, &X, &Y, &Z);
+    entry_side[t] = side_of(Y, in->npads[ci->row], E);
+    orc_coords(in, co, &X, &Y, &Z);
+    exit_side[t] = side_of(Y, in->npads[co->row], E);
+  }
+  /* best candidates (chi2, index) both ways */
+  double* bb = (double*)malloc(sizeof(double) * (nt + 1));
+  double* ba = (double*)malloc(sizeof(double) * (nt + 1));
+  int32_t* ib = (int32_t*)malloc(sizeof(int32_t) * (nt + 1));
+  int32_t* ia = (int32_t*)malloc(sizeof(int32_t) * (nt + 1));
+  for (int64_t t = 0; t < nt; t++) { bb[t] = ba[t] = -1.0; ib[t] = ia[t] = -1; }
+  for (int64_t a = 0; a < nt; a++) {
+    if (!exit_side[a] || fits[a].flags) continue;
+    int sb = neighbour_sector(sec[a], exit_side[a]);
+    for (int64_t b = 0; b < nt; b++) {
+      if (sec[b] != sb || entry_side[b] != -exit_side[a] || row_out[a] >= row_in[b] || fits[b].flags) continue;
+      double c2 = orc_xs_chi2(P, &fits[a], sector_alpha(sec[a]), &fits[b], sector_alpha(sec[b]));
+      if (c2 < 0.0 || c2 > XP->chi2_cut) continue;
+      if (ib[a] < 0 || c2 < bb[a] || (c2 == bb[a] && b < ib[a])) { bb[a] = c2; ib[a] = (int32_t)b; }
+      if (ia[b] < 0 || c2 < ba[b] || (c2 == ba[b] && a < ia[b])) { ba[b] = c2; ia[b] = (int32_t)a; }
+    }
+  }
+  int32_t* prev = (int32_t*)malloc(sizeof(int32_t) * (nt + 1));
+  for (int64_t t = 0; t < nt; t++) { link[t] = -1; prev[t] = -1; best_chi2[t] = bb[t]; }
+  for (int64_t a = 0; a < nt; a++)
+    if (ib[a] >= 0 && ia[ib[a]] == a) { link[a] = ib[a]; prev[ib[a]] = (int32_t)a; }
+  /* groups in the order of their innermost piece */
+  int64_t ng = 0;
+  for (int64_t r = 0; r < nt; r++) {
+    if (prev[r] >= 0) continue;
+    int np_ = 0, ncl = 0;
+    for (int64_t t = r; t >= 0; t = link[t]) { group_of[t] = (int32_t)ng; np_++; ncl += (int)(cnt[t + 1] - cnt[t]); }
+    g_first[ng] = (int32_t)lst[cnt[r]];
+    g_ncl[ng] = ncl;
+    g_npieces[ng] = np_;
+    if (np_ == 1) {
+      gfit[ng] = fits[r];
+    } else {
+      double* x = (double*)malloc(sizeof(double) * 4 * ncl);
+      double *y = x + ncl, *z = x + 2 * ncl, *al = x + 3 * ncl;
+      int m = 0;
+      for (int64_t t = r; t >= 0; t = link[t])
+        for (int64_t q = cnt[t]; q < cnt[t + 1]; q++) {
+          int64_t X, Y, Z;
+          orc_coords(in, &cl[lst[q]], &X, &Y, &Z);
+          x[m] = (double)X * u; y[m] = (double)Y * u; z[m] = (double)Z * u;
+          al[m] = sector_alpha(cl[lst[q]].sector);
+          m++;
+        }
+      orc_fit_points_xs(P, ncl, x, y, z, al, &gfit[ng]);
+      free(x);
+    }
+    ng++;
+  }
+  free(cnt); free(lst); free(fill); free(sec); free(exit_side); free(entry_side); free(row_in);
+  free(row_out); free(bb); free(ba); free(ib); free(ia); free(prev);
+  return ng;
+}

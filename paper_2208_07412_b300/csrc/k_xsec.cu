@@ -1,0 +1,495 @@
+// k_xsec.cu — optional cross-sector merge (step 9 of the library's definition;
+// the paper's section "Hardware and data flow" names the full TPC tracking on
+// the EPN GPUs, and joining the pieces of a track that crosses a sector border
+// is this library's last step of it).
+//
+//   - a track exits through the +y (-y) edge of its sector when its outermost
+//     cluster lies within E = edge_cm / u of that edge of the pad plane
+//     (|Y| >= 256 (npads - 1) - E, integer u); it enters through an edge when its
+//     innermost cluster does;
+//   - candidate pairs: A exiting through +y (-y) of sector s, B entering through
+//     -y (+y) of the neighbouring sector s+1 (s-1) of the same side, A's
+//     outermost row below B's innermost row, neither fit flagged;
+//   - B's fitted state is rotated into A's frame (about the beam axis) and
+//     transported to A's reference x; chi2 = d^T (C_A + J C_B J^T)^-1 d;
+//   - mutual best pairs with chi2 <= chi2_cut link (64-bit atomicMin on
+//     (chi2 bits << 32 | index): ties to the lower index);
+//   - each chain of linked pieces becomes one track, refitted over all its
+//     clusters in FP32 (U D U^T factors, FP64 redo on a failed PD check) with
+//     the state and the factors rotated into a piece's frame before its first
+//     cluster is reached.
+// Rotation by delta = alpha_old - alpha_new of a state at x: the point (x, y)
+// maps to (x cos d - y sin d, x sin d + y cos d), the direction gains d; its
+// first-order Jacobian at the rotated reference (the point moves with y by
+// dx' = -sin d dy and is carried back along the helix): dy' = (cos d + tan(phi')
+// sin d) dy, dzeta' = dzeta + (tgl / cos(phi')) sin d dy, dsnp' = (cos d - sin d
+// snp / cos(phi)) dsnp + k sin d dy.  The factors follow by W = R U and a
+// modified weighted Gram-Schmidt re-triangularisation of W D W^T.
+#include "fit_common.cuh"
+
+namespace tpc {
+
+
+__device__ __forceinline__ unsigned long long n_tracks_x(const DevWork& W) {
+  const unsigned long long n = W.ctr[CTR_NTRK];
+  return n < W.cap_ch ? n : W.cap_ch;
+}
+
+__device__ __forceinline__ int side_code(int Y, int np, int E) {
+  const int hw = 256 * (np - 1);
+  return Y >= hw - E ? 1 : (Y <= -(hw - E) ? 2 : 0);
+}
+
+__device__ __forceinline__ float sector_alpha(int phys) {
+  return ((float)(phys % 18) + 0.5f) * (20.f * 3.14159265358979f / 180.f);
+}
+
+__global__ void k_xs_ends(DevGeom G, DevWork W, XsWork X) {
+  const unsigned long long nt = n_tracks_x(W);
+  for (unsigned long long t = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; t < nt;
+       t += (unsigned long long)gridDim.x * blockDim.x) {
+    const int n = W.trk_ncl[t];
+    const int off = W.trk_off[t];
+    const int4 pi = W.trk_xyz[off], po = W.trk_xyz[off + n - 1];
+    const int ri = (__ldg(reinterpret_cast<const uint4*>(W.clusters) + pi.w).z >> 24) & 0xff;
+    const int ro = (__ldg(reinterpret_cast<const uint4*>(W.clusters) + po.w).z >> 24) & 0xff;
+    X.side[t] = (uint8_t)(side_code(po.y, G.npads[ro], X.edge_u) | (side_code(pi.y, G.npads[ri], X.edge_u) << 2));
+    X.row_in[t] = ri;
+    X.row_out[t] = ro;
+    X.best_b[t] = ~0ull;
+    X.best_a[t] = ~0ull;
+    X.link[t] = -1;
+    X.prev[t] = -1;
+  }
+}
+
+// State + covariance (dense) of a fitted track record.
+__device__ __forceinline__ void load_fit(const tpc_track& tr, float* s, float (&C)[5][5]) {
+#pragma unroll
+  for (int i = 0; i < 5; i++) s[i] = tr.par[i];
+  int m = 0;
+#pragma unroll
+  for (int i = 0; i < 5; i++)
+#pragma unroll
+    for (int j = 0; j <= i; j++) { C[i][j] = tr.cov[m]; C[j][i] = tr.cov[m]; m++; }
+}
+
+// Rotation of a state at x by delta (see the header comment); fills the
+// nonzero off-identity entries of R.  false if |snp| would reach 0.999.
+struct Rot { float r00, r10, r20, r22; };
+__device__ __forceinline__ bool rotate_state(float kfac, float* s, float& x, float delta, Rot& R) {
+  float sd, cd;
+  sincosf(delta, &sd, &cd);
+  const float sn = s[2];
+  if (fabsf(sn) >= 0.999f) return false;
+  const float cs = sqrtf(1.f - sn * sn);
+  const float sn2 = sn * cd + cs * sd;
+  if (fabsf(sn2) >= 0.999f) return false;
+  const float cs2 = sqrtf(1.f - sn2 * sn2);
+  R.r00 = cd + (sn2 / cs2) * sd;
+  R.r10 = (s[3] / cs2) * sd;
+  R.r20 = kfac * s[4] * sd;
+  R.r22 = cd - sd * sn / cs;
+  const float xn = x * cd - s[0] * sd;
+  const float yn = x * sd + s[0] * cd;
+  s[0] = yn;
+  s[2] = sn2;
+  x = xn;
+  return true;
+}
+
+// chi2 = d^T M^-1 d for a symmetric positive definite 5x5 M (Cholesky); -1 if not PD.
+__device__ __forceinline__ float chi2_spd(float (&M)[5][5], const float* d) {
+  float L[5][5];
+#pragma unroll
+  for (int j = 0; j < 5; j++) {
+    float acc = M[j][j];
+#pragma unroll
+    for (int k = 0; k < j; k++) acc -= L[j][k] * L[j][k];
+    if (!(acc > 0.f)) return -1.f;
+    L[j][j] = sqrtf(acc);
+    const float inv = 1.f / L[j][j];
+#pragma unroll
+    for (int i = j + 1; i < 5; i++) {
+      float a = M[i][j];
+#pragma unroll
+      for (int k = 0; k < j; k++) a -= L[i][k] * L[j][k];
+      L[i][j] = a * inv;
+    }
+  }
+  float w[5], c2 = 0.f;
+#pragma unroll
+  for (int i = 0; i < 5; i++) {
+    float a = d[i];
+#pragma unroll
+    for (int k = 0; k < i; k++) a -= L[i][k] * w[k];
+    w[i] = a / L[i][i];
+    c2 += w[i] * w[i];
+  }
+  return c2;
+}
+
+// Matching chi2 of A (inner piece) and B (outer piece); -1 if B cannot be
+// carried to A's reference.
+__device__ float xs_chi2(float kfac, const tpc_track& A, const tpc_track& B) {
+  float sa[5], sb[5], CA[5][5], CB[5][5];
+  load_fit(A, sa, CA);
+  load_fit(B, sb, CB);
+  float x = B.x;
+  Rot R;
+  if (!rotate_state(kfac, sb, x, B.alpha - A.alpha, R)) return -1.f;
+  Jac<float> F;
+  if (!transport(kfac, sb, A.x - x, F)) return -1.f;
+  // J = F R: F unit upper triangular with a = F02, b = F04, e = F12, g = F13,
+  // h = F14, m = F24; R identity except r00, r10, r20, r22
+  float J[5][5];
+#pragma unroll
+  for (int i = 0; i < 5; i++)
+#pragma unroll
+    for (int j = 0; j < 5; j++) J[i][j] = (i == j) ? 1.f : 0.f;
+  J[0][0] = R.r00 + F.a * R.r20;
+  J[0][2] = F.a * R.r22;
+  J[0][3] = 0.f;
+  J[0][4] = F.b;
+  J[1][0] = R.r10 + F.e * R.r20;
+  J[1][2] = F.e * R.r22;
+  J[1][3] = F.g;
+  J[1][4] = F.h;
+  J[2][0] = R.r20;
+  J[2][2] = R.r22;
+  J[2][4] = F.m;
+  // C = C_A + J C_B J^T
+  float T[5][5];
+#pragma unroll
+  for (int i = 0; i < 5; i++)
+#pragma unroll
+    for (int j = 0; j < 5; j++) {
+      float acc = 0.f;
+#pragma unroll
+      for (int l = 0; l < 5; l++) acc += J[i][l] * CB[l][j];
+      T[i][j] = acc;
+    }
+#pragma unroll
+  for (int i = 0; i < 5; i++)
+#pragma unroll
+    for (int j = 0; j < 5; j++) {
+      float acc = 0.f;
+#pragma unroll
+      for (int l = 0; l < 5; l++) acc += T[i][l] * J[j][l];
+      CA[i][j] += acc;
+    }
+  float d[5];
+#pragma unroll
+  for (int i = 0; i < 5; i++) d[i] = sa[i] - sb[i];
+  return chi2_spd(CA, d);
+}
+
+// First track whose lowest cluster is at or past c (tracks ascend by it).
+__device__ __forceinline__ unsigned lower_bound_first(const int32_t* first, unsigned n, unsigned c) {
+  unsigned lo = 0, hi = n;
+  while (lo < hi) {
+    const unsigned mid = (lo + hi) >> 1;
+    if ((unsigned)__ldg(first + mid) < c) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void k_xs_pairs(DevGeom G, DevParams P, DevWork W, XsWork X) {
+  const unsigned long long nt = n_tracks_x(W);
+  const int R = G.n_rows;
+  for (unsigned long long a = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; a < nt;
+       a += (unsigned long long)gridDim.x * blockDim.x) {
+    const int ex = X.side[a] & 3;
+    if (!ex) continue;
+    const tpc_track A = W.tracks[a];
+    if (A.flags) continue;
+    const int c0 = W.trk_first[a];
+    const int vs = vsector_of(G, W, (unsigned)c0, A.sector);
+    const int phys = vs % G.n_phys, base = vs - phys;
+    const int side_base = phys < 18 ? 0 : 18;
+    const int nphys = side_base + ((phys - side_base) + (ex == 1 ? 1 : 17)) % 18;
+    if (nphys >= G.n_phys) continue;
+    const int vb = base + nphys;
+    const unsigned b0 = lower_bound_first(W.trk_first, (unsigned)nt, W.row_start[vb * R]);
+    const unsigned b1 = lower_bound_first(W.trk_first, (unsigned)nt, W.row_start[vb * R + R]);
+    const int want_entry = ex == 1 ? 2 : 1;
+    const int ro = X.row_out[a];
+    unsigned long long best = ~0ull;
+    for (unsigned b = b0; b < b1; b++) {
+      if (((X.side[b] >> 2) & 3) != want_entry || X.row_in[b] <= ro) continue;
+      const tpc_track B = W.tracks[b];
+      if (B.flags) continue;
+      const float c2 = xs_chi2(P.kfac, A, B);
+      if (!(c2 >= 0.f) || c2 > X.chi2_cut) continue;
+      const unsigned long long cb = (unsigned long long)__float_as_uint(c2) << 32;
+      best = min(best, cb | b);
+      atomicMin(&X.best_a[b], cb | (unsigned)a);
+    }
+    X.best_b[a] = best;
+  }
+}
+
+__global__ void k_xs_link(DevWork W, XsWork X) {
+  const unsigned long long nt = n_tracks_x(W);
+  unsigned nl = 0;
+  for (unsigned long long a = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; a < nt;
+       a += (unsigned long long)gridDim.x * blockDim.x) {
+    const unsigned long long key = X.best_b[a];
+    if (key == ~0ull) continue;
+    const unsigned b = (unsigned)key;
+    if ((unsigned)X.best_a[b] == (unsigned)a) {
+      X.link[a] = (int)b;
+      X.prev[b] = (int)a;
+      nl++;
+    }
+  }
+  nl = __reduce_add_sync(0xffffffffu, nl);
+  if ((threadIdx.x & 31) == 0 && nl) atomicAdd(&X.ctl[1], (unsigned long long)nl);
+}
+
+__global__ void k_xs_roots(DevWork W, XsWork X) {
+  const unsigned long long nt = n_tracks_x(W);
+  for (unsigned long long t = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; t < nt;
+       t += (unsigned long long)gridDim.x * blockDim.x)
+    X.scan[t] = X.prev[t] < 0 ? 1ull : 0ull;
+}
+
+// Point i of a chain walk: the piece's cluster list entry and frame.
+struct XsPoint { float x, y, z; int sector_phys; };
+
+__device__ __forceinline__ XsPoint xs_point(const DevGeom& G, const DevWork& W, int piece, int l, int Z0) {
+  const int4 p = W.trk_xyz[W.trk_off[piece] + l];
+  XsPoint q;
+  q.x = (float)p.x * kU;
+  q.y = (float)p.y * kU;
+  q.z = (float)(p.z - Z0) * kU;
+  q.sector_phys = (int)(__ldg(reinterpret_cast<const uint4*>(W.clusters) + p.w).w >> 24);
+  return q;
+}
+
+// U D U^T <- R U D U^T R^T for the sparse rotation Jacobian, by W = R U and a
+// modified weighted Gram-Schmidt re-triangularisation (D-weighted rows,
+// last to first).
+__device__ __forceinline__ void ud_rotate(UD<float>& M, const Rot& R) {
+  float w[5][5];
+#pragma unroll
+  for (int i = 0; i < 5; i++)
+#pragma unroll
+    for (int j = 0; j < 5; j++) w[i][j] = (i == j) ? 1.f : (j > i ? M.u[i][j] : 0.f);
+#pragma unroll
+  for (int j = 0; j < 5; j++) {
+    const float u0 = w[0][j], u2 = w[2][j];
+    w[1][j] += R.r10 * u0;
+    w[2][j] = R.r22 * u2 + R.r20 * u0;
+    w[0][j] = R.r00 * u0;
+  }
+  float d[5];
+#pragma unroll
+  for (int k = 0; k < 5; k++) d[k] = M.d[k];
+#pragma unroll
+  for (int j = 4; j >= 0; j--) {
+    float dj = 0.f;
+#pragma unroll
+    for (int k = 0; k < 5; k++) dj += d[k] * w[j][k] * w[j][k];
+    M.d[j] = dj;
+    const float inv = 1.f / dj;
+#pragma unroll
+    for (int i = 0; i < j; i++) {
+      float uij = 0.f;
+#pragma unroll
+      for (int k = 0; k < 5; k++) uij += d[k] * w[i][k] * w[j][k];
+      uij *= inv;
+      M.u[i][j] = uij;
+#pragma unroll
+      for (int k = 0; k < 5; k++) w[i][k] -= uij * w[j][k];
+    }
+  }
+}
+
+// One (y, zeta) measurement in FP32 with the FP64 redo on a failed PD check.
+__device__ __forceinline__ float xs_measure(const DevParams& P, float* s, UD<float>& M, float y, float z,
+                                            int& flags, int& nfp64) {
+  float s0[5];
+  UD<float> M0 = M;
+#pragma unroll
+  for (int a = 0; a < 5; a++) s0[a] = s[a];
+  float dchi = ud_update<float, 0>(s, M, y, P.sy2);
+  dchi += ud_update<float, 1>(s, M, z, P.sz2);
+  if (!ud_pd(M)) {
+    double sd[5];
+    UD<double> Md;
+#pragma unroll
+    for (int a = 0; a < 5; a++) {
+      sd[a] = s0[a];
+      Md.d[a] = M0.d[a];
+#pragma unroll
+      for (int b = 0; b < 5; b++) Md.u[a][b] = M0.u[a][b];
+    }
+    double dd = ud_update<double, 0>(sd, Md, (double)y, P.sy2_d);
+    dd += ud_update<double, 1>(sd, Md, (double)z, P.sz2_d);
+    if (!ud_pd(Md)) flags |= TPC_TRK_NOT_PD;
+#pragma unroll
+    for (int a = 0; a < 5; a++) {
+      s[a] = (float)sd[a];
+      M.d[a] = (float)Md.d[a];
+#pragma unroll
+      for (int b = 0; b < 5; b++) M.u[a][b] = (float)Md.u[a][b];
+    }
+    dchi = (float)dd;
+    nfp64++;
+  }
+  return dchi;
+}
+
+// One thread per merged track (a root piece): numbering, piece assignment,
+// record copy (one piece) or multi-frame refit (several).
+__global__ void k_xs_emit(DevGeom G, DevParams P, DevWork W, XsWork X) {
+  const unsigned long long nt = n_tracks_x(W);
+  for (unsigned long long r = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; r < nt;
+       r += (unsigned long long)gridDim.x * blockDim.x) {
+    if (X.prev[r] >= 0) continue;
+    const int g = (int)X.scan[r];
+    int npieces = 0, ncl = 0, last = (int)r;
+    for (int t = (int)r; t >= 0 && npieces < 64; t = X.link[t]) {
+      X.group[t] = g;
+      npieces++;
+      ncl += W.trk_ncl[t];
+      last = t;
+    }
+    if (npieces == 1) {
+      X.tracks_out[g] = W.tracks[r];
+      continue;
+    }
+    // ---- refit over all pieces: points innermost (root, cluster 0) first
+    const int Z0 = W.trk_xyz[W.trk_off[r]].z;
+    const int mid = (ncl - 1) / 2;
+    XsPoint p1 = xs_point(G, W, (int)r, 0, Z0), p3 = xs_point(G, W, last, W.trk_ncl[last] - 1, Z0), p2 = p1;
+    {
+      int t = (int)r, base = 0;
+      while (t >= 0 && base + W.trk_ncl[t] <= mid) { base += W.trk_ncl[t]; t = X.link[t]; }
+      if (t >= 0) p2 = xs_point(G, W, t, mid - base, Z0);
+    }
+    const float a3 = sector_alpha(p3.sector_phys);
+    auto in_frame3 = [&](const XsPoint& q, float& xo, float& yo) {
+      float sd, cd;
+      sincosf(sector_alpha(q.sector_phys) - a3, &sd, &cd);
+      xo = q.x * cd - q.y * sd;
+      yo = q.x * sd + q.y * cd;
+    };
+    float x1, y1, x2, y2, x3, y3;
+    in_frame3(p1, x1, y1);
+    in_frame3(p2, x2, y2);
+    in_frame3(p3, x3, y3);
+    const float ax = x2 - x1, ay = y2 - y1, cx = x3 - x1, cy = y3 - y1;
+    const float bx = cx - ax, by = cy - ay;
+    const float la = sqrtf(ax * ax + ay * ay), lb = sqrtf(bx * bx + by * by), lc = sqrtf(cx * cx + cy * cy);
+    const float kc = 2.f * (ax * cy - ay * cx) / (la * lb * lc);
+    const float hh = fminf(1.f, fmaxf(-1.f, 0.5f * kc * lc));
+    const float half = asinf(hh);
+    const float phic = atan2f(cy, cx);
+    const float klc = kc * lc;
+    const float arc = fabsf(klc) < 1e-3f ? lc * (1.f + klc * klc * (1.f / 24.f)) : 2.f * half / kc;
+    float s[5] = {y3, p3.z, sinf(phic + half), (p3.z - p1.z) / arc, kc / P.kfac};
+    UD<float> M;
+    float xcur = p3.x, acur = a3;
+    int flags = 0, n_used = 0, nfp64 = 0;
+    float chi2 = 0.f;
+    for (int pass = 0; pass < P.fit_passes; pass++) {
+      ud_reset(M, P.c0);
+      chi2 = 0.f;
+      n_used = 0;
+      const bool inward = (pass & 1) == 0;
+      int t = inward ? last : (int)r;
+      int l = inward ? W.trk_ncl[last] - 1 : 0;
+      for (int jj = 0; jj < ncl && t >= 0; jj++) {
+        const XsPoint q = xs_point(G, W, t, l, Z0);
+        const float aq = sector_alpha(q.sector_phys);
+        if (aq != acur) {
+          Rot Rr;
+          if (!rotate_state(P.kfac, s, xcur, acur - aq, Rr)) { flags |= TPC_TRK_STOPPED; break; }
+          ud_rotate(M, Rr);
+          acur = aq;
+        }
+        const float dx = q.x - xcur;
+        if (dx != 0.f) {
+          Jac<float> J;
+          if (!transport(P.kfac, s, dx, J)) { flags |= TPC_TRK_STOPPED; break; }
+          ud_propagate(M, J);
+          xcur = q.x;
+        }
+        chi2 += xs_measure(P, s, M, q.y, q.z, flags, nfp64);
+        n_used++;
+        // next point along the chain
+        if (inward) {
+          if (--l < 0) { t = X.prev[t]; if (t >= 0) l = W.trk_ncl[t] - 1; }
+        } else {
+          if (++l >= W.trk_ncl[t]) { t = X.link[t]; l = 0; }
+        }
+      }
+    }
+    tpc_track out;
+    out.par[0] = s[0];
+    out.par[1] = s[1] + (float)Z0 * kU;
+    out.par[2] = s[2];
+    out.par[3] = s[3];
+    out.par[4] = s[4];
+    out.x = xcur;
+    out.alpha = acur;
+    out.chi2 = chi2;
+    int m = 0;
+#pragma unroll
+    for (int i = 0; i < 5; i++)
+#pragma unroll
+      for (int j = 0; j <= i; j++) {
+        float acc = M.d[i] * (j == i ? 1.f : M.u[j][i]);
+#pragma unroll
+        for (int k = i + 1; k < 5; k++) acc += M.u[i][k] * M.d[k] * M.u[j][k];
+        out.cov[m++] = acc;
+      }
+    out.ndf = 2 * n_used - 5;
+    out.n_clusters = ncl;
+    out.first_cluster = W.trk_first[r];
+    out.sector = W.tracks[r].sector;
+    out.flags = (uint16_t)(flags | TPC_TRK_XSECTOR);
+    out.n_fp64 = nfp64;
+    X.tracks_out[g] = out;
+  }
+}
+
+__global__ void k_xs_map(DevWork W, XsWork X) {
+  unsigned long long n = W.ctr[CTR_NCL];
+  if (n > W.cap_cl) n = W.cap_cl;
+  for (unsigned long long c = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; c < n;
+       c += (unsigned long long)gridDim.x * blockDim.x) {
+    const int t = W.cl2trk[c];
+    X.cl2trk_out[c] = t >= 0 ? X.group[t] : -1;
+  }
+}
+
+cudaError_t launch_scan(uint64_t* v, const unsigned long long* n_ptr, unsigned long long cap,
+                        unsigned long long* state, unsigned int* ticket, unsigned long long* total, uint32_t* err,
+                        int n_sm, cudaStream_t st);
+
+static inline unsigned grid_x(unsigned long long cap, int n_sm, int per_sm) {
+  unsigned long long g = (cap + 255) / 256;
+  const unsigned long long m = (unsigned long long)n_sm * per_sm;
+  if (g > m) g = m;
+  return (unsigned)(g ? g : 1);
+}
+
+cudaError_t launch_xsec(const DevGeom& G, const DevParams& P, const DevWork& W, const XsWork& X, int n_sm,
+                        cudaStream_t st) {
+  const unsigned g = grid_x(W.cap_ch, n_sm, 8);
+  k_xs_ends<<<g, 256, 0, st>>>(G, W, X);
+  k_xs_pairs<<<grid_x(W.cap_ch, n_sm, 16), 64, 0, st>>>(G, P, W, X);
+  k_xs_link<<<g, 256, 0, st>>>(W, X);
+  k_xs_roots<<<g, 256, 0, st>>>(W, X);
+  cudaError_t e = launch_scan(X.scan, W.ctr + CTR_NTRK, W.cap_ch, X.scan_state,
+                              reinterpret_cast<unsigned int*>(X.ctl + 2), X.ctl, W.err, n_sm, st);
+  if (e != cudaSuccess) return e;
+  k_xs_emit<<<grid_x(W.cap_ch, n_sm, 16), 64, 0, st>>>(G, P, W, X);
+  k_xs_map<<<grid_x(W.cap_cl, n_sm, 8), 256, 0, st>>>(W, X);
+  return cudaGetLastError();
+}
+
+}  // namespace tpc

@@ -29,6 +29,7 @@ cudaError_t launch_merge(const DevGeom&, const DevParams&, const DevWork&, int, 
 cudaError_t launch_fit(const DevGeom&, const DevParams&, const DevWork&, int, const LaunchCfg&, cudaStream_t, int*);
 size_t scan_tiles(unsigned long long cap);
 cudaError_t prepare_find();
+cudaError_t launch_xsec(const DevGeom&, const DevParams&, const DevWork&, const XsWork&, int, cudaStream_t);
 }  // namespace tpc
 
 using namespace tpc;
@@ -64,13 +65,17 @@ struct Slot {
   // device buffers
   Buf pages, offsets, winstate, cl, clx, cly, clz, clt, rowstart, chrow, up, down, score, edge, jump, chlen, scanv,
       scanst, chainof, clchain, ch_i32, besta, bestb, trk_i32, trackcl, cl2trk, tracks, ctrl, scratch, wincnt, winsoff,
-      candab, candsc, lenhist, evinfo;
+      candab, candsc, lenhist, evinfo, xs;
   unsigned long long* h_ctrl = nullptr;   // pinned copy of [ctr | err]
   // batch tables, device (evinfo) and pinned host copy, same layout:
   // u64 base[kMaxBatch], u64 bytes[kMaxBatch], u32 cl_start[kMaxBatch + 1],
   // u32 trk_start[kMaxBatch + 1]
   uint64_t* h_ev = nullptr;
   uint32_t n_events = 1;
+  // cross-sector merge results of the current ticket (tpc_merge_sectors)
+  bool xs_done = false;
+  uint64_t xs_n = 0, xs_links = 0;
+  size_t xs_bytes = 0;
   // capacities
   uint64_t cap_pages = 0, cap_windows = 0, cap_cl = 0, cap_ch = 0;
   // ticket
@@ -303,7 +308,7 @@ static void slot_free(tpc_context* ctx, Slot& s) {
   Buf* all[] = {&s.pages, &s.offsets, &s.winstate, &s.cl, &s.clx, &s.cly, &s.clz, &s.clt, &s.rowstart, &s.chrow, &s.up,
                 &s.down, &s.score, &s.edge, &s.jump, &s.chlen, &s.scanv, &s.scanst, &s.chainof, &s.clchain,
                 &s.ch_i32, &s.besta, &s.bestb, &s.trk_i32, &s.trackcl, &s.cl2trk, &s.tracks, &s.ctrl,
-                &s.scratch, &s.wincnt, &s.winsoff, &s.candab, &s.candsc, &s.lenhist, &s.evinfo};
+                &s.scratch, &s.wincnt, &s.winsoff, &s.candab, &s.candsc, &s.lenhist, &s.evinfo, &s.xs};
   for (Buf* b : all) free_buf(*b);
   for (auto& e : s.ev_stage) if (e) cudaEventDestroy(e);
   if (s.ev_done) cudaEventDestroy(s.ev_done);
@@ -541,6 +546,7 @@ static tpc_status check_desc(const tpc_timeframe_desc* tf) {
 static tpc_status start_timeframe(tpc_context* ctx, Slot* s, const tpc_timeframe_desc* tf) {
   const bool dev_in = tf->flags & TPC_TF_DEVICE_INPUT;
   s->n_events = 1;
+  s->xs_done = false;
   const unsigned nfrag = (tf->n_time_bins + kFrag - 1) / kFrag;
   const uint64_t nwin = (uint64_t)ctx->geom.n_sectors * ctx->geom.n_rows * nfrag;
   if (nwin > 0xffffffffull) return fail(TPC_E_INVAL, "too many windows");
@@ -571,6 +577,7 @@ static tpc_status start_timeframe(tpc_context* ctx, Slot* s, const tpc_timeframe
 // Start a batch of events on free slot s (lock held); descriptors validated.
 static tpc_status start_batch(tpc_context* ctx, Slot* s, const tpc_timeframe_desc* tfs, uint32_t n_events) {
   const uint32_t T = tfs[0].n_time_bins;
+  s->xs_done = false;
   std::vector<uint64_t> base(n_events), bytes(n_events);
   uint64_t total = 0;
   for (uint32_t e = 0; e < n_events; e++) {
@@ -639,8 +646,11 @@ static void reclaim_idle(tpc_context* ctx, const Slot* keep) {
     Buf* big[] = {&c.pages, &c.offsets, &c.winstate, &c.cl, &c.clx, &c.cly, &c.clz, &c.clt, &c.up, &c.down,
                   &c.score, &c.edge, &c.jump, &c.chlen, &c.scanv, &c.scanst, &c.chainof, &c.clchain, &c.ch_i32,
                   &c.besta, &c.bestb, &c.trk_i32, &c.trackcl, &c.cl2trk, &c.tracks, &c.scratch, &c.wincnt,
-                  &c.winsoff, &c.candab, &c.candsc};
+                  &c.winsoff, &c.candab, &c.candsc, &c.xs};
     for (Buf* b : big) free_buf(*b);
+    ctx->used -= c.xs_bytes;
+    c.xs_bytes = 0;
+    c.xs_done = false;
     c.cap_pages = c.cap_windows = c.cap_cl = c.cap_ch = 0;
   }
 }
@@ -944,6 +954,91 @@ extern "C" tpc_status tpc_get_event_tracks(tpc_context* ctx, uint64_t ticket, ui
   if (cluster_to_track)
     for (uint64_t i = 0; i < c1 - c0; i++)
       if (cluster_to_track[i] >= 0) cluster_to_track[i] -= (int32_t)t0;
+  return TPC_OK;
+}
+
+// ------------------------------------------------------------------ step 9
+extern "C" tpc_status tpc_merge_sectors(tpc_context* ctx, uint64_t ticket, const tpc_xs_params* xp,
+                                        uint64_t* n_tracks) {
+  if (!ctx) return fail(TPC_E_INVAL, "tpc_merge_sectors: null argument");
+  const double chi2_cut = xp ? xp->chi2_cut : 100.0, edge_cm = xp ? xp->edge_cm : 6.0;
+  if (!(chi2_cut >= 0.0) || !(edge_cm >= 0.0) || edge_cm > 100.0) return fail(TPC_E_INVAL, "tpc_merge_sectors: bad parameters");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  Slot* s;
+  tpc_status st = done_slot(ctx, ticket, &s);
+  if (st) return st;
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  const uint64_t C = s->cap_ch, Ncl = s->cap_cl;
+  const size_t tiles = scan_tiles(C);
+  auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  const size_t need = al(C) + 2 * al(C * 4) + 2 * al(C * 8) + 3 * al(C * 4) + al(C * 8) + al(tiles * 8) + al(64) +
+                      al(C * sizeof(tpc_track)) + al(Ncl * 4);
+  if (need > s->xs.bytes) {
+    if (ctx->used - s->xs_bytes + need > ctx->budget) return fail(TPC_E_NOMEM, "tpc_merge_sectors: over the memory budget");
+    CUDA_TRY(ensure(s->xs, need));
+    ctx->used = ctx->used - s->xs_bytes + need;
+    s->xs_bytes = need;
+  }
+  uint8_t* p = (uint8_t*)s->xs.p;
+  XsWork X;
+  auto take = [&](size_t b) { uint8_t* q = p; p += al(b); return q; };
+  X.side = take(C);
+  X.row_in = (int32_t*)take(C * 4);
+  X.row_out = (int32_t*)take(C * 4);
+  X.best_b = (unsigned long long*)take(C * 8);
+  X.best_a = (unsigned long long*)take(C * 8);
+  X.link = (int32_t*)take(C * 4);
+  X.prev = (int32_t*)take(C * 4);
+  X.group = (int32_t*)take(C * 4);
+  X.scan = (uint64_t*)take(C * 8);
+  X.scan_state = (unsigned long long*)take(tiles * 8);
+  X.ctl = (unsigned long long*)take(64);
+  X.tracks_out = (tpc_track*)take(C * sizeof(tpc_track));
+  X.cl2trk_out = (int32_t*)take(Ncl * 4);
+  X.chi2_cut = (float)chi2_cut;
+  X.edge_u = (int)std::floor(edge_cm / 7.8125e-4 + 0.5);
+  DevGeom G = ctx->G;
+  G.n_time_bins = (int)s->n_time_bins;
+  G.n_frag = (int)((s->n_time_bins + kFrag - 1) / kFrag);
+  G.n_events = (int)s->n_events;
+  G.n_sectors = ctx->geom.n_sectors * (int)s->n_events;
+  CUDA_TRY(cudaMemsetAsync(X.scan_state, 0, tiles * 8, s->stream));
+  CUDA_TRY(cudaMemsetAsync(X.ctl, 0, 64, s->stream));
+  CUDA_TRY(launch_xsec(G, ctx->P, s->W, X, ctx->n_sm, s->stream));
+  unsigned long long ctl[2];
+  CUDA_TRY(cudaMemcpyAsync(ctl, X.ctl, 16, cudaMemcpyDeviceToHost, s->stream));
+  CUDA_TRY(cudaStreamSynchronize(s->stream));
+  s->xs_done = true;
+  s->xs_n = ctl[0];
+  s->xs_links = ctl[1];
+  if (n_tracks) *n_tracks = s->xs_n;
+  return TPC_OK;
+}
+
+extern "C" tpc_status tpc_get_merged_tracks(tpc_context* ctx, uint64_t ticket, tpc_track* out, uint64_t cap,
+                                            uint64_t* n, int32_t* cluster_to_track, int32_t* link) {
+  if (!ctx || !n) return fail(TPC_E_INVAL, "tpc_get_merged_tracks: null argument");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  Slot* s;
+  tpc_status st = done_slot(ctx, ticket, &s);
+  if (st) return st;
+  if (!s->xs_done) return fail(TPC_E_NOTREADY, "tpc_merge_sectors has not run on this ticket");
+  *n = s->xs_n;
+  if (!out && !cluster_to_track && !link) return TPC_OK;
+  if (out && cap < *n) return fail(TPC_E_OVERFLOW, "output buffer too small");
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  const uint64_t C = s->cap_ch;
+  auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  const uint8_t* base = (const uint8_t*)s->xs.p;
+  const size_t o_link = al(C) + 2 * al(C * 4) + 2 * al(C * 8);
+  const size_t o_tracks = o_link + 3 * al(C * 4) + al(C * 8) + al(scan_tiles(C) * 8) + al(64);
+  const size_t o_map = o_tracks + al(C * sizeof(tpc_track));
+  const uint64_t ncl = n_cl_of(*s), ntr = n_trk_of(*s);
+  if (out && *n) CUDA_TRY(cudaMemcpyAsync(out, base + o_tracks, *n * sizeof(tpc_track), cudaMemcpyDeviceToHost, s->stream));
+  if (cluster_to_track && ncl)
+    CUDA_TRY(cudaMemcpyAsync(cluster_to_track, base + o_map, ncl * 4, cudaMemcpyDeviceToHost, s->stream));
+  if (link && ntr) CUDA_TRY(cudaMemcpyAsync(link, base + o_link, ntr * 4, cudaMemcpyDeviceToHost, s->stream));
+  CUDA_TRY(cudaStreamSynchronize(s->stream));
   return TPC_OK;
 }
 

@@ -246,6 +246,25 @@ __device__ __forceinline__ unsigned long long lookback_wait(unsigned long long* 
   return excl;
 }
 
+// Work space of the optional cross-sector merge (step 9), in one slot buffer.
+struct XsWork {
+  uint8_t* side;                 // [cap_ch] exit side (bits 0-1: 1 = +y, 2 = -y), entry side (bits 2-3)
+  int32_t* row_in;               // [cap_ch] row of the innermost cluster
+  int32_t* row_out;              // [cap_ch] row of the outermost cluster
+  unsigned long long* best_b;    // [cap_ch] best outer partner of A: chi2 bits << 32 | B
+  unsigned long long* best_a;    // [cap_ch] best inner partner of B
+  int32_t* link;                 // [cap_ch] outer piece or -1
+  int32_t* prev;                 // [cap_ch] inner piece or -1
+  int32_t* group;                // [cap_ch] merged track of every piece
+  uint64_t* scan;                // [cap_ch] root flags, scanned to merged track indices
+  unsigned long long* scan_state;
+  unsigned long long* ctl;       // [0] merged tracks, [1] links, [2] (u32) scan ticket
+  tpc_track* tracks_out;         // [cap_ch]
+  int32_t* cl2trk_out;           // [cap_cl]
+  float chi2_cut;
+  int edge_u;
+};
+
 // Warp-aggregated atomicAdd of 1 on one counter: the lanes that call it
 // together take consecutive values with a single atomic (correct under
 // independent thread scheduling: the group is whoever is converged here).

@@ -71,6 +71,10 @@ class tpc_tuning(ctypes.Structure):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
 
 
+class tpc_xs_params(ctypes.Structure):
+    _fields_ = [("chi2_cut", ctypes.c_double), ("edge_cm", ctypes.c_double)]
+
+
 class tpc_timeframe_desc(ctypes.Structure):
     _fields_ = [("pages", _P), ("pages_bytes", _u64), ("page_offsets", _P),
                 ("n_time_bins", ctypes.c_uint32), ("flags", ctypes.c_uint32)]
@@ -81,7 +85,7 @@ EXPORTS = ("tpc_params_default", "tpc_create_geometry", "tpc_destroy_geometry", 
            "tpc_get_tracks", "tpc_get_links", "tpc_get_device_results", "tpc_get_stage_times",
            "tpc_get_counters", "tpc_release", "tpc_last_error", "tpc_find_clusters_noalloc",
            "tpc_submit_batch", "tpc_get_batch_info", "tpc_get_event_clusters", "tpc_get_event_tracks",
-           "tpc_get_tuning", "tpc_set_tuning", "tpc_autotune")
+           "tpc_get_tuning", "tpc_set_tuning", "tpc_autotune", "tpc_merge_sectors", "tpc_get_merged_tracks")
 
 _lib = None
 
@@ -128,6 +132,8 @@ def load(build_if_missing: bool = True):
     L.tpc_get_tuning.argtypes = [_P, ctypes.POINTER(tpc_tuning)]
     L.tpc_set_tuning.argtypes = [_P, ctypes.POINTER(tpc_tuning)]
     L.tpc_autotune.argtypes = [_P, ctypes.POINTER(tpc_timeframe_desc), ctypes.c_int, ctypes.POINTER(tpc_tuning)]
+    L.tpc_merge_sectors.argtypes = [_P, _u64, ctypes.POINTER(tpc_xs_params), ctypes.POINTER(_u64)]
+    L.tpc_get_merged_tracks.argtypes = [_P, _u64, _P, _u64, ctypes.POINTER(_u64), _P, _P]
     L.tpc_last_error.argtypes = []
     L.tpc_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -276,6 +282,30 @@ def tpc_autotune(ctx, pages, page_offsets, n_time_bins: int, reps: int = 3) -> d
     t = tpc_tuning()
     _check(load().tpc_autotune(ctx, ctypes.byref(d), int(reps), ctypes.byref(t)))
     return t.as_dict()
+
+
+TPC_TRK_XSECTOR = 4
+
+
+def tpc_merge_sectors(ctx, ticket: int, chi2_cut: float = 100.0, edge_cm: float = 6.0) -> int:
+    """Cross-sector merge of a finished ticket; returns the number of tracks after it."""
+    n = _u64()
+    xp = tpc_xs_params(float(chi2_cut), float(edge_cm))
+    _check(load().tpc_merge_sectors(ctx, ticket, ctypes.byref(xp), ctypes.byref(n)))
+    return int(n.value)
+
+
+def tpc_get_merged_tracks(ctx, ticket: int, n_clusters: int, n_tracks: int):
+    """Returns (merged tracks, cluster_to_track, link per step-8 track)."""
+    L = load()
+    n = _u64()
+    _check(L.tpc_get_merged_tracks(ctx, ticket, None, 0, ctypes.byref(n), None, None))
+    out = np.zeros(n.value, TRACK_DTYPE)
+    m = np.zeros(n_clusters, np.int32)
+    link = np.zeros(n_tracks, np.int32)
+    _check(L.tpc_get_merged_tracks(ctx, ticket, out.ctypes.data if n.value else None, n.value, ctypes.byref(n),
+                                   m.ctypes.data if n_clusters else None, link.ctypes.data if n_tracks else None))
+    return out, m, link
 
 
 def tpc_poll(ctx, ticket: int, timeout_us: int = 0xFFFFFFFF) -> int:
