@@ -403,6 +403,35 @@ def cross_sector_timing(tpc, torch, R, pages_d, offs_d, tf, reps=5):
             "links": n_in - n_out, "timing": f"host wall clock of the call, median of {reps}"}
 
 
+def compression_stats(tpc, R, pages_d, offs_d, tf, reps=5):
+    """The optional step 10 (tpc_compress_clusters): time of the call and the
+    size of the position information of the clusters on tracks, as the Shannon
+    entropy of the residual codes against the 32 bits of the raw (pad_fp,
+    time_fp) pair."""
+    t = R.submit(pages_d, offs_d, tf.n_time_bins)
+    R.wait(t)
+    n_cl = tpc.tpc_get_counters(R.ctx, t)["clusters"]
+    tpc.tpc_compress_clusters(R.ctx, t)   # warm-up (allocates its work space)
+    times = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        coded, escaped = tpc.tpc_compress_clusters(R.ctx, t)
+        times.append(time.perf_counter() - t0)
+    cy, cz, st = tpc.tpc_get_compressed(R.ctx, t, n_cl)
+    tpc.tpc_release(R.ctx, t)
+
+    def entropy(v):
+        _, c = np.unique(v, return_counts=True)
+        p = c / c.sum()
+        return float(-(p * np.log2(p)).sum())
+    ok = st == 1
+    bits = entropy(cy[ok]) + entropy(cz[ok]) if ok.any() else 0.0
+    return {"ms": 1e3 * statistics.median(times), "clusters": int(n_cl), "coded": coded, "escaped": escaped,
+            "position_bits_per_coded_cluster": bits, "raw_position_bits": 32,
+            "position_compression": 32.0 / bits if bits else None,
+            "timing": f"host wall clock of the call, median of {reps}"}
+
+
 def run_ours(args, world, rank, local):
     import torch
     from paper_2208_07412_b300 import tpc
@@ -540,6 +569,7 @@ def run_ours(args, world, rank, local):
         }
         if world == 1 and args.workload == "full_tpc":
             line["cross_sector"] = cross_sector_timing(tpc, torch, R, pages_d, offs_d, tf)
+            line["compression"] = compression_stats(tpc, R, pages_d, offs_d, tf)
         if world == 1 and not args.no_batched and args.workload == "full_tpc":
             line["batched"] = batched_vs_plain(tpc, torch, local, tuning=tuning)
         if world == 1 and not args.no_cpu_baseline:

@@ -374,6 +374,36 @@ tpc_status tpc_merge_sectors(tpc_context* ctx, uint64_t ticket, const tpc_xs_par
 tpc_status tpc_get_merged_tracks(tpc_context* ctx, uint64_t ticket, tpc_track* out, uint64_t cap, uint64_t* n,
                                  int32_t* cluster_to_track, int32_t* link);
 
+/* Track-model compression parameters (step 10). */
+typedef struct {
+  double step_y_cm;  /* 0.0125    quantisation step of the y residual (1/32 pad) */
+  double step_z_cm;  /* 0.015625  quantisation step of the zeta residual (1/32 time bin) */
+} tpc_cmp_params;
+
+/* Step 10, optional: track-model compression of the clusters on the step-8
+ * tracks of a finished ticket (the paper gives the online reconstruction as
+ * the means to reduce the TPC data, "Hardware and data flow"; this is the
+ * library's definition):
+ *   - per track, its fitted parameters at the innermost cluster are carried
+ *     along the exact helix from row to row (the predicted state only, clusters
+ *     innermost first, no measurement updates);
+ *   - a cluster's codes are rint(residual / step) (ties away from zero) of its
+ *     measured y and zeta minus the prediction at its row;
+ *   - coded if both |codes| <= 127, else escaped (kept raw); clusters after a
+ *     failed transport are escaped;
+ *   - decoding: prediction + code * step, within half a step of the measured
+ *     position.
+ * cp: NULL for the defaults.  *n_coded / *n_escaped may be NULL.  Runs on the
+ * ticket's stream and waits; results until tpc_release.
+ * Errors: TPC_E_NOTREADY, TPC_E_NOTFOUND, TPC_E_INVAL, TPC_E_CUDA, TPC_E_NOMEM. */
+tpc_status tpc_compress_clusters(tpc_context* ctx, uint64_t ticket, const tpc_cmp_params* cp, uint64_t* n_coded,
+                                 uint64_t* n_escaped);
+
+/* Codes and status of every cluster (n_clusters entries each; any pointer may
+ * be NULL): status 0 not on a track, 1 coded (code_y, code_z valid), 2 escaped.
+ * TPC_E_NOTREADY if tpc_compress_clusters has not run on the ticket. */
+tpc_status tpc_get_compressed(tpc_context* ctx, uint64_t ticket, int8_t* code_y, int8_t* code_z, uint8_t* status);
+
 /* Layout of a finished ticket's results by event: *n_events (1 for a plain
  * timeframe) and, if not NULL, cluster_start[n_events + 1] and
  * track_start[n_events + 1], each event's first cluster / track in the

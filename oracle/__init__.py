@@ -134,6 +134,8 @@ def _load():
         L.orc_merge_sectors.argtypes = [_P, _P, _P, _P, ctypes.c_int64, _P, ctypes.c_int64, _P, _P, _P, _P,
                                         _P, _P, _P, _P]
         L.orc_merge_sectors.restype = ctypes.c_int64
+        L.orc_compress.argtypes = [_P, _P, _P, _P, ctypes.c_int64, _P, ctypes.c_int64, _P, _P, _P, _P]
+        L.orc_compress.restype = ctypes.c_int64
         _lib = L
     return _lib
 
@@ -392,6 +394,34 @@ def merge_sectors(tf, res, params: OracleParams | None = None, xs: XsParams | No
     new_c2t = np.where(c2t >= 0, grp[np.maximum(c2t, 0)], -1).astype(np.int32)
     return XsResult(link[:nt].copy(), best[:nt].copy(), grp[:nt].copy(), gfit[:ng].copy(), gf[:ng].copy(),
                     gn[:ng].copy(), gp[:ng].copy(), new_c2t)
+
+
+class _CmpParams(ctypes.Structure):
+    _fields_ = [("step_y", ctypes.c_double), ("step_z", ctypes.c_double)]
+
+
+STEP_Y = 0.4 / 32     # 1/32 pad, cm
+STEP_Z = 0.5 / 32     # 1/32 time bin, cm
+
+
+def compress(tf, res, step_y: float = STEP_Y, step_z: float = STEP_Z, params: OracleParams | None = None):
+    """Track-model compression of the clusters on an OracleResult's tracks
+    (step 10).  Returns (code_y, code_z, status) per cluster."""
+    L = _load()
+    p = (params or OracleParams())._c()
+    cp = _CmpParams(float(step_y), float(step_z))
+    inp = _In.from_tf(tf)
+    cl = np.ascontiguousarray(res.clusters)
+    n = len(cl)
+    c2t = np.ascontiguousarray(res.cl2trk, np.int32)
+    fits = np.ascontiguousarray(res.fits)
+    cy = np.zeros(max(n, 1), np.int8)
+    cz = np.zeros(max(n, 1), np.int8)
+    st = np.zeros(max(n, 1), np.uint8)
+    L.orc_compress(inp.ref, ctypes.byref(p), ctypes.byref(cp), cl.ctypes.data if n else None, n,
+                   c2t.ctypes.data if n else None, len(fits), fits.ctypes.data if len(fits) else None,
+                   cy.ctypes.data, cz.ctypes.data, st.ctypes.data)
+    return cy[:n].copy(), cz[:n].copy(), st[:n].copy()
 
 
 @dataclass

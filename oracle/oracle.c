@@ -946,3 +946,66 @@ int64_t orc_merge_sectors(const orc_input* in, const orc_params* P, const orc_xs
   free(row_out); free(bb); free(ba); free(ib); free(ia); free(prev);
   return ng;
 }
+
+/* ------------------------------------------------------------ 10. track-model compression
+ * The paper gives online tracking as the way to compress TPC data ("Hardware
+ * and data flow": the reconstruction runs online to reduce the data); this is
+ * the library's definition of that compression of the clusters on tracks:
+ *   - the track model is the step-8 fit: parameters p at x0 (the innermost
+ *     cluster) carried along the exact helix from row to row (the predicted
+ *     state only, no measurement updates), clusters taken innermost first;
+ *   - a cluster's residuals are its measured (y, zeta) minus the prediction at
+ *     its row; codes = rint(residual / step) (ties away from zero) for steps
+ *     step_y, step_z;
+ *   - a cluster is coded if both |codes| <= 127, otherwise escaped (kept raw);
+ *     clusters after a failed transport are escaped;
+ *   - decoding: prediction + code * step; the coded position is within step/2.
+ * Output per cluster: status 0 (not on a track), 1 (coded), 2 (escaped). */
+typedef struct {
+  double step_y;   /* 0.0125 cm (1/32 pad) */
+  double step_z;   /* 0.015625 cm (1/32 time bin) */
+} orc_cmp_params;
+
+int64_t orc_compress(const orc_input* in, const orc_params* P, const orc_cmp_params* CP, const orc_cluster* cl,
+                     int64_t n, const int32_t* cl2trk, int64_t nt, const orc_fit* fits, int8_t* code_y,
+                     int8_t* code_z, uint8_t* status) {
+  const double u = 7.8125e-4;
+  for (int64_t i = 0; i < n; i++) { code_y[i] = 0; code_z[i] = 0; status[i] = 0; }
+  int64_t* cnt = (int64_t*)calloc((size_t)nt + 1, sizeof(int64_t));
+  for (int64_t i = 0; i < n; i++) if (cl2trk[i] >= 0) cnt[cl2trk[i] + 1]++;
+  for (int64_t t = 0; t < nt; t++) cnt[t + 1] += cnt[t];
+  int64_t* lst = (int64_t*)malloc(sizeof(int64_t) * (cnt[nt] + 1));
+  int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * (nt + 1));
+  memcpy(fill, cnt, sizeof(int64_t) * nt);
+  for (int64_t i = 0; i < n; i++) if (cl2trk[i] >= 0) lst[fill[cl2trk[i]]++] = i;
+  int64_t coded = 0;
+  for (int64_t t = 0; t < nt; t++) {
+    double s[5], x = fits[t].x;
+    for (int k = 0; k < 5; k++) s[k] = fits[t].par[k];
+    int ok = 1;
+    for (int64_t q = cnt[t]; q < cnt[t + 1]; q++) {
+      const int64_t c = lst[q];
+      int64_t X, Y, Z;
+      orc_coords(in, &cl[c], &X, &Y, &Z);
+      const double xc = (double)X * u;
+      if (ok && xc != x) {
+        double ns[5];
+        if (orc_transport(P, s, xc - x, ns, NULL)) ok = 0;
+        else { memcpy(s, ns, sizeof(ns)); x = xc; }
+      }
+      if (!ok) { status[c] = 2; continue; }
+      const double ry = ((double)Y * u - s[0]) / CP->step_y, rz = ((double)Z * u - s[1]) / CP->step_z;
+      const double cy = round(ry), cz = round(rz);
+      if (fabs(cy) <= 127.0 && fabs(cz) <= 127.0) {
+        code_y[c] = (int8_t)cy;
+        code_z[c] = (int8_t)cz;
+        status[c] = 1;
+        coded++;
+      } else {
+        status[c] = 2;
+      }
+    }
+  }
+  free(cnt); free(lst); free(fill);
+  return coded;
+}

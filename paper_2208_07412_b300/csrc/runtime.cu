@@ -30,6 +30,7 @@ cudaError_t launch_fit(const DevGeom&, const DevParams&, const DevWork&, int, co
 size_t scan_tiles(unsigned long long cap);
 cudaError_t prepare_find();
 cudaError_t launch_xsec(const DevGeom&, const DevParams&, const DevWork&, const XsWork&, int, cudaStream_t);
+cudaError_t launch_compress(const DevParams&, const DevWork&, const CmpWork&, int, cudaStream_t);
 }  // namespace tpc
 
 using namespace tpc;
@@ -65,7 +66,7 @@ struct Slot {
   // device buffers
   Buf pages, offsets, winstate, cl, clx, cly, clz, clt, rowstart, chrow, up, down, score, edge, jump, chlen, scanv,
       scanst, chainof, clchain, ch_i32, besta, bestb, trk_i32, trackcl, cl2trk, tracks, ctrl, scratch, wincnt, winsoff,
-      candab, candsc, lenhist, evinfo, xs;
+      candab, candsc, lenhist, evinfo, xs, cmp;
   unsigned long long* h_ctrl = nullptr;   // pinned copy of [ctr | err]
   // batch tables, device (evinfo) and pinned host copy, same layout:
   // u64 base[kMaxBatch], u64 bytes[kMaxBatch], u32 cl_start[kMaxBatch + 1],
@@ -76,6 +77,9 @@ struct Slot {
   bool xs_done = false;
   uint64_t xs_n = 0, xs_links = 0;
   size_t xs_bytes = 0;
+  // track-model compression of the current ticket (tpc_compress_clusters)
+  bool cmp_done = false;
+  size_t cmp_bytes = 0;
   // capacities
   uint64_t cap_pages = 0, cap_windows = 0, cap_cl = 0, cap_ch = 0;
   // ticket
@@ -308,7 +312,7 @@ static void slot_free(tpc_context* ctx, Slot& s) {
   Buf* all[] = {&s.pages, &s.offsets, &s.winstate, &s.cl, &s.clx, &s.cly, &s.clz, &s.clt, &s.rowstart, &s.chrow, &s.up,
                 &s.down, &s.score, &s.edge, &s.jump, &s.chlen, &s.scanv, &s.scanst, &s.chainof, &s.clchain,
                 &s.ch_i32, &s.besta, &s.bestb, &s.trk_i32, &s.trackcl, &s.cl2trk, &s.tracks, &s.ctrl,
-                &s.scratch, &s.wincnt, &s.winsoff, &s.candab, &s.candsc, &s.lenhist, &s.evinfo, &s.xs};
+                &s.scratch, &s.wincnt, &s.winsoff, &s.candab, &s.candsc, &s.lenhist, &s.evinfo, &s.xs, &s.cmp};
   for (Buf* b : all) free_buf(*b);
   for (auto& e : s.ev_stage) if (e) cudaEventDestroy(e);
   if (s.ev_done) cudaEventDestroy(s.ev_done);
@@ -547,6 +551,7 @@ static tpc_status start_timeframe(tpc_context* ctx, Slot* s, const tpc_timeframe
   const bool dev_in = tf->flags & TPC_TF_DEVICE_INPUT;
   s->n_events = 1;
   s->xs_done = false;
+  s->cmp_done = false;
   const unsigned nfrag = (tf->n_time_bins + kFrag - 1) / kFrag;
   const uint64_t nwin = (uint64_t)ctx->geom.n_sectors * ctx->geom.n_rows * nfrag;
   if (nwin > 0xffffffffull) return fail(TPC_E_INVAL, "too many windows");
@@ -578,6 +583,7 @@ static tpc_status start_timeframe(tpc_context* ctx, Slot* s, const tpc_timeframe
 static tpc_status start_batch(tpc_context* ctx, Slot* s, const tpc_timeframe_desc* tfs, uint32_t n_events) {
   const uint32_t T = tfs[0].n_time_bins;
   s->xs_done = false;
+  s->cmp_done = false;
   std::vector<uint64_t> base(n_events), bytes(n_events);
   uint64_t total = 0;
   for (uint32_t e = 0; e < n_events; e++) {
@@ -646,11 +652,11 @@ static void reclaim_idle(tpc_context* ctx, const Slot* keep) {
     Buf* big[] = {&c.pages, &c.offsets, &c.winstate, &c.cl, &c.clx, &c.cly, &c.clz, &c.clt, &c.up, &c.down,
                   &c.score, &c.edge, &c.jump, &c.chlen, &c.scanv, &c.scanst, &c.chainof, &c.clchain, &c.ch_i32,
                   &c.besta, &c.bestb, &c.trk_i32, &c.trackcl, &c.cl2trk, &c.tracks, &c.scratch, &c.wincnt,
-                  &c.winsoff, &c.candab, &c.candsc, &c.xs};
+                  &c.winsoff, &c.candab, &c.candsc, &c.xs, &c.cmp};
     for (Buf* b : big) free_buf(*b);
-    ctx->used -= c.xs_bytes;
-    c.xs_bytes = 0;
-    c.xs_done = false;
+    ctx->used -= c.xs_bytes + c.cmp_bytes;
+    c.xs_bytes = c.cmp_bytes = 0;
+    c.xs_done = c.cmp_done = false;
     c.cap_pages = c.cap_windows = c.cap_cl = c.cap_ch = 0;
   }
 }
@@ -1038,6 +1044,71 @@ extern "C" tpc_status tpc_get_merged_tracks(tpc_context* ctx, uint64_t ticket, t
   if (cluster_to_track && ncl)
     CUDA_TRY(cudaMemcpyAsync(cluster_to_track, base + o_map, ncl * 4, cudaMemcpyDeviceToHost, s->stream));
   if (link && ntr) CUDA_TRY(cudaMemcpyAsync(link, base + o_link, ntr * 4, cudaMemcpyDeviceToHost, s->stream));
+  CUDA_TRY(cudaStreamSynchronize(s->stream));
+  return TPC_OK;
+}
+
+// ------------------------------------------------------------------ step 10
+static CmpWork cmp_work(Slot& s) {
+  CmpWork C;
+  uint8_t* p = (uint8_t*)s.cmp.p;
+  const size_t n = (s.cap_cl + 255) & ~(size_t)255;
+  C.code_y = (int8_t*)p;
+  C.code_z = (int8_t*)(p + n);
+  C.status = p + 2 * n;
+  C.ctl = (unsigned long long*)(p + 3 * n);
+  return C;
+}
+
+extern "C" tpc_status tpc_compress_clusters(tpc_context* ctx, uint64_t ticket, const tpc_cmp_params* cp,
+                                            uint64_t* n_coded, uint64_t* n_escaped) {
+  if (!ctx) return fail(TPC_E_INVAL, "tpc_compress_clusters: null argument");
+  const double sy = cp ? cp->step_y_cm : 0.4 / 32, sz = cp ? cp->step_z_cm : 0.5 / 32;
+  if (!(sy > 0.0) || !(sz > 0.0)) return fail(TPC_E_INVAL, "tpc_compress_clusters: steps must be positive");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  Slot* s;
+  tpc_status st = done_slot(ctx, ticket, &s);
+  if (st) return st;
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  const size_t need = 3 * ((s->cap_cl + 255) & ~(size_t)255) + 256;
+  if (need > s->cmp.bytes) {
+    if (ctx->used - s->cmp_bytes + need > ctx->budget) return fail(TPC_E_NOMEM, "tpc_compress_clusters: over the memory budget");
+    CUDA_TRY(ensure(s->cmp, need));
+    ctx->used = ctx->used - s->cmp_bytes + need;
+    s->cmp_bytes = need;
+  }
+  CmpWork C = cmp_work(*s);
+  C.step_y = (float)sy;
+  C.step_z = (float)sz;
+  const uint64_t ncl = n_cl_of(*s);
+  CUDA_TRY(cudaMemsetAsync(C.status, 0, ncl ? ncl : 1, s->stream));
+  CUDA_TRY(cudaMemsetAsync(C.ctl, 0, 16, s->stream));
+  CUDA_TRY(launch_compress(ctx->P, s->W, C, ctx->n_sm, s->stream));
+  unsigned long long ctl[2];
+  CUDA_TRY(cudaMemcpyAsync(ctl, C.ctl, 16, cudaMemcpyDeviceToHost, s->stream));
+  CUDA_TRY(cudaStreamSynchronize(s->stream));
+  s->cmp_done = true;
+  if (n_coded) *n_coded = ctl[0];
+  if (n_escaped) *n_escaped = ctl[1];
+  return TPC_OK;
+}
+
+extern "C" tpc_status tpc_get_compressed(tpc_context* ctx, uint64_t ticket, int8_t* code_y, int8_t* code_z,
+                                         uint8_t* status) {
+  if (!ctx) return fail(TPC_E_INVAL, "tpc_get_compressed: null argument");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  Slot* s;
+  tpc_status st = done_slot(ctx, ticket, &s);
+  if (st) return st;
+  if (!s->cmp_done) return fail(TPC_E_NOTREADY, "tpc_compress_clusters has not run on this ticket");
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  const CmpWork C = cmp_work(*s);
+  const uint64_t ncl = n_cl_of(*s);
+  if (ncl) {
+    if (code_y) CUDA_TRY(cudaMemcpyAsync(code_y, C.code_y, ncl, cudaMemcpyDeviceToHost, s->stream));
+    if (code_z) CUDA_TRY(cudaMemcpyAsync(code_z, C.code_z, ncl, cudaMemcpyDeviceToHost, s->stream));
+    if (status) CUDA_TRY(cudaMemcpyAsync(status, C.status, ncl, cudaMemcpyDeviceToHost, s->stream));
+  }
   CUDA_TRY(cudaStreamSynchronize(s->stream));
   return TPC_OK;
 }

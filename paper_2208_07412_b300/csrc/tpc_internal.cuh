@@ -265,6 +265,15 @@ struct XsWork {
   int edge_u;
 };
 
+// Work space of the optional track-model compression (step 10).
+struct CmpWork {
+  int8_t* code_y;                // [cap_cl] residual codes (coded clusters)
+  int8_t* code_z;
+  uint8_t* status;               // [cap_cl] 0 not on a track, 1 coded, 2 escaped
+  unsigned long long* ctl;       // [0] coded, [1] escaped
+  float step_y, step_z;          // cm
+};
+
 // Warp-aggregated atomicAdd of 1 on one counter: the lanes that call it
 // together take consecutive values with a single atomic (correct under
 // independent thread scheduling: the group is whoever is converged here).

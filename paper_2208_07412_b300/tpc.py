@@ -75,6 +75,10 @@ class tpc_xs_params(ctypes.Structure):
     _fields_ = [("chi2_cut", ctypes.c_double), ("edge_cm", ctypes.c_double)]
 
 
+class tpc_cmp_params(ctypes.Structure):
+    _fields_ = [("step_y_cm", ctypes.c_double), ("step_z_cm", ctypes.c_double)]
+
+
 class tpc_timeframe_desc(ctypes.Structure):
     _fields_ = [("pages", _P), ("pages_bytes", _u64), ("page_offsets", _P),
                 ("n_time_bins", ctypes.c_uint32), ("flags", ctypes.c_uint32)]
@@ -85,7 +89,8 @@ EXPORTS = ("tpc_params_default", "tpc_create_geometry", "tpc_destroy_geometry", 
            "tpc_get_tracks", "tpc_get_links", "tpc_get_device_results", "tpc_get_stage_times",
            "tpc_get_counters", "tpc_release", "tpc_last_error", "tpc_find_clusters_noalloc",
            "tpc_submit_batch", "tpc_get_batch_info", "tpc_get_event_clusters", "tpc_get_event_tracks",
-           "tpc_get_tuning", "tpc_set_tuning", "tpc_autotune", "tpc_merge_sectors", "tpc_get_merged_tracks")
+           "tpc_get_tuning", "tpc_set_tuning", "tpc_autotune", "tpc_merge_sectors", "tpc_get_merged_tracks",
+           "tpc_compress_clusters", "tpc_get_compressed")
 
 _lib = None
 
@@ -134,6 +139,9 @@ def load(build_if_missing: bool = True):
     L.tpc_autotune.argtypes = [_P, ctypes.POINTER(tpc_timeframe_desc), ctypes.c_int, ctypes.POINTER(tpc_tuning)]
     L.tpc_merge_sectors.argtypes = [_P, _u64, ctypes.POINTER(tpc_xs_params), ctypes.POINTER(_u64)]
     L.tpc_get_merged_tracks.argtypes = [_P, _u64, _P, _u64, ctypes.POINTER(_u64), _P, _P]
+    L.tpc_compress_clusters.argtypes = [_P, _u64, ctypes.POINTER(tpc_cmp_params), ctypes.POINTER(_u64),
+                                        ctypes.POINTER(_u64)]
+    L.tpc_get_compressed.argtypes = [_P, _u64, _P, _P, _P]
     L.tpc_last_error.argtypes = []
     L.tpc_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -306,6 +314,23 @@ def tpc_get_merged_tracks(ctx, ticket: int, n_clusters: int, n_tracks: int):
     _check(L.tpc_get_merged_tracks(ctx, ticket, out.ctypes.data if n.value else None, n.value, ctypes.byref(n),
                                    m.ctypes.data if n_clusters else None, link.ctypes.data if n_tracks else None))
     return out, m, link
+
+
+def tpc_compress_clusters(ctx, ticket: int, step_y_cm: float = 0.4 / 32, step_z_cm: float = 0.5 / 32):
+    """Track-model compression of a finished ticket; returns (n_coded, n_escaped)."""
+    a, b = _u64(), _u64()
+    cp = tpc_cmp_params(float(step_y_cm), float(step_z_cm))
+    _check(load().tpc_compress_clusters(ctx, ticket, ctypes.byref(cp), ctypes.byref(a), ctypes.byref(b)))
+    return int(a.value), int(b.value)
+
+
+def tpc_get_compressed(ctx, ticket: int, n_clusters: int):
+    """Returns (code_y, code_z, status) per cluster."""
+    cy = np.zeros(max(n_clusters, 1), np.int8)
+    cz = np.zeros(max(n_clusters, 1), np.int8)
+    st = np.zeros(max(n_clusters, 1), np.uint8)
+    _check(load().tpc_get_compressed(ctx, ticket, cy.ctypes.data, cz.ctypes.data, st.ctypes.data))
+    return cy[:n_clusters], cz[:n_clusters], st[:n_clusters]
 
 
 def tpc_poll(ctx, ticket: int, timeout_us: int = 0xFFFFFFFF) -> int:
