@@ -432,6 +432,23 @@ def compression_stats(tpc, R, pages_d, offs_d, tf, reps=5):
             "timing": f"host wall clock of the call, median of {reps}"}
 
 
+def calibration_stats(tpc, R, pages_d, offs_d, tf, reps=5):
+    """The optional step 11 (tpc_calibrate_drift): time of the call and the
+    vertex time it finds (the workload's collision is at t0 = 250 bins with
+    the nominal drift velocity, so eps_vd should be ~0)."""
+    t = R.submit(pages_d, offs_d, tf.n_time_bins)
+    R.wait(t)
+    tpc.tpc_calibrate_drift(R.ctx, t, 250.0)   # warm-up (allocates its work space)
+    times = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        tv, eps, t0v, n = tpc.tpc_calibrate_drift(R.ctx, t, 250.0)
+        times.append(time.perf_counter() - t0)
+    tpc.tpc_release(R.ctx, t)
+    return {"ms": 1e3 * statistics.median(times), "t_vertex_bins": tv, "eps_vd": eps, "tracks_used": n,
+            "timing": f"host wall clock of the call, median of {reps}"}
+
+
 def run_ours(args, world, rank, local):
     import torch
     from paper_2208_07412_b300 import tpc
@@ -570,6 +587,7 @@ def run_ours(args, world, rank, local):
         if world == 1 and args.workload == "full_tpc":
             line["cross_sector"] = cross_sector_timing(tpc, torch, R, pages_d, offs_d, tf)
             line["compression"] = compression_stats(tpc, R, pages_d, offs_d, tf)
+            line["calibration"] = calibration_stats(tpc, R, pages_d, offs_d, tf)
         if world == 1 and not args.no_batched and args.workload == "full_tpc":
             line["batched"] = batched_vs_plain(tpc, torch, local, tuning=tuning)
         if world == 1 and not args.no_cpu_baseline:

@@ -404,6 +404,26 @@ tpc_status tpc_compress_clusters(tpc_context* ctx, uint64_t ticket, const tpc_cm
  * TPC_E_NOTREADY if tpc_compress_clusters has not run on the ticket. */
 tpc_status tpc_get_compressed(tpc_context* ctx, uint64_t ticket, int8_t* code_y, int8_t* code_z, uint8_t* status);
 
+/* Step 11, optional: drift-velocity / T0 calibration from the step-8 tracks of
+ * a finished ticket holding one collision whose vertex lies on the beam axis
+ * at z = 0 (the paper lists calibration among the EPNs' tasks, "Hardware and
+ * data flow"; this is the library's definition):
+ *   - per track with >= 20 clusters and no flag, its state is carried along
+ *     the exact helix to x = 0 and used if |y| < 3 cm there; its vertex time
+ *     bin is t_v = zeta / 0.5 cm (zeta is 0.5 cm per time bin);
+ *   - the fullest whole bin b* of floor(t_v) (over 2^20 bins, the lowest on
+ *     ties) seeds a mean over |t_v - (b* + 0.5)| <= 3, then a mean over
+ *     |t_v - mean| <= 1.5: *t_vertex_bins;
+ *   - the vertex's charge drifts the whole length L, so with the collision
+ *     time t0_bins known the drift velocity is off by
+ *     *eps_vd = (L / 0.5 cm) / (t_vertex - t0) - 1, and with the drift
+ *     velocity known the collision time is *t0_from_vertex = t_vertex - L / 0.5 cm.
+ * Any output pointer may be NULL; *n_used: tracks in the final mean (0: no
+ * estimate, outputs 0).  Runs on the ticket's stream and waits.
+ * Errors: TPC_E_NOTREADY, TPC_E_NOTFOUND, TPC_E_INVAL, TPC_E_CUDA, TPC_E_NOMEM. */
+tpc_status tpc_calibrate_drift(tpc_context* ctx, uint64_t ticket, double t0_bins, double drift_length_cm,
+                               double* t_vertex_bins, double* eps_vd, double* t0_from_vertex, uint64_t* n_used);
+
 /* Layout of a finished ticket's results by event: *n_events (1 for a plain
  * timeframe) and, if not NULL, cluster_start[n_events + 1] and
  * track_start[n_events + 1], each event's first cluster / track in the

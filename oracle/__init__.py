@@ -136,6 +136,8 @@ def _load():
         L.orc_merge_sectors.restype = ctypes.c_int64
         L.orc_compress.argtypes = [_P, _P, _P, _P, ctypes.c_int64, _P, ctypes.c_int64, _P, _P, _P, _P]
         L.orc_compress.restype = ctypes.c_int64
+        L.orc_calibrate_drift.argtypes = [_P, _P, _P, ctypes.c_int64, ctypes.c_double, _P, _P, _P]
+        L.orc_calibrate_drift.restype = ctypes.c_int64
         _lib = L
     return _lib
 
@@ -422,6 +424,27 @@ def compress(tf, res, step_y: float = STEP_Y, step_z: float = STEP_Z, params: Or
                    c2t.ctypes.data if n else None, len(fits), fits.ctypes.data if len(fits) else None,
                    cy.ctypes.data, cz.ctypes.data, st.ctypes.data)
     return cy[:n].copy(), cz[:n].copy(), st[:n].copy()
+
+
+ZETA_PER_BIN = 0.5   # cm of the drift coordinate per time bin (Z = 640 u per bin)
+
+
+def calibrate_drift(res, t0_bins: float, drift_length_cm: float = 250.0, params: OracleParams | None = None):
+    """Drift calibration from an OracleResult's tracks (step 11).  Returns
+    (t_vertex_bins, eps_vd, t0_from_vertex_bins, n_used)."""
+    L = _load()
+    p = (params or OracleParams())._c()
+    fits = np.ascontiguousarray(res.fits)
+    ncl = np.ascontiguousarray(res.track_ncl, np.int32)
+    nt = len(fits)
+    tv = ctypes.c_double(0.0)
+    per = np.zeros(max(nt, 1))
+    used = np.zeros(max(nt, 1), np.uint8)
+    n = L.orc_calibrate_drift(ctypes.byref(p), fits.ctypes.data if nt else None, ncl.ctypes.data if nt else None,
+                              nt, ZETA_PER_BIN, ctypes.byref(tv), per.ctypes.data, used.ctypes.data)
+    full = drift_length_cm / ZETA_PER_BIN
+    eps = full / (tv.value - t0_bins) - 1.0 if n else float("nan")
+    return tv.value, eps, tv.value - full, int(n)
 
 
 @dataclass

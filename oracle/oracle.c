@@ -1009,3 +1009,57 @@ int64_t orc_compress(const orc_input* in, const orc_params* P, const orc_cmp_par
   free(cnt); free(lst); free(fill);
   return coded;
 }
+
+/* ------------------------------------------------------------ 11. drift calibration
+ * The paper lists calibration among the EPNs' tasks ("Hardware and data flow");
+ * this is the library's definition of a drift-velocity / T0 calibration from
+ * tracks of a collision whose vertex lies on the beam axis at z = 0:
+ *   - per step-8 track with >= 20 clusters and no flag, its state is carried
+ *     along the exact helix from its reference x to x = 0 (the beam axis); it
+ *     is used if |y| there is below 3 cm;
+ *   - the time bin of the vertex, t_v = zeta(x = 0) / (zeta per time bin):
+ *     its most populated whole bin b* (tracks with floor(t_v) = b, lowest b on
+ *     ties) locates it; the mean over the tracks within 3 bins of b* + 0.5,
+ *     then over those within 1.5 bins of that mean, estimates it;
+ *   - with a known collision time t0 and drift length L, the drift velocity is
+ *     off by eps = (L / zeta_per_bin) / (t_v - t0) - 1 (the vertex's charge
+ *     drifts the full length); with a known drift velocity, t0 = t_v - L /
+ *     zeta_per_bin. */
+int64_t orc_calibrate_drift(const orc_params* P, const orc_fit* fits, const int32_t* ncl, int64_t nt,
+                            double zeta_per_bin, double* t_vertex, double* tv_track, uint8_t* used) {
+  for (int64_t t = 0; t < nt; t++) {
+    used[t] = 0;
+    tv_track[t] = 0.0;
+    if (ncl[t] < 20 || fits[t].flags) continue;
+    double s[5], out[5];
+    for (int k = 0; k < 5; k++) s[k] = fits[t].par[k];
+    if (orc_transport(P, s, -fits[t].x, out, NULL)) continue;
+    if (fabs(out[0]) >= 3.0) continue;
+    tv_track[t] = out[1] / zeta_per_bin;
+    used[t] = 1;
+  }
+  /* mode of floor(t_v) over [0, nbins) */
+  const int64_t nbins = 1 << 20;
+  int64_t* h = (int64_t*)calloc((size_t)nbins, sizeof(int64_t));
+  for (int64_t t = 0; t < nt; t++)
+    if (used[t] && tv_track[t] >= 0.0 && tv_track[t] < (double)nbins) h[(int64_t)floor(tv_track[t])]++;
+  int64_t best = -1;
+  for (int64_t b = 0; b < nbins; b++)
+    if (h[b] > 0 && (best < 0 || h[b] > h[best])) best = b;
+  free(h);
+  if (best < 0) { *t_vertex = 0.0; return 0; }
+  double centre = (double)best + 0.5;
+  const double win[2] = {3.0, 1.5};
+  int64_t nu = 0;
+  for (int pass = 0; pass < 2; pass++) {
+    double sum = 0.0;
+    int64_t cnt = 0;
+    for (int64_t t = 0; t < nt; t++)
+      if (used[t] && fabs(tv_track[t] - centre) <= win[pass]) { sum += tv_track[t]; cnt++; }
+    if (cnt == 0) { *t_vertex = 0.0; return 0; }
+    centre = sum / (double)cnt;
+    nu = cnt;
+  }
+  *t_vertex = centre;
+  return nu;
+}

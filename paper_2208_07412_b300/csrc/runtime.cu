@@ -31,6 +31,7 @@ size_t scan_tiles(unsigned long long cap);
 cudaError_t prepare_find();
 cudaError_t launch_xsec(const DevGeom&, const DevParams&, const DevWork&, const XsWork&, int, cudaStream_t);
 cudaError_t launch_compress(const DevParams&, const DevWork&, const CmpWork&, int, cudaStream_t);
+cudaError_t launch_calibrate(const DevParams&, const DevWork&, const CalWork&, int, cudaStream_t);
 }  // namespace tpc
 
 using namespace tpc;
@@ -66,7 +67,7 @@ struct Slot {
   // device buffers
   Buf pages, offsets, winstate, cl, clx, cly, clz, clt, rowstart, chrow, up, down, score, edge, jump, chlen, scanv,
       scanst, chainof, clchain, ch_i32, besta, bestb, trk_i32, trackcl, cl2trk, tracks, ctrl, scratch, wincnt, winsoff,
-      candab, candsc, lenhist, evinfo, xs, cmp;
+      candab, candsc, lenhist, evinfo, xs, cmp, cal;
   unsigned long long* h_ctrl = nullptr;   // pinned copy of [ctr | err]
   // batch tables, device (evinfo) and pinned host copy, same layout:
   // u64 base[kMaxBatch], u64 bytes[kMaxBatch], u32 cl_start[kMaxBatch + 1],
@@ -79,7 +80,7 @@ struct Slot {
   size_t xs_bytes = 0;
   // track-model compression of the current ticket (tpc_compress_clusters)
   bool cmp_done = false;
-  size_t cmp_bytes = 0;
+  size_t cmp_bytes = 0, cal_bytes = 0;
   // capacities
   uint64_t cap_pages = 0, cap_windows = 0, cap_cl = 0, cap_ch = 0;
   // ticket
@@ -312,7 +313,7 @@ static void slot_free(tpc_context* ctx, Slot& s) {
   Buf* all[] = {&s.pages, &s.offsets, &s.winstate, &s.cl, &s.clx, &s.cly, &s.clz, &s.clt, &s.rowstart, &s.chrow, &s.up,
                 &s.down, &s.score, &s.edge, &s.jump, &s.chlen, &s.scanv, &s.scanst, &s.chainof, &s.clchain,
                 &s.ch_i32, &s.besta, &s.bestb, &s.trk_i32, &s.trackcl, &s.cl2trk, &s.tracks, &s.ctrl,
-                &s.scratch, &s.wincnt, &s.winsoff, &s.candab, &s.candsc, &s.lenhist, &s.evinfo, &s.xs, &s.cmp};
+                &s.scratch, &s.wincnt, &s.winsoff, &s.candab, &s.candsc, &s.lenhist, &s.evinfo, &s.xs, &s.cmp, &s.cal};
   for (Buf* b : all) free_buf(*b);
   for (auto& e : s.ev_stage) if (e) cudaEventDestroy(e);
   if (s.ev_done) cudaEventDestroy(s.ev_done);
@@ -652,10 +653,10 @@ static void reclaim_idle(tpc_context* ctx, const Slot* keep) {
     Buf* big[] = {&c.pages, &c.offsets, &c.winstate, &c.cl, &c.clx, &c.cly, &c.clz, &c.clt, &c.up, &c.down,
                   &c.score, &c.edge, &c.jump, &c.chlen, &c.scanv, &c.scanst, &c.chainof, &c.clchain, &c.ch_i32,
                   &c.besta, &c.bestb, &c.trk_i32, &c.trackcl, &c.cl2trk, &c.tracks, &c.scratch, &c.wincnt,
-                  &c.winsoff, &c.candab, &c.candsc, &c.xs, &c.cmp};
+                  &c.winsoff, &c.candab, &c.candsc, &c.xs, &c.cmp, &c.cal};
     for (Buf* b : big) free_buf(*b);
-    ctx->used -= c.xs_bytes + c.cmp_bytes;
-    c.xs_bytes = c.cmp_bytes = 0;
+    ctx->used -= c.xs_bytes + c.cmp_bytes + c.cal_bytes;
+    c.xs_bytes = c.cmp_bytes = c.cal_bytes = 0;
     c.xs_done = c.cmp_done = false;
     c.cap_pages = c.cap_windows = c.cap_cl = c.cap_ch = 0;
   }
@@ -1110,6 +1111,51 @@ extern "C" tpc_status tpc_get_compressed(tpc_context* ctx, uint64_t ticket, int8
     if (status) CUDA_TRY(cudaMemcpyAsync(status, C.status, ncl, cudaMemcpyDeviceToHost, s->stream));
   }
   CUDA_TRY(cudaStreamSynchronize(s->stream));
+  return TPC_OK;
+}
+
+// ------------------------------------------------------------------ step 11
+extern "C" tpc_status tpc_calibrate_drift(tpc_context* ctx, uint64_t ticket, double t0_bins, double drift_length_cm,
+                                          double* t_vertex_bins, double* eps_vd, double* t0_from_vertex,
+                                          uint64_t* n_used) {
+  if (!ctx) return fail(TPC_E_INVAL, "tpc_calibrate_drift: null argument");
+  if (!(drift_length_cm > 0.0)) return fail(TPC_E_INVAL, "tpc_calibrate_drift: drift length must be positive");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  Slot* s;
+  tpc_status st = done_slot(ctx, ticket, &s);
+  if (st) return st;
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  const size_t nb = (size_t)1 << 20;
+  const size_t need = ((s->cap_ch * 4 + 255) & ~(size_t)255) + nb * 4 + 256;
+  if (need > s->cal.bytes) {
+    if (ctx->used - s->cal_bytes + need > ctx->budget) return fail(TPC_E_NOMEM, "tpc_calibrate_drift: over the memory budget");
+    CUDA_TRY(ensure(s->cal, need));
+    ctx->used = ctx->used - s->cal_bytes + need;
+    s->cal_bytes = need;
+  }
+  uint8_t* p = (uint8_t*)s->cal.p;
+  CalWork C;
+  C.tv = (float*)p;
+  p += (s->cap_ch * 4 + 255) & ~(size_t)255;
+  C.hist = (unsigned*)p;
+  p += nb * 4;
+  C.mode = (unsigned long long*)p;
+  C.sum = (double*)(p + 8);
+  C.cnt = (unsigned long long*)(p + 24);
+  C.zeta_per_bin = 0.5f;
+  CUDA_TRY(cudaMemsetAsync(C.hist, 0, nb * 4 + 64, s->stream));
+  CUDA_TRY(launch_calibrate(ctx->P, s->W, C, ctx->n_sm, s->stream));
+  unsigned long long h[5];
+  CUDA_TRY(cudaMemcpyAsync(h, C.mode, 40, cudaMemcpyDeviceToHost, s->stream));
+  CUDA_TRY(cudaStreamSynchronize(s->stream));
+  double sums[2];
+  std::memcpy(sums, &h[1], 16);
+  const uint64_t n = h[4];
+  const double tv = n ? sums[1] / (double)n : 0.0, full = drift_length_cm / 0.5;
+  if (t_vertex_bins) *t_vertex_bins = tv;
+  if (eps_vd) *eps_vd = (n && tv != t0_bins) ? full / (tv - t0_bins) - 1.0 : 0.0;
+  if (t0_from_vertex) *t0_from_vertex = n ? tv - full : 0.0;
+  if (n_used) *n_used = n;
   return TPC_OK;
 }
 

@@ -274,6 +274,16 @@ struct CmpWork {
   float step_y, step_z;          // cm
 };
 
+// Work space of the optional drift calibration (step 11).
+struct CalWork {
+  float* tv;                     // [cap_ch] vertex time bin per track, -1 if unused
+  unsigned* hist;                // [2^20] tracks per whole vertex time bin
+  unsigned long long* mode;      // count << 32 | (2^20 - 1 - bin) of the fullest bin
+  double* sum;                   // [2] window sums of t_v
+  unsigned long long* cnt;       // [2] window counts
+  float zeta_per_bin;            // cm of the drift coordinate per time bin
+};
+
 // Warp-aggregated atomicAdd of 1 on one counter: the lanes that call it
 // together take consecutive values with a single atomic (correct under
 // independent thread scheduling: the group is whoever is converged here).

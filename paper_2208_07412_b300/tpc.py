@@ -90,7 +90,7 @@ EXPORTS = ("tpc_params_default", "tpc_create_geometry", "tpc_destroy_geometry", 
            "tpc_get_counters", "tpc_release", "tpc_last_error", "tpc_find_clusters_noalloc",
            "tpc_submit_batch", "tpc_get_batch_info", "tpc_get_event_clusters", "tpc_get_event_tracks",
            "tpc_get_tuning", "tpc_set_tuning", "tpc_autotune", "tpc_merge_sectors", "tpc_get_merged_tracks",
-           "tpc_compress_clusters", "tpc_get_compressed")
+           "tpc_compress_clusters", "tpc_get_compressed", "tpc_calibrate_drift")
 
 _lib = None
 
@@ -142,6 +142,9 @@ def load(build_if_missing: bool = True):
     L.tpc_compress_clusters.argtypes = [_P, _u64, ctypes.POINTER(tpc_cmp_params), ctypes.POINTER(_u64),
                                         ctypes.POINTER(_u64)]
     L.tpc_get_compressed.argtypes = [_P, _u64, _P, _P, _P]
+    L.tpc_calibrate_drift.argtypes = [_P, _u64, ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(_u64)]
     L.tpc_last_error.argtypes = []
     L.tpc_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -331,6 +334,14 @@ def tpc_get_compressed(ctx, ticket: int, n_clusters: int):
     st = np.zeros(max(n_clusters, 1), np.uint8)
     _check(load().tpc_get_compressed(ctx, ticket, cy.ctypes.data, cz.ctypes.data, st.ctypes.data))
     return cy[:n_clusters], cz[:n_clusters], st[:n_clusters]
+
+
+def tpc_calibrate_drift(ctx, ticket: int, t0_bins: float, drift_length_cm: float = 250.0):
+    """Drift calibration of a finished ticket: (t_vertex_bins, eps_vd, t0_from_vertex, n_used)."""
+    tv, eps, t0, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_double(), _u64()
+    _check(load().tpc_calibrate_drift(ctx, ticket, float(t0_bins), float(drift_length_cm), ctypes.byref(tv),
+                                      ctypes.byref(eps), ctypes.byref(t0), ctypes.byref(n)))
+    return tv.value, eps.value, t0.value, int(n.value)
 
 
 def tpc_poll(ctx, ticket: int, timeout_us: int = 0xFFFFFFFF) -> int:
