@@ -37,8 +37,11 @@ __device__ __forceinline__ bool transport(float kfac, float* s, float dx, Jac<fl
   const float kd = k * d;
   const float x = 0.5f * kd;
   float A, Ak;
-  if (fabsf(kd) < 1e-3f) {
-    A = d * (1.f + kd * kd * (1.f / 24.f));
+  if (fabsf(x) < 0.1f) {
+    // arc = (2 / k) asin(kd / 2) = d asin(x) / x, x = kd / 2: the Taylor series
+    // of asin(x) / x to x^6 (the next term is below 3e-10 here)
+    const float x2 = x * x;
+    A = d * (1.f + x2 * ((1.f / 6.f) + x2 * ((3.f / 40.f) + x2 * (5.f / 112.f))));
   } else {
     A = 2.f * asinf(fminf(1.f, fmaxf(-1.f, x))) * rcp(k);
   }
