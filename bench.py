@@ -449,6 +449,41 @@ def calibration_stats(tpc, R, pages_d, offs_d, tf, reps=5):
             "timing": f"host wall clock of the call, median of {reps}"}
 
 
+def finder_variants(tpc, torch, tf, pages_d, offs_d, tuning, flush, fused_ms, reps=5):
+    """The measured variant pair of steps 1-4: the default fused finder (each
+    window's pages decoded straight into shared memory) against the dense-plane
+    finder (a decode pass writes a dense (sector row, time bin, pad) ADC plane
+    to device memory, a find pass reads it back).  Find-stage time from the
+    library's stage events, L2 flushed before each step, the same tuning."""
+    stride = (int(tf.npads.max()) + 7) & ~7
+    plane = tf.n_sectors * len(tf.npads) * tf.n_time_bins * stride * 2
+    n_frag = (tf.n_time_bins + 255) // 256
+    alloc = tf.n_sectors * len(tf.npads) * n_frag * 256 * stride * 2
+    free_now, _ = torch.cuda.mem_get_info()
+    if alloc + 40 * tf.pages.nbytes > 0.8 * free_now:
+        return {"skipped": f"the dense plane needs {alloc / 1e9:.1f} GB"}
+    Rd = tpc.Reconstructor.for_timeframe(tf, device=torch.cuda.current_device(),
+                                         flags=tpc.TPC_CTX_STAGE_TIMING | tpc.TPC_CTX_DENSE_FINDER,
+                                         mem_budget=int(0.8 * free_now))
+    tpc.tpc_set_tuning(Rd.ctx, **tuning)
+    times = []
+    for i in range(reps + 2):
+        flush.fill_(1)
+        t = Rd.submit(pages_d, offs_d, tf.n_time_bins)
+        Rd.wait(t)
+        if i >= 2:
+            times.append(tpc.tpc_get_stage_times(Rd.ctx, t)["find"])
+        tpc.tpc_release(Rd.ctx, t)
+    Rd.close()
+    dense_ms = statistics.mean(times)
+    # algorithmic bytes of the dense pair: the pages once, the plane written
+    # once and read once (+6 halo rows per 256-bin window)
+    dense_bytes = tf.pages.nbytes + plane + plane * (262 / 256)
+    return {"fused_find_ms": fused_ms, "dense_find_ms": dense_ms, "dense_over_fused": dense_ms / fused_ms,
+            "dense_plane_bytes": int(plane), "dense_algorithmic_gbs": dense_bytes / (dense_ms * 1e-3) / 1e9,
+            "timing": f"find stage (decode + find + scan + compaction), mean of {reps}, L2 flushed"}
+
+
 def run_ours(args, world, rank, local):
     import torch
     from paper_2208_07412_b300 import tpc
@@ -465,7 +500,8 @@ def run_ours(args, world, rank, local):
     # the library would replace by a stream of its own)
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    flags = tpc.TPC_CTX_STAGE_TIMING | (tpc.TPC_CTX_NO_GRAPHS if args.no_graphs else 0)
+    flags = tpc.TPC_CTX_STAGE_TIMING | (tpc.TPC_CTX_NO_GRAPHS if args.no_graphs else 0) | \
+        (tpc.TPC_CTX_DENSE_FINDER if args.dense_finder else 0)
     # device memory for one slot: the pages, ~150 B per cluster of capacity
     # (pages/12 clusters) and the rest; the budget is what the GPU has free
     free_b, _ = torch.cuda.mem_get_info()
@@ -556,7 +592,8 @@ def run_ours(args, world, rank, local):
     # submit queues and the loop degrades to one timeframe at a time)
     free_now, _ = torch.cuda.mem_get_info()
     depth = 3
-    Rp = tpc.Reconstructor.for_timeframe(tf, device=local, flags=0, mem_budget=int(free_now * 0.85), n_slots=depth)
+    Rp = tpc.Reconstructor.for_timeframe(tf, device=local, flags=tpc.TPC_CTX_DENSE_FINDER if args.dense_finder else 0,
+                                         mem_budget=int(free_now * 0.85), n_slots=depth)
     tpc.tpc_set_tuning(Rp.ctx, **tuning)
 
     def fetch(t):
@@ -589,6 +626,9 @@ def run_ours(args, world, rank, local):
         hbm = float(peaks["hbm_gbs"])
         n_windows = len(tf.page_offsets)
         alg_bytes = tf.pages.nbytes + 8 * n_windows + 16 * n_cl
+        if args.dense_finder:   # + the dense plane written once and read once (with 6 halo rows per window)
+            plane = tf.n_sectors * len(tf.npads) * tf.n_time_bins * ((int(tf.npads.max()) + 7) & ~7) * 2
+            alg_bytes += plane + plane * 262 // 256
         achieved = alg_bytes / (stages["find"] * 1e-3) / 1e9
         line = {
             "metric": METRIC, "value": cl_all / dev_s_max, "unit": "clusters/s", "n_gpus": world,
@@ -600,15 +640,16 @@ def run_ours(args, world, rank, local):
                        "l2": "flushed before every step (256 MB write)", "parallelism": f"replicas x{world}",
                        "tuning": {"autotuned": not (args.no_autotune or args.tuning), **tuning},
                        "path": ("plain per-timeframe kernel launches" if args.no_graphs
-                                else "per-timeframe pipeline replayed from a captured CUDA graph")},
+                                else "per-timeframe pipeline replayed from a captured CUDA graph"),
+                       "finder": "dense-plane variant" if args.dense_finder else "fused"},
             "tracks_per_s": tr_all / dev_s_max,
             "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
             "stages_ms": stages,
             "wall_ms_per_step": 1e3 * wall / args.steps,
             "roofline": {"kernel": "k_find_clusters", "bound": "hbm", "achieved": achieved, "peak": hbm,
                          "unit": "GB/s", "frac": achieved / hbm,
-                         "traffic": (FINDER_DRAM_BYTES.get(args.workload) if args.seed == 1 and not args.time_bins
-                                     else None),
+                         "traffic": (FINDER_DRAM_BYTES.get(args.workload)
+                                     if args.seed == 1 and not args.time_bins and not args.dense_finder else None),
                          "peak_kind": f"{peak_kind} hbm_gbs (copy)",
                          "algorithmic_bytes_per_launch": int(alg_bytes)},
             "e2e": {"value": cl_all / e2e_s_max, "unit": "clusters/s", "h2d_bytes_per_step": int(h2d),
@@ -623,6 +664,9 @@ def run_ours(args, world, rank, local):
             line["cross_sector"] = cross_sector_timing(tpc, torch, R, pages_d, offs_d, tf)
             line["compression"] = compression_stats(tpc, R, pages_d, offs_d, tf)
             line["calibration"] = calibration_stats(tpc, R, pages_d, offs_d, tf)
+        if world == 1 and not (args.no_variants or args.dense_finder) and args.workload in ("full_tpc", "continuous_50khz"):
+            line["finder_variants"] = finder_variants(tpc, torch, tf, pages_d, offs_d, tuning, flush,
+                                                      stages["find"])
         if world == 1 and not args.no_batched and args.workload == "full_tpc":
             line["batched"] = batched_vs_plain(tpc, torch, local, tuning=tuning)
         if world == 1 and not args.no_cpu_baseline:
@@ -649,6 +693,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graphs", action="store_true", help="enqueue every kernel instead of graph replay")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain comparison")
+    ap.add_argument("--no-variants", action="store_true", help="skip the fused-vs-dense finder comparison")
+    ap.add_argument("--dense-finder", action="store_true",
+                    help="time the dense-plane finder variant instead of the fused finder")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch configuration")
     ap.add_argument("--tuning", default="", help="fixed launch configuration, e.g. find_threads=384,fit_threads=32")
     args = ap.parse_args()

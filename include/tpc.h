@@ -99,6 +99,11 @@ typedef int32_t tpc_status;
 /* Context flags. */
 #define TPC_CTX_STAGE_TIMING 1u   /* record CUDA events around each stage (tpc_get_stage_times) */
 #define TPC_CTX_NO_GRAPHS    2u   /* enqueue every kernel instead of replaying the slot's captured CUDA graph */
+#define TPC_CTX_DENSE_FINDER 4u   /* steps 1-4 as the dense-plane variant: pages decoded into a dense
+                                     (sector row, time bin, pad) ADC plane in device memory (2 bytes per
+                                     pixel, 1.6 GB for the full TPC at 1000 bins), then windows read back
+                                     from it; the same clusters as the default fused finder, which decodes
+                                     each window into shared memory and never writes the plane */
 
 /* Pipeline stages, in launch order (indices into tpc_get_stage_times). */
 #define TPC_STAGE_FIND       0    /* ZS decode + peak finder + cluster moments + compaction */

@@ -67,6 +67,7 @@ constexpr int kHaloStage = 2048;             // bytes per neighbouring page's ha
 constexpr int kHaloRunOff = 16, kHaloAdcOff = 800;
 constexpr int kList = 4096;                  // digits listed by the decoder (beyond: bitmap walk)
 constexpr int kPad = 2;                      // empty pads on each side of a plane row
+constexpr int kDenseU = 7;                   // dense-plane chunks a thread has in flight
 constexpr int kMaxRuns = 2048;               // runs of a window decoded run-parallel (beyond: per entry)
 constexpr int kRunMapWords = kList / 32;     // run-start bitmap over the listed digits
 
@@ -525,6 +526,37 @@ __device__ __forceinline__ void make_cluster(const FindSmem& S, int ps_stride, i
   xyz = make_int4(xrow, 2 * (pad_fp - 128 * (np - 1)), 5 * (32768 * f + time_fp - 512), t);
 }
 
+// L2 prefetch of the next window's input while the current one is being
+// processed.  Fused finder and decode pass: its page and both neighbours,
+// contiguous in the usual layout (at most 64 KB).  Find pass of the dense
+// variant: its 262 plane rows, contiguous in the dense plane.
+__device__ __forceinline__ void prefetch_l2(const void* p, unsigned long long n) {
+  n = min(n, 65536ull) & ~15ull;
+  if (n) {
+    const size_t ga = __cvta_generic_to_global(p);
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(ga), "r"((unsigned)n) : "memory");
+  }
+}
+
+__device__ __forceinline__ void prefetch_next_pages(const DevWork& W, const unsigned long long (&noffs)[4]) {
+  const unsigned long long lo = noffs[0] != ~0ull ? noffs[0] : noffs[1];
+  unsigned long long hi = noffs[3] != ~0ull ? noffs[3] : W.pages_bytes;
+  if (lo < hi && lo < W.pages_bytes && (lo & 15) == 0)
+    prefetch_l2(W.pages + lo, min(hi, (unsigned long long)W.pages_bytes) - lo);
+}
+
+__device__ __forceinline__ void prefetch_next_dense(const DevGeom& G, const DevWork& W, unsigned nt) {
+  const unsigned sr = nt / (unsigned)G.n_frag, f = nt - sr * (unsigned)G.n_frag;
+  const long long T = G.n_time_bins;
+  const long long t0 = max(0ll, (long long)kFrag * f - kHalo), t1 = min(T, (long long)kFrag * (f + 1) + kHalo);
+  if (t0 >= t1) return;
+  const size_t row = (size_t)W.dense_stride * 2;   // bytes, a multiple of 16
+  const uint8_t* base = reinterpret_cast<const uint8_t*>(W.dense) + ((size_t)sr * T + t0) * row;
+  const unsigned long long n = (unsigned long long)(t1 - t0) * row;
+  prefetch_l2(base, n);
+  if (n > 65536ull) prefetch_l2(base + 65536, n - 65536ull);
+}
+
 // Output modes.  kScratch (the pipeline): each window reserves a span of the
 // scratch buffer with one atomic and writes its records there; a scan over the
 // window counts and k_compact_clusters then place them in canonical order and
@@ -532,7 +564,11 @@ __device__ __forceinline__ void make_cluster(const FindSmem& S, int ps_stride, i
 // another.  Otherwise (the allocation-free entry point, which has no scratch
 // buffer for records): a decoupled look-back over the windows gives each its
 // canonical offset and the records are written in place; only the records.
-template <bool kScratch, int kThreads>
+// kMode: 0 the fused finder (pages -> clusters); 1 and 2 the dense-plane
+// variant: 1 decodes each window's own page into a dense HBM plane of ADC
+// values, 2 reads a window and its 3-bin halos back from that plane and runs
+// the same peak / cluster steps.  All three give the same clusters.
+template <bool kScratch, int kThreads, int kMode>
 __global__ void __launch_bounds__(kThreads, 2)
 k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -596,7 +632,7 @@ k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
   // after the peak test.  In look-back mode a held window would stall every
   // successor's look-back: there the ticket is taken only at the top.
   if (kScratch && tid == 0) {
-    const unsigned w0 = atomicAdd(&W.tickets[TK_FIND], 1u);
+    const unsigned w0 = atomicAdd(&W.tickets[kMode == 2 ? TK_FIND2 : TK_FIND], 1u);
     S.misc[1] = (int)w0;
     S.misc[2] = w0 < n_windows ? window_frs(G, w0) : 0;
     for (int k = 0; k < 4; k++) {
@@ -616,7 +652,7 @@ k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
     __syncthreads();
     const unsigned int w = (unsigned int)S.misc[1];
     if (w >= n_windows) break;
-    if (kScratch && tid == 0) nt = atomicAdd(&W.tickets[TK_FIND], 1u);
+    if (kScratch && tid == 0) nt = atomicAdd(&W.tickets[kMode == 2 ? TK_FIND2 : TK_FIND], 1u);
     if (!kScratch && tid < 4) {
       const long long j = (long long)w - 1 + tid;
       S.offs[tid] = (j >= 0 && j < (long long)n_windows) ? W.page_offsets[j] : ~0ull;
@@ -635,128 +671,211 @@ k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
     const int T = G.n_time_bins;
     const uint64_t off = S.offs[1];
 
-    // ---- 1. one round trip: stage the page (length guessed from the next
-    // page's offset) and load both neighbours' headers
-    uint32_t copied = 0;
-    if (off <= W.pages_bytes && W.pages_bytes - off >= 32 && (off & 15) == 0) {
-      uint64_t guess = (S.offs[2] != ~0ull && S.offs[2] > off) ? S.offs[2] - off : W.pages_bytes - off;
-      guess = min(guess, (uint64_t)own_stage_bytes);
-      guess = min(guess, W.pages_bytes - off);
-      copied = (uint32_t)(guess & ~15ull);
-      const uint4* src = reinterpret_cast<const uint4*>(W.pages + off);
-      for (uint32_t i = tid; i < copied / 16; i += blockDim.x) reinterpret_cast<uint4*>(own_stage)[i] = __ldg(src + i);
-    }
-    if (tid < 4) {
-      const uint64_t o2 = S.offs[tid < 2 ? 0 : 2];
-      const bool want = (tid < 2 ? f > 0 : f + 1 < G.n_frag) && o2 != ~0ull && (o2 & 15) == 0 && o2 <= W.pages_bytes &&
-                        W.pages_bytes - o2 >= 32;
-      S.hdr[tid] = want ? __ldg(reinterpret_cast<const uint4*>(W.pages + o2) + (tid & 1)) : make_uint4(0, 0, 0, 0);
-    }
-    __syncthreads();
+    bool ok;
+    int ndig;
+    bool listed;
+    if (kMode != 2) {
+      // ---- 1. one round trip: stage the page (length guessed from the next
+      // page's offset) and load both neighbours' headers
+      uint32_t copied = 0;
+      if (off <= W.pages_bytes && W.pages_bytes - off >= 32 && (off & 15) == 0) {
+        uint64_t guess = (S.offs[2] != ~0ull && S.offs[2] > off) ? S.offs[2] - off : W.pages_bytes - off;
+        guess = min(guess, (uint64_t)own_stage_bytes);
+        guess = min(guess, W.pages_bytes - off);
+        copied = (uint32_t)(guess & ~15ull);
+        const uint4* src = reinterpret_cast<const uint4*>(W.pages + off);
+        for (uint32_t i = tid; i < copied / 16; i += blockDim.x) reinterpret_cast<uint4*>(own_stage)[i] = __ldg(src + i);
+      }
+      if (tid < 4) {
+        const uint64_t o2 = S.offs[tid < 2 ? 0 : 2];
+        const bool want = (tid < 2 ? f > 0 : f + 1 < G.n_frag) && o2 != ~0ull && (o2 & 15) == 0 && o2 <= W.pages_bytes &&
+                          W.pages_bytes - o2 >= 32;
+        S.hdr[tid] = want ? __ldg(reinterpret_cast<const uint4*>(W.pages + o2) + (tid & 1)) : make_uint4(0, 0, 0, 0);
+      }
+      __syncthreads();
 
-    // ---- 2. the three headers and the neighbours' halo byte ranges: warps 0-2
-    // copy the previous page's entries / runs / ADC words of its last 3 bins,
-    // warps 3-5 the next page's of its first 3 bins, each warp parsing the
-    // header it needs (one round trip, all six copies in flight); warp 6 parses
-    // the own header
-    const bool own_global = copied < 32;
-    {
-      const int wid = tid >> 5, lane = tid & 31;
-      if (wid < 6) {
-        const int nb = wid < 3 ? 0 : 1;   // 0: previous page, 1: next page
-        PageHdr hh;
-        uint32_t a = 0, b = 0;
-        int okk = 0;
-        if (lane == 0) {
-          const bool want = nb == 0 ? f > 0 : f + 1 < G.n_frag;
-          okk = want && parse_header(S.hdr + 2 * nb, S.offs[2 * nb], W.pages_bytes, hh);
-          if (nb == 0)
-            okk = okk && 2 * (hh.n_tb - hh.hi_tb) <= kHaloRunOff &&
-                  2 * (hh.n_runs - hh.hi_runs) <= kHaloAdcOff - kHaloRunOff &&
-                  4 * ((hh.n_dig + 2) / 3 - hh.hi_dig / 3) <= kHaloStage - kHaloAdcOff;
-          else
-            okk = okk && 2 * hh.lo_tb <= kHaloRunOff && 2 * hh.lo_runs <= kHaloAdcOff - kHaloRunOff &&
-                  4 * ((hh.lo_dig + 2) / 3) <= kHaloStage - kHaloAdcOff;
-          if (okk) {
-            const int part = wid % 3;
-            if (nb == 0) {
-              if (part == 0) { a = 32 + 2 * hh.hi_tb; b = 32 + 2 * hh.n_tb; }
-              else if (part == 1) { a = 32 + 2 * hh.n_tb + 2 * hh.hi_runs; b = 32 + 2 * hh.n_tb + 2 * hh.n_runs; }
-              else { a = hh.body + 4 * (hh.hi_dig / 3); b = hh.body + 4 * ((hh.n_dig + 2) / 3); }
-            } else {
-              if (part == 0) { a = 32; b = 32 + 2 * hh.lo_tb; }
-              else if (part == 1) { a = 32 + 2 * hh.n_tb; b = 32 + 2 * hh.n_tb + 2 * hh.lo_runs; }
-              else { a = hh.body; b = hh.body + 4 * ((hh.lo_dig + 2) / 3); }
+      // ---- 2. the three headers and the neighbours' halo byte ranges: warps 0-2
+      // copy the previous page's entries / runs / ADC words of its last 3 bins,
+      // warps 3-5 the next page's of its first 3 bins, each warp parsing the
+      // header it needs (one round trip, all six copies in flight); warp 6 parses
+      // the own header
+      const bool own_global = copied < 32;
+      {
+        const int wid = tid >> 5, lane = tid & 31;
+        if (wid < 6) {
+          const int nb = wid < 3 ? 0 : 1;   // 0: previous page, 1: next page
+          PageHdr hh;
+          uint32_t a = 0, b = 0;
+          int okk = 0;
+          if (lane == 0) {
+            const bool want = kMode != 1 && (nb == 0 ? f > 0 : f + 1 < G.n_frag);
+            okk = want && parse_header(S.hdr + 2 * nb, S.offs[2 * nb], W.pages_bytes, hh);
+            if (nb == 0)
+              okk = okk && 2 * (hh.n_tb - hh.hi_tb) <= kHaloRunOff &&
+                    2 * (hh.n_runs - hh.hi_runs) <= kHaloAdcOff - kHaloRunOff &&
+                    4 * ((hh.n_dig + 2) / 3 - hh.hi_dig / 3) <= kHaloStage - kHaloAdcOff;
+            else
+              okk = okk && 2 * hh.lo_tb <= kHaloRunOff && 2 * hh.lo_runs <= kHaloAdcOff - kHaloRunOff &&
+                    4 * ((hh.lo_dig + 2) / 3) <= kHaloStage - kHaloAdcOff;
+            if (okk) {
+              const int part = wid % 3;
+              if (nb == 0) {
+                if (part == 0) { a = 32 + 2 * hh.hi_tb; b = 32 + 2 * hh.n_tb; }
+                else if (part == 1) { a = 32 + 2 * hh.n_tb + 2 * hh.hi_runs; b = 32 + 2 * hh.n_tb + 2 * hh.n_runs; }
+                else { a = hh.body + 4 * (hh.hi_dig / 3); b = hh.body + 4 * ((hh.n_dig + 2) / 3); }
+              } else {
+                if (part == 0) { a = 32; b = 32 + 2 * hh.lo_tb; }
+                else if (part == 1) { a = 32 + 2 * hh.n_tb; b = 32 + 2 * hh.n_tb + 2 * hh.lo_runs; }
+                else { a = hh.body; b = hh.body + 4 * ((hh.lo_dig + 2) / 3); }
+              }
+            }
+            if (wid == 0 || wid == 3) {
+              S.ph[1 + nb] = hh;
+              S.misc[5 + nb] = okk;
             }
           }
-          if (wid == 0 || wid == 3) {
-            S.ph[1 + nb] = hh;
-            S.misc[5 + nb] = okk;
+          okk = __shfl_sync(0xffffffffu, okk, 0);
+          a = __shfl_sync(0xffffffffu, a, 0);
+          b = __shfl_sync(0xffffffffu, b, 0);
+          if (okk) {
+            const int part = wid % 3;
+            const int doff = part == 0 ? 0 : (part == 1 ? kHaloRunOff : kHaloAdcOff);
+            copy_u16_warp(reinterpret_cast<uint16_t*>(S.halo + nb * kHaloStage + doff),
+                          W.pages + S.offs[2 * nb], a, b);
+          }
+        } else if (wid == 6 && lane == 0) {
+          PageHdr hh;
+          const bool okk = parse_header(reinterpret_cast<const uint4*>(own_global ? W.pages + off : own_stage), off,
+                                        W.pages_bytes, hh) &&
+                           hh.sector == s && hh.row == r && hh.frag == f;
+          S.ph[0] = hh;
+          S.misc[4] = okk;
+        }
+      }
+      __syncthreads();
+      ok = S.misc[4];
+      const bool okp = S.misc[5], okn = S.misc[6];
+      const PageHdr& h = S.ph[0];
+      const PageHdr& hp = S.ph[1];
+      const PageHdr& hn = S.ph[2];
+      const uint8_t* own = (own_global || h.len > copied) ? W.pages + off : own_stage;
+      uint8_t* hprev = S.halo;
+      uint8_t* hnext = S.halo + kHaloStage;
+
+      // ---- 3. decode the own page (block) and the two halos (the last two warps,
+      // while the others write the own digits); digits listed as own | previous
+      // halo | next halo
+      const int n_own = ok ? h.n_dig : 0;
+      const int n_prev = okp ? hp.n_dig - hp.hi_dig : 0;
+      const int n_next = okn ? hn.lo_dig : 0;
+      ndig = n_own + n_prev + n_next;
+      listed = use_list && ndig <= kList;
+      {
+        const Seg gp{reinterpret_cast<const uint16_t*>(hprev), hp.n_tb - hp.hi_tb,
+                     reinterpret_cast<const uint16_t*>(hprev + kHaloRunOff), hp.n_runs - hp.hi_runs,
+                     reinterpret_cast<const uint32_t*>(hprev + kHaloAdcOff), hp.hi_dig % 3, n_prev,
+                     kHalo - kFrag, kFrag * (f - 1), listed ? n_own : kList, false};
+        const Seg gn{reinterpret_cast<const uint16_t*>(hnext), hn.lo_tb,
+                     reinterpret_cast<const uint16_t*>(hnext + kHaloRunOff), hn.lo_runs,
+                     reinterpret_cast<const uint32_t*>(hnext + kHaloAdcOff), 0, n_next, kHalo + kFrag, kFrag * (f + 1),
+                     listed ? n_own + n_prev : kList, false};
+        const Seg go{reinterpret_cast<const uint16_t*>(own + 32), h.n_tb,
+                     reinterpret_cast<const uint16_t*>(own + 32 + 2 * h.n_tb), h.n_runs,
+                     reinterpret_cast<const uint32_t*>(own + h.body), 0, h.n_dig, kHalo, kFrag * f,
+                     listed ? 0 : kList, true};
+        const int nrun_all = (okp ? hp.n_runs - hp.hi_runs : 0) + (ok ? h.n_runs : 0) + (okn ? hn.lo_runs : 0);
+        if (ok && listed && nrun_all <= kMaxRuns) {
+          const WinSeg s0{gp.ent, gp.run, gp.adc, okp ? gp.ne : 0, okp ? gp.nrun : 0, n_prev, gp.dfirst, gp.tt_base,
+                          gp.t_base_abs};
+          const WinSeg s1{go.ent, go.run, go.adc, go.ne, go.nrun, n_own, 0, go.tt_base, go.t_base_abs};
+          const WinSeg s2{gn.ent, gn.run, gn.adc, okn ? gn.ne : 0, okn ? gn.nrun : 0, n_next, 0, gn.tt_base,
+                          gn.t_base_abs};
+          ok = decode_window(s0, s1, s2, np, ps_stride, nw, T, S);
+        } else {
+          ok = decode_seg(go, ok, np, ps_stride, nw, T, S, okp ? &gp : nullptr, okn ? &gn : nullptr);
+        }
+      }
+      if (!ok && tid == 0) atomicOr(W.err, kErrCorrupt);
+      __syncthreads();
+    } else {
+      // ---- 1-3 (dense variant): rows t0-3 .. t0+258 of the dense plane, as
+      // 16-byte chunks of 8 pads (a warp-uniform loop, kDenseU chunks a thread
+      // in flight), into the shared plane with their occupancy bits; the digit
+      // list is filled in the same pass.  Its order is free (the peak test and
+      // the clearing do not depend on it): a warp scan of the chunks' digit
+      // counts and one shared atomic per warp and round give the slots.
+      const int sr = (int)(w / (unsigned)G.n_frag);
+      const size_t rbase = (size_t)sr * T;
+      const int cpr = (int)(W.dense_stride >> 3);
+      const int nitems = kWinT * cpr;
+      const uint4* dsrc = reinterpret_cast<const uint4*>(W.dense);
+      const int lane = tid & 31;
+      if (tid == 0) S.misc[8] = 0;
+      __syncthreads();
+      const uint32_t cmagic = (uint32_t)((0x100000000ull + cpr - 1) / cpr);   // i / cpr = umulhi(i, cmagic)
+      for (int i0 = tid - lane; i0 < nitems; i0 += kDenseU * (int)blockDim.x) {
+        uint4 v[kDenseU];
+#pragma unroll
+        for (int u = 0; u < kDenseU; u++) {
+          const int i = i0 + u * (int)blockDim.x + lane;
+          v[u] = make_uint4(0u, 0u, 0u, 0u);
+          if (i < nitems) {
+            const int tt = (int)__umulhi((uint32_t)i, cmagic), c = i - tt * cpr;
+            const int t = kFrag * f + tt - kHalo;
+            if (t >= 0 && t < T) v[u] = __ldg(dsrc + (rbase + t) * cpr + c);
           }
         }
-        okk = __shfl_sync(0xffffffffu, okk, 0);
-        a = __shfl_sync(0xffffffffu, a, 0);
-        b = __shfl_sync(0xffffffffu, b, 0);
-        if (okk) {
-          const int part = wid % 3;
-          const int doff = part == 0 ? 0 : (part == 1 ? kHaloRunOff : kHaloAdcOff);
-          copy_u16_warp(reinterpret_cast<uint16_t*>(S.halo + nb * kHaloStage + doff),
-                        W.pages + S.offs[2 * nb], a, b);
+        // plane and occupancy; the chunks' digit bits kept for the list
+        unsigned long long bits = 0;
+        int n = 0;
+#pragma unroll
+        for (int u = 0; u < kDenseU; u++) {
+          const uint32_t wv[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+          if (wv[0] | wv[1] | wv[2] | wv[3]) {   // most chunks are empty
+            const int i = i0 + u * (int)blockDim.x + lane;
+            const int tt = (int)__umulhi((uint32_t)i, cmagic), c = i - tt * cpr;
+            const int L0 = tt * ps_stride + kPad + 8 * c;
+            uint32_t bits8 = 0;
+#pragma unroll
+            for (int j = 0; j < 8; j++) {
+              const uint16_t q = (uint16_t)(wv[j >> 1] >> (16 * (j & 1)));
+              if (q && 8 * c + j < np) {
+                S.plane[L0 + j] = q;
+                bits8 |= 1u << j;
+              }
+            }
+            if (bits8) atomicOr(&S.occ[tt * nw + ((8 * c) >> 5)], bits8 << ((8 * c) & 31));
+            bits |= (unsigned long long)bits8 << (8 * u);
+            n += __popc(bits8);
+          }
         }
-      } else if (wid == 6 && lane == 0) {
-        PageHdr hh;
-        const bool okk = parse_header(reinterpret_cast<const uint4*>(own_global ? W.pages + off : own_stage), off,
-                                      W.pages_bytes, hh) &&
-                         hh.sector == s && hh.row == r && hh.frag == f;
-        S.ph[0] = hh;
-        S.misc[4] = okk;
+        // list slots: a warp scan of the threads' digit counts, one atomic a warp
+        int incl = n;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+          const int y = __shfl_up_sync(0xffffffffu, incl, d);
+          if (lane >= d) incl += y;
+        }
+        int base = 0;
+        if (lane == 31 && incl) base = atomicAdd(&S.misc[8], incl);
+        base = __shfl_sync(0xffffffffu, base, 31);
+        int k = base + incl - n;
+        while (bits) {
+          const int bpos = __ffsll((long long)bits) - 1;
+          bits &= bits - 1;
+          const int u = bpos >> 3, j = bpos & 7;
+          const int i = i0 + u * (int)blockDim.x + lane;
+          const int tt = (int)__umulhi((uint32_t)i, cmagic), c = i - tt * cpr;
+          if (use_list && k < kList) S.list[k] = (uint16_t)(tt * ps_stride + kPad + 8 * c + j);
+          k++;
+        }
       }
+      __syncthreads();
+      ndig = S.misc[8];
+      listed = use_list && ndig <= kList;
+      ok = true;
+      __syncthreads();
     }
-    __syncthreads();
-    bool ok = S.misc[4];
-    const bool okp = S.misc[5], okn = S.misc[6];
-    const PageHdr& h = S.ph[0];
-    const PageHdr& hp = S.ph[1];
-    const PageHdr& hn = S.ph[2];
-    const uint8_t* own = (own_global || h.len > copied) ? W.pages + off : own_stage;
-    uint8_t* hprev = S.halo;
-    uint8_t* hnext = S.halo + kHaloStage;
-
-    // ---- 3. decode the own page (block) and the two halos (the last two warps,
-    // while the others write the own digits); digits listed as own | previous
-    // halo | next halo
-    const int n_own = ok ? h.n_dig : 0;
-    const int n_prev = okp ? hp.n_dig - hp.hi_dig : 0;
-    const int n_next = okn ? hn.lo_dig : 0;
-    const int ndig = n_own + n_prev + n_next;
-    const bool listed = use_list && ndig <= kList;
-    {
-      const Seg gp{reinterpret_cast<const uint16_t*>(hprev), hp.n_tb - hp.hi_tb,
-                   reinterpret_cast<const uint16_t*>(hprev + kHaloRunOff), hp.n_runs - hp.hi_runs,
-                   reinterpret_cast<const uint32_t*>(hprev + kHaloAdcOff), hp.hi_dig % 3, n_prev,
-                   kHalo - kFrag, kFrag * (f - 1), listed ? n_own : kList, false};
-      const Seg gn{reinterpret_cast<const uint16_t*>(hnext), hn.lo_tb,
-                   reinterpret_cast<const uint16_t*>(hnext + kHaloRunOff), hn.lo_runs,
-                   reinterpret_cast<const uint32_t*>(hnext + kHaloAdcOff), 0, n_next, kHalo + kFrag, kFrag * (f + 1),
-                   listed ? n_own + n_prev : kList, false};
-      const Seg go{reinterpret_cast<const uint16_t*>(own + 32), h.n_tb,
-                   reinterpret_cast<const uint16_t*>(own + 32 + 2 * h.n_tb), h.n_runs,
-                   reinterpret_cast<const uint32_t*>(own + h.body), 0, h.n_dig, kHalo, kFrag * f,
-                   listed ? 0 : kList, true};
-      const int nrun_all = (okp ? hp.n_runs - hp.hi_runs : 0) + (ok ? h.n_runs : 0) + (okn ? hn.lo_runs : 0);
-      if (ok && listed && nrun_all <= kMaxRuns) {
-        const WinSeg s0{gp.ent, gp.run, gp.adc, okp ? gp.ne : 0, okp ? gp.nrun : 0, n_prev, gp.dfirst, gp.tt_base,
-                        gp.t_base_abs};
-        const WinSeg s1{go.ent, go.run, go.adc, go.ne, go.nrun, n_own, 0, go.tt_base, go.t_base_abs};
-        const WinSeg s2{gn.ent, gn.run, gn.adc, okn ? gn.ne : 0, okn ? gn.nrun : 0, n_next, 0, gn.tt_base,
-                        gn.t_base_abs};
-        ok = decode_window(s0, s1, s2, np, ps_stride, nw, T, S);
-      } else {
-        ok = decode_seg(go, ok, np, ps_stride, nw, T, S, okp ? &gp : nullptr, okn ? &gn : nullptr);
-      }
-    }
-    if (!ok && tid == 0) atomicOr(W.err, kErrCorrupt);
-    __syncthreads();
 
     if (kScratch && tid == 0 && nt < n_windows) {
       for (int k = 0; k < 4; k++) {
@@ -765,136 +884,149 @@ k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
       }
     }
 
-    // ---- 4. peak test, one digit per thread (rows 1..260; rows 0 and 261 only
-    // serve as neighbours)
-    if (ok) {
-      if (listed) {
-        for (int i = tid; i < ndig; i += blockDim.x) {
-          const int L = S.list[i];
-          if (L >= nplane) continue;
-          const int tt = (int)__umulhi((uint32_t)L, magic);
-          if (tt < 1 || tt > kWinT - 2) continue;
-          if (peak_at(S.plane, L, ps_stride, P.q_peak_min)) {
-            const int p = L - tt * ps_stride - kPad;
-            atomicOr(&S.pk[tt * nw + (p >> 5)], 1u << (p & 31));
+    if (kMode == 1) {
+      if (kScratch && tid == 0 && nt < n_windows) prefetch_next_pages(W, noffs);
+      // ---- dense variant, decode pass: the window's own rows into the dense
+      // plane, 16-byte chunks of 8 pads (pads past the row's end written as 0)
+      const int sr = (int)(w / (unsigned)G.n_frag);
+      const int nrows = min(kFrag, T - kFrag * f);
+      const int cpr = (int)(W.dense_stride >> 3);
+      uint4* ddst = reinterpret_cast<uint4*>(W.dense) + ((size_t)sr * T + (size_t)kFrag * f) * cpr;
+      for (int i = tid; i < nrows * cpr; i += blockDim.x) {
+        const int q = i / cpr, c = i - q * cpr;
+        const uint16_t* src = S.plane + (q + kHalo) * ps_stride + kPad + 8 * c;
+        uint32_t wv[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+          const uint32_t lo = 8 * c + 2 * j < np ? src[2 * j] : 0u;
+          const uint32_t hi = 8 * c + 2 * j + 1 < np ? src[2 * j + 1] : 0u;
+          wv[j] = lo | (hi << 16);
+        }
+        ddst[i] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+      }
+      __syncthreads();
+    } else {
+      // ---- 4. peak test, one digit per thread (rows 1..260; rows 0 and 261 only
+      // serve as neighbours)
+      if (ok) {
+        if (listed) {
+          for (int i = tid; i < ndig; i += blockDim.x) {
+            const int L = S.list[i];
+            if (L >= nplane) continue;
+            const int tt = (int)__umulhi((uint32_t)L, magic);
+            if (tt < 1 || tt > kWinT - 2) continue;
+            if (peak_at(S.plane, L, ps_stride, P.q_peak_min)) {
+              const int p = L - tt * ps_stride - kPad;
+              atomicOr(&S.pk[tt * nw + (p >> 5)], 1u << (p & 31));
+            }
+          }
+        } else {
+          // too many digits to list: walk the occupancy bitmap
+          for (int wi_ = nw + tid; wi_ < (kWinT - 1) * nw; wi_ += blockDim.x) {
+            uint32_t word = S.occ[wi_];
+            const int tt = wi_ / nw, p0 = (wi_ % nw) * 32;
+            while (word) {
+              const int b = __ffs(word) - 1;
+              word &= word - 1;
+              if (peak_at(S.plane, tt * ps_stride + kPad + p0 + b, ps_stride, P.q_peak_min))
+                atomicOr(&S.pk[wi_], 1u << b);
+            }
           }
         }
-      } else {
-        // too many digits to list: walk the occupancy bitmap
-        for (int wi_ = nw + tid; wi_ < (kWinT - 1) * nw; wi_ += blockDim.x) {
-          uint32_t word = S.occ[wi_];
-          const int tt = wi_ / nw, p0 = (wi_ % nw) * 32;
+      }
+      __syncthreads();
+
+      if (kScratch && tid == 0 && nt < n_windows) {
+        if (kMode == 2) prefetch_next_dense(G, W, nt);
+        else prefetch_next_pages(W, noffs);
+      }
+
+      // ---- 5. rank the own peaks (rows 3..258) in canonical order, list the
+      // first kStage, publish the window's count
+      int npk;
+      {
+        const int w0 = tid * opt, w1 = min(w0 + opt, nown_words);
+        int c = 0;
+        for (int i = w0; i < w1; i++) c += __popc(S.pk[kHalo * nw + i]);
+        uint32_t tot;
+        const uint32_t pre = block_excl_scan32((uint32_t)c, reinterpret_cast<uint32_t*>(S.scan), &tot);
+        int run = (int)pre;
+        for (int i = w0; i < w1; i++) {
+          uint32_t word = S.pk[kHalo * nw + i];
+          S.ppre[i] = (uint16_t)run;
           while (word) {
             const int b = __ffs(word) - 1;
             word &= word - 1;
-            if (peak_at(S.plane, tt * ps_stride + kPad + p0 + b, ps_stride, P.q_peak_min))
-              atomicOr(&S.pk[wi_], 1u << b);
+            if (run < kStage && use_list) {
+              const int wi_ = i + kHalo * nw;
+              S.plist[run] = (uint16_t)((wi_ / nw) * ps_stride + kPad + (wi_ % nw) * 32 + b);
+            }
+            run++;
           }
         }
+        if (tid == 0) {
+          S.ppre[nown_words] = (uint16_t)tot;
+          if (!kScratch) lookback_publish(W.win_state, (long long)w, tot);
+        }
+        npk = (int)tot;
       }
-    }
-    __syncthreads();
+      __syncthreads();
 
-    if (kScratch && tid == 0 && nt < n_windows) {
-      // next window: its page and both neighbours are contiguous in the usual
-      // layout; prefetch that byte range (at most 64 KB) into L2
-      const unsigned long long lo = noffs[0] != ~0ull ? noffs[0] : noffs[1];
-      unsigned long long hi = noffs[3] != ~0ull ? noffs[3] : W.pages_bytes;
-      if (lo < hi && lo < W.pages_bytes && (lo & 15) == 0) {
-        hi = min(hi, (unsigned long long)W.pages_bytes);
-        const unsigned long long n = min(hi - lo, 65536ull) & ~15ull;
-        if (n) {
-          const size_t ga = __cvta_generic_to_global(W.pages + lo);
-          asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(ga), "r"((unsigned)n) : "memory");
+      // ---- 6. clusters of the first kStage peaks, one thread each, staged
+      const int nst = min(npk, kStage);
+      for (int k = tid; k < nst; k += blockDim.x) {
+        int tt, p;
+        if (use_list) {
+          const int L = S.plist[k];
+          tt = (int)__umulhi((uint32_t)L, magic);
+          p = L - tt * ps_stride - kPad;
+        } else {   // rows too wide for 16-bit plane indices
+          const int wo = rank_search(S.ppre, nown_words + 1, k);
+          tt = kHalo + wo / nw;
+          p = (wo % nw) * 32 + __fns(S.pk[kHalo * nw + wo], 0, k - (int)S.ppre[wo] + 1);
+        }
+        make_cluster(S, ps_stride, nw, np, T, s, r, f, tt, p, G.xrow[r], S.st_rec[k], S.st_xyz[k]);
+      }
+
+      // ---- 7. where the records go: a scratch span (one atomic) or, without
+      // scratch, the canonical offset from the decoupled look-back
+      if (kScratch) {
+        if (tid == 0) {
+          const unsigned long long so = atomicAdd(&W.ctr[CTR_SCURSOR], (unsigned long long)npk);
+          if (so + npk > W.cap_cl) atomicOr(W.err, kErrOverflowCl);
+          W.win_cnt[w] = (unsigned long long)npk;
+          W.win_soff[w] = (uint32_t)min(so, (unsigned long long)W.cap_cl);
+          S.scan[33] = so;
+        }
+      } else if (tid < 32) {
+        const unsigned long long base = lookback_wait(W.win_state, (long long)w, (unsigned long long)npk, W.err);
+        if (tid == 0) {
+          S.scan[33] = base;
+          if (w == n_windows - 1) W.ctr[CTR_NCL] = base + npk;
+          if (base + npk > W.cap_cl) atomicOr(W.err, kErrOverflowCl);
         }
       }
-    }
+      __syncthreads();
+      const unsigned long long base = S.scan[33];
+      tpc_cluster* const dst = kScratch ? W.scratch_cl : W.clusters;
 
-    // ---- 5. rank the own peaks (rows 3..258) in canonical order, list the
-    // first kStage, publish the window's count
-    int npk;
-    {
-      const int w0 = tid * opt, w1 = min(w0 + opt, nown_words);
-      int c = 0;
-      for (int i = w0; i < w1; i++) c += __popc(S.pk[kHalo * nw + i]);
-      uint32_t tot;
-      const uint32_t pre = block_excl_scan32((uint32_t)c, reinterpret_cast<uint32_t*>(S.scan), &tot);
-      int run = (int)pre;
-      for (int i = w0; i < w1; i++) {
-        uint32_t word = S.pk[kHalo * nw + i];
-        S.ppre[i] = (uint16_t)run;
-        while (word) {
-          const int b = __ffs(word) - 1;
-          word &= word - 1;
-          if (run < kStage && use_list) {
-            const int wi_ = i + kHalo * nw;
-            S.plist[run] = (uint16_t)((wi_ / nw) * ps_stride + kPad + (wi_ % nw) * 32 + b);
-          }
-          run++;
+      // ---- 8. write out: staged records coalesced, any beyond one thread each
+      for (int k = tid; k < npk; k += blockDim.x) {
+        const unsigned long long idx = base + k;
+        if (idx >= W.cap_cl) break;   // overflow: keep [0, cap) free of gaps, drop the rest
+        uint4 rec;
+        int4 xyz;
+        if (k < kStage) {
+          rec = S.st_rec[k];
+        } else {
+          const int wo = rank_search(S.ppre, nown_words + 1, k);
+          const int bit = __fns(S.pk[kHalo * nw + wo], 0, k - (int)S.ppre[wo] + 1);
+          make_cluster(S, ps_stride, nw, np, T, s, r, f, kHalo + wo / nw, (wo % nw) * 32 + bit, G.xrow[r], rec, xyz);
         }
+        reinterpret_cast<uint4*>(dst)[idx] = rec;
       }
-      if (tid == 0) {
-        S.ppre[nown_words] = (uint16_t)tot;
-        if (!kScratch) lookback_publish(W.win_state, (long long)w, tot);
-      }
-      npk = (int)tot;
+      __syncthreads();
     }
-    __syncthreads();
-
-    // ---- 6. clusters of the first kStage peaks, one thread each, staged
-    const int nst = min(npk, kStage);
-    for (int k = tid; k < nst; k += blockDim.x) {
-      int tt, p;
-      if (use_list) {
-        const int L = S.plist[k];
-        tt = (int)__umulhi((uint32_t)L, magic);
-        p = L - tt * ps_stride - kPad;
-      } else {   // rows too wide for 16-bit plane indices
-        const int wo = rank_search(S.ppre, nown_words + 1, k);
-        tt = kHalo + wo / nw;
-        p = (wo % nw) * 32 + __fns(S.pk[kHalo * nw + wo], 0, k - (int)S.ppre[wo] + 1);
-      }
-      make_cluster(S, ps_stride, nw, np, T, s, r, f, tt, p, G.xrow[r], S.st_rec[k], S.st_xyz[k]);
-    }
-
-    // ---- 7. where the records go: a scratch span (one atomic) or, without
-    // scratch, the canonical offset from the decoupled look-back
-    if (kScratch) {
-      if (tid == 0) {
-        const unsigned long long so = atomicAdd(&W.ctr[CTR_SCURSOR], (unsigned long long)npk);
-        if (so + npk > W.cap_cl) atomicOr(W.err, kErrOverflowCl);
-        W.win_cnt[w] = (unsigned long long)npk;
-        W.win_soff[w] = (uint32_t)min(so, (unsigned long long)W.cap_cl);
-        S.scan[33] = so;
-      }
-    } else if (tid < 32) {
-      const unsigned long long base = lookback_wait(W.win_state, (long long)w, (unsigned long long)npk, W.err);
-      if (tid == 0) {
-        S.scan[33] = base;
-        if (w == n_windows - 1) W.ctr[CTR_NCL] = base + npk;
-        if (base + npk > W.cap_cl) atomicOr(W.err, kErrOverflowCl);
-      }
-    }
-    __syncthreads();
-    const unsigned long long base = S.scan[33];
-    tpc_cluster* const dst = kScratch ? W.scratch_cl : W.clusters;
-
-    // ---- 8. write out: staged records coalesced, any beyond one thread each
-    for (int k = tid; k < npk; k += blockDim.x) {
-      const unsigned long long idx = base + k;
-      if (idx >= W.cap_cl) break;   // overflow: keep [0, cap) free of gaps, drop the rest
-      uint4 rec;
-      int4 xyz;
-      if (k < kStage) {
-        rec = S.st_rec[k];
-      } else {
-        const int wo = rank_search(S.ppre, nown_words + 1, k);
-        const int bit = __fns(S.pk[kHalo * nw + wo], 0, k - (int)S.ppre[wo] + 1);
-        make_cluster(S, ps_stride, nw, np, T, s, r, f, kHalo + wo / nw, (wo % nw) * 32 + bit, G.xrow[r], rec, xyz);
-      }
-      reinterpret_cast<uint4*>(dst)[idx] = rec;
-    }
-    __syncthreads();
 
     if (kScratch && tid == 0) {
       S.misc[1] = (int)nt;
@@ -970,13 +1102,33 @@ cudaError_t launch_scan(uint64_t* v, const unsigned long long* n_ptr, unsigned l
 
 // Raise the finder's dynamic shared-memory limit on the current device (once
 // per context, outside any stream capture).
-cudaError_t prepare_find() {
-  cudaError_t e = cudaFuncSetAttribute(k_find_clusters<true, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+template <int kMode>
+static cudaError_t prepare_mode() {
+  cudaError_t e = cudaFuncSetAttribute(k_find_clusters<true, 256, kMode>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       227 * 1024);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_find_clusters<true, 384>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    e = cudaFuncSetAttribute(k_find_clusters<true, 384, kMode>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_find_clusters<true, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    e = cudaFuncSetAttribute(k_find_clusters<true, 512, kMode>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   return e;
+}
+
+cudaError_t prepare_find() {
+  cudaError_t e = prepare_mode<0>();
+  if (e == cudaSuccess) e = prepare_mode<1>();
+  if (e == cudaSuccess) e = prepare_mode<2>();
+  return e;
+}
+
+template <int kMode>
+static void launch_find_mode(const DevGeom& G, const DevParams& P, const DevWork& W, unsigned int n_windows,
+                             unsigned grid, int threads, size_t sm, cudaStream_t st) {
+  if (threads == 256)
+    k_find_clusters<true, 256, kMode><<<grid, 256, sm, st>>>(G, P, W, n_windows);
+  else if (threads == 512)
+    k_find_clusters<true, 512, kMode><<<grid, 512, sm, st>>>(G, P, W, n_windows);
+  else
+    k_find_clusters<true, 384, kMode><<<grid, 384, sm, st>>>(G, P, W, n_windows);
 }
 
 cudaError_t launch_find(const DevGeom& G, const DevParams& P, const DevWork& W, unsigned int n_windows,
@@ -986,12 +1138,14 @@ cudaError_t launch_find(const DevGeom& G, const DevParams& P, const DevWork& W, 
   // persistent CTAs: find_ctas_per_sm per SM (at most 2 fit the shared memory)
   unsigned int grid = (unsigned int)min((long long)n_windows, (long long)n_sm * L.find_ctas_per_sm);
   if (grid == 0) grid = 1;
-  if (L.find_threads == 256)
-    k_find_clusters<true, 256><<<grid, 256, sm, st>>>(G, P, W, n_windows);
-  else if (L.find_threads == 512)
-    k_find_clusters<true, 512><<<grid, 512, sm, st>>>(G, P, W, n_windows);
-  else
-    k_find_clusters<true, 384><<<grid, 384, sm, st>>>(G, P, W, n_windows);
+  if (W.dense) {
+    // dense-plane variant: decode every window into the plane, then find
+    launch_find_mode<1>(G, P, W, n_windows, grid, L.find_threads, sm, st);
+    launch_find_mode<2>(G, P, W, n_windows, grid, L.find_threads, sm, st);
+    *launches += 1;
+  } else {
+    launch_find_mode<0>(G, P, W, n_windows, grid, L.find_threads, sm, st);
+  }
   cudaError_t e = launch_scan(reinterpret_cast<uint64_t*>(W.win_cnt), W.ctr + CTR_NWIN, n_windows, win_scan_state,
                               W.tickets + TK_SCAN_W, W.ctr + CTR_NCL, W.err, n_sm, st);
   if (e != cudaSuccess) return e;
@@ -1059,7 +1213,7 @@ extern "C" tpc_status tpc_find_clusters_noalloc(const tpc_geometry* geom, const 
       void* ptr = nullptr;
       if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr)
         return fail(TPC_E_CUDA, "tpc_find_clusters_noalloc: cudaGetSymbolAddress failed");
-      if (cudaFuncSetAttribute(k_find_clusters<false, kFindThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) !=
+      if (cudaFuncSetAttribute(k_find_clusters<false, kFindThreads, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) !=
           cudaSuccess)
         return fail(TPC_E_CUDA, "tpc_find_clusters_noalloc: cudaFuncSetAttribute failed");
       g_noalloc_addr[device] = static_cast<unsigned long long*>(ptr);
@@ -1098,7 +1252,7 @@ extern "C" tpc_status tpc_find_clusters_noalloc(const tpc_geometry* geom, const 
   int n_sm = 148;
   cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, device);
   unsigned grid = (unsigned)std::min<unsigned long long>(nwin, (unsigned long long)n_sm * 2);
-  k_find_clusters<false, kFindThreads><<<grid ? grid : 1, kFindThreads, smem, st>>>(G, P, W, (unsigned)nwin);
+  k_find_clusters<false, kFindThreads, 0><<<grid ? grid : 1, kFindThreads, smem, st>>>(G, P, W, (unsigned)nwin);
   if (cudaGetLastError() != cudaSuccess) return fail(TPC_E_CUDA, "tpc_find_clusters_noalloc: launch failed");
   unsigned long long ctrl[CTR_COUNT + 1];
   if (cudaMemcpyAsync(ctrl, W.ctr, sizeof ctrl, cudaMemcpyDeviceToHost, st) != cudaSuccess ||

@@ -67,7 +67,7 @@ struct Slot {
   // device buffers
   Buf pages, offsets, winstate, cl, clx, cly, clz, clt, rowstart, chrow, up, down, score, edge, jump, chlen, scanv,
       scanst, chainof, clchain, ch_i32, besta, bestb, trk_i32, trackcl, cl2trk, tracks, ctrl, scratch, wincnt, winsoff,
-      candab, candsc, lenhist, evinfo, xs, cmp, cal;
+      candab, candsc, lenhist, evinfo, xs, cmp, cal, dense;
   unsigned long long* h_ctrl = nullptr;   // pinned copy of [ctr | err]
   // batch tables, device (evinfo) and pinned host copy, same layout:
   // u64 base[kMaxBatch], u64 bytes[kMaxBatch], u32 cl_start[kMaxBatch + 1],
@@ -210,8 +210,9 @@ static cudaError_t ensure(Buf& b, size_t bytes) {
   return e;
 }
 
-static size_t slot_bytes(uint64_t pages, uint64_t windows, uint64_t cap_cl, uint64_t cap_ch, int nsr) {
-  size_t b = pages + 16 + windows * 28 + cap_cl * (16 + 16 + 16 + 8 + 8 + 8 + 8 + 4 + 8 + 4 + 4 + 4 + 4) +
+static size_t slot_bytes(uint64_t pages, uint64_t windows, uint64_t cap_cl, uint64_t cap_ch, int nsr,
+                         size_t dense = 0) {
+  size_t b = dense + pages + 16 + windows * 28 + cap_cl * (16 + 16 + 16 + 8 + 8 + 8 + 8 + 4 + 8 + 4 + 4 + 4 + 4) +
              (scan_tiles(cap_cl) + scan_tiles(cap_ch) + scan_tiles(windows)) * 8 +
              cap_ch * (14 * 4 + 8 + 16 + sizeof(tpc_track) + 4 * 12) +
              (size_t)(nsr + 1) * 8 + 1024;
@@ -223,9 +224,13 @@ static tpc_status slot_reserve(tpc_context* ctx, Slot& s, uint64_t pages_bytes, 
   const int nsr = ctx->geom.n_sectors * ctx->geom.n_rows * (int)s.n_events;
   uint64_t cap_ch = cap_cl / (uint64_t)ctx->params.min_chain + 16;
   uint64_t want_pages = need_pages ? pages_bytes : 0;
-  size_t cur = slot_bytes(s.cap_pages, s.cap_windows, s.cap_cl, s.cap_ch, nsr);
+  // dense-plane finder variant: one ADC per (sector row, time bin, pad)
+  const size_t dstride = (size_t)((ctx->geom.npmax + 7) & ~7);
+  const size_t want_dense = (ctx->flags & TPC_CTX_DENSE_FINDER) ? (size_t)windows * kFrag * dstride * 2 : 0;
+  size_t cur = slot_bytes(s.cap_pages, s.cap_windows, s.cap_cl, s.cap_ch, nsr, s.dense.bytes);
   size_t need = slot_bytes(std::max(s.cap_pages, want_pages), std::max(s.cap_windows, windows),
-                           std::max(s.cap_cl, cap_cl), std::max(s.cap_ch, cap_ch), nsr);
+                           std::max(s.cap_cl, cap_cl), std::max(s.cap_ch, cap_ch), nsr,
+                           std::max(s.dense.bytes, want_dense));
   if (ctx->used - cur + need > ctx->budget)
     return fail(TPC_E_NOMEM, "timeframe needs " + std::to_string(need) + " device bytes; budget left " +
                                  std::to_string(ctx->budget - ctx->used + cur));
@@ -262,15 +267,18 @@ static tpc_status slot_reserve(tpc_context* ctx, Slot& s, uint64_t pages_bytes, 
   CUDA_TRY(ensure(s.scanst, (scan_tiles(s.cap_cl) + scan_tiles(s.cap_ch) + scan_tiles(s.cap_windows)) * 8));
   CUDA_TRY(ensure(s.rowstart, (size_t)(nsr + 1) * 4));
   CUDA_TRY(ensure(s.chrow, (size_t)(nsr + 1) * 4));
+  if (want_dense) CUDA_TRY(ensure(s.dense, want_dense));
   CUDA_TRY(ensure(s.ctrl, 256));
   CUDA_TRY(ensure(s.lenhist, 512 * 4));
-  ctx->used = ctx->used - cur + slot_bytes(s.cap_pages, s.cap_windows, s.cap_cl, s.cap_ch, nsr);
+  ctx->used = ctx->used - cur + slot_bytes(s.cap_pages, s.cap_windows, s.cap_cl, s.cap_ch, nsr, s.dense.bytes);
   // wire the work-space pointers
   DevWork& W = s.W;
   W.clusters = (tpc_cluster*)s.cl.p;
   W.cl_x = (int32_t*)s.clx.p; W.cl_y = (int32_t*)s.cly.p; W.cl_z = (int32_t*)s.clz.p; W.cl_t = (int32_t*)s.clt.p;
   W.row_start = (uint32_t*)s.rowstart.p;
   W.ch_row_start = (uint32_t*)s.chrow.p;
+  W.dense = (ctx->flags & TPC_CTX_DENSE_FINDER) ? (uint16_t*)s.dense.p : nullptr;
+  W.dense_stride = (uint32_t)dstride;
   W.win_state = (unsigned long long*)s.winstate.p;
   W.scratch_cl = (tpc_cluster*)s.scratch.p;
   W.win_cnt = (unsigned long long*)s.wincnt.p;
@@ -313,7 +321,7 @@ static void slot_free(tpc_context* ctx, Slot& s) {
   Buf* all[] = {&s.pages, &s.offsets, &s.winstate, &s.cl, &s.clx, &s.cly, &s.clz, &s.clt, &s.rowstart, &s.chrow, &s.up,
                 &s.down, &s.score, &s.edge, &s.jump, &s.chlen, &s.scanv, &s.scanst, &s.chainof, &s.clchain,
                 &s.ch_i32, &s.besta, &s.bestb, &s.trk_i32, &s.trackcl, &s.cl2trk, &s.tracks, &s.ctrl,
-                &s.scratch, &s.wincnt, &s.winsoff, &s.candab, &s.candsc, &s.lenhist, &s.evinfo, &s.xs, &s.cmp, &s.cal};
+                &s.scratch, &s.wincnt, &s.winsoff, &s.candab, &s.candsc, &s.lenhist, &s.evinfo, &s.xs, &s.cmp, &s.cal, &s.dense};
   for (Buf* b : all) free_buf(*b);
   for (auto& e : s.ev_stage) if (e) cudaEventDestroy(e);
   if (s.ev_done) cudaEventDestroy(s.ev_done);
@@ -649,11 +657,11 @@ static void reclaim_idle(tpc_context* ctx, const Slot* keep) {
   for (auto& c : ctx->slots) {
     if (c.in_use || &c == keep || !c.cap_pages && !c.cap_cl) continue;
     cudaStreamSynchronize(c.stream);
-    ctx->used -= slot_bytes(c.cap_pages, c.cap_windows, c.cap_cl, c.cap_ch, nsr1 * (int)c.n_events);
+    ctx->used -= slot_bytes(c.cap_pages, c.cap_windows, c.cap_cl, c.cap_ch, nsr1 * (int)c.n_events, c.dense.bytes);
     Buf* big[] = {&c.pages, &c.offsets, &c.winstate, &c.cl, &c.clx, &c.cly, &c.clz, &c.clt, &c.up, &c.down,
                   &c.score, &c.edge, &c.jump, &c.chlen, &c.scanv, &c.scanst, &c.chainof, &c.clchain, &c.ch_i32,
                   &c.besta, &c.bestb, &c.trk_i32, &c.trackcl, &c.cl2trk, &c.tracks, &c.scratch, &c.wincnt,
-                  &c.winsoff, &c.candab, &c.candsc, &c.xs, &c.cmp, &c.cal};
+                  &c.winsoff, &c.candab, &c.candsc, &c.xs, &c.cmp, &c.cal, &c.dense};
     for (Buf* b : big) free_buf(*b);
     ctx->used -= c.xs_bytes + c.cmp_bytes + c.cal_bytes;
     c.xs_bytes = c.cmp_bytes = c.cal_bytes = 0;

@@ -84,6 +84,8 @@ struct DevWork {
   tpc_cluster* clusters;
   int32_t* cl_x; int32_t* cl_y; int32_t* cl_z; int32_t* cl_t;
   uint32_t* row_start;           // [n_sectors * n_rows + 1]
+  uint16_t* dense;               // dense-plane finder variant: [sector row][time bin][dense_stride] ADC
+  uint32_t dense_stride;         // pads per dense time row (npmax rounded up to 8)
   unsigned long long* win_state;  // look-back states of the finder windows (allocation-free mode)
   tpc_cluster* scratch_cl;       // finder output, window spans in completion order
   unsigned long long* win_cnt;   // clusters per window, scanned in place to canonical bases
@@ -138,7 +140,7 @@ enum {
   CTR_NCAND = 23,     // merge candidate pairs found
   CTR_COUNT = 24
 };
-enum { TK_FIND = 0, TK_SCAN_A = 1, TK_SCAN_B = 2, TK_SCAN_W = 3, kNumTickets = 4 };
+enum { TK_FIND = 0, TK_SCAN_A = 1, TK_SCAN_B = 2, TK_SCAN_W = 3, TK_FIND2 = 4, kNumTickets = 5 };
 
 // ------------------------------------------------------------------ helpers
 __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {

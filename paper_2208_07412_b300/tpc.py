@@ -26,6 +26,7 @@ TPC_TF_DEVICE_INPUT = 1
 TPC_TF_NOWAIT = 2
 TPC_CTX_STAGE_TIMING = 1
 TPC_CTX_NO_GRAPHS = 2
+TPC_CTX_DENSE_FINDER = 4
 STAGES = ("find", "ca", "merge", "fit")
 
 CLUSTER_DTYPE = np.dtype([("pad_fp", "<u2"), ("time_fp", "<u2"), ("qmax", "<u2"), ("qtot", "<u2"),
