@@ -484,6 +484,30 @@ def finder_variants(tpc, torch, tf, pages_d, offs_d, tuning, flush, fused_ms, re
             "timing": f"find stage (decode + find + scan + compaction), mean of {reps}, L2 flushed"}
 
 
+def noise_suppression_stats(tpc, torch, tf, pages_d, offs_d, tuning, flush, n_cl, fused_ms, dip=10, reps=5):
+    """The optional step 2b (5x5 noise suppression, tpc_params.ns_min_dip):
+    clusters and tracks it leaves, and the find-stage time with it on."""
+    prm = tpc.tpc_params_default()
+    prm.ns_min_dip = dip
+    free_now, _ = torch.cuda.mem_get_info()
+    Rn = tpc.Reconstructor.for_timeframe(tf, params=prm, device=torch.cuda.current_device(),
+                                         flags=tpc.TPC_CTX_STAGE_TIMING, mem_budget=int(0.5 * free_now))
+    tpc.tpc_set_tuning(Rn.ctx, **tuning)
+    times = []
+    for i in range(reps + 2):
+        flush.fill_(1)
+        t = Rn.submit(pages_d, offs_d, tf.n_time_bins)
+        Rn.wait(t)
+        ctr = tpc.tpc_get_counters(Rn.ctx, t)
+        if i >= 2:
+            times.append(tpc.tpc_get_stage_times(Rn.ctx, t)["find"])
+        tpc.tpc_release(Rn.ctx, t)
+    Rn.close()
+    return {"ns_min_dip": dip, "clusters": ctr["clusters"], "tracks": ctr["tracks"],
+            "clusters_removed_frac": 1.0 - ctr["clusters"] / n_cl, "find_ms": statistics.mean(times),
+            "find_ms_without": fused_ms, "timing": f"find stage, mean of {reps}, L2 flushed"}
+
+
 def run_ours(args, world, rank, local):
     import torch
     from paper_2208_07412_b300 import tpc
@@ -667,6 +691,9 @@ def run_ours(args, world, rank, local):
         if world == 1 and not (args.no_variants or args.dense_finder) and args.workload in ("full_tpc", "continuous_50khz"):
             line["finder_variants"] = finder_variants(tpc, torch, tf, pages_d, offs_d, tuning, flush,
                                                       stages["find"])
+        if world == 1 and not args.no_variants and args.workload == "full_tpc":
+            line["noise_suppression"] = noise_suppression_stats(tpc, torch, tf, pages_d, offs_d, tuning, flush,
+                                                                n_cl, stages["find"])
         if world == 1 and not args.no_batched and args.workload == "full_tpc":
             line["batched"] = batched_vs_plain(tpc, torch, local, tuning=tuning)
         if world == 1 and not args.no_cpu_baseline:

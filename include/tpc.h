@@ -139,7 +139,7 @@ typedef struct {
   int32_t  merge_max_passes; /* 8 */
   int32_t  min_track;        /* 10   clusters per output track */
   int32_t  fit_passes;       /* 3    inward, outward, inward */
-  int32_t  reserved0;
+  int32_t  ns_min_dip;       /* 0    5x5 noise suppression (step 2b): 0 off, else 1..1023 ADC */
   double   bz;               /* 0.5  T */
   double   sigma_y;          /* 0.02 cm */
   double   sigma_z;          /* 0.03 cm */
@@ -233,6 +233,12 @@ void       tpc_destroy_context(tpc_context* ctx);
  *   2 peaks    pixel c is a peak iff q(c) >= q_peak_min and its key
  *              (q, -(t*npads + p)) is lexicographically greater than the key of
  *              each of its 8 neighbours in the same row.
+ *   2b noise suppression (only with ns_min_dip > 0): a peak c is dropped iff a
+ *              peak n of step 2 with a greater key lies on the ring of c's 5x5
+ *              window (max(|dp|, |dt|) = 2) and q(c) - q(m) < ns_min_dip, m the
+ *              pixel between them (the inner pixel of step 3 toward n).  Decided
+ *              on step 2's peak set, so the order of the peaks does not matter;
+ *              flag bit 2 of a cluster keeps referring to that set too.
  *   3 cluster  5x5 window around each peak: the inner 3x3 is always included; an
  *              outer pixel (dp, dt) is included iff q(outer) <= q(inner) and
  *              q(inner) > 0, inner = (sgn dp*min(|dp|,1), sgn dt*min(|dt|,1)).
@@ -513,7 +519,7 @@ tpc_status tpc_autotune(tpc_context* ctx, const tpc_timeframe_desc* sample, int 
  * cannot afford.  It computes exactly the clusters tpc_submit_timeframe
  * computes, with no context and no allocation of any kind.
  *   geom          host geometry object
- *   params        NULL for defaults; only q_peak_min is used
+ *   params        NULL for defaults; only q_peak_min and ns_min_dip are used
  *   device        CUDA device the pointers live on
  *   pages, page_offsets, pages_bytes, n_time_bins   as in tpc_timeframe_desc,
  *                 device memory, borrowed for the call; pages 16-byte aligned

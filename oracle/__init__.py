@@ -65,7 +65,7 @@ class _Params(ctypes.Structure):
                 ("min_chain", ctypes.c_int32), ("merge_cut", ctypes.c_int32),
                 ("gap_min", ctypes.c_int32), ("gap_max", ctypes.c_int32),
                 ("merge_passes", ctypes.c_int32), ("min_track", ctypes.c_int32),
-                ("fit_passes", ctypes.c_int32), ("bz", ctypes.c_double),
+                ("fit_passes", ctypes.c_int32), ("ns_min_dip", ctypes.c_int32), ("bz", ctypes.c_double),
                 ("sigma_y", ctypes.c_double), ("sigma_z", ctypes.c_double),
                 ("c0", ctypes.c_double * 5)]
 
@@ -86,6 +86,7 @@ class OracleParams:
     merge_passes: int = 8
     min_track: int = 10
     fit_passes: int = 3
+    ns_min_dip: int = 0        # 5x5 noise suppression (step 2b): 0 off
     bz: float = 0.5
     sigma_y: float = 0.02
     sigma_z: float = 0.03
@@ -94,7 +95,7 @@ class OracleParams:
     def _c(self) -> _Params:
         p = _Params()
         for k in ("q_peak_min", "sy_num", "sy_den", "sz_num", "sz_den", "ca_cut", "min_chain",
-                  "merge_cut", "gap_min", "gap_max", "merge_passes", "min_track", "fit_passes"):
+                  "merge_cut", "gap_min", "gap_max", "merge_passes", "min_track", "fit_passes", "ns_min_dip"):
             setattr(p, k, int(getattr(self, k)))
         p.bz, p.sigma_y, p.sigma_z = self.bz, self.sigma_y, self.sigma_z
         for i in range(5):
@@ -116,6 +117,7 @@ def _load():
         L.orc_find_clusters.argtypes = [_P, _P, _P, ctypes.c_int64]
         L.orc_find_clusters.restype = ctypes.c_int64
         L.orc_peaks_plane.argtypes = [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P]
+        L.orc_peaks_plane_ns.argtypes = [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P]
         L.orc_cluster_at.argtypes = [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                      ctypes.c_int, _P]
         L.orc_ca.argtypes = [_P, _P, _P, ctypes.c_int64, _P, _P, _P]
@@ -183,13 +185,17 @@ def decode_all(tf) -> np.ndarray:
     return out
 
 
-def peaks_plane(plane: np.ndarray, q_peak_min: int = 10) -> np.ndarray:
-    """Peak flags of one dense plane q[t, pad]."""
+def peaks_plane(plane: np.ndarray, q_peak_min: int = 10, ns_min_dip: int = 0) -> np.ndarray:
+    """Peak flags of one dense plane q[t, pad] (after step 2b's noise
+    suppression when ns_min_dip > 0)."""
     L = _load()
     plane = np.ascontiguousarray(plane, dtype=np.uint16)
     T, np_ = plane.shape
     fl = np.zeros((T, np_), dtype=np.uint8)
-    L.orc_peaks_plane(plane.ctypes.data, np_, T, q_peak_min, fl.ctypes.data)
+    if ns_min_dip:
+        L.orc_peaks_plane_ns(plane.ctypes.data, np_, T, q_peak_min, ns_min_dip, fl.ctypes.data)
+    else:
+        L.orc_peaks_plane(plane.ctypes.data, np_, T, q_peak_min, fl.ctypes.data)
     return fl.astype(bool)
 
 

@@ -43,6 +43,7 @@ typedef struct {
   int32_t merge_cut, gap_min, gap_max, merge_passes;
   int32_t min_track;
   int32_t fit_passes;
+  int32_t ns_min_dip;   /* 5x5 noise suppression: 0 off, else the minimum dip in ADC */
   double bz, sigma_y, sigma_z;
   double c0[5];
 } orc_params;
@@ -157,6 +158,28 @@ static int is_peak(const uint16_t* plane, int np, int T, int p, int t, int qmin)
 static int sgn(int v) { return (v > 0) - (v < 0); }
 static int imin(int a, int b) { return a < b ? a : b; }
 
+/* Step 2b (optional noise suppression): the peak at (p, t) is dropped when some
+ * other peak n of step 2, with a greater key, sits on the ring of its 5x5 window
+ * (max(|dp|, |dt|) = 2) and the pixel m between them -- the inner pixel of the
+ * cluster rule in n's direction -- lies less than min_dip ADC below the peak.
+ * The test reads step 2's peak set, so it does not depend on any order. */
+static int ns_suppressed(const uint16_t* plane, int np, int T, int p, int t, int qmin, int min_dip) {
+  if (min_dip <= 0) return 0;
+  int qc = q_at(plane, np, T, p, t);
+  int64_t lc = (int64_t)t * np + p;
+  for (int dt = -2; dt <= 2; dt++)
+    for (int dp = -2; dp <= 2; dp++) {
+      if (abs(dp) < 2 && abs(dt) < 2) continue;          /* ring only */
+      int pn = p + dp, tn = t + dt;
+      if (pn < 0 || pn >= np || tn < 0 || tn >= T) continue;
+      if (!is_peak(plane, np, T, pn, tn, qmin)) continue;
+      if (!key_greater(q_at(plane, np, T, pn, tn), (int64_t)tn * np + pn, qc, lc)) continue;
+      int qm = q_at(plane, np, T, p + sgn(dp) * imin(abs(dp), 1), t + sgn(dt) * imin(abs(dt), 1));
+      if (qc - qm < min_dip) return 1;
+    }
+  return 0;
+}
+
 static orc_cluster make_cluster(const uint16_t* plane, int np, int T, int s, int r, int p, int t,
                                 int qmin) {
   int64_t Q = 0, Sp = 0, St = 0, Spp = 0, Stt = 0;
@@ -215,7 +238,8 @@ int64_t orc_find_clusters(const orc_input* in, const orc_params* P, orc_cluster*
       if (orc_decode_row(in, s, r, plane) != 0) { free(plane); return ORC_E_CORRUPT; }
       for (int t = 0; t < T; t++)
         for (int p = 0; p < np; p++)
-          if (is_peak(plane, np, T, p, t, P->q_peak_min)) {
+          if (is_peak(plane, np, T, p, t, P->q_peak_min) &&
+              !ns_suppressed(plane, np, T, p, t, P->q_peak_min, P->ns_min_dip)) {
             if (out && n < cap) out[n] = make_cluster(plane, np, T, s, r, p, t, P->q_peak_min);
             n++;
           }
@@ -245,6 +269,14 @@ int orc_decode_all(const orc_input* in, uint16_t* out, int npmax) {
 void orc_peaks_plane(const uint16_t* plane, int np, int T, int qmin, uint8_t* flags) {
   for (int t = 0; t < T; t++)
     for (int p = 0; p < np; p++) flags[(size_t)t * np + p] = (uint8_t)is_peak(plane, np, T, p, t, qmin);
+}
+
+/* Surviving peaks of step 2b on one dense plane (tests). */
+void orc_peaks_plane_ns(const uint16_t* plane, int np, int T, int qmin, int min_dip, uint8_t* flags) {
+  for (int t = 0; t < T; t++)
+    for (int p = 0; p < np; p++)
+      flags[(size_t)t * np + p] =
+          (uint8_t)(is_peak(plane, np, T, p, t, qmin) && !ns_suppressed(plane, np, T, p, t, qmin, min_dip));
 }
 
 /* One cluster from a dense plane (tests). */

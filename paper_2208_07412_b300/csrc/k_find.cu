@@ -476,6 +476,30 @@ __device__ __forceinline__ uint32_t bits5(const uint32_t* row, int nw, int p) {
   return (uint32_t)(v >> (lo - 32 * w0)) & 31u;
 }
 
+// Step 2b, 5x5 noise suppression of the peak at (tt, p): dropped when a peak
+// of step 2 with a greater key lies on the ring of its 5x5 window and the
+// pixel between the two (the inner pixel of the cluster rule toward it) lies
+// less than min_dip ADC below the peak.  Reads the step-2 peak bitmap only.
+__device__ __forceinline__ bool ns_drop(const FindSmem& S, int ps_stride, int nw, int tt, int p, int min_dip) {
+  const uint16_t* c = S.plane + tt * ps_stride + kPad + p;
+  const int qc = c[0];
+#pragma unroll
+  for (int dt = -2; dt <= 2; dt++) {
+    uint32_t b = bits5(S.pk + (tt + dt) * nw, nw, p);
+    if (dt > -2 && dt < 2) b &= 0x11u;        // rows -1..1: the pads at distance 2 only
+    while (b) {
+      const int dp = __ffs(b) - 3;
+      b &= b - 1;
+      const int qn = c[dt * ps_stride + dp];
+      // greater key: more charge, or equal charge and a lower (t, p) index
+      if (qn < qc || (qn == qc && (dt > 0 || (dt == 0 && dp > 0)))) continue;
+      const int it = dt > 0 ? 1 : (dt < 0 ? -1 : 0), ip = dp > 0 ? 1 : (dp < 0 ? -1 : 0);
+      if (qc - (int)c[it * ps_stride + ip] < min_dip) return true;
+    }
+  }
+  return false;
+}
+
 // Cluster of the peak at (tt, p): 5x5 window with the inner/outer rule, the
 // neighbourhood held in registers.
 __device__ __forceinline__ void make_cluster(const FindSmem& S, int ps_stride, int nw, int np, int T, int s, int r,
@@ -567,8 +591,9 @@ __device__ __forceinline__ void prefetch_next_dense(const DevGeom& G, const DevW
 // kMode: 0 the fused finder (pages -> clusters); 1 and 2 the dense-plane
 // variant: 1 decodes each window's own page into a dense HBM plane of ADC
 // values, 2 reads a window and its 3-bin halos back from that plane and runs
-// the same peak / cluster steps.  All three give the same clusters.
-template <bool kScratch, int kThreads, int kMode>
+// the same peak / cluster steps.  All three give the same clusters.  kNs:
+// step 2b (5x5 noise suppression) compiled in, for ns_min_dip > 0.
+template <bool kScratch, int kThreads, int kMode, bool kNs>
 __global__ void __launch_bounds__(kThreads, 2)
 k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -936,6 +961,25 @@ k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
       }
       __syncthreads();
 
+      // ---- 4b. noise suppression (optional): the surviving own peaks go to
+      // the own rows of the occupancy bitmap, which afterwards only serves to
+      // clear the plane of an unlisted window (then cleared whole instead)
+      if (kNs) {
+        for (int i = tid; i < nown_words; i += blockDim.x) {
+          uint32_t word = S.pk[kHalo * nw + i], keep = word;
+          const int tt = kHalo + i / nw, p0 = (i % nw) * 32;
+          while (word) {
+            const int b = __ffs(word) - 1;
+            word &= word - 1;
+            if (ns_drop(S, ps_stride, nw, tt, p0 + b, P.ns_min_dip)) keep &= ~(1u << b);
+          }
+          S.occ[kHalo * nw + i] = keep;
+        }
+        __syncthreads();
+      }
+      // the own peaks that become clusters (rows 3..258)
+      const uint32_t* const sv = (kNs ? S.occ : S.pk) + kHalo * nw;
+
       if (kScratch && tid == 0 && nt < n_windows) {
         if (kMode == 2) prefetch_next_dense(G, W, nt);
         else prefetch_next_pages(W, noffs);
@@ -947,12 +991,12 @@ k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
       {
         const int w0 = tid * opt, w1 = min(w0 + opt, nown_words);
         int c = 0;
-        for (int i = w0; i < w1; i++) c += __popc(S.pk[kHalo * nw + i]);
+        for (int i = w0; i < w1; i++) c += __popc(sv[i]);
         uint32_t tot;
         const uint32_t pre = block_excl_scan32((uint32_t)c, reinterpret_cast<uint32_t*>(S.scan), &tot);
         int run = (int)pre;
         for (int i = w0; i < w1; i++) {
-          uint32_t word = S.pk[kHalo * nw + i];
+          uint32_t word = sv[i];
           S.ppre[i] = (uint16_t)run;
           while (word) {
             const int b = __ffs(word) - 1;
@@ -983,7 +1027,7 @@ k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
         } else {   // rows too wide for 16-bit plane indices
           const int wo = rank_search(S.ppre, nown_words + 1, k);
           tt = kHalo + wo / nw;
-          p = (wo % nw) * 32 + __fns(S.pk[kHalo * nw + wo], 0, k - (int)S.ppre[wo] + 1);
+          p = (wo % nw) * 32 + __fns(sv[wo], 0, k - (int)S.ppre[wo] + 1);
         }
         make_cluster(S, ps_stride, nw, np, T, s, r, f, tt, p, G.xrow[r], S.st_rec[k], S.st_xyz[k]);
       }
@@ -1020,7 +1064,7 @@ k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
           rec = S.st_rec[k];
         } else {
           const int wo = rank_search(S.ppre, nown_words + 1, k);
-          const int bit = __fns(S.pk[kHalo * nw + wo], 0, k - (int)S.ppre[wo] + 1);
+          const int bit = __fns(sv[wo], 0, k - (int)S.ppre[wo] + 1);
           make_cluster(S, ps_stride, nw, np, T, s, r, f, kHalo + wo / nw, (wo % nw) * 32 + bit, G.xrow[r], rec, xyz);
         }
         reinterpret_cast<uint4*>(dst)[idx] = rec;
@@ -1040,6 +1084,9 @@ k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
         const int L = S.list[i];
         if (L < nplane) S.plane[L] = 0;
       }
+    } else if (kNs) {   // occ's own rows hold the surviving peaks
+      for (int i = tid; i < nplane / 2; i += blockDim.x) reinterpret_cast<uint32_t*>(S.plane)[i] = 0u;
+      if (tid == 0 && (nplane & 1)) S.plane[nplane - 1] = 0;
     } else {
       for (int wi_ = tid; wi_ < kWinT * nw; wi_ += blockDim.x) {
         uint32_t word = S.occ[wi_];
@@ -1102,33 +1149,37 @@ cudaError_t launch_scan(uint64_t* v, const unsigned long long* n_ptr, unsigned l
 
 // Raise the finder's dynamic shared-memory limit on the current device (once
 // per context, outside any stream capture).
-template <int kMode>
+template <int kMode, bool kNs>
 static cudaError_t prepare_mode() {
-  cudaError_t e = cudaFuncSetAttribute(k_find_clusters<true, 256, kMode>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       227 * 1024);
+  cudaError_t e = cudaFuncSetAttribute(k_find_clusters<true, 256, kMode, kNs>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_find_clusters<true, 384, kMode>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    e = cudaFuncSetAttribute(k_find_clusters<true, 384, kMode, kNs>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             227 * 1024);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_find_clusters<true, 512, kMode>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    e = cudaFuncSetAttribute(k_find_clusters<true, 512, kMode, kNs>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             227 * 1024);
   return e;
 }
 
 cudaError_t prepare_find() {
-  cudaError_t e = prepare_mode<0>();
-  if (e == cudaSuccess) e = prepare_mode<1>();
-  if (e == cudaSuccess) e = prepare_mode<2>();
+  cudaError_t e = prepare_mode<0, false>();
+  if (e == cudaSuccess) e = prepare_mode<0, true>();
+  if (e == cudaSuccess) e = prepare_mode<1, false>();
+  if (e == cudaSuccess) e = prepare_mode<2, false>();
+  if (e == cudaSuccess) e = prepare_mode<2, true>();
   return e;
 }
 
-template <int kMode>
+template <int kMode, bool kNs>
 static void launch_find_mode(const DevGeom& G, const DevParams& P, const DevWork& W, unsigned int n_windows,
                              unsigned grid, int threads, size_t sm, cudaStream_t st) {
   if (threads == 256)
-    k_find_clusters<true, 256, kMode><<<grid, 256, sm, st>>>(G, P, W, n_windows);
+    k_find_clusters<true, 256, kMode, kNs><<<grid, 256, sm, st>>>(G, P, W, n_windows);
   else if (threads == 512)
-    k_find_clusters<true, 512, kMode><<<grid, 512, sm, st>>>(G, P, W, n_windows);
+    k_find_clusters<true, 512, kMode, kNs><<<grid, 512, sm, st>>>(G, P, W, n_windows);
   else
-    k_find_clusters<true, 384, kMode><<<grid, 384, sm, st>>>(G, P, W, n_windows);
+    k_find_clusters<true, 384, kMode, kNs><<<grid, 384, sm, st>>>(G, P, W, n_windows);
 }
 
 cudaError_t launch_find(const DevGeom& G, const DevParams& P, const DevWork& W, unsigned int n_windows,
@@ -1138,13 +1189,18 @@ cudaError_t launch_find(const DevGeom& G, const DevParams& P, const DevWork& W, 
   // persistent CTAs: find_ctas_per_sm per SM (at most 2 fit the shared memory)
   unsigned int grid = (unsigned int)min((long long)n_windows, (long long)n_sm * L.find_ctas_per_sm);
   if (grid == 0) grid = 1;
+  // step 2b (noise suppression) compiled in only where it is switched on
+  const bool ns = P.ns_min_dip > 0;
   if (W.dense) {
     // dense-plane variant: decode every window into the plane, then find
-    launch_find_mode<1>(G, P, W, n_windows, grid, L.find_threads, sm, st);
-    launch_find_mode<2>(G, P, W, n_windows, grid, L.find_threads, sm, st);
+    launch_find_mode<1, false>(G, P, W, n_windows, grid, L.find_threads, sm, st);
+    if (ns) launch_find_mode<2, true>(G, P, W, n_windows, grid, L.find_threads, sm, st);
+    else launch_find_mode<2, false>(G, P, W, n_windows, grid, L.find_threads, sm, st);
     *launches += 1;
+  } else if (ns) {
+    launch_find_mode<0, true>(G, P, W, n_windows, grid, L.find_threads, sm, st);
   } else {
-    launch_find_mode<0>(G, P, W, n_windows, grid, L.find_threads, sm, st);
+    launch_find_mode<0, false>(G, P, W, n_windows, grid, L.find_threads, sm, st);
   }
   cudaError_t e = launch_scan(reinterpret_cast<uint64_t*>(W.win_cnt), W.ctr + CTR_NWIN, n_windows, win_scan_state,
                               W.tickets + TK_SCAN_W, W.ctr + CTR_NCL, W.err, n_sm, st);
@@ -1190,6 +1246,8 @@ extern "C" tpc_status tpc_find_clusters_noalloc(const tpc_geometry* geom, const 
   if (params && params->version != TPC_PARAMS_VERSION)
     return fail(TPC_E_INVAL, "tpc_find_clusters_noalloc: params version mismatch");
   if (q_peak_min < 1 || q_peak_min > 1023) return fail(TPC_E_INVAL, "tpc_find_clusters_noalloc: bad q_peak_min");
+  const int ns_min_dip = params ? params->ns_min_dip : 0;
+  if (ns_min_dip < 0 || ns_min_dip > 1023) return fail(TPC_E_INVAL, "tpc_find_clusters_noalloc: bad ns_min_dip");
   const unsigned long long nfrag = (n_time_bins + kFrag - 1) / kFrag;
   const unsigned long long nwin = (unsigned long long)geom->n_sectors * geom->n_rows * nfrag;
   if (nwin > kNoAllocMaxWindows)
@@ -1213,8 +1271,10 @@ extern "C" tpc_status tpc_find_clusters_noalloc(const tpc_geometry* geom, const 
       void* ptr = nullptr;
       if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr)
         return fail(TPC_E_CUDA, "tpc_find_clusters_noalloc: cudaGetSymbolAddress failed");
-      if (cudaFuncSetAttribute(k_find_clusters<false, kFindThreads, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) !=
-          cudaSuccess)
+      if (cudaFuncSetAttribute(k_find_clusters<false, kFindThreads, 0, false>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) != cudaSuccess ||
+          cudaFuncSetAttribute(k_find_clusters<false, kFindThreads, 0, true>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) != cudaSuccess)
         return fail(TPC_E_CUDA, "tpc_find_clusters_noalloc: cudaFuncSetAttribute failed");
       g_noalloc_addr[device] = static_cast<unsigned long long*>(ptr);
       g_noalloc_ready[device] = true;
@@ -1234,6 +1294,7 @@ extern "C" tpc_status tpc_find_clusters_noalloc(const tpc_geometry* geom, const 
   for (int r = 0; r < geom->n_rows; r++) { G.npads[r] = geom->npads[r]; G.xrow[r] = 64 * geom->row_x[r]; }
   DevParams P{};
   P.q_peak_min = q_peak_min;
+  P.ns_min_dip = ns_min_dip;
   DevWork W{};
   W.pages = static_cast<const uint8_t*>(pages);
   W.page_offsets = page_offsets;
@@ -1252,7 +1313,10 @@ extern "C" tpc_status tpc_find_clusters_noalloc(const tpc_geometry* geom, const 
   int n_sm = 148;
   cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, device);
   unsigned grid = (unsigned)std::min<unsigned long long>(nwin, (unsigned long long)n_sm * 2);
-  k_find_clusters<false, kFindThreads, 0><<<grid ? grid : 1, kFindThreads, smem, st>>>(G, P, W, (unsigned)nwin);
+  if (ns_min_dip > 0)
+    k_find_clusters<false, kFindThreads, 0, true><<<grid ? grid : 1, kFindThreads, smem, st>>>(G, P, W, (unsigned)nwin);
+  else
+    k_find_clusters<false, kFindThreads, 0, false><<<grid ? grid : 1, kFindThreads, smem, st>>>(G, P, W, (unsigned)nwin);
   if (cudaGetLastError() != cudaSuccess) return fail(TPC_E_CUDA, "tpc_find_clusters_noalloc: launch failed");
   unsigned long long ctrl[CTR_COUNT + 1];
   if (cudaMemcpyAsync(ctrl, W.ctr, sizeof ctrl, cudaMemcpyDeviceToHost, st) != cudaSuccess ||

@@ -177,6 +177,7 @@ extern "C" void tpc_destroy_geometry(tpc_geometry* g) { delete g; }
 static tpc_status check_params(const tpc_params& p, const tpc_geometry& g) {
   if (p.version != TPC_PARAMS_VERSION) return fail(TPC_E_INVAL, "params: version mismatch");
   if (p.q_peak_min < 1 || p.q_peak_min > 1023) return fail(TPC_E_INVAL, "params: q_peak_min out of range");
+  if (p.ns_min_dip < 0 || p.ns_min_dip > 1023) return fail(TPC_E_INVAL, "params: ns_min_dip out of range");
   if (p.ca_slope_y_num < 0 || p.ca_slope_y_den < 1 || p.ca_slope_z_num < 0 || p.ca_slope_z_den < 1 ||
       p.ca_slope_y_num > 1000 || p.ca_slope_z_num > 1000 || p.ca_slope_y_den > 1000 || p.ca_slope_z_den > 1000)
     return fail(TPC_E_INVAL, "params: CA slopes out of range");
@@ -364,6 +365,7 @@ extern "C" tpc_status tpc_create_context(const tpc_geometry* geom, const tpc_par
   for (int r = 0; r < geom->n_rows; r++) { G.npads[r] = geom->npads[r]; G.xrow[r] = 64 * geom->row_x[r]; }
   DevParams& P = ctx->P;
   P.q_peak_min = p.q_peak_min;
+  P.ns_min_dip = p.ns_min_dip;
   P.sy_num = p.ca_slope_y_num; P.sy_den = p.ca_slope_y_den;
   P.sz_num = p.ca_slope_z_num; P.sz_den = p.ca_slope_z_den;
   P.ca_cut = p.ca_cut; P.min_chain = p.min_chain;

@@ -58,7 +58,7 @@ class tpc_params(ctypes.Structure):
                 ("merge_cut", ctypes.c_int32), ("merge_gap_min", ctypes.c_int32),
                 ("merge_gap_max", ctypes.c_int32), ("merge_max_passes", ctypes.c_int32),
                 ("min_track", ctypes.c_int32), ("fit_passes", ctypes.c_int32),
-                ("reserved0", ctypes.c_int32), ("bz", ctypes.c_double),
+                ("ns_min_dip", ctypes.c_int32), ("bz", ctypes.c_double),
                 ("sigma_y", ctypes.c_double), ("sigma_z", ctypes.c_double),
                 ("c0", ctypes.c_double * 5)]
 

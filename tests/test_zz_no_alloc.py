@@ -8,6 +8,7 @@ already run every other test."""
 import numpy as np
 import pytest
 
+import oracle
 import tpcgen
 
 pytestmark = pytest.mark.gpu
@@ -64,3 +65,23 @@ def test_noalloc_rejects_too_many_windows(lib):
         assert ei.value.code == -1
     finally:
         lib.tpc_destroy_geometry(geom)
+
+
+def test_noalloc_noise_suppression_matches_oracle(lib):
+    """Step 2b through the allocation-free entry point."""
+    import torch
+    tf = tpcgen.generate(tpcgen.single_sector(9, n_tracks=400))
+    want = oracle.find_clusters(tf, oracle.OracleParams(ns_min_dip=10))
+    p = lib.tpc_params_default()
+    p.ns_min_dip = 10
+    geom = lib.tpc_create_geometry(tf.npads, tf.row_x, tf.n_sectors)
+    try:
+        pages = torch.from_numpy(tf.pages).cuda()
+        offs = torch.from_numpy(tf.page_offsets.view(np.int64)).cuda()
+        out = torch.zeros(16 * (len(want) + 64), dtype=torch.uint8, device="cuda")
+        n = lib.tpc_find_clusters_noalloc(geom, pages, offs, tf.n_time_bins, out, params=p)
+        torch.cuda.synchronize()
+    finally:
+        lib.tpc_destroy_geometry(geom)
+    assert n == len(want)
+    assert out[:16 * n].cpu().numpy().tobytes() == want.tobytes()
