@@ -134,24 +134,29 @@ def barrier(world):
         dist.barrier()
 
 
-def max_over_ranks(world, v: float) -> float:
-    if world == 1:
-        return v
+def _reduce(v: float, op: str) -> float:
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
     return float(t.item())
+
+
+def max_over_ranks(world, v: float) -> float:
+    return v if world == 1 else _reduce(v, "max")
 
 
 def sum_over_ranks(world, v: float) -> float:
-    if world == 1:
-        return v
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return float(t.item())
+    return v if world == 1 else _reduce(v, "sum")
+
+
+def job_totals(world, n_cl: int, n_tr: int, steps: int, dev_s: float):
+    """Whole-job totals of the replicas: every rank reconstructs its own
+    timeframes, so the job's clusters and tracks are the sum over ranks and its
+    time the slowest rank's.  Returns (clusters, tracks, seconds)."""
+    return (sum_over_ranks(world, n_cl * steps), sum_over_ranks(world, n_tr * steps),
+            max_over_ranks(world, dev_s))
 
 
 def ref_sample_sectors(tf, sample_bytes: float = REF_SAMPLE_BYTES) -> int:
@@ -175,6 +180,51 @@ def cpu_baseline(tf, steps=1, sample_bytes: float = REF_SAMPLE_BYTES):
                       f"{ncl} clusters, {ntr} tracks per step"}
 
 
+def _oracle_sector_job(sub):
+    """Worker of the all-cores oracle run: one single-sector timeframe."""
+    import oracle
+    r = oracle.reconstruct(sub)
+    return len(r.clusters), len(r.track_first)
+
+
+def _oracle_warm(_):
+    import oracle
+    oracle.build()
+    return os.getpid()
+
+
+class OraclePool:
+    """A spawn pool of one oracle process per host core (spawned, never forked:
+    the parent may already hold a CUDA context).  Sectors are independent
+    through step 8, so the all-cores run gives each process whole sectors."""
+
+    def __init__(self, procs: int | None = None):
+        import multiprocessing as mp
+        self.procs = procs or os.cpu_count() or 1
+        self.pool = mp.get_context("spawn").Pool(self.procs)
+        self.pool.map(_oracle_warm, range(self.procs))   # imports and loads outside the timed region
+
+    def run(self, tf, sample_bytes: float = REF_SAMPLE_BYTES, steps: int = 1):
+        """Time `steps` passes over the first max(procs, sample) sectors, one
+        task per sector, rounded down to a multiple of the process count."""
+        n1 = ref_sample_sectors(tf, sample_bytes)
+        n = min(tf.n_sectors, max(self.procs, (n1 // self.procs) * self.procs))
+        subs = [tpcgen.sector_slice(tf, s) for s in range(n)]
+        times, ncl, ntr = [], 0, 0
+        for _ in range(steps):
+            t0 = time.perf_counter()
+            res = self.pool.map(_oracle_sector_job, subs, chunksize=1)
+            times.append(time.perf_counter() - t0)
+            ncl, ntr = sum(r[0] for r in res), sum(r[1] for r in res)
+        return {"times": times, "clusters": ncl, "tracks": ntr, "cores": min(self.procs, n),
+                "sample": f"sectors 0-{n - 1} of the same timeframe ({n}/{tf.n_sectors}), one oracle process "
+                          f"per sector on a spawn pool of {self.procs}, {ncl} clusters, {ntr} tracks per step"}
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return
@@ -187,9 +237,15 @@ def run_reference(args, world, rank):
     # each step a bounded sample, smaller when many steps are asked for, so the
     # whole run stays around a minute of CPU time
     per_step = REF_SAMPLE_BYTES * min(1.0, 20.0 / max(args.steps + args.warmup, 1))
-    for _ in range(args.warmup):
-        cpu_baseline(tf, 1, per_step)
-    cb = cpu_baseline(tf, args.steps, per_step)
+    # the oracle on all host cores, one process per sector (the single-core
+    # figure is kept beside it)
+    pool = OraclePool()
+    try:
+        pool.run(tf, per_step, args.warmup)
+        cb = pool.run(tf, per_step, args.steps)
+    finally:
+        pool.close()
+    one = cpu_baseline(tf, 1, per_step)
     t = sum(cb["times"])
     v = cb["clusters"] * args.steps / t
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "clusters/s", "n_gpus": args.gpus,
@@ -197,7 +253,10 @@ def run_reference(args, world, rank):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i64+f64",
             "data": "synthetic", "config": {"workload": desc, "seed": args.seed},
             "tracks_per_s": cb["tracks"] * args.steps / t,
-            "cpu_baseline": {"value": v, "unit": "clusters/s", "cores": 1, "kind": "oracle", "sample": cb["sample"]},
+            "cpu_baseline": {"value": v, "unit": "clusters/s", "cores": cb["cores"], "kind": "oracle",
+                             "sample": cb["sample"]},
+            "single_core": {"value": one["clusters"] / one["times"][0], "unit": "clusters/s", "cores": 1,
+                            "sample": one["sample"]},
             "e2e": {"value": v, "unit": "clusters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -574,10 +633,7 @@ def run_ours(args, world, rank, local):
     step_ms = [a.elapsed_time(b) for a, b, _, _ in recs]
     ctr = recs[-1][2]
     n_cl, n_tr = ctr["clusters"], ctr["tracks"]
-    dev_s = sum(step_ms) / 1e3
-    dev_s_max = max_over_ranks(world, dev_s)
-    cl_all = sum_over_ranks(world, n_cl * args.steps)
-    tr_all = sum_over_ranks(world, n_tr * args.steps)
+    cl_all, tr_all, dev_s_max = job_totals(world, n_cl, n_tr, args.steps, sum(step_ms) / 1e3)
     stages = {k: statistics.mean(r[3][k] for r in recs) for k in tpc.STAGES}
     launches = sum(r[2]["kernel_launches"] for r in recs)
 
@@ -700,6 +756,13 @@ def run_ours(args, world, rank, local):
             cb = cpu_baseline(tf, 1)
             line["cpu_baseline"] = {"value": cb["clusters"] / cb["times"][0], "unit": "clusters/s", "cores": 1,
                                     "kind": "oracle", "sample": cb["sample"]}
+            pool = OraclePool()
+            try:
+                pb = pool.run(tf, REF_SAMPLE_BYTES, 1)
+            finally:
+                pool.close()
+            line["cpu_baseline_all_cores"] = {"value": pb["clusters"] / pb["times"][0], "unit": "clusters/s",
+                                              "cores": pb["cores"], "kind": "oracle", "sample": pb["sample"]}
         print(json.dumps(line), flush=True)
     R.close()
 

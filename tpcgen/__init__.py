@@ -291,6 +291,25 @@ def continuous_tf(seed: int = 1, n_time_bins: int = 55000, rate_per_bin: float =
     return GenConfig(**d)
 
 
+def sector_slice(tf: Timeframe, sector: int) -> Timeframe:
+    """One sector of a timeframe as a single-sector timeframe of its own: it
+    becomes sector 0 (the sector byte at offset 10 of every page header is
+    rewritten) and the offsets are rebased to its first page, which keeps their
+    16-byte alignment."""
+    import copy
+    nw = tf.n_rows * tf.n_fragments
+    a = int(tf.page_offsets[sector * nw])
+    b = int(tf.page_offsets[(sector + 1) * nw]) if (sector + 1) * nw < len(tf.page_offsets) else len(tf.pages)
+    s = copy.copy(tf)
+    s.page_offsets = tf.page_offsets[sector * nw:(sector + 1) * nw] - np.uint64(a)
+    s.pages = tf.pages[a:b].copy()
+    s.pages[s.page_offsets.astype(np.int64) + 10] = 0
+    s.n_sectors = 1
+    s.digit_labels = None           # no generator truth: the slice is input only
+    s.tracks, s.hits = tf.tracks[:0], tf.hits[:0]
+    return s
+
+
 def sector_prefix(tf: Timeframe, n_sectors: int) -> Timeframe:
     """The first n_sectors sectors of a timeframe as a timeframe of their own.
     Pages are laid out window by window with the sector outermost, so these
