@@ -49,7 +49,7 @@ REF_SAMPLE_BYTES = 20 << 20
 # DRAM bytes (read + write) of one k_find_clusters launch, from an ncu capture of
 # the current kernel on the workload (seed 1); None where no capture exists.
 # Must be reset to None whenever the finder kernel changes.
-FINDER_DRAM_BYTES = {"full_tpc": 70_607_872 + 6_649_088}
+FINDER_DRAM_BYTES = {"full_tpc": 70_606_592 + 6_217_472}
 L2_FLUSH_BYTES = 256 << 20
 
 
