@@ -519,7 +519,7 @@ def finder_variants(tpc, torch, tf, pages_d, offs_d, tuning, flush, fused_ms, re
     n_frag = (tf.n_time_bins + 255) // 256
     alloc = tf.n_sectors * len(tf.npads) * n_frag * 256 * stride * 2
     free_now, _ = torch.cuda.mem_get_info()
-    if alloc + 40 * tf.pages.nbytes > 0.8 * free_now:
+    if alloc + 8 * tf.pages.nbytes > 0.8 * free_now:   # the plane + a slot (~5x the pages)
         return {"skipped": f"the dense plane needs {alloc / 1e9:.1f} GB"}
     Rd = tpc.Reconstructor.for_timeframe(tf, device=torch.cuda.current_device(),
                                          flags=tpc.TPC_CTX_STAGE_TIMING | tpc.TPC_CTX_DENSE_FINDER,
@@ -740,9 +740,10 @@ def run_ours(args, world, rank, local):
             "clocks": clk.summary(),
             "gpu_launches": int(launches),
         }
-        if world == 1 and args.workload == "full_tpc":
+        if world == 1 and args.workload in ("full_tpc", "continuous_50khz"):
             line["cross_sector"] = cross_sector_timing(tpc, torch, R, pages_d, offs_d, tf)
             line["compression"] = compression_stats(tpc, R, pages_d, offs_d, tf)
+        if world == 1 and args.workload == "full_tpc":   # one collision: its vertex time
             line["calibration"] = calibration_stats(tpc, R, pages_d, offs_d, tf)
         if world == 1 and not (args.no_variants or args.dense_finder) and args.workload in ("full_tpc", "continuous_50khz"):
             line["finder_variants"] = finder_variants(tpc, torch, tf, pages_d, offs_d, tuning, flush,

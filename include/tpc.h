@@ -342,6 +342,9 @@ typedef struct {
   double chi2_cut;   /* 100  matching chi2 (5 parameters) for a link */
   double edge_cm;    /* 6    a piece's end counts as at a sector edge within this distance
                               of the pad plane's edge (rounded to u = 7.8125 um) */
+  double dz_cm;      /* 250  |zeta(B innermost) - zeta(A outermost)| bound of a candidate pair
+                              (the drift length: the pieces of one track lie within it),
+                              rounded to u; 0 < dz_cm <= 1e4 */
 } tpc_xs_params;
 
 /* Step 9, optional: join the pieces of tracks that cross a sector border, on
@@ -355,7 +358,8 @@ typedef struct {
  *   - candidates: A exiting through +y (-y) of sector s, B entering through -y
  *     (+y) of the neighbouring sector s+1 (s-1) of the same side (sectors
  *     0..17 and 18..35, cyclic), A's outermost row below B's innermost row,
- *     neither fit flagged;
+ *     |Z(B's innermost cluster) - Z(A's outermost cluster)| <= dz (u), neither
+ *     fit flagged;
  *   - B's state is rotated into A's frame and transported to A's reference x:
  *     chi2 = d^T (C_A + J C_B J^T)^-1 d over the 5 parameters; with the
  *     rotation by delta = alpha_B - alpha_A of a state at x: (x, y) ->
@@ -372,9 +376,10 @@ typedef struct {
  *   Unlinked tracks keep their step-8 records.
  * xp: NULL for the defaults.  *n_tracks (may be NULL): tracks after the merge.
  * Runs on the ticket's stream and waits for it; results until tpc_release.
- * The candidate search compares every exiting piece with every track of the
- * neighbouring sector: cheap at full-TPC occupancy (~800 tracks per sector),
- * quadratic on much larger timeframes.
+ * The candidate search bins the entering pieces of every sector by zeta (bins
+ * at least dz wide), so an exiting piece is compared with the entering pieces
+ * of at most three bins of the neighbouring sector: linear in the timeframe's
+ * length for continuous timeframes.
  * Errors: TPC_E_NOTREADY (ticket not done), TPC_E_NOTFOUND, TPC_E_CUDA, TPC_E_NOMEM. */
 tpc_status tpc_merge_sectors(tpc_context* ctx, uint64_t ticket, const tpc_xs_params* xp, uint64_t* n_tracks);
 

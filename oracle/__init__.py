@@ -318,7 +318,7 @@ def update(state, C, my, mz, params: OracleParams | None = None):
 
 
 class _XsParams(ctypes.Structure):
-    _fields_ = [("chi2_cut", ctypes.c_double), ("edge_cm", ctypes.c_double)]
+    _fields_ = [("chi2_cut", ctypes.c_double), ("edge_cm", ctypes.c_double), ("dz_cm", ctypes.c_double)]
 
 
 @dataclass
@@ -326,9 +326,10 @@ class XsParams:
     """Cross-sector merge constants."""
     chi2_cut: float = 100.0
     edge_cm: float = 6.0
+    dz_cm: float = 250.0       # the drift length: pieces of one track lie within it in zeta
 
     def _c(self) -> _XsParams:
-        return _XsParams(float(self.chi2_cut), float(self.edge_cm))
+        return _XsParams(float(self.chi2_cut), float(self.edge_cm), float(self.dz_cm))
 
 
 def sector_alpha(s: int) -> float:

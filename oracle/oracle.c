@@ -712,6 +712,7 @@ int orc_fit_all(const orc_input* in, const orc_params* P, const orc_cluster* cl,
 typedef struct {
   double chi2_cut;   /* 100 */
   double edge_cm;    /* 6 */
+  double dz_cm;      /* 250: |zeta(B innermost) - zeta(A outermost)| bound of a candidate pair */
 } orc_xs_params;
 
 static double sector_alpha(int s) { return ((double)(s % 18) + 0.5) * (20.0 * 3.14159265358979323846 / 180.0); }
@@ -912,6 +913,9 @@ int64_t orc_merge_sectors(const orc_input* in, const orc_params* P, const orc_xs
   int* entry_side = (int*)malloc(sizeof(int) * (nt + 1));
   int* row_in = (int*)malloc(sizeof(int) * (nt + 1));
   int* row_out = (int*)malloc(sizeof(int) * (nt + 1));
+  int64_t* z_in = (int64_t*)malloc(sizeof(int64_t) * (nt + 1));
+  int64_t* z_out = (int64_t*)malloc(sizeof(int64_t) * (nt + 1));
+  const int64_t Dz = (int64_t)floor(XP->dz_cm / u + 0.5);
   for (int64_t t = 0; t < nt; t++) {
     const orc_cluster* ci = &cl[lst[cnt[t]]];
     const orc_cluster* co = &cl[lst[cnt[t + 1] - 1]];
@@ -922,8 +926,10 @@ int64_t orc_merge_sectors(const orc_input* in, const orc_params* P, const orc_xs
     const int64_t E = (int64_t)floor(XP->edge_cm / u + 0.5);
     orc_coords(in, ci, &X, &Y, &Z);
     entry_side[t] = side_of(Y, in->npads[ci->row], E);
+    z_in[t] = Z;
     orc_coords(in, co, &X, &Y, &Z);
     exit_side[t] = side_of(Y, in->npads[co->row], E);
+    z_out[t] = Z;
   }
   /* best candidates (chi2, index) both ways */
   double* bb = (double*)malloc(sizeof(double) * (nt + 1));
@@ -936,6 +942,7 @@ int64_t orc_merge_sectors(const orc_input* in, const orc_params* P, const orc_xs
     int sb = neighbour_sector(sec[a], exit_side[a]);
     for (int64_t b = 0; b < nt; b++) {
       if (sec[b] != sb || entry_side[b] != -exit_side[a] || row_out[a] >= row_in[b] || fits[b].flags) continue;
+      if (llabs(z_in[b] - z_out[a]) > Dz) continue;
       double c2 = orc_xs_chi2(P, &fits[a], sector_alpha(sec[a]), &fits[b], sector_alpha(sec[b]));
       if (c2 < 0.0 || c2 > XP->chi2_cut) continue;
       if (ib[a] < 0 || c2 < bb[a] || (c2 == bb[a] && b < ib[a])) { bb[a] = c2; ib[a] = (int32_t)b; }
@@ -975,7 +982,7 @@ int64_t orc_merge_sectors(const orc_input* in, const orc_params* P, const orc_xs
     ng++;
   }
   free(cnt); free(lst); free(fill); free(sec); free(exit_side); free(entry_side); free(row_in);
-  free(row_out); free(bb); free(ba); free(ib); free(ia); free(prev);
+  free(row_out); free(z_in); free(z_out); free(bb); free(ba); free(ib); free(ia); free(prev);
   return ng;
 }
 

@@ -44,6 +44,13 @@ __device__ __forceinline__ float sector_alpha(int phys) {
   return ((float)(phys % 18) + 0.5f) * (20.f * 3.14159265358979f / 180.f);
 }
 
+// Zeta bin of Z (u): bins of bin_w from Z = -2560 (the smallest Z a cluster can
+// have), clamped to the bins of a virtual sector.
+__device__ __forceinline__ int zbin(const XsWork& X, long long z) {
+  const long long b = (z + 2560) / X.bin_w;
+  return (int)(b < 0 ? 0 : (b >= X.n_zb ? X.n_zb - 1 : b));
+}
+
 __global__ void k_xs_ends(DevGeom G, DevWork W, XsWork X) {
   const unsigned long long nt = n_tracks_x(W);
   for (unsigned long long t = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; t < nt;
@@ -56,6 +63,13 @@ __global__ void k_xs_ends(DevGeom G, DevWork W, XsWork X) {
     X.side[t] = (uint8_t)(side_code(po.y, G.npads[ro], X.edge_u) | (side_code(pi.y, G.npads[ri], X.edge_u) << 2));
     X.row_in[t] = ri;
     X.row_out[t] = ro;
+    X.z_in[t] = pi.z;
+    X.z_out[t] = po.z;
+    if (((X.side[t] >> 2) & 3) && !W.tracks[t].flags) {   // an entering piece: into its zeta bin
+      const int sec = (int)(__ldg(reinterpret_cast<const uint4*>(W.clusters) + pi.w).w >> 24);
+      const int vs = vsector_of(G, W, (unsigned)W.trk_first[t], sec);
+      atomicAdd(reinterpret_cast<unsigned long long*>(X.bin_off) + (size_t)vs * X.n_zb + zbin(X, pi.z), 1ull);
+    }
     X.best_b[t] = ~0ull;
     X.best_a[t] = ~0ull;
     X.link[t] = -1;
@@ -184,19 +198,22 @@ __device__ float xs_chi2(float kfac, const tpc_track& A, const tpc_track& B) {
   return chi2_spd(CA, d);
 }
 
-// First track whose lowest cluster is at or past c (tracks ascend by it).
-__device__ __forceinline__ unsigned lower_bound_first(const int32_t* first, unsigned n, unsigned c) {
-  unsigned lo = 0, hi = n;
-  while (lo < hi) {
-    const unsigned mid = (lo + hi) >> 1;
-    if ((unsigned)__ldg(first + mid) < c) lo = mid + 1; else hi = mid;
+// The entering unflagged pieces into their bins (bin_off holds the exclusive
+// offsets); the order within a bin is free: the matching keys carry indices.
+__global__ void k_xs_fill(DevGeom G, DevWork W, XsWork X) {
+  const unsigned long long nt = n_tracks_x(W);
+  for (unsigned long long t = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; t < nt;
+       t += (unsigned long long)gridDim.x * blockDim.x) {
+    if (!((X.side[t] >> 2) & 3) || W.tracks[t].flags) continue;
+    const int c = W.trk_first[t];
+    const int sec = (int)(__ldg(reinterpret_cast<const uint4*>(W.clusters) + c).w >> 24);
+    const size_t bin = (size_t)vsector_of(G, W, (unsigned)c, sec) * X.n_zb + zbin(X, X.z_in[t]);
+    X.ent[X.bin_off[bin] + atomicAdd(&X.bin_cur[bin], 1u)] = (uint32_t)t;
   }
-  return lo;
 }
 
 __global__ void k_xs_pairs(DevGeom G, DevParams P, DevWork W, XsWork X) {
   const unsigned long long nt = n_tracks_x(W);
-  const int R = G.n_rows;
   for (unsigned long long a = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; a < nt;
        a += (unsigned long long)gridDim.x * blockDim.x) {
     const int ex = X.side[a] & 3;
@@ -210,15 +227,20 @@ __global__ void k_xs_pairs(DevGeom G, DevParams P, DevWork W, XsWork X) {
     const int nphys = side_base + ((phys - side_base) + (ex == 1 ? 1 : 17)) % 18;
     if (nphys >= G.n_phys) continue;
     const int vb = base + nphys;
-    const unsigned b0 = lower_bound_first(W.trk_first, (unsigned)nt, W.row_start[vb * R]);
-    const unsigned b1 = lower_bound_first(W.trk_first, (unsigned)nt, W.row_start[vb * R + R]);
     const int want_entry = ex == 1 ? 2 : 1;
     const int ro = X.row_out[a];
+    const long long za = X.z_out[a];
     unsigned long long best = ~0ull;
-    for (unsigned b = b0; b < b1; b++) {
+    // the entering unflagged pieces of the neighbouring sector in the zeta
+    // bins that can hold |Z_B - Z_A| <= dz (bins are at least dz wide: <= 3)
+    const size_t bb = (size_t)vb * X.n_zb;
+    const int zl = zbin(X, za - X.dz_u), zh = zbin(X, za + X.dz_u);
+    for (unsigned long long e = X.bin_off[bb + zl]; e < X.bin_off[bb + zh + 1]; e++) {
+      const unsigned b = X.ent[e];
       if (((X.side[b] >> 2) & 3) != want_entry || X.row_in[b] <= ro) continue;
+      const long long dz = (long long)X.z_in[b] - za;
+      if (dz > X.dz_u || dz < -(long long)X.dz_u) continue;
       const tpc_track B = W.tracks[b];
-      if (B.flags) continue;
       const float c2 = xs_chi2(P.kfac, A, B);
       if (!(c2 >= 0.f) || c2 > X.chi2_cut) continue;
       const unsigned long long cb = (unsigned long long)__float_as_uint(c2) << 32;
@@ -481,6 +503,11 @@ cudaError_t launch_xsec(const DevGeom& G, const DevParams& P, const DevWork& W, 
                         cudaStream_t st) {
   const unsigned g = grid_x(W.cap_ch, n_sm, 8);
   k_xs_ends<<<g, 256, 0, st>>>(G, W, X);
+  // bins: counts -> exclusive offsets (n_bins + 1 entries, the last the total)
+  cudaError_t e0 = launch_scan(X.bin_off, X.ctl + 3, (unsigned long long)G.n_sectors * X.n_zb + 1, X.bin_state,
+                               reinterpret_cast<unsigned int*>(X.ctl + 4), X.ctl + 5, W.err, n_sm, st);
+  if (e0 != cudaSuccess) return e0;
+  k_xs_fill<<<g, 256, 0, st>>>(G, W, X);
   k_xs_pairs<<<grid_x(W.cap_ch, n_sm, 16), 64, 0, st>>>(G, P, W, X);
   k_xs_link<<<g, 256, 0, st>>>(W, X);
   k_xs_roots<<<g, 256, 0, st>>>(W, X);

@@ -979,7 +979,9 @@ extern "C" tpc_status tpc_merge_sectors(tpc_context* ctx, uint64_t ticket, const
                                         uint64_t* n_tracks) {
   if (!ctx) return fail(TPC_E_INVAL, "tpc_merge_sectors: null argument");
   const double chi2_cut = xp ? xp->chi2_cut : 100.0, edge_cm = xp ? xp->edge_cm : 6.0;
-  if (!(chi2_cut >= 0.0) || !(edge_cm >= 0.0) || edge_cm > 100.0) return fail(TPC_E_INVAL, "tpc_merge_sectors: bad parameters");
+  const double dz_cm = xp ? xp->dz_cm : 250.0;
+  if (!(chi2_cut >= 0.0) || !(edge_cm >= 0.0) || edge_cm > 100.0 || !(dz_cm > 0.0) || dz_cm > 1e4)
+    return fail(TPC_E_INVAL, "tpc_merge_sectors: bad parameters");
   std::lock_guard<std::mutex> lk(ctx->mu);
   Slot* s;
   tpc_status st = done_slot(ctx, ticket, &s);
@@ -987,9 +989,20 @@ extern "C" tpc_status tpc_merge_sectors(tpc_context* ctx, uint64_t ticket, const
   CUDA_TRY(cudaSetDevice(ctx->device));
   const uint64_t C = s->cap_ch, Ncl = s->cap_cl;
   const size_t tiles = scan_tiles(C);
+  // zeta bins of the candidate search: Z = 5 (32768 f + time_fp - 512) spans
+  // [-2560, zmax]; bins at least dz wide, at most ~4M bins over all virtual sectors
+  const int n_vs = ctx->geom.n_sectors * (int)s->n_events;
+  const long long n_frag = (long long)((s->n_time_bins + kFrag - 1) / kFrag);
+  const long long zrange = 5 * (32768 * (n_frag - 1) + 65535 - 512) + 2560 + 1;
+  const long long dz_u = (long long)std::floor(dz_cm / 7.8125e-4 + 0.5);
+  const long long bin_w = std::max({dz_u, 1ll, (zrange * n_vs + (1ll << 22) - 1) >> 22});
+  const long long n_zb = zrange / bin_w + 1;
+  const uint64_t n_bins = (uint64_t)n_vs * (uint64_t)n_zb;
+  const size_t btiles = scan_tiles(n_bins + 1);
   auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
   const size_t need = al(C) + 2 * al(C * 4) + 2 * al(C * 8) + 3 * al(C * 4) + al(C * 8) + al(tiles * 8) + al(64) +
-                      al(C * sizeof(tpc_track)) + al(Ncl * 4);
+                      al(C * sizeof(tpc_track)) + al(Ncl * 4) + 3 * al(C * 4) + al((n_bins + 1) * 8) +
+                      al(n_bins * 4) + al(btiles * 8);
   if (need > s->xs.bytes) {
     if (ctx->used - s->xs_bytes + need > ctx->budget) return fail(TPC_E_NOMEM, "tpc_merge_sectors: over the memory budget");
     CUDA_TRY(ensure(s->xs, need));
@@ -1012,15 +1025,32 @@ extern "C" tpc_status tpc_merge_sectors(tpc_context* ctx, uint64_t ticket, const
   X.ctl = (unsigned long long*)take(64);
   X.tracks_out = (tpc_track*)take(C * sizeof(tpc_track));
   X.cl2trk_out = (int32_t*)take(Ncl * 4);
+  X.z_in = (int32_t*)take(C * 4);
+  X.z_out = (int32_t*)take(C * 4);
+  X.ent = (uint32_t*)take(C * 4);
+  X.bin_off = (uint64_t*)take((n_bins + 1) * 8);
+  X.bin_cur = (uint32_t*)take(n_bins * 4);
+  X.bin_state = (unsigned long long*)take(btiles * 8);
   X.chi2_cut = (float)chi2_cut;
   X.edge_u = (int)std::floor(edge_cm / 7.8125e-4 + 0.5);
+  X.dz_u = (int)dz_u;
+  X.bin_w = (int)bin_w;
+  X.n_zb = (int)n_zb;
   DevGeom G = ctx->G;
   G.n_time_bins = (int)s->n_time_bins;
   G.n_frag = (int)((s->n_time_bins + kFrag - 1) / kFrag);
   G.n_events = (int)s->n_events;
   G.n_sectors = ctx->geom.n_sectors * (int)s->n_events;
   CUDA_TRY(cudaMemsetAsync(X.scan_state, 0, tiles * 8, s->stream));
-  CUDA_TRY(cudaMemsetAsync(X.ctl, 0, 64, s->stream));
+  CUDA_TRY(cudaMemsetAsync(X.bin_state, 0, btiles * 8, s->stream));
+  CUDA_TRY(cudaMemsetAsync(X.bin_off, 0, (n_bins + 1) * 8, s->stream));
+  CUDA_TRY(cudaMemsetAsync(X.bin_cur, 0, n_bins * 4, s->stream));
+  {
+    // ctl: [0] merged tracks, [1] links, [2] scan ticket, [3] bins + 1, [4] bin scan ticket, [5] bin total
+    unsigned long long c[8] = {0, 0, 0, n_bins + 1, 0, 0, 0, 0};
+    CUDA_TRY(cudaMemcpyAsync(X.ctl, c, sizeof c, cudaMemcpyHostToDevice, s->stream));
+    CUDA_TRY(cudaStreamSynchronize(s->stream));   // c lives on this stack frame
+  }
   CUDA_TRY(launch_xsec(G, ctx->P, s->W, X, ctx->n_sm, s->stream));
   unsigned long long ctl[2];
   CUDA_TRY(cudaMemcpyAsync(ctl, X.ctl, 16, cudaMemcpyDeviceToHost, s->stream));

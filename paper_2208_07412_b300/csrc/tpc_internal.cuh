@@ -261,11 +261,21 @@ struct XsWork {
   int32_t* group;                // [cap_ch] merged track of every piece
   uint64_t* scan;                // [cap_ch] root flags, scanned to merged track indices
   unsigned long long* scan_state;
-  unsigned long long* ctl;       // [0] merged tracks, [1] links, [2] (u32) scan ticket
+  unsigned long long* ctl;       // [0] merged tracks, [1] links, [2] (u32) scan ticket, [3] bins + 1,
+                                 // [4] (u32) bin scan ticket, [5] entering pieces binned
   tpc_track* tracks_out;         // [cap_ch]
   int32_t* cl2trk_out;           // [cap_cl]
+  int32_t* z_in;                 // [cap_ch] Z (u) of the innermost cluster
+  int32_t* z_out;                // [cap_ch] Z (u) of the outermost cluster
+  uint64_t* bin_off;             // [n_bins + 1] entering pieces per (virtual sector, zeta bin) -> offsets
+  uint32_t* bin_cur;             // [n_bins] fill cursors
+  uint32_t* ent;                 // [cap_ch] entering unflagged pieces grouped by bin
+  unsigned long long* bin_state; // scan state of bin_off
   float chi2_cut;
   int edge_u;
+  int dz_u;                      // |Z(B innermost) - Z(A outermost)| bound of a candidate (u)
+  int bin_w;                     // zeta bin width (u), >= dz_u
+  int n_zb;                      // zeta bins per virtual sector
 };
 
 // Work space of the optional track-model compression (step 10).

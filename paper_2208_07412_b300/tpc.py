@@ -73,7 +73,7 @@ class tpc_tuning(ctypes.Structure):
 
 
 class tpc_xs_params(ctypes.Structure):
-    _fields_ = [("chi2_cut", ctypes.c_double), ("edge_cm", ctypes.c_double)]
+    _fields_ = [("chi2_cut", ctypes.c_double), ("edge_cm", ctypes.c_double), ("dz_cm", ctypes.c_double)]
 
 
 class tpc_cmp_params(ctypes.Structure):
@@ -299,10 +299,10 @@ def tpc_autotune(ctx, pages, page_offsets, n_time_bins: int, reps: int = 3) -> d
 TPC_TRK_XSECTOR = 4
 
 
-def tpc_merge_sectors(ctx, ticket: int, chi2_cut: float = 100.0, edge_cm: float = 6.0) -> int:
+def tpc_merge_sectors(ctx, ticket: int, chi2_cut: float = 100.0, edge_cm: float = 6.0, dz_cm: float = 250.0) -> int:
     """Cross-sector merge of a finished ticket; returns the number of tracks after it."""
     n = _u64()
-    xp = tpc_xs_params(float(chi2_cut), float(edge_cm))
+    xp = tpc_xs_params(float(chi2_cut), float(edge_cm), float(dz_cm))
     _check(load().tpc_merge_sectors(ctx, ticket, ctypes.byref(xp), ctypes.byref(n)))
     return int(n.value)
 

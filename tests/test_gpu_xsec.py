@@ -39,7 +39,17 @@ def gpu_merge(lib, tf):
 
 
 def test_full_tpc_cross_sector_parity(lib):
-    tf = tpcgen.generate(tpcgen.full_tpc(1))
+    check_parity(lib, tpcgen.generate(tpcgen.full_tpc(1)), min_multi=1000)
+
+
+def test_continuous_timeframe_cross_sector_parity(lib):
+    """2000 bins of the 50 kHz continuous timeframe: the candidate search runs
+    over several zeta bins per sector, and pieces of different collisions
+    overlap in time."""
+    check_parity(lib, tpcgen.generate(tpcgen.continuous_tf(1, n_time_bins=2000)), min_multi=300)
+
+
+def check_parity(lib, tf, min_multi):
     orc = oracle.reconstruct(tf)
     ox = oracle.merge_sectors(tf, orc)
     cl, tr, m, mt, mm, link = gpu_merge(lib, tf)
@@ -71,7 +81,7 @@ def test_full_tpc_cross_sector_parity(lib):
     oi = {c: i for i, c in enumerate(oc)}
     gi = {c: i for i, c in enumerate(gc)}
     multi = [c for c in common if len(c) > 1]
-    assert len(multi) > 1000
+    assert len(multi) > min_multi
     diag = [0, 2, 5, 9, 14]
     worst = np.zeros(5)
     worst_cov = 0.0
