@@ -15,6 +15,8 @@
 
 namespace tpc {
 
+constexpr int kAhead = 8;   // clusters loaded ahead of the one being fitted
+
 template <int kThreads>
 __global__ void __launch_bounds__(kThreads)
 k_fit(DevGeom G, DevParams P, DevWork W) {
@@ -51,10 +53,15 @@ k_fit(DevGeom G, DevParams P, DevWork W) {
       chi2 = 0.f;
       n_used = 0;
       const bool inward = (pass & 1) == 0;
-      int4 nxt = pts[inward ? n - 1 : 0];
+      // the next kAhead clusters in flight (an L2 round trip is longer than one update)
+      int4 q[kAhead];
+#pragma unroll
+      for (int a = 0; a < kAhead; a++) q[a] = a < n ? pts[inward ? n - 1 - a : a] : make_int4(0, 0, 0, 0);
       for (int jj = 0; jj < n; jj++) {
-        const int4 cur = nxt;
-        if (jj + 1 < n) nxt = pts[inward ? n - 2 - jj : jj + 1];   // one cluster ahead
+        const int4 cur = q[0];
+#pragma unroll
+        for (int a = 0; a + 1 < kAhead; a++) q[a] = q[a + 1];
+        if (jj + kAhead < n) q[kAhead - 1] = pts[inward ? n - 1 - kAhead - jj : jj + kAhead];
         const int Xi = cur.x;
         if (Xi != xcur) {
           Jac<float> J;

@@ -421,10 +421,34 @@ __global__ void k_xs_emit(DevGeom G, DevParams P, DevWork W, XsWork X) {
       chi2 = 0.f;
       n_used = 0;
       const bool inward = (pass & 1) == 0;
+      // the chain walk keeps its piece's offset, length and sector, and the
+      // next point's load is in flight while the current one is fitted
       int t = inward ? last : (int)r;
-      int l = inward ? W.trk_ncl[last] - 1 : 0;
-      for (int jj = 0; jj < ncl && t >= 0; jj++) {
-        const XsPoint q = xs_point(G, W, t, l, Z0);
+      int off = W.trk_off[t], nn = W.trk_ncl[t], sec = W.tracks[t].sector;
+      int l = inward ? nn - 1 : 0;
+      int4 nxt = W.trk_xyz[off + l];
+      int nsec = sec;
+      bool more = true;
+      for (int jj = 0; jj < ncl && more; jj++) {
+        const int4 pq = nxt;
+        XsPoint q;
+        q.x = (float)pq.x * kU;
+        q.y = (float)pq.y * kU;
+        q.z = (float)(pq.z - Z0) * kU;
+        q.sector_phys = nsec;
+        if (inward) {
+          if (--l < 0) {
+            t = X.prev[t];
+            if (t >= 0) { off = W.trk_off[t]; nn = W.trk_ncl[t]; sec = W.tracks[t].sector; l = nn - 1; }
+          }
+        } else {
+          if (++l >= nn) {
+            t = X.link[t];
+            if (t >= 0) { off = W.trk_off[t]; nn = W.trk_ncl[t]; sec = W.tracks[t].sector; l = 0; }
+          }
+        }
+        more = t >= 0;
+        if (more) { nxt = W.trk_xyz[off + l]; nsec = sec; }
         const float aq = sector_alpha(q.sector_phys);
         if (aq != acur) {
           Rot Rr;
@@ -441,12 +465,6 @@ __global__ void k_xs_emit(DevGeom G, DevParams P, DevWork W, XsWork X) {
         }
         chi2 += xs_measure(P, s, M, q.y, q.z, flags, nfp64);
         n_used++;
-        // next point along the chain
-        if (inward) {
-          if (--l < 0) { t = X.prev[t]; if (t >= 0) l = W.trk_ncl[t] - 1; }
-        } else {
-          if (++l >= W.trk_ncl[t]) { t = X.link[t]; l = 0; }
-        }
       }
     }
     tpc_track out;
