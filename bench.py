@@ -723,6 +723,7 @@ def run_ours(args, world, rank, local):
                                 else "per-timeframe pipeline replayed from a captured CUDA graph"),
                        "finder": "dense-plane variant" if args.dense_finder else "fused"},
             "tracks_per_s": tr_all / dev_s_max,
+            "fp64_redos_per_tf": int(ctr["fp64_redos"]),
             "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
             "stages_ms": stages,
             "wall_ms_per_step": 1e3 * wall / args.steps,
