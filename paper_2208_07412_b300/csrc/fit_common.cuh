@@ -14,7 +14,10 @@ struct Jac { T a, b, e, g, h, m; };  // F02, F04, F12, F13, F14, F24
 
 __device__ __forceinline__ float sgnf(float v) { return v > 0.f ? 1.f : (v < 0.f ? -1.f : 0.f); }
 
-__device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
+// FP32 reciprocal: the hardware approximation (2 ulp), not the IEEE-rounded
+// one, whose correction steps sit on the fit's serial chain (the longest
+// track's 3 x 152 updates set the fit's time).
+__device__ __forceinline__ float rcp(float x) { return __fdividef(1.f, x); }
 __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
 
 // Exact helix transport by dx (state in place).  false: |snp| would reach
