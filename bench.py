@@ -50,6 +50,12 @@ REF_SAMPLE_BYTES = 20 << 20
 # the current kernel on the workload (seed 1); None where no capture exists.
 # Must be reset to None whenever the finder kernel changes.
 FINDER_DRAM_BYTES = {"full_tpc": 70_606_592 + 6_217_472}
+# Warp instructions (smsp__inst_executed.sum) of the same launch, for the issue
+# roofline; reset together with FINDER_DRAM_BYTES.
+FINDER_WARP_INSTR = {"full_tpc": 568_526_592}
+# Warp-instruction issue peak: 148 SMs x 4 schedulers x 1 instruction per cycle
+# at the 2032 MHz maximum SM clock.
+ISSUE_PEAK = 148 * 4 * 2.032e9
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -733,6 +739,14 @@ def run_ours(args, world, rank, local):
                                      if args.seed == 1 and not args.time_bins and not args.dense_finder else None),
                          "peak_kind": f"{peak_kind} hbm_gbs (copy)",
                          "algorithmic_bytes_per_launch": int(alg_bytes)},
+            "roofline_issue": (None if not (args.seed == 1 and not args.time_bins and not args.dense_finder
+                                            and args.workload in FINDER_WARP_INSTR) else
+                               {"kernel": "k_find_clusters", "bound": "issue",
+                                "achieved": FINDER_WARP_INSTR[args.workload] / (stages["find"] * 1e-3),
+                                "peak": ISSUE_PEAK, "unit": "warp-instr/s",
+                                "frac": FINDER_WARP_INSTR[args.workload] / (stages["find"] * 1e-3) / ISSUE_PEAK,
+                                "instructions": "ncu smsp__inst_executed.sum of one launch",
+                                "peak_kind": "148 SMs x 4 schedulers x 2032 MHz"}),
             "e2e": {"value": cl_all / e2e_s_max, "unit": "clusters/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h),
                     "path": "submit from pinned host pages, read clusters, tracks and map back into pinned "
