@@ -588,6 +588,32 @@ __device__ __forceinline__ void prefetch_next_dense(const DevGeom& G, const DevW
 // another.  Otherwise (the allocation-free entry point, which has no scratch
 // buffer for records): a decoupled look-back over the windows gives each its
 // canonical offset and the records are written in place; only the records.
+// The neighbour pages' 32-byte headers of a window into hdr[0..3] (two 16-byte
+// halves of the previous page, then of the next page), zero where the window
+// has no such neighbour or the offset is unusable; plain loads, or 16-byte
+// cp.async copies (one group, committed) that the caller waits for before use.
+__device__ __forceinline__ void cp_async16(void* dst_smem, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(__cvta_generic_to_global(src)) : "memory");
+}
+
+template <int kMode, bool kAsync>
+__device__ __forceinline__ void load_nb_headers(const DevGeom& G, const DevWork& W, int frs, uint64_t op, uint64_t on,
+                                                uint4* hdr) {
+  const int f = frs & 0xffff;
+#pragma unroll
+  for (int k = 0; k < 4; k++) {
+    const uint64_t o2 = k < 2 ? op : on;
+    const bool want = kMode == 0 && (k < 2 ? f > 0 : f + 1 < G.n_frag) && o2 != ~0ull && (o2 & 15) == 0 &&
+                      o2 <= W.pages_bytes && W.pages_bytes - o2 >= 32;
+    const uint4* src = reinterpret_cast<const uint4*>(W.pages + (want ? o2 : 0)) + (k & 1);
+    if (!want) hdr[k] = make_uint4(0u, 0u, 0u, 0u);
+    else if (kAsync) cp_async16(hdr + k, src);
+    else hdr[k] = __ldg(src);
+  }
+  if (kAsync) asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
 // kMode: 0 the fused finder (pages -> clusters); 1 and 2 the dense-plane
 // variant: 1 decodes each window's own page into a dense HBM plane of ADC
 // values, 2 reads a window and its 3-bin halos back from that plane and runs
@@ -664,23 +690,29 @@ k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
       const long long j = (long long)w0 - 1 + k;
       S.offs[k] = (j >= 0 && j < (long long)n_windows && w0 < n_windows) ? W.page_offsets[j] : ~0ull;
     }
+    if (kMode != 2 && w0 < n_windows) load_nb_headers<kMode, false>(G, W, S.misc[2], S.offs[0], S.offs[2], S.hdr);
   }
   unsigned int nt = 0;                  // next window (thread 0, scratch mode)
   unsigned long long noffs[4] = {~0ull, ~0ull, ~0ull, ~0ull};
   while (true) {
-    // ---- 0. window w
+    // ---- 0. window w (scratch mode: its neighbours' headers were copied
+    // during the previous window)
     if (!kScratch && tid == 0) {
       const unsigned wt = atomicAdd(&W.tickets[TK_FIND], 1u);
       S.misc[1] = (int)wt;
       S.misc[2] = wt < n_windows ? window_frs(G, wt) : 0;
     }
+    if (kScratch && kMode != 2 && tid == 0) asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
     const unsigned int w = (unsigned int)S.misc[1];
     if (w >= n_windows) break;
     if (kScratch && tid == 0) nt = atomicAdd(&W.tickets[kMode == 2 ? TK_FIND2 : TK_FIND], 1u);
-    if (!kScratch && tid < 4) {
-      const long long j = (long long)w - 1 + tid;
-      S.offs[tid] = (j >= 0 && j < (long long)n_windows) ? W.page_offsets[j] : ~0ull;
+    if (!kScratch && tid == 0) {
+      for (int k = 0; k < 4; k++) {
+        const long long j = (long long)w - 1 + k;
+        S.offs[k] = (j >= 0 && j < (long long)n_windows) ? W.page_offsets[j] : ~0ull;
+      }
+      if (kMode != 2) load_nb_headers<kMode, false>(G, W, S.misc[2], S.offs[0], S.offs[2], S.hdr);
     }
     {
       // occ, pk and dbm are adjacent: clear them as 16-byte words (the tail word by word)
@@ -701,7 +733,10 @@ k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
     bool listed;
     if (kMode != 2) {
       // ---- 1. one round trip: stage the page (length guessed from the next
-      // page's offset) and load both neighbours' headers
+      // page's offset); warps 0-2 copy the previous page's entries / runs / ADC
+      // words of its last 3 bins, warps 3-5 the next page's of its first 3 bins
+      // (the neighbours' headers are already in shared memory), warp 6 parses
+      // the own header from global memory: all copies in flight together
       uint32_t copied = 0;
       if (off <= W.pages_bytes && W.pages_bytes - off >= 32 && (off & 15) == 0) {
         uint64_t guess = (S.offs[2] != ~0ull && S.offs[2] > off) ? S.offs[2] - off : W.pages_bytes - off;
@@ -711,19 +746,6 @@ k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
         const uint4* src = reinterpret_cast<const uint4*>(W.pages + off);
         for (uint32_t i = tid; i < copied / 16; i += blockDim.x) reinterpret_cast<uint4*>(own_stage)[i] = __ldg(src + i);
       }
-      if (tid < 4) {
-        const uint64_t o2 = S.offs[tid < 2 ? 0 : 2];
-        const bool want = (tid < 2 ? f > 0 : f + 1 < G.n_frag) && o2 != ~0ull && (o2 & 15) == 0 && o2 <= W.pages_bytes &&
-                          W.pages_bytes - o2 >= 32;
-        S.hdr[tid] = want ? __ldg(reinterpret_cast<const uint4*>(W.pages + o2) + (tid & 1)) : make_uint4(0, 0, 0, 0);
-      }
-      __syncthreads();
-
-      // ---- 2. the three headers and the neighbours' halo byte ranges: warps 0-2
-      // copy the previous page's entries / runs / ADC words of its last 3 bins,
-      // warps 3-5 the next page's of its first 3 bins, each warp parsing the
-      // header it needs (one round trip, all six copies in flight); warp 6 parses
-      // the own header
       const bool own_global = copied < 32;
       {
         const int wid = tid >> 5, lane = tid & 31;
@@ -770,8 +792,7 @@ k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
           }
         } else if (wid == 6 && lane == 0) {
           PageHdr hh;
-          const bool okk = parse_header(reinterpret_cast<const uint4*>(own_global ? W.pages + off : own_stage), off,
-                                        W.pages_bytes, hh) &&
+          const bool okk = parse_header(reinterpret_cast<const uint4*>(W.pages + off), off, W.pages_bytes, hh) &&
                            hh.sector == s && hh.row == r && hh.frag == f;
           S.ph[0] = hh;
           S.misc[4] = okk;
@@ -910,7 +931,10 @@ k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
     }
 
     if (kMode == 1) {
-      if (kScratch && tid == 0 && nt < n_windows) prefetch_next_pages(W, noffs);
+      if (kScratch && tid == 0 && nt < n_windows) {
+        prefetch_next_pages(W, noffs);
+        load_nb_headers<kMode, true>(G, W, window_frs(G, nt), noffs[0], noffs[2], S.hdr);
+      }
       // ---- dense variant, decode pass: the window's own rows into the dense
       // plane, 16-byte chunks of 8 pads (pads past the row's end written as 0)
       const int sr = (int)(w / (unsigned)G.n_frag);
@@ -981,8 +1005,12 @@ k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
       const uint32_t* const sv = (kNs ? S.occ : S.pk) + kHalo * nw;
 
       if (kScratch && tid == 0 && nt < n_windows) {
-        if (kMode == 2) prefetch_next_dense(G, W, nt);
-        else prefetch_next_pages(W, noffs);
+        if (kMode == 2) {
+          prefetch_next_dense(G, W, nt);
+        } else {
+          prefetch_next_pages(W, noffs);
+          load_nb_headers<kMode, true>(G, W, window_frs(G, nt), noffs[0], noffs[2], S.hdr);
+        }
       }
 
       // ---- 5. rank the own peaks (rows 3..258) in canonical order, list the
