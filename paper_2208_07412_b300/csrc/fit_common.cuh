@@ -152,12 +152,14 @@ __device__ __forceinline__ T ud_update(T s[5], UD<T>& M, T z, T r) {
   return innov * g;
 }
 
+// Positive-definiteness check of the factors (every D entry in (0, 1e30)),
+// without short-circuit branches on the update chain.
 template <typename T>
 __device__ __forceinline__ bool ud_pd(const UD<T>& M) {
-  bool ok = true;
+  int ok = 1;
 #pragma unroll
-  for (int i = 0; i < 5; i++) ok = ok && (M.d[i] > T(0)) && (M.d[i] < T(1e30));
-  return ok;
+  for (int i = 0; i < 5; i++) ok &= (int)(M.d[i] > T(0)) & (int)(M.d[i] < T(1e30));
+  return ok != 0;
 }
 
 }  // namespace tpc
