@@ -165,6 +165,17 @@ def job_totals(world, n_cl: int, n_tr: int, steps: int, dev_s: float):
             max_over_ranks(world, dev_s))
 
 
+def ref_sample_tf(tf, sample_bytes: float = REF_SAMPLE_BYTES):
+    """The timeframe the oracle samples from: the whole one, or, where one
+    sector holds more than sample_bytes of pages (long continuous timeframes),
+    its first fragments, as many as keep one sector near sample_bytes."""
+    per_sector = tf.pages.nbytes / max(tf.n_sectors, 1)
+    if per_sector <= sample_bytes:
+        return tf, ""
+    k = max(1, int(tf.n_fragments * sample_bytes / per_sector))
+    return tpcgen.time_prefix(tf, k), f"the first {min(tf.n_time_bins, 256 * k)} time bins of "
+
+
 def ref_sample_sectors(tf, sample_bytes: float = REF_SAMPLE_BYTES) -> int:
     """Sectors in the oracle's sample: about sample_bytes of ZS pages (20 MB: a
     few seconds of single-core CPU work), at least one sector."""
@@ -174,6 +185,7 @@ def ref_sample_sectors(tf, sample_bytes: float = REF_SAMPLE_BYTES) -> int:
 
 def cpu_baseline(tf, steps=1, sample_bytes: float = REF_SAMPLE_BYTES):
     import oracle
+    tf, what = ref_sample_tf(tf, sample_bytes)
     sub = tpcgen.sector_prefix(tf, ref_sample_sectors(tf, sample_bytes))
     times, ncl, ntr = [], 0, 0
     for _ in range(steps):
@@ -182,7 +194,7 @@ def cpu_baseline(tf, steps=1, sample_bytes: float = REF_SAMPLE_BYTES):
         times.append(time.perf_counter() - t0)
         ncl, ntr = len(r.clusters), len(r.track_first)
     return {"times": times, "clusters": ncl, "tracks": ntr,
-            "sample": f"sectors 0-{sub.n_sectors - 1} of the same timeframe ({sub.n_sectors}/{tf.n_sectors}), "
+            "sample": f"{what}sectors 0-{sub.n_sectors - 1} of the same timeframe ({sub.n_sectors}/{tf.n_sectors}), "
                       f"{ncl} clusters, {ntr} tracks per step"}
 
 
@@ -211,10 +223,12 @@ class OraclePool:
         self.pool.map(_oracle_warm, range(self.procs))   # imports and loads outside the timed region
 
     def run(self, tf, sample_bytes: float = REF_SAMPLE_BYTES, steps: int = 1):
-        """Time `steps` passes over the first max(procs, sample) sectors, one
-        task per sector, rounded down to a multiple of the process count."""
-        n1 = ref_sample_sectors(tf, sample_bytes)
-        n = min(tf.n_sectors, max(self.procs, (n1 // self.procs) * self.procs))
+        """Time `steps` passes over the first sectors, one task per sector: as
+        many sectors as processes, but no more ZS bytes than sample_bytes per
+        process (the work stays bounded on long timeframes), at least one."""
+        tf, what = ref_sample_tf(tf, sample_bytes)
+        per_sector = tf.pages.nbytes / max(tf.n_sectors, 1)
+        n = int(min(tf.n_sectors, self.procs, max(1, self.procs * sample_bytes // max(per_sector, 1))))
         subs = [tpcgen.sector_slice(tf, s) for s in range(n)]
         times, ncl, ntr = [], 0, 0
         for _ in range(steps):
@@ -223,7 +237,7 @@ class OraclePool:
             times.append(time.perf_counter() - t0)
             ncl, ntr = sum(r[0] for r in res), sum(r[1] for r in res)
         return {"times": times, "clusters": ncl, "tracks": ntr, "cores": min(self.procs, n),
-                "sample": f"sectors 0-{n - 1} of the same timeframe ({n}/{tf.n_sectors}), one oracle process "
+                "sample": f"{what}sectors 0-{n - 1} of the same timeframe ({n}/{tf.n_sectors}), one oracle process "
                           f"per sector on a spawn pool of {self.procs}, {ncl} clusters, {ntr} tracks per step"}
 
     def close(self):
@@ -525,21 +539,23 @@ def finder_variants(tpc, torch, tf, pages_d, offs_d, tuning, flush, fused_ms, re
     n_frag = (tf.n_time_bins + 255) // 256
     alloc = tf.n_sectors * len(tf.npads) * n_frag * 256 * stride * 2
     free_now, _ = torch.cuda.mem_get_info()
-    if alloc + 8 * tf.pages.nbytes > 0.8 * free_now:   # the plane + a slot (~5x the pages)
-        return {"skipped": f"the dense plane needs {alloc / 1e9:.1f} GB"}
     Rd = tpc.Reconstructor.for_timeframe(tf, device=torch.cuda.current_device(),
                                          flags=tpc.TPC_CTX_STAGE_TIMING | tpc.TPC_CTX_DENSE_FINDER,
-                                         mem_budget=int(0.8 * free_now))
+                                         mem_budget=int(0.9 * free_now))
     tpc.tpc_set_tuning(Rd.ctx, **tuning)
     times = []
-    for i in range(reps + 2):
-        flush.fill_(1)
-        t = Rd.submit(pages_d, offs_d, tf.n_time_bins)
-        Rd.wait(t)
-        if i >= 2:
-            times.append(tpc.tpc_get_stage_times(Rd.ctx, t)["find"])
-        tpc.tpc_release(Rd.ctx, t)
-    Rd.close()
+    try:
+        for i in range(reps + 2):
+            flush.fill_(1)
+            t = Rd.submit(pages_d, offs_d, tf.n_time_bins)
+            Rd.wait(t)
+            if i >= 2:
+                times.append(tpc.tpc_get_stage_times(Rd.ctx, t)["find"])
+            tpc.tpc_release(Rd.ctx, t)
+    except tpc.TpcError as e:   # the plane and a slot do not fit the free memory
+        return {"skipped": f"the dense plane ({alloc / 1e9:.1f} GB) with a slot does not fit: {e}"}
+    finally:
+        Rd.close()
     dense_ms = statistics.mean(times)
     # algorithmic bytes of the dense pair: the pages once, the plane written
     # once and read once (+6 halo rows per 256-bin window)
@@ -760,6 +776,7 @@ def run_ours(args, world, rank, local):
             line["compression"] = compression_stats(tpc, R, pages_d, offs_d, tf)
         if world == 1 and args.workload == "full_tpc":   # one collision: its vertex time
             line["calibration"] = calibration_stats(tpc, R, pages_d, offs_d, tf)
+        R.close()   # its slot's memory goes to the comparisons below
         if world == 1 and not (args.no_variants or args.dense_finder) and args.workload in ("full_tpc", "continuous_50khz"):
             line["finder_variants"] = finder_variants(tpc, torch, tf, pages_d, offs_d, tuning, flush,
                                                       stages["find"])

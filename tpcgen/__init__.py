@@ -291,6 +291,30 @@ def continuous_tf(seed: int = 1, n_time_bins: int = 55000, rate_per_bin: float =
     return GenConfig(**d)
 
 
+def time_prefix(tf: Timeframe, n_fragments: int) -> Timeframe:
+    """The first n_fragments 256-bin fragments of every (sector, row) of a
+    timeframe as a timeframe of their own (pages copied in window order; a
+    page's header keeps its fragment number, and the last kept fragment simply
+    has no next neighbour)."""
+    import copy
+    nf_old = tf.n_fragments
+    k = max(1, min(int(n_fragments), nf_old))
+    if k == nf_old:
+        return tf
+    offs = tf.page_offsets.astype(np.int64)
+    ends = np.append(offs[1:], len(tf.pages))
+    idx = (np.arange(tf.n_sectors * tf.n_rows)[:, None] * nf_old + np.arange(k)[None, :]).ravel()
+    lens = ends[idx] - offs[idx]
+    new_offs = np.concatenate([[0], np.cumsum(lens)[:-1]]).astype(np.uint64)
+    pages = np.concatenate([tf.pages[offs[i]:ends[i]] for i in idx]) if len(idx) else tf.pages[:0]
+    s = copy.copy(tf)
+    s.pages, s.page_offsets = pages, new_offs
+    s.n_time_bins = min(tf.n_time_bins, 256 * k)
+    s.digit_labels = None
+    s.tracks, s.hits = tf.tracks[:0], tf.hits[:0]
+    return s
+
+
 def sector_slice(tf: Timeframe, sector: int) -> Timeframe:
     """One sector of a timeframe as a single-sector timeframe of its own: it
     becomes sector 0 (the sector byte at offset 10 of every page header is
