@@ -31,7 +31,8 @@ __device__ __forceinline__ long long llabs_(long long v) { return v < 0 ? -v : v
 // A slice larger than the stage is read from global memory instead.  The
 // iteration order (d ascending, then u ascending, strict <) is the definition's
 // tie rule.
-constexpr int kCaThreads = 256, kCaChunk = 256, kCaStage = 1536;
+constexpr int kCaThreads = 128, kCaChunk = 128, kCaStage = 768;
+static_assert(kCaThreads >= 128 && kCaThreads % 32 == 0, "four warps compute the four slice bounds");
 
 struct Slice {
   const int32_t* t; const int32_t* y; const int32_t* z;
