@@ -49,10 +49,10 @@ REF_SAMPLE_BYTES = 20 << 20
 # DRAM bytes (read + write) of one k_find_clusters launch, from an ncu capture of
 # the current kernel on the workload (seed 1); None where no capture exists.
 # Must be reset to None whenever the finder kernel changes.
-FINDER_DRAM_BYTES = {"full_tpc": 70_624_256 + 5_735_680}
+FINDER_DRAM_BYTES = {}
 # Warp instructions (smsp__inst_executed.sum) of the same launch, for the issue
 # roofline; reset together with FINDER_DRAM_BYTES.
-FINDER_WARP_INSTR = {"full_tpc": 569_099_464}
+FINDER_WARP_INSTR = {}
 # Warp-instruction issue peak: 148 SMs x 4 schedulers x 1 instruction per cycle
 # at the 2032 MHz maximum SM clock.
 ISSUE_PEAK = 148 * 4 * 2.032e9

@@ -70,6 +70,13 @@ constexpr int kPad = 2;                      // empty pads on each side of a pla
 constexpr int kDenseU = 7;                   // dense-plane chunks a thread has in flight
 constexpr int kMaxRuns = 2048;               // runs of a window decoded run-parallel (beyond: per entry)
 constexpr int kRunMapWords = kList / 32;     // run-start bitmap over the listed digits
+// Windows with more than kList digits (a dense row) are decoded the same
+// balanced way, the list area then holding, instead of one plane index per
+// digit, one per run (run_L), the run-start bitmap over up to kMaxDig digits
+// and the run starts before each bitmap word; they skip the digit list.
+constexpr int kMaxDig = 16384;
+constexpr int kBigWords = kMaxDig / 32;
+static_assert(kMaxRuns * 2 + kBigWords * 4 + kBigWords * 2 <= kList * 2, "the big-window maps fit the list area");
 
 struct FindSmem {
   uint16_t* plane;     // [kWinT][ps], pixel (tt, p) at tt * ps + p + kPad; zero where no digit
@@ -321,6 +328,9 @@ __device__ __forceinline__ int window_frs(const DevGeom& G, unsigned int w) {
 //     the run start in a bitmap and sets its occupancy bits;
 //   digits (strided): the run start below the digit from the bitmap, the
 //     digit's plane index from it, its ADC value into the plane.
+// A big window (more than kList digits, at most kMaxDig) keeps the plane
+// index per run instead of per digit; a digit finds its run's number from the
+// run starts counted before its bitmap word, and no digit list is made.
 // Every read is bounds-checked against the segment counts from the headers and
 // every write against the plane and the list.  Segment k may be empty.  Returns
 // true (block-uniform) if every check passed.
@@ -335,12 +345,19 @@ __device__ __forceinline__ V sel3(int k, V a, V b, V c) { return k == 0 ? a : (k
 // (The three segments are separate by-value parameters: indexing an array of
 // them with a runtime segment number would place it in local memory.)
 __device__ __forceinline__ bool decode_window(const WinSeg s0, const WinSeg s1, const WinSeg s2, int np, int ps_stride,
-                                              int nw, int T, const FindSmem& S) {
+                                              int nw, int T, const FindSmem& S, bool big) {
   const int tid = threadIdx.x, nt = (int)blockDim.x;
   const int ebase1 = s0.ne, ebase2 = s0.ne + s1.ne, ne = ebase2 + s2.ne;
   const int rbase1 = s0.nrun, rbase2 = s0.nrun + s1.nrun, nrun = rbase2 + s2.nrun;
   const int dbase1 = s0.ndig, dbase2 = s0.ndig + s1.ndig, ndig = dbase2 + s2.ndig;
   bool bad = ne > 2 * nt;
+  // big window: run_L | run-start bitmap | run starts before each word, in the list area
+  uint16_t* const runL = S.list;
+  uint32_t* const dbmB = reinterpret_cast<uint32_t*>(S.list + kMaxRuns);
+  uint16_t* const wpre = reinterpret_cast<uint16_t*>(dbmB + kBigWords);
+  uint32_t* const dbm = big ? dbmB : S.dbm;
+  if (big)
+    for (int i = tid; i < kBigWords; i += nt) dbmB[i] = 0u;   // first read after the entries' barrier
   // ---- entries
   int e_t[2] = {0, 0}, e_nr[2] = {0, 0}, my_nr = 0;
 #pragma unroll
@@ -408,9 +425,10 @@ __device__ __forceinline__ bool decode_window(const WinSeg s0, const WinSeg s1, 
       // a segment's first run must start at the segment's first digit
       if ((r == rbase1 && s1.nrun > 0 && d != dbase1) || (r == rbase2 && s2.nrun > 0 && d != dbase2)) bad = true;
       const int tt = S.run_t[r] + sel3(k, s0.tt_base, s1.tt_base, s2.tt_base);   // stale if its entry failed: checked
-      if (d + len <= ndig && d + len <= kList && tt >= 0 && tt < kWinT) {
-        S.list[d] = (uint16_t)(tt * ps_stride + kPad + ps);
-        atomicOr(&S.dbm[d >> 5], 1u << (d & 31));
+      if (d + len <= ndig && d + len <= (big ? kMaxDig : kList) && tt >= 0 && tt < kWinT && r < kMaxRuns) {
+        const uint16_t L0 = (uint16_t)(tt * ps_stride + kPad + ps);
+        if (big) runL[r] = L0; else S.list[d] = L0;
+        atomicOr(&dbm[d >> 5], 1u << (d & 31));
         set_occ(S, nw, tt, ps, len);
       } else {
         bad = true;
@@ -420,15 +438,38 @@ __device__ __forceinline__ bool decode_window(const WinSeg s0, const WinSeg s1, 
   }
   const bool valid = !__syncthreads_or(bad);
   if (!valid) return false;
+  if (big) {
+    // run starts before each bitmap word (run r starts at the r-th set bit)
+    const int nwd = (ndig + 31) >> 5;
+    const int per = (nwd + nt - 1) / nt;
+    const int wa = min(tid * per, nwd), wb = min(wa + per, nwd);
+    uint32_t c = 0;
+    for (int i = wa; i < wb; i++) c += __popc(dbmB[i]);
+    uint32_t tot3;
+    uint32_t pre = block_excl_scan32(c, reinterpret_cast<uint32_t*>(S.scan), &tot3);
+    for (int i = wa; i < wb; i++) {
+      wpre[i] = (uint16_t)pre;
+      pre += __popc(dbmB[i]);
+    }
+    __syncthreads();
+  }
   // ---- digits
   const int nplane = kWinT * ps_stride;
   for (int d = tid; d < ndig; d += nt) {
     int w = d >> 5;
-    uint32_t m = S.dbm[w] & (0xffffffffu >> (31 - (d & 31)));
-    while (m == 0 && w > 0) m = S.dbm[--w];   // digit 0 always starts a run
-    const int st = 32 * w + 31 - __clz(m);
-    const int L = (int)S.list[st] + (d - st);
-    if (d != st) S.list[d] = (uint16_t)L;
+    uint32_t m = dbm[w] & (0xffffffffu >> (31 - (d & 31)));
+    int L;
+    if (big) {
+      const int rr = min(max((int)wpre[w] + __popc(m) - 1, 0), kMaxRuns - 1);   // the run holding digit d
+      while (m == 0 && w > 0) m = dbmB[--w];          // digit 0 always starts a run
+      const int st = 32 * w + 31 - __clz(m);
+      L = (int)runL[rr] + (d - st);
+    } else {
+      while (m == 0 && w > 0) m = S.dbm[--w];   // digit 0 always starts a run
+      const int st = 32 * w + 31 - __clz(m);
+      L = (int)S.list[st] + (d - st);
+      if (d != st) S.list[d] = (uint16_t)L;
+    }
     const int k = d < dbase1 ? 0 : (d < dbase2 ? 1 : 2);
     const int idx = sel3(k, s0.dfirst, s1.dfirst, s2.dfirst) + d - (k == 0 ? 0 : (k == 1 ? dbase1 : dbase2));
     const uint32_t word = sel3(k, s0.adc, s1.adc, s2.adc)[idx / 3];
@@ -830,13 +871,13 @@ k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
                      reinterpret_cast<const uint32_t*>(own + h.body), 0, h.n_dig, kHalo, kFrag * f,
                      listed ? 0 : kList, true};
         const int nrun_all = (okp ? hp.n_runs - hp.hi_runs : 0) + (ok ? h.n_runs : 0) + (okn ? hn.lo_runs : 0);
-        if (ok && listed && nrun_all <= kMaxRuns) {
+        if (ok && use_list && nrun_all <= kMaxRuns && ndig <= kMaxDig) {
           const WinSeg s0{gp.ent, gp.run, gp.adc, okp ? gp.ne : 0, okp ? gp.nrun : 0, n_prev, gp.dfirst, gp.tt_base,
                           gp.t_base_abs};
           const WinSeg s1{go.ent, go.run, go.adc, go.ne, go.nrun, n_own, 0, go.tt_base, go.t_base_abs};
           const WinSeg s2{gn.ent, gn.run, gn.adc, okn ? gn.ne : 0, okn ? gn.nrun : 0, n_next, 0, gn.tt_base,
                           gn.t_base_abs};
-          ok = decode_window(s0, s1, s2, np, ps_stride, nw, T, S);
+          ok = decode_window(s0, s1, s2, np, ps_stride, nw, T, S, !listed);
         } else {
           ok = decode_seg(go, ok, np, ps_stride, nw, T, S, okp ? &gp : nullptr, okn ? &gn : nullptr);
         }
