@@ -1011,15 +1011,54 @@ k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
             }
           }
         } else {
-          // too many digits to list: walk the occupancy bitmap
-          for (int wi_ = nw + tid; wi_ < (kWinT - 1) * nw; wi_ += blockDim.x) {
-            uint32_t word = S.occ[wi_];
-            const int tt = wi_ / nw, p0 = (wi_ % nw) * 32;
-            while (word) {
-              const int b = __ffs(word) - 1;
-              word &= word - 1;
-              if (peak_at(S.plane, tt * ps_stride + kPad + p0 + b, ps_stride, P.q_peak_min))
-                atomicOr(&S.pk[wi_], 1u << b);
+          // too many digits to list: the occupied pixels of rows 1..260 in
+          // equal shares per thread; a scan of the occupancy words' counts,
+          // kept in the (now free) list area, finds each share's first word
+          const int w0 = nw, nwd = (kWinT - 2) * nw;
+          uint16_t* const wpre = S.list;
+          const int per = (nwd + (int)blockDim.x - 1) / (int)blockDim.x;
+          const int a = min(tid * per, nwd), b = min(a + per, nwd);
+          uint32_t c = 0;
+          for (int i = a; i < b; i++) c += __popc(S.occ[w0 + i]);
+          uint32_t tot;
+          uint32_t pre = block_excl_scan32(c, reinterpret_cast<uint32_t*>(S.scan), &tot);
+          for (int i = a; i < b; i++) {
+            wpre[i] = (uint16_t)pre;
+            pre += __popc(S.occ[w0 + i]);
+          }
+          __syncthreads();
+          if (tot <= 65535u) {
+            const uint32_t share = (tot + blockDim.x - 1) / blockDim.x;
+            const uint32_t k0 = min(tid * share, tot), k1 = min(k0 + share, tot);
+            if (k0 < k1) {
+              int lo = 0, hi = nwd - 1;   // the last word whose count prefix is <= k0
+              while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if ((uint32_t)wpre[mid] <= k0) lo = mid; else hi = mid - 1;
+              }
+              int wi = lo;
+              uint32_t word = S.occ[w0 + wi];
+              for (uint32_t q = k0 - wpre[wi]; q > 0; q--) word &= word - 1;
+              for (uint32_t k = k0; k < k1; k++) {
+                while (word == 0 && wi + 1 < nwd) word = S.occ[w0 + ++wi];
+                if (word == 0) break;
+                const int bb = __ffs(word) - 1;
+                word &= word - 1;
+                const int gw = w0 + wi, tt = gw / nw, p0 = (gw % nw) * 32;
+                if (peak_at(S.plane, tt * ps_stride + kPad + p0 + bb, ps_stride, P.q_peak_min))
+                  atomicOr(&S.pk[gw], 1u << bb);
+              }
+            }
+          } else {   // more than 2^16 occupied pixels: word by word
+            for (int wi_ = nw + tid; wi_ < (kWinT - 1) * nw; wi_ += blockDim.x) {
+              uint32_t word = S.occ[wi_];
+              const int tt = wi_ / nw, p0 = (wi_ % nw) * 32;
+              while (word) {
+                const int bq = __ffs(word) - 1;
+                word &= word - 1;
+                if (peak_at(S.plane, tt * ps_stride + kPad + p0 + bq, ps_stride, P.q_peak_min))
+                  atomicOr(&S.pk[wi_], 1u << bq);
+              }
             }
           }
         }
@@ -1153,19 +1192,12 @@ k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
         const int L = S.list[i];
         if (L < nplane) S.plane[L] = 0;
       }
-    } else if (kNs) {   // occ's own rows hold the surviving peaks
-      for (int i = tid; i < nplane / 2; i += blockDim.x) reinterpret_cast<uint32_t*>(S.plane)[i] = 0u;
-      if (tid == 0 && (nplane & 1)) S.plane[nplane - 1] = 0;
     } else {
-      for (int wi_ = tid; wi_ < kWinT * nw; wi_ += blockDim.x) {
-        uint32_t word = S.occ[wi_];
-        const int tt = wi_ / nw, p0 = (wi_ % nw) * 32;
-        while (word) {
-          const int b = __ffs(word) - 1;
-          word &= word - 1;
-          S.plane[tt * ps_stride + kPad + p0 + b] = 0;
-        }
-      }
+      // an unlisted window is dense: clear the whole plane, 16 bytes a store
+      // (balanced; with noise suppression occ's own rows no longer hold the digits)
+      const int n16 = nplane / 8;
+      for (int i = tid; i < n16; i += blockDim.x) reinterpret_cast<uint4*>(S.plane)[i] = make_uint4(0u, 0u, 0u, 0u);
+      for (int i = 8 * n16 + tid; i < nplane; i += blockDim.x) S.plane[i] = 0;
     }
   }
 }
