@@ -541,16 +541,11 @@ __device__ __forceinline__ bool ns_drop(const FindSmem& S, int ps_stride, int nw
   return false;
 }
 
-// Cluster of the peak at (tt, p): 5x5 window with the inner/outer rule, the
-// neighbourhood held in registers.
-__device__ __forceinline__ void make_cluster(const FindSmem& S, int ps_stride, int nw, int np, int T, int s, int r,
-                                             int f, int tt, int p, int xrow, uint4& rec, int4& xyz) {
-  const uint16_t* c = S.plane + tt * ps_stride + kPad + p;
-  int q[5][5];
-#pragma unroll
-  for (int dt = 0; dt < 5; dt++)
-#pragma unroll
-    for (int dp = 0; dp < 5; dp++) q[dt][dp] = c[(dt - 2) * ps_stride + dp - 2];
+// The record of the cluster of the peak at (tt, p) from its 5x5 charges
+// q[dt + 2][dp + 2] and whether another peak lies in the 5x5 (other): the
+// inner/outer rule, integer moments, packed 16-byte record and coordinates.
+__device__ __forceinline__ void cluster_record(const int (&q)[5][5], bool other, int np, int T, int s, int r, int f,
+                                               int tt, int p, int xrow, uint4& rec, int4& xyz) {
   int Q = 0, Sp = 0, St = 0, Spp = 0, Stt = 0;
   bool excl = false;
 #pragma unroll
@@ -568,13 +563,6 @@ __device__ __forceinline__ void make_cluster(const FindSmem& S, int ps_stride, i
       if (inc) { Q += v; Sp += v * dp; St += v * dt; Spp += v * dp * dp; Stt += v * dt * dt; }
     }
   }
-  uint32_t other = 0;
-#pragma unroll
-  for (int dt = -2; dt <= 2; dt++) {
-    uint32_t b = bits5(S.pk + (tt + dt) * nw, nw, p);
-    if (dt == 0) b &= ~4u;
-    other |= b;
-  }
   const int t_in = tt - kHalo;
   const int t = kFrag * f + t_in;
   const int pad_fp = 256 * p + floordiv32(512 * Sp + Q, 2 * Q);
@@ -589,6 +577,26 @@ __device__ __forceinline__ void make_cluster(const FindSmem& S, int ps_stride, i
   rec.z = (uint32_t)vp | ((uint32_t)vt << 8) | ((uint32_t)flags << 16) | ((uint32_t)r << 24);
   rec.w = (uint32_t)t | ((uint32_t)p << 16) | ((uint32_t)s << 24);
   xyz = make_int4(xrow, 2 * (pad_fp - 128 * (np - 1)), 5 * (32768 * f + time_fp - 512), t);
+}
+
+// Cluster of the peak at (tt, p) of the window in shared memory: the 5x5 from
+// the plane, the other peaks from the peak bitmap.
+__device__ __forceinline__ void make_cluster(const FindSmem& S, int ps_stride, int nw, int np, int T, int s, int r,
+                                             int f, int tt, int p, int xrow, uint4& rec, int4& xyz) {
+  const uint16_t* c = S.plane + tt * ps_stride + kPad + p;
+  int q[5][5];
+#pragma unroll
+  for (int dt = 0; dt < 5; dt++)
+#pragma unroll
+    for (int dp = 0; dp < 5; dp++) q[dt][dp] = c[(dt - 2) * ps_stride + dp - 2];
+  uint32_t other = 0;
+#pragma unroll
+  for (int dt = -2; dt <= 2; dt++) {
+    uint32_t b = bits5(S.pk + (tt + dt) * nw, nw, p);
+    if (dt == 0) b &= ~4u;
+    other |= b;
+  }
+  cluster_record(q, other != 0, np, T, s, r, f, tt, p, xrow, rec, xyz);
 }
 
 // L2 prefetch of the next window's input while the current one is being
@@ -723,8 +731,14 @@ k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
   // after the decode, and its three-page byte range is prefetched into L2
   // after the peak test.  In look-back mode a held window would stall every
   // successor's look-back: there the ticket is taken only at the top.
+  // windows of this kernel: all, or (with the light path) the heavy list
+  const unsigned long long n_heavy = (kScratch && W.heavy_list) ? W.ctr[CTR_NHEAVY] : 0ull;
+  auto window_of = [&](unsigned tk) -> unsigned {
+    if (!(kScratch && W.heavy_list)) return tk;
+    return (unsigned long long)tk < n_heavy ? W.heavy_list[tk] : n_windows;
+  };
   if (kScratch && tid == 0) {
-    const unsigned w0 = atomicAdd(&W.tickets[kMode == 2 ? TK_FIND2 : TK_FIND], 1u);
+    const unsigned w0 = window_of(atomicAdd(&W.tickets[kMode == 2 ? TK_FIND2 : TK_FIND], 1u));
     S.misc[1] = (int)w0;
     S.misc[2] = w0 < n_windows ? window_frs(G, w0) : 0;
     for (int k = 0; k < 4; k++) {
@@ -747,7 +761,7 @@ k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
     __syncthreads();
     const unsigned int w = (unsigned int)S.misc[1];
     if (w >= n_windows) break;
-    if (kScratch && tid == 0) nt = atomicAdd(&W.tickets[kMode == 2 ? TK_FIND2 : TK_FIND], 1u);
+    if (kScratch && tid == 0) nt = window_of(atomicAdd(&W.tickets[kMode == 2 ? TK_FIND2 : TK_FIND], 1u));
     if (!kScratch && tid == 0) {
       for (int k = 0; k < 4; k++) {
         const long long j = (long long)w - 1 + k;
@@ -1202,6 +1216,366 @@ k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Light windows.  Half of a full-TPC timeframe's windows hold at most a few
+// hundred digits (noise and the outer tracks), yet a window costs the block
+// finder about 10 k cycles of fixed latency (round trips, block barriers,
+// scans over its 74 KB plane).  Such a window (at most kLightDig digits and
+// runs with its halos) is given to one warp instead: its digits are decoded
+// straight from global memory into a per-warp sorted list, indexed by a
+// small open-addressing hash on (plane row, pad), and the peak test and the
+// 5x5 clusters look pixels up there.  The results are those of the block path
+// (the same rules, the same record builder).
+constexpr int kLightDig = 256;               // digits (and runs) of a light window, halos included
+constexpr int kLightWarps = 6;               // warps per light block
+constexpr int kLightBlocksPerSm = 4;
+constexpr int kLightOwn = 1408;              // bytes: a light window's own page (<= 256 entries, runs, digits)
+constexpr int kLightHalo = 896;              // bytes per neighbour's halo: entries | runs at 16 | ADC words at 528
+
+struct LightWarp {
+  uint4 own[kLightOwn / 16];    // the own page, staged
+  uint4 halo[2][kLightHalo / 16];   // the neighbours' halo entries / runs / ADC words, staged
+  uint16_t row0[kWinT + 2];     // first digit of each plane row (digits are sorted by row, pad)
+  uint16_t row1[kWinT + 2];     // one past its last
+  uint16_t dt[kLightDig];       // plane row of digit d (0..261)
+  uint16_t dq[kLightDig];       // its ADC value
+  uint8_t dp[kLightDig];        // its pad
+  uint8_t run_t[kLightDig];     // time bin (within its page) of run r
+  uint32_t pk[kLightDig / 32];  // digit d is a peak of step 2
+};
+
+// Digit index of pixel (row tt, pad p) of the warp's window, or -1: a short
+// scan of the row's digits (pads ascending).
+__device__ __forceinline__ int light_find(const LightWarp& L, int tt, int p, int np) {
+  if (p < 0 || p >= np || tt < 0 || tt >= kWinT) return -1;
+  const int e = L.row1[tt];
+  for (int i = L.row0[tt]; i < e; i++) {
+    const int pi = L.dp[i];
+    if (pi == p) return i;
+    if (pi > p) break;
+  }
+  return -1;
+}
+
+__device__ __forceinline__ int light_q(const LightWarp& L, int tt, int p, int np) {
+  const int i = light_find(L, tt, p, np);
+  return i < 0 ? 0 : (int)L.dq[i];
+}
+
+// One segment of a light window: a page's entries / runs / digits in a range.
+struct LightSeg {
+  const uint16_t* ent;   // its first entry
+  const uint16_t* run;   // its first run
+  const uint32_t* adc;   // the page's ADC words
+  int ne, nrun, ndig;    // counts in the segment
+  int dfirst;            // page digit index of the segment's first digit
+  int tt_base;           // plane row = t_in + tt_base
+  int t_base;            // absolute time bin = t_in + t_base
+};
+
+// Classify the windows: light (one warp) or block.  A window is light when its
+// own header and its neighbours' are valid and, halos included, it holds at
+// most kLightDig digits and runs.  Lists in arbitrary order (the window counts
+// and spans place the records canonically).
+__global__ void __launch_bounds__(256) k_find_classify(DevGeom G, DevWork W, unsigned int n_windows) {
+  const int lane = threadIdx.x & 31;
+  for (unsigned long long b = (blockIdx.x * (unsigned long long)blockDim.x) + (threadIdx.x & ~31u); b < n_windows;
+       b += (unsigned long long)gridDim.x * blockDim.x) {
+    const unsigned w = (unsigned)b + lane;
+    bool light = false;
+    if (w < n_windows) {
+      const int frs = window_frs(G, w);
+      const int f = frs & 0xffff, r = (frs >> 16) & 0xff, s = (frs >> 24) & 0xff;
+      PageHdr h, hp, hn;
+      const uint64_t o = W.page_offsets[w];
+      bool ok = parse_header(reinterpret_cast<const uint4*>(W.pages + (o <= W.pages_bytes ? o : 0)), o,
+                             W.pages_bytes, h) && h.sector == s && h.row == r && h.frag == f;
+      int nd = ok ? h.n_dig : 0, nr = ok ? h.n_runs : 0;
+      if (ok && f > 0) {
+        const uint64_t op = W.page_offsets[w - 1];
+        ok = parse_header(reinterpret_cast<const uint4*>(W.pages + (op <= W.pages_bytes ? op : 0)), op,
+                          W.pages_bytes, hp);
+        nd += ok ? hp.n_dig - hp.hi_dig : 0;
+        nr += ok ? hp.n_runs - hp.hi_runs : 0;
+      }
+      if (ok && f + 1 < G.n_frag) {
+        const uint64_t on = W.page_offsets[w + 1];
+        ok = parse_header(reinterpret_cast<const uint4*>(W.pages + (on <= W.pages_bytes ? on : 0)), on,
+                          W.pages_bytes, hn);
+        nd += ok ? hn.lo_dig : 0;
+        nr += ok ? hn.lo_runs : 0;
+      }
+      light = ok && nd <= kLightDig && nr <= kLightDig;
+    }
+    const bool valid = w < n_windows;
+    const uint32_t ml = __ballot_sync(0xffffffffu, valid && light), mh = __ballot_sync(0xffffffffu, valid && !light);
+    unsigned long long bl = 0, bh = 0;
+    if (lane == 0) {
+      if (ml) bl = atomicAdd(&W.ctr[CTR_NLIGHT], (unsigned long long)__popc(ml));
+      if (mh) bh = atomicAdd(&W.ctr[CTR_NHEAVY], (unsigned long long)__popc(mh));
+    }
+    bl = __shfl_sync(0xffffffffu, bl, 0);
+    bh = __shfl_sync(0xffffffffu, bh, 0);
+    const uint32_t lt = (1u << lane) - 1u;
+    if (valid && light) W.light_list[bl + __popc(ml & lt)] = w;
+    if (valid && !light) W.heavy_list[bh + __popc(mh & lt)] = w;
+  }
+}
+
+// Warp inclusive scan.
+__device__ __forceinline__ int warp_incl(int v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += y;
+  }
+  return v;
+}
+
+__global__ void __launch_bounds__(kLightWarps * 32, kLightBlocksPerSm)
+k_find_light(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
+  __shared__ LightWarp LS[kLightWarps];
+  LightWarp& L = LS[threadIdx.x >> 5];
+  const int lane = threadIdx.x & 31;
+  const unsigned long long n_light = W.ctr[CTR_NLIGHT];
+  const int T = G.n_time_bins;
+  // tickets one window ahead: the next window's pages are prefetched into L2
+  // while this one is processed
+  unsigned t = 0;
+  if (lane == 0) t = atomicAdd(&W.tickets[TK_LIGHT], 1u);
+  t = __shfl_sync(0xffffffffu, t, 0);
+  while (true) {
+    if ((unsigned long long)t >= n_light) break;
+    const unsigned w = W.light_list[t];
+    unsigned tn = 0;
+    if (lane == 0) {
+      tn = atomicAdd(&W.tickets[TK_LIGHT], 1u);
+      if ((unsigned long long)tn < n_light) {
+        const unsigned wn = W.light_list[tn];
+        const unsigned long long lo = W.page_offsets[wn > 0 ? wn - 1 : wn];
+        const unsigned long long hi = wn + 2 < n_windows ? W.page_offsets[wn + 2] : W.pages_bytes;
+        if (lo < hi && lo < W.pages_bytes && (lo & 15) == 0)
+          prefetch_l2(W.pages + lo, min(hi, (unsigned long long)W.pages_bytes) - lo);
+      }
+    }
+    t = __shfl_sync(0xffffffffu, tn, 0);
+    const int frs = window_frs(G, w);
+    const int f = frs & 0xffff, r = (frs >> 16) & 0xff, s = (frs >> 24) & 0xff;
+    const int np = G.npads[r];
+    // ---- the three segments, staged in one round trip: the own page whole,
+    // the neighbours' halo entries / runs / ADC words (headers valid: checked
+    // by the classification)
+    LightSeg sg[3];
+    bool bad = false;
+    {
+      PageHdr h, hp, hn;
+      const uint64_t o = W.page_offsets[w];
+      const uint64_t op = f > 0 ? W.page_offsets[w - 1] : 0ull;
+      const uint64_t on = f + 1 < G.n_frag ? W.page_offsets[w + 1] : 0ull;
+      parse_header(reinterpret_cast<const uint4*>(W.pages + o), o, W.pages_bytes, h);
+      if (f > 0) parse_header(reinterpret_cast<const uint4*>(W.pages + op), op, W.pages_bytes, hp);
+      if (f + 1 < G.n_frag) parse_header(reinterpret_cast<const uint4*>(W.pages + on), on, W.pages_bytes, hn);
+      if (h.len > (uint32_t)kLightOwn) bad = true;
+      const uint8_t* own = reinterpret_cast<const uint8_t*>(L.own);
+      const uint4* src = reinterpret_cast<const uint4*>(W.pages + o);
+      for (int i = lane; i < (int)(min(h.len, (uint32_t)kLightOwn) / 16); i += 32) L.own[i] = __ldg(src + i);
+      sg[1] = LightSeg{reinterpret_cast<const uint16_t*>(own + 32), reinterpret_cast<const uint16_t*>(own + 32 + 2 * h.n_tb),
+                       reinterpret_cast<const uint32_t*>(own + h.body), h.n_tb, h.n_runs, h.n_dig, 0, kHalo, kFrag * f};
+      sg[0] = LightSeg{nullptr, nullptr, nullptr, 0, 0, 0, 0, kHalo - kFrag, kFrag * (f - 1)};
+      sg[2] = LightSeg{nullptr, nullptr, nullptr, 0, 0, 0, 0, kHalo + kFrag, kFrag * (f + 1)};
+      uint16_t* hs0 = reinterpret_cast<uint16_t*>(L.halo[0]);
+      uint16_t* hs1 = reinterpret_cast<uint16_t*>(L.halo[1]);
+      if (f > 0) {
+        const uint32_t e0 = 32 + 2 * hp.hi_tb, e1 = 32 + 2 * hp.n_tb;
+        const uint32_t r0 = 32 + 2 * hp.n_tb + 2 * hp.hi_runs, r1 = 32 + 2 * hp.n_tb + 2 * hp.n_runs;
+        const uint32_t a0 = hp.body + 4 * (hp.hi_dig / 3), a1 = hp.body + 4 * ((hp.n_dig + 2) / 3);
+        if (e1 - e0 > 16 || r1 - r0 > 512 || a1 - a0 > kLightHalo - 528) bad = true;
+        if (!bad) {
+          copy_u16_warp(hs0, W.pages + op, e0, e1);
+          copy_u16_warp(hs0 + 8, W.pages + op, r0, r1);
+          copy_u16_warp(hs0 + 264, W.pages + op, a0, a1);
+        }
+        sg[0].ent = hs0; sg[0].run = hs0 + 8; sg[0].adc = reinterpret_cast<const uint32_t*>(hs0 + 264);
+        sg[0].ne = hp.n_tb - hp.hi_tb; sg[0].nrun = hp.n_runs - hp.hi_runs; sg[0].ndig = hp.n_dig - hp.hi_dig;
+        sg[0].dfirst = hp.hi_dig % 3;
+      }
+      if (f + 1 < G.n_frag) {
+        const uint32_t e1 = 32 + 2 * hn.lo_tb;
+        const uint32_t r0 = 32 + 2 * hn.n_tb, r1 = r0 + 2 * hn.lo_runs;
+        const uint32_t a0 = hn.body, a1 = hn.body + 4 * ((hn.lo_dig + 2) / 3);
+        if (e1 - 32 > 16 || r1 - r0 > 512 || a1 - a0 > kLightHalo - 528) bad = true;
+        if (!bad) {
+          copy_u16_warp(hs1, W.pages + on, 32, e1);
+          copy_u16_warp(hs1 + 8, W.pages + on, r0, r1);
+          copy_u16_warp(hs1 + 264, W.pages + on, a0, a1);
+        }
+        sg[2].ent = hs1; sg[2].run = hs1 + 8; sg[2].adc = reinterpret_cast<const uint32_t*>(hs1 + 264);
+        sg[2].ne = hn.lo_tb; sg[2].nrun = hn.lo_runs; sg[2].ndig = hn.lo_dig;
+      }
+      bad = __any_sync(0xffffffffu, bad);
+      __syncwarp();
+    }
+    const int ne = sg[0].ne + sg[1].ne + sg[2].ne;
+    const int nrun = sg[0].nrun + sg[1].nrun + sg[2].nrun;
+    const int ndig = sg[0].ndig + sg[1].ndig + sg[2].ndig;
+    bad = bad || nrun > kLightDig || ndig > kLightDig;
+    for (int i = lane; i < kWinT + 2; i += 32) { L.row0[i] = 0; L.row1[i] = 0; }
+    // ---- entries: run counts -> each run's time bin
+    {
+      int carry = 0, cnt[3] = {0, 0, 0};
+      for (int c0 = 0; c0 < ne && !bad; c0 += 32) {
+        const int e = c0 + lane;
+        int nr = 0, t_in = 0, k = 0;
+        if (e < ne) {
+          k = e < sg[0].ne ? 0 : (e < sg[0].ne + sg[1].ne ? 1 : 2);
+          const int el = e - (k == 0 ? 0 : (k == 1 ? sg[0].ne : sg[0].ne + sg[1].ne));
+          const LightSeg& g = sg[k];
+          const uint32_t v = g.ent[el];
+          t_in = (int)(v & 0xffu);
+          nr = (int)(v >> 8);
+          const int tt = t_in + g.tt_base;
+          if (nr < 1 || tt < 0 || tt >= kWinT || g.t_base + t_in >= T) bad = true;
+          if (el > 0 && (int)(g.ent[el - 1] & 0xffu) >= t_in) bad = true;
+        }
+        const int incl = warp_incl(nr);
+        int r0 = carry + incl - nr;
+        for (int q = 0; q < nr; q++)
+          if (r0 + q < kLightDig) L.run_t[r0 + q] = (uint8_t)t_in;
+#pragma unroll
+        for (int kk = 0; kk < 3; kk++) cnt[kk] += __reduce_add_sync(0xffffffffu, (e < ne && k == kk) ? nr : 0);
+        carry += __shfl_sync(0xffffffffu, incl, 31);
+        bad = __any_sync(0xffffffffu, bad);
+      }
+      // every segment's entries list exactly its runs
+      if (cnt[0] != sg[0].nrun || cnt[1] != sg[1].nrun || cnt[2] != sg[2].nrun) bad = true;
+    }
+    __syncwarp();
+    // ---- runs: digit offsets -> each digit's pixel
+    if (!bad) {
+      int carry = 0, cnt[3] = {0, 0, 0};
+      for (int c0 = 0; c0 < nrun && !bad; c0 += 32) {
+        const int rr = c0 + lane;
+        int len = 0, ps = 0, k = 0;
+        if (rr < nrun) {
+          k = rr < sg[0].nrun ? 0 : (rr < sg[0].nrun + sg[1].nrun ? 1 : 2);
+          const int rl = rr - (k == 0 ? 0 : (k == 1 ? sg[0].nrun : sg[0].nrun + sg[1].nrun));
+          const LightSeg& g = sg[k];
+          const uint32_t rv = g.run[rl];
+          ps = (int)(rv & 0xffu);
+          len = (int)(rv >> 8);
+          if (len < 1 || ps + len > np) bad = true;
+          if (rl > 0 && L.run_t[rr - 1] == L.run_t[rr]) {   // same time bin: ascending, disjoint
+            const uint32_t pv = g.run[rl - 1];
+            if (ps < (int)(pv & 0xffu) + (int)(pv >> 8)) bad = true;
+          }
+        }
+        const int incl = warp_incl(len);
+        const int d0 = carry + incl - len;
+        if (!bad && rr < nrun) {
+          const int tt = (int)L.run_t[rr] + sg[k].tt_base;
+          for (int q = 0; q < len; q++)
+            if (d0 + q < kLightDig) {
+              L.dt[d0 + q] = (uint16_t)tt;
+              L.dp[d0 + q] = (uint8_t)(ps + q);
+            }
+        }
+#pragma unroll
+        for (int kk = 0; kk < 3; kk++) cnt[kk] += __reduce_add_sync(0xffffffffu, (rr < nrun && k == kk) ? len : 0);
+        carry += __shfl_sync(0xffffffffu, incl, 31);
+        bad = __any_sync(0xffffffffu, bad);
+      }
+      if (cnt[0] != sg[0].ndig || cnt[1] != sg[1].ndig || cnt[2] != sg[2].ndig) bad = true;
+    }
+    __syncwarp();
+    // ---- digits: ADC values, row bounds (digits sorted by row, then pad:
+    // segments in time order, entries ascending in time, runs of a time bin
+    // ascending and disjoint, as checked above)
+    if (!bad) {
+      for (int d = lane; d < ndig; d += 32) {
+        const int k = d < sg[0].ndig ? 0 : (d < sg[0].ndig + sg[1].ndig ? 1 : 2);
+        const int dl = d - (k == 0 ? 0 : (k == 1 ? sg[0].ndig : sg[0].ndig + sg[1].ndig));
+        const int idx = sg[k].dfirst + dl;
+        const uint32_t word = sg[k].adc[idx / 3];
+        L.dq[d] = (uint16_t)((word >> (10 * (idx % 3))) & 1023u);
+        const int tt = L.dt[d];
+        if (d == 0 || L.dt[d - 1] != tt) L.row0[tt] = (uint16_t)d;
+        if (d == ndig - 1 || L.dt[d + 1] != tt) L.row1[tt] = (uint16_t)(d + 1);
+      }
+    }
+    __syncwarp();
+    if (bad) {
+      if (lane == 0) {
+        atomicOr(W.err, kErrCorrupt);
+        W.win_cnt[w] = 0ull;
+        W.win_soff[w] = 0u;
+      }
+      __syncwarp();
+      continue;
+    }
+    // ---- step 2: peaks (rows 1..260), one digit a lane
+    for (int c0 = 0; c0 < ndig; c0 += 32) {
+      const int d = c0 + lane;
+      bool pkf = false;
+      if (d < ndig) {
+        const int tt = L.dt[d], p = L.dp[d], q = L.dq[d];
+        if (tt >= 1 && tt <= kWinT - 2 && q >= P.q_peak_min) {
+          const int lo = max(max(light_q(L, tt - 1, p - 1, np), light_q(L, tt - 1, p, np)),
+                             max(light_q(L, tt - 1, p + 1, np), light_q(L, tt, p - 1, np)));
+          const int hi = max(max(light_q(L, tt, p + 1, np), light_q(L, tt + 1, p - 1, np)),
+                             max(light_q(L, tt + 1, p, np), light_q(L, tt + 1, p + 1, np)));
+          pkf = q > lo && q >= hi;
+        }
+      }
+      const uint32_t m = __ballot_sync(0xffffffffu, pkf);
+      if (lane == 0) L.pk[c0 >> 5] = m;
+    }
+    __syncwarp();
+    // ---- steps 3-4: the own peaks (rows 3..258) in canonical order
+    int npk = 0;
+    for (int c0 = 0; c0 < ndig; c0 += 32) {
+      const int d = c0 + lane;
+      const bool own = d < ndig && ((L.pk[c0 >> 5] >> lane) & 1u) && L.dt[d] >= kHalo && L.dt[d] < kHalo + kFrag;
+      npk += __popc(__ballot_sync(0xffffffffu, own));
+    }
+    unsigned long long so = 0;
+    if (lane == 0) {
+      so = npk ? atomicAdd(&W.ctr[CTR_SCURSOR], (unsigned long long)npk) : 0ull;
+      if (so + npk > W.cap_cl) atomicOr(W.err, kErrOverflowCl);
+      W.win_cnt[w] = (unsigned long long)npk;
+      W.win_soff[w] = (uint32_t)min(so, (unsigned long long)W.cap_cl);
+    }
+    so = __shfl_sync(0xffffffffu, so, 0);
+    int rank0 = 0;
+    for (int c0 = 0; c0 < ndig && npk; c0 += 32) {
+      const int d = c0 + lane;
+      const bool own = d < ndig && ((L.pk[c0 >> 5] >> lane) & 1u) && L.dt[d] >= kHalo && L.dt[d] < kHalo + kFrag;
+      const uint32_t m = __ballot_sync(0xffffffffu, own);
+      if (own) {
+        const int tt = L.dt[d], p = L.dp[d];
+        int q[5][5];
+        bool other = false;
+#pragma unroll
+        for (int a = 0; a < 5; a++)
+#pragma unroll
+          for (int b = 0; b < 5; b++) {
+            if (a == 2 && b == 2) { q[a][b] = L.dq[d]; continue; }
+            const int i = light_find(L, tt + a - 2, p + b - 2, np);
+            q[a][b] = i < 0 ? 0 : (int)L.dq[i];
+            if (i >= 0 && ((L.pk[i >> 5] >> (i & 31)) & 1u)) other = true;
+          }
+        uint4 rec;
+        int4 xyz;
+        cluster_record(q, other, np, T, s, r, f, tt, p, G.xrow[r], rec, xyz);
+        const unsigned long long idx = so + rank0 + __popc(m & ((1u << lane) - 1u));
+        if (idx < W.cap_cl) reinterpret_cast<uint4*>(W.scratch_cl)[idx] = rec;
+      }
+      rank0 += __popc(m);
+    }
+    __syncwarp();
+  }
+}
+
 // Places every window's scratch span at its canonical offset (win_cnt holds the
 // exclusive scan of the window counts; the total is in ctr[CTR_NCL]) and
 // derives the (X, Y, Z, t_peak) arrays and the row starts.  One warp per window.
@@ -1284,24 +1658,45 @@ static void launch_find_mode(const DevGeom& G, const DevParams& P, const DevWork
 }
 
 cudaError_t launch_find(const DevGeom& G, const DevParams& P, const DevWork& W, unsigned int n_windows,
-                        int n_sm, const LaunchCfg& L, cudaStream_t st, unsigned long long* win_scan_state,
-                        int* launches) {
+                        int n_sm, const LaunchCfg& L, cudaStream_t st, cudaStream_t aux, cudaEvent_t ev_fork,
+                        cudaEvent_t ev_join, unsigned long long* win_scan_state, int* launches) {
   const size_t sm = find_smem_bytes(G.npmax, G.nw);
   // persistent CTAs: find_ctas_per_sm per SM (at most 2 fit the shared memory)
   unsigned int grid = (unsigned int)min((long long)n_windows, (long long)n_sm * L.find_ctas_per_sm);
   if (grid == 0) grid = 1;
   // step 2b (noise suppression) compiled in only where it is switched on
   const bool ns = P.ns_min_dip > 0;
+  // light windows to one warp each (fused finder without noise suppression)
+  const bool light = W.light_list && W.heavy_list && !W.dense && !ns;
+  DevWork Wh = W;
+  if (!light) Wh.light_list = Wh.heavy_list = nullptr;
+  if (light) {
+    // the light windows on a second stream, beside the block finder: whichever
+    // kernel's blocks retire first leaves its SMs to the other
+    unsigned gc = (unsigned)min((n_windows + 255ull) / 256ull, (unsigned long long)n_sm * 8);
+    k_find_classify<<<gc ? gc : 1, 256, 0, st>>>(G, W, n_windows);
+    cudaError_t e0 = cudaEventRecord(ev_fork, st);
+    if (e0 == cudaSuccess) e0 = cudaStreamWaitEvent(aux, ev_fork, 0);
+    if (e0 != cudaSuccess) return e0;
+    k_find_light<<<(unsigned)(n_sm * kLightBlocksPerSm), kLightWarps * 32, 0, aux>>>(G, P, W, n_windows);
+    e0 = cudaEventRecord(ev_join, aux);
+    if (e0 != cudaSuccess) return e0;
+    *launches += 2;
+  }
   if (W.dense) {
     // dense-plane variant: decode every window into the plane, then find
-    launch_find_mode<1, false>(G, P, W, n_windows, grid, L.find_threads, sm, st);
-    if (ns) launch_find_mode<2, true>(G, P, W, n_windows, grid, L.find_threads, sm, st);
-    else launch_find_mode<2, false>(G, P, W, n_windows, grid, L.find_threads, sm, st);
+    launch_find_mode<1, false>(G, P, Wh, n_windows, grid, L.find_threads, sm, st);
+    if (ns) launch_find_mode<2, true>(G, P, Wh, n_windows, grid, L.find_threads, sm, st);
+    else launch_find_mode<2, false>(G, P, Wh, n_windows, grid, L.find_threads, sm, st);
     *launches += 1;
   } else if (ns) {
-    launch_find_mode<0, true>(G, P, W, n_windows, grid, L.find_threads, sm, st);
+    launch_find_mode<0, true>(G, P, Wh, n_windows, grid, L.find_threads, sm, st);
   } else {
-    launch_find_mode<0, false>(G, P, W, n_windows, grid, L.find_threads, sm, st);
+    launch_find_mode<0, false>(G, P, Wh, n_windows, grid, L.find_threads, sm, st);
+  }
+  if (light) {
+    const cudaError_t e1 = cudaStreamWaitEvent(st, ev_join, 0);
+    if (e1 != cudaSuccess) return e1;
   }
   cudaError_t e = launch_scan(reinterpret_cast<uint64_t*>(W.win_cnt), W.ctr + CTR_NWIN, n_windows, win_scan_state,
                               W.tickets + TK_SCAN_W, W.ctr + CTR_NCL, W.err, n_sm, st);

@@ -22,7 +22,7 @@
 namespace tpc {
 size_t find_smem_bytes(int npmax, int nw);
 cudaError_t launch_find(const DevGeom&, const DevParams&, const DevWork&, unsigned int, int, const LaunchCfg&,
-                        cudaStream_t, unsigned long long*, int*);
+                        cudaStream_t, cudaStream_t, cudaEvent_t, cudaEvent_t, unsigned long long*, int*);
 cudaError_t launch_ca(const DevGeom&, const DevParams&, const DevWork&, int, const LaunchCfg&, cudaStream_t, int*);
 cudaError_t launch_merge(const DevGeom&, const DevParams&, const DevWork&, int, const LaunchCfg&, cudaStream_t,
                          unsigned long long*, int*);
@@ -64,6 +64,8 @@ struct Slot {
   bool own_stream = false;
   cudaEvent_t ev_stage[TPC_N_STAGES + 1] = {};
   cudaEvent_t ev_done = nullptr, ev_input = nullptr;
+  cudaStream_t aux = nullptr;                         // second stream of the finder (light windows)
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   // device buffers
   Buf pages, offsets, winstate, cl, clx, cly, clz, clt, rowstart, chrow, up, down, score, edge, jump, chlen, scanv,
       scanst, chainof, clchain, ch_i32, besta, bestb, trk_i32, trackcl, cl2trk, tracks, ctrl, scratch, wincnt, winsoff,
@@ -213,7 +215,7 @@ static cudaError_t ensure(Buf& b, size_t bytes) {
 
 static size_t slot_bytes(uint64_t pages, uint64_t windows, uint64_t cap_cl, uint64_t cap_ch, int nsr,
                          size_t dense = 0) {
-  size_t b = dense + pages + 16 + windows * 28 + cap_cl * (16 + 16 + 16 + 8 + 8 + 8 + 8 + 4 + 8 + 4 + 4 + 4 + 4) +
+  size_t b = dense + pages + 16 + windows * 36 + cap_cl * (16 + 16 + 16 + 8 + 8 + 8 + 8 + 4 + 8 + 4 + 4 + 4 + 4) +
              (scan_tiles(cap_cl) + scan_tiles(cap_ch) + scan_tiles(windows)) * 8 +
              cap_ch * (14 * 4 + 8 + 16 + sizeof(tpc_track) + 4 * 12) +
              (size_t)(nsr + 1) * 8 + 1024;
@@ -240,7 +242,7 @@ static tpc_status slot_reserve(tpc_context* ctx, Slot& s, uint64_t pages_bytes, 
     CUDA_TRY(ensure(s.offsets, windows * 8));
     CUDA_TRY(ensure(s.winstate, windows * 8));
     CUDA_TRY(ensure(s.wincnt, windows * 8));
-    CUDA_TRY(ensure(s.winsoff, windows * 4));
+    CUDA_TRY(ensure(s.winsoff, windows * 12));   // span starts | light list | heavy list
     s.cap_windows = windows;
   }
   if (cap_cl > s.cap_cl) {
@@ -284,6 +286,8 @@ static tpc_status slot_reserve(tpc_context* ctx, Slot& s, uint64_t pages_bytes, 
   W.scratch_cl = (tpc_cluster*)s.scratch.p;
   W.win_cnt = (unsigned long long*)s.wincnt.p;
   W.win_soff = (uint32_t*)s.winsoff.p;
+  W.light_list = (uint32_t*)s.winsoff.p + s.cap_windows;
+  W.heavy_list = (uint32_t*)s.winsoff.p + 2 * s.cap_windows;
   W.up = (int32_t*)s.up.p; W.down = (int32_t*)s.down.p;
   W.score = (int64_t*)s.score.p;
   W.edge_key = (unsigned long long*)s.edge.p;
@@ -327,6 +331,9 @@ static void slot_free(tpc_context* ctx, Slot& s) {
   for (auto& e : s.ev_stage) if (e) cudaEventDestroy(e);
   if (s.ev_done) cudaEventDestroy(s.ev_done);
   if (s.ev_input) cudaEventDestroy(s.ev_input);
+  if (s.ev_fork) cudaEventDestroy(s.ev_fork);
+  if (s.ev_join) cudaEventDestroy(s.ev_join);
+  if (s.aux) cudaStreamDestroy(s.aux);
   if (s.gexec) cudaGraphExecDestroy(s.gexec);
   if (s.own_stream && s.stream) cudaStreamDestroy(s.stream);
   if (s.h_ctrl) cudaFreeHost(s.h_ctrl);
@@ -388,6 +395,9 @@ extern "C" tpc_status tpc_create_context(const tpc_geometry* geom, const tpc_par
     for (auto& ev : s.ev_stage) if (e == cudaSuccess) e = cudaEventCreate(&ev);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.ev_done, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.ev_input, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s.aux, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.ev_join, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&s.h_ctrl, 256);
     if (e != cudaSuccess) {
       for (auto& s2 : ctx->slots) slot_free(ctx, s2);
@@ -462,7 +472,8 @@ static tpc_status enqueue_body(tpc_context* ctx, Slot& s, bool capturing) {
   CUDA_TRY(cudaMemsetAsync(W.scan_state, 0, (tiles_a + tiles_b + scan_tiles(s.n_windows)) * 8, st));
   if (timing) CUDA_TRY(cudaEventRecordWithFlags(s.ev_stage[0], st, evf));
   const LaunchCfg& L = ctx->L;
-  CUDA_TRY(launch_find(G, ctx->P, W, s.n_windows, ctx->n_sm, L, st, W.scan_state + tiles_a + tiles_b, &s.launches));
+  CUDA_TRY(launch_find(G, ctx->P, W, s.n_windows, ctx->n_sm, L, st, s.aux, s.ev_fork, s.ev_join,
+                       W.scan_state + tiles_a + tiles_b, &s.launches));
   if (timing) CUDA_TRY(cudaEventRecordWithFlags(s.ev_stage[1], st, evf));
   CUDA_TRY(launch_ca(G, ctx->P, W, ctx->n_sm, L, st, &s.launches));
   if (timing) CUDA_TRY(cudaEventRecordWithFlags(s.ev_stage[2], st, evf));

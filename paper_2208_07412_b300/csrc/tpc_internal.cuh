@@ -91,6 +91,8 @@ struct DevWork {
   tpc_cluster* scratch_cl;       // finder output, window spans in completion order
   unsigned long long* win_cnt;   // clusters per window, scanned in place to canonical bases
   uint32_t* win_soff;            // start of each window's span in scratch_cl
+  uint32_t* light_list;          // [n_windows] windows of the light path (first CTR_NLIGHT), or null
+  uint32_t* heavy_list;          // [n_windows] the other windows (first CTR_NHEAVY)
   // CA
   int32_t* up; int32_t* down;
   int64_t* score;
@@ -139,9 +141,11 @@ enum {
   CTR_SCURSOR = 21,   // next free scratch record of the finder
   CTR_NWIN = 22,      // windows of the timeframe
   CTR_NCAND = 23,     // merge candidate pairs found
-  CTR_COUNT = 24
+  CTR_NLIGHT = 24,    // windows the light finder path takes
+  CTR_NHEAVY = 25,    // windows the block-per-window finder takes
+  CTR_COUNT = 26
 };
-enum { TK_FIND = 0, TK_SCAN_A = 1, TK_SCAN_B = 2, TK_SCAN_W = 3, TK_FIND2 = 4, kNumTickets = 5 };
+enum { TK_FIND = 0, TK_SCAN_A = 1, TK_SCAN_B = 2, TK_SCAN_W = 3, TK_FIND2 = 4, TK_LIGHT = 5, kNumTickets = 6 };
 
 // ------------------------------------------------------------------ helpers
 __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
