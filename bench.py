@@ -46,13 +46,14 @@ WORKLOADS = {
                          "floor(15000 U^7.82) (mean ~1,700), 5% loopers, same charge/noise/ZS model"),
 }
 REF_SAMPLE_BYTES = 20 << 20
-# DRAM bytes (read + write) of one k_find_clusters launch, from an ncu capture of
-# the current kernel on the workload (seed 1); None where no capture exists.
-# Must be reset to None whenever the finder kernel changes.
-FINDER_DRAM_BYTES = {}
-# Warp instructions (smsp__inst_executed.sum) of the same launch, for the issue
+# DRAM bytes (read + write) of one finder stage (k_find_classify, k_find_light
+# and k_find_clusters, summed), from an ncu capture of the current kernels on the
+# workload (seed 1); absent where no capture exists.  Must be cleared whenever a
+# finder kernel changes.
+FINDER_DRAM_BYTES = {"full_tpc": 87_106_304 + 2_334_720}
+# Warp instructions (smsp__inst_executed.sum) of the same kernels, for the issue
 # roofline; reset together with FINDER_DRAM_BYTES.
-FINDER_WARP_INSTR = {}
+FINDER_WARP_INSTR = {"full_tpc": 484_925_296}
 # Warp-instruction issue peak: 148 SMs x 4 schedulers x 1 instruction per cycle
 # at the 2032 MHz maximum SM clock.
 ISSUE_PEAK = 148 * 4 * 2.032e9
@@ -749,7 +750,8 @@ def run_ours(args, world, rank, local):
             "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
             "stages_ms": stages,
             "wall_ms_per_step": 1e3 * wall / args.steps,
-            "roofline": {"kernel": "k_find_clusters", "bound": "hbm", "achieved": achieved, "peak": hbm,
+            "roofline": {"kernel": "find stage: k_find_classify + k_find_light + k_find_clusters",
+                         "bound": "hbm", "achieved": achieved, "peak": hbm,
                          "unit": "GB/s", "frac": achieved / hbm,
                          "traffic": (FINDER_DRAM_BYTES.get(args.workload)
                                      if args.seed == 1 and not args.time_bins and not args.dense_finder else None),
@@ -757,7 +759,8 @@ def run_ours(args, world, rank, local):
                          "algorithmic_bytes_per_launch": int(alg_bytes)},
             "roofline_issue": (None if not (args.seed == 1 and not args.time_bins and not args.dense_finder
                                             and args.workload in FINDER_WARP_INSTR) else
-                               {"kernel": "k_find_clusters", "bound": "issue",
+                               {"kernel": "find stage: k_find_classify + k_find_light + k_find_clusters",
+                                "bound": "issue",
                                 "achieved": FINDER_WARP_INSTR[args.workload] / (stages["find"] * 1e-3),
                                 "peak": ISSUE_PEAK, "unit": "warp-instr/s",
                                 "frac": FINDER_WARP_INSTR[args.workload] / (stages["find"] * 1e-3) / ISSUE_PEAK,

@@ -1226,11 +1226,14 @@ k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
 // small open-addressing hash on (plane row, pad), and the peak test and the
 // 5x5 clusters look pixels up there.  The results are those of the block path
 // (the same rules, the same record builder).
-constexpr int kLightDig = 256;               // digits (and runs) of a light window, halos included
+constexpr int kLightDig = 256;               // digits (and runs) of a light window, halos included (512: slower)
 constexpr int kLightWarps = 6;               // warps per light block
 constexpr int kLightBlocksPerSm = 4;
-constexpr int kLightOwn = 1408;              // bytes: a light window's own page (<= 256 entries, runs, digits)
-constexpr int kLightHalo = 896;              // bytes per neighbour's halo: entries | runs at 16 | ADC words at 528
+// a light window's own page: header, <= 256 entries, <= kLightDig runs and digits
+constexpr int kLightOwn = (32 + 2 * 256 + 2 * kLightDig + 4 * ((kLightDig + 2) / 3) + 15) / 16 * 16;
+// a neighbour's halo: <= 3 entries | runs at byte 16 | ADC words at kHaloAdcAt
+constexpr int kHaloAdcAt = 16 + 2 * kLightDig;
+constexpr int kLightHalo = (kHaloAdcAt + 4 * (kLightDig / 3 + 2) + 15) / 16 * 16;
 
 struct LightWarp {
   uint4 own[kLightOwn / 16];    // the own page, staged
@@ -1340,7 +1343,7 @@ k_find_light(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
   const int lane = threadIdx.x & 31;
   const unsigned long long n_light = W.ctr[CTR_NLIGHT];
   const int T = G.n_time_bins;
-  // tickets one window ahead: the next window's pages are prefetched into L2
+  // tickets one window ahead: the next window's page is prefetched into L2
   // while this one is processed
   unsigned t = 0;
   if (lane == 0) t = atomicAdd(&W.tickets[TK_LIGHT], 1u);
@@ -1352,9 +1355,9 @@ k_find_light(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
     if (lane == 0) {
       tn = atomicAdd(&W.tickets[TK_LIGHT], 1u);
       if ((unsigned long long)tn < n_light) {
-        const unsigned wn = W.light_list[tn];
-        const unsigned long long lo = W.page_offsets[wn > 0 ? wn - 1 : wn];
-        const unsigned long long hi = wn + 2 < n_windows ? W.page_offsets[wn + 2] : W.pages_bytes;
+        const unsigned wn = W.light_list[tn];   // its own page (the halos are a few bytes)
+        const unsigned long long lo = W.page_offsets[wn];
+        const unsigned long long hi = wn + 1 < n_windows ? W.page_offsets[wn + 1] : W.pages_bytes;
         if (lo < hi && lo < W.pages_bytes && (lo & 15) == 0)
           prefetch_l2(W.pages + lo, min(hi, (unsigned long long)W.pages_bytes) - lo);
       }
@@ -1390,13 +1393,13 @@ k_find_light(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
         const uint32_t e0 = 32 + 2 * hp.hi_tb, e1 = 32 + 2 * hp.n_tb;
         const uint32_t r0 = 32 + 2 * hp.n_tb + 2 * hp.hi_runs, r1 = 32 + 2 * hp.n_tb + 2 * hp.n_runs;
         const uint32_t a0 = hp.body + 4 * (hp.hi_dig / 3), a1 = hp.body + 4 * ((hp.n_dig + 2) / 3);
-        if (e1 - e0 > 16 || r1 - r0 > 512 || a1 - a0 > kLightHalo - 528) bad = true;
+        if (e1 - e0 > 16 || r1 - r0 > 2 * kLightDig || a1 - a0 > kLightHalo - kHaloAdcAt) bad = true;
         if (!bad) {
           copy_u16_warp(hs0, W.pages + op, e0, e1);
           copy_u16_warp(hs0 + 8, W.pages + op, r0, r1);
-          copy_u16_warp(hs0 + 264, W.pages + op, a0, a1);
+          copy_u16_warp(hs0 + kHaloAdcAt / 2, W.pages + op, a0, a1);
         }
-        sg[0].ent = hs0; sg[0].run = hs0 + 8; sg[0].adc = reinterpret_cast<const uint32_t*>(hs0 + 264);
+        sg[0].ent = hs0; sg[0].run = hs0 + 8; sg[0].adc = reinterpret_cast<const uint32_t*>(hs0 + kHaloAdcAt / 2);
         sg[0].ne = hp.n_tb - hp.hi_tb; sg[0].nrun = hp.n_runs - hp.hi_runs; sg[0].ndig = hp.n_dig - hp.hi_dig;
         sg[0].dfirst = hp.hi_dig % 3;
       }
@@ -1404,13 +1407,13 @@ k_find_light(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
         const uint32_t e1 = 32 + 2 * hn.lo_tb;
         const uint32_t r0 = 32 + 2 * hn.n_tb, r1 = r0 + 2 * hn.lo_runs;
         const uint32_t a0 = hn.body, a1 = hn.body + 4 * ((hn.lo_dig + 2) / 3);
-        if (e1 - 32 > 16 || r1 - r0 > 512 || a1 - a0 > kLightHalo - 528) bad = true;
+        if (e1 - 32 > 16 || r1 - r0 > 2 * kLightDig || a1 - a0 > kLightHalo - kHaloAdcAt) bad = true;
         if (!bad) {
           copy_u16_warp(hs1, W.pages + on, 32, e1);
           copy_u16_warp(hs1 + 8, W.pages + on, r0, r1);
-          copy_u16_warp(hs1 + 264, W.pages + on, a0, a1);
+          copy_u16_warp(hs1 + kHaloAdcAt / 2, W.pages + on, a0, a1);
         }
-        sg[2].ent = hs1; sg[2].run = hs1 + 8; sg[2].adc = reinterpret_cast<const uint32_t*>(hs1 + 264);
+        sg[2].ent = hs1; sg[2].run = hs1 + 8; sg[2].adc = reinterpret_cast<const uint32_t*>(hs1 + kHaloAdcAt / 2);
         sg[2].ne = hn.lo_tb; sg[2].nrun = hn.lo_runs; sg[2].ndig = hn.lo_dig;
       }
       bad = __any_sync(0xffffffffu, bad);
