@@ -1229,6 +1229,7 @@ k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
 constexpr int kLightDig = 256;               // digits (and runs) of a light window, halos included (512: slower)
 constexpr int kLightWarps = 6;               // warps per light block
 constexpr int kLightBlocksPerSm = 4;
+constexpr unsigned kLightMinWindows = 4096;  // smaller timeframes: block finder only
 // a light window's own page: header, <= 256 entries, <= kLightDig runs and digits
 constexpr int kLightOwn = (32 + 2 * 256 + 2 * kLightDig + 4 * ((kLightDig + 2) / 3) + 15) / 16 * 16;
 // a neighbour's halo: <= 3 entries | runs at byte 16 | ADC words at kHaloAdcAt
@@ -1669,8 +1670,10 @@ cudaError_t launch_find(const DevGeom& G, const DevParams& P, const DevWork& W, 
   if (grid == 0) grid = 1;
   // step 2b (noise suppression) compiled in only where it is switched on
   const bool ns = P.ns_min_dip > 0;
-  // light windows to one warp each (fused finder without noise suppression)
-  const bool light = W.light_list && W.heavy_list && !W.dense && !ns;
+  // light windows to one warp each (fused finder without noise suppression),
+  // on timeframes large enough that the light kernel's per-window latency
+  // hides behind the block finder (a single sector gets slower with it)
+  const bool light = W.light_list && W.heavy_list && !W.dense && !ns && n_windows >= kLightMinWindows;
   DevWork Wh = W;
   if (!light) Wh.light_list = Wh.heavy_list = nullptr;
   if (light) {
