@@ -1246,6 +1246,7 @@ struct LightWarp {
   uint8_t dp[kLightDig];        // its pad
   uint8_t run_t[kLightDig];     // time bin (within its page) of run r
   uint32_t pk[kLightDig / 32];  // digit d is a peak of step 2
+  uint32_t sv[kLightDig / 32];  // ... and survives step 2b (the clusters)
 };
 
 // Digit index of pixel (row tt, pad p) of the warp's window, or -1: a short
@@ -1535,11 +1536,34 @@ k_find_light(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
       if (lane == 0) L.pk[c0 >> 5] = m;
     }
     __syncwarp();
-    // ---- steps 3-4: the own peaks (rows 3..258) in canonical order
+    // ---- step 2b (noise suppression, optional): an own peak with a greater
+    // step-2 peak on its 5x5 ring and a shallow dip towards it is dropped
+    for (int c0 = 0; c0 < ndig; c0 += 32) {
+      const int d = c0 + lane;
+      bool keep = d < ndig && ((L.pk[c0 >> 5] >> lane) & 1u);
+      if (keep && P.ns_min_dip > 0 && L.dt[d] >= kHalo && L.dt[d] < kHalo + kFrag) {
+        const int tt = L.dt[d], p = L.dp[d], qc = L.dq[d];
+        for (int dtt = -2; dtt <= 2 && keep; dtt++)
+          for (int dpp = -2; dpp <= 2 && keep; dpp++) {
+            if (dtt > -2 && dtt < 2 && dpp > -2 && dpp < 2) continue;   // the ring only
+            const int i = light_find(L, tt + dtt, p + dpp, np);
+            if (i < 0 || !((L.pk[i >> 5] >> (i & 31)) & 1u)) continue;
+            const int qn = L.dq[i];
+            // greater key: more charge, or equal charge and a lower (t, p) index
+            if (qn < qc || (qn == qc && (dtt > 0 || (dtt == 0 && dpp > 0)))) continue;
+            const int it = dtt > 0 ? 1 : (dtt < 0 ? -1 : 0), ip = dpp > 0 ? 1 : (dpp < 0 ? -1 : 0);
+            if (qc - light_q(L, tt + it, p + ip, np) < P.ns_min_dip) keep = false;
+          }
+      }
+      const uint32_t m = __ballot_sync(0xffffffffu, keep);
+      if (lane == 0) L.sv[c0 >> 5] = m;
+    }
+    __syncwarp();
+    // ---- steps 3-4: the own surviving peaks (rows 3..258) in canonical order
     int npk = 0;
     for (int c0 = 0; c0 < ndig; c0 += 32) {
       const int d = c0 + lane;
-      const bool own = d < ndig && ((L.pk[c0 >> 5] >> lane) & 1u) && L.dt[d] >= kHalo && L.dt[d] < kHalo + kFrag;
+      const bool own = d < ndig && ((L.sv[c0 >> 5] >> lane) & 1u) && L.dt[d] >= kHalo && L.dt[d] < kHalo + kFrag;
       npk += __popc(__ballot_sync(0xffffffffu, own));
     }
     unsigned long long so = 0;
@@ -1553,7 +1577,7 @@ k_find_light(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
     int rank0 = 0;
     for (int c0 = 0; c0 < ndig && npk; c0 += 32) {
       const int d = c0 + lane;
-      const bool own = d < ndig && ((L.pk[c0 >> 5] >> lane) & 1u) && L.dt[d] >= kHalo && L.dt[d] < kHalo + kFrag;
+      const bool own = d < ndig && ((L.sv[c0 >> 5] >> lane) & 1u) && L.dt[d] >= kHalo && L.dt[d] < kHalo + kFrag;
       const uint32_t m = __ballot_sync(0xffffffffu, own);
       if (own) {
         const int tt = L.dt[d], p = L.dp[d];
@@ -1670,10 +1694,10 @@ cudaError_t launch_find(const DevGeom& G, const DevParams& P, const DevWork& W, 
   if (grid == 0) grid = 1;
   // step 2b (noise suppression) compiled in only where it is switched on
   const bool ns = P.ns_min_dip > 0;
-  // light windows to one warp each (fused finder without noise suppression),
+  // light windows to one warp each (the fused finder, with or without step 2b),
   // on timeframes large enough that the light kernel's per-window latency
   // hides behind the block finder (a single sector gets slower with it)
-  const bool light = W.light_list && W.heavy_list && !W.dense && !ns && n_windows >= kLightMinWindows;
+  const bool light = W.light_list && W.heavy_list && !W.dense && n_windows >= kLightMinWindows;
   DevWork Wh = W;
   if (!light) Wh.light_list = Wh.heavy_list = nullptr;
   if (light) {
