@@ -168,3 +168,45 @@ def test_graph_replay_matches_plain_launches(lib):
                 assert cl.tobytes() == a["clusters"].tobytes()
                 assert tr.tobytes() == a["tracks"].tobytes()
                 assert np.array_equal(m, a["cl2trk"])
+
+
+def _hdr(pages, o):
+    h = pages[o:o + 32].view(np.uint16)
+    return {"n_tb": int(h[2]), "n_runs": int(h[3]), "n_dig": int(h[4]), "lo_dig": int(h[10]), "lo_runs": int(h[9]),
+            "hi_dig": int(h[13]), "hi_runs": int(h[12])}
+
+
+@pytest.mark.parametrize("where", ["run", "entry"])
+def test_corrupt_light_window_reported(lib, where):
+    """A full-TPC timeframe (its sparse windows go to the one-warp path): a
+    page body broken in such a window -- a run past the row's end, or time
+    bins out of order -- is reported as corruption, and the context stays usable."""
+    tf = tpcgen.generate(tpcgen.full_tpc(5, n_tracks=2000))
+    nf = tf.n_fragments
+    offs = tf.page_offsets.astype(np.int64)
+    w = None
+    for cand in range(1, len(offs) - 1):
+        if cand % nf in (0, nf - 1):
+            continue
+        h, hp, hn = (_hdr(tf.pages, int(offs[cand + k])) for k in (0, -1, 1))
+        total = h["n_dig"] + hp["n_dig"] - hp["hi_dig"] + hn["lo_dig"]
+        if 4 <= h["n_tb"] and 0 < total <= 200:
+            w = cand
+            break
+    assert w is not None
+    o = int(offs[w])
+    h = _hdr(tf.pages, o)
+    bad = copy.copy(tf)
+    bad.pages = tf.pages.copy()
+    if where == "run":
+        bad.pages[o + 32 + 2 * h["n_tb"] + 1] = 200          # run 0's length: past any row
+    else:
+        bad.pages[o + 32 + 2] = bad.pages[o + 32]             # entry 1 at entry 0's time bin
+    with lib.Reconstructor.for_timeframe(bad) as R:
+        t = R.submit(bad.pages, bad.page_offsets, bad.n_time_bins)
+        with pytest.raises(lib.TpcError) as ei:
+            R.wait(t)
+        assert ei.value.code == -5
+        lib.tpc_release(R.ctx, t)
+        good = R.run(tf)
+    assert good["clusters"].tobytes() == oracle.find_clusters(tf).tobytes()
