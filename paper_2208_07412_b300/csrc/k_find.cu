@@ -1,26 +1,28 @@
 // k_find.cu — ZS decode + 3x3 peak finder + 5x5 cluster moments + stable
-// compaction, fused in one persistent kernel (steps 1-4 of the library's
-// definition; the paper's section "Hardware and data flow" places this first
-// step of the TPC reconstruction on the EPN GPUs, after FPGA zero suppression).
+// compaction (steps 1-4 of the library's definition; the paper's section
+// "Hardware and data flow" places this first step of the TPC reconstruction on
+// the EPN GPUs, after FPGA zero suppression).
 //
-// One CTA iteration processes one window = (sector, row, 256-bin fragment).
-// Memory round trips are the cost to avoid: the page is staged in shared
-// memory by one coalesced copy (issued together with the neighbours' headers),
-// and the neighbours' 3-bin halo byte ranges by a second one; everything after
-// that reads shared memory.  The small halo segments are decoded by one warp
-// each, without block barriers.
-// Digits are decoded into a zero-padded plane (two empty pads on each side of
-// the row) that is cleared lazily: at the end of a window only the cells its
-// digits wrote are reset, never the 74 KB plane, so the work scales with the
-// digits and every pixel lookup is a single shared load.  The decoder lists
-// the digits as it writes them; one thread per listed digit runs the peak
-// test; own peaks are ranked in canonical (t, pad) order by popcount prefixes
-// over the peak bitmap, and one thread per peak builds its cluster from the
-// 5x5 neighbourhood held in registers.
-// A decoupled look-back over the windows (handed out in index order by the
-// ticket) gives each window's global offset; its aggregate is published before
-// the clusters are built, so the wait overlaps that work, and the clusters are
-// written once, coalesced, at their final place.
+// A window is (sector, row, 256-bin fragment) with 3-bin halos from both
+// neighbouring pages.  k_find_classify sorts the windows by their page
+// headers: a light window (at most 256 digits and runs with its halos) goes to
+// one warp of k_find_light, the others to the persistent block finder
+// k_find_clusters; the two run side by side on two streams.
+// Block finder: one CTA iteration per window.  The page, both halo byte ranges
+// and the own header travel in one round trip (the neighbours' headers were
+// copied during the previous window); everything after that reads shared
+// memory.  Digits are decoded (entries, runs, digits in balanced block-wide
+// phases) into a zero-padded plane (two empty pads on each side of the row)
+// kept empty between windows: a listed window resets only the cells its digits
+// wrote, a dense one clears the plane with 16-byte stores, so every pixel
+// lookup is a single shared load.  The peak test runs one thread per listed
+// digit (dense windows: equal shares of the occupied pixels); own peaks are
+// ranked in canonical (t, pad) order by popcount prefixes over the peak
+// bitmap, and one thread per peak builds its cluster from the 5x5
+// neighbourhood held in registers.  Each window reserves a span of a scratch
+// buffer with one atomic; a scan of the window counts and a compaction place
+// the records canonically.  The allocation-free entry point instead gives each
+// window its offset by a decoupled look-back over the windows.
 #include <algorithm>
 #include <mutex>
 
@@ -1222,10 +1224,11 @@ k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
 // finder about 10 k cycles of fixed latency (round trips, block barriers,
 // scans over its 74 KB plane).  Such a window (at most kLightDig digits and
 // runs with its halos) is given to one warp instead: its digits are decoded
-// straight from global memory into a per-warp sorted list, indexed by a
-// small open-addressing hash on (plane row, pad), and the peak test and the
-// 5x5 clusters look pixels up there.  The results are those of the block path
-// (the same rules, the same record builder).
+// from its page and halo ranges (staged in the warp's shared memory) into a
+// per-warp list sorted by (plane row, pad) with each row's digit range, and
+// the peak test and the 5x5 clusters look pixels up by scanning a row.  The
+// results are those of the block path (the same rules, the same record
+// builder).
 constexpr int kLightDig = 256;               // digits (and runs) of a light window, halos included (512: slower)
 constexpr int kLightWarps = 6;               // warps per light block
 constexpr int kLightBlocksPerSm = 4;
