@@ -50,10 +50,10 @@ REF_SAMPLE_BYTES = 20 << 20
 # and k_find_clusters, summed), from an ncu capture of the current kernels on the
 # workload (seed 1); absent where no capture exists.  Must be cleared whenever a
 # finder kernel changes.
-FINDER_DRAM_BYTES = {"full_tpc": 87_106_304 + 2_334_720}
+FINDER_DRAM_BYTES = {}
 # Warp instructions (smsp__inst_executed.sum) of the same kernels, for the issue
 # roofline; reset together with FINDER_DRAM_BYTES.
-FINDER_WARP_INSTR = {"full_tpc": 484_925_296}
+FINDER_WARP_INSTR = {}
 # Warp-instruction issue peak: 148 SMs x 4 schedulers x 1 instruction per cycle
 # at the 2032 MHz maximum SM clock.
 ISSUE_PEAK = 148 * 4 * 2.032e9

@@ -650,6 +650,22 @@ __device__ __forceinline__ void cp_async16(void* dst_smem, const void* src) {
 
 template <int kMode, bool kAsync>
 __device__ __forceinline__ void load_nb_headers(const DevGeom& G, const DevWork& W, int frs, uint64_t op, uint64_t on,
+                                                uint4* hdr);
+
+// The next window (index in S.misc[1], coordinates in S.misc[2], its page
+// offsets in S.offs): its three pages prefetched into L2, its neighbours'
+// headers copied into shared memory.
+template <int kMode>
+__device__ __forceinline__ void issue_next(const DevGeom& G, const DevWork& W, const FindSmem& S,
+                                           unsigned int n_windows) {
+  if ((unsigned)S.misc[1] >= n_windows) return;
+  const unsigned long long no[4] = {S.offs[0], S.offs[1], S.offs[2], S.offs[3]};
+  prefetch_next_pages(W, no);
+  load_nb_headers<kMode, true>(G, W, S.misc[2], no[0], no[2], S.hdr);
+}
+
+template <int kMode, bool kAsync>
+__device__ __forceinline__ void load_nb_headers(const DevGeom& G, const DevWork& W, int frs, uint64_t op, uint64_t on,
                                                 uint4* hdr) {
   const int f = frs & 0xffff;
 #pragma unroll
@@ -750,7 +766,11 @@ k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
     if (kMode != 2 && w0 < n_windows) load_nb_headers<kMode, false>(G, W, S.misc[2], S.offs[0], S.offs[2], S.hdr);
   }
   unsigned int nt = 0;                  // next window (thread 0, scratch mode)
-  unsigned long long noffs[4] = {~0ull, ~0ull, ~0ull, ~0ull};
+  // the thread that prefetches the next window and copies its neighbours'
+  // headers (cp.async groups belong to the issuing thread, which also waits):
+  // the last one in the fused finder, idle while the first threads build the
+  // clusters; thread 0 in the dense variant's decode pass
+  const int issuer = kMode == 0 ? (int)blockDim.x - 1 : 0;
   while (true) {
     // ---- 0. window w (scratch mode: its neighbours' headers were copied
     // during the previous window)
@@ -759,7 +779,7 @@ k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
       S.misc[1] = (int)wt;
       S.misc[2] = wt < n_windows ? window_frs(G, wt) : 0;
     }
-    if (kScratch && kMode != 2 && tid == 0) asm volatile("cp.async.wait_all;" ::: "memory");
+    if (kScratch && kMode != 2 && tid == issuer) asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
     const unsigned int w = (unsigned int)S.misc[1];
     if (w >= n_windows) break;
@@ -980,18 +1000,19 @@ k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
       __syncthreads();
     }
 
-    if (kScratch && tid == 0 && nt < n_windows) {
+    if (kScratch && tid == 0) {
+      // the next window's index, coordinates and page offsets (this window
+      // reads neither S.misc[1..2] nor S.offs any more)
+      S.misc[1] = (int)nt;
+      S.misc[2] = nt < n_windows ? window_frs(G, nt) : 0;
       for (int k = 0; k < 4; k++) {
         const long long j = (long long)nt - 1 + k;
-        noffs[k] = (j >= 0 && j < (long long)n_windows) ? W.page_offsets[j] : ~0ull;
+        S.offs[k] = (nt < n_windows && j >= 0 && j < (long long)n_windows) ? W.page_offsets[j] : ~0ull;
       }
     }
 
     if (kMode == 1) {
-      if (kScratch && tid == 0 && nt < n_windows) {
-        prefetch_next_pages(W, noffs);
-        load_nb_headers<kMode, true>(G, W, window_frs(G, nt), noffs[0], noffs[2], S.hdr);
-      }
+      if (kScratch && tid == issuer) issue_next<kMode>(G, W, S, n_windows);
       // ---- dense variant, decode pass: the window's own rows into the dense
       // plane, 16-byte chunks of 8 pads (pads past the row's end written as 0)
       const int sr = (int)(w / (unsigned)G.n_frag);
@@ -1100,14 +1121,7 @@ k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
       // the own peaks that become clusters (rows 3..258)
       const uint32_t* const sv = (kNs ? S.occ : S.pk) + kHalo * nw;
 
-      if (kScratch && tid == 0 && nt < n_windows) {
-        if (kMode == 2) {
-          prefetch_next_dense(G, W, nt);
-        } else {
-          prefetch_next_pages(W, noffs);
-          load_nb_headers<kMode, true>(G, W, window_frs(G, nt), noffs[0], noffs[2], S.hdr);
-        }
-      }
+      if (kMode == 2 && kScratch && tid == 0 && nt < n_windows) prefetch_next_dense(G, W, nt);
 
       // ---- 5. rank the own peaks (rows 3..258) in canonical order, list the
       // first kStage, publish the window's count
@@ -1139,6 +1153,8 @@ k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
         npk = (int)tot;
       }
       __syncthreads();
+
+      if (kMode == 0 && kScratch && tid == issuer) issue_next<kMode>(G, W, S, n_windows);
 
       // ---- 6. clusters of the first kStage peaks, one thread each, staged
       const int nst = min(npk, kStage);
@@ -1194,12 +1210,6 @@ k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
         reinterpret_cast<uint4*>(dst)[idx] = rec;
       }
       __syncthreads();
-    }
-
-    if (kScratch && tid == 0) {
-      S.misc[1] = (int)nt;
-      S.misc[2] = nt < n_windows ? window_frs(G, nt) : 0;
-      for (int k = 0; k < 4; k++) S.offs[k] = noffs[k];
     }
 
     // ---- 9. leave the plane empty for the next window
