@@ -98,6 +98,12 @@ k_ca_neighbours(DevGeom G, DevParams P, DevWork W) {
     const int wd = (int)((P.sz_num * dxd) / (P.sz_den * 640LL)) + 5;
     const int wu = (int)((P.sz_num * dxu) / (P.sz_den * 640LL)) + 5;
     const long long lim = (long long)P.ca_cut * (Xu - Xd);
+    // the window cuts |dY| den > num dX as |dY| > floor(num dX / den) (den >= 1):
+    // one 32-bit compare per candidate (coordinate differences fit 32 bits)
+    const int yld = (int)min((P.sy_num * dxd) / P.sy_den, 2147483647LL);
+    const int zld = (int)min((P.sz_num * dxd) / P.sz_den, 2147483647LL);
+    const int ylu = (int)min((P.sy_num * dxu) / P.sy_den, 2147483647LL);
+    const int zlu = (int)min((P.sz_num * dxu) / P.sz_den, 2147483647LL);
     const unsigned dlo = W.row_start[sr - 1], dhi = min((unsigned long long)W.row_start[sr], n);
     const unsigned ulo = min((unsigned long long)W.row_start[sr + 1], n), uhi = min((unsigned long long)W.row_start[sr + 2], n);
     for (unsigned cs = lo; cs < hi; cs += kCaChunk) {
@@ -133,7 +139,7 @@ k_ca_neighbours(DevGeom G, DevParams P, DevWork W) {
       __syncthreads();
       const unsigned c = cs + tid;
       if (c < ce) {
-        const long long Yc = W.cl_y[c], Zc = W.cl_z[c];
+        const int Yc = W.cl_y[c], Zc = W.cl_z[c];
         const int tc = W.cl_t[c];
         const unsigned d0 = lb_slice(sl[0].t, sl[0].n, tc - wd);
         const unsigned u0 = lb_slice(sl[1].t, sl[1].n, tc - wu);
@@ -143,14 +149,14 @@ k_ca_neighbours(DevGeom G, DevParams P, DevWork W) {
         int nd = 0, nu = 0;
         bool spill = false;
         for (unsigned i = d0; i < sl[0].n && sl[0].t[i] <= tc + wd; i++) {
-          if (llabs_(Yc - sl[0].y[i]) * P.sy_den > P.sy_num * dxd) continue;
-          if (llabs_(Zc - sl[0].z[i]) * P.sz_den > P.sz_num * dxd) continue;
+          if (abs(Yc - sl[0].y[i]) > yld) continue;
+          if (abs(Zc - sl[0].z[i]) > zld) continue;
           if (nd < kMaxCand) di[nd] = i; else spill = true;
           nd++;
         }
         for (unsigned j = u0; nd > 0 && j < sl[1].n && sl[1].t[j] <= tc + wu; j++) {
-          if (llabs_(sl[1].y[j] - Yc) * P.sy_den > P.sy_num * dxu) continue;
-          if (llabs_(sl[1].z[j] - Zc) * P.sz_den > P.sz_num * dxu) continue;
+          if (abs(sl[1].y[j] - Yc) > ylu) continue;
+          if (abs(sl[1].z[j] - Zc) > zlu) continue;
           if (nu < kMaxCand) ui[nu] = j; else spill = true;
           nu++;
         }
@@ -158,11 +164,11 @@ k_ca_neighbours(DevGeom G, DevParams P, DevWork W) {
         int bd = -1, bu = -1;
         if (!spill) {
           for (int a = 0; a < nd; a++) {
-            const long long Yd = sl[0].y[di[a]], Zd = sl[0].z[di[a]];
+            const int Yd = sl[0].y[di[a]], Zd = sl[0].z[di[a]];
             for (int b = 0; b < nu; b++) {
-              const long long Yu = sl[1].y[ui[b]], Zu = sl[1].z[ui[b]];
-              const long long devy = (Yu - Yc) * dxd - (Yc - Yd) * dxu;
-              const long long devz = (Zu - Zc) * dxd - (Zc - Zd) * dxu;
+              const int Yu = sl[1].y[ui[b]], Zu = sl[1].z[ui[b]];
+              const long long devy = (long long)(Yu - Yc) * dxd - (long long)(Yc - Yd) * dxu;
+              const long long devz = (long long)(Zu - Zc) * dxd - (long long)(Zc - Zd) * dxu;
               if (llabs_(devy) > lim || llabs_(devz) > lim) continue;
               const long long sc = devy * devy + devz * devz;
               if (best < 0 || sc < best) { best = sc; bd = (int)(sl[0].base + di[a]); bu = (int)(sl[1].base + ui[b]); }
@@ -172,16 +178,16 @@ k_ca_neighbours(DevGeom G, DevParams P, DevWork W) {
           // more candidates than the lists hold: the plain double loop
           for (unsigned i = d0; i < sl[0].n; i++) {
             if (sl[0].t[i] > tc + wd) break;
-            const long long Yd = sl[0].y[i], Zd = sl[0].z[i];
-            if (llabs_(Yc - Yd) * P.sy_den > P.sy_num * dxd) continue;
-            if (llabs_(Zc - Zd) * P.sz_den > P.sz_num * dxd) continue;
+            const int Yd = sl[0].y[i], Zd = sl[0].z[i];
+            if (abs(Yc - Yd) > yld) continue;
+            if (abs(Zc - Zd) > zld) continue;
             for (unsigned j = u0; j < sl[1].n; j++) {
               if (sl[1].t[j] > tc + wu) break;
-              const long long Yu = sl[1].y[j], Zu = sl[1].z[j];
-              if (llabs_(Yu - Yc) * P.sy_den > P.sy_num * dxu) continue;
-              if (llabs_(Zu - Zc) * P.sz_den > P.sz_num * dxu) continue;
-              const long long devy = (Yu - Yc) * dxd - (Yc - Yd) * dxu;
-              const long long devz = (Zu - Zc) * dxd - (Zc - Zd) * dxu;
+              const int Yu = sl[1].y[j], Zu = sl[1].z[j];
+              if (abs(Yu - Yc) > ylu) continue;
+              if (abs(Zu - Zc) > zlu) continue;
+              const long long devy = (long long)(Yu - Yc) * dxd - (long long)(Yc - Yd) * dxu;
+              const long long devz = (long long)(Zu - Zc) * dxd - (long long)(Zc - Zd) * dxu;
               if (llabs_(devy) > lim || llabs_(devz) > lim) continue;
               const long long sc = devy * devy + devz * devz;
               if (best < 0 || sc < best) { best = sc; bd = (int)(sl[0].base + i); bu = (int)(sl[1].base + j); }

@@ -1239,7 +1239,7 @@ k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
 // the peak test and the 5x5 clusters look pixels up by scanning a row.  The
 // results are those of the block path (the same rules, the same record
 // builder).
-constexpr int kLightDig = 256;               // digits (and runs) of a light window, halos included (512: slower)
+constexpr int kLightDig = 256;               // digits (and runs) of a light window, halos included (384, 512: no faster)
 constexpr int kLightWarps = 6;               // warps per light block
 constexpr int kLightBlocksPerSm = 4;
 constexpr unsigned kLightMinWindows = 4096;  // smaller timeframes: block finder only
