@@ -48,12 +48,12 @@ WORKLOADS = {
 REF_SAMPLE_BYTES = 20 << 20
 # DRAM bytes (read + write) of one finder stage (k_find_classify, k_find_light
 # and k_find_clusters, summed), from an ncu capture of the current kernels on the
-# workload (seed 1); absent where no capture exists.  Must be cleared whenever a
-# finder kernel changes.
-FINDER_DRAM_BYTES = {}
+# workload (seed 1), keyed by (workload, block finder threads); absent where no
+# capture exists.  Must be cleared whenever a finder kernel changes.
+FINDER_DRAM_BYTES = {("full_tpc", 512): 87284480 + 2501376}
 # Warp instructions (smsp__inst_executed.sum) of the same kernels, for the issue
 # roofline; reset together with FINDER_DRAM_BYTES.
-FINDER_WARP_INSTR = {}
+FINDER_WARP_INSTR = {("full_tpc", 512): 514128571}
 # Warp-instruction issue peak: 148 SMs x 4 schedulers x 1 instruction per cycle
 # at the 2032 MHz maximum SM clock.
 ISSUE_PEAK = 148 * 4 * 2.032e9
@@ -733,6 +733,7 @@ def run_ours(args, world, rank, local):
             plane = tf.n_sectors * len(tf.npads) * tf.n_time_bins * ((int(tf.npads.max()) + 7) & ~7) * 2
             alg_bytes += plane + plane * 262 // 256
         achieved = alg_bytes / (stages["find"] * 1e-3) / 1e9
+        counter_key = (args.workload, int(tuning["find_threads"]))
         line = {
             "metric": METRIC, "value": cl_all / dev_s_max, "unit": "clusters/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dev_s_max / args.steps,
@@ -753,17 +754,17 @@ def run_ours(args, world, rank, local):
             "roofline": {"kernel": "find stage: k_find_classify + k_find_light + k_find_clusters",
                          "bound": "hbm", "achieved": achieved, "peak": hbm,
                          "unit": "GB/s", "frac": achieved / hbm,
-                         "traffic": (FINDER_DRAM_BYTES.get(args.workload)
+                         "traffic": (FINDER_DRAM_BYTES.get(counter_key)
                                      if args.seed == 1 and not args.time_bins and not args.dense_finder else None),
                          "peak_kind": f"{peak_kind} hbm_gbs (copy)",
                          "algorithmic_bytes_per_launch": int(alg_bytes)},
             "roofline_issue": (None if not (args.seed == 1 and not args.time_bins and not args.dense_finder
-                                            and args.workload in FINDER_WARP_INSTR) else
+                                            and counter_key in FINDER_WARP_INSTR) else
                                {"kernel": "find stage: k_find_classify + k_find_light + k_find_clusters",
                                 "bound": "issue",
-                                "achieved": FINDER_WARP_INSTR[args.workload] / (stages["find"] * 1e-3),
+                                "achieved": FINDER_WARP_INSTR[counter_key] / (stages["find"] * 1e-3),
                                 "peak": ISSUE_PEAK, "unit": "warp-instr/s",
-                                "frac": FINDER_WARP_INSTR[args.workload] / (stages["find"] * 1e-3) / ISSUE_PEAK,
+                                "frac": FINDER_WARP_INSTR[counter_key] / (stages["find"] * 1e-3) / ISSUE_PEAK,
                                 "instructions": "ncu smsp__inst_executed.sum of one launch",
                                 "peak_kind": "148 SMs x 4 schedulers x 2032 MHz"}),
             "e2e": {"value": cl_all / e2e_s_max, "unit": "clusters/s", "h2d_bytes_per_step": int(h2d),
