@@ -212,10 +212,15 @@ __global__ void k_xs_fill(DevGeom G, DevWork W, XsWork X) {
   }
 }
 
+// One warp per exiting piece A; its lanes share A's candidates, whose chi2 (a
+// 5x5 transport, similarity transform and Cholesky solve each) dominates the
+// step.  The keys (chi2 bits, index) are unique, so the minima do not depend
+// on which lane finds them.
 __global__ void k_xs_pairs(DevGeom G, DevParams P, DevWork W, XsWork X) {
   const unsigned long long nt = n_tracks_x(W);
-  for (unsigned long long a = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; a < nt;
-       a += (unsigned long long)gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const unsigned long long wpb = blockDim.x >> 5;
+  for (unsigned long long a = blockIdx.x * wpb + (threadIdx.x >> 5); a < nt; a += (unsigned long long)gridDim.x * wpb) {
     const int ex = X.side[a] & 3;
     if (!ex) continue;
     const tpc_track A = W.tracks[a];
@@ -235,7 +240,8 @@ __global__ void k_xs_pairs(DevGeom G, DevParams P, DevWork W, XsWork X) {
     // bins that can hold |Z_B - Z_A| <= dz (bins are at least dz wide: <= 3)
     const size_t bb = (size_t)vb * X.n_zb;
     const int zl = zbin(X, za - X.dz_u), zh = zbin(X, za + X.dz_u);
-    for (unsigned long long e = X.bin_off[bb + zl]; e < X.bin_off[bb + zh + 1]; e++) {
+    const unsigned long long e1 = X.bin_off[bb + zh + 1];
+    for (unsigned long long e = X.bin_off[bb + zl] + lane; e < e1; e += 32) {
       const unsigned b = X.ent[e];
       if (((X.side[b] >> 2) & 3) != want_entry || X.row_in[b] <= ro) continue;
       const long long dz = (long long)X.z_in[b] - za;
@@ -247,7 +253,9 @@ __global__ void k_xs_pairs(DevGeom G, DevParams P, DevWork W, XsWork X) {
       best = min(best, cb | b);
       atomicMin(&X.best_a[b], cb | (unsigned)a);
     }
-    X.best_b[a] = best;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(0xffffffffu, best, o));
+    if (lane == 0) X.best_b[a] = best;
   }
 }
 
@@ -526,7 +534,12 @@ cudaError_t launch_xsec(const DevGeom& G, const DevParams& P, const DevWork& W, 
                                reinterpret_cast<unsigned int*>(X.ctl + 4), X.ctl + 5, W.err, n_sm, st);
   if (e0 != cudaSuccess) return e0;
   k_xs_fill<<<g, 256, 0, st>>>(G, W, X);
-  k_xs_pairs<<<grid_x(W.cap_ch, n_sm, 16), 64, 0, st>>>(G, P, W, X);
+  {   // a warp per piece: 8 pieces per 256-thread block
+    unsigned long long gp = (W.cap_ch + 7) / 8;
+    const unsigned long long mp = (unsigned long long)n_sm * 16;
+    if (gp > mp) gp = mp;
+    k_xs_pairs<<<(unsigned)(gp ? gp : 1), 256, 0, st>>>(G, P, W, X);
+  }
   k_xs_link<<<g, 256, 0, st>>>(W, X);
   k_xs_roots<<<g, 256, 0, st>>>(W, X);
   cudaError_t e = launch_scan(X.scan, W.ctr + CTR_NTRK, W.cap_ch, X.scan_state,
