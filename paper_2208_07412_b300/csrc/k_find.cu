@@ -752,8 +752,12 @@ k_find_clusters(DevGeom G, DevParams P, DevWork W, unsigned int n_windows) {
   // windows of this kernel: all, or (with the light path) the heavy list
   const unsigned long long n_heavy = (kScratch && W.heavy_list) ? W.ctr[CTR_NHEAVY] : 0ull;
   auto window_of = [&](unsigned tk) -> unsigned {
-    if (!(kScratch && W.heavy_list)) return tk;
-    return (unsigned long long)tk < n_heavy ? W.heavy_list[tk] : n_windows;
+    if constexpr (!kScratch) {
+      return tk;
+    } else {
+      if (!W.heavy_list) return tk;
+      return (unsigned long long)tk < n_heavy ? W.heavy_list[tk] : n_windows;
+    }
   };
   if (kScratch && tid == 0) {
     const unsigned w0 = window_of(atomicAdd(&W.tickets[kMode == 2 ? TK_FIND2 : TK_FIND], 1u));

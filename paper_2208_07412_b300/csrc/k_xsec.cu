@@ -143,17 +143,33 @@ __device__ __forceinline__ float chi2_spd(float (&M)[5][5], const float* d) {
   return c2;
 }
 
-// Matching chi2 of A (inner piece) and B (outer piece); -1 if B cannot be
-// carried to A's reference.
-__device__ float xs_chi2(float kfac, const tpc_track& A, const tpc_track& B) {
-  float sa[5], sb[5], CA[5][5], CB[5][5];
-  load_fit(A, sa, CA);
-  load_fit(B, sb, CB);
-  float x = B.x;
+// Matching chi2 of A (inner piece: state sa, covariance CA at xa in frame
+// alpha_a) and B (outer piece); -1 if B cannot be carried to A's reference.
+// Early exit: for the symmetric positive definite M = C_A + J C_B J^T,
+// d^T M^-1 d >= d_i^2 / M_ii for every i (the minimum of the quadratic form
+// over the other components), so a pair with d_i^2 > 4 cut M_ii for i = y or
+// zeta has chi2 > cut by a factor far beyond FP32 rounding and is returned as
+// +inf without the full 5x5 transform and solve; every other pair gets the
+// full chi2, so the accepted pairs and their chi2 are those of the plain
+// computation.
+__device__ float xs_chi2(float kfac, const float* sa, const float (&CA)[5][5], float xa, float alpha_a,
+                         const float (&fb)[24], float cut) {
+  // fb: B's tpc_track words par[0..4], x, alpha, chi2, cov[0..14]
+  float sb[5], CB[5][5];
+#pragma unroll
+  for (int i = 0; i < 5; i++) sb[i] = fb[i];
+  {
+    int m = 0;
+#pragma unroll
+    for (int i = 0; i < 5; i++)
+#pragma unroll
+      for (int j = 0; j <= i; j++) { CB[i][j] = fb[8 + m]; CB[j][i] = fb[8 + m]; m++; }
+  }
+  float x = fb[5];
   Rot R;
-  if (!rotate_state(kfac, sb, x, B.alpha - A.alpha, R)) return -1.f;
+  if (!rotate_state(kfac, sb, x, fb[6] - alpha_a, R)) return -1.f;
   Jac<float> F;
-  if (!transport(kfac, sb, A.x - x, F)) return -1.f;
+  if (!transport(kfac, sb, xa - x, F)) return -1.f;
   // J = F R: F unit upper triangular with a = F02, b = F04, e = F12, g = F13,
   // h = F14, m = F24; R identity except r00, r10, r20, r22
   float J[5][5];
@@ -172,8 +188,21 @@ __device__ float xs_chi2(float kfac, const tpc_track& A, const tpc_track& B) {
   J[2][0] = R.r20;
   J[2][2] = R.r22;
   J[2][4] = F.m;
+  float d[5];
+#pragma unroll
+  for (int i = 0; i < 5; i++) d[i] = sa[i] - sb[i];
+  // the y and zeta diagonal entries of M first
+#pragma unroll
+  for (int i = 0; i < 2; i++) {
+    float mii = CA[i][i];
+#pragma unroll
+    for (int k = 0; k < 5; k++)
+#pragma unroll
+      for (int l = 0; l < 5; l++) mii += J[i][k] * CB[k][l] * J[i][l];
+    if (d[i] * d[i] > 4.f * cut * mii) return __int_as_float(0x7f800000);
+  }
   // C = C_A + J C_B J^T
-  float T[5][5];
+  float T[5][5], M[5][5];
 #pragma unroll
   for (int i = 0; i < 5; i++)
 #pragma unroll
@@ -190,16 +219,15 @@ __device__ float xs_chi2(float kfac, const tpc_track& A, const tpc_track& B) {
       float acc = 0.f;
 #pragma unroll
       for (int l = 0; l < 5; l++) acc += T[i][l] * J[j][l];
-      CA[i][j] += acc;
+      M[i][j] = CA[i][j] + acc;
     }
-  float d[5];
-#pragma unroll
-  for (int i = 0; i < 5; i++) d[i] = sa[i] - sb[i];
-  return chi2_spd(CA, d);
+  return chi2_spd(M, d);
 }
 
 // The entering unflagged pieces into their bins (bin_off holds the exclusive
-// offsets); the order within a bin is free: the matching keys carry indices.
+// offsets), each with its candidate-gate fields and fitted state beside it, so
+// that the search reads them in bin order; the order within a bin is free:
+// the matching keys carry indices.
 __global__ void k_xs_fill(DevGeom G, DevWork W, XsWork X) {
   const unsigned long long nt = n_tracks_x(W);
   for (unsigned long long t = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; t < nt;
@@ -208,7 +236,12 @@ __global__ void k_xs_fill(DevGeom G, DevWork W, XsWork X) {
     const int c = W.trk_first[t];
     const int sec = (int)(__ldg(reinterpret_cast<const uint4*>(W.clusters) + c).w >> 24);
     const size_t bin = (size_t)vsector_of(G, W, (unsigned)c, sec) * X.n_zb + zbin(X, X.z_in[t]);
-    X.ent[X.bin_off[bin] + atomicAdd(&X.bin_cur[bin], 1u)] = (uint32_t)t;
+    const unsigned long long e = X.bin_off[bin] + atomicAdd(&X.bin_cur[bin], 1u);
+    X.ent[e] = make_uint4((uint32_t)t, (uint32_t)X.z_in[t],
+                          (uint32_t)X.row_in[t] | ((uint32_t)((X.side[t] >> 2) & 3) << 8), 0u);
+    const uint4* src = reinterpret_cast<const uint4*>(W.tracks + t);
+#pragma unroll
+    for (int q = 0; q < 6; q++) X.ent_fit[e * 6 + q] = src[q];
   }
 }
 
@@ -225,6 +258,8 @@ __global__ void k_xs_pairs(DevGeom G, DevParams P, DevWork W, XsWork X) {
     if (!ex) continue;
     const tpc_track A = W.tracks[a];
     if (A.flags) continue;
+    float sa[5], CA[5][5];
+    load_fit(A, sa, CA);
     const int c0 = W.trk_first[a];
     const int vs = vsector_of(G, W, (unsigned)c0, A.sector);
     const int phys = vs % G.n_phys, base = vs - phys;
@@ -241,13 +276,25 @@ __global__ void k_xs_pairs(DevGeom G, DevParams P, DevWork W, XsWork X) {
     const size_t bb = (size_t)vb * X.n_zb;
     const int zl = zbin(X, za - X.dz_u), zh = zbin(X, za + X.dz_u);
     const unsigned long long e1 = X.bin_off[bb + zh + 1];
-    for (unsigned long long e = X.bin_off[bb + zl] + lane; e < e1; e += 32) {
-      const unsigned b = X.ent[e];
-      if (((X.side[b] >> 2) & 3) != want_entry || X.row_in[b] <= ro) continue;
-      const long long dz = (long long)X.z_in[b] - za;
+    unsigned long long e = X.bin_off[bb + zl] + lane;
+    uint4 key = e < e1 ? X.ent[e] : make_uint4(0u, 0u, 0u, 0u);
+    for (; e < e1; e += 32) {
+      const uint4 cur = key;                       // the next candidate's gate fields in flight
+      if (e + 32 < e1) key = X.ent[e + 32];
+      const unsigned b = cur.x;
+      if ((int)(cur.z >> 8) != want_entry || (int)(cur.z & 0xffu) <= ro) continue;
+      const long long dz = (long long)(int)cur.y - za;
       if (dz > X.dz_u || dz < -(long long)X.dz_u) continue;
-      const tpc_track B = W.tracks[b];
-      const float c2 = xs_chi2(P.kfac, A, B);
+      float fb[24];
+#pragma unroll
+      for (int q = 0; q < 6; q++) {
+        const uint4 v = X.ent_fit[e * 6 + q];
+        fb[4 * q] = __uint_as_float(v.x);
+        fb[4 * q + 1] = __uint_as_float(v.y);
+        fb[4 * q + 2] = __uint_as_float(v.z);
+        fb[4 * q + 3] = __uint_as_float(v.w);
+      }
+      const float c2 = xs_chi2(P.kfac, sa, CA, A.x, A.alpha, fb, X.chi2_cut);
       if (!(c2 >= 0.f) || c2 > X.chi2_cut) continue;
       const unsigned long long cb = (unsigned long long)__float_as_uint(c2) << 32;
       best = min(best, cb | b);
@@ -372,7 +419,9 @@ __device__ __forceinline__ float xs_measure(const DevParams& P, float* s, UD<flo
 }
 
 // One thread per merged track (a root piece): numbering, piece assignment,
-// record copy (one piece) or multi-frame refit (several).
+// record copy (one piece) or multi-frame refit (several).  The grid covers
+// every piece (up to 512 blocks per SM): a refit is a long serial chain, and a
+// thread given two would take twice the step's time.
 __global__ void k_xs_emit(DevGeom G, DevParams P, DevWork W, XsWork X) {
   const unsigned long long nt = n_tracks_x(W);
   for (unsigned long long r = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; r < nt;
@@ -545,7 +594,13 @@ cudaError_t launch_xsec(const DevGeom& G, const DevParams& P, const DevWork& W, 
   cudaError_t e = launch_scan(X.scan, W.ctr + CTR_NTRK, W.cap_ch, X.scan_state,
                               reinterpret_cast<unsigned int*>(X.ctl + 2), X.ctl, W.err, n_sm, st);
   if (e != cudaSuccess) return e;
-  k_xs_emit<<<grid_x(W.cap_ch, n_sm, 16), 64, 0, st>>>(G, P, W, X);
+  {   // a thread per piece up to 148 x 512 x 64 = 4.8 M pieces, so that no thread
+      // refits two chains one after the other
+    unsigned long long ge = (W.cap_ch + 63) / 64;
+    const unsigned long long me = (unsigned long long)n_sm * 512;
+    if (ge > me) ge = me;
+    k_xs_emit<<<(unsigned)(ge ? ge : 1), 64, 0, st>>>(G, P, W, X);
+  }
   k_xs_map<<<grid_x(W.cap_cl, n_sm, 8), 256, 0, st>>>(W, X);
   return cudaGetLastError();
 }

@@ -1012,7 +1012,8 @@ extern "C" tpc_status tpc_merge_sectors(tpc_context* ctx, uint64_t ticket, const
   const size_t btiles = scan_tiles(n_bins + 1);
   auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
   const size_t need = al(C) + 2 * al(C * 4) + 2 * al(C * 8) + 3 * al(C * 4) + al(C * 8) + al(tiles * 8) + al(64) +
-                      al(C * sizeof(tpc_track)) + al(Ncl * 4) + 3 * al(C * 4) + al((n_bins + 1) * 8) +
+                      al(C * sizeof(tpc_track)) + al(Ncl * 4) + 2 * al(C * 4) + al(C * 16) + al(C * 96) +
+                      al((n_bins + 1) * 8) +
                       al(n_bins * 4) + al(btiles * 8);
   if (need > s->xs.bytes) {
     if (ctx->used - s->xs_bytes + need > ctx->budget) return fail(TPC_E_NOMEM, "tpc_merge_sectors: over the memory budget");
@@ -1038,7 +1039,8 @@ extern "C" tpc_status tpc_merge_sectors(tpc_context* ctx, uint64_t ticket, const
   X.cl2trk_out = (int32_t*)take(Ncl * 4);
   X.z_in = (int32_t*)take(C * 4);
   X.z_out = (int32_t*)take(C * 4);
-  X.ent = (uint32_t*)take(C * 4);
+  X.ent = (uint4*)take(C * 16);
+  X.ent_fit = (uint4*)take(C * 96);
   X.bin_off = (uint64_t*)take((n_bins + 1) * 8);
   X.bin_cur = (uint32_t*)take(n_bins * 4);
   X.bin_state = (unsigned long long*)take(btiles * 8);

@@ -273,7 +273,10 @@ struct XsWork {
   int32_t* z_out;                // [cap_ch] Z (u) of the outermost cluster
   uint64_t* bin_off;             // [n_bins + 1] entering pieces per (virtual sector, zeta bin) -> offsets
   uint32_t* bin_cur;             // [n_bins] fill cursors
-  uint32_t* ent;                 // [cap_ch] entering unflagged pieces grouped by bin
+  uint4* ent;                    // [cap_ch] entering unflagged pieces grouped by bin: (piece, Z of the
+                                 // innermost cluster, innermost row | entry edge << 8, 0)
+  uint4* ent_fit;                // [cap_ch][6] the same pieces' first 96 bytes of tpc_track (state,
+                                 // x, alpha, chi2, covariance), in the same order
   unsigned long long* bin_state; // scan state of bin_off
   float chi2_cut;
   int edge_u;
