@@ -25,10 +25,16 @@ __device__ __forceinline__ long long floordiv_ll(long long a, long long b) {  //
   return q;
 }
 __device__ __forceinline__ long long absll(long long v) { return v < 0 ? -v : v; }
-// trunc(((yb - y2)(x2 - x1) - (y2 - y1)(xb - x2)) / (x2 - x1))
-__device__ __forceinline__ long long extrap_res(long long x1, long long y1, long long x2, long long y2,
-                                                long long xb, long long yb) {
-  return ((yb - y2) * (x2 - x1) - (y2 - y1) * (xb - x2)) / (x2 - x1);
+// Residual r = trunc(n / d), n = (yb - y2)(x2 - x1) - (y2 - y1)(xb - x2),
+// d = x2 - x1: true when |r| <= MC, r then set.  |trunc(n / d)| =
+// floor(|n| / |d|) exceeds MC exactly when |n| >= (MC + 1) |d|, so a pair past
+// the cut costs a multiply, not a 64-bit division.
+__device__ __forceinline__ bool extrap_res_within(long long x1, long long y1, long long x2, long long y2,
+                                                  long long xb, long long yb, long long MC, long long& r) {
+  const long long n = (yb - y2) * (x2 - x1) - (y2 - y1) * (xb - x2), d = x2 - x1;
+  if (absll(n) >= (MC + 1) * absll(d)) return false;
+  r = n / d;
+  return true;
 }
 __device__ __forceinline__ unsigned lower_bound_tm(const int32_t* __restrict__ t, unsigned lo, unsigned hi, long long v) {
   while (lo < hi) {
@@ -67,11 +73,12 @@ __global__ void k_merge_cand(DevGeom G, DevParams P, DevWork W) {
       const int b2 = W.ch_b2[kb];
       const long long Xb1 = W.cl_x[b1], Yb1 = W.cl_y[b1], Zb1 = W.cl_z[b1];
       const long long Xb2 = W.cl_x[b2], Yb2 = W.cl_y[b2], Zb2 = W.cl_z[b2];
-      const long long ry = extrap_res(Xa1, Ya1, Xa2, Ya2, Xb1, Yb1);
-      const long long rz = extrap_res(Xa1, Za1, Xa2, Za2, Xb1, Zb1);
-      const long long sy = extrap_res(Xb2, Yb2, Xb1, Yb1, Xa2, Ya2);
-      const long long sz = extrap_res(Xb2, Zb2, Xb1, Zb1, Xa2, Za2);
-      if (absll(ry) > MC || absll(rz) > MC || absll(sy) > MC || absll(sz) > MC) continue;
+      long long ry, rz, sy, sz;
+      if (!extrap_res_within(Xa1, Ya1, Xa2, Ya2, Xb1, Yb1, MC, ry) ||
+          !extrap_res_within(Xa1, Za1, Xa2, Za2, Xb1, Zb1, MC, rz) ||
+          !extrap_res_within(Xb2, Yb2, Xb1, Yb1, Xa2, Ya2, MC, sy) ||
+          !extrap_res_within(Xb2, Zb2, Xb1, Zb1, Xa2, Za2, MC, sz))
+        continue;
       const unsigned long long sc = (unsigned long long)(ry * ry + rz * rz + sy * sy + sz * sz);
       // pass 0: every chain is both a group top and a group bottom
       atomicMin(&W.best_b[k], (sc << 32) | (unsigned)kb);
