@@ -50,10 +50,10 @@ REF_SAMPLE_BYTES = 20 << 20
 # and k_find_clusters, summed), from an ncu capture of the current kernels on the
 # workload (seed 1), keyed by (workload, block finder threads); absent where no
 # capture exists.  Must be cleared whenever a finder kernel changes.
-FINDER_DRAM_BYTES = {("full_tpc", 512): 87284480 + 2501376}
+FINDER_DRAM_BYTES = {("full_tpc", 512): 87284480 + 2501376, ("full_tpc", 384): 87140096 + 2155264}
 # Warp instructions (smsp__inst_executed.sum) of the same kernels, for the issue
 # roofline; reset together with FINDER_DRAM_BYTES.
-FINDER_WARP_INSTR = {("full_tpc", 512): 514128571}
+FINDER_WARP_INSTR = {("full_tpc", 512): 514128571, ("full_tpc", 384): 467540997}
 # Warp-instruction issue peak: 148 SMs x 4 schedulers x 1 instruction per cycle
 # at the 2032 MHz maximum SM clock.
 ISSUE_PEAK = 148 * 4 * 2.032e9
