@@ -24,6 +24,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -71,10 +72,10 @@ def load_peaks():
 class ClockSampler:
     """nvidia-smi clocks / throttle reasons sampled during the timed region."""
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, out_dir=None):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        self.path = os.path.join(out_dir or tempfile.gettempdir(), f"tpc_clocks_rank{gpu_index}.csv")
 
     def __enter__(self):
         try:
@@ -645,7 +646,7 @@ def run_ours(args, world, rank, local):
     torch.cuda.synchronize()
     barrier(world)
     recs = []
-    with ClockSampler(local) as clk:
+    with ClockSampler(local, args.clocks_dir) as clk:
         torch.cuda.synchronize()
         w0 = time.perf_counter()
         for _ in range(args.steps):
@@ -818,6 +819,8 @@ def main():
                     help="offered load as fractions of the plain path's saturation rate")
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--clocks-dir", default=None,
+                    help="where the nvidia-smi clock samples of the timed region are written (default: the temp dir)")
     ap.add_argument("--no-graphs", action="store_true", help="enqueue every kernel instead of graph replay")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain comparison")
     ap.add_argument("--no-variants", action="store_true", help="skip the fused-vs-dense finder comparison")
