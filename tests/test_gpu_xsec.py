@@ -138,3 +138,21 @@ def test_batch_merge_equals_events_alone(lib):
         assert np.array_equal(mp, amm)
         off += len(amt)
     assert off == len(mt)
+
+
+def test_degenerate_inputs(lib):
+    """No digits, noise only, and one sector (no neighbouring sector to enter):
+    step 9 links nothing and every piece is its own merged track, unchanged."""
+    cases = [tpcgen.single_sector(6, n_tracks=0, zs_threshold=1024),
+             tpcgen.single_sector(6, n_tracks=0),
+             tpcgen.single_sector(1)]
+    for cfg in cases:
+        tf = tpcgen.generate(cfg)
+        cl, tr, m, mt, mm, link = gpu_merge(lib, tf)
+        assert len(mt) == len(tr)
+        assert np.all(np.asarray(link) < 0)
+        if len(tr):
+            assert np.array_equal(mt["par"], tr["par"]) and np.array_equal(mt["cov"], tr["cov"])
+            assert np.array_equal(mt["n_clusters"], tr["n_clusters"])
+            assert np.array_equal(mm, m)
+            assert not np.any(mt["flags"] & lib.TPC_TRK_XSECTOR)
