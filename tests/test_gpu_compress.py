@@ -46,3 +46,21 @@ def test_full_tpc_compression_parity(lib):
     assert same_status >= 0.999
     assert dy.max() <= 1 and dz.max() <= 1
     assert np.mean(dy > 0) <= 0.01 and np.mean(dz > 0) <= 0.01
+
+
+def test_degenerate_inputs_steps_10_11(lib):
+    """No digits and noise only (no tracks): step 10 codes nothing, every cluster
+    keeps status 0; step 11 finds no track to use and reports no estimate."""
+    for cfg in (tpcgen.single_sector(6, n_tracks=0, zs_threshold=1024), tpcgen.single_sector(6, n_tracks=0)):
+        tf = tpcgen.generate(cfg)
+        with lib.Reconstructor.for_timeframe(tf) as R:
+            t = R.submit(tf.pages, tf.page_offsets, tf.n_time_bins)
+            R.wait(t)
+            cl = lib.tpc_get_clusters(R.ctx, t)
+            tr, _ = lib.tpc_get_tracks(R.ctx, t, len(cl))
+            assert len(tr) == 0
+            assert lib.tpc_compress_clusters(R.ctx, t) == (0, 0)
+            cy, cz, st = lib.tpc_get_compressed(R.ctx, t, len(cl))
+            assert len(st) == len(cl) and not np.any(st)
+            assert lib.tpc_calibrate_drift(R.ctx, t, 750.0) == (0.0, 0.0, 0.0, 0)
+            lib.tpc_release(R.ctx, t)
