@@ -67,7 +67,7 @@ class _Params(ctypes.Structure):
                 ("merge_passes", ctypes.c_int32), ("min_track", ctypes.c_int32),
                 ("fit_passes", ctypes.c_int32), ("ns_min_dip", ctypes.c_int32), ("bz", ctypes.c_double),
                 ("sigma_y", ctypes.c_double), ("sigma_z", ctypes.c_double),
-                ("c0", ctypes.c_double * 5)]
+                ("c0", ctypes.c_double * 5), ("search_all", ctypes.c_int32)]
 
 
 @dataclass
@@ -91,11 +91,13 @@ class OracleParams:
     sigma_y: float = 0.02
     sigma_z: float = 0.03
     c0: tuple = (4.0, 4.0, 0.25, 1.0, 100.0)
+    search_all: bool = False   # CA / merge visit every candidate (no time window)
 
     def _c(self) -> _Params:
         p = _Params()
         for k in ("q_peak_min", "sy_num", "sy_den", "sz_num", "sz_den", "ca_cut", "min_chain",
-                  "merge_cut", "gap_min", "gap_max", "merge_passes", "min_track", "fit_passes", "ns_min_dip"):
+                  "merge_cut", "gap_min", "gap_max", "merge_passes", "min_track", "fit_passes", "ns_min_dip",
+                  "search_all"):
             setattr(p, k, int(getattr(self, k)))
         p.bz, p.sigma_y, p.sigma_z = self.bz, self.sigma_y, self.sigma_z
         for i in range(5):

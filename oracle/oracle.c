@@ -13,6 +13,10 @@
  * brute force over all candidate pairs, mutual links and chains, integer
  * segment merge, and the FP64 Kalman helix fit.  Integers are exact; the fit is
  * double precision.  No blocking, fusion or reordering beyond the definition.
+ * The CA and merge searches visit candidates in the definition's order but skip
+ * index ranges that a bound proves are rejected (a candidate window in time
+ * bins, see ca_time_window and the merge); search_all = 1 visits every
+ * candidate, and the tests check that the two give identical results.
  *
  * Pins (tests, not this file): ZS round trip, peak finder against a 3x3
  * maximum filter, centroid closed forms, CA special cases and hand-worked
@@ -46,6 +50,7 @@ typedef struct {
   int32_t ns_min_dip;   /* 5x5 noise suppression: 0 off, else the minimum dip in ADC */
   double bz, sigma_y, sigma_z;
   double c0[5];
+  int32_t search_all;   /* 1: CA and merge visit every candidate (no window) */
 } orc_params;
 
 /* 16-byte cluster record, field for field as documented by the library. */
@@ -295,6 +300,25 @@ void orc_coords(const orc_input* in, const orc_cluster* c, int64_t* X, int64_t* 
 }
 
 /* ------------------------------------------------------------ 5-6. CA */
+/* First index i in [lo, hi) whose cluster has t_peak >= t (clusters of one
+ * (sector, row) are in (t_peak, pad) order); hi if none. */
+static int64_t first_t_at_least(const orc_cluster* cl, int64_t lo, int64_t hi, int64_t t) {
+  while (lo < hi) {
+    int64_t mid = lo + (hi - lo) / 2;
+    if ((int64_t)cl[mid].t_peak < t) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+/* Time-bin half width of the CA candidate window between rows dX apart.  Step
+ * 4 gives Z = 640 t_peak + 5 R(128 St, Q) with |St| <= 2 Q, so |5 R| <= 1280 and
+ * |Z_c - Z_d| >= 640 |t_c - t_d| - 2560.  A candidate passing the window test
+ * |Z_c - Z_d| sz_den <= sz_num dX thus has |t_c - t_d| <= (sz_num dX / sz_den +
+ * 2560) / 640; one bin more is kept for safety. */
+static int64_t ca_time_window(const orc_params* P, int64_t dx) {
+  return ((int64_t)P->sz_num * dx / P->sz_den + 2560) / 640 + 1;
+}
+
 /* up / down / best score for every cluster by brute force over all (d, u) pairs,
  * then mutual links and chains.  chain_of[c] = index of the lowest cluster of
  * the chain holding c if that chain has >= min_chain clusters, else -1. */
@@ -312,13 +336,22 @@ int orc_ca(const orc_input* in, const orc_params* P, const orc_cluster* cl, int6
   for (int s = 0; s < in->n_sectors; s++)
     for (int r = 1; r <= R - 2; r++) {
       int64_t bc = (int64_t)s * R + r;
+      const int64_t wd = ca_time_window(P, 64 * ((int64_t)in->row_x[r] - in->row_x[r - 1]));
+      const int64_t wu = ca_time_window(P, 64 * ((int64_t)in->row_x[r + 1] - in->row_x[r]));
       for (int64_t c = rs[bc]; c < rs[bc + 1]; c++) {
         int64_t best = -1, bd = -1, bu = -1;
-        for (int64_t d = rs[bc - 1]; d < rs[bc]; d++) {
+        int64_t d_lo = rs[bc - 1], d_hi = rs[bc], u_lo = rs[bc + 1], u_hi = rs[bc + 2];
+        if (!P->search_all) {
+          d_lo = first_t_at_least(cl, d_lo, d_hi, (int64_t)cl[c].t_peak - wd);
+          d_hi = first_t_at_least(cl, d_lo, d_hi, (int64_t)cl[c].t_peak + wd + 1);
+          u_lo = first_t_at_least(cl, u_lo, u_hi, (int64_t)cl[c].t_peak - wu);
+          u_hi = first_t_at_least(cl, u_lo, u_hi, (int64_t)cl[c].t_peak + wu + 1);
+        }
+        for (int64_t d = d_lo; d < d_hi; d++) {
           int64_t dxd = X[c] - X[d];
           if (iabs64(Y[c] - Y[d]) * P->sy_den > (int64_t)P->sy_num * dxd) continue;
           if (iabs64(Z[c] - Z[d]) * P->sz_den > (int64_t)P->sz_num * dxd) continue;
-          for (int64_t u = rs[bc + 1]; u < rs[bc + 2]; u++) {
+          for (int64_t u = u_lo; u < u_hi; u++) {
             int64_t dxu = X[u] - X[c];
             if (iabs64(Y[u] - Y[c]) * P->sy_den > (int64_t)P->sy_num * dxu) continue;
             if (iabs64(Z[u] - Z[c]) * P->sz_den > (int64_t)P->sz_num * dxu) continue;
@@ -335,25 +368,28 @@ int orc_ca(const orc_input* in, const orc_params* P, const orc_cluster* cl, int6
       }
       (void)0;
     }
-  /* edge rows */
+  /* edge rows: up[d] for d on row 0 is the c on row 1 with down[c] = d and
+   * the smallest score (c ascending, strict <: ties to the smallest c); the
+   * last row mirrors it.  One pass over the c's of row 1 (row R-2) finds it
+   * for every d (u) at once. */
+  int64_t* edge_best = (int64_t*)malloc(sizeof(int64_t) * (n + 1));
   for (int s = 0; s < in->n_sectors; s++) {
     int64_t b0 = (int64_t)s * R, b1 = b0 + 1;
-    for (int64_t d = rs[b0]; d < rs[b0 + 1]; d++) {
-      int64_t best = -1, arg = -1;
-      for (int64_t c = rs[b1]; c < rs[b1 + 1]; c++)
-        if (down[c] == d && (best < 0 || score[c] < best)) { best = score[c]; arg = c; }
-      up[d] = (int32_t)arg;
-      down[d] = -1;
+    for (int64_t d = rs[b0]; d < rs[b0 + 1]; d++) { up[d] = -1; edge_best[d] = -1; }
+    for (int64_t c = rs[b1]; c < rs[b1 + 1]; c++) {
+      int64_t d = down[c];
+      if (d >= 0 && (edge_best[d] < 0 || score[c] < edge_best[d])) { edge_best[d] = score[c]; up[d] = (int32_t)c; }
     }
+    for (int64_t d = rs[b0]; d < rs[b0 + 1]; d++) down[d] = -1;
     int64_t bl = (int64_t)s * R + R - 1, bm = bl - 1;
-    for (int64_t u = rs[bl]; u < rs[bl + 1]; u++) {
-      int64_t best = -1, arg = -1;
-      for (int64_t c = rs[bm]; c < rs[bm + 1]; c++)
-        if (up[c] == u && (best < 0 || score[c] < best)) { best = score[c]; arg = c; }
-      down[u] = (int32_t)arg;
-      up[u] = -1;
+    for (int64_t u = rs[bl]; u < rs[bl + 1]; u++) { down[u] = -1; edge_best[u] = -1; }
+    for (int64_t c = rs[bm]; c < rs[bm + 1]; c++) {
+      int64_t u = up[c];
+      if (u >= 0 && (edge_best[u] < 0 || score[c] < edge_best[u])) { edge_best[u] = score[c]; down[u] = (int32_t)c; }
     }
+    for (int64_t u = rs[bl]; u < rs[bl + 1]; u++) up[u] = -1;
   }
+  free(edge_best);
   /* links and chains */
   for (int64_t i = 0; i < n; i++) chain_of[i] = -1;
   for (int64_t c = 0; c < n; c++) {
@@ -411,9 +447,14 @@ int64_t orc_merge(const orc_input* in, const orc_params* P, const orc_cluster* c
       for (int64_t i = 0; i < len; i++) { ch[k].cl[i] = cur; if (i + 1 < len) cur = up[cur]; }
       k++;
     }
-  int64_t* sec_lo = (int64_t*)calloc((size_t)in->n_sectors + 2, sizeof(int64_t));
-  for (int64_t i = 0; i < nch; i++) sec_lo[cl[ch[i].root].sector + 1]++;
-  for (int s = 0; s < in->n_sectors; s++) sec_lo[s + 1] += sec_lo[s];
+  /* chains are in id order, hence grouped by (sector, row of the root) and,
+   * within one, in (t_peak, pad) order of the root: crs[s R + r] is the first
+   * chain whose root lies in (sector s, row r) or later */
+  const int R = in->n_rows;
+  const int64_t nsr = (int64_t)in->n_sectors * R;
+  int64_t* crs = (int64_t*)calloc((size_t)nsr + 1, sizeof(int64_t));
+  for (int64_t i = 0; i < nch; i++) crs[(int64_t)cl[ch[i].root].sector * R + cl[ch[i].root].row + 1]++;
+  for (int64_t b = 0; b < nsr; b++) crs[b + 1] += crs[b];
   int64_t* bestB = (int64_t*)malloc(sizeof(int64_t) * (nch + 1));
   int64_t* bestBs = (int64_t*)malloc(sizeof(int64_t) * (nch + 1));
   int64_t* bestA = (int64_t*)malloc(sizeof(int64_t) * (nch + 1));
@@ -424,24 +465,55 @@ int64_t orc_merge(const orc_input* in, const orc_params* P, const orc_cluster* c
     for (int64_t a = 0; a < nch; a++) {
       if (ch[a].next >= 0) continue;                 /* not a top end */
       int64_t a2 = ch[a].cl[ch[a].len - 1], a1 = ch[a].cl[ch[a].len - 2];
-      /* chains are in id order, hence grouped by sector: scan only a2's sector */
-      for (int64_t b = sec_lo[cl[a2].sector]; b < sec_lo[cl[a2].sector + 1]; b++) {
-        if (ch[b].prev >= 0) continue;               /* not a bottom end */
-        int64_t b1 = ch[b].cl[0], b2 = ch[b].cl[1];
-        if (cl[b1].sector != cl[a2].sector) continue;
-        int gap = (int)cl[b1].row - (int)cl[a2].row;
-        if (gap < P->gap_min || gap > P->gap_max) continue;
-        int64_t ry = extrap_res(X[a1], Y[a1], X[a2], Y[a2], X[b1], Y[b1]);
-        int64_t rz = extrap_res(X[a1], Z[a1], X[a2], Z[a2], X[b1], Z[b1]);
-        int64_t sy = extrap_res(X[b2], Y[b2], X[b1], Y[b1], X[a2], Y[a2]);
-        int64_t sz = extrap_res(X[b2], Z[b2], X[b1], Z[b1], X[a2], Z[a2]);
-        if (iabs64(ry) > P->merge_cut || iabs64(rz) > P->merge_cut || iabs64(sy) > P->merge_cut ||
-            iabs64(sz) > P->merge_cut)
-          continue;
-        int64_t sc = ry * ry + rz * rz + sy * sy + sz * sz;
-        /* ties to the lower chain id: chains are visited in id order, strict < */
-        if (bestB[a] < 0 || sc < bestBs[a]) { bestB[a] = b; bestBs[a] = sc; }
-        if (bestA[b] < 0 || sc < bestAs[b]) { bestA[b] = a; bestAs[b] = sc; }
+      /* candidate bottoms b1 lie in a2's sector, gap_min..gap_max rows above
+       * a2: those chains form one id range.  The forward residual bounds b1's
+       * time: |trunc(n / dX_a)| <= cut needs |Z_b1 - Zp| < cut + 1, Zp the line
+       * (a1, a2) at X_b1, and Z = 640 t_peak + 5 R with |5 R| <= 1280 (see
+       * ca_time_window), so only roots with t_peak within that band (one bin
+       * of margin) can pass; within a row they are one id range.  Visiting the
+       * rows in ascending order keeps the chains in id order. */
+      const int sa = cl[a2].sector, ra = cl[a2].row;
+      int r_lo = ra + P->gap_min, r_hi = ra + P->gap_max;
+      if (r_hi > R - 1) r_hi = R - 1;
+      if (P->search_all) { r_lo = 0; r_hi = R - 1; }
+      for (int rb = r_lo; rb <= r_hi; rb++) {
+        int64_t b_lo = crs[(int64_t)sa * R + rb], b_hi = crs[(int64_t)sa * R + rb + 1];
+        if (!P->search_all) {
+          const double xb = 64.0 * in->row_x[rb];
+          const double zp = (double)Z[a2] + (double)(Z[a2] - Z[a1]) * (xb - (double)X[a2]) / (double)(X[a2] - X[a1]);
+          const int64_t t_lo = (int64_t)floor((zp - P->merge_cut - 1 - 1280.0) / 640.0) - 1;
+          const int64_t t_hi = (int64_t)ceil((zp + P->merge_cut + 1 + 1280.0) / 640.0) + 1;
+          int64_t lo = b_lo, hi = b_hi;
+          while (lo < hi) {                            /* first root with t_peak >= t_lo */
+            int64_t mid = lo + (hi - lo) / 2;
+            if ((int64_t)cl[ch[mid].root].t_peak < t_lo) lo = mid + 1; else hi = mid;
+          }
+          b_lo = lo;
+          hi = b_hi;
+          while (lo < hi) {                            /* first root with t_peak > t_hi */
+            int64_t mid = lo + (hi - lo) / 2;
+            if ((int64_t)cl[ch[mid].root].t_peak <= t_hi) lo = mid + 1; else hi = mid;
+          }
+          b_hi = lo;
+        }
+        for (int64_t b = b_lo; b < b_hi; b++) {
+          if (ch[b].prev >= 0) continue;               /* not a bottom end */
+          int64_t b1 = ch[b].cl[0], b2 = ch[b].cl[1];
+          if (cl[b1].sector != cl[a2].sector) continue;
+          int gap = (int)cl[b1].row - (int)cl[a2].row;
+          if (gap < P->gap_min || gap > P->gap_max) continue;
+          int64_t ry = extrap_res(X[a1], Y[a1], X[a2], Y[a2], X[b1], Y[b1]);
+          int64_t rz = extrap_res(X[a1], Z[a1], X[a2], Z[a2], X[b1], Z[b1]);
+          int64_t sy = extrap_res(X[b2], Y[b2], X[b1], Y[b1], X[a2], Y[a2]);
+          int64_t sz = extrap_res(X[b2], Z[b2], X[b1], Z[b1], X[a2], Z[a2]);
+          if (iabs64(ry) > P->merge_cut || iabs64(rz) > P->merge_cut || iabs64(sy) > P->merge_cut ||
+              iabs64(sz) > P->merge_cut)
+            continue;
+          int64_t sc = ry * ry + rz * rz + sy * sy + sz * sz;
+          /* ties to the lower chain id: chains are visited in id order, strict < */
+          if (bestB[a] < 0 || sc < bestBs[a]) { bestB[a] = b; bestBs[a] = sc; }
+          if (bestA[b] < 0 || sc < bestAs[b]) { bestA[b] = a; bestAs[b] = sc; }
+        }
       }
     }
     int any = 0;
@@ -466,7 +538,7 @@ int64_t orc_merge(const orc_input* in, const orc_params* P, const orc_cluster* c
   }
   if (passes_merged) *passes_merged = merged_passes;
   for (int64_t i = 0; i < nch; i++) free(ch[i].cl);
-  free(sec_lo); free(ch); free(bestB); free(bestBs); free(bestA); free(bestAs); free(X); free(Y); free(Z);
+  free(crs); free(ch); free(bestB); free(bestBs); free(bestA); free(bestAs); free(X); free(Y); free(Z);
   return ntr;
 }
 

@@ -36,7 +36,7 @@ def _worker(rank, world, port, out):
 
 def test_job_totals_over_two_gloo_ranks():
     import torch.multiprocessing as mp
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()   # never fork: the process may hold a CUDA context
     out = mgr.dict()
     mp.spawn(_worker, args=(2, free_port(), out), nprocs=2, join=True)
     for r in range(2):

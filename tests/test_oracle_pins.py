@@ -12,7 +12,7 @@ from scipy import ndimage
 
 import oracle
 import tpcgen
-from synth import Geom, U_CM, helix_points, make_clusters
+from synth import Geom, U_CM, encode_planes, helix_points, make_clusters
 
 
 # ---------------------------------------------------------------- geometry
@@ -27,77 +27,13 @@ def test_geometry_closed_forms():
 
 
 # ---------------------------------------------------------------- ZS
-def _encode_independent(planes, n_time_bins):
-    """Re-encode dense planes [s, r, t, p] to the documented page format."""
-    out = bytearray()
-    offs = []
-    S, R, T, _ = planes.shape
-    npads, _ = tpcgen.default_geometry()
-    nf = (n_time_bins + 255) // 256
-    for s in range(S):
-        for r in range(R):
-            np_ = int(npads[r])
-            for f in range(nf):
-                ents, runs, adcs = [], [], []
-                lo = hi = None
-                for tt in range(256):
-                    t = 256 * f + tt
-                    if tt == 253 and hi is None:
-                        hi = (len(ents), len(runs), len(adcs))
-                    if t < n_time_bins:
-                        row = planes[s, r, t, :np_]
-                        nz = np.nonzero(row)[0]
-                        if len(nz):
-                            # maximal runs of consecutive pads
-                            splits = np.nonzero(np.diff(nz) > 1)[0] + 1
-                            groups = np.split(nz, splits)
-                            ents.append((tt, len(groups)))
-                            for g in groups:
-                                runs.append((int(g[0]), len(g)))
-                                adcs.extend(int(v) for v in row[g])
-                    if tt == 2:
-                        lo = (len(ents), len(runs), len(adcs))
-                if hi is None:
-                    hi = (len(ents), len(runs), len(adcs))
-                body = 32 + 2 * len(ents) + 2 * len(runs)
-                body = (body + 3) // 4 * 4
-                nw = (len(adcs) + 2) // 3
-                ln = (body + 4 * nw + 15) // 16 * 16
-                pg = bytearray(ln)
-                pg[0:4] = ln.to_bytes(4, "little")
-                pg[4:6] = len(ents).to_bytes(2, "little")
-                pg[6:8] = len(runs).to_bytes(2, "little")
-                pg[8:10] = len(adcs).to_bytes(2, "little")
-                pg[10], pg[11] = s, r
-                pg[12:14] = f.to_bytes(2, "little")
-                pg[14:16] = (0x5A53).to_bytes(2, "little")
-                for i, v in enumerate(lo + hi):
-                    pg[16 + 2 * i:18 + 2 * i] = v.to_bytes(2, "little")
-                o = 32
-                for (t, n) in ents:
-                    pg[o], pg[o + 1] = t, n
-                    o += 2
-                for (p, n) in runs:
-                    pg[o], pg[o + 1] = p, n
-                    o += 2
-                for w in range(nw):
-                    word = 0
-                    for k in range(3):
-                        if 3 * w + k < len(adcs):
-                            word |= adcs[3 * w + k] << (10 * k)
-                    pg[body + 4 * w:body + 4 * w + 4] = word.to_bytes(4, "little")
-                offs.append(len(out))
-                out += pg
-    return np.frombuffer(bytes(out), np.uint8), np.array(offs, np.uint64)
-
-
 def test_zs_round_trip():
     cfg = tpcgen.single_sector(3, n_tracks=20, n_time_bins=300)
     tf = tpcgen.generate(cfg)
     planes = oracle.decode_all(tf)
     assert int((planes > 0).sum()) == tf.n_digits == len(tf.digit_labels)
     assert planes.max() <= 1023 and planes[planes > 0].min() >= 3
-    pages, offs = _encode_independent(planes, tf.n_time_bins)
+    pages, offs = encode_planes(planes, tf.n_time_bins)
     assert np.array_equal(offs, tf.page_offsets)
     assert np.array_equal(pages, tf.pages)
 
