@@ -36,28 +36,33 @@ import tpcgen  # noqa: E402
 
 METRIC = "TPC clusters/s & tracks/s per B300; timeframe p50/p99 latency, batched vs plain"
 WORKLOADS = {
-    "full_tpc": (lambda seed: tpcgen.full_tpc(seed),
+    "full_tpc": (lambda seed, bins=0: tpcgen.full_tpc(seed),
                  "full_tpc: 36 sectors x 152 rows (66-138 pads), 1000 time bins, 10,000 tracks "
                  "(5% loopers) from one vertex, Bz 0.5 T, Landau(60) Gaussian clouds, noise 1 ADC, ZS >= 3"),
-    "single_sector": (lambda seed: tpcgen.single_sector(seed),
+    "single_sector": (lambda seed, bins=0: tpcgen.single_sector(seed),
                       "single_sector: 1 sector x 152 rows, 500 time bins, 150 tracks"),
-    "continuous_50khz": (lambda seed, bins=55000: tpcgen.continuous_tf(seed, n_time_bins=bins),
+    "continuous_50khz": (lambda seed, bins=0: tpcgen.continuous_tf(seed, n_time_bins=bins or 55000),
                          "continuous_50khz: 36 sectors x 152 rows, 55,000 time bins (11 ms at 5 MHz), "
                          "Poisson(550) Pb-Pb-like collisions at uniform start times, multiplicity "
                          "floor(15000 U^7.82) (mean ~1,700), 5% loopers, same charge/noise/ZS model"),
 }
 REF_SAMPLE_BYTES = 20 << 20
-# DRAM bytes (read + write) of one finder stage (k_find_classify, k_find_light
-# and k_find_clusters, summed), from an ncu capture of the current kernels on the
-# workload (seed 1), keyed by (workload, block finder threads); absent where no
-# capture exists.  Must be cleared whenever a finder kernel changes.
-FINDER_DRAM_BYTES = {("full_tpc", 512): 87284480 + 2501376, ("full_tpc", 384): 87140096 + 2155264}
-# Warp instructions (smsp__inst_executed.sum) of the same kernels, for the issue
-# roofline; reset together with FINDER_DRAM_BYTES.
-FINDER_WARP_INSTR = {("full_tpc", 512): 514128571, ("full_tpc", 384): 467540997}
+# ncu counters of one find stage (its kernels summed: decode, find units, scan
+# and compaction for the two-pass finder): DRAM bytes read + written and warp
+# instructions (smsp__inst_executed.sum), from a capture of the current kernels,
+# keyed by (workload, finder, finder threads), with the ZS bytes of the captured case.  The
+# 55,000-bin continuous timeframe (5.7 GB) is beyond a capture's size, so its
+# figures are those of the first 11,000 bins of the same timeframe scaled by
+# the ZS bytes (the stage's traffic and instructions grow with the pages and
+# clusters).  Must be cleared whenever a finder kernel changes.
+FINDER_COUNTERS = {}
 # Warp-instruction issue peak: 148 SMs x 4 schedulers x 1 instruction per cycle
 # at the 2032 MHz maximum SM clock.
 ISSUE_PEAK = 148 * 4 * 2.032e9
+# FP32 peak from the unit counts: 148 SMs x 128 FP32 lanes x 2 FLOP per FMA x 2032 MHz.
+FP32_NOMINAL = 148 * 128 * 2 * 2.032e9
+# Algorithmic FLOP of the step-8 fit per cluster on a track: ~400 per pass x 3 passes.
+FIT_FLOP_PER_CLUSTER = 1200
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -530,41 +535,53 @@ def calibration_stats(tpc, R, pages_d, offs_d, tf, reps=5):
             "timing": f"host wall clock of the call, median of {reps}"}
 
 
-def finder_variants(tpc, torch, tf, pages_d, offs_d, tuning, flush, fused_ms, reps=5):
-    """The measured variant pair of steps 1-4: the default fused finder (each
-    window's pages decoded straight into shared memory) against the dense-plane
-    finder (a decode pass writes a dense (sector row, time bin, pad) ADC plane
-    to device memory, a find pass reads it back).  Find-stage time from the
-    library's stage events, L2 flushed before each step, the same tuning."""
+def finder_variants(tpc, torch, tf, pages_d, offs_d, flush, main_ms, reps=5):
+    """The measured variants of steps 1-4 beside the default two-pass finder
+    (pages decoded into 4-byte digit words in device memory, then each 64-bin
+    time chunk of a window clustered in a small shared plane): the fused
+    finder (each window's pages decoded straight into a shared plane of the
+    whole window) and the dense-plane finder (a decode pass writes a dense
+    (sector row, time bin, pad) ADC plane to device memory, a find pass reads it
+    back).  Find-stage time from the library's stage events, L2 flushed before
+    each step, each variant with its own autotuned launch shape."""
     stride = (int(tf.npads.max()) + 7) & ~7
     plane = tf.n_sectors * len(tf.npads) * tf.n_time_bins * stride * 2
     n_frag = (tf.n_time_bins + 255) // 256
     alloc = tf.n_sectors * len(tf.npads) * n_frag * 256 * stride * 2
-    free_now, _ = torch.cuda.mem_get_info()
-    Rd = tpc.Reconstructor.for_timeframe(tf, device=torch.cuda.current_device(),
-                                         flags=tpc.TPC_CTX_STAGE_TIMING | tpc.TPC_CTX_DENSE_FINDER,
-                                         mem_budget=int(0.9 * free_now))
-    tpc.tpc_set_tuning(Rd.ctx, **tuning)
-    times = []
-    try:
-        for i in range(reps + 2):
-            flush.fill_(1)
-            t = Rd.submit(pages_d, offs_d, tf.n_time_bins)
-            Rd.wait(t)
-            if i >= 2:
-                times.append(tpc.tpc_get_stage_times(Rd.ctx, t)["find"])
-            tpc.tpc_release(Rd.ctx, t)
-    except tpc.TpcError as e:   # the plane and a slot do not fit the free memory
-        return {"skipped": f"the dense plane ({alloc / 1e9:.1f} GB) with a slot does not fit: {e}"}
-    finally:
-        Rd.close()
-    dense_ms = statistics.mean(times)
-    # algorithmic bytes of the dense pair: the pages once, the plane written
-    # once and read once (+6 halo rows per 256-bin window)
-    dense_bytes = tf.pages.nbytes + plane + plane * (262 / 256)
-    return {"fused_find_ms": fused_ms, "dense_find_ms": dense_ms, "dense_over_fused": dense_ms / fused_ms,
-            "dense_plane_bytes": int(plane), "dense_algorithmic_gbs": dense_bytes / (dense_ms * 1e-3) / 1e9,
-            "timing": f"find stage (decode + find + scan + compaction), mean of {reps}, L2 flushed"}
+    out = {"two_pass_find_ms": main_ms}
+    for name, flag in (("fused", tpc.TPC_CTX_FUSED_FINDER), ("dense", tpc.TPC_CTX_DENSE_FINDER)):
+        free_now, _ = torch.cuda.mem_get_info()
+        times = []
+        try:
+            Rv = tpc.Reconstructor.for_timeframe(tf, device=torch.cuda.current_device(),
+                                                 flags=tpc.TPC_CTX_STAGE_TIMING | flag, mem_budget=int(0.9 * free_now))
+        except tpc.TpcError as e:
+            out[f"{name}_skipped"] = str(e)
+            continue
+        try:
+            tpc.tpc_autotune(Rv.ctx, pages_d, offs_d, tf.n_time_bins, reps=2)
+            for i in range(reps + 2):
+                flush.fill_(1)
+                t = Rv.submit(pages_d, offs_d, tf.n_time_bins)
+                Rv.wait(t)
+                if i >= 2:
+                    times.append(tpc.tpc_get_stage_times(Rv.ctx, t)["find"])
+                tpc.tpc_release(Rv.ctx, t)
+        except tpc.TpcError as e:   # the dense plane and a slot do not fit the free memory
+            out[f"{name}_skipped"] = f"{alloc / 1e9:.1f} GB dense plane or slot does not fit: {e}"
+            continue
+        finally:
+            Rv.close()
+        out[f"{name}_find_ms"] = statistics.mean(times)
+        out[f"{name}_over_two_pass"] = statistics.mean(times) / main_ms
+    if "dense_find_ms" in out:
+        # algorithmic bytes of the dense pair: the pages once, the plane written
+        # once and read once (+6 halo rows per 256-bin window)
+        dense_bytes = tf.pages.nbytes + plane + plane * (262 / 256)
+        out["dense_plane_bytes"] = int(plane)
+        out["dense_algorithmic_gbs"] = dense_bytes / (out["dense_find_ms"] * 1e-3) / 1e9
+    out["timing"] = f"find stage (decode + find + scan + compaction), mean of {reps}, L2 flushed"
+    return out
 
 
 def noise_suppression_stats(tpc, torch, tf, pages_d, offs_d, tuning, flush, n_cl, fused_ms, dip=10, reps=5):
@@ -591,6 +608,103 @@ def noise_suppression_stats(tpc, torch, tf, pages_d, offs_d, tuning, flush, n_cl
             "find_ms_without": fused_ms, "timing": f"find stage, mean of {reps}, L2 flushed"}
 
 
+FINDER_KERNELS = {"two_pass": "find stage: k_decode_digits + k_find_units + k_scan + k_compact_clusters",
+                  "fused": "find stage: k_find_classify + k_find_light + k_find_clusters + k_scan + k_compact_clusters",
+                  "dense": "find stage: k_find_clusters (dense-plane decode and find passes) + k_scan + "
+                           "k_compact_clusters"}
+
+
+def finder_roofline(tf, n_cl, find_ms, find_threads, workload, seed, time_bins, finder, hbm, peak_kind):
+    """HBM roofline of the find stage (algorithmic bytes: ZS pages + 8 B page
+    offset per window + 16 B per cluster record, over the stage's CUDA-event
+    time) and its issue roofline, with the ncu traffic of a capture of the
+    current kernels where one exists (scaled by ZS bytes from the captured
+    case), else null."""
+    n_windows = len(tf.page_offsets)
+    alg_bytes = tf.pages.nbytes + 8 * n_windows + 16 * n_cl
+    if finder == "dense":   # + the dense plane written once and read once (with 6 halo rows per window)
+        plane = tf.n_sectors * len(tf.npads) * tf.n_time_bins * ((int(tf.npads.max()) + 7) & ~7) * 2
+        alg_bytes += plane + plane * 262 // 256
+    achieved = alg_bytes / (find_ms * 1e-3) / 1e9
+    cap = None
+    if seed == 1 and (workload == "full_tpc" or (workload == "continuous_50khz" and not time_bins)):
+        cap = FINDER_COUNTERS.get((workload, finder, int(find_threads)))
+    scale = tf.pages.nbytes / cap["zs"] if cap else None
+    kernel = FINDER_KERNELS[finder]
+    roof = {"kernel": kernel, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm, "traffic": int(cap["dram"] * scale) if cap else None,
+            "peak_kind": f"{peak_kind} hbm_gbs (copy)", "algorithmic_bytes_per_launch": int(alg_bytes)}
+    issue = None
+    if cap:
+        ins = cap["instr"] * scale
+        issue = {"kernel": kernel, "bound": "issue", "achieved": ins / (find_ms * 1e-3), "peak": ISSUE_PEAK,
+                 "unit": "warp-instr/s", "frac": ins / (find_ms * 1e-3) / ISSUE_PEAK,
+                 "instructions": "ncu smsp__inst_executed.sum of one launch" +
+                                 (", scaled by ZS bytes from the captured case" if scale != 1.0 else ""),
+                 "peak_kind": "148 SMs x 4 schedulers x 2032 MHz"}
+    return roof, issue
+
+
+def fit_roofline(n_cl_on_tracks, fit_ms, fma_peak):
+    """ALU roofline of the step-8 fit: algorithmic FLOP (1,200 per cluster on a
+    track) over the fit stage's CUDA-event time, against the measured FP32 FMA
+    peak (and the nominal one from the unit counts)."""
+    flops = FIT_FLOP_PER_CLUSTER * n_cl_on_tracks
+    achieved = flops / (fit_ms * 1e-3) / 1e12
+    peak = (fma_peak or FP32_NOMINAL) / 1e12
+    return {"kernel": "k_fit", "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "algorithmic_flop_per_launch": int(flops),
+            "flop_per_cluster": FIT_FLOP_PER_CLUSTER, "nominal_peak": FP32_NOMINAL / 1e12,
+            "peak_kind": "measured FP32 FMA probe (tpc_measure_fma_peak)" if fma_peak else
+                         "nominal 148 SMs x 128 lanes x 2 x 2032 MHz"}
+
+
+def extra_workload(tpc, torch, local, name, seed, steps, warmup, flush, hbm, peak_kind, fma_peak):
+    """A second workload measured like the main one (device-resident pages, L2
+    flushed before every step, CUDA events on the library's stream, the
+    autotuner's configuration): clusters/s, tracks/s, latency, stages and
+    rooflines."""
+    make, desc = WORKLOADS[name]
+    tf = tpcgen.generate(make(seed))
+    stream = torch.cuda.Stream()
+    free_b, _ = torch.cuda.mem_get_info()
+    R = tpc.Reconstructor.for_timeframe(tf, device=local, stream=stream.cuda_stream, flags=tpc.TPC_CTX_STAGE_TIMING,
+                                        mem_budget=int(min(free_b * 0.5, max(16 << 30, 40 * tf.pages.nbytes))))
+    try:
+        pages_d = torch.from_numpy(tf.pages).to("cuda")
+        offs_d = torch.from_numpy(tf.page_offsets.view(np.int64)).to("cuda")
+        torch.cuda.synchronize()
+        tuning = tpc.tpc_autotune(R.ctx, pages_d, offs_d, tf.n_time_bins, reps=3)
+        recs = []
+        for i in range(warmup + steps):
+            flush.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            t = R.submit(pages_d, offs_d, tf.n_time_bins)
+            e1.record(stream)
+            R.wait(t)
+            if i >= warmup:
+                recs.append((e0, e1, tpc.tpc_get_counters(R.ctx, t), tpc.tpc_get_stage_times(R.ctx, t)))
+            tpc.tpc_release(R.ctx, t)
+    finally:
+        R.close()
+    step_ms = [a.elapsed_time(b) for a, b, _, _ in recs]
+    ctr = recs[-1][2]
+    stages = {k: statistics.mean(r[3][k] for r in recs) for k in tpc.STAGES}
+    t_s = sum(step_ms) / 1e3
+    roof, issue = finder_roofline(tf, ctr["clusters"], stages["find"], tuning["find_threads"], name, seed, 0,
+                                  "two_pass", hbm, peak_kind)
+    return {"workload": desc, "seed": seed, "zs_bytes": int(tf.pages.nbytes), "clusters_per_tf": ctr["clusters"],
+            "tracks_per_tf": ctr["tracks"], "clusters_per_s": ctr["clusters"] * steps / t_s,
+            "tracks_per_s": ctr["tracks"] * steps / t_s, "ms_per_step": 1e3 * t_s / steps,
+            "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
+            "stages_ms": stages, "roofline": roof, "roofline_issue": issue,
+            "roofline_fit": fit_roofline(ctr["clusters_on_tracks"], stages["fit"], fma_peak),
+            "tuning": tuning, "steps": steps, "warmup": warmup,
+            "timing": "CUDA events on the library's stream, L2 flushed before every step"}
+
+
 def run_ours(args, world, rank, local):
     import torch
     from paper_2208_07412_b300 import tpc
@@ -608,7 +722,7 @@ def run_ours(args, world, rank, local):
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     flags = tpc.TPC_CTX_STAGE_TIMING | (tpc.TPC_CTX_NO_GRAPHS if args.no_graphs else 0) | \
-        (tpc.TPC_CTX_DENSE_FINDER if args.dense_finder else 0)
+        (tpc.TPC_CTX_DENSE_FINDER if args.dense_finder else 0) | (tpc.TPC_CTX_FUSED_FINDER if args.fused_finder else 0)
     # device memory for one slot: the pages, ~150 B per cluster of capacity
     # (pages/12 clusters) and the rest; the budget is what the GPU has free
     free_b, _ = torch.cuda.mem_get_info()
@@ -696,7 +810,7 @@ def run_ours(args, world, rank, local):
     # submit queues and the loop degrades to one timeframe at a time)
     free_now, _ = torch.cuda.mem_get_info()
     depth = 3
-    Rp = tpc.Reconstructor.for_timeframe(tf, device=local, flags=tpc.TPC_CTX_DENSE_FINDER if args.dense_finder else 0,
+    Rp = tpc.Reconstructor.for_timeframe(tf, device=local, flags=flags & ~tpc.TPC_CTX_STAGE_TIMING,
                                          mem_budget=int(free_now * 0.85), n_slots=depth)
     tpc.tpc_set_tuning(Rp.ctx, **tuning)
 
@@ -728,13 +842,14 @@ def run_ours(args, world, rank, local):
     if rank == 0:
         peaks, peak_kind = load_peaks()
         hbm = float(peaks["hbm_gbs"])
-        n_windows = len(tf.page_offsets)
-        alg_bytes = tf.pages.nbytes + 8 * n_windows + 16 * n_cl
-        if args.dense_finder:   # + the dense plane written once and read once (with 6 halo rows per window)
-            plane = tf.n_sectors * len(tf.npads) * tf.n_time_bins * ((int(tf.npads.max()) + 7) & ~7) * 2
-            alg_bytes += plane + plane * 262 // 256
-        achieved = alg_bytes / (stages["find"] * 1e-3) / 1e9
-        counter_key = (args.workload, int(tuning["find_threads"]))
+        finder = "dense" if args.dense_finder else ("fused" if args.fused_finder else "two_pass")
+        roof, issue = finder_roofline(tf, n_cl, stages["find"], tuning["find_threads"], args.workload, args.seed,
+                                      args.time_bins, finder, hbm, peak_kind)
+        fma_peak = None
+        try:
+            fma_peak = tpc.tpc_measure_fma_peak(local, 5)
+        except tpc.TpcError:
+            pass
         line = {
             "metric": METRIC, "value": cl_all / dev_s_max, "unit": "clusters/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dev_s_max / args.steps,
@@ -746,28 +861,16 @@ def run_ours(args, world, rank, local):
                        "tuning": {"autotuned": not (args.no_autotune or args.tuning), **tuning},
                        "path": ("plain per-timeframe kernel launches" if args.no_graphs
                                 else "per-timeframe pipeline replayed from a captured CUDA graph"),
-                       "finder": "dense-plane variant" if args.dense_finder else "fused"},
+                       "finder": ("dense-plane variant" if args.dense_finder else
+                                  "fused variant" if args.fused_finder else "two-pass")},
             "tracks_per_s": tr_all / dev_s_max,
             "fp64_redos_per_tf": int(ctr["fp64_redos"]),
             "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
             "stages_ms": stages,
             "wall_ms_per_step": 1e3 * wall / args.steps,
-            "roofline": {"kernel": "find stage: k_find_classify + k_find_light + k_find_clusters",
-                         "bound": "hbm", "achieved": achieved, "peak": hbm,
-                         "unit": "GB/s", "frac": achieved / hbm,
-                         "traffic": (FINDER_DRAM_BYTES.get(counter_key)
-                                     if args.seed == 1 and not args.time_bins and not args.dense_finder else None),
-                         "peak_kind": f"{peak_kind} hbm_gbs (copy)",
-                         "algorithmic_bytes_per_launch": int(alg_bytes)},
-            "roofline_issue": (None if not (args.seed == 1 and not args.time_bins and not args.dense_finder
-                                            and counter_key in FINDER_WARP_INSTR) else
-                               {"kernel": "find stage: k_find_classify + k_find_light + k_find_clusters",
-                                "bound": "issue",
-                                "achieved": FINDER_WARP_INSTR[counter_key] / (stages["find"] * 1e-3),
-                                "peak": ISSUE_PEAK, "unit": "warp-instr/s",
-                                "frac": FINDER_WARP_INSTR[counter_key] / (stages["find"] * 1e-3) / ISSUE_PEAK,
-                                "instructions": "ncu smsp__inst_executed.sum of one launch",
-                                "peak_kind": "148 SMs x 4 schedulers x 2032 MHz"}),
+            "roofline": roof,
+            "roofline_issue": issue,
+            "roofline_fit": fit_roofline(ctr["clusters_on_tracks"], stages["fit"], fma_peak),
             "e2e": {"value": cl_all / e2e_s_max, "unit": "clusters/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h),
                     "path": "submit from pinned host pages, read clusters, tracks and map back into pinned "
@@ -782,14 +885,20 @@ def run_ours(args, world, rank, local):
         if world == 1 and args.workload == "full_tpc":   # one collision: its vertex time
             line["calibration"] = calibration_stats(tpc, R, pages_d, offs_d, tf)
         R.close()   # its slot's memory goes to the comparisons below
-        if world == 1 and not (args.no_variants or args.dense_finder) and args.workload in ("full_tpc", "continuous_50khz"):
-            line["finder_variants"] = finder_variants(tpc, torch, tf, pages_d, offs_d, tuning, flush,
-                                                      stages["find"])
+        if world == 1 and not (args.no_variants or args.dense_finder or args.fused_finder) and \
+                args.workload in ("full_tpc", "continuous_50khz"):
+            line["finder_variants"] = finder_variants(tpc, torch, tf, pages_d, offs_d, flush, stages["find"])
         if world == 1 and not args.no_variants and args.workload == "full_tpc":
             line["noise_suppression"] = noise_suppression_stats(tpc, torch, tf, pages_d, offs_d, tuning, flush,
                                                                 n_cl, stages["find"])
-        if world == 1 and not args.no_batched and args.workload == "full_tpc":
-            line["batched"] = batched_vs_plain(tpc, torch, local, tuning=tuning)
+        if world == 1 and not args.no_extras and args.workload == "continuous_50khz" and not args.time_bins:
+            # the full-TPC collision (one timeframe of 1000 bins) measured the same way
+            line["full_tpc"] = extra_workload(tpc, torch, local, "full_tpc", 1, 20, 3, flush, hbm, peak_kind,
+                                              fma_peak)
+        if world == 1 and not args.no_batched and args.workload in ("full_tpc", "continuous_50khz"):
+            line["batched"] = batched_vs_plain(tpc, torch, local,
+                                               tuning=tuning if args.workload == "full_tpc"
+                                               else line.get("full_tpc", {}).get("tuning"))
         if world == 1 and not args.no_cpu_baseline:
             cb = cpu_baseline(tf, 1)
             line["cpu_baseline"] = {"value": cb["clusters"] / cb["times"][0], "unit": "clusters/s", "cores": 1,
@@ -811,7 +920,7 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["serve"], default="full_tpc")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["serve"], default="continuous_50khz")
     ap.add_argument("--serve-bins", type=int, default=5500,
                     help="longest served timeframe in time bins (1.1 ms; lengths uniform down to 2/11 of it)")
     ap.add_argument("--time-bins", type=int, default=0, help="continuous_50khz: time bins (default 55,000)")
@@ -823,9 +932,13 @@ def main():
                     help="where the nvidia-smi clock samples of the timed region are written (default: the temp dir)")
     ap.add_argument("--no-graphs", action="store_true", help="enqueue every kernel instead of graph replay")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain comparison")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="continuous_50khz: skip the extra full_tpc measurement")
     ap.add_argument("--no-variants", action="store_true", help="skip the fused-vs-dense finder comparison")
     ap.add_argument("--dense-finder", action="store_true",
                     help="time the dense-plane finder variant instead of the fused finder")
+    ap.add_argument("--fused-finder", action="store_true",
+                    help="time the fused finder variant instead of the two-pass finder")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch configuration")
     ap.add_argument("--tuning", default="", help="fixed launch configuration, e.g. find_threads=384,fit_threads=32")
     args = ap.parse_args()

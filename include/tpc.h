@@ -88,12 +88,16 @@ typedef int32_t tpc_status;
 /* Ticket states reported by tpc_poll (monotone). */
 #define TPC_STATE_QUEUED          0   /* admitted, waiting for a slot */
 #define TPC_STATE_RUNNING         1   /* work enqueued on the device */
-#define TPC_STATE_INPUT_RELEASED  2   /* input pages copied; caller may reuse them */
+#define TPC_STATE_INPUT_RELEASED  2   /* input pages copied; caller may reuse them (host input
+                                          only: device input is read in place until DONE / FAILED) */
 #define TPC_STATE_DONE            3   /* results resident on the device */
 #define TPC_STATE_FAILED          4   /* finished with an error; tpc_poll returns it */
 
 /* Timeframe flags. */
-#define TPC_TF_DEVICE_INPUT  1u   /* pages / page_offsets are device pointers */
+#define TPC_TF_DEVICE_INPUT  1u   /* pages / page_offsets are device pointers, read in place: borrowed
+                                     until tpc_poll reports TPC_STATE_DONE or TPC_STATE_FAILED (a
+                                     capacity overflow re-runs the pipeline from them), so such a
+                                     timeframe never reports TPC_STATE_INPUT_RELEASED */
 #define TPC_TF_NOWAIT        2u   /* fail with TPC_E_BUSY instead of waiting for a slot */
 
 /* Context flags. */
@@ -102,8 +106,13 @@ typedef int32_t tpc_status;
 #define TPC_CTX_DENSE_FINDER 4u   /* steps 1-4 as the dense-plane variant: pages decoded into a dense
                                      (sector row, time bin, pad) ADC plane in device memory (2 bytes per
                                      pixel, 1.6 GB for the full TPC at 1000 bins), then windows read back
-                                     from it; the same clusters as the default fused finder, which decodes
-                                     each window into shared memory and never writes the plane */
+                                     from it */
+#define TPC_CTX_FUSED_FINDER 8u   /* steps 1-4 as the fused variant: each window's pages decoded straight
+                                     into a shared-memory plane of the whole window and clustered there.
+                                     Without either flag the two-pass finder runs: every page decoded
+                                     into 4-byte digit words (pad, time bin, ADC) in device memory (about
+                                     1.7x the ZS bytes), then each 64-bin time chunk of a window clustered
+                                     in a small shared plane.  All three give the same clusters. */
 
 /* Pipeline stages, in launch order (indices into tpc_get_stage_times). */
 #define TPC_STAGE_FIND       0    /* ZS decode + peak finder + cluster moments + compaction */
@@ -144,12 +153,18 @@ typedef struct {
   double   sigma_y;          /* 0.02 cm */
   double   sigma_z;          /* 0.03 cm */
   double   c0[5];            /* 4, 4, 0.25, 1, 100 initial covariance diagonal */
+  double   fp32_pd_margin;   /* 0    step 8's FP32 positive-definiteness check asks every factor
+                                     D_i of C = U D U^T to be > 0; with a margin m in [0, 1) it asks
+                                     D_i > m * c0_i (c0 in the fit's unit), so that updates whose
+                                     factors shrank below that are redone in FP64 (the FP64 check
+                                     stays D_i > 0) */
 } tpc_params;
 
-#define TPC_PARAMS_VERSION 1u
+#define TPC_PARAMS_VERSION 2u
 
 /* Timeframe descriptor.  pages / page_offsets are borrowed until tpc_poll
- * reports a state >= TPC_STATE_INPUT_RELEASED. */
+ * reports a state >= TPC_STATE_INPUT_RELEASED (host input) or >=
+ * TPC_STATE_DONE (TPC_TF_DEVICE_INPUT). */
 typedef struct {
   const void*     pages;         /* concatenated ZS pages (16-byte aligned) */
   uint64_t        pages_bytes;   /* total bytes of pages */
@@ -488,10 +503,12 @@ tpc_status tpc_release(tpc_context* ctx, uint64_t ticket);
 
 /* Launch configuration of the pipeline's kernels (per context).  Every choice
  * gives the same results, bit for bit; only the speed differs.  Defaults:
- * 384, 2, 8, 8, 64, 32. */
+ * 128, 8, 8, 8, 64, 32 (two-pass finder) or 384, 2, 8, 8, 64, 32 (fused or
+ * dense-plane finder). */
 typedef struct {
-  int32_t find_threads;        /* 256 | 384 | 512 threads per persistent finder CTA */
-  int32_t find_ctas_per_sm;    /* 1 | 2 finder CTAs per SM */
+  int32_t find_threads;        /* two-pass finder: 128 | 256 threads per unit CTA; fused and dense-plane
+                                  finders: 256 | 384 | 512 threads per persistent window CTA */
+  int32_t find_ctas_per_sm;    /* two-pass: 4 | 8 unit CTAs per SM; fused and dense-plane: 1 | 2 */
   int32_t ca_blocks_per_sm;    /* 4 | 8 | 16 CA-neighbour blocks per SM */
   int32_t elem_blocks_per_sm;  /* 4 | 8 | 16 blocks per SM of the grid-stride CA / merge kernels */
   int32_t fit_threads;         /* 32 | 64 | 128 tracks per fit block */
@@ -546,6 +563,15 @@ tpc_status tpc_find_clusters_noalloc(const tpc_geometry* geom, const tpc_params*
                                      const void* pages, uint64_t pages_bytes, const uint64_t* page_offsets,
                                      uint32_t n_time_bins, tpc_cluster* clusters, uint64_t cap,
                                      uint64_t* n_clusters, void* stream);
+
+/* Diagnostics: the FP32 FMA throughput of device `device` in FLOP/s (an FMA
+ * counts two), the best of `reps` (1..1000) timed launches of a kernel in
+ * which every thread runs eight independent FMA chains, 8 blocks of 256
+ * threads per SM.  It is the measured ALU peak the step-8 fit's achieved
+ * FLOP/s is compared with; the paper has no counterpart.  Allocates and frees
+ * a small scratch buffer and its own stream; changes no device setting.
+ * Errors: TPC_E_INVAL, TPC_E_CUDA. */
+tpc_status tpc_measure_fma_peak(int device, int reps, double* flops_per_s);
 
 /* Thread-local message describing the last error on this thread ("" if none). */
 const char* tpc_last_error(void);

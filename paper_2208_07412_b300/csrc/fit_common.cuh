@@ -20,12 +20,25 @@ __device__ __forceinline__ float sgnf(float v) { return v > 0.f ? 1.f : (v < 0.f
 __device__ __forceinline__ float rcp(float x) { return __fdividef(1.f, x); }
 __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
 
+// s + e = a + b exactly (Knuth's TwoSum, no condition on the magnitudes).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
 // Exact helix transport by dx (state in place).  false: |snp| would reach
 // 0.999.  Written for a short dependency chain: square roots come with their
 // reciprocals, and divisions are reciprocals computed off the critical path.
-__device__ __forceinline__ bool transport(float kfac, float* s, float dx, Jac<float>& J) {
+// slo (may be null): the low part of snp, carried so that snp = s[2] + *slo
+// keeps the row-to-row increments k dx (~1e-4 of snp on stiff tracks) whole
+// instead of rounding each to the ulp of snp.
+__device__ __forceinline__ bool transport(float kfac, float* s, float dx, Jac<float>& J, float* slo = nullptr) {
   const float k = kfac * s[4];
-  const float s1 = s[2], s2 = fmaf(k, dx, s1);
+  const float s1 = s[2];
+  float s2, s2lo = 0.f;
+  if (slo) two_sum(s1, fmaf(k, dx, *slo), s2, s2lo);
+  else s2 = fmaf(k, dx, s1);
   if (fabsf(s1) >= 0.999f || fabsf(s2) >= 0.999f) return false;
   const float e1 = 1.f - s1 * s1, e2 = 1.f - s2 * s2;
   const float rc1 = rsqrtf(e1), rc2 = rsqrtf(e2);     // 1 / cos
@@ -72,6 +85,7 @@ __device__ __forceinline__ bool transport(float kfac, float* s, float dx, Jac<fl
   s[0] += dy;
   s[1] = fmaf(s[3] * sg, A, s[1]);
   s[2] = s2;
+  if (slo) *slo = s2lo;
   return true;
 }
 
@@ -117,9 +131,11 @@ __device__ __forceinline__ void ud_propagate(UD<T>& M, const Jac<T>& J) {
 // Bierman's scalar measurement update of component `row` (0: y, 1: zeta) with
 // variance r.  Updates the state and the factors; returns innovation^2 / its
 // variance (the chi2 increment).  The partial sums alpha_j form a short FMA
-// chain; their reciprocals are then independent of each other.
+// chain; their reciprocals are then independent of each other.  slo (may be
+// null): the low part of snp (see transport), to which the snp correction is
+// added before the two parts are renormalised.
 template <typename T, int ROW>
-__device__ __forceinline__ T ud_update(T s[5], UD<T>& M, T z, T r) {
+__device__ __forceinline__ T ud_update(T s[5], UD<T>& M, T z, T r, float* slo = nullptr) {
   T f[5], v[5], b[5], al[5], ia[5];
 #pragma unroll
   for (int j = 0; j < 5; j++) {
@@ -148,7 +164,16 @@ __device__ __forceinline__ T ud_update(T s[5], UD<T>& M, T z, T r) {
   const T innov = z - s[ROW];
   const T g = ia[4] * innov;
 #pragma unroll
-  for (int i = 0; i < 5; i++) s[i] += b[i] * g;
+  for (int i = 0; i < 5; i++) {
+    if (i == 2 && slo) {
+      float hi, lo;
+      two_sum((float)s[2], fmaf((float)b[2], (float)g, *slo), hi, lo);
+      s[2] = (T)hi;
+      *slo = lo;
+    } else {
+      s[i] += b[i] * g;
+    }
+  }
   return innov * g;
 }
 
@@ -159,6 +184,16 @@ __device__ __forceinline__ bool ud_pd(const UD<T>& M) {
   int ok = 1;
 #pragma unroll
   for (int i = 0; i < 5; i++) ok &= (int)(M.d[i] > T(0)) & (int)(M.d[i] < T(1e30));
+  return ok != 0;
+}
+
+// The FP32 check of the step-8 fit: every D entry above its floor dmin (0 by
+// default: the plain positivity check) and below 1e30.  A floor above 0 sends
+// updates whose factors have shrunk below it to the FP64 redo.
+__device__ __forceinline__ bool ud_pd_above(const UD<float>& M, const float* dmin) {
+  int ok = 1;
+#pragma unroll
+  for (int i = 0; i < 5; i++) ok &= (int)(M.d[i] > dmin[i]) & (int)(M.d[i] < 1e30f);
   return ok != 0;
 }
 

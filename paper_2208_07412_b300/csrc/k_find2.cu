@@ -1,0 +1,501 @@
+// k_find2.cu — the two-pass cluster finder, the pipeline's default for steps
+// 1-4 (ZS decode, 3x3 peaks, 5x5 clusters, canonical order).  The paper's
+// section "Hardware and data flow" places this first step of the TPC
+// reconstruction on the EPN GPUs, after FPGA zero suppression.
+//
+// Pass 1, k_decode_digits: one warp per page.  Entries, runs and digits are
+// walked in chunks of 32 with warp scans (no block barrier): every digit
+// becomes one 32-bit word (pad | t_in << 8 | adc << 16) in page order, i.e.
+// ascending (time bin, pad), in a span of a digit array the page reserves
+// with one atomic.  A table row per window gives the span and the number of
+// digits before the time bins 3, 61, 67, 125, 131, 189, 195 and 253, the
+// boundaries of the find units' row ranges (the digit index of the first run
+// at or past each, stored by the lane that finds it).  Every check of the page format
+// is made here; a bad page sets the corruption bit and gets an empty span.
+//
+// Pass 2, k_find_units: one CTA at a time per unit = (window, 64-bin time
+// chunk).  The unit's digits (its 64 time bins with 3-bin halos on both sides,
+// from the window and, at the fragment edges, its neighbours) go into a
+// zero-padded shared plane of 70 rows (20 KB for 138 pads instead of the 74 KB
+// a whole window needs, so that several CTAs share an SM).  The peak test runs
+// strided over the digits; a peak is marked in the plane (bit 15 of its ADC
+// word), which the 5x5 of a cluster reads as "another peak" and step 2b as the
+// step-2 peak set; warp ballots rank the own peaks in canonical order into a
+// list, over which the clusters are built.  Each unit reserves a span of the
+// scratch buffer with one atomic; the unit-count scan and the compaction of
+// k_find.cu then place the spans canonically.
+#include "find_common.cuh"
+
+namespace tpc {
+
+constexpr int kChunkT = 64;                          // own time bins of a unit
+constexpr int kUnitsPerWin = kFrag / kChunkT;        // 4
+constexpr int kURows = kChunkT + 2 * kHalo;          // 70 plane rows
+constexpr int kDecThreads = 256;                     // decode block (8 warps, one page each)
+// Digit counts recorded per window: digits with t_in < kBound[k].
+__constant__ int kBound[8] = {3, 61, 67, 125, 131, 189, 195, 253};
+constexpr uint16_t kPeakBit = 0x8000;                // plane word: a peak of step 2
+constexpr uint16_t kDropBit = 0x4000;                // plane word: dropped by step 2b
+constexpr uint32_t kAdcMask = 1023u;
+
+__device__ __forceinline__ int warp_incl_scan32(int v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int n = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += n;
+  }
+  return v;
+}
+
+// The largest lane j < n whose value key (held by lane j, ascending over the
+// lanes) is <= x, or 0.  Every lane searches for its own x.
+__device__ __forceinline__ int warp_search(int key, int n, int x) {
+  int j = 0;
+#pragma unroll
+  for (int st = 16; st; st >>= 1) {
+    const int c = j + st;
+    const int kc = __shfl_sync(0xffffffffu, key, c & 31);
+    if (c < n && kc <= x) j = c;
+  }
+  return j;
+}
+
+// L2 prefetch of n bytes at p (16-byte aligned, at most 64 KB per instruction).
+__device__ __forceinline__ void prefetch_l2_bytes(const void* p, unsigned long long n) {
+  for (unsigned long long o = 0; o < n; o += 65536ull) {
+    const unsigned m = (unsigned)min(n - o, 65536ull) & ~15u;
+    if (m) {
+      const size_t ga = __cvta_generic_to_global(reinterpret_cast<const uint8_t*>(p) + o);
+      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(ga), "r"(m) : "memory");
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kDecThreads, 5) k_decode_digits(DevGeom G, DevWork W, unsigned int n_windows) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int T = G.n_time_bins;
+  while (true) {
+    unsigned int w = 0;
+    if (lane == 0) w = atomicAdd(W.tickets + TK_DEC, 1u);
+    w = __shfl_sync(FULL, w, 0);
+    if (w >= n_windows) break;
+    const int frs = window_frs(G, w);
+    const int f = frs & 0xffff, r = (frs >> 16) & 0xff, s = (frs >> 24) & 0xff;
+    const int np = G.npads[r];
+    const uint64_t o = W.page_offsets[w];
+    PageHdr h;
+    bool ok = parse_header(reinterpret_cast<const uint4*>(W.pages + (o <= W.pages_bytes ? o : 0)), o,
+                           W.pages_bytes, h) &&
+              h.sector == s && h.row == r && h.frag == f;
+    unsigned long long base = 0;
+    if (ok && lane == 0) base = atomicAdd(&W.ctr[CTR_NDIG], (unsigned long long)h.n_dig);
+    base = __shfl_sync(FULL, base, 0);
+    // a valid timeframe cannot exceed the array (each digit takes 10 bits of its page)
+    if (ok && base + (unsigned long long)h.n_dig > W.cap_dig) ok = false;
+    bool bad = !ok;
+    int r_cur = 0, d_cur = 0, t_last = -1;
+    int carry_t = -1;                     // time bin of the last run seen (boundary crossings)
+    // boundary counts (digits before time bin kBound[k]): n_dig unless a run at
+    // or past the bin is found, whose first digit index then is the count
+    uint16_t* btab = reinterpret_cast<uint16_t*>(W.dtab + 2ull * w + 1);
+    if (lane < 8) btab[lane] = (uint16_t)(ok ? h.n_dig : 0);
+    __syncwarp();
+    if (ok) {
+      const uint8_t* pg = W.pages + o;
+      // the whole page into L2 at once: its chunks are then read from L2, not
+      // one DRAM round trip after the other
+      if (lane == 0 && h.len > 32) prefetch_l2_bytes(pg + 32, h.len - 32);
+      const uint16_t* ent = reinterpret_cast<const uint16_t*>(pg + 32);
+      const uint16_t* run = ent + h.n_tb;
+      const uint32_t* adc = reinterpret_cast<const uint32_t*>(pg + h.body);
+      uint32_t* out = W.digits + base;
+      for (int E = 0; E < h.n_tb && !bad; E += 32) {
+        // ---- 32 entries: time bin, run count, first run
+        const int e = E + lane, n_ent = min(32, h.n_tb - E);
+        int t = 0, nr = 0;
+        if (lane < n_ent) {
+          const uint32_t v = __ldg(ent + e);
+          t = v & 0xff;
+          nr = v >> 8;
+        }
+        const int tup = __shfl_up_sync(FULL, t, 1);
+        const int tp = lane == 0 ? t_last : tup;
+        if (lane < n_ent && (nr < 1 || t <= tp || kFrag * f + t >= T)) bad = true;
+        const int incl = warp_incl_scan32(nr);
+        const int rs = r_cur + incl - nr;                  // first run of entry e
+        const int r_end = r_cur + __shfl_sync(FULL, incl, 31);
+        t_last = __shfl_sync(FULL, t, n_ent - 1);
+        bad = __any_sync(FULL, bad) || r_end > h.n_runs;
+        int carry_end = 0, carry_j = -1;
+        for (int R = r_cur; R < r_end && !bad; R += 32) {
+          // ---- 32 runs: checks, their entry's time bin, digit offsets
+          const int ri = R + lane, n_run = min(32, r_end - R);
+          int ps = 0, len = 0;
+          if (lane < n_run) {
+            const uint32_t rv = __ldg(run + ri);
+            ps = rv & 0xff;
+            len = rv >> 8;
+          }
+          const int j = warp_search(rs, n_ent, ri);         // entry of run ri
+          const int tr = __shfl_sync(FULL, t, j);
+          const int end = ps + len;
+          const int pend = __shfl_up_sync(FULL, end, 1), pj = __shfl_up_sync(FULL, j, 1);
+          const int prev_end = lane == 0 ? carry_end : pend, prev_j = lane == 0 ? carry_j : pj;
+          if (lane < n_run && (len < 1 || end > np || (prev_j == j && ps < prev_end))) bad = true;
+          const int tup_r = __shfl_up_sync(FULL, tr, 1);
+          const int t_prev_run = lane == 0 ? carry_t : tup_r;
+          carry_end = __shfl_sync(FULL, end, 31);
+          carry_j = __shfl_sync(FULL, j, 31);
+          carry_t = __shfl_sync(FULL, tr, 31);
+          const int dinc = warp_incl_scan32(len);
+          const int drel = dinc - len;                       // first digit of run ri, within the chunk
+          const int n_rd = __shfl_sync(FULL, dinc, 31);
+          bad = __any_sync(FULL, bad) || d_cur + n_rd > h.n_dig;
+          if (bad) break;
+          if (lane < n_run) {
+#pragma unroll
+            for (int k = 0; k < 8; k++)
+              if (t_prev_run < kBound[k] && tr >= kBound[k]) btab[k] = (uint16_t)(d_cur + drel);
+          }
+          // ---- the chunk's digits, 32 at a time: run by search, ADC from its word
+          for (int D = 0; D < n_rd; D += 32) {
+            const int dk = D + lane;
+            const int k = warp_search(drel, n_run, dk);
+            const int ps_k = __shfl_sync(FULL, ps, k), rel_k = __shfl_sync(FULL, drel, k);
+            const int t_k = __shfl_sync(FULL, tr, k);
+            if (dk < n_rd) {
+              const unsigned di = (unsigned)(d_cur + dk);
+              const uint32_t wv = __ldg(adc + di / 3u);
+              const uint32_t q = (wv >> (10u * (di % 3u))) & kAdcMask;
+              out[di] = (uint32_t)(ps_k + dk - rel_k) | ((uint32_t)t_k << 8) | (q << 16);
+            }
+          }
+          d_cur += n_rd;
+        }
+        r_cur = r_end;
+      }
+      if (!bad && (r_cur != h.n_runs || d_cur != h.n_dig)) bad = true;
+    }
+    __syncwarp();
+    if (lane == 0) {
+      if (bad) atomicOr(W.err, kErrCorrupt);
+      const uint32_t n = bad ? 0u : (uint32_t)h.n_dig;
+      W.dtab[2ull * w] = make_uint4((uint32_t)base, (uint32_t)(base >> 32), n, 0u);
+      if (bad) W.dtab[2ull * w + 1] = make_uint4(0u, 0u, 0u, 0u);
+    }
+  }
+}
+
+// Digits of window w's table row before boundary k (k = -1: 0; k = 8: all).
+__device__ __forceinline__ uint32_t tab_count(const uint4& b, uint32_t n, int k) {
+  if (k < 0) return 0u;
+  if (k >= 8) return n;
+  const uint32_t word = k < 2 ? b.x : (k < 4 ? b.y : (k < 6 ? b.z : b.w));
+  return (k & 1) ? word >> 16 : word & 0xffffu;
+}
+
+// One unit's digit segments: the previous window's halo, the own chunk, the
+// next window's halo.
+struct UnitDesc {
+  unsigned long long seg_start[3];   // global digit index of each segment's first digit
+  int seg_n[3];                      // digits per segment
+  int frs, c;                        // window coordinates (f | r << 16 | s << 24), chunk
+};
+
+// The descriptor of unit u from the decode table (thread 0 only).
+__device__ __forceinline__ void unit_desc(const DevGeom& G, const DevWork& W, unsigned int u, UnitDesc& D) {
+  const unsigned int w = u / kUnitsPerWin;
+  const int c = (int)(u % kUnitsPerWin);
+  const int frs = window_frs(G, w);
+  const int f = frs & 0xffff;
+  const uint4 a = W.dtab[2ull * w], b = W.dtab[2ull * w + 1];
+  const unsigned long long db = a.x | ((unsigned long long)a.y << 32);
+  // own digits: time bins [64c - 3, 64c + 67) of the window
+  const uint32_t lo = tab_count(b, a.z, c == 0 ? -1 : 2 * c - 1);
+  const uint32_t hi = tab_count(b, a.z, c == kUnitsPerWin - 1 ? 8 : 2 * c + 2);
+  D.seg_start[1] = db + lo;
+  D.seg_n[1] = (int)(hi > lo ? hi - lo : 0u);
+  D.seg_n[0] = D.seg_n[2] = 0;
+  D.seg_start[0] = D.seg_start[2] = 0;
+  if (c == 0 && f > 0) {          // the previous window's time bins >= 253
+    const uint4 ap = W.dtab[2ull * (w - 1)], bp = W.dtab[2ull * (w - 1) + 1];
+    const uint32_t l0 = tab_count(bp, ap.z, 7);
+    D.seg_start[0] = (ap.x | ((unsigned long long)ap.y << 32)) + l0;
+    D.seg_n[0] = (int)(ap.z > l0 ? ap.z - l0 : 0u);
+  }
+  if (c == kUnitsPerWin - 1 && f + 1 < G.n_frag) {   // the next window's time bins < 3
+    const uint4 an = W.dtab[2ull * (w + 1)], bn = W.dtab[2ull * (w + 1) + 1];
+    D.seg_start[2] = an.x | ((unsigned long long)an.y << 32);
+    D.seg_n[2] = (int)tab_count(bn, an.z, 0);
+  }
+  D.frs = frs;
+  D.c = c;
+}
+
+template <int kThreads>
+struct UnitSmem {
+  UnitDesc d;                        // the current unit
+  unsigned long long sbase;          // the unit's span of the scratch buffer
+  uint32_t scan[16];
+  uint32_t wtot[2][kThreads / 32];   // per-round warp counts of own peaks (double-buffered)
+};
+
+// Step 2 on the plane (bit 15 of a word marks a step-2 peak, bit 14 a peak
+// dropped by step 2b; charges are the low 10 bits): neighbours with a lower
+// linear index (t * npads + p) must be strictly lower, the others lower or
+// equal.
+__device__ __forceinline__ bool peak_test(const uint16_t* pl, int L, int ps, int q, int qmin) {
+  const uint16_t* u = pl + L - ps;
+  const uint16_t* d = pl + L + ps;
+  const int lo = max(max((int)(u[-1] & kAdcMask), (int)(u[0] & kAdcMask)),
+                     max((int)(u[1] & kAdcMask), (int)(pl[L - 1] & kAdcMask)));
+  const int hi = max(max((int)(pl[L + 1] & kAdcMask), (int)(d[-1] & kAdcMask)),
+                     max((int)(d[0] & kAdcMask), (int)(d[1] & kAdcMask)));
+  return (q >= qmin) & (q > lo) & (q >= hi);
+}
+
+// Step 2b for the step-2 peak at plane index L: dropped when a step-2 peak
+// with a greater key lies on the ring of its 5x5 window and the inner pixel
+// toward it lies less than min_dip below the peak.
+__device__ __forceinline__ bool ns_drop_plane(const uint16_t* pl, int L, int ps, int min_dip) {
+  const int qc = pl[L] & kAdcMask;
+#pragma unroll
+  for (int dt = -2; dt <= 2; dt++) {
+#pragma unroll
+    for (int dp = -2; dp <= 2; dp++) {
+      if (dt > -2 && dt < 2 && dp > -2 && dp < 2) continue;   // the ring only
+      const uint16_t vn = pl[L + dt * ps + dp];
+      if (!(vn & kPeakBit)) continue;
+      const int qn = vn & kAdcMask;
+      if (qn < qc || (qn == qc && (dt > 0 || (dt == 0 && dp > 0)))) continue;   // not a greater key
+      const int it = dt > 0 ? 1 : (dt < 0 ? -1 : 0), ip = dp > 0 ? 1 : (dp < 0 ? -1 : 0);
+      if (qc - (int)(pl[L + it * ps + ip] & kAdcMask) < min_dip) return true;
+    }
+  }
+  return false;
+}
+
+// Plane row offsets of the three segments: row = t_in + offset.
+__device__ __forceinline__ int seg_row_offset(int k, int c) {
+  return k == 0 ? kHalo - kFrag : (k == 1 ? kHalo - kChunkT * c : kHalo + kFrag - kChunkT * (kUnitsPerWin - 1));
+}
+
+// Units are taken round-robin (unit blockIdx.x + k gridDim.x); thread 0 reads
+// the next unit's descriptor while the current one is processed.  Per unit:
+// the plane is built from the digits (strided over the threads), step 2 runs
+// strided too, and each round of kThreads digits ranks its own peaks by warp
+// ballots and a prefix over the warps, appending their plane indices to a list
+// in canonical order; the clusters are then built strided over that list.
+template <int kThreads, bool kNs>
+__global__ void __launch_bounds__(kThreads) k_find_units(DevGeom G, DevParams P, DevWork W, unsigned int n_units) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ UnitSmem<kThreads> U;
+  constexpr int kWarps = kThreads / 32;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int ps = G.npmax + 2 * kPad;                 // plane row stride in pads
+  uint16_t* plane = reinterpret_cast<uint16_t*>(smem_raw);
+  const int plane_bytes = (kURows * ps * 2 + 15) & ~15;
+  const int plane_words16 = plane_bytes / 16;
+  uint4* plane16 = reinterpret_cast<uint4*>(smem_raw);
+  uint16_t* plist = reinterpret_cast<uint16_t*>(smem_raw + plane_bytes);   // own peaks, canonical order
+  for (int i = tid; i < plane_words16; i += kThreads) plane16[i] = make_uint4(0u, 0u, 0u, 0u);
+  if (blockIdx.x == 0 && tid == 0) W.ctr[CTR_NWIN] = n_units;
+  const int T = G.n_time_bins;
+  UnitDesc nxt;                                       // thread 0: the next unit's descriptor
+  unsigned int u = blockIdx.x;
+  if (tid == 0 && u < n_units) unit_desc(G, W, u, nxt);
+  for (; u < n_units; u += gridDim.x) {
+    if (tid == 0) {
+      U.d = nxt;
+      if (u + gridDim.x < n_units) unit_desc(G, W, u + gridDim.x, nxt);   // consumed next iteration
+    }
+    __syncthreads();
+    const int n0 = U.d.seg_n[0], n01 = n0 + U.d.seg_n[1], n_all = n01 + U.d.seg_n[2];
+    const int c = U.d.c;
+    const unsigned long long st0 = U.d.seg_start[0], st1 = U.d.seg_start[1] - n0, st2 = U.d.seg_start[2] - n01;
+    const int of0 = seg_row_offset(0, c), of1 = seg_row_offset(1, c), of2 = seg_row_offset(2, c);
+    // digit i of the unit -> (its word, its plane row offset)
+    auto digit = [&](int i, int& off) -> uint32_t {
+      const unsigned long long g = i < n0 ? st0 + i : (i < n01 ? st1 + i : st2 + i);
+      off = i < n0 ? of0 : (i < n01 ? of1 : of2);
+      return __ldg(W.digits + g);
+    };
+    // ---- build the plane
+    for (int i = tid; i < n_all; i += kThreads) {
+      int off;
+      const uint32_t d = digit(i, off);
+      const int row = (int)((d >> 8) & 255u) + off;
+      if (row >= 0 && row < kURows) plane[row * ps + kPad + (int)(d & 255u)] = (uint16_t)(d >> 16);
+    }
+    __syncthreads();
+    // ---- step 2 (rows 1..68), peaks marked; without step 2b the own ones are ranked at once
+    uint32_t running = 0;                               // own peaks listed so far (block-uniform)
+    int parity = 0;
+    for (int base = 0; base < n_all; base += kThreads) {
+      const int i = base + tid;
+      bool own = false;
+      int L = 0;
+      if (i < n_all) {
+        int off;
+        const uint32_t d = digit(i, off);
+        const int row = (int)((d >> 8) & 255u) + off;
+        if (row >= 1 && row <= kURows - 2) {
+          L = row * ps + kPad + (int)(d & 255u);
+          const int q = plane[L];
+          if (q >= P.q_peak_min && peak_test(plane, L, ps, q, P.q_peak_min)) {
+            plane[L] = (uint16_t)(q | kPeakBit);       // only this thread writes this pixel
+            own = !kNs && row >= kHalo && row < kHalo + kChunkT;
+          }
+        }
+      }
+      if (!kNs) {
+        const unsigned m = __ballot_sync(0xffffffffu, own);
+        if (lane == 0) U.wtot[parity][wid] = (uint32_t)__popc(m);
+        __syncthreads();
+        uint32_t before = running;
+#pragma unroll
+        for (int k = 0; k < kWarps; k++) {
+          const uint32_t v = U.wtot[parity][k];
+          before += k < wid ? v : 0u;
+          running += v;
+        }
+        if (own) plist[before + (uint32_t)__popc(m & ((1u << lane) - 1u))] = (uint16_t)L;
+        parity ^= 1;
+      }
+    }
+    if (kNs) {
+      __syncthreads();   // every step-2 peak marked: step 2b reads the ring
+      for (int base = 0; base < n_all; base += kThreads) {
+        const int i = base + tid;
+        bool own = false;
+        int L = 0;
+        if (i < n_all) {
+          int off;
+          const uint32_t d = digit(i, off);
+          const int row = (int)((d >> 8) & 255u) + off;
+          if (row >= kHalo && row < kHalo + kChunkT) {
+            L = row * ps + kPad + (int)(d & 255u);
+            const uint16_t v = plane[L];
+            if (v & kPeakBit) {
+              if (ns_drop_plane(plane, L, ps, P.ns_min_dip)) plane[L] = (uint16_t)(v | kDropBit);
+              else own = true;
+            }
+          }
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, own);
+        if (lane == 0) U.wtot[parity][wid] = (uint32_t)__popc(m);
+        __syncthreads();
+        uint32_t before = running;
+#pragma unroll
+        for (int k = 0; k < kWarps; k++) {
+          const uint32_t v = U.wtot[parity][k];
+          before += k < wid ? v : 0u;
+          running += v;
+        }
+        if (own) plist[before + (uint32_t)__popc(m & ((1u << lane) - 1u))] = (uint16_t)L;
+        parity ^= 1;
+      }
+    }
+    const uint32_t total = running;
+    if (tid == 0) {
+      const unsigned long long sb = total ? atomicAdd(&W.ctr[CTR_SCURSOR], (unsigned long long)total) : 0ull;
+      if (sb + total > W.cap_cl) atomicOr(W.err, kErrOverflowCl);
+      U.sbase = sb;
+      W.win_cnt[u] = total;
+      W.win_soff[u] = (uint32_t)min(sb, (unsigned long long)0xffffffffu);
+    }
+    __syncthreads();   // list complete, every peak marked, span reserved
+    // ---- clusters of the own peaks, strided over the list (canonical order)
+    if (total) {
+      const unsigned long long sb = U.sbase;
+      const int frs = U.d.frs;
+      const int f = frs & 0xffff, r = (frs >> 16) & 0xff, s = (frs >> 24) & 0xff;
+      const int np = G.npads[r], xrow = G.xrow[r];
+      const int t0 = kChunkT * c - kHalo;          // time bin (within the window) of plane row 0
+      for (uint32_t j = tid; j < total; j += kThreads) {
+        const int L = plist[j];
+        const int row = L / ps, p = L - row * ps - kPad;
+        int q[5][5];
+        bool other = false;
+#pragma unroll
+        for (int dt = 0; dt < 5; dt++)
+#pragma unroll
+          for (int dp = 0; dp < 5; dp++) {
+            const uint16_t x = plane[L + (dt - 2) * ps + dp - 2];
+            q[dt][dp] = x & kAdcMask;
+            if (dt != 2 || dp != 2) other |= (x & kPeakBit) != 0;
+          }
+        uint4 rec;
+        int4 xyz;
+        cluster_record(q, other, np, T, s, r, f, t0 + row + kHalo, p, xrow, rec, xyz);
+        const unsigned long long idx = sb + j;
+        if (idx < W.cap_cl) reinterpret_cast<uint4*>(W.scratch_cl)[idx] = rec;
+      }
+    }
+    __syncthreads();
+    for (int i = tid; i < plane_words16; i += kThreads) plane16[i] = make_uint4(0u, 0u, 0u, 0u);
+  }
+}
+
+// Dynamic shared memory of k_find_units: the plane, then the list of a unit's
+// own peaks (at most one per pair of pads of each of its 64 rows).
+size_t find2_smem_bytes(int npmax) {
+  return (((size_t)kURows * (npmax + 2 * kPad) * 2 + 15) & ~(size_t)15) + (size_t)kChunkT * ((npmax + 1) / 2) * 2;
+}
+
+cudaError_t prepare_find2() {
+  cudaError_t e = cudaFuncSetAttribute(k_find_units<128, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       96 * 1024);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_find_units<128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_find_units<256, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_find_units<256, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+  return e;
+}
+
+cudaError_t launch_scan(uint64_t* v, const unsigned long long* n_ptr, unsigned long long cap,
+                        unsigned long long* state, unsigned int* ticket, unsigned long long* total, uint32_t* err,
+                        int n_sm, cudaStream_t st);
+cudaError_t launch_compact(const DevGeom& G, const DevWork& W, unsigned int n_units, int units_per_window, int n_sm,
+                           cudaStream_t st);
+
+// Steps 1-4 by the two passes: decode, then find per unit; then the scan of
+// the unit counts and the canonical compaction.
+cudaError_t launch_find2(const DevGeom& G, const DevParams& P, const DevWork& W, unsigned int n_windows, int n_sm,
+                         const LaunchCfg& L, cudaStream_t st, unsigned long long* unit_scan_state, int* launches) {
+  const unsigned gd = (unsigned)std::min<unsigned long long>((n_windows + 7ull) / 8ull, (unsigned long long)n_sm * 8);
+  k_decode_digits<<<gd ? gd : 1, kDecThreads, 0, st>>>(G, W, n_windows);
+  const unsigned int n_units = n_windows * kUnitsPerWin;
+  const size_t sm = find2_smem_bytes(G.npmax);
+  const bool ns = P.ns_min_dip > 0;
+  const int nt = L.find_threads == 256 ? 256 : 128;
+  const void* fn = nt == 256 ? (ns ? (const void*)k_find_units<256, true> : (const void*)k_find_units<256, false>)
+                             : (ns ? (const void*)k_find_units<128, true> : (const void*)k_find_units<128, false>);
+  // CTAs that are all resident at once (each takes every gridDim.x-th unit)
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, nt, sm) != cudaSuccess || per_sm < 1) per_sm = 1;
+  per_sm = std::min(per_sm, L.find_ctas_per_sm);
+  const unsigned gu = (unsigned)std::max<unsigned long long>(
+      1ull, std::min<unsigned long long>(n_units, (unsigned long long)n_sm * per_sm));
+  if (nt == 256) {
+    if (ns) k_find_units<256, true><<<gu, 256, sm, st>>>(G, P, W, n_units);
+    else k_find_units<256, false><<<gu, 256, sm, st>>>(G, P, W, n_units);
+  } else {
+    if (ns) k_find_units<128, true><<<gu, 128, sm, st>>>(G, P, W, n_units);
+    else k_find_units<128, false><<<gu, 128, sm, st>>>(G, P, W, n_units);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  e = launch_scan(reinterpret_cast<uint64_t*>(W.win_cnt), W.ctr + CTR_NWIN, n_units, unit_scan_state,
+                  W.tickets + TK_SCAN_W, W.ctr + CTR_NCL, W.err, n_sm, st);
+  if (e != cudaSuccess) return e;
+  e = launch_compact(G, W, n_units, kUnitsPerWin, n_sm, st);
+  *launches += 4;
+  return e;
+}
+
+}  // namespace tpc

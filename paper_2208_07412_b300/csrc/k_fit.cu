@@ -7,10 +7,12 @@
 // measurement updates.  The covariance is kept as U D U^T factors (below): the
 // same Kalman filter in exact arithmetic, far less rounding loss in FP32.  An
 // update whose result fails the positive-definiteness check (a D entry not
-// positive) is recomputed in FP64 from the pre-update state and counted; FP64
-// is used nowhere else.  Measurements are
-// integer coordinates relative to the track's first cluster, so they reach
-// FP32 exactly before the single scaling to cm.
+// above its floor) is recomputed in FP64 from the pre-update state and
+// counted; FP64 is used nowhere else.  The fit runs in the integer coordinate
+// unit u (7.8125 um, 2^-7 mm) rather than in cm: measurements and row
+// distances are integers, exact in FP32, and only the emitted record is scaled
+// to cm.  y and zeta are carried relative to the current cluster, snp as a
+// high and a low part.
 #include "fit_common.cuh"
 
 namespace tpc {
@@ -30,26 +32,33 @@ k_fit(DevGeom G, DevParams P, DevWork W) {
     const int4* pts = W.trk_xyz + W.trk_off[t];   // (X, Y, Z, cluster), innermost first
     const int4 p0 = pts[0], pm = pts[(n - 1) / 2], po = pts[n - 1];
     const int c0 = p0.w;
-    const int X0 = p0.x, Y0 = p0.y, Z0 = p0.z;
     // ---- initial state: circle through innermost, middle and outermost clusters
-    const float ax = (float)(pm.x - X0) * kU, ay = (float)(pm.y - Y0) * kU;
-    const float cx = (float)(po.x - X0) * kU, cy = (float)(po.y - Y0) * kU;
+    // (integer differences in u: exact in FP32)
+    const float ax = (float)(pm.x - p0.x), ay = (float)(pm.y - p0.y);
+    const float cx = (float)(po.x - p0.x), cy = (float)(po.y - p0.y);
     const float bx = cx - ax, by = cy - ay;
     const float la = sqrtf(ax * ax + ay * ay), lb = sqrtf(bx * bx + by * by), lc = sqrtf(cx * cx + cy * cy);
-    const float kc = 2.f * (ax * cy - ay * cx) / (la * lb * lc);
+    const float kc = 2.f * (ax * cy - ay * cx) / (la * lb * lc);   // 1/u
     const float hh = fminf(1.f, fmaxf(-1.f, 0.5f * kc * lc));
     const float half = asinf(hh);
     const float phic = atan2f(cy, cx);
     const float klc = kc * lc;
     const float arc = fabsf(klc) < 1e-3f ? lc * (1.f + klc * klc * (1.f / 24.f)) : 2.f * half / kc;
-    const float zo = (float)(po.z - Z0) * kU;
-    float s[5] = {cy, zo, sinf(phic + half), zo / arc, kc / P.kfac};
+    const float zo = (float)(po.z - p0.z);
+    // State (y - Yr, zeta - Zr, snp, tgl, q/pT) with y, zeta in u, relative to
+    // the integer reference (Yr, Zr), which moves to each cluster before its
+    // update: the measurement is then exactly 0 and the state's first two
+    // components stay of the size of the residuals, so their FP32 rounding is
+    // that of a few hundred u, not of the track's whole extent.
+    float s[5] = {0.f, 0.f, sinf(phic + half), zo / arc, kc / P.kfac_u};
+    float slo = 0.f;   // low part of snp: snp = s[2] + slo
+    int Yr = po.y, Zr = po.z;
     UD<float> M;
     int xcur = po.x;
     int flags = 0, n_used = 0, nfp64 = 0;
     float chi2 = 0.f;
     for (int pass = 0; pass < P.fit_passes; pass++) {
-      ud_reset(M, P.c0);
+      ud_reset(M, P.c0_u);
       chi2 = 0.f;
       n_used = 0;
       const bool inward = (pass & 1) == 0;
@@ -65,34 +74,40 @@ k_fit(DevGeom G, DevParams P, DevWork W) {
         const int Xi = cur.x;
         if (Xi != xcur) {
           Jac<float> J;
-          if (!transport(P.kfac, s, (float)(Xi - xcur) * kU, J)) { flags |= TPC_TRK_STOPPED; break; }
+          if (!transport(P.kfac_u, s, (float)(Xi - xcur), J, &slo)) { flags |= TPC_TRK_STOPPED; break; }
           ud_propagate(M, J);
           xcur = Xi;
         }
-        const int dY = cur.y - Y0, dZ = cur.z - Z0;
+        // reference to this cluster (integer shifts, exact in FP32 below 2^24 u)
+        s[0] -= (float)(cur.y - Yr);
+        s[1] -= (float)(cur.z - Zr);
+        Yr = cur.y;
+        Zr = cur.z;
         float s0[5];
+        const float slo0 = slo;
         UD<float> M0 = M;
 #pragma unroll
         for (int a = 0; a < 5; a++) s0[a] = s[a];
-        float dchi = ud_update<float, 0>(s, M, (float)dY * kU, P.sy2);
-        dchi += ud_update<float, 1>(s, M, (float)dZ * kU, P.sz2);
-        if (!ud_pd(M)) {
+        float dchi = ud_update<float, 0>(s, M, 0.f, P.sy2_u, &slo);
+        dchi += ud_update<float, 1>(s, M, 0.f, P.sz2_u, &slo);
+        if (!ud_pd_above(M, P.pd_min_u)) {
           // redo this update in FP64 from the pre-update state
           double sd[5];
           UD<double> Md;
 #pragma unroll
           for (int a = 0; a < 5; a++) {
-            sd[a] = s0[a];
+            sd[a] = a == 2 ? (double)s0[2] + (double)slo0 : (double)s0[a];
             Md.d[a] = M0.d[a];
 #pragma unroll
             for (int b = 0; b < 5; b++) Md.u[a][b] = M0.u[a][b];
           }
-          double dd = ud_update<double, 0>(sd, Md, (double)dY * kUd, P.sy2_d);
-          dd += ud_update<double, 1>(sd, Md, (double)dZ * kUd, P.sz2_d);
+          double dd = ud_update<double, 0>(sd, Md, 0.0, P.sy2_ud);
+          dd += ud_update<double, 1>(sd, Md, 0.0, P.sz2_ud);
           if (!ud_pd(Md)) flags |= TPC_TRK_NOT_PD;
 #pragma unroll
           for (int a = 0; a < 5; a++) {
             s[a] = (float)sd[a];
+            if (a == 2) slo = (float)(sd[2] - (double)s[2]);
             M.d[a] = (float)Md.d[a];
 #pragma unroll
             for (int b = 0; b < 5; b++) M.u[a][b] = (float)Md.u[a][b];
@@ -104,11 +119,11 @@ k_fit(DevGeom G, DevParams P, DevWork W) {
         n_used++;
       }
     }
-    // ---- emit: C = U D U^T
+    // ---- emit in cm: C = U D U^T, rows / columns of y and zeta scaled by kU
     tpc_track out;
-    out.par[0] = s[0] + (float)Y0 * kU;
-    out.par[1] = s[1] + (float)Z0 * kU;
-    out.par[2] = s[2];
+    out.par[0] = ((float)Yr + s[0]) * kU;
+    out.par[1] = (float)Zr * kU + s[1] * kU;
+    out.par[2] = s[2] + slo;
     out.par[3] = s[3];
     out.par[4] = s[4];
     out.x = (float)xcur * kU;
@@ -123,7 +138,8 @@ k_fit(DevGeom G, DevParams P, DevWork W) {
         float acc = M.d[i] * (j == i ? 1.f : M.u[j][i]);
 #pragma unroll
         for (int k = i + 1; k < 5; k++) acc += M.u[i][k] * M.d[k] * M.u[j][k];
-        out.cov[m++] = acc;
+        const float sc = (i < 2 ? kU : 1.f) * (j < 2 ? kU : 1.f);
+        out.cov[m++] = acc * sc;
       }
     out.ndf = 2 * n_used - 5;
     out.n_clusters = n;

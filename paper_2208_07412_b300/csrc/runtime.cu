@@ -29,6 +29,9 @@ cudaError_t launch_merge(const DevGeom&, const DevParams&, const DevWork&, int, 
 cudaError_t launch_fit(const DevGeom&, const DevParams&, const DevWork&, int, const LaunchCfg&, cudaStream_t, int*);
 size_t scan_tiles(unsigned long long cap);
 cudaError_t prepare_find();
+cudaError_t prepare_find2();
+cudaError_t launch_find2(const DevGeom&, const DevParams&, const DevWork&, unsigned int, int, const LaunchCfg&,
+                         cudaStream_t, unsigned long long*, int*);
 cudaError_t launch_xsec(const DevGeom&, const DevParams&, const DevWork&, const XsWork&, int, cudaStream_t);
 cudaError_t launch_compress(const DevParams&, const DevWork&, const CmpWork&, int, cudaStream_t);
 cudaError_t launch_calibrate(const DevParams&, const DevWork&, const CalWork&, int, cudaStream_t);
@@ -69,7 +72,7 @@ struct Slot {
   // device buffers
   Buf pages, offsets, winstate, cl, clx, cly, clz, clt, rowstart, chrow, up, down, score, edge, jump, chlen, scanv,
       scanst, chainof, clchain, ch_i32, besta, bestb, trk_i32, trackcl, cl2trk, tracks, ctrl, scratch, wincnt, winsoff,
-      candab, candsc, lenhist, evinfo, xs, cmp, cal, dense;
+      candab, candsc, lenhist, evinfo, xs, cmp, cal, dense, digits, dtab;
   unsigned long long* h_ctrl = nullptr;   // pinned copy of [ctr | err]
   // batch tables, device (evinfo) and pinned host copy, same layout:
   // u64 base[kMaxBatch], u64 bytes[kMaxBatch], u32 cl_start[kMaxBatch + 1],
@@ -84,7 +87,7 @@ struct Slot {
   bool cmp_done = false;
   size_t cmp_bytes = 0, cal_bytes = 0;
   // capacities
-  uint64_t cap_pages = 0, cap_windows = 0, cap_cl = 0, cap_ch = 0;
+  uint64_t cap_pages = 0, cap_windows = 0, cap_cl = 0, cap_ch = 0, cap_dig = 0;
   // ticket
   bool in_use = false;
   uint64_t ticket = 0;
@@ -149,6 +152,7 @@ extern "C" tpc_status tpc_params_default(tpc_params* p) {
   p->bz = 0.5;
   p->sigma_y = 0.02; p->sigma_z = 0.03;
   p->c0[0] = 4.0; p->c0[1] = 4.0; p->c0[2] = 0.25; p->c0[3] = 1.0; p->c0[4] = 100.0;
+  p->fp32_pd_margin = 0.0;
   return TPC_OK;
 }
 
@@ -191,6 +195,8 @@ static tpc_status check_params(const tpc_params& p, const tpc_geometry& g) {
     return fail(TPC_E_INVAL, "params: fit settings out of range");
   for (int i = 0; i < 5; i++)
     if (!(p.c0[i] > 0)) return fail(TPC_E_INVAL, "params: c0 must be positive");
+  if (!(p.fp32_pd_margin >= 0 && p.fp32_pd_margin < 1))
+    return fail(TPC_E_INVAL, "params: fp32_pd_margin must be in [0, 1)");
   // CA scores must fit the 41-bit field of the edge-row keys
   for (int r = 1; r + 1 < g.n_rows; r++) {
     long double lim = (long double)p.ca_cut * 64.0L * (g.row_x[r + 1] - g.row_x[r - 1]);
@@ -213,10 +219,24 @@ static cudaError_t ensure(Buf& b, size_t bytes) {
   return e;
 }
 
+// Steps 1-4 by the two-pass finder (the default) rather than the fused or the
+// dense-plane variant.
+static bool two_pass(const tpc_context* ctx) {
+  return !(ctx->flags & (TPC_CTX_DENSE_FINDER | TPC_CTX_FUSED_FINDER));
+}
+
+// Units of the two-pass finder per window (its scan and span arrays are sized for them).
+constexpr uint64_t kUnitsPerWindow = 4;
+
+// Digits the two-pass finder's array must hold for pages_bytes of pages: each
+// digit takes 10 of the 32 bits of an ADC word inside its page.
+static uint64_t digit_cap(uint64_t pages_bytes) { return pages_bytes / 4 * 3 + 3; }
+
 static size_t slot_bytes(uint64_t pages, uint64_t windows, uint64_t cap_cl, uint64_t cap_ch, int nsr,
-                         size_t dense = 0) {
-  size_t b = dense + pages + 16 + windows * 36 + cap_cl * (16 + 16 + 16 + 8 + 8 + 8 + 8 + 4 + 8 + 4 + 4 + 4 + 4) +
-             (scan_tiles(cap_cl) + scan_tiles(cap_ch) + scan_tiles(windows)) * 8 +
+                         size_t dense = 0, uint64_t cap_dig = 0) {
+  size_t b = dense + pages + 16 + windows * (8 + 8 + 8 * kUnitsPerWindow + 4 * (kUnitsPerWindow + 2) + 32) +
+             cap_dig * 4 + cap_cl * (16 + 16 + 16 + 8 + 8 + 8 + 8 + 4 + 8 + 4 + 4 + 4 + 4) +
+             (scan_tiles(cap_cl) + scan_tiles(cap_ch) + scan_tiles(windows * kUnitsPerWindow)) * 8 +
              cap_ch * (14 * 4 + 8 + 16 + sizeof(tpc_track) + 4 * 12) +
              (size_t)(nsr + 1) * 8 + 1024;
   return b;
@@ -230,10 +250,11 @@ static tpc_status slot_reserve(tpc_context* ctx, Slot& s, uint64_t pages_bytes, 
   // dense-plane finder variant: one ADC per (sector row, time bin, pad)
   const size_t dstride = (size_t)((ctx->geom.npmax + 7) & ~7);
   const size_t want_dense = (ctx->flags & TPC_CTX_DENSE_FINDER) ? (size_t)windows * kFrag * dstride * 2 : 0;
-  size_t cur = slot_bytes(s.cap_pages, s.cap_windows, s.cap_cl, s.cap_ch, nsr, s.dense.bytes);
+  const uint64_t want_dig = two_pass(ctx) ? digit_cap(pages_bytes) : 0;
+  size_t cur = slot_bytes(s.cap_pages, s.cap_windows, s.cap_cl, s.cap_ch, nsr, s.dense.bytes, s.cap_dig);
   size_t need = slot_bytes(std::max(s.cap_pages, want_pages), std::max(s.cap_windows, windows),
                            std::max(s.cap_cl, cap_cl), std::max(s.cap_ch, cap_ch), nsr,
-                           std::max(s.dense.bytes, want_dense));
+                           std::max(s.dense.bytes, want_dense), std::max(s.cap_dig, want_dig));
   if (ctx->used - cur + need > ctx->budget)
     return fail(TPC_E_NOMEM, "timeframe needs " + std::to_string(need) + " device bytes; budget left " +
                                  std::to_string(ctx->budget - ctx->used + cur));
@@ -241,9 +262,15 @@ static tpc_status slot_reserve(tpc_context* ctx, Slot& s, uint64_t pages_bytes, 
   if (windows > s.cap_windows) {
     CUDA_TRY(ensure(s.offsets, windows * 8));
     CUDA_TRY(ensure(s.winstate, windows * 8));
-    CUDA_TRY(ensure(s.wincnt, windows * 8));
-    CUDA_TRY(ensure(s.winsoff, windows * 12));   // span starts | light list | heavy list
+    CUDA_TRY(ensure(s.wincnt, windows * kUnitsPerWindow * 8));
+    // span starts (one per unit) | light list | heavy list
+    CUDA_TRY(ensure(s.winsoff, windows * (kUnitsPerWindow + 2) * 4));
+    CUDA_TRY(ensure(s.dtab, windows * 32));
     s.cap_windows = windows;
+  }
+  if (want_dig > s.cap_dig) {
+    CUDA_TRY(ensure(s.digits, want_dig * 4));
+    s.cap_dig = want_dig;
   }
   if (cap_cl > s.cap_cl) {
     CUDA_TRY(ensure(s.cl, cap_cl * 16));
@@ -267,13 +294,15 @@ static tpc_status slot_reserve(tpc_context* ctx, Slot& s, uint64_t pages_bytes, 
     CUDA_TRY(ensure(s.candsc, cap_ch * 4 * 4));
     s.cap_ch = cap_ch;
   }
-  CUDA_TRY(ensure(s.scanst, (scan_tiles(s.cap_cl) + scan_tiles(s.cap_ch) + scan_tiles(s.cap_windows)) * 8));
+  CUDA_TRY(ensure(s.scanst,
+                  (scan_tiles(s.cap_cl) + scan_tiles(s.cap_ch) + scan_tiles(s.cap_windows * kUnitsPerWindow)) * 8));
   CUDA_TRY(ensure(s.rowstart, (size_t)(nsr + 1) * 4));
   CUDA_TRY(ensure(s.chrow, (size_t)(nsr + 1) * 4));
   if (want_dense) CUDA_TRY(ensure(s.dense, want_dense));
   CUDA_TRY(ensure(s.ctrl, 256));
   CUDA_TRY(ensure(s.lenhist, 512 * 4));
-  ctx->used = ctx->used - cur + slot_bytes(s.cap_pages, s.cap_windows, s.cap_cl, s.cap_ch, nsr, s.dense.bytes);
+  ctx->used = ctx->used - cur + slot_bytes(s.cap_pages, s.cap_windows, s.cap_cl, s.cap_ch, nsr, s.dense.bytes,
+                                           s.cap_dig);
   // wire the work-space pointers
   DevWork& W = s.W;
   W.clusters = (tpc_cluster*)s.cl.p;
@@ -286,8 +315,11 @@ static tpc_status slot_reserve(tpc_context* ctx, Slot& s, uint64_t pages_bytes, 
   W.scratch_cl = (tpc_cluster*)s.scratch.p;
   W.win_cnt = (unsigned long long*)s.wincnt.p;
   W.win_soff = (uint32_t*)s.winsoff.p;
-  W.light_list = (uint32_t*)s.winsoff.p + s.cap_windows;
-  W.heavy_list = (uint32_t*)s.winsoff.p + 2 * s.cap_windows;
+  W.light_list = (uint32_t*)s.winsoff.p + kUnitsPerWindow * s.cap_windows;
+  W.heavy_list = (uint32_t*)s.winsoff.p + (kUnitsPerWindow + 1) * s.cap_windows;
+  W.digits = (uint32_t*)s.digits.p;
+  W.dtab = (uint4*)s.dtab.p;
+  W.cap_dig = s.cap_dig;
   W.up = (int32_t*)s.up.p; W.down = (int32_t*)s.down.p;
   W.score = (int64_t*)s.score.p;
   W.edge_key = (unsigned long long*)s.edge.p;
@@ -326,7 +358,8 @@ static void slot_free(tpc_context* ctx, Slot& s) {
   Buf* all[] = {&s.pages, &s.offsets, &s.winstate, &s.cl, &s.clx, &s.cly, &s.clz, &s.clt, &s.rowstart, &s.chrow, &s.up,
                 &s.down, &s.score, &s.edge, &s.jump, &s.chlen, &s.scanv, &s.scanst, &s.chainof, &s.clchain,
                 &s.ch_i32, &s.besta, &s.bestb, &s.trk_i32, &s.trackcl, &s.cl2trk, &s.tracks, &s.ctrl,
-                &s.scratch, &s.wincnt, &s.winsoff, &s.candab, &s.candsc, &s.lenhist, &s.evinfo, &s.xs, &s.cmp, &s.cal, &s.dense};
+                &s.scratch, &s.wincnt, &s.winsoff, &s.candab, &s.candsc, &s.lenhist, &s.evinfo, &s.xs, &s.cmp, &s.cal, &s.dense,
+                &s.digits, &s.dtab};
   for (Buf* b : all) free_buf(*b);
   for (auto& e : s.ev_stage) if (e) cudaEventDestroy(e);
   if (s.ev_done) cudaEventDestroy(s.ev_done);
@@ -383,8 +416,26 @@ extern "C" tpc_status tpc_create_context(const tpc_geometry* geom, const tpc_par
   P.sy2_d = p.sigma_y * p.sigma_y; P.sz2_d = p.sigma_z * p.sigma_z;
   P.sy2 = (float)P.sy2_d; P.sz2 = (float)P.sz2_d;
   for (int i = 0; i < 5; i++) P.c0[i] = (float)p.c0[i];
+  const double u = 7.8125e-4;   // cm per u
+  P.kfac_u = (float)(P.kfac_d * u);
+  P.sy2_ud = P.sy2_d / (u * u);
+  P.sz2_ud = P.sz2_d / (u * u);
+  P.sy2_u = (float)P.sy2_ud;
+  P.sz2_u = (float)P.sz2_ud;
+  for (int i = 0; i < 5; i++) {
+    const double c = p.c0[i] / (i < 2 ? u * u : 1.0);
+    P.c0_u[i] = (float)c;
+    P.pd_min_u[i] = (float)(p.fp32_pd_margin * c);
+  }
   if (find_smem_bytes(G.npmax, G.nw) > 227 * 1024) { delete ctx; return fail(TPC_E_INVAL, "rows too wide"); }
-  if (prepare_find() != cudaSuccess) { delete ctx; return fail(TPC_E_CUDA, "cudaFuncSetAttribute failed"); }
+  if (prepare_find() != cudaSuccess || prepare_find2() != cudaSuccess) {
+    delete ctx;
+    return fail(TPC_E_CUDA, "cudaFuncSetAttribute failed");
+  }
+  if (two_pass(ctx)) {   // the two-pass finder's launch shape: 128-thread CTAs, 8 per SM
+    ctx->L.find_threads = 128;
+    ctx->L.find_ctas_per_sm = 8;
+  }
   ctx->slots.resize(n_slots);
   for (int i = 0; i < n_slots; i++) {
     Slot& s = ctx->slots[i];
@@ -469,11 +520,15 @@ static tpc_status enqueue_body(tpc_context* ctx, Slot& s, bool capturing) {
   CUDA_TRY(cudaMemsetAsync(s.ctrl.p, 0, 256, st));
   CUDA_TRY(cudaMemsetAsync(W.len_hist, 0, 512 * 4, st));
   const size_t tiles_a = scan_tiles(s.cap_cl), tiles_b = scan_tiles(s.cap_ch);
-  CUDA_TRY(cudaMemsetAsync(W.scan_state, 0, (tiles_a + tiles_b + scan_tiles(s.n_windows)) * 8, st));
+  CUDA_TRY(cudaMemsetAsync(W.scan_state, 0, (tiles_a + tiles_b + scan_tiles(s.n_windows * kUnitsPerWindow)) * 8, st));
   if (timing) CUDA_TRY(cudaEventRecordWithFlags(s.ev_stage[0], st, evf));
   const LaunchCfg& L = ctx->L;
-  CUDA_TRY(launch_find(G, ctx->P, W, s.n_windows, ctx->n_sm, L, st, s.aux, s.ev_fork, s.ev_join,
-                       W.scan_state + tiles_a + tiles_b, &s.launches));
+  if (two_pass(ctx))
+    CUDA_TRY(launch_find2(G, ctx->P, W, s.n_windows, ctx->n_sm, L, st, W.scan_state + tiles_a + tiles_b,
+                          &s.launches));
+  else
+    CUDA_TRY(launch_find(G, ctx->P, W, s.n_windows, ctx->n_sm, L, st, s.aux, s.ev_fork, s.ev_join,
+                         W.scan_state + tiles_a + tiles_b, &s.launches));
   if (timing) CUDA_TRY(cudaEventRecordWithFlags(s.ev_stage[1], st, evf));
   CUDA_TRY(launch_ca(G, ctx->P, W, ctx->n_sm, L, st, &s.launches));
   if (timing) CUDA_TRY(cudaEventRecordWithFlags(s.ev_stage[2], st, evf));
@@ -553,9 +608,15 @@ static Slot* find_ticket(tpc_context* ctx, uint64_t ticket) {
   return nullptr;
 }
 
+// An upper bound of the clusters any valid timeframe of pages_bytes can hold.
+// A cluster needs a peak digit (4/3 B: three 10-bit ADCs per 32-bit word).
+// Two peaks of one time bin are at least two pads apart (peaks are never
+// adjacent), so between consecutive peaks of an entry lies either a digit
+// (4/3 B) or the start of another run (2 B): at least 8/3 B per peak beyond the
+// first of each entry, whose entry and run headers (4 B) cost more.  Hence
+// clusters <= 3 pages_bytes / 8.
 static uint64_t guaranteed_cap_cl(uint64_t pages_bytes) {
-  // a cluster needs a peak digit with its own run (2 B) and 10-bit ADC: > 3 B each
-  return pages_bytes / 3 + 1024;
+  return pages_bytes / 8 * 3 + 3 + 1024;
 }
 
 // Validation of one descriptor (before any slot is touched).
@@ -670,16 +731,17 @@ static void reclaim_idle(tpc_context* ctx, const Slot* keep) {
   for (auto& c : ctx->slots) {
     if (c.in_use || &c == keep || !c.cap_pages && !c.cap_cl) continue;
     cudaStreamSynchronize(c.stream);
-    ctx->used -= slot_bytes(c.cap_pages, c.cap_windows, c.cap_cl, c.cap_ch, nsr1 * (int)c.n_events, c.dense.bytes);
+    ctx->used -= slot_bytes(c.cap_pages, c.cap_windows, c.cap_cl, c.cap_ch, nsr1 * (int)c.n_events, c.dense.bytes,
+                            c.cap_dig);
     Buf* big[] = {&c.pages, &c.offsets, &c.winstate, &c.cl, &c.clx, &c.cly, &c.clz, &c.clt, &c.up, &c.down,
                   &c.score, &c.edge, &c.jump, &c.chlen, &c.scanv, &c.scanst, &c.chainof, &c.clchain, &c.ch_i32,
                   &c.besta, &c.bestb, &c.trk_i32, &c.trackcl, &c.cl2trk, &c.tracks, &c.scratch, &c.wincnt,
-                  &c.winsoff, &c.candab, &c.candsc, &c.xs, &c.cmp, &c.cal, &c.dense};
+                  &c.winsoff, &c.candab, &c.candsc, &c.xs, &c.cmp, &c.cal, &c.dense, &c.digits, &c.dtab};
     for (Buf* b : big) free_buf(*b);
     ctx->used -= c.xs_bytes + c.cmp_bytes + c.cal_bytes;
     c.xs_bytes = c.cmp_bytes = c.cal_bytes = 0;
     c.xs_done = c.cmp_done = false;
-    c.cap_pages = c.cap_windows = c.cap_cl = c.cap_ch = 0;
+    c.cap_pages = c.cap_windows = c.cap_cl = c.cap_ch = c.cap_dig = 0;
   }
 }
 
@@ -848,7 +910,10 @@ extern "C" tpc_status tpc_poll(tpc_context* ctx, uint64_t ticket, uint32_t timeo
           s->status = TPC_E_CUDA;
           *state = s->state;
           return fail(TPC_E_CUDA, std::string("device error: ") + cudaGetErrorString(q));
-        } else if (s->state == TPC_STATE_RUNNING && cudaEventQuery(s->ev_input) == cudaSuccess) {
+        } else if (s->state == TPC_STATE_RUNNING && !(s->tf_flags & TPC_TF_DEVICE_INPUT) &&
+                   cudaEventQuery(s->ev_input) == cudaSuccess) {
+          // host input has been copied into the slot; device input is read in
+          // place by every run (an overflow re-runs from it) until DONE
           s->state = TPC_STATE_INPUT_RELEASED;
         }
         *state = s->state;
@@ -1302,6 +1367,10 @@ extern "C" tpc_status tpc_release(tpc_context* ctx, uint64_t ticket) {
 }
 
 // ------------------------------------------------------------------ tuning
+// Finder launch shapes (threads per CTA x CTAs per SM): the two-pass finder's
+// small-plane CTAs, or the fused / dense-plane finder's whole-window ones.
+static const int kFind2ThreadsC[] = {128, 256};
+static const int kFind2CtasC[] = {4, 8};
 static const int kFindThreadsC[] = {256, 384, 512};
 static const int kFindCtasC[] = {1, 2};
 static const int kPerSmC[] = {4, 8, 16};
@@ -1333,8 +1402,9 @@ extern "C" tpc_status tpc_get_tuning(tpc_context* ctx, tpc_tuning* out) {
 
 extern "C" tpc_status tpc_set_tuning(tpc_context* ctx, const tpc_tuning* t) {
   if (!ctx || !t) return fail(TPC_E_INVAL, "tpc_set_tuning: null argument");
-  if (!one_of(t->find_threads, kFindThreadsC) || !one_of(t->find_ctas_per_sm, kFindCtasC) ||
-      !one_of(t->ca_blocks_per_sm, kPerSmC) || !one_of(t->elem_blocks_per_sm, kPerSmC) ||
+  const bool find_ok = two_pass(ctx) ? one_of(t->find_threads, kFind2ThreadsC) && one_of(t->find_ctas_per_sm, kFind2CtasC)
+                                      : one_of(t->find_threads, kFindThreadsC) && one_of(t->find_ctas_per_sm, kFindCtasC);
+  if (!find_ok || !one_of(t->ca_blocks_per_sm, kPerSmC) || !one_of(t->elem_blocks_per_sm, kPerSmC) ||
       !one_of(t->fit_threads, kFitThreadsC) || !one_of(t->fit_blocks_per_sm, kFitBlocksC))
     return fail(TPC_E_INVAL, "tpc_set_tuning: a value outside its candidate set");
   std::lock_guard<std::mutex> lk(ctx->mu);
@@ -1378,17 +1448,26 @@ extern "C" tpc_status tpc_autotune(tpc_context* ctx, const tpc_timeframe_desc* s
   const uint32_t flags0 = ctx->flags;
   const LaunchCfg L0 = ctx->L;
   ctx->flags = (flags0 | TPC_CTX_STAGE_TIMING | TPC_CTX_NO_GRAPHS);
-  // joint trials: trial i uses finder choice i % 6, CA/merge choice i % 9 and
-  // fit choice i % 9; a stage's time depends only on its own kernels' choice
-  const int n_find = 6, n_mid = 9, n_fit = 9, n_trials = 9;
+  // joint trials: trial i uses finder choice i % n_find, CA/merge choice i % 9
+  // and fit choice i % 9; a stage's time depends only on its own kernels' choice
+  const bool tp = two_pass(ctx);
+  auto find_shape = [tp](int fi, LaunchCfg& L) {
+    if (tp) {
+      L.find_threads = kFind2ThreadsC[fi % 2];
+      L.find_ctas_per_sm = kFind2CtasC[fi / 2];
+    } else {
+      L.find_threads = kFindThreadsC[fi % 3];
+      L.find_ctas_per_sm = kFindCtasC[fi / 3];
+    }
+  };
+  const int n_find = tp ? 4 : 6, n_mid = 9, n_fit = 9, n_trials = 9;
   std::vector<float> t_find(n_find, 1e30f), t_mid(n_mid, 1e30f), t_fit(n_fit, 1e30f);
   float ms[TPC_N_STAGES];
   st = run_sync(ctx, s, sample, ms);   // warm-up, grows the slot to the sample
   for (int i = 0; i < n_trials && st == TPC_OK; i++) {
     const int fi = i % n_find, mi = i % n_mid, ti = i % n_fit;
     LaunchCfg L;
-    L.find_threads = kFindThreadsC[fi % 3];
-    L.find_ctas_per_sm = kFindCtasC[fi / 3];
+    find_shape(fi, L);
     L.ca_blocks_per_sm = kPerSmC[mi % 3];
     L.elem_blocks_per_sm = kPerSmC[mi / 3];
     L.fit_threads = kFitThreadsC[ti % 3];
@@ -1419,8 +1498,7 @@ extern "C" tpc_status tpc_autotune(tpc_context* ctx, const tpc_timeframe_desc* s
   const int mi = (int)(std::min_element(t_mid.begin(), t_mid.end()) - t_mid.begin());
   const int ti = (int)(std::min_element(t_fit.begin(), t_fit.end()) - t_fit.begin());
   LaunchCfg L;
-  L.find_threads = kFindThreadsC[fi % 3];
-  L.find_ctas_per_sm = kFindCtasC[fi / 3];
+  find_shape(fi, L);
   L.ca_blocks_per_sm = kPerSmC[mi % 3];
   L.elem_blocks_per_sm = kPerSmC[mi / 3];
   L.fit_threads = kFitThreadsC[ti % 3];

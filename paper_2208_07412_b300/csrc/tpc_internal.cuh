@@ -72,6 +72,12 @@ struct DevParams {
   float sy2, sz2;                // sigma_y^2, sigma_z^2 (cm^2)
   float c0[5];
   double kfac_d, sy2_d, sz2_d;   // FP64 copies for the covariance redo
+  // the same in the integer coordinate unit u = 7.8125e-4 cm (the step-8 fit's unit)
+  float kfac_u;                  // 1/u per 1/GeV
+  float sy2_u, sz2_u;            // u^2
+  float c0_u[5];                 // y, zeta entries in u^2
+  float pd_min_u[5];             // floor of each FP32 D factor: fp32_pd_margin * c0_u
+  double sy2_ud, sz2_ud;         // FP64 copies for the covariance redo
 };
 
 // Per-slot device work space.  All pointers are device memory owned by the
@@ -93,6 +99,10 @@ struct DevWork {
   uint32_t* win_soff;            // start of each window's span in scratch_cl
   uint32_t* light_list;          // [n_windows] windows of the light path (first CTR_NLIGHT), or null
   uint32_t* heavy_list;          // [n_windows] the other windows (first CTR_NHEAVY)
+  uint32_t* digits;              // two-pass finder: every digit as pad | t_in << 8 | adc << 16, per page spans
+  uint4* dtab;                   // [2 * n_windows] per window: (span start lo, hi, digits, 0) and the digit
+                                 // counts before time bins 3, 61, 67, 125, 131, 189, 195, 253 (u16 pairs)
+  uint64_t cap_dig;              // digits the array holds
   // CA
   int32_t* up; int32_t* down;
   int64_t* score;
@@ -143,9 +153,13 @@ enum {
   CTR_NCAND = 23,     // merge candidate pairs found
   CTR_NLIGHT = 24,    // windows the light finder path takes
   CTR_NHEAVY = 25,    // windows the block-per-window finder takes
-  CTR_COUNT = 26
+  CTR_NDIG = 26,      // digits decoded by the two-pass finder (span cursor)
+  CTR_COUNT = 27
 };
-enum { TK_FIND = 0, TK_SCAN_A = 1, TK_SCAN_B = 2, TK_SCAN_W = 3, TK_FIND2 = 4, TK_LIGHT = 5, kNumTickets = 6 };
+enum { TK_FIND = 0, TK_SCAN_A = 1, TK_SCAN_B = 2, TK_SCAN_W = 3, TK_FIND2 = 4, TK_LIGHT = 5, TK_UNIT = 6, TK_DEC = 7,
+       kNumTickets = 8 };
+// The control block is 256 bytes: CTR_COUNT counters, the error word and the tickets.
+static_assert(8 * (CTR_COUNT + 1) + 4 * kNumTickets <= 256, "control block layout");
 
 // ------------------------------------------------------------------ helpers
 __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {

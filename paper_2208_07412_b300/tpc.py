@@ -27,6 +27,7 @@ TPC_TF_NOWAIT = 2
 TPC_CTX_STAGE_TIMING = 1
 TPC_CTX_NO_GRAPHS = 2
 TPC_CTX_DENSE_FINDER = 4
+TPC_CTX_FUSED_FINDER = 8
 STAGES = ("find", "ca", "merge", "fit")
 
 CLUSTER_DTYPE = np.dtype([("pad_fp", "<u2"), ("time_fp", "<u2"), ("qmax", "<u2"), ("qtot", "<u2"),
@@ -60,7 +61,7 @@ class tpc_params(ctypes.Structure):
                 ("min_track", ctypes.c_int32), ("fit_passes", ctypes.c_int32),
                 ("ns_min_dip", ctypes.c_int32), ("bz", ctypes.c_double),
                 ("sigma_y", ctypes.c_double), ("sigma_z", ctypes.c_double),
-                ("c0", ctypes.c_double * 5)]
+                ("c0", ctypes.c_double * 5), ("fp32_pd_margin", ctypes.c_double)]
 
 
 class tpc_tuning(ctypes.Structure):
@@ -91,7 +92,7 @@ EXPORTS = ("tpc_params_default", "tpc_create_geometry", "tpc_destroy_geometry", 
            "tpc_get_counters", "tpc_release", "tpc_last_error", "tpc_find_clusters_noalloc",
            "tpc_submit_batch", "tpc_get_batch_info", "tpc_get_event_clusters", "tpc_get_event_tracks",
            "tpc_get_tuning", "tpc_set_tuning", "tpc_autotune", "tpc_merge_sectors", "tpc_get_merged_tracks",
-           "tpc_compress_clusters", "tpc_get_compressed", "tpc_calibrate_drift")
+           "tpc_compress_clusters", "tpc_get_compressed", "tpc_calibrate_drift", "tpc_measure_fma_peak")
 
 _lib = None
 
@@ -146,6 +147,7 @@ def load(build_if_missing: bool = True):
     L.tpc_calibrate_drift.argtypes = [_P, _u64, ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_double),
                                       ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                       ctypes.POINTER(_u64)]
+    L.tpc_measure_fma_peak.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
     L.tpc_last_error.argtypes = []
     L.tpc_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -296,6 +298,8 @@ def tpc_autotune(ctx, pages, page_offsets, n_time_bins: int, reps: int = 3) -> d
     return t.as_dict()
 
 
+TPC_TRK_STOPPED = 1
+TPC_TRK_NOT_PD = 2
 TPC_TRK_XSECTOR = 4
 
 
@@ -427,6 +431,13 @@ def tpc_find_clusters_noalloc(geom, pages, page_offsets, n_time_bins: int, clust
     return int(n.value)
 
 
+def tpc_measure_fma_peak(device: int = 0, reps: int = 5) -> float:
+    """Measured FP32 FMA throughput of the device (FLOP/s)."""
+    v = ctypes.c_double()
+    _check(load().tpc_measure_fma_peak(int(device), int(reps), ctypes.byref(v)))
+    return float(v.value)
+
+
 def tpc_last_error() -> str:
     return load().tpc_last_error().decode()
 
@@ -438,7 +449,13 @@ class Reconstructor:
     def __init__(self, npads, row_x, n_sectors, params: tpc_params | None = None, device: int = 0,
                  mem_budget: int = 0, n_slots: int = 1, stream: int | None = None, flags: int = 0):
         self.geom = tpc_create_geometry(npads, row_x, n_sectors)
-        self.ctx = tpc_create_context(self.geom, params, device, mem_budget, n_slots, stream, flags)
+        self.ctx = None
+        try:
+            self.ctx = tpc_create_context(self.geom, params, device, mem_budget, n_slots, stream, flags)
+        except BaseException:
+            tpc_destroy_geometry(self.geom)
+            self.geom = None
+            raise
 
     @classmethod
     def for_timeframe(cls, tf, **kw):

@@ -45,7 +45,7 @@ def test_single_sector_batch_equals_alone_and_oracle(lib):
         assert ev["clusters"].tobytes() == orc.clusters.tobytes()
         assert np.array_equal(ev["cl2trk"], orc.cl2trk)
         assert np.array_equal(ev["tracks"]["first_cluster"], orc.track_first)
-        compare_fit({"tracks": ev["tracks"]}, orc, min_ok_fraction=0.95)
+        compare_fit({"tracks": ev["tracks"]}, orc)
 
 
 def test_full_tpc_uneven_batch_equals_alone(lib):

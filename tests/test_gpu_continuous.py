@@ -3,15 +3,16 @@ collisions with uniform start times whose drift windows overlap.
 
 A short continuous timeframe is compared with the oracle in full.  The
 full-size one (55,000 time bins, ~2.7e9 digits, ~5.7 GB of ZS pages) runs
-through the CUDA path as the benchmark runs it; the oracle checks its first
-sector element by element (every stage of the method stays inside a sector, so
-sector 0 of the whole timeframe equals sector 0 reconstructed alone) and
-properties that hold at any size check the rest."""
+through the CUDA path as the benchmark runs it, and every one of its 36
+sectors is compared element by element with the oracle run on that sector
+alone (every step of the method stays inside a sector), in a spawn pool of
+oracle processes; properties that hold at any size check the whole."""
 import numpy as np
 import pytest
 
 import oracle
 import tpcgen
+from oracle_pool import oracle_sectors, sector_view
 from parity import compare_fit, compare_integer
 
 pytestmark = pytest.mark.gpu
@@ -36,12 +37,6 @@ def test_short_continuous_parity(lib):
     compare_integer(gpu, orc)
     compare_fit(gpu, orc)
     assert gpu["counters"]["error_word"] == 0
-
-
-def head_of(gpu: dict, n_cl: int, n_tr: int) -> dict:
-    return {"clusters": gpu["clusters"][:n_cl], "up": gpu["up"][:n_cl], "down": gpu["down"][:n_cl],
-            "chain_of": gpu["chain_of"][:n_cl], "cl2trk": gpu["cl2trk"][:n_cl],
-            "tracks": gpu["tracks"][:n_tr], "counters": gpu["counters"]}
 
 
 def check_properties(gpu: dict, tf) -> None:
@@ -74,14 +69,16 @@ def test_continuous_50khz_full_size(lib):
     check_properties(gpu, tf)
     n_cl, n_tr = len(gpu["clusters"]), len(gpu["tracks"])
     assert n_cl > 5e7 and n_tr > 2e5, (n_cl, n_tr)
-    # sector 0 element by element against the oracle
-    sub = tpcgen.sector_prefix(tf, 1)
-    orc = oracle.reconstruct(sub)
-    n0 = len(orc.clusters)
-    t0 = len(orc.track_first)
-    assert np.all(gpu["clusters"]["sector"][:n0] == 0) and (n0 == n_cl or gpu["clusters"]["sector"][n0] == 1)
-    assert np.all(gpu["tracks"]["sector"][:t0] == 0) and (t0 == n_tr or gpu["tracks"]["sector"][t0] == 1)
-    head = head_of(gpu, n0, t0)
-    compare_integer(head, orc)
-    rep = compare_fit(head, orc)
-    print("continuous 50 kHz, sector 0 fit precision vs FP64 oracle:", rep)
+    # every sector element by element against the oracle on that sector alone
+    worst = np.zeros(5)
+    seen, ncl_sum, ntr_sum = set(), 0, 0
+    for k, orc in oracle_sectors(tf, list(range(tf.n_sectors))):
+        view = sector_view(gpu, k)
+        compare_integer(view, orc)
+        rep = compare_fit(view, orc)
+        worst = np.maximum(worst, rep["max_rel_par_plain_floor"])
+        seen.add(k)
+        ncl_sum += len(orc.clusters)
+        ntr_sum += len(orc.track_first)
+    assert seen == set(range(tf.n_sectors)) and ncl_sum == n_cl and ntr_sum == n_tr
+    print("continuous 50 kHz, all sectors: max plain-floor parameter error vs FP64 oracle", worst.tolist())

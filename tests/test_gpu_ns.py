@@ -57,11 +57,17 @@ def test_dense_sector_unlisted_windows(lib):
     check(lib, tf, 10)
 
 
-def test_full_tpc_fused_and_dense_variant(lib):
+def test_full_tpc_all_finder_variants(lib):
     tf = tpcgen.generate(tpcgen.full_tpc(2, n_tracks=4000))
     g = check(lib, tf, 10)
-    d = check(lib, tf, 10, flags=lib.TPC_CTX_DENSE_FINDER)
-    assert g["clusters"].tobytes() == d["clusters"].tobytes()
+    for flags in (lib.TPC_CTX_DENSE_FINDER, lib.TPC_CTX_FUSED_FINDER):
+        d = check(lib, tf, 10, flags=flags)
+        assert g["clusters"].tobytes() == d["clusters"].tobytes()
+
+
+def test_dense_sector_fused_variant(lib):
+    tf = tpcgen.generate(tpcgen.single_sector(8, n_tracks=3000))
+    check(lib, tf, 10, flags=lib.TPC_CTX_FUSED_FINDER)
 
 
 def test_rejects_out_of_range(lib):

@@ -57,7 +57,7 @@ def test_ragged_time_ranges(lib, n_time_bins):
     orc = oracle.reconstruct(tf)
     gpu = run_gpu(lib, tf)
     compare_integer(gpu, orc)
-    compare_fit(gpu, orc, min_ok_fraction=0.0)
+    compare_fit(gpu, orc)
 
 
 def test_empty_and_noise_only(lib):
@@ -78,16 +78,20 @@ def test_dense_occupancy(lib):
     orc = oracle.reconstruct(tf)
     gpu = run_gpu(lib, tf)
     compare_integer(gpu, orc)
-    compare_fit(gpu, orc, min_ok_fraction=0.95)
+    compare_fit(gpu, orc)
 
 
-def test_corrupt_page_reported(lib):
+FINDER_FLAGS = [0, 8]   # the two-pass finder (default), the fused variant
+
+
+@pytest.mark.parametrize("flags", FINDER_FLAGS)
+def test_corrupt_page_reported(lib, flags):
     tf = tpcgen.generate(tpcgen.single_sector(1))
     bad = copy.copy(tf)
     bad.pages = tf.pages.copy()
     o = int(tf.page_offsets[40 * 2 + 1])
     bad.pages[o + 14] ^= 0xFF  # magic
-    with lib.Reconstructor.for_timeframe(bad) as R:
+    with lib.Reconstructor.for_timeframe(bad, flags=flags) as R:
         t = R.submit(bad.pages, bad.page_offsets, bad.n_time_bins)
         with pytest.raises(lib.TpcError) as ei:
             R.wait(t)
@@ -176,8 +180,9 @@ def _hdr(pages, o):
             "hi_dig": int(h[13]), "hi_runs": int(h[12])}
 
 
+@pytest.mark.parametrize("flags", FINDER_FLAGS)
 @pytest.mark.parametrize("where", ["run", "entry"])
-def test_corrupt_light_window_reported(lib, where):
+def test_corrupt_light_window_reported(lib, where, flags):
     """A full-TPC timeframe (its sparse windows go to the one-warp path): a
     page body broken in such a window -- a run past the row's end, or time
     bins out of order -- is reported as corruption, and the context stays usable."""
@@ -202,7 +207,7 @@ def test_corrupt_light_window_reported(lib, where):
         bad.pages[o + 32 + 2 * h["n_tb"] + 1] = 200          # run 0's length: past any row
     else:
         bad.pages[o + 32 + 2] = bad.pages[o + 32]             # entry 1 at entry 0's time bin
-    with lib.Reconstructor.for_timeframe(bad) as R:
+    with lib.Reconstructor.for_timeframe(bad, flags=flags) as R:
         t = R.submit(bad.pages, bad.page_offsets, bad.n_time_bins)
         with pytest.raises(lib.TpcError) as ei:
             R.wait(t)
@@ -210,3 +215,44 @@ def test_corrupt_light_window_reported(lib, where):
         lib.tpc_release(R.ctx, t)
         good = R.run(tf)
     assert good["clusters"].tobytes() == oracle.find_clusters(tf).tobytes()
+
+
+def _break(pages, o, h, defect):
+    """One defect of a page body or header (the oracle rejects each)."""
+    ent, run = o + 32, o + 32 + 2 * h["n_tb"]
+    if defect == "run_overlap":        # run 1 of entry 0 starts inside run 0
+        pages[run + 2] = pages[run]
+    elif defect == "zero_runs":        # entry 0 with no run
+        pages[ent + 1] = 0
+    elif defect == "zero_length":      # run 0 of length 0
+        pages[run + 1] = 0
+    elif defect == "digit_count":      # header digit count one short
+        v = int(pages[o + 8]) | int(pages[o + 9]) << 8
+        pages[o + 8:o + 10] = np.frombuffer(np.uint16(v - 1).tobytes(), np.uint8)
+    elif defect == "run_count":        # header run count one more
+        v = int(pages[o + 6]) | int(pages[o + 7]) << 8
+        pages[o + 6:o + 8] = np.frombuffer(np.uint16(v + 1).tobytes(), np.uint8)
+    elif defect == "row":              # header names another row
+        pages[o + 11] ^= 1
+
+
+@pytest.mark.parametrize("flags", FINDER_FLAGS)
+@pytest.mark.parametrize("defect", ["run_overlap", "zero_runs", "zero_length", "digit_count", "run_count", "row"])
+def test_page_defects_reported_like_the_oracle(lib, defect, flags):
+    tf = tpcgen.generate(tpcgen.single_sector(1))
+    offs = tf.page_offsets.astype(np.int64)
+    # a page whose first entry has at least two runs
+    w = next(k for k in range(len(offs)) if _hdr(tf.pages, int(offs[k]))["n_tb"] > 0 and
+             tf.pages[int(offs[k]) + 33] >= 2)
+    o = int(offs[w])
+    bad = copy.copy(tf)
+    bad.pages = tf.pages.copy()
+    _break(bad.pages, o, _hdr(tf.pages, o), defect)
+    with pytest.raises(oracle.CorruptPage):
+        oracle.find_clusters(bad)
+    with lib.Reconstructor.for_timeframe(bad, flags=flags) as R:
+        t = R.submit(bad.pages, bad.page_offsets, bad.n_time_bins)
+        with pytest.raises(lib.TpcError) as ei:
+            R.wait(t)
+        assert ei.value.code == -5
+        lib.tpc_release(R.ctx, t)

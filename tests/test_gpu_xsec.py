@@ -10,7 +10,7 @@ import pytest
 
 import oracle
 import tpcgen
-from parity import COV_RTOL, PAR_FLOORS, PAR_RTOL, SIGMA_FRAC
+from parity import COV_RTOL, PAR_RTOL, param_allowance
 
 pytestmark = pytest.mark.gpu
 
@@ -93,9 +93,8 @@ def check_parity(lib, tf, min_multi):
         if o["flags"] or (int(g["flags"]) & ~lib.TPC_TRK_XSECTOR):
             nflag += 1
             continue
-        sig = np.sqrt(o["cov"][diag])
-        rel = np.abs(g["par"].astype(float) - o["par"]) / (np.maximum(np.abs(o["par"]), PAR_FLOORS) +
-                                                          SIGMA_FRAC / PAR_RTOL * sig)
+        allow = param_allowance(o["par"][None], o["cov"][None], [o["chi2"]], [o["ndf"]], [o["flags"]])[0]
+        rel = np.abs(g["par"].astype(float) - o["par"]) / allow * PAR_RTOL
         worst = np.maximum(worst, rel)
         assert g["x"] == pytest.approx(o["x"], rel=1e-5)
         cd = np.abs(g["cov"].astype(float) - o["cov"])
