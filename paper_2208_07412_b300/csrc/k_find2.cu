@@ -72,9 +72,13 @@ __device__ __forceinline__ void prefetch_l2_bytes(const void* p, unsigned long l
   }
 }
 
+constexpr int kDecStage = 4096;                      // bytes of a page body staged per warp
+
 __global__ void __launch_bounds__(kDecThreads, 5) k_decode_digits(DevGeom G, DevWork W, unsigned int n_windows) {
+  __shared__ __align__(16) uint8_t stage_all[kDecThreads / 32][kDecStage];
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
+  uint8_t* stage = stage_all[threadIdx.x >> 5];
   const int T = G.n_time_bins;
   while (true) {
     unsigned int w = 0;
@@ -104,19 +108,30 @@ __global__ void __launch_bounds__(kDecThreads, 5) k_decode_digits(DevGeom G, Dev
     __syncwarp();
     if (ok) {
       const uint8_t* pg = W.pages + o;
-      // the whole page into L2 at once: its chunks are then read from L2, not
-      // one DRAM round trip after the other
-      if (lane == 0 && h.len > 32) prefetch_l2_bytes(pg + 32, h.len - 32);
-      const uint16_t* ent = reinterpret_cast<const uint16_t*>(pg + 32);
+      // the page body in one round trip: staged in the warp's shared memory
+      // (16-byte loads) when it fits, else prefetched into L2 so that its
+      // chunks are read from L2 rather than one DRAM round trip after another
+      const uint8_t* body = pg + 32;
+      const unsigned body_len = h.len - 32u;
+      if (body_len <= (unsigned)kDecStage) {
+        const uint4* src = reinterpret_cast<const uint4*>(body);
+        uint4* dst = reinterpret_cast<uint4*>(stage);
+        for (unsigned i = lane; i < body_len / 16u; i += 32u) dst[i] = __ldg(src + i);
+        __syncwarp();
+        body = stage;
+      } else if (lane == 0) {
+        prefetch_l2_bytes(body, body_len);
+      }
+      const uint16_t* ent = reinterpret_cast<const uint16_t*>(body);
       const uint16_t* run = ent + h.n_tb;
-      const uint32_t* adc = reinterpret_cast<const uint32_t*>(pg + h.body);
+      const uint32_t* adc = reinterpret_cast<const uint32_t*>(body + (h.body - 32u));
       uint32_t* out = W.digits + base;
       for (int E = 0; E < h.n_tb && !bad; E += 32) {
         // ---- 32 entries: time bin, run count, first run
         const int e = E + lane, n_ent = min(32, h.n_tb - E);
         int t = 0, nr = 0;
         if (lane < n_ent) {
-          const uint32_t v = __ldg(ent + e);
+          const uint32_t v = ent[e];
           t = v & 0xff;
           nr = v >> 8;
         }
@@ -134,7 +149,7 @@ __global__ void __launch_bounds__(kDecThreads, 5) k_decode_digits(DevGeom G, Dev
           const int ri = R + lane, n_run = min(32, r_end - R);
           int ps = 0, len = 0;
           if (lane < n_run) {
-            const uint32_t rv = __ldg(run + ri);
+            const uint32_t rv = run[ri];
             ps = rv & 0xff;
             len = rv >> 8;
           }
@@ -167,7 +182,7 @@ __global__ void __launch_bounds__(kDecThreads, 5) k_decode_digits(DevGeom G, Dev
             const int t_k = __shfl_sync(FULL, tr, k);
             if (dk < n_rd) {
               const unsigned di = (unsigned)(d_cur + dk);
-              const uint32_t wv = __ldg(adc + di / 3u);
+              const uint32_t wv = adc[di / 3u];
               const uint32_t q = (wv >> (10u * (di % 3u))) & kAdcMask;
               out[di] = (uint32_t)(ps_k + dk - rel_k) | ((uint32_t)t_k << 8) | (q << 16);
             }
@@ -178,7 +193,7 @@ __global__ void __launch_bounds__(kDecThreads, 5) k_decode_digits(DevGeom G, Dev
       }
       if (!bad && (r_cur != h.n_runs || d_cur != h.n_dig)) bad = true;
     }
-    __syncwarp();
+    __syncwarp();   // the stage is free again
     if (lane == 0) {
       if (bad) atomicOr(W.err, kErrCorrupt);
       const uint32_t n = bad ? 0u : (uint32_t)h.n_dig;
@@ -277,6 +292,13 @@ __device__ __forceinline__ bool ns_drop_plane(const uint16_t* pl, int L, int ps,
   return false;
 }
 
+// L2 prefetch of n digit words from p (widened to whole 16-byte blocks).
+__device__ __forceinline__ void prefetch_l2_span(const uint32_t* p, int n) {
+  const uintptr_t a = reinterpret_cast<uintptr_t>(p) & ~(uintptr_t)15;
+  const uintptr_t b = (reinterpret_cast<uintptr_t>(p + n) + 15) & ~(uintptr_t)15;
+  prefetch_l2_bytes(reinterpret_cast<const void*>(a), (unsigned long long)(b - a));
+}
+
 // Plane row offsets of the three segments: row = t_in + offset.
 __device__ __forceinline__ int seg_row_offset(int k, int c) {
   return k == 0 ? kHalo - kFrag : (k == 1 ? kHalo - kChunkT * c : kHalo + kFrag - kChunkT * (kUnitsPerWin - 1));
@@ -309,7 +331,12 @@ __global__ void __launch_bounds__(kThreads) k_find_units(DevGeom G, DevParams P,
   for (; u < n_units; u += gridDim.x) {
     if (tid == 0) {
       U.d = nxt;
-      if (u + gridDim.x < n_units) unit_desc(G, W, u + gridDim.x, nxt);   // consumed next iteration
+      if (u + gridDim.x < n_units) {
+        unit_desc(G, W, u + gridDim.x, nxt);          // consumed next iteration
+#pragma unroll
+        for (int k = 0; k < 3; k++)                   // its digits into L2 meanwhile
+          if (nxt.seg_n[k] > 0) prefetch_l2_span(W.digits + nxt.seg_start[k], nxt.seg_n[k]);
+      }
     }
     __syncthreads();
     const int n0 = U.d.seg_n[0], n01 = n0 + U.d.seg_n[1], n_all = n01 + U.d.seg_n[2];
