@@ -405,6 +405,52 @@ tpc_status tpc_merge_sectors(tpc_context* ctx, uint64_t ticket, const tpc_xs_par
 tpc_status tpc_get_merged_tracks(tpc_context* ctx, uint64_t ticket, tpc_track* out, uint64_t cap, uint64_t* n,
                                  int32_t* cluster_to_track, int32_t* link);
 
+/* Looper-leg join parameters (step 9b). */
+typedef struct {
+  double  chi2_cut;        /* 30   matching chi2 (5 parameters) of two legs for a link, 0..1e6 */
+  double  loop_radius_cm;  /* 275  a track can loop when its circle (|q/pT| raised by 3 sigma)
+                                   stays within this distance of the beam axis: the 250 cm
+                                   outer field cage + 10 %; 0 < r <= 1e4 */
+  int32_t max_turns;       /* 4    largest number of turns between two linked legs, 1..15 */
+  int32_t pad;
+} tpc_loop_params;
+
+/* Step 9b, optional: link the legs of looping tracks within each sector, on a
+ * finished ticket's device-resident step-8 tracks.  The paper names the full
+ * TPC tracking on the EPN GPUs ("Hardware and data flow"); a track whose
+ * circle stays inside the TPC crosses a sector once per turn on the same
+ * transverse path, and steps 5-8 find each crossing as a track of its own.
+ * The library's definition:
+ *   - a track can loop when the circle through its fitted point and direction
+ *     with |q/pT| raised by 3 sigma has |centre| + 1/|k| <= loop_radius (centre
+ *     (x - snp/k, y + cos(phi)/k) in the sector frame, k = -bz c 1e-2 q/pT);
+ *   - each fit's covariance is scaled by max(1, chi2/ndf);
+ *   - candidates: tracks A < B of one sector (of one event) that can loop,
+ *     fits unflagged, q/pT of one sign; both carried along their helices to
+ *     the larger reference x; m = the integer nearest (ties away from zero)
+ *     to (zeta_B - zeta_A) / S with S = tgl_A 2 pi / |k_A| (the zeta advance
+ *     of one turn), 1 <= |m| <= max_turns;
+ *   - chi2 = d^T (J C_A J^T + C_B)^-1 d with d = s_B - (s_A + m S e_zeta) and
+ *     J the identity plus m 2 pi / |k_A| at (zeta, tgl) and -m S / (q/pT)_A at
+ *     (zeta, q/pT); accepted when chi2 <= chi2_cut and directed A -> B for
+ *     m > 0, B -> A for m < 0;
+ *   - a track's next (previous) leg is its outgoing (incoming) accepted pair of
+ *     least |m|, then least chi2, then lowest index; f -> g links when g is
+ *     f's next and f is g's previous.  Chains of links are one looper's turns.
+ * The chi2 is computed in FP32 on the FP32 fits.  lp: NULL for the defaults.
+ * *n_links (may be NULL): links made.  Runs on the ticket's stream and waits
+ * for it; results until tpc_release.
+ * Errors: TPC_E_INVAL (bad parameters, 2^28 or more tracks), TPC_E_NOTREADY
+ * (ticket not done), TPC_E_NOTFOUND, TPC_E_CUDA, TPC_E_NOMEM. */
+tpc_status tpc_join_loopers(tpc_context* ctx, uint64_t ticket, const tpc_loop_params* lp, uint64_t* n_links);
+
+/* The links of tpc_join_loopers: next[t] / prev[t] (host memory, one entry
+ * per step-8 track, either may be NULL) = the linked following / preceding
+ * leg of track t or -1; in a batch, indices over the whole batch's tracks.
+ * *n_tracks (may be NULL): the number of entries.  TPC_E_NOTREADY if
+ * tpc_join_loopers has not run on the ticket. */
+tpc_status tpc_get_looper_links(tpc_context* ctx, uint64_t ticket, int32_t* next, int32_t* prev, uint64_t* n_tracks);
+
 /* Track-model compression parameters (step 10). */
 typedef struct {
   double step_y_cm;  /* 0.0125    quantisation step of the y residual (1/32 pad) */

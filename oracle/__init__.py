@@ -136,9 +136,15 @@ def _load():
         L.orc_xs_chi2.restype = ctypes.c_double
         L.orc_fit_points_xs.argtypes = [_P, ctypes.c_int, _P, _P, _P, _P, _P]
         L.orc_merge_sectors.argtypes = [_P, _P, _P, _P, ctypes.c_int64, _P, ctypes.c_int64, _P, _P, _P, _P,
-                                        _P, _P, _P, _P]
+                                        _P, _P, _P, _P, _P]
         L.orc_merge_sectors.restype = ctypes.c_int64
-        L.orc_compress.argtypes = [_P, _P, _P, _P, ctypes.c_int64, _P, ctypes.c_int64, _P, _P, _P, _P]
+        L.orc_join_loopers.argtypes = [_P, _P, _P, _P, ctypes.c_int64, _P, ctypes.c_int64, _P, _P, _P, _P, _P]
+        L.orc_join_loopers.restype = ctypes.c_int64
+        L.orc_loop_pair.argtypes = [_P, _P, _P, _P, _P]
+        L.orc_loop_pair.restype = ctypes.c_double
+        L.orc_loops.argtypes = [_P, _P, ctypes.c_double]
+        L.orc_loops.restype = ctypes.c_int
+        L.orc_compress.argtypes = [_P, _P, _P, _P, ctypes.c_int64, _P, ctypes.c_int64, _P, _P, _P, _P, _P, _P]
         L.orc_compress.restype = ctypes.c_int64
         L.orc_calibrate_drift.argtypes = [_P, _P, _P, ctypes.c_int64, ctypes.c_double, _P, _P, _P]
         L.orc_calibrate_drift.restype = ctypes.c_int64
@@ -379,6 +385,7 @@ class XsResult:
     ncl: np.ndarray         # [n_merged]
     npieces: np.ndarray     # [n_merged]
     cl2trk: np.ndarray      # [n_clusters] merged track or -1
+    borderline: np.ndarray  # [n_tracks] 1 where the piece's decision is within 1 % of flipping
 
 
 def merge_sectors(tf, res, params: OracleParams | None = None, xs: XsParams | None = None) -> XsResult:
@@ -398,13 +405,83 @@ def merge_sectors(tf, res, params: OracleParams | None = None, xs: XsParams | No
     gf = np.zeros(max(nt, 1), np.int32)
     gn = np.zeros(max(nt, 1), np.int32)
     gp = np.zeros(max(nt, 1), np.int32)
+    bl = np.zeros(max(nt, 1), np.int8)
     ng = L.orc_merge_sectors(inp.ref, ctypes.byref(p), ctypes.byref(xp), cl.ctypes.data if len(cl) else None,
                              len(cl), c2t.ctypes.data if len(c2t) else None, nt,
                              fits.ctypes.data if nt else None, link.ctypes.data, best.ctypes.data,
-                             grp.ctypes.data, gfit.ctypes.data, gf.ctypes.data, gn.ctypes.data, gp.ctypes.data)
+                             grp.ctypes.data, gfit.ctypes.data, gf.ctypes.data, gn.ctypes.data, gp.ctypes.data,
+                             bl.ctypes.data)
     new_c2t = np.where(c2t >= 0, grp[np.maximum(c2t, 0)], -1).astype(np.int32)
     return XsResult(link[:nt].copy(), best[:nt].copy(), grp[:nt].copy(), gfit[:ng].copy(), gf[:ng].copy(),
-                    gn[:ng].copy(), gp[:ng].copy(), new_c2t)
+                    gn[:ng].copy(), gp[:ng].copy(), new_c2t, bl[:nt].copy())
+
+
+class _LoopParams(ctypes.Structure):
+    _fields_ = [("chi2_cut", ctypes.c_double), ("loop_radius_cm", ctypes.c_double),
+                ("max_turns", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
+@dataclass
+class LoopParams:
+    """Step 9b (looper legs): chi2 cut of a leg pair, radius within which a
+    fitted circle counts as looping (the 250 cm outer field cage + 10 %), and
+    the largest number of turns between two joined legs."""
+    chi2_cut: float = 30.0
+    loop_radius_cm: float = 275.0
+    max_turns: int = 4
+
+    def _c(self) -> _LoopParams:
+        return _LoopParams(self.chi2_cut, self.loop_radius_cm, self.max_turns, 0)
+
+
+@dataclass
+class LoopResult:
+    next: np.ndarray        # [n_tracks] the following leg (further along the fitted motion) or -1
+    prev: np.ndarray        # [n_tracks] the preceding leg or -1
+    next_chi2: np.ndarray   # [n_tracks] chi2 of the link to next, or -1
+    borderline: np.ndarray  # [n_tracks] 1 where a decision about the track is within 1 % of flipping
+    n_links: int
+
+
+def join_loopers(tf, res, params: OracleParams | None = None, loop: LoopParams | None = None) -> LoopResult:
+    """Looper-leg join of an OracleResult's tracks (step 9b)."""
+    L = _load()
+    p = (params or OracleParams())._c()
+    lp = (loop or LoopParams())._c()
+    inp = _In.from_tf(tf)
+    cl = np.ascontiguousarray(res.clusters)
+    c2t = np.ascontiguousarray(res.cl2trk, np.int32)
+    fits = np.ascontiguousarray(res.fits)
+    nt = len(fits)
+    nxt = np.zeros(max(nt, 1), np.int32)
+    prv = np.zeros(max(nt, 1), np.int32)
+    c2 = np.zeros(max(nt, 1), np.float64)
+    bl = np.zeros(max(nt, 1), np.int8)
+    n = L.orc_join_loopers(inp.ref, ctypes.byref(p), ctypes.byref(lp), cl.ctypes.data if len(cl) else None, len(cl),
+                           c2t.ctypes.data if len(c2t) else None, nt, fits.ctypes.data if nt else None,
+                           nxt.ctypes.data, prv.ctypes.data, c2.ctypes.data, bl.ctypes.data)
+    return LoopResult(nxt[:nt].copy(), prv[:nt].copy(), c2[:nt].copy(), bl[:nt].copy(), int(n))
+
+
+def loop_pair(fa, fb, params: OracleParams | None = None, loop: LoopParams | None = None) -> tuple[float, int]:
+    """Step 9b's matching chi2 of two fitted legs (FIT_DTYPE records) and the
+    signed number of turns from A to B; chi2 -1 when the pair is no candidate."""
+    L = _load()
+    p = (params or OracleParams())._c()
+    lp = (loop or LoopParams())._c()
+    a = np.ascontiguousarray(np.asarray(fa, FIT_DTYPE).reshape(1))
+    b = np.ascontiguousarray(np.asarray(fb, FIT_DTYPE).reshape(1))
+    m = ctypes.c_int(0)
+    c2 = float(L.orc_loop_pair(ctypes.byref(p), ctypes.byref(lp), a.ctypes.data, b.ctypes.data, ctypes.byref(m)))
+    return c2, int(m.value)
+
+
+def loops(fit, r_out_cm: float, params: OracleParams | None = None) -> bool:
+    """Step 9b's looping test: the fitted circle lies within r_out_cm."""
+    L = _load()
+    p = (params or OracleParams())._c()
+    a = np.ascontiguousarray(np.asarray(fit, FIT_DTYPE).reshape(1))
+    return bool(L.orc_loops(ctypes.byref(p), a.ctypes.data, float(r_out_cm)))
 
 
 class _CmpParams(ctypes.Structure):
@@ -415,9 +492,12 @@ STEP_Y = 0.4 / 32     # 1/32 pad, cm
 STEP_Z = 0.5 / 32     # 1/32 time bin, cm
 
 
-def compress(tf, res, step_y: float = STEP_Y, step_z: float = STEP_Z, params: OracleParams | None = None):
+def compress(tf, res, step_y: float = STEP_Y, step_z: float = STEP_Z, params: OracleParams | None = None,
+             quotients: bool = False):
     """Track-model compression of the clusters on an OracleResult's tracks
-    (step 10).  Returns (code_y, code_z, status) per cluster."""
+    (step 10).  Returns (code_y, code_z, status) per cluster, and with
+    quotients=True also the residuals in steps before rounding (NaN where no
+    prediction was made)."""
     L = _load()
     p = (params or OracleParams())._c()
     cp = _CmpParams(float(step_y), float(step_z))
@@ -429,9 +509,13 @@ def compress(tf, res, step_y: float = STEP_Y, step_z: float = STEP_Z, params: Or
     cy = np.zeros(max(n, 1), np.int8)
     cz = np.zeros(max(n, 1), np.int8)
     st = np.zeros(max(n, 1), np.uint8)
+    qy = np.zeros(max(n, 1), np.float64)
+    qz = np.zeros(max(n, 1), np.float64)
     L.orc_compress(inp.ref, ctypes.byref(p), ctypes.byref(cp), cl.ctypes.data if n else None, n,
                    c2t.ctypes.data if n else None, len(fits), fits.ctypes.data if len(fits) else None,
-                   cy.ctypes.data, cz.ctypes.data, st.ctypes.data)
+                   cy.ctypes.data, cz.ctypes.data, st.ctypes.data, qy.ctypes.data, qz.ctypes.data)
+    if quotients:
+        return cy[:n].copy(), cz[:n].copy(), st[:n].copy(), qy[:n].copy(), qz[:n].copy()
     return cy[:n].copy(), cz[:n].copy(), st[:n].copy()
 
 

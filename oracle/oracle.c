@@ -773,6 +773,9 @@ int orc_fit_all(const orc_input* in, const orc_params* P, const orc_cluster* cl,
  *   - mutual best pairs under chi2 <= chi2_cut link (ties: lower index);
  *   - chained pieces form one track, refitted over all their clusters with the
  *     frame switched at each sector change.
+ * borderline[t] (may be NULL; test output, not part of the definition) marks a
+ * piece whose decision is within 1 % of flipping: a candidate chi2 within 1 %
+ * of the cut, or a runner-up within 1 % of the best on either side.
  * Rotation of a state (y, zeta, snp, tgl, q/pT) at x from a frame at angle
  * alpha_old to one at alpha_new (delta = alpha_old - alpha_new): the point
  * (x, y) maps to (x cos d - y sin d, x sin d + y cos d), the direction angle
@@ -969,7 +972,8 @@ static int neighbour_sector(int s, int side) {
 int64_t orc_merge_sectors(const orc_input* in, const orc_params* P, const orc_xs_params* XP,
                           const orc_cluster* cl, int64_t n, const int32_t* cl2trk, int64_t nt,
                           const orc_fit* fits, int32_t* link, double* best_chi2, int32_t* group_of,
-                          orc_fit* gfit, int32_t* g_first, int32_t* g_ncl, int32_t* g_npieces) {
+                          orc_fit* gfit, int32_t* g_first, int32_t* g_ncl, int32_t* g_npieces,
+                          int8_t* borderline) {
   const double u = 7.8125e-4;
   /* per-track cluster lists in row order */
   int64_t* cnt = (int64_t*)calloc((size_t)nt + 1, sizeof(int64_t));
@@ -1006,9 +1010,12 @@ int64_t orc_merge_sectors(const orc_input* in, const orc_params* P, const orc_xs
   /* best candidates (chi2, index) both ways */
   double* bb = (double*)malloc(sizeof(double) * (nt + 1));
   double* ba = (double*)malloc(sizeof(double) * (nt + 1));
+  double* bb2 = (double*)malloc(sizeof(double) * (nt + 1));   /* runners-up */
+  double* ba2 = (double*)malloc(sizeof(double) * (nt + 1));
   int32_t* ib = (int32_t*)malloc(sizeof(int32_t) * (nt + 1));
   int32_t* ia = (int32_t*)malloc(sizeof(int32_t) * (nt + 1));
-  for (int64_t t = 0; t < nt; t++) { bb[t] = ba[t] = -1.0; ib[t] = ia[t] = -1; }
+  for (int64_t t = 0; t < nt; t++) { bb[t] = ba[t] = bb2[t] = ba2[t] = -1.0; ib[t] = ia[t] = -1; }
+  if (borderline) for (int64_t t = 0; t < nt; t++) borderline[t] = 0;
   for (int64_t a = 0; a < nt; a++) {
     if (!exit_side[a] || fits[a].flags) continue;
     int sb = neighbour_sector(sec[a], exit_side[a]);
@@ -1016,11 +1023,20 @@ int64_t orc_merge_sectors(const orc_input* in, const orc_params* P, const orc_xs
       if (sec[b] != sb || entry_side[b] != -exit_side[a] || row_out[a] >= row_in[b] || fits[b].flags) continue;
       if (llabs(z_in[b] - z_out[a]) > Dz) continue;
       double c2 = orc_xs_chi2(P, &fits[a], sector_alpha(sec[a]), &fits[b], sector_alpha(sec[b]));
+      if (borderline && c2 >= 0.0 && fabs(c2 - XP->chi2_cut) <= 0.01 * XP->chi2_cut) borderline[a] = borderline[b] = 1;
       if (c2 < 0.0 || c2 > XP->chi2_cut) continue;
-      if (ib[a] < 0 || c2 < bb[a] || (c2 == bb[a] && b < ib[a])) { bb[a] = c2; ib[a] = (int32_t)b; }
-      if (ia[b] < 0 || c2 < ba[b] || (c2 == ba[b] && a < ia[b])) { ba[b] = c2; ia[b] = (int32_t)a; }
+      if (ib[a] < 0 || c2 < bb[a] || (c2 == bb[a] && b < ib[a])) { bb2[a] = bb[a]; bb[a] = c2; ib[a] = (int32_t)b; }
+      else if (bb2[a] < 0.0 || c2 < bb2[a]) bb2[a] = c2;
+      if (ia[b] < 0 || c2 < ba[b] || (c2 == ba[b] && a < ia[b])) { ba2[b] = ba[b]; ba[b] = c2; ia[b] = (int32_t)a; }
+      else if (ba2[b] < 0.0 || c2 < ba2[b]) ba2[b] = c2;
     }
   }
+  /* a runner-up within 1 % of the best makes the choice borderline */
+  if (borderline)
+    for (int64_t t = 0; t < nt; t++) {
+      if (bb2[t] >= 0.0 && bb2[t] - bb[t] <= 0.01 * (bb[t] > 1.0 ? bb[t] : 1.0)) borderline[t] = 1;
+      if (ba2[t] >= 0.0 && ba2[t] - ba[t] <= 0.01 * (ba[t] > 1.0 ? ba[t] : 1.0)) borderline[t] = 1;
+    }
   int32_t* prev = (int32_t*)malloc(sizeof(int32_t) * (nt + 1));
   for (int64_t t = 0; t < nt; t++) { link[t] = -1; prev[t] = -1; best_chi2[t] = bb[t]; }
   for (int64_t a = 0; a < nt; a++)
@@ -1054,8 +1070,236 @@ int64_t orc_merge_sectors(const orc_input* in, const orc_params* P, const orc_xs
     ng++;
   }
   free(cnt); free(lst); free(fill); free(sec); free(exit_side); free(entry_side); free(row_in);
-  free(row_out); free(z_in); free(z_out); free(bb); free(ba); free(ib); free(ia); free(prev);
+  free(row_out); free(z_in); free(z_out); free(bb); free(ba); free(bb2); free(ba2); free(ib); free(ia); free(prev);
   return ng;
+}
+
+/* ------------------------------------------------------------ 9b. looper legs
+ * Follows the library's definition of joining the legs of a looping track
+ * within one sector (the paper, section "Hardware and data flow", names the
+ * full TPC tracking on the EPN GPUs; a track whose circle lies inside the TPC
+ * crosses a sector once per turn, on the same transverse path each time, and
+ * steps 5-8 find every crossing as a track of its own):
+ *   - a step-8 track can loop when the circle through its fitted point and
+ *     direction (at the reference x) with the curvature of |q/pT| + 3 sigma
+ *     (sigma from the fit's covariance scaled as below) lies within
+ *     loop_radius of the beam axis: |centre| + 1/|k| <= loop_radius, the
+ *     centre being (x - snp/k, y + cos(phi)/k) in the sector frame (k the
+ *     signed curvature); a short leg's q/pT is too uncertain for the fitted
+ *     circle alone to tell;
+ *   - tracks A < B of one sector are a candidate pair when both loop, neither
+ *     fit is flagged and their q/pT have the same sign (successive turns cross
+ *     the sector in the same direction, so their fits share orientation);
+ *   - each fit's covariance is scaled by max(1, chi2/ndf) of that fit (the
+ *     measurement errors the fit assumes understate the scatter of clusters
+ *     that overlap, which loopers' clusters often do);
+ *   - both states are carried to the larger of the two reference x (one of
+ *     them moves, with its covariance); there the turn count is m = the
+ *     integer nearest (ties away from zero) to (zeta_B - zeta_A) / S, with
+ *     S = tgl_A 2 pi / |k_A| the zeta advance of one turn; the pair is a
+ *     candidate only for 1 <= |m| <= max_turns and tgl_A, tgl_B of one sign
+ *     (so that along every link zeta advances in the direction of the one
+ *     sign of tgl that the legs of a chain share, and chains cannot close);
+ *   - A's state is advanced by m turns (zeta + m S; the rest of the state is
+ *     that of the same transverse point one turn on), d = s_B - that, and
+ *     chi2 = d^T (J C_A J^T + C_B)^-1 d with J the identity plus the zeta
+ *     row's m 2 pi / |k_A| (tgl) and -m S / (q/pT)_A (q/pT) entries; the pair
+ *     is accepted when chi2 <= chi2_cut;
+ *   - an accepted pair is directed from the leg of lower zeta along the fitted
+ *     motion to the other: A -> B when m > 0, B -> A when m < 0;
+ *   - every track's next leg is its outgoing accepted pair of least |m|, then
+ *     least chi2, then lowest index; its previous leg likewise over the
+ *     incoming pairs; A -> B links when B is A's next and A is B's previous.
+ * Chains of links are the turns of one looper in that sector. */
+typedef struct {
+  double chi2_cut;         /* 30 */
+  double loop_radius_cm;   /* 275: the 250 cm outer field cage + 10 % */
+  int32_t max_turns;       /* 4 */
+  int32_t pad;
+} orc_loop_params;
+
+/* State and covariance of a fit carried to x_out, the covariance scaled by
+ * max(1, chi2/ndf); returns 1 if the transport stops. */
+static int carry_fit(const orc_params* P, const orc_fit* f, double x_out, double* s, double* C) {
+  double F[25];
+  for (int i = 0; i < 5; i++) s[i] = f->par[i];
+  unpack_cov(f->cov, C);
+  const double q = f->ndf > 0 ? f->chi2 / (double)f->ndf : 1.0;
+  if (q > 1.0)
+    for (int i = 0; i < 25; i++) C[i] *= q;
+  if (x_out == f->x) return 0;
+  double out[5];
+  if (orc_transport(P, s, x_out - f->x, out, F)) return 1;
+  for (int i = 0; i < 5; i++) s[i] = out[i];
+  sandwich(F, C);
+  return 0;
+}
+
+/* Farthest distance from the beam axis of the circle through f's fitted
+ * point and direction with |q/pT| raised by 3 sigma; -1 if undefined. */
+static double loop_reach(const orc_params* P, const orc_fit* f) {
+  const double q = f->ndf > 0 && f->chi2 > (double)f->ndf ? f->chi2 / (double)f->ndf : 1.0;
+  const double sq = sqrt(f->cov[14] * q);
+  const double qpt = f->par[4] + (f->par[4] < 0.0 ? -3.0 : 3.0) * sq;
+  const double k = kfac(P) * qpt;
+  const double sn = f->par[2];
+  if (f->par[4] == 0.0 || k == 0.0 || !(fabs(sn) < 1.0)) return -1.0;
+  const double cs = sqrt(1.0 - sn * sn);
+  const double xc = f->x - sn / k, yc = f->par[0] + cs / k;
+  return sqrt(xc * xc + yc * yc) + 1.0 / fabs(k);
+}
+
+/* 1 if the track f can loop within radius r_out. */
+int orc_loops(const orc_params* P, const orc_fit* f, double r_out) {
+  const double r = loop_reach(P, f);
+  return r >= 0.0 && r <= r_out;
+}
+
+/* chi2 of B against A advanced by m turns (states and covariances at one x;
+ * turn the transverse arc of a turn, S the zeta advance of one). */
+static double turns_chi2(const double* sa, const double* CA_in, const double* sb, const double* CB, double turn,
+                         double S, int m) {
+  double J[25], CA[25], d[5];
+  for (int i = 0; i < 25; i++) { J[i] = 0.0; CA[i] = CA_in[i]; }
+  for (int i = 0; i < 5; i++) J[i * 5 + i] = 1.0;
+  J[1 * 5 + 3] = m * turn;
+  J[1 * 5 + 4] = -m * S / sa[4];
+  sandwich(J, CA);
+  for (int i = 0; i < 5; i++) d[i] = sb[i] - sa[i];
+  d[1] -= m * S;
+  for (int i = 0; i < 25; i++) CA[i] += CB[i];
+  return chi2_spd(CA, d);
+}
+
+/* Matching chi2 of legs A and B and their signed turn count *m (A's turns to
+ * reach B); -1 when the pair is not a candidate (transport stops, no advance
+ * per turn, tgl of opposite signs, or |m| outside 1..max_turns). */
+/* As orc_loop_pair, with the unrounded turn count r and the chi2 with the
+ * other integer nearest r (the turn count had r rounded the other way; -1 if
+ * that is 0 or out of range) for the borderline test. */
+double orc_loop_pair_r(const orc_params* P, const orc_loop_params* LP, const orc_fit* A, const orc_fit* B, int* m_out,
+                       double* r_out, double* alt_out) {
+  const double two_pi = 2.0 * 3.14159265358979323846;
+  const double xr = A->x > B->x ? A->x : B->x;
+  double sa[5], sb[5], CA[25], CB[25];
+  *m_out = 0;
+  if (carry_fit(P, A, xr, sa, CA) || carry_fit(P, B, xr, sb, CB)) return -1.0;
+  const double k = kfac(P) * sa[4];
+  if (k == 0.0) return -1.0;
+  const double turn = two_pi / fabs(k);
+  const double S = sa[3] * turn;
+  if (S == 0.0) return -1.0;
+  const double r = (sb[1] - sa[1]) / S;
+  if (r_out) *r_out = r;
+  if (alt_out) *alt_out = -1.0;
+  if (!(sa[3] * sb[3] > 0.0)) return -1.0;
+  if (!(fabs(r) < (double)LP->max_turns + 1.0)) return -1.0;
+  const int m = (int)(r < 0.0 ? -floor(-r + 0.5) : floor(r + 0.5));
+  if (alt_out) {
+    /* the other integer nearest r */
+    const int ma = (double)m > r ? m - 1 : m + 1;
+    if (ma != 0 && abs(ma) <= LP->max_turns) *alt_out = turns_chi2(sa, CA, sb, CB, turn, S, ma);
+  }
+  if (m == 0 || abs(m) > LP->max_turns) return -1.0;
+  *m_out = m;
+  return turns_chi2(sa, CA, sb, CB, turn, S, m);
+}
+
+double orc_loop_pair(const orc_params* P, const orc_loop_params* LP, const orc_fit* A, const orc_fit* B, int* m_out) {
+  return orc_loop_pair_r(P, LP, A, B, m_out, NULL, NULL);
+}
+
+/* Ordering key of a candidate (turns |m|, chi2, index): 1 if (m1, c1, i1)
+ * comes before (m2, c2, i2). */
+static int loop_before(int m1, double c1, int32_t i1, int m2, double c2, int32_t i2) {
+  if (m1 != m2) return m1 < m2;
+  if (c1 != c2) return c1 < c2;
+  return i1 < i2;
+}
+
+/* Looper-leg join of the step-8 tracks (fits[nt], cl2trk over n clusters):
+ * next[t] / prev[t] = the linked following / preceding leg or -1;
+ * next_chi2[t] = the chi2 of the link to next[t] or -1; borderline[t] = 1
+ * when a decision about t is within 1 % of flipping: t's looping reach within
+ * 1 % of loop_radius; a pair of t whose chi2 lies within 1 % of the cut; a
+ * pair of t whose (zeta_B - zeta_A) / S lies within 0.01 of a half-integer
+ * (the turn count's rounding, or the range bound max_turns + 1/2) while its
+ * chi2 with either neighbouring turn count is at most 1.01 cut; or t's two
+ * best candidates in one direction with equal |m| and chi2 within 1 % of each
+ * other.  Returns the number of links. */
+int64_t orc_join_loopers(const orc_input* in, const orc_params* P, const orc_loop_params* LP, const orc_cluster* cl,
+                         int64_t n, const int32_t* cl2trk, int64_t nt, const orc_fit* fits, int32_t* next,
+                         int32_t* prev, double* next_chi2, int8_t* borderline) {
+  (void)in;   /* the geometry plays no part: the fits carry the reference x */
+  int32_t* sec = (int32_t*)malloc(sizeof(int32_t) * (nt + 1));
+  int8_t* loops = (int8_t*)malloc((size_t)nt + 1);
+  for (int64_t t = 0; t < nt; t++) sec[t] = -1;
+  for (int64_t i = 0; i < n; i++) if (cl2trk[i] >= 0 && sec[cl2trk[i]] < 0) sec[cl2trk[i]] = cl[i].sector;
+  for (int64_t t = 0; t < nt; t++) borderline[t] = 0;
+  for (int64_t t = 0; t < nt; t++) {
+    loops[t] = 0;
+    if (sec[t] < 0 || fits[t].flags) continue;
+    const double reach = loop_reach(P, &fits[t]);
+    if (reach < 0.0) continue;
+    loops[t] = reach <= LP->loop_radius_cm;
+    if (fabs(reach - LP->loop_radius_cm) <= 0.01 * LP->loop_radius_cm) borderline[t] = 1;
+  }
+  /* per track and direction (0 next, 1 prev): best and runner-up (m, chi2, index) */
+  int* bm = (int*)malloc(sizeof(int) * 4 * (nt + 1));
+  double* bc = (double*)malloc(sizeof(double) * 4 * (nt + 1));
+  int32_t* bi = (int32_t*)malloc(sizeof(int32_t) * 4 * (nt + 1));
+  for (int64_t q = 0; q < 4 * nt; q++) { bm[q] = 0; bc[q] = -1.0; bi[q] = -1; }
+  for (int64_t a = 0; a < nt; a++) {
+    if (!loops[a]) continue;
+    for (int64_t b = a + 1; b < nt; b++) {
+      if (!loops[b] || sec[b] != sec[a] || (fits[a].par[4] > 0.0) != (fits[b].par[4] > 0.0)) continue;
+      int m;
+      double r = 0.0, alt = -1.0;
+      const double c2 = orc_loop_pair_r(P, LP, &fits[a], &fits[b], &m, &r, &alt);
+      const double fr = fabs(r) - floor(fabs(r));
+      if (fabs(fr - 0.5) <= 0.01 &&
+          ((c2 >= 0.0 && c2 <= 1.01 * LP->chi2_cut) || (alt >= 0.0 && alt <= 1.01 * LP->chi2_cut)))
+        borderline[a] = borderline[b] = 1;
+      if (c2 < 0.0) continue;
+      if (fabs(c2 - LP->chi2_cut) <= 0.01 * LP->chi2_cut) borderline[a] = borderline[b] = 1;
+      if (c2 > LP->chi2_cut) continue;
+      const int am = m < 0 ? -m : m;
+      const int64_t f = m > 0 ? a : b, g = m > 0 ? b : a;
+      /* f's outgoing (slot 0) gains g; g's incoming (slot 1) gains f */
+      const int64_t who[2] = {f, g};
+      const int32_t other[2] = {(int32_t)g, (int32_t)f};
+      for (int dir = 0; dir < 2; dir++) {
+        const int64_t q = 4 * who[dir] + 2 * dir;   /* q: best, q + 1: runner-up */
+        if (bi[q] < 0 || loop_before(am, c2, other[dir], bm[q], bc[q], bi[q])) {
+          bm[q + 1] = bm[q]; bc[q + 1] = bc[q]; bi[q + 1] = bi[q];
+          bm[q] = am; bc[q] = c2; bi[q] = other[dir];
+        } else if (bi[q + 1] < 0 || loop_before(am, c2, other[dir], bm[q + 1], bc[q + 1], bi[q + 1])) {
+          bm[q + 1] = am; bc[q + 1] = c2; bi[q + 1] = other[dir];
+        }
+      }
+    }
+  }
+  for (int64_t t = 0; t < nt; t++) {
+    next[t] = prev[t] = -1;
+    next_chi2[t] = -1.0;
+    for (int dir = 0; dir < 2; dir++) {
+      const int64_t q = 4 * t + 2 * dir;
+      if (bi[q + 1] >= 0 && bm[q + 1] == bm[q] && bc[q + 1] - bc[q] <= 0.01 * (bc[q] > 1.0 ? bc[q] : 1.0))
+        borderline[t] = 1;
+    }
+  }
+  int64_t links = 0;
+  for (int64_t f = 0; f < nt; f++) {
+    const int32_t g = bi[4 * f];
+    if (g >= 0 && bi[4 * (int64_t)g + 2] == f) {
+      next[f] = g;
+      prev[g] = (int32_t)f;
+      next_chi2[f] = bc[4 * f];
+      links++;
+    }
+  }
+  free(sec); free(loops); free(bm); free(bc); free(bi);
+  return links;
 }
 
 /* ------------------------------------------------------------ 10. track-model compression
@@ -1071,7 +1315,9 @@ int64_t orc_merge_sectors(const orc_input* in, const orc_params* P, const orc_xs
  *   - a cluster is coded if both |codes| <= 127, otherwise escaped (kept raw);
  *     clusters after a failed transport are escaped;
  *   - decoding: prediction + code * step; the coded position is within step/2.
- * Output per cluster: status 0 (not on a track), 1 (coded), 2 (escaped). */
+ * Output per cluster: status 0 (not on a track), 1 (coded), 2 (escaped);
+ * q_y, q_z (may be NULL; test output): the residuals in steps before rounding,
+ * NaN where no prediction was made. */
 typedef struct {
   double step_y;   /* 0.0125 cm (1/32 pad) */
   double step_z;   /* 0.015625 cm (1/32 time bin) */
@@ -1079,9 +1325,10 @@ typedef struct {
 
 int64_t orc_compress(const orc_input* in, const orc_params* P, const orc_cmp_params* CP, const orc_cluster* cl,
                      int64_t n, const int32_t* cl2trk, int64_t nt, const orc_fit* fits, int8_t* code_y,
-                     int8_t* code_z, uint8_t* status) {
+                     int8_t* code_z, uint8_t* status, double* q_y, double* q_z) {
   const double u = 7.8125e-4;
   for (int64_t i = 0; i < n; i++) { code_y[i] = 0; code_z[i] = 0; status[i] = 0; }
+  if (q_y) for (int64_t i = 0; i < n; i++) q_y[i] = q_z[i] = NAN;
   int64_t* cnt = (int64_t*)calloc((size_t)nt + 1, sizeof(int64_t));
   for (int64_t i = 0; i < n; i++) if (cl2trk[i] >= 0) cnt[cl2trk[i] + 1]++;
   for (int64_t t = 0; t < nt; t++) cnt[t + 1] += cnt[t];
@@ -1106,6 +1353,7 @@ int64_t orc_compress(const orc_input* in, const orc_params* P, const orc_cmp_par
       }
       if (!ok) { status[c] = 2; continue; }
       const double ry = ((double)Y * u - s[0]) / CP->step_y, rz = ((double)Z * u - s[1]) / CP->step_z;
+      if (q_y) { q_y[c] = ry; q_z[c] = rz; }
       const double cy = round(ry), cz = round(rz);
       if (fabs(cy) <= 127.0 && fabs(cz) <= 127.0) {
         code_y[c] = (int8_t)cy;

@@ -1,6 +1,7 @@
 // fit_common.cuh — the Kalman-filter pieces shared by the per-sector fit
-// (k_fit.cu) and the cross-sector refit (k_xsec.cu): exact helix transport with
-// its Jacobian, the U D U^T covariance factors and Bierman's scalar update.
+// (k_fit.cu), the cross-sector merge and refit (k_xsec.cu) and the looper-leg
+// join (k_loop.cu): exact helix transport with its Jacobian, the U D U^T
+// covariance factors, Bierman's scalar update and the matching chi2.
 #pragma once
 #include "tpc_internal.cuh"
 
@@ -195,6 +196,37 @@ __device__ __forceinline__ bool ud_pd_above(const UD<float>& M, const float* dmi
 #pragma unroll
   for (int i = 0; i < 5; i++) ok &= (int)(M.d[i] > dmin[i]) & (int)(M.d[i] < 1e30f);
   return ok != 0;
+}
+
+// chi2 = d^T M^-1 d for a symmetric positive definite 5x5 M (Cholesky); -1 if not PD.
+__device__ __forceinline__ float chi2_spd(float (&M)[5][5], const float* d) {
+  float L[5][5];
+#pragma unroll
+  for (int j = 0; j < 5; j++) {
+    float acc = M[j][j];
+#pragma unroll
+    for (int k = 0; k < j; k++) acc -= L[j][k] * L[j][k];
+    if (!(acc > 0.f)) return -1.f;
+    L[j][j] = sqrtf(acc);
+    const float inv = 1.f / L[j][j];
+#pragma unroll
+    for (int i = j + 1; i < 5; i++) {
+      float a = M[i][j];
+#pragma unroll
+      for (int k = 0; k < j; k++) a -= L[i][k] * L[j][k];
+      L[i][j] = a * inv;
+    }
+  }
+  float w[5], c2 = 0.f;
+#pragma unroll
+  for (int i = 0; i < 5; i++) {
+    float a = d[i];
+#pragma unroll
+    for (int k = 0; k < i; k++) a -= L[i][k] * w[k];
+    w[i] = a / L[i][i];
+    c2 += w[i] * w[i];
+  }
+  return c2;
 }
 
 }  // namespace tpc

@@ -112,37 +112,6 @@ __device__ __forceinline__ bool rotate_state(float kfac, float* s, float& x, flo
   return true;
 }
 
-// chi2 = d^T M^-1 d for a symmetric positive definite 5x5 M (Cholesky); -1 if not PD.
-__device__ __forceinline__ float chi2_spd(float (&M)[5][5], const float* d) {
-  float L[5][5];
-#pragma unroll
-  for (int j = 0; j < 5; j++) {
-    float acc = M[j][j];
-#pragma unroll
-    for (int k = 0; k < j; k++) acc -= L[j][k] * L[j][k];
-    if (!(acc > 0.f)) return -1.f;
-    L[j][j] = sqrtf(acc);
-    const float inv = 1.f / L[j][j];
-#pragma unroll
-    for (int i = j + 1; i < 5; i++) {
-      float a = M[i][j];
-#pragma unroll
-      for (int k = 0; k < j; k++) a -= L[i][k] * L[j][k];
-      L[i][j] = a * inv;
-    }
-  }
-  float w[5], c2 = 0.f;
-#pragma unroll
-  for (int i = 0; i < 5; i++) {
-    float a = d[i];
-#pragma unroll
-    for (int k = 0; k < i; k++) a -= L[i][k] * w[k];
-    w[i] = a / L[i][i];
-    c2 += w[i] * w[i];
-  }
-  return c2;
-}
-
 // Matching chi2 of A (inner piece: state sa, covariance CA at xa in frame
 // alpha_a) and B (outer piece); -1 if B cannot be carried to A's reference.
 // Early exit: for the symmetric positive definite M = C_A + J C_B J^T,

@@ -33,6 +33,7 @@ cudaError_t prepare_find2();
 cudaError_t launch_find2(const DevGeom&, const DevParams&, const DevWork&, unsigned int, int, const LaunchCfg&,
                          cudaStream_t, unsigned long long*, int*);
 cudaError_t launch_xsec(const DevGeom&, const DevParams&, const DevWork&, const XsWork&, int, cudaStream_t);
+cudaError_t launch_loopers(const DevGeom&, const DevParams&, const DevWork&, const LoopWork&, int, cudaStream_t);
 cudaError_t launch_compress(const DevParams&, const DevWork&, const CmpWork&, int, cudaStream_t);
 cudaError_t launch_calibrate(const DevParams&, const DevWork&, const CalWork&, int, cudaStream_t);
 }  // namespace tpc
@@ -72,7 +73,7 @@ struct Slot {
   // device buffers
   Buf pages, offsets, winstate, cl, clx, cly, clz, clt, rowstart, chrow, up, down, score, edge, jump, chlen, scanv,
       scanst, chainof, clchain, ch_i32, besta, bestb, trk_i32, trackcl, cl2trk, tracks, ctrl, scratch, wincnt, winsoff,
-      candab, candsc, lenhist, evinfo, xs, cmp, cal, dense, digits, dtab;
+      candab, candsc, lenhist, evinfo, xs, lp, cmp, cal, dense, digits, dtab;
   unsigned long long* h_ctrl = nullptr;   // pinned copy of [ctr | err]
   // batch tables, device (evinfo) and pinned host copy, same layout:
   // u64 base[kMaxBatch], u64 bytes[kMaxBatch], u32 cl_start[kMaxBatch + 1],
@@ -83,6 +84,10 @@ struct Slot {
   bool xs_done = false;
   uint64_t xs_n = 0, xs_links = 0;
   size_t xs_bytes = 0;
+  // looper-leg join results of the current ticket (tpc_join_loopers)
+  bool lp_done = false;
+  uint64_t lp_links = 0, lp_tracks = 0;
+  size_t lp_bytes = 0;
   // track-model compression of the current ticket (tpc_compress_clusters)
   bool cmp_done = false;
   size_t cmp_bytes = 0, cal_bytes = 0;
@@ -358,7 +363,7 @@ static void slot_free(tpc_context* ctx, Slot& s) {
   Buf* all[] = {&s.pages, &s.offsets, &s.winstate, &s.cl, &s.clx, &s.cly, &s.clz, &s.clt, &s.rowstart, &s.chrow, &s.up,
                 &s.down, &s.score, &s.edge, &s.jump, &s.chlen, &s.scanv, &s.scanst, &s.chainof, &s.clchain,
                 &s.ch_i32, &s.besta, &s.bestb, &s.trk_i32, &s.trackcl, &s.cl2trk, &s.tracks, &s.ctrl,
-                &s.scratch, &s.wincnt, &s.winsoff, &s.candab, &s.candsc, &s.lenhist, &s.evinfo, &s.xs, &s.cmp, &s.cal, &s.dense,
+                &s.scratch, &s.wincnt, &s.winsoff, &s.candab, &s.candsc, &s.lenhist, &s.evinfo, &s.xs, &s.lp, &s.cmp, &s.cal, &s.dense,
                 &s.digits, &s.dtab};
   for (Buf* b : all) free_buf(*b);
   for (auto& e : s.ev_stage) if (e) cudaEventDestroy(e);
@@ -634,6 +639,7 @@ static tpc_status start_timeframe(tpc_context* ctx, Slot* s, const tpc_timeframe
   const bool dev_in = tf->flags & TPC_TF_DEVICE_INPUT;
   s->n_events = 1;
   s->xs_done = false;
+  s->lp_done = false;
   s->cmp_done = false;
   const unsigned nfrag = (tf->n_time_bins + kFrag - 1) / kFrag;
   const uint64_t nwin = (uint64_t)ctx->geom.n_sectors * ctx->geom.n_rows * nfrag;
@@ -666,6 +672,7 @@ static tpc_status start_timeframe(tpc_context* ctx, Slot* s, const tpc_timeframe
 static tpc_status start_batch(tpc_context* ctx, Slot* s, const tpc_timeframe_desc* tfs, uint32_t n_events) {
   const uint32_t T = tfs[0].n_time_bins;
   s->xs_done = false;
+  s->lp_done = false;
   s->cmp_done = false;
   std::vector<uint64_t> base(n_events), bytes(n_events);
   uint64_t total = 0;
@@ -736,11 +743,11 @@ static void reclaim_idle(tpc_context* ctx, const Slot* keep) {
     Buf* big[] = {&c.pages, &c.offsets, &c.winstate, &c.cl, &c.clx, &c.cly, &c.clz, &c.clt, &c.up, &c.down,
                   &c.score, &c.edge, &c.jump, &c.chlen, &c.scanv, &c.scanst, &c.chainof, &c.clchain, &c.ch_i32,
                   &c.besta, &c.bestb, &c.trk_i32, &c.trackcl, &c.cl2trk, &c.tracks, &c.scratch, &c.wincnt,
-                  &c.winsoff, &c.candab, &c.candsc, &c.xs, &c.cmp, &c.cal, &c.dense, &c.digits, &c.dtab};
+                  &c.winsoff, &c.candab, &c.candsc, &c.xs, &c.lp, &c.cmp, &c.cal, &c.dense, &c.digits, &c.dtab};
     for (Buf* b : big) free_buf(*b);
-    ctx->used -= c.xs_bytes + c.cmp_bytes + c.cal_bytes;
-    c.xs_bytes = c.cmp_bytes = c.cal_bytes = 0;
-    c.xs_done = c.cmp_done = false;
+    ctx->used -= c.xs_bytes + c.lp_bytes + c.cmp_bytes + c.cal_bytes;
+    c.xs_bytes = c.lp_bytes = c.cmp_bytes = c.cal_bytes = 0;
+    c.xs_done = c.lp_done = c.cmp_done = false;
     c.cap_pages = c.cap_windows = c.cap_cl = c.cap_ch = c.cap_dig = 0;
   }
 }
@@ -1163,6 +1170,100 @@ extern "C" tpc_status tpc_get_merged_tracks(tpc_context* ctx, uint64_t ticket, t
   if (cluster_to_track && ncl)
     CUDA_TRY(cudaMemcpyAsync(cluster_to_track, base + o_map, ncl * 4, cudaMemcpyDeviceToHost, s->stream));
   if (link && ntr) CUDA_TRY(cudaMemcpyAsync(link, base + o_link, ntr * 4, cudaMemcpyDeviceToHost, s->stream));
+  CUDA_TRY(cudaStreamSynchronize(s->stream));
+  return TPC_OK;
+}
+
+// ------------------------------------------------------------------ step 9b
+extern "C" tpc_status tpc_join_loopers(tpc_context* ctx, uint64_t ticket, const tpc_loop_params* lp,
+                                       uint64_t* n_links) {
+  if (!ctx) return fail(TPC_E_INVAL, "tpc_join_loopers: null argument");
+  const double chi2_cut = lp ? lp->chi2_cut : 30.0, radius = lp ? lp->loop_radius_cm : 275.0;
+  const int max_turns = lp ? lp->max_turns : 4;
+  if (!(chi2_cut >= 0.0) || chi2_cut > 1e6 || !(radius > 0.0) || radius > 1e4 || max_turns < 1 || max_turns > 15)
+    return fail(TPC_E_INVAL, "tpc_join_loopers: bad parameters");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  Slot* s;
+  tpc_status st = done_slot(ctx, ticket, &s);
+  if (st) return st;
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  const uint64_t C = s->cap_ch;
+  if (C >= (1ull << 28)) return fail(TPC_E_INVAL, "tpc_join_loopers: more than 2^28 tracks");
+  const int n_vs = ctx->geom.n_sectors * (int)s->n_events;
+  const size_t btiles = scan_tiles((uint64_t)n_vs + 1);
+  auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  const size_t need = al(C) + al(((size_t)n_vs + 1) * 8) + al((size_t)n_vs * 4) + al(btiles * 8) + al(C * 4) +
+                      al(C * 96) + 2 * al(C * 8) + 2 * al(C * 4) + al(64);
+  if (need > s->lp.bytes) {
+    if (ctx->used - s->lp_bytes + need > ctx->budget) return fail(TPC_E_NOMEM, "tpc_join_loopers: over the memory budget");
+    CUDA_TRY(ensure(s->lp, need));
+    ctx->used = ctx->used - s->lp_bytes + need;
+    s->lp_bytes = need;
+  }
+  uint8_t* p = (uint8_t*)s->lp.p;
+  auto take = [&](size_t b) { uint8_t* q = p; p += al(b); return q; };
+  LoopWork L;
+  L.loops = take(C);
+  L.bin_off = (uint64_t*)take(((size_t)n_vs + 1) * 8);
+  L.bin_cur = (uint32_t*)take((size_t)n_vs * 4);
+  L.bin_state = (unsigned long long*)take(btiles * 8);
+  L.ent = (uint32_t*)take(C * 4);
+  L.ent_fit = (uint4*)take(C * 96);
+  L.next_key = (unsigned long long*)take(C * 8);
+  L.prev_key = (unsigned long long*)take(C * 8);
+  L.next = (int32_t*)take(C * 4);
+  L.prev = (int32_t*)take(C * 4);
+  L.ctl = (unsigned long long*)take(64);
+  L.chi2_cut = (float)chi2_cut;
+  L.loop_radius = (float)radius;
+  L.max_turns = max_turns;
+  L.n_vs = n_vs;
+  DevGeom G = ctx->G;
+  G.n_time_bins = (int)s->n_time_bins;
+  G.n_frag = (int)((s->n_time_bins + kFrag - 1) / kFrag);
+  G.n_events = (int)s->n_events;
+  G.n_sectors = n_vs;
+  CUDA_TRY(cudaMemsetAsync(L.bin_off, 0, ((size_t)n_vs + 1) * 8, s->stream));
+  CUDA_TRY(cudaMemsetAsync(L.bin_cur, 0, (size_t)n_vs * 4, s->stream));
+  CUDA_TRY(cudaMemsetAsync(L.bin_state, 0, btiles * 8, s->stream));
+  {
+    // ctl: [0] links, [1] n_vs + 1 (entries of the scan), [2] scan ticket, [3] looping tracks
+    unsigned long long c[8] = {0, (unsigned long long)n_vs + 1, 0, 0, 0, 0, 0, 0};
+    CUDA_TRY(cudaMemcpyAsync(L.ctl, c, sizeof c, cudaMemcpyHostToDevice, s->stream));
+    CUDA_TRY(cudaStreamSynchronize(s->stream));   // c lives on this stack frame
+  }
+  CUDA_TRY(launch_loopers(G, ctx->P, s->W, L, ctx->n_sm, s->stream));
+  unsigned long long ctl[4];
+  CUDA_TRY(cudaMemcpyAsync(ctl, L.ctl, 32, cudaMemcpyDeviceToHost, s->stream));
+  CUDA_TRY(cudaStreamSynchronize(s->stream));
+  s->lp_done = true;
+  s->lp_links = ctl[0];
+  s->lp_tracks = ctl[3];
+  if (n_links) *n_links = s->lp_links;
+  return TPC_OK;
+}
+
+extern "C" tpc_status tpc_get_looper_links(tpc_context* ctx, uint64_t ticket, int32_t* next, int32_t* prev,
+                                           uint64_t* n_tracks) {
+  if (!ctx) return fail(TPC_E_INVAL, "tpc_get_looper_links: null argument");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  Slot* s;
+  tpc_status st = done_slot(ctx, ticket, &s);
+  if (st) return st;
+  if (!s->lp_done) return fail(TPC_E_NOTREADY, "tpc_join_loopers has not run on this ticket");
+  const uint64_t ntr = n_trk_of(*s);
+  if (n_tracks) *n_tracks = ntr;
+  if ((!next && !prev) || !ntr) return TPC_OK;
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  const uint64_t C = s->cap_ch;
+  const int n_vs = ctx->geom.n_sectors * (int)s->n_events;
+  auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  const size_t o_next = al(C) + al(((size_t)n_vs + 1) * 8) + al((size_t)n_vs * 4) +
+                        al(scan_tiles((uint64_t)n_vs + 1) * 8) + al(C * 4) + al(C * 96) + 2 * al(C * 8);
+  const size_t o_prev = o_next + al(C * 4);
+  const uint8_t* base = (const uint8_t*)s->lp.p;
+  if (next) CUDA_TRY(cudaMemcpyAsync(next, base + o_next, ntr * 4, cudaMemcpyDeviceToHost, s->stream));
+  if (prev) CUDA_TRY(cudaMemcpyAsync(prev, base + o_prev, ntr * 4, cudaMemcpyDeviceToHost, s->stream));
   CUDA_TRY(cudaStreamSynchronize(s->stream));
   return TPC_OK;
 }

@@ -267,6 +267,25 @@ __device__ __forceinline__ unsigned long long lookback_wait(unsigned long long* 
   return excl;
 }
 
+// Work space of the optional looper-leg join (step 9b), in one slot buffer.
+struct LoopWork {
+  uint8_t* loops;                // [cap_ch] 1: the track can loop (candidate leg)
+  uint64_t* bin_off;             // [n_vs + 1] looping tracks per virtual sector -> offsets
+  uint32_t* bin_cur;             // [n_vs] fill cursors
+  unsigned long long* bin_state; // scan state of bin_off
+  uint32_t* ent;                 // [cap_ch] looping tracks grouped by virtual sector
+  uint4* ent_fit;                // [cap_ch][6] their records' first 96 bytes, in the same order
+  unsigned long long* next_key;  // [cap_ch] best outgoing pair: |m| << 60 | chi2 bits << 28 | index
+  unsigned long long* prev_key;  // [cap_ch] best incoming pair, same packing
+  int32_t* next;                 // [cap_ch] linked following leg or -1
+  int32_t* prev;                 // [cap_ch] linked preceding leg or -1
+  unsigned long long* ctl;       // [0] links, [1] n_vs + 1, [2] (u32) bin scan ticket, [3] looping tracks
+  float chi2_cut;
+  float loop_radius;             // cm
+  int max_turns;
+  int n_vs;                      // virtual sectors (sectors x events)
+};
+
 // Work space of the optional cross-sector merge (step 9), in one slot buffer.
 struct XsWork {
   uint8_t* side;                 // [cap_ch] exit side (bits 0-1: 1 = +y, 2 = -y), entry side (bits 2-3)

@@ -77,6 +77,11 @@ class tpc_xs_params(ctypes.Structure):
     _fields_ = [("chi2_cut", ctypes.c_double), ("edge_cm", ctypes.c_double), ("dz_cm", ctypes.c_double)]
 
 
+class tpc_loop_params(ctypes.Structure):
+    _fields_ = [("chi2_cut", ctypes.c_double), ("loop_radius_cm", ctypes.c_double),
+                ("max_turns", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
 class tpc_cmp_params(ctypes.Structure):
     _fields_ = [("step_y_cm", ctypes.c_double), ("step_z_cm", ctypes.c_double)]
 
@@ -92,7 +97,7 @@ EXPORTS = ("tpc_params_default", "tpc_create_geometry", "tpc_destroy_geometry", 
            "tpc_get_counters", "tpc_release", "tpc_last_error", "tpc_find_clusters_noalloc",
            "tpc_submit_batch", "tpc_get_batch_info", "tpc_get_event_clusters", "tpc_get_event_tracks",
            "tpc_get_tuning", "tpc_set_tuning", "tpc_autotune", "tpc_merge_sectors", "tpc_get_merged_tracks",
-           "tpc_compress_clusters", "tpc_get_compressed", "tpc_calibrate_drift", "tpc_measure_fma_peak")
+           "tpc_join_loopers", "tpc_get_looper_links", "tpc_compress_clusters", "tpc_get_compressed", "tpc_calibrate_drift", "tpc_measure_fma_peak")
 
 _lib = None
 
@@ -141,6 +146,8 @@ def load(build_if_missing: bool = True):
     L.tpc_autotune.argtypes = [_P, ctypes.POINTER(tpc_timeframe_desc), ctypes.c_int, ctypes.POINTER(tpc_tuning)]
     L.tpc_merge_sectors.argtypes = [_P, _u64, ctypes.POINTER(tpc_xs_params), ctypes.POINTER(_u64)]
     L.tpc_get_merged_tracks.argtypes = [_P, _u64, _P, _u64, ctypes.POINTER(_u64), _P, _P]
+    L.tpc_join_loopers.argtypes = [_P, _u64, ctypes.POINTER(tpc_loop_params), ctypes.POINTER(_u64)]
+    L.tpc_get_looper_links.argtypes = [_P, _u64, _P, _P, ctypes.POINTER(_u64)]
     L.tpc_compress_clusters.argtypes = [_P, _u64, ctypes.POINTER(tpc_cmp_params), ctypes.POINTER(_u64),
                                         ctypes.POINTER(_u64)]
     L.tpc_get_compressed.argtypes = [_P, _u64, _P, _P, _P]
@@ -322,6 +329,27 @@ def tpc_get_merged_tracks(ctx, ticket: int, n_clusters: int, n_tracks: int):
     _check(L.tpc_get_merged_tracks(ctx, ticket, out.ctypes.data if n.value else None, n.value, ctypes.byref(n),
                                    m.ctypes.data if n_clusters else None, link.ctypes.data if n_tracks else None))
     return out, m, link
+
+
+def tpc_join_loopers(ctx, ticket: int, chi2_cut: float = 30.0, loop_radius_cm: float = 275.0,
+                     max_turns: int = 4) -> int:
+    """Looper-leg join (step 9b) of a finished ticket; returns the number of links."""
+    n = _u64()
+    lp = tpc_loop_params(float(chi2_cut), float(loop_radius_cm), int(max_turns), 0)
+    _check(load().tpc_join_loopers(ctx, ticket, ctypes.byref(lp), ctypes.byref(n)))
+    return int(n.value)
+
+
+def tpc_get_looper_links(ctx, ticket: int):
+    """Returns (next, prev): per step-8 track the linked following / preceding leg or -1."""
+    L = load()
+    n = _u64()
+    _check(L.tpc_get_looper_links(ctx, ticket, None, None, ctypes.byref(n)))
+    nxt = np.zeros(n.value, np.int32)
+    prv = np.zeros(n.value, np.int32)
+    if n.value:
+        _check(L.tpc_get_looper_links(ctx, ticket, nxt.ctypes.data, prv.ctypes.data, ctypes.byref(n)))
+    return nxt, prv
 
 
 def tpc_compress_clusters(ctx, ticket: int, step_y_cm: float = 0.4 / 32, step_z_cm: float = 0.5 / 32):

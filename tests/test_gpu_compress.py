@@ -1,13 +1,19 @@
 """Parity of the track-model compression (step 10) with the oracle.  The codes
-are rounded float residuals to the FP32 (GPU) or FP64 (oracle) track model, so
-a residual within the fit difference of a rounding boundary can round either
-way: statuses and codes must agree for all but a small fraction of clusters,
-and never differ by more than one step."""
+are rounded float residuals to the FP32 (GPU) or FP64 (oracle) track model: a
+code may differ only where the oracle's residual, in steps, lies within
+DELTA = 0.05 step of a rounding boundary (a half-integer), and then by one
+step; a status (coded or escaped) only where it lies within DELTA of the
++-127.5 escape bound.  The FP32 and FP64 predictions differ by ~1e-3 step
+(the observed difference rates, 2e-4 of the y codes and 2e-3 of the zeta codes,
+are those of a band of that width), so DELTA is a fifty-fold margin that
+still fails any code computed from a wrong prediction."""
 import numpy as np
 import pytest
 
 import oracle
 import tpcgen
+
+DELTA = 0.05
 
 pytestmark = pytest.mark.gpu
 
@@ -25,7 +31,7 @@ def lib():
 def test_full_tpc_compression_parity(lib):
     tf = tpcgen.generate(tpcgen.full_tpc(1))
     orc = oracle.reconstruct(tf)
-    ocy, ocz, ost = oracle.compress(tf, orc)
+    ocy, ocz, ost, qy, qz = oracle.compress(tf, orc, quotients=True)
     with lib.Reconstructor.for_timeframe(tf) as R:
         t = R.submit(tf.pages, tf.page_offsets, tf.n_time_bins)
         R.wait(t)
@@ -36,16 +42,27 @@ def test_full_tpc_compression_parity(lib):
     assert cl.tobytes() == orc.clusters.tobytes()
     assert n_coded == int((st == 1).sum()) and n_esc == int((st == 2).sum())
     assert np.array_equal(st == 0, ost == 0)            # on a track or not: integer, exact
-    on = ost > 0
-    same_status = (st == ost)[on].mean()
+
+    def to_boundary(q):
+        """Distance (in steps) of the unrounded residual from the nearest half-integer."""
+        return np.abs(np.abs(q - np.floor(q)) - 0.5)
+
+    # statuses: a difference needs a residual within DELTA of the escape bound
+    sd = np.nonzero(st != ost)[0]
+    near_escape = (np.abs(np.abs(qy[sd]) - 127.5) <= DELTA) | (np.abs(np.abs(qz[sd]) - 127.5) <= DELTA)
+    assert np.all(near_escape), sd[~near_escape][:10]
     both = (st == 1) & (ost == 1)
-    dy = np.abs(cy[both].astype(int) - ocy[both])
-    dz = np.abs(cz[both].astype(int) - ocz[both])
-    print(f"clusters on tracks {on.sum()}, coded {n_coded}, escaped {n_esc}; status agree {same_status:.6f}; "
-          f"codes differ y {np.mean(dy > 0):.2e} z {np.mean(dz > 0):.2e}")
-    assert same_status >= 0.999
-    assert dy.max() <= 1 and dz.max() <= 1
-    assert np.mean(dy > 0) <= 0.01 and np.mean(dz > 0) <= 0.01
+    dy = cy[both].astype(int) - ocy[both]
+    dz = cz[both].astype(int) - ocz[both]
+    assert np.abs(dy).max(initial=0) <= 1 and np.abs(dz).max(initial=0) <= 1
+    by, bz = to_boundary(qy[both]), to_boundary(qz[both])
+    worst_y = float(by[dy != 0].max(initial=0.0))
+    worst_z = float(bz[dz != 0].max(initial=0.0))
+    print(f"clusters on tracks {int((ost > 0).sum())}, coded {n_coded}, escaped {n_esc}; statuses differ {len(sd)}; "
+          f"codes differ y {np.mean(dy != 0):.2e} z {np.mean(dz != 0):.2e}; farthest differing code from its "
+          f"boundary y {worst_y:.2e} z {worst_z:.2e} step; within DELTA of a boundary y {np.mean(by <= DELTA):.2e} "
+          f"z {np.mean(bz <= DELTA):.2e}")
+    assert worst_y <= DELTA and worst_z <= DELTA
 
 
 def test_degenerate_inputs_steps_10_11(lib):
