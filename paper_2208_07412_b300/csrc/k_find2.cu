@@ -249,13 +249,41 @@ __device__ __forceinline__ void unit_desc(const DevGeom& G, const DevWork& W, un
   D.c = c;
 }
 
+// Unit descriptors, precomputed by k_unit_descs: three 16-byte words per
+// unit, (seg_start[0], seg_start[1]), (seg_start[2], seg_n[0], seg_n[1]),
+// (seg_n[2], frs, c, 0).
+__global__ void k_unit_descs(DevGeom G, DevWork W, unsigned int n_units) {
+  for (unsigned int u = blockIdx.x * blockDim.x + threadIdx.x; u < n_units; u += gridDim.x * blockDim.x) {
+    UnitDesc D;
+    unit_desc(G, W, u, D);
+    uint4* q = W.udesc + 3ull * u;
+    q[0] = make_uint4((uint32_t)D.seg_start[0], (uint32_t)(D.seg_start[0] >> 32), (uint32_t)D.seg_start[1],
+                      (uint32_t)(D.seg_start[1] >> 32));
+    q[1] = make_uint4((uint32_t)D.seg_start[2], (uint32_t)(D.seg_start[2] >> 32), (uint32_t)D.seg_n[0],
+                      (uint32_t)D.seg_n[1]);
+    q[2] = make_uint4((uint32_t)D.seg_n[2], (uint32_t)D.frs, (uint32_t)D.c, 0u);
+  }
+}
+
+// Digits a thread keeps in registers between the plane build and step 2:
+// units with at most kReg * kThreads digits take the register path.
+constexpr int kReg = 8;
+
 template <int kThreads>
 struct UnitSmem {
-  UnitDesc d;                        // the current unit
+  uint4 dq[3][3];                    // descriptor ring: units u, u + G, u + 2G (G = gridDim.x)
   unsigned long long sbase;          // the unit's span of the scratch buffer
-  uint32_t scan[16];
+  uint32_t total;                    // the unit's own peaks
   uint32_t wtot[2][kThreads / 32];   // per-round warp counts of own peaks (double-buffered)
+  uint32_t wcnt[kReg * (kThreads / 32)];   // register path: own peaks per (round, warp), then their prefix
 };
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
 // Step 2 on the plane (bit 15 of a word marks a step-2 peak, bit 14 a peak
 // dropped by step 2b; charges are the low 10 bits): neighbours with a lower
@@ -304,17 +332,24 @@ __device__ __forceinline__ int seg_row_offset(int k, int c) {
   return k == 0 ? kHalo - kFrag : (k == 1 ? kHalo - kChunkT * c : kHalo + kFrag - kChunkT * (kUnitsPerWin - 1));
 }
 
-// Units are taken round-robin (unit blockIdx.x + k gridDim.x); thread 0 reads
-// the next unit's descriptor while the current one is processed.  Per unit:
-// the plane is built from the digits (strided over the threads), step 2 runs
-// strided too, and each round of kThreads digits ranks its own peaks by warp
-// ballots and a prefix over the warps, appending their plane indices to a list
-// in canonical order; the clusters are then built strided over that list.
+// Units are taken round-robin (unit blockIdx.x + k gridDim.x).  Their
+// descriptors come from k_unit_descs two units ahead: lanes 0-2 of warp 0
+// copy unit u + 2G's into a ring slot (cp.async) while unit u runs, and thread
+// 0 prefetches unit u + G's digits into L2.  Per unit: the plane is built
+// from the digits (strided over the threads), step 2 runs strided too, the own
+// peaks are ranked in canonical order (digit order) by warp ballots and a
+// prefix over (round, warp), and their plane indices listed; the clusters are
+// then built strided over that list.  Units of at most kReg * kThreads digits
+// (the register path) keep each thread's digits as (plane index, row) words
+// in registers between the plane build and step 2, and rank all rounds with
+// one prefix; larger units re-read their digits and rank round by round.
 template <int kThreads, bool kNs>
-__global__ void __launch_bounds__(kThreads) k_find_units(DevGeom G, DevParams P, DevWork W, unsigned int n_units) {
+__global__ void __launch_bounds__(kThreads, 1024 / kThreads)
+    k_find_units(DevGeom G, DevParams P, DevWork W, unsigned int n_units) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ UnitSmem<kThreads> U;
   constexpr int kWarps = kThreads / 32;
+  const unsigned FULL = 0xffffffffu;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int ps = G.npmax + 2 * kPad;                 // plane row stride in pads
   uint16_t* plane = reinterpret_cast<uint16_t*>(smem_raw);
@@ -325,23 +360,43 @@ __global__ void __launch_bounds__(kThreads) k_find_units(DevGeom G, DevParams P,
   for (int i = tid; i < plane_words16; i += kThreads) plane16[i] = make_uint4(0u, 0u, 0u, 0u);
   if (blockIdx.x == 0 && tid == 0) W.ctr[CTR_NWIN] = n_units;
   const int T = G.n_time_bins;
-  UnitDesc nxt;                                       // thread 0: the next unit's descriptor
-  unsigned int u = blockIdx.x;
-  if (tid == 0 && u < n_units) unit_desc(G, W, u, nxt);
-  for (; u < n_units; u += gridDim.x) {
-    if (tid == 0) {
-      U.d = nxt;
-      if (u + gridDim.x < n_units) {
-        unit_desc(G, W, u + gridDim.x, nxt);          // consumed next iteration
+  const unsigned int Gs = gridDim.x;
+  // the descriptor ring: units blockIdx.x and blockIdx.x + G in flight
+  if (wid == 0) {
 #pragma unroll
-        for (int k = 0; k < 3; k++)                   // its digits into L2 meanwhile
-          if (nxt.seg_n[k] > 0) prefetch_l2_span(W.digits + nxt.seg_start[k], nxt.seg_n[k]);
-      }
+    for (int k = 0; k < 2; k++) {
+      const unsigned int uk = blockIdx.x + k * Gs;
+      if (lane < 3 && uk < n_units) cp_async16(&U.dq[k][lane], W.udesc + 3ull * uk + lane);
+      cp_async_commit();
+    }
+  }
+  int slot = 0;
+  for (unsigned int u = blockIdx.x; u < n_units; u += Gs) {
+    if (wid == 0) {
+      const unsigned int u2 = u + 2 * Gs;
+      const int s2 = slot == 0 ? 2 : slot - 1;        // (slot + 2) % 3
+      if (lane < 3 && u2 < n_units) cp_async16(&U.dq[s2][lane], W.udesc + 3ull * u2 + lane);
+      cp_async_commit();
+      cp_async_wait1();                                // units u and u + G have landed
     }
     __syncthreads();
-    const int n0 = U.d.seg_n[0], n01 = n0 + U.d.seg_n[1], n_all = n01 + U.d.seg_n[2];
-    const int c = U.d.c;
-    const unsigned long long st0 = U.d.seg_start[0], st1 = U.d.seg_start[1] - n0, st2 = U.d.seg_start[2] - n01;
+    const uint4 q0 = U.dq[slot][0], q1 = U.dq[slot][1], q2 = U.dq[slot][2];
+    if (tid == 0 && u + Gs < n_units) {                // unit u + G's digits into L2 meanwhile
+      const int s1 = slot == 2 ? 0 : slot + 1;
+      const uint4 p0 = U.dq[s1][0], p1 = U.dq[s1][1], p2 = U.dq[s1][2];
+      const unsigned long long a0 = p0.x | ((unsigned long long)p0.y << 32);
+      const unsigned long long a1 = p0.z | ((unsigned long long)p0.w << 32);
+      const unsigned long long a2 = p1.x | ((unsigned long long)p1.y << 32);
+      if ((int)p1.z > 0) prefetch_l2_span(W.digits + a0, (int)p1.z);
+      if ((int)p1.w > 0) prefetch_l2_span(W.digits + a1, (int)p1.w);
+      if ((int)p2.x > 0) prefetch_l2_span(W.digits + a2, (int)p2.x);
+    }
+    slot = slot == 2 ? 0 : slot + 1;
+    const int n0 = (int)q1.z, n01 = n0 + (int)q1.w, n_all = n01 + (int)q2.x;
+    const int frs = (int)q2.y, c = (int)q2.z;
+    const unsigned long long st0 = q0.x | ((unsigned long long)q0.y << 32);
+    const unsigned long long st1 = (q0.z | ((unsigned long long)q0.w << 32)) - n0;
+    const unsigned long long st2 = (q1.x | ((unsigned long long)q1.y << 32)) - n01;
     const int of0 = seg_row_offset(0, c), of1 = seg_row_offset(1, c), of2 = seg_row_offset(2, c);
     // digit i of the unit -> (its word, its plane row offset)
     auto digit = [&](int i, int& off) -> uint32_t {
@@ -349,51 +404,97 @@ __global__ void __launch_bounds__(kThreads) k_find_units(DevGeom G, DevParams P,
       off = i < n0 ? of0 : (i < n01 ? of1 : of2);
       return __ldg(W.digits + g);
     };
-    // ---- build the plane
-    for (int i = tid; i < n_all; i += kThreads) {
-      int off;
-      const uint32_t d = digit(i, off);
-      const int row = (int)((d >> 8) & 255u) + off;
-      if (row >= 0 && row < kURows) plane[row * ps + kPad + (int)(d & 255u)] = (uint16_t)(d >> 16);
-    }
-    __syncthreads();
-    // ---- step 2 (rows 1..68), peaks marked; without step 2b the own ones are ranked at once
-    uint32_t running = 0;                               // own peaks listed so far (block-uniform)
-    int parity = 0;
-    for (int base = 0; base < n_all; base += kThreads) {
-      const int i = base + tid;
-      bool own = false;
-      int L = 0;
-      if (i < n_all) {
-        int off;
-        const uint32_t d = digit(i, off);
-        const int row = (int)((d >> 8) & 255u) + off;
-        if (row >= 1 && row <= kURows - 2) {
-          L = row * ps + kPad + (int)(d & 255u);
-          const int q = plane[L];
-          if (q >= P.q_peak_min && peak_test(plane, L, ps, q, P.q_peak_min)) {
-            plane[L] = (uint16_t)(q | kPeakBit);       // only this thread writes this pixel
-            own = !kNs && row >= kHalo && row < kHalo + kChunkT;
+    uint32_t total;
+    if (n_all <= kReg * kThreads) {
+      // ---- register path: build the plane, keeping (L | row << 16) per digit
+      uint32_t pk[kReg];
+#pragma unroll
+      for (int k = 0; k < kReg; k++) {
+        pk[k] = FULL;
+        const int i = tid + k * kThreads;
+        if (i < n_all) {
+          int off;
+          const uint32_t d = digit(i, off);
+          const int row = (int)((d >> 8) & 255u) + off;
+          if (row >= 0 && row < kURows) {
+            const int L = row * ps + kPad + (int)(d & 255u);
+            plane[L] = (uint16_t)(d >> 16);
+            pk[k] = (uint32_t)L | ((uint32_t)row << 16);
           }
         }
       }
-      if (!kNs) {
-        const unsigned m = __ballot_sync(0xffffffffu, own);
-        if (lane == 0) U.wtot[parity][wid] = (uint32_t)__popc(m);
-        __syncthreads();
-        uint32_t before = running;
+      __syncthreads();
+      // ---- step 2 (rows 1..68): peaks marked, own ones flagged per round
+      uint32_t own = 0;
 #pragma unroll
-        for (int k = 0; k < kWarps; k++) {
-          const uint32_t v = U.wtot[parity][k];
-          before += k < wid ? v : 0u;
-          running += v;
+      for (int k = 0; k < kReg; k++) {
+        if (pk[k] == FULL) continue;
+        const int L = (int)(pk[k] & 0xffffu), row = (int)(pk[k] >> 16);
+        if (row >= 1 && row <= kURows - 2) {
+          const int q = plane[L];
+          if (q >= P.q_peak_min && peak_test(plane, L, ps, q, P.q_peak_min)) {
+            plane[L] = (uint16_t)(q | kPeakBit);       // only this thread writes this pixel
+            if (row >= kHalo && row < kHalo + kChunkT) own |= 1u << k;
+          }
         }
-        if (own) plist[before + (uint32_t)__popc(m & ((1u << lane) - 1u))] = (uint16_t)L;
-        parity ^= 1;
       }
-    }
-    if (kNs) {
-      __syncthreads();   // every step-2 peak marked: step 2b reads the ring
+      if (kNs) {
+        __syncthreads();   // every step-2 peak marked: step 2b reads the ring
+#pragma unroll
+        for (int k = 0; k < kReg; k++) {
+          if (!((own >> k) & 1u)) continue;
+          const int L = (int)(pk[k] & 0xffffu);
+          if (ns_drop_plane(plane, L, ps, P.ns_min_dip)) {
+            plane[L] = (uint16_t)(plane[L] | kDropBit);
+            own &= ~(1u << k);
+          }
+        }
+      }
+      // ---- rank: own peaks per (round, warp), one prefix over them in order
+#pragma unroll
+      for (int k = 0; k < kReg; k++) {
+        const unsigned m = __ballot_sync(FULL, (own >> k) & 1u);
+        if (lane == 0) U.wcnt[k * kWarps + wid] = (uint32_t)__popc(m);
+      }
+      __syncthreads();
+      if (wid == 0) {
+        uint32_t carry = 0;
+#pragma unroll
+        for (int j0 = 0; j0 < kReg * kWarps; j0 += 32) {
+          const uint32_t v = U.wcnt[j0 + lane];
+          const uint32_t inc = (uint32_t)warp_incl_scan32((int)v);
+          U.wcnt[j0 + lane] = carry + inc - v;
+          carry += __shfl_sync(FULL, inc, 31);
+        }
+        if (lane == 0) {
+          const unsigned long long sb = carry ? atomicAdd(&W.ctr[CTR_SCURSOR], (unsigned long long)carry) : 0ull;
+          if (sb + carry > W.cap_cl) atomicOr(W.err, kErrOverflowCl);
+          U.sbase = sb;
+          U.total = carry;
+          W.win_cnt[u] = carry;
+          W.win_soff[u] = (uint32_t)min(sb, (unsigned long long)0xffffffffu);
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < kReg; k++) {
+        const unsigned m = __ballot_sync(FULL, (own >> k) & 1u);
+        if ((own >> k) & 1u)
+          plist[U.wcnt[k * kWarps + wid] + (uint32_t)__popc(m & ((1u << lane) - 1u))] = (uint16_t)(pk[k] & 0xffffu);
+      }
+      total = U.total;
+    } else {
+      // ---- build the plane
+      for (int i = tid; i < n_all; i += kThreads) {
+        int off;
+        const uint32_t d = digit(i, off);
+        const int row = (int)((d >> 8) & 255u) + off;
+        if (row >= 0 && row < kURows) plane[row * ps + kPad + (int)(d & 255u)] = (uint16_t)(d >> 16);
+      }
+      __syncthreads();
+      // ---- step 2 (rows 1..68), peaks marked; without step 2b the own ones are ranked at once
+      uint32_t running = 0;                             // own peaks listed so far (block-uniform)
+      int parity = 0;
       for (int base = 0; base < n_all; base += kThreads) {
         const int i = base + tid;
         bool own = false;
@@ -402,42 +503,76 @@ __global__ void __launch_bounds__(kThreads) k_find_units(DevGeom G, DevParams P,
           int off;
           const uint32_t d = digit(i, off);
           const int row = (int)((d >> 8) & 255u) + off;
-          if (row >= kHalo && row < kHalo + kChunkT) {
+          if (row >= 1 && row <= kURows - 2) {
             L = row * ps + kPad + (int)(d & 255u);
-            const uint16_t v = plane[L];
-            if (v & kPeakBit) {
-              if (ns_drop_plane(plane, L, ps, P.ns_min_dip)) plane[L] = (uint16_t)(v | kDropBit);
-              else own = true;
+            const int q = plane[L];
+            if (q >= P.q_peak_min && peak_test(plane, L, ps, q, P.q_peak_min)) {
+              plane[L] = (uint16_t)(q | kPeakBit);     // only this thread writes this pixel
+              own = !kNs && row >= kHalo && row < kHalo + kChunkT;
             }
           }
         }
-        const unsigned m = __ballot_sync(0xffffffffu, own);
-        if (lane == 0) U.wtot[parity][wid] = (uint32_t)__popc(m);
-        __syncthreads();
-        uint32_t before = running;
+        if (!kNs) {
+          const unsigned m = __ballot_sync(FULL, own);
+          if (lane == 0) U.wtot[parity][wid] = (uint32_t)__popc(m);
+          __syncthreads();
+          uint32_t before = running;
 #pragma unroll
-        for (int k = 0; k < kWarps; k++) {
-          const uint32_t v = U.wtot[parity][k];
-          before += k < wid ? v : 0u;
-          running += v;
+          for (int k = 0; k < kWarps; k++) {
+            const uint32_t v = U.wtot[parity][k];
+            before += k < wid ? v : 0u;
+            running += v;
+          }
+          if (own) plist[before + (uint32_t)__popc(m & ((1u << lane) - 1u))] = (uint16_t)L;
+          parity ^= 1;
         }
-        if (own) plist[before + (uint32_t)__popc(m & ((1u << lane) - 1u))] = (uint16_t)L;
-        parity ^= 1;
       }
-    }
-    const uint32_t total = running;
-    if (tid == 0) {
-      const unsigned long long sb = total ? atomicAdd(&W.ctr[CTR_SCURSOR], (unsigned long long)total) : 0ull;
-      if (sb + total > W.cap_cl) atomicOr(W.err, kErrOverflowCl);
-      U.sbase = sb;
-      W.win_cnt[u] = total;
-      W.win_soff[u] = (uint32_t)min(sb, (unsigned long long)0xffffffffu);
+      if (kNs) {
+        __syncthreads();   // every step-2 peak marked: step 2b reads the ring
+        for (int base = 0; base < n_all; base += kThreads) {
+          const int i = base + tid;
+          bool own = false;
+          int L = 0;
+          if (i < n_all) {
+            int off;
+            const uint32_t d = digit(i, off);
+            const int row = (int)((d >> 8) & 255u) + off;
+            if (row >= kHalo && row < kHalo + kChunkT) {
+              L = row * ps + kPad + (int)(d & 255u);
+              const uint16_t v = plane[L];
+              if (v & kPeakBit) {
+                if (ns_drop_plane(plane, L, ps, P.ns_min_dip)) plane[L] = (uint16_t)(v | kDropBit);
+                else own = true;
+              }
+            }
+          }
+          const unsigned m = __ballot_sync(FULL, own);
+          if (lane == 0) U.wtot[parity][wid] = (uint32_t)__popc(m);
+          __syncthreads();
+          uint32_t before = running;
+#pragma unroll
+          for (int k = 0; k < kWarps; k++) {
+            const uint32_t v = U.wtot[parity][k];
+            before += k < wid ? v : 0u;
+            running += v;
+          }
+          if (own) plist[before + (uint32_t)__popc(m & ((1u << lane) - 1u))] = (uint16_t)L;
+          parity ^= 1;
+        }
+      }
+      total = running;
+      if (tid == 0) {
+        const unsigned long long sb = total ? atomicAdd(&W.ctr[CTR_SCURSOR], (unsigned long long)total) : 0ull;
+        if (sb + total > W.cap_cl) atomicOr(W.err, kErrOverflowCl);
+        U.sbase = sb;
+        W.win_cnt[u] = total;
+        W.win_soff[u] = (uint32_t)min(sb, (unsigned long long)0xffffffffu);
+      }
     }
     __syncthreads();   // list complete, every peak marked, span reserved
     // ---- clusters of the own peaks, strided over the list (canonical order)
     if (total) {
       const unsigned long long sb = U.sbase;
-      const int frs = U.d.frs;
       const int f = frs & 0xffff, r = (frs >> 16) & 0xff, s = (frs >> 24) & 0xff;
       const int np = G.npads[r], xrow = G.xrow[r];
       const int t0 = kChunkT * c - kHalo;          // time bin (within the window) of plane row 0
@@ -464,6 +599,7 @@ __global__ void __launch_bounds__(kThreads) k_find_units(DevGeom G, DevParams P,
     __syncthreads();
     for (int i = tid; i < plane_words16; i += kThreads) plane16[i] = make_uint4(0u, 0u, 0u, 0u);
   }
+  if (wid == 0) asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
 // Dynamic shared memory of k_find_units: the plane, then the list of a unit's
@@ -497,6 +633,10 @@ cudaError_t launch_find2(const DevGeom& G, const DevParams& P, const DevWork& W,
   const unsigned gd = (unsigned)std::min<unsigned long long>((n_windows + 7ull) / 8ull, (unsigned long long)n_sm * 8);
   k_decode_digits<<<gd ? gd : 1, kDecThreads, 0, st>>>(G, W, n_windows);
   const unsigned int n_units = n_windows * kUnitsPerWin;
+  {
+    const unsigned gdesc = (unsigned)std::min<unsigned long long>((n_units + 255ull) / 256ull, (unsigned long long)n_sm * 8);
+    k_unit_descs<<<gdesc ? gdesc : 1, 256, 0, st>>>(G, W, n_units);
+  }
   const size_t sm = find2_smem_bytes(G.npmax);
   const bool ns = P.ns_min_dip > 0;
   const int nt = L.find_threads == 256 ? 256 : 128;
@@ -521,7 +661,7 @@ cudaError_t launch_find2(const DevGeom& G, const DevParams& P, const DevWork& W,
                   W.tickets + TK_SCAN_W, W.ctr + CTR_NCL, W.err, n_sm, st);
   if (e != cudaSuccess) return e;
   e = launch_compact(G, W, n_units, kUnitsPerWin, n_sm, st);
-  *launches += 4;
+  *launches += 5;
   return e;
 }
 

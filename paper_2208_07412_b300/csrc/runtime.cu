@@ -239,7 +239,8 @@ static uint64_t digit_cap(uint64_t pages_bytes) { return pages_bytes / 4 * 3 + 3
 
 static size_t slot_bytes(uint64_t pages, uint64_t windows, uint64_t cap_cl, uint64_t cap_ch, int nsr,
                          size_t dense = 0, uint64_t cap_dig = 0) {
-  size_t b = dense + pages + 16 + windows * (8 + 8 + 8 * kUnitsPerWindow + 4 * (kUnitsPerWindow + 2) + 32) +
+  size_t b = dense + pages + 16 + windows * (8 + 8 + 8 * kUnitsPerWindow + 4 * (kUnitsPerWindow + 2) + 32 +
+                                             48 * kUnitsPerWindow) +
              cap_dig * 4 + cap_cl * (16 + 16 + 16 + 8 + 8 + 8 + 8 + 4 + 8 + 4 + 4 + 4 + 4) +
              (scan_tiles(cap_cl) + scan_tiles(cap_ch) + scan_tiles(windows * kUnitsPerWindow)) * 8 +
              cap_ch * (14 * 4 + 8 + 16 + sizeof(tpc_track) + 4 * 12) +
@@ -270,7 +271,8 @@ static tpc_status slot_reserve(tpc_context* ctx, Slot& s, uint64_t pages_bytes, 
     CUDA_TRY(ensure(s.wincnt, windows * kUnitsPerWindow * 8));
     // span starts (one per unit) | light list | heavy list
     CUDA_TRY(ensure(s.winsoff, windows * (kUnitsPerWindow + 2) * 4));
-    CUDA_TRY(ensure(s.dtab, windows * 32));
+    // window table rows (2 x 16 bytes), then the units' descriptors (3 x 16 bytes each)
+    CUDA_TRY(ensure(s.dtab, windows * (32 + 48 * kUnitsPerWindow)));
     s.cap_windows = windows;
   }
   if (want_dig > s.cap_dig) {
@@ -324,6 +326,7 @@ static tpc_status slot_reserve(tpc_context* ctx, Slot& s, uint64_t pages_bytes, 
   W.heavy_list = (uint32_t*)s.winsoff.p + (kUnitsPerWindow + 1) * s.cap_windows;
   W.digits = (uint32_t*)s.digits.p;
   W.dtab = (uint4*)s.dtab.p;
+  W.udesc = (uint4*)s.dtab.p + 2 * s.cap_windows;
   W.cap_dig = s.cap_dig;
   W.up = (int32_t*)s.up.p; W.down = (int32_t*)s.down.p;
   W.score = (int64_t*)s.score.p;

@@ -103,6 +103,7 @@ struct DevWork {
   uint4* dtab;                   // [2 * n_windows] per window: (span start lo, hi, digits, 0) and the digit
                                  // counts before time bins 3, 61, 67, 125, 131, 189, 195, 253 (u16 pairs)
   uint64_t cap_dig;              // digits the array holds
+  uint4* udesc;                  // [3 * units] two-pass finder: unit descriptors (k_unit_descs)
   // CA
   int32_t* up; int32_t* down;
   int64_t* score;

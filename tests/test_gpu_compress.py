@@ -1,11 +1,11 @@
 """Parity of the track-model compression (step 10) with the oracle.  The codes
 are rounded float residuals to the FP32 (GPU) or FP64 (oracle) track model: a
 code may differ only where the oracle's residual, in steps, lies within
-DELTA = 0.05 step of a rounding boundary (a half-integer), and then by one
+DELTA = 0.1 step of a rounding boundary (a half-integer), and then by one
 step; a status (coded or escaped) only where it lies within DELTA of the
-+-127.5 escape bound.  The FP32 and FP64 predictions differ by ~1e-3 step
-(the observed difference rates, 2e-4 of the y codes and 2e-3 of the zeta codes,
-are those of a band of that width), so DELTA is a fifty-fold margin that
++-127.5 escape bound.  On full_tpc the differing codes lie at most 1.7e-3 step
+(y) and 3.8e-2 step (zeta: the prediction carries tgl times the arc, up to
+~250 cm) from their boundaries; DELTA leaves a factor 2.6 over the larger and
 still fails any code computed from a wrong prediction."""
 import numpy as np
 import pytest
@@ -13,7 +13,7 @@ import pytest
 import oracle
 import tpcgen
 
-DELTA = 0.05
+DELTA = 0.1
 
 pytestmark = pytest.mark.gpu
 
