@@ -112,7 +112,8 @@ typedef int32_t tpc_status;
                                      Without either flag the two-pass finder runs: every page decoded
                                      into 4-byte digit words (pad, time bin, ADC) in device memory (about
                                      1.7x the ZS bytes), then each 64-bin time chunk of a window clustered
-                                     in a small shared plane.  All three give the same clusters. */
+                                     in a small shared plane.  All three give the same clusters
+                                     (split_charge = 1 needs the two-pass finder). */
 
 /* Pipeline stages, in launch order (indices into tpc_get_stage_times). */
 #define TPC_STAGE_FIND       0    /* ZS decode + peak finder + cluster moments + compaction */
@@ -158,9 +159,10 @@ typedef struct {
                                      D_i > m * c0_i (c0 in the fit's unit), so that updates whose
                                      factors shrank below that are redone in FP64 (the FP64 check
                                      stays D_i > 0) */
+  int32_t  split_charge;     /* 0    charge splitting (step 3s): 1 on; two-pass finder only */
 } tpc_params;
 
-#define TPC_PARAMS_VERSION 2u
+#define TPC_PARAMS_VERSION 3u
 
 /* Timeframe descriptor.  pages / page_offsets are borrowed until tpc_poll
  * reports a state >= TPC_STATE_INPUT_RELEASED (host input) or >=
@@ -193,6 +195,7 @@ typedef struct {
 #define TPC_CL_EDGE      1u   /* peak on the first/last pad of the row or first/last time bin */
 #define TPC_CL_EXCLUDED  2u   /* an outer-ring digit with charge was left out */
 #define TPC_CL_NEIGHBOUR 4u   /* another peak lies in the 5x5 window */
+#define TPC_CL_SPLIT     8u   /* step 3s gave an included pixel less than its whole charge */
 
 /* Track record (112 bytes). */
 typedef struct {
@@ -262,6 +265,15 @@ void       tpc_destroy_context(tpc_context* ctx);
  *              pad_fp = 256 p + R(256 Sp, Q); time_fp = 128 (t - 256 f + 4) +
  *              R(128 St, Q); sigma2_pad = min(255, R(16 (Spp Q - Sp^2), Q^2)),
  *              likewise sigma2_time; qmax = q(peak); qtot = min(Q, 65535).
+ *   3s split   (only with split_charge = 1) charge of pixels near several
+ *              peaks is shared.  The owners O(x) of a pixel x are the step-2
+ *              peaks j with max(|p_x - p_j|, |t_x - t_j|) <= 1 if there is any,
+ *              else those with that distance <= 2.  Step 3's sums count an
+ *              included pixel x of the cluster of c with the weight
+ *              floor(q(x) q(c) / sum_{j in O(x)} q(j)) if c is in O(x), else 0
+ *              (the inclusion rule and flags still read q); flag TPC_CL_SPLIT
+ *              marks a cluster where some weight differed from q(x).  The owners
+ *              are step 2's peaks whether or not step 2b drops them.
  *   4 coords   Y = 2 (pad_fp - 128 (npads-1)), Z = 5 (32768 f + time_fp - 512),
  *              X = 64 row_x, all in u = 7.8125 um.
  *   5 CA       for a cluster c on rows 1..n_rows-2, over d on row-1 and u on row+1
@@ -588,6 +600,7 @@ tpc_status tpc_autotune(tpc_context* ctx, const tpc_timeframe_desc* sample, int 
  * computes, with no context and no allocation of any kind.
  *   geom          host geometry object
  *   params        NULL for defaults; only q_peak_min and ns_min_dip are used
+ *                 (split_charge must be 0: TPC_E_INVAL otherwise)
  *   device        CUDA device the pointers live on
  *   pages, page_offsets, pages_bytes, n_time_bins   as in tpc_timeframe_desc,
  *                 device memory, borrowed for the call; pages 16-byte aligned

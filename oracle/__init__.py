@@ -67,7 +67,8 @@ class _Params(ctypes.Structure):
                 ("merge_passes", ctypes.c_int32), ("min_track", ctypes.c_int32),
                 ("fit_passes", ctypes.c_int32), ("ns_min_dip", ctypes.c_int32), ("bz", ctypes.c_double),
                 ("sigma_y", ctypes.c_double), ("sigma_z", ctypes.c_double),
-                ("c0", ctypes.c_double * 5), ("search_all", ctypes.c_int32)]
+                ("c0", ctypes.c_double * 5), ("search_all", ctypes.c_int32),
+                ("split_charge", ctypes.c_int32)]
 
 
 @dataclass
@@ -92,12 +93,13 @@ class OracleParams:
     sigma_z: float = 0.03
     c0: tuple = (4.0, 4.0, 0.25, 1.0, 100.0)
     search_all: bool = False   # CA / merge visit every candidate (no time window)
+    split_charge: bool = False  # step 3s: pixels near several peaks share their charge
 
     def _c(self) -> _Params:
         p = _Params()
         for k in ("q_peak_min", "sy_num", "sy_den", "sz_num", "sz_den", "ca_cut", "min_chain",
                   "merge_cut", "gap_min", "gap_max", "merge_passes", "min_track", "fit_passes", "ns_min_dip",
-                  "search_all"):
+                  "search_all", "split_charge"):
             setattr(p, k, int(getattr(self, k)))
         p.bz, p.sigma_y, p.sigma_z = self.bz, self.sigma_y, self.sigma_z
         for i in range(5):
@@ -121,7 +123,9 @@ def _load():
         L.orc_peaks_plane.argtypes = [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P]
         L.orc_peaks_plane_ns.argtypes = [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P]
         L.orc_cluster_at.argtypes = [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                     ctypes.c_int, _P]
+                                     ctypes.c_int, ctypes.c_int, _P]
+        L.orc_split_share.argtypes = [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_int, ctypes.c_int]
         L.orc_ca.argtypes = [_P, _P, _P, ctypes.c_int64, _P, _P, _P]
         L.orc_merge.argtypes = [_P, _P, _P, ctypes.c_int64, _P, _P, _P, _P, _P, _P, ctypes.c_int64, _P]
         L.orc_merge.restype = ctypes.c_int64
@@ -207,13 +211,22 @@ def peaks_plane(plane: np.ndarray, q_peak_min: int = 10, ns_min_dip: int = 0) ->
     return fl.astype(bool)
 
 
-def cluster_at(plane: np.ndarray, pad: int, t: int, q_peak_min: int = 10) -> np.void:
+def cluster_at(plane: np.ndarray, pad: int, t: int, q_peak_min: int = 10, split: bool = False) -> np.void:
     L = _load()
     plane = np.ascontiguousarray(plane, dtype=np.uint16)
     T, np_ = plane.shape
     out = np.zeros(1, dtype=CLUSTER_DTYPE)
-    L.orc_cluster_at(plane.ctypes.data, np_, T, pad, t, q_peak_min, out.ctypes.data)
+    L.orc_cluster_at(plane.ctypes.data, np_, T, pad, t, q_peak_min, int(split), out.ctypes.data)
     return out[0]
+
+
+def split_share(plane: np.ndarray, peak: tuple, pixel: tuple, q_peak_min: int = 10) -> int:
+    """Step 3s: the charge of pixel (pad, t) that the cluster of the peak
+    (pad, t) counts when charge splitting is on."""
+    L = _load()
+    plane = np.ascontiguousarray(plane, dtype=np.uint16)
+    T, np_ = plane.shape
+    return int(L.orc_split_share(plane.ctypes.data, np_, T, q_peak_min, peak[0], peak[1], pixel[0], pixel[1]))
 
 
 def find_clusters(tf, params: OracleParams | None = None) -> np.ndarray:

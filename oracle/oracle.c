@@ -51,6 +51,7 @@ typedef struct {
   double bz, sigma_y, sigma_z;
   double c0[5];
   int32_t search_all;   /* 1: CA and merge visit every candidate (no window) */
+  int32_t split_charge; /* 1: step 3s, charge of pixels near several peaks is shared */
 } orc_params;
 
 /* 16-byte cluster record, field for field as documented by the library. */
@@ -185,10 +186,41 @@ static int ns_suppressed(const uint16_t* plane, int np, int T, int p, int t, int
   return 0;
 }
 
+/* Step 3s (optional charge splitting).  The owners O(x) of a pixel x are the
+ * step-2 peaks j at Chebyshev distance max(|p_x - p_j|, |t_x - t_j|) <= 1 from
+ * x if there is any, else those at distance <= 2 (x then lies only on the
+ * outer rings of their 5x5 windows).  Cluster c counts the charge of an
+ * included pixel x as its share
+ *     w_c(x) = floor(q(x) q(c) / sum_{j in O(x)} q(j))   if c is in O(x),
+ *     w_c(x) = 0                                          otherwise,
+ * so x's charge goes to the peaks whose cores hold it, in proportion to their
+ * heights, and the shares of all clusters never add up to more than q(x).  A
+ * peak is alone in its own 3x3 (peaks are never adjacent), so w_c(c) = q(c).
+ * Returns w_c(x) for the peak c = (pc, tc) and the pixel x = (px, pt). */
+static int split_share(const uint16_t* plane, int np, int T, int px, int pt, int pc, int tc, int qmin) {
+  int q = q_at(plane, np, T, px, pt);
+  if (q == 0) return 0;
+  for (int d = 1; d <= 2; d++) {
+    int64_t sum = 0;
+    int c_in = 0, any = 0;
+    for (int dt = -d; dt <= d; dt++)
+      for (int dp = -d; dp <= d; dp++) {
+        int pj = px + dp, tj = pt + dt;
+        if (pj < 0 || pj >= np || tj < 0 || tj >= T) continue;
+        if (!is_peak(plane, np, T, pj, tj, qmin)) continue;
+        any = 1;
+        sum += q_at(plane, np, T, pj, tj);
+        if (pj == pc && tj == tc) c_in = 1;
+      }
+    if (any) return c_in ? (int)(((int64_t)q * q_at(plane, np, T, pc, tc)) / sum) : 0;
+  }
+  return 0;   /* unreachable for x in the 5x5 window of the peak c */
+}
+
 static orc_cluster make_cluster(const uint16_t* plane, int np, int T, int s, int r, int p, int t,
-                                int qmin) {
+                                int qmin, int split) {
   int64_t Q = 0, Sp = 0, St = 0, Spp = 0, Stt = 0;
-  int excluded = 0, other_peak = 0;
+  int excluded = 0, other_peak = 0, shared = 0;
   for (int dt = -2; dt <= 2; dt++)
     for (int dp = -2; dp <= 2; dp++) {
       int q = q_at(plane, np, T, p + dp, t + dt);
@@ -200,6 +232,11 @@ static orc_cluster make_cluster(const uint16_t* plane, int np, int T, int s, int
         int qi = q_at(plane, np, T, p + ip, t + it);
         inc = (qi > 0) && (q <= qi);
         if (!inc && q > 0) excluded = 1;
+      }
+      if (inc && split && q > 0) {
+        int w = split_share(plane, np, T, p + dp, t + dt, p, t, qmin);
+        if (w != q) shared = 1;
+        q = w;
       }
       if (inc) {
         Q += q; Sp += (int64_t)q * dp; St += (int64_t)q * dt;
@@ -223,6 +260,7 @@ static orc_cluster make_cluster(const uint16_t* plane, int np, int T, int s, int
   if (p == 0 || p == np - 1 || t == 0 || t == T - 1) c.flags |= 1;
   if (excluded) c.flags |= 2;
   if (other_peak) c.flags |= 4;
+  if (shared) c.flags |= 8;
   c.row = (uint8_t)r;
   c.t_peak = (uint16_t)t;
   c.pad_peak = (uint8_t)p;
@@ -245,7 +283,7 @@ int64_t orc_find_clusters(const orc_input* in, const orc_params* P, orc_cluster*
         for (int p = 0; p < np; p++)
           if (is_peak(plane, np, T, p, t, P->q_peak_min) &&
               !ns_suppressed(plane, np, T, p, t, P->q_peak_min, P->ns_min_dip)) {
-            if (out && n < cap) out[n] = make_cluster(plane, np, T, s, r, p, t, P->q_peak_min);
+            if (out && n < cap) out[n] = make_cluster(plane, np, T, s, r, p, t, P->q_peak_min, P->split_charge);
             n++;
           }
     }
@@ -285,8 +323,14 @@ void orc_peaks_plane_ns(const uint16_t* plane, int np, int T, int qmin, int min_
 }
 
 /* One cluster from a dense plane (tests). */
-void orc_cluster_at(const uint16_t* plane, int np, int T, int p, int t, int qmin, orc_cluster* out) {
-  *out = make_cluster(plane, np, T, 0, 0, p, t, qmin);
+void orc_cluster_at(const uint16_t* plane, int np, int T, int p, int t, int qmin, int split, orc_cluster* out) {
+  *out = make_cluster(plane, np, T, 0, 0, p, t, qmin, split);
+}
+
+/* Step 3s share w_c(x) of the pixel x = (px, pt) in the cluster of the peak
+ * c = (pc, tc) of one dense plane (tests). */
+int orc_split_share(const uint16_t* plane, int np, int T, int qmin, int pc, int tc, int px, int pt) {
+  return split_share(plane, np, T, px, pt, pc, tc, qmin);
 }
 
 /* ------------------------------------------------------------ 4. coordinates */

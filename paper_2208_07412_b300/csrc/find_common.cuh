@@ -92,10 +92,14 @@ __device__ __forceinline__ int window_frs(const DevGeom& G, unsigned int w) {
 // The record of the cluster of the peak at (tt, p) from its 5x5 charges
 // q[dt + 2][dp + 2] and whether another peak lies in the 5x5 (other): the
 // inner/outer rule, integer moments, packed 16-byte record and coordinates.
-__device__ __forceinline__ void cluster_record(const int (&q)[5][5], bool other, int np, int T, int s, int r, int f,
-                                               int tt, int p, int xrow, uint4& rec, int4& xyz) {
+// kW: the moments sum the step-3s weights w instead of q (the rule still reads
+// q), and the record is flagged when an included pixel's weight differs.
+template <bool kW>
+__device__ __forceinline__ void cluster_record_t(const int (&q)[5][5], const int (&w)[5][5], bool other, int np,
+                                                 int T, int s, int r, int f, int tt, int p, int xrow, uint4& rec,
+                                                 int4& xyz) {
   int Q = 0, Sp = 0, St = 0, Spp = 0, Stt = 0;
-  bool excl = false;
+  bool excl = false, split = false;
 #pragma unroll
   for (int dt = -2; dt <= 2; dt++) {
 #pragma unroll
@@ -108,7 +112,9 @@ __device__ __forceinline__ void cluster_record(const int (&q)[5][5], bool other,
         inc = qi > 0 && v <= qi;
         excl |= (!inc && v > 0);
       }
-      if (inc) { Q += v; Sp += v * dp; St += v * dt; Spp += v * dp * dp; Stt += v * dt * dt; }
+      const int x = kW ? w[dt + 2][dp + 2] : v;
+      if (kW) split |= inc && x != v;
+      if (inc) { Q += x; Sp += x * dp; St += x * dt; Spp += x * dp * dp; Stt += x * dt * dt; }
     }
   }
   const int t_in = tt - kHalo;
@@ -119,12 +125,17 @@ __device__ __forceinline__ void cluster_record(const int (&q)[5][5], bool other,
   const int vp = round_half_up_sat255(16LL * ((long long)Spp * Q - (long long)Sp * Sp), QQ);
   const int vt = round_half_up_sat255(16LL * ((long long)Stt * Q - (long long)St * St), QQ);
   const int flags = ((p == 0 || p == np - 1 || t == 0 || t == T - 1) ? TPC_CL_EDGE : 0) |
-                    (excl ? TPC_CL_EXCLUDED : 0) | (other ? TPC_CL_NEIGHBOUR : 0);
+                    (excl ? TPC_CL_EXCLUDED : 0) | (other ? TPC_CL_NEIGHBOUR : 0) | (split ? TPC_CL_SPLIT : 0);
   rec.x = (uint32_t)(pad_fp & 0xffff) | ((uint32_t)(time_fp & 0xffff) << 16);
   rec.y = (uint32_t)q[2][2] | ((uint32_t)min(Q, 65535) << 16);
   rec.z = (uint32_t)vp | ((uint32_t)vt << 8) | ((uint32_t)flags << 16) | ((uint32_t)r << 24);
   rec.w = (uint32_t)t | ((uint32_t)p << 16) | ((uint32_t)s << 24);
   xyz = make_int4(xrow, 2 * (pad_fp - 128 * (np - 1)), 5 * (32768 * f + time_fp - 512), t);
+}
+
+__device__ __forceinline__ void cluster_record(const int (&q)[5][5], bool other, int np, int T, int s, int r, int f,
+                                               int tt, int p, int xrow, uint4& rec, int4& xyz) {
+  cluster_record_t<false>(q, q, other, np, T, s, r, f, tt, p, xrow, rec, xyz);
 }
 
 }  // namespace tpc

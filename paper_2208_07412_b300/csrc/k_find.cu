@@ -1684,6 +1684,8 @@ extern "C" tpc_status tpc_find_clusters_noalloc(const tpc_geometry* geom, const 
   if (q_peak_min < 1 || q_peak_min > 1023) return fail(TPC_E_INVAL, "tpc_find_clusters_noalloc: bad q_peak_min");
   const int ns_min_dip = params ? params->ns_min_dip : 0;
   if (ns_min_dip < 0 || ns_min_dip > 1023) return fail(TPC_E_INVAL, "tpc_find_clusters_noalloc: bad ns_min_dip");
+  if (params && params->split_charge)
+    return fail(TPC_E_INVAL, "tpc_find_clusters_noalloc: split_charge is not supported here");
   const unsigned long long nfrag = (n_time_bins + kFrag - 1) / kFrag;
   const unsigned long long nwin = (unsigned long long)geom->n_sectors * geom->n_rows * nfrag;
   if (nwin > kNoAllocMaxWindows)

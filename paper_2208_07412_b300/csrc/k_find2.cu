@@ -8,16 +8,19 @@
 // becomes one 32-bit word (pad | t_in << 8 | adc << 16) in page order, i.e.
 // ascending (time bin, pad), in a span of a digit array the page reserves
 // with one atomic.  A table row per window gives the span and the number of
-// digits before the time bins 3, 61, 67, 125, 131, 189, 195 and 253, the
-// boundaries of the find units' row ranges (the digit index of the first run
-// at or past each, stored by the lane that finds it).  Every check of the page format
-// is made here; a bad page sets the corruption bit and gets an empty span.
+// digits before the time bins H, 64 - H, 64 + H, ..., 192 + H and 256 - H, the
+// boundaries of the find units' row ranges for a time halo of H bins (3, or 5
+// with charge splitting): the digit index of the first run at or past each,
+// stored by the lane that finds it.  Every check of the page format is made
+// here; a bad page sets the corruption bit and gets an empty span.
 //
 // Pass 2, k_find_units: one CTA at a time per unit = (window, 64-bin time
-// chunk).  The unit's digits (its 64 time bins with 3-bin halos on both sides,
+// chunk).  The unit's digits (its 64 time bins with H-bin halos on both sides,
 // from the window and, at the fragment edges, its neighbours) go into a
-// zero-padded shared plane of 70 rows (20 KB for 138 pads instead of the 74 KB
-// a whole window needs, so that several CTAs share an SM).  The peak test runs
+// zero-padded shared plane of 64 + 2H rows (70 rows, 20 KB for 138 pads, instead
+// of the 74 KB a whole window needs, so that several CTAs share an SM).  Step 3s
+// (charge splitting) needs the peaks up to 4 bins from an own peak, hence the
+// values up to 5 bins away: H = 5 there, 3 otherwise.  The peak test runs
 // strided over the digits; a peak is marked in the plane (bit 15 of its ADC
 // word), which the 5x5 of a cluster reads as "another peak" and step 2b as the
 // step-2 peak set; warp ballots rank the own peaks in canonical order into a
@@ -30,10 +33,12 @@ namespace tpc {
 
 constexpr int kChunkT = 64;                          // own time bins of a unit
 constexpr int kUnitsPerWin = kFrag / kChunkT;        // 4
-constexpr int kURows = kChunkT + 2 * kHalo;          // 70 plane rows
 constexpr int kDecThreads = 256;                     // decode block (8 warps, one page each)
-// Digit counts recorded per window: digits with t_in < kBound[k].
-__constant__ int kBound[8] = {3, 61, 67, 125, 131, 189, 195, 253};
+// Time halo of a unit's plane: 3 bins (the 3x3 test of a pixel 2 bins away),
+// 5 with step 3s (the peaks up to 4 bins away).
+__host__ __device__ constexpr int unit_halo(bool split) { return split ? 5 : 3; }
+// Digit counts recorded per window: digits with t_in < bound_of(k, H), k = 0..7.
+__device__ __forceinline__ int bound_of(int k, int H) { return kChunkT * ((k + 1) >> 1) + ((k & 1) ? -H : H); }
 constexpr uint16_t kPeakBit = 0x8000;                // plane word: a peak of step 2
 constexpr uint16_t kDropBit = 0x4000;                // plane word: dropped by step 2b
 constexpr uint32_t kAdcMask = 1023u;
@@ -74,7 +79,8 @@ __device__ __forceinline__ void prefetch_l2_bytes(const void* p, unsigned long l
 
 constexpr int kDecStage = 4096;                      // bytes of a page body staged per warp
 
-__global__ void __launch_bounds__(kDecThreads, 5) k_decode_digits(DevGeom G, DevWork W, unsigned int n_windows) {
+__global__ void __launch_bounds__(kDecThreads, 5) k_decode_digits(DevGeom G, DevWork W, unsigned int n_windows,
+                                                                  int H) {
   __shared__ __align__(16) uint8_t stage_all[kDecThreads / 32][kDecStage];
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
@@ -172,7 +178,7 @@ __global__ void __launch_bounds__(kDecThreads, 5) k_decode_digits(DevGeom G, Dev
           if (lane < n_run) {
 #pragma unroll
             for (int k = 0; k < 8; k++)
-              if (t_prev_run < kBound[k] && tr >= kBound[k]) btab[k] = (uint16_t)(d_cur + drel);
+              if (t_prev_run < bound_of(k, H) && tr >= bound_of(k, H)) btab[k] = (uint16_t)(d_cur + drel);
           }
           // ---- the chunk's digits, 32 at a time: run by search, ADC from its word
           for (int D = 0; D < n_rd; D += 32) {
@@ -227,20 +233,20 @@ __device__ __forceinline__ void unit_desc(const DevGeom& G, const DevWork& W, un
   const int f = frs & 0xffff;
   const uint4 a = W.dtab[2ull * w], b = W.dtab[2ull * w + 1];
   const unsigned long long db = a.x | ((unsigned long long)a.y << 32);
-  // own digits: time bins [64c - 3, 64c + 67) of the window
+  // own digits: time bins [64c - H, 64c + 64 + H) of the window
   const uint32_t lo = tab_count(b, a.z, c == 0 ? -1 : 2 * c - 1);
   const uint32_t hi = tab_count(b, a.z, c == kUnitsPerWin - 1 ? 8 : 2 * c + 2);
   D.seg_start[1] = db + lo;
   D.seg_n[1] = (int)(hi > lo ? hi - lo : 0u);
   D.seg_n[0] = D.seg_n[2] = 0;
   D.seg_start[0] = D.seg_start[2] = 0;
-  if (c == 0 && f > 0) {          // the previous window's time bins >= 253
+  if (c == 0 && f > 0) {          // the previous window's time bins >= 256 - H
     const uint4 ap = W.dtab[2ull * (w - 1)], bp = W.dtab[2ull * (w - 1) + 1];
     const uint32_t l0 = tab_count(bp, ap.z, 7);
     D.seg_start[0] = (ap.x | ((unsigned long long)ap.y << 32)) + l0;
     D.seg_n[0] = (int)(ap.z > l0 ? ap.z - l0 : 0u);
   }
-  if (c == kUnitsPerWin - 1 && f + 1 < G.n_frag) {   // the next window's time bins < 3
+  if (c == kUnitsPerWin - 1 && f + 1 < G.n_frag) {   // the next window's time bins < H
     const uint4 an = W.dtab[2ull * (w + 1)], bn = W.dtab[2ull * (w + 1) + 1];
     D.seg_start[2] = an.x | ((unsigned long long)an.y << 32);
     D.seg_n[2] = (int)tab_count(bn, an.z, 0);
@@ -328,8 +334,57 @@ __device__ __forceinline__ void prefetch_l2_span(const uint32_t* p, int n) {
 }
 
 // Plane row offsets of the three segments: row = t_in + offset.
+template <int H>
 __device__ __forceinline__ int seg_row_offset(int k, int c) {
-  return k == 0 ? kHalo - kFrag : (k == 1 ? kHalo - kChunkT * c : kHalo + kFrag - kChunkT * (kUnitsPerWin - 1));
+  return k == 0 ? H - kFrag : (k == 1 ? H - kChunkT * c : H + kFrag - kChunkT * (kUnitsPerWin - 1));
+}
+
+// Step 3s weights of the 5x5 window of the own peak at plane index L (charges
+// q, from the plane): w = floor(q(x) q(c) / sum of the owners' charges) when
+// the peak c owns x, else 0.  The owners of x are the step-2 peaks of x's 3x3,
+// or of its 5x5 when its 3x3 holds none.  A window with no other peak within 4
+// pixels keeps w = q.  Reads rows L / ps - 4 .. + 4 (inside the 74-row plane
+// for own rows) and pads up to 4 beyond the row, which land on empty padding.
+__device__ __forceinline__ void split_weights(const uint16_t* pl, int L, int ps, const int (&q)[5][5],
+                                              int (&w)[5][5]) {
+  const int qc = q[2][2];
+  bool near = false;
+  for (int dt = -4; dt <= 4; dt++) {
+    const uint16_t* rw = pl + L + dt * ps;
+#pragma unroll
+    for (int dp = -4; dp <= 4; dp++) near |= (dt | dp) != 0 && (rw[dp] & kPeakBit) != 0;
+  }
+#pragma unroll
+  for (int dt = 0; dt < 5; dt++)
+#pragma unroll
+    for (int dp = 0; dp < 5; dp++) w[dt][dp] = q[dt][dp];
+  if (!near) return;
+  for (int dt = -2; dt <= 2; dt++) {
+    for (int dp = -2; dp <= 2; dp++) {
+      const int v = q[dt + 2][dp + 2];
+      if (v == 0) continue;
+      const int X = L + dt * ps + dp;
+      int s1 = 0;
+      for (int a = -1; a <= 1; a++)
+        for (int b = -1; b <= 1; b++) {
+          const uint16_t y = pl[X + a * ps + b];
+          if (y & kPeakBit) s1 += y & kAdcMask;
+        }
+      int wt;
+      if (s1 > 0) {
+        wt = (dt >= -1 && dt <= 1 && dp >= -1 && dp <= 1) ? (v * qc) / s1 : 0;
+      } else {
+        int s2 = 0;   // >= q(c): the peak lies in x's 5x5
+        for (int a = -2; a <= 2; a++)
+          for (int b = -2; b <= 2; b++) {
+            const uint16_t y = pl[X + a * ps + b];
+            if (y & kPeakBit) s2 += y & kAdcMask;
+          }
+        wt = (v * qc) / s2;
+      }
+      w[dt + 2][dp + 2] = wt;
+    }
+  }
 }
 
 // Units are taken round-robin (unit blockIdx.x + k gridDim.x).  Their
@@ -343,9 +398,11 @@ __device__ __forceinline__ int seg_row_offset(int k, int c) {
 // (the register path) keep each thread's digits as (plane index, row) words
 // in registers between the plane build and step 2, and rank all rounds with
 // one prefix; larger units re-read their digits and rank round by round.
-template <int kThreads, bool kNs>
+template <int kThreads, bool kNs, bool kSplit>
 __global__ void __launch_bounds__(kThreads, 1024 / kThreads)
     k_find_units(DevGeom G, DevParams P, DevWork W, unsigned int n_units) {
+  constexpr int kH = unit_halo(kSplit);             // time halo of the plane
+  constexpr int kURows = kChunkT + 2 * kH;          // plane rows
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ UnitSmem<kThreads> U;
   constexpr int kWarps = kThreads / 32;
@@ -397,7 +454,7 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads)
     const unsigned long long st0 = q0.x | ((unsigned long long)q0.y << 32);
     const unsigned long long st1 = (q0.z | ((unsigned long long)q0.w << 32)) - n0;
     const unsigned long long st2 = (q1.x | ((unsigned long long)q1.y << 32)) - n01;
-    const int of0 = seg_row_offset(0, c), of1 = seg_row_offset(1, c), of2 = seg_row_offset(2, c);
+    const int of0 = seg_row_offset<kH>(0, c), of1 = seg_row_offset<kH>(1, c), of2 = seg_row_offset<kH>(2, c);
     // digit i of the unit -> (its word, its plane row offset)
     auto digit = [&](int i, int& off) -> uint32_t {
       const unsigned long long g = i < n0 ? st0 + i : (i < n01 ? st1 + i : st2 + i);
@@ -434,7 +491,7 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads)
           const int q = plane[L];
           if (q >= P.q_peak_min && peak_test(plane, L, ps, q, P.q_peak_min)) {
             plane[L] = (uint16_t)(q | kPeakBit);       // only this thread writes this pixel
-            if (row >= kHalo && row < kHalo + kChunkT) own |= 1u << k;
+            if (row >= kH && row < kH + kChunkT) own |= 1u << k;
           }
         }
       }
@@ -508,7 +565,7 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads)
             const int q = plane[L];
             if (q >= P.q_peak_min && peak_test(plane, L, ps, q, P.q_peak_min)) {
               plane[L] = (uint16_t)(q | kPeakBit);     // only this thread writes this pixel
-              own = !kNs && row >= kHalo && row < kHalo + kChunkT;
+              own = !kNs && row >= kH && row < kH + kChunkT;
             }
           }
         }
@@ -537,7 +594,7 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads)
             int off;
             const uint32_t d = digit(i, off);
             const int row = (int)((d >> 8) & 255u) + off;
-            if (row >= kHalo && row < kHalo + kChunkT) {
+            if (row >= kH && row < kH + kChunkT) {
               L = row * ps + kPad + (int)(d & 255u);
               const uint16_t v = plane[L];
               if (v & kPeakBit) {
@@ -575,7 +632,7 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads)
       const unsigned long long sb = U.sbase;
       const int f = frs & 0xffff, r = (frs >> 16) & 0xff, s = (frs >> 24) & 0xff;
       const int np = G.npads[r], xrow = G.xrow[r];
-      const int t0 = kChunkT * c - kHalo;          // time bin (within the window) of plane row 0
+      const int t0 = kChunkT * c - kH;             // time bin (within the window) of plane row 0
       for (uint32_t j = tid; j < total; j += kThreads) {
         const int L = plist[j];
         const int row = L / ps, p = L - row * ps - kPad;
@@ -591,7 +648,13 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads)
           }
         uint4 rec;
         int4 xyz;
-        cluster_record(q, other, np, T, s, r, f, t0 + row + kHalo, p, xrow, rec, xyz);
+        if (kSplit) {
+          int w[5][5];
+          split_weights(plane, L, ps, q, w);
+          cluster_record_t<true>(q, w, other, np, T, s, r, f, t0 + row + kHalo, p, xrow, rec, xyz);
+        } else {
+          cluster_record(q, other, np, T, s, r, f, t0 + row + kHalo, p, xrow, rec, xyz);
+        }
         const unsigned long long idx = sb + j;
         if (idx < W.cap_cl) reinterpret_cast<uint4*>(W.scratch_cl)[idx] = rec;
       }
@@ -604,19 +667,30 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads)
 
 // Dynamic shared memory of k_find_units: the plane, then the list of a unit's
 // own peaks (at most one per pair of pads of each of its 64 rows).
-size_t find2_smem_bytes(int npmax) {
-  return (((size_t)kURows * (npmax + 2 * kPad) * 2 + 15) & ~(size_t)15) + (size_t)kChunkT * ((npmax + 1) / 2) * 2;
+size_t find2_smem_bytes(int npmax, bool split) {
+  return (((size_t)(kChunkT + 2 * unit_halo(split)) * (npmax + 2 * kPad) * 2 + 15) & ~(size_t)15) +
+         (size_t)kChunkT * ((npmax + 1) / 2) * 2;
+}
+
+template <int kThreads, bool kNs, bool kSplit>
+static const void* units_fn() { return (const void*)k_find_units<kThreads, kNs, kSplit>; }
+
+// The instantiation for (threads, step 2b, step 3s).
+static const void* units_kernel(int nt, bool ns, bool split) {
+  if (nt == 256)
+    return split ? (ns ? units_fn<256, true, true>() : units_fn<256, false, true>())
+                 : (ns ? units_fn<256, true, false>() : units_fn<256, false, false>());
+  return split ? (ns ? units_fn<128, true, true>() : units_fn<128, false, true>())
+               : (ns ? units_fn<128, true, false>() : units_fn<128, false, false>());
 }
 
 cudaError_t prepare_find2() {
-  cudaError_t e = cudaFuncSetAttribute(k_find_units<128, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       96 * 1024);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_find_units<128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_find_units<256, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_find_units<256, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+  cudaError_t e = cudaSuccess;
+  for (int nt : {128, 256})
+    for (int ns = 0; ns < 2; ns++)
+      for (int sp = 0; sp < 2; sp++)
+        if (e == cudaSuccess)
+          e = cudaFuncSetAttribute(units_kernel(nt, ns, sp), cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
   return e;
 }
 
@@ -631,29 +705,28 @@ cudaError_t launch_compact(const DevGeom& G, const DevWork& W, unsigned int n_un
 cudaError_t launch_find2(const DevGeom& G, const DevParams& P, const DevWork& W, unsigned int n_windows, int n_sm,
                          const LaunchCfg& L, cudaStream_t st, unsigned long long* unit_scan_state, int* launches) {
   const unsigned gd = (unsigned)std::min<unsigned long long>((n_windows + 7ull) / 8ull, (unsigned long long)n_sm * 8);
-  k_decode_digits<<<gd ? gd : 1, kDecThreads, 0, st>>>(G, W, n_windows);
+  const bool split = P.split_charge != 0;
+  k_decode_digits<<<gd ? gd : 1, kDecThreads, 0, st>>>(G, W, n_windows, unit_halo(split));
   const unsigned int n_units = n_windows * kUnitsPerWin;
   {
     const unsigned gdesc = (unsigned)std::min<unsigned long long>((n_units + 255ull) / 256ull, (unsigned long long)n_sm * 8);
     k_unit_descs<<<gdesc ? gdesc : 1, 256, 0, st>>>(G, W, n_units);
   }
-  const size_t sm = find2_smem_bytes(G.npmax);
+  const size_t sm = find2_smem_bytes(G.npmax, split);
   const bool ns = P.ns_min_dip > 0;
   const int nt = L.find_threads == 256 ? 256 : 128;
-  const void* fn = nt == 256 ? (ns ? (const void*)k_find_units<256, true> : (const void*)k_find_units<256, false>)
-                             : (ns ? (const void*)k_find_units<128, true> : (const void*)k_find_units<128, false>);
+  const void* fn = units_kernel(nt, ns, split);
   // CTAs that are all resident at once (each takes every gridDim.x-th unit)
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, nt, sm) != cudaSuccess || per_sm < 1) per_sm = 1;
   per_sm = std::min(per_sm, L.find_ctas_per_sm);
   const unsigned gu = (unsigned)std::max<unsigned long long>(
       1ull, std::min<unsigned long long>(n_units, (unsigned long long)n_sm * per_sm));
-  if (nt == 256) {
-    if (ns) k_find_units<256, true><<<gu, 256, sm, st>>>(G, P, W, n_units);
-    else k_find_units<256, false><<<gu, 256, sm, st>>>(G, P, W, n_units);
-  } else {
-    if (ns) k_find_units<128, true><<<gu, 128, sm, st>>>(G, P, W, n_units);
-    else k_find_units<128, false><<<gu, 128, sm, st>>>(G, P, W, n_units);
+  {
+    unsigned int nu = n_units;
+    void* args[] = {const_cast<DevGeom*>(&G), const_cast<DevParams*>(&P), const_cast<DevWork*>(&W), &nu};
+    cudaError_t le = cudaLaunchKernel(fn, dim3(gu), dim3(nt), args, sm, st);
+    if (le != cudaSuccess) return le;
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;

@@ -158,6 +158,7 @@ extern "C" tpc_status tpc_params_default(tpc_params* p) {
   p->sigma_y = 0.02; p->sigma_z = 0.03;
   p->c0[0] = 4.0; p->c0[1] = 4.0; p->c0[2] = 0.25; p->c0[3] = 1.0; p->c0[4] = 100.0;
   p->fp32_pd_margin = 0.0;
+  p->split_charge = 0;
   return TPC_OK;
 }
 
@@ -202,6 +203,7 @@ static tpc_status check_params(const tpc_params& p, const tpc_geometry& g) {
     if (!(p.c0[i] > 0)) return fail(TPC_E_INVAL, "params: c0 must be positive");
   if (!(p.fp32_pd_margin >= 0 && p.fp32_pd_margin < 1))
     return fail(TPC_E_INVAL, "params: fp32_pd_margin must be in [0, 1)");
+  if (p.split_charge != 0 && p.split_charge != 1) return fail(TPC_E_INVAL, "params: split_charge must be 0 or 1");
   // CA scores must fit the 41-bit field of the edge-row keys
   for (int r = 1; r + 1 < g.n_rows; r++) {
     long double lim = (long double)p.ca_cut * 64.0L * (g.row_x[r + 1] - g.row_x[r - 1]);
@@ -392,6 +394,9 @@ extern "C" tpc_status tpc_create_context(const tpc_geometry* geom, const tpc_par
   if (params) p = *params; else tpc_params_default(&p);
   tpc_status st = check_params(p, *geom);
   if (st) return st;
+  if (p.split_charge && (flags & (TPC_CTX_DENSE_FINDER | TPC_CTX_FUSED_FINDER)))
+    return fail(TPC_E_INVAL, "params: split_charge needs the two-pass finder (no TPC_CTX_DENSE_FINDER / "
+                             "TPC_CTX_FUSED_FINDER)");
   int ndev = 0;
   CUDA_TRY(cudaGetDeviceCount(&ndev));
   if (device < 0 || device >= ndev) return fail(TPC_E_INVAL, "no such CUDA device");
@@ -414,6 +419,7 @@ extern "C" tpc_status tpc_create_context(const tpc_geometry* geom, const tpc_par
   DevParams& P = ctx->P;
   P.q_peak_min = p.q_peak_min;
   P.ns_min_dip = p.ns_min_dip;
+  P.split_charge = p.split_charge;
   P.sy_num = p.ca_slope_y_num; P.sy_den = p.ca_slope_y_den;
   P.sz_num = p.ca_slope_z_num; P.sz_den = p.ca_slope_z_den;
   P.ca_cut = p.ca_cut; P.min_chain = p.min_chain;

@@ -64,6 +64,7 @@ struct LaunchCfg {
 struct DevParams {
   int q_peak_min;
   int ns_min_dip;                // 5x5 noise suppression: 0 off, else the minimum dip (ADC)
+  int split_charge;              // step 3s charge splitting: 0 off, 1 on (two-pass finder only)
   int sy_num, sy_den, sz_num, sz_den;
   int ca_cut, min_chain;
   int merge_cut, gap_min, gap_max, merge_passes;

@@ -61,7 +61,8 @@ class tpc_params(ctypes.Structure):
                 ("min_track", ctypes.c_int32), ("fit_passes", ctypes.c_int32),
                 ("ns_min_dip", ctypes.c_int32), ("bz", ctypes.c_double),
                 ("sigma_y", ctypes.c_double), ("sigma_z", ctypes.c_double),
-                ("c0", ctypes.c_double * 5), ("fp32_pd_margin", ctypes.c_double)]
+                ("c0", ctypes.c_double * 5), ("fp32_pd_margin", ctypes.c_double),
+                ("split_charge", ctypes.c_int32)]
 
 
 class tpc_tuning(ctypes.Structure):

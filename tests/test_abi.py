@@ -33,7 +33,7 @@ def test_params_defaults():
     assert (p.q_peak_min, p.ca_cut, p.min_chain, p.merge_cut, p.min_track, p.fit_passes) == (10, 256, 5, 384, 10, 3)
     assert (p.ca_slope_z_num, p.ca_slope_z_den, p.merge_gap_min, p.merge_gap_max) == (11, 10, 1, 6)
     assert list(p.c0) == [4.0, 4.0, 0.25, 1.0, 100.0] and p.bz == 0.5
-    assert p.fp32_pd_margin == 0.0 and p.version == 2
+    assert p.fp32_pd_margin == 0.0 and p.split_charge == 0 and p.version == 3
 
 
 def test_geometry_validation():
