@@ -1,32 +1,36 @@
 // k_find2.cu — the two-pass cluster finder, the pipeline's default for steps
-// 1-4 (ZS decode, 3x3 peaks, 5x5 clusters, canonical order).  The paper's
-// section "Hardware and data flow" places this first step of the TPC
-// reconstruction on the EPN GPUs, after FPGA zero suppression.
+// 1-4 (ZS decode, 3x3 peaks, 5x5 clusters, canonical order) and the optional
+// steps 2b and 3s.  The paper's section "Hardware and data flow" places this
+// first step of the TPC reconstruction on the EPN GPUs, after FPGA zero
+// suppression.
 //
-// Pass 1, k_decode_digits: one warp per page.  Entries, runs and digits are
-// walked in chunks of 32 with warp scans (no block barrier): every digit
-// becomes one 32-bit word (pad | t_in << 8 | adc << 16) in page order, i.e.
-// ascending (time bin, pad), in a span of a digit array the page reserves
-// with one atomic.  A table row per window gives the span and the number of
-// digits before the time bins H, 64 - H, 64 + H, ..., 192 + H and 256 - H, the
-// boundaries of the find units' row ranges for a time halo of H bins (3, or 5
-// with charge splitting): the digit index of the first run at or past each,
-// stored by the lane that finds it.  Every check of the page format is made
-// here; a bad page sets the corruption bit and gets an empty span.
+// Pass 1, k_decode_runs: one warp per page.  Entries and runs are walked in
+// chunks of 32 with warp scans (no block barrier); every check of the page
+// format is made here, and a bad page sets the corruption bit and gets an empty
+// span.  Each pad run becomes one 8-byte record (pad, length, time bin, index
+// of its first digit in the page) in a span of a run array the page reserves
+// with one atomic.  Digits are not touched: their ADCs stay in the page.  A
+// table row per window gives the span, the ADC words' offset and the index of
+// the first run at or past each of the time bins H, 64 - H, 64 + H, ...,
+// 192 + H, 256 - H: the boundaries of the find units' time ranges for a halo of
+// H bins (3; 5 with charge splitting, step 3s).
 //
 // Pass 2, k_find_units: one CTA at a time per unit = (window, 64-bin time
-// chunk).  The unit's digits (its 64 time bins with H-bin halos on both sides,
-// from the window and, at the fragment edges, its neighbours) go into a
-// zero-padded shared plane of 64 + 2H rows (70 rows, 20 KB for 138 pads, instead
-// of the 74 KB a whole window needs, so that several CTAs share an SM).  Step 3s
-// (charge splitting) needs the peaks up to 4 bins from an own peak, hence the
-// values up to 5 bins away: H = 5 there, 3 otherwise.  The peak test runs
-// strided over the digits; a peak is marked in the plane (bit 15 of its ADC
-// word), which the 5x5 of a cluster reads as "another peak" and step 2b as the
-// step-2 peak set; warp ballots rank the own peaks in canonical order into a
-// list, over which the clusters are built.  Each unit reserves a span of the
-// scratch buffer with one atomic; the unit-count scan and the compaction of
-// k_find.cu then place the spans canonically.
+// chunk).  A unit's runs (its 64 time bins with H-bin halos on both sides, from
+// the window and, at the fragment edges, its neighbours) are expanded into a
+// zero-padded shared plane of 64 + 2H rows (20 KB for 138 pads, so that seven
+// CTAs share an SM): one thread per run, its ADCs read from the page (the
+// unit's runs and ADC words are prefetched into L2 while the previous unit
+// runs; a run's words are then L1 hits after the first).  The expansion also lists
+// every digit's plane index in page order (time-major, pad-ascending); step 2
+// runs over that list with one thread per digit, marks peaks in the plane (bit
+// 15 of the word: what the 5x5 of a cluster reads as "another peak", step 2b as
+// the step-2 peak set and step 3s as the owners) and keeps a per-thread bit
+// mask of its own peaks, which warp ballots and one prefix rank in canonical
+// order.  Units with more digits than the list holds test every pixel of the
+// plane instead.  Clusters are built over the ranked list; each unit reserves
+// a span of the scratch buffer with one atomic, and the unit-count scan and
+// the compaction of k_find.cu place the spans canonically.
 #include "find_common.cuh"
 
 namespace tpc {
@@ -34,10 +38,12 @@ namespace tpc {
 constexpr int kChunkT = 64;                          // own time bins of a unit
 constexpr int kUnitsPerWin = kFrag / kChunkT;        // 4
 constexpr int kDecThreads = 256;                     // decode block (8 warps, one page each)
+constexpr int kDigCap = 2048;                        // digits a unit lists for the digit-driven step 2
+constexpr int kDescWords = 7;                        // 16-byte words of a unit descriptor
 // Time halo of a unit's plane: 3 bins (the 3x3 test of a pixel 2 bins away),
 // 5 with step 3s (the peaks up to 4 bins away).
 __host__ __device__ constexpr int unit_halo(bool split) { return split ? 5 : 3; }
-// Digit counts recorded per window: digits with t_in < bound_of(k, H), k = 0..7.
+// Run indices recorded per window: the first run with t_in >= bound_of(k, H), k = 0..7.
 __device__ __forceinline__ int bound_of(int k, int H) { return kChunkT * ((k + 1) >> 1) + ((k & 1) ? -H : H); }
 constexpr uint16_t kPeakBit = 0x8000;                // plane word: a peak of step 2
 constexpr uint16_t kDropBit = 0x4000;                // plane word: dropped by step 2b
@@ -77,10 +83,16 @@ __device__ __forceinline__ void prefetch_l2_bytes(const void* p, unsigned long l
   }
 }
 
-constexpr int kDecStage = 4096;                      // bytes of a page body staged per warp
+// L2 prefetch of the bytes [p, p + n), widened to whole 16-byte blocks.
+__device__ __forceinline__ void prefetch_l2_range(const void* p, unsigned long long n) {
+  const uintptr_t a = reinterpret_cast<uintptr_t>(p) & ~(uintptr_t)15;
+  const uintptr_t b = (reinterpret_cast<uintptr_t>(p) + n + 15) & ~(uintptr_t)15;
+  prefetch_l2_bytes(reinterpret_cast<const void*>(a), (unsigned long long)(b - a));
+}
 
-__global__ void __launch_bounds__(kDecThreads, 5) k_decode_digits(DevGeom G, DevWork W, unsigned int n_windows,
-                                                                  int H) {
+constexpr int kDecStage = 4096;                      // bytes of a page's entries and runs staged per warp
+
+__global__ void __launch_bounds__(kDecThreads, 5) k_decode_runs(DevGeom G, DevWork W, unsigned int n_windows, int H) {
   __shared__ __align__(16) uint8_t stage_all[kDecThreads / 32][kDecStage];
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
@@ -100,40 +112,37 @@ __global__ void __launch_bounds__(kDecThreads, 5) k_decode_digits(DevGeom G, Dev
                            W.pages_bytes, h) &&
               h.sector == s && h.row == r && h.frag == f;
     unsigned long long base = 0;
-    if (ok && lane == 0) base = atomicAdd(&W.ctr[CTR_NDIG], (unsigned long long)h.n_dig);
+    if (ok && lane == 0) base = atomicAdd(&W.ctr[CTR_NRUN], (unsigned long long)h.n_runs);
     base = __shfl_sync(FULL, base, 0);
-    // a valid timeframe cannot exceed the array (each digit takes 10 bits of its page)
-    if (ok && base + (unsigned long long)h.n_dig > W.cap_dig) ok = false;
+    // a valid timeframe cannot exceed the array (each run takes more than 3 bytes of its page)
+    if (ok && base + (unsigned long long)h.n_runs > W.cap_runs) ok = false;
     bool bad = !ok;
     int r_cur = 0, d_cur = 0, t_last = -1;
-    int carry_t = -1;                     // time bin of the last run seen (boundary crossings)
-    // boundary counts (digits before time bin kBound[k]): n_dig unless a run at
-    // or past the bin is found, whose first digit index then is the count
-    uint16_t* btab = reinterpret_cast<uint16_t*>(W.dtab + 2ull * w + 1);
-    if (lane < 8) btab[lane] = (uint16_t)(ok ? h.n_dig : 0);
+    // boundary run indices: n_runs unless an entry at or past the bin is found,
+    // whose first run then is the index
+    uint16_t* btab = reinterpret_cast<uint16_t*>(W.dtab + 3ull * w + 1);
+    if (lane < 8) btab[lane] = (uint16_t)(ok ? h.n_runs : 0);
     __syncwarp();
     if (ok) {
       const uint8_t* pg = W.pages + o;
-      // the page body in one round trip: staged in the warp's shared memory
-      // (16-byte loads) when it fits, else prefetched into L2 so that its
-      // chunks are read from L2 rather than one DRAM round trip after another
+      // entries and runs in one round trip: staged in the warp's shared memory
+      // (16-byte loads, within the page) when they fit, else prefetched into L2
       const uint8_t* body = pg + 32;
-      const unsigned body_len = h.len - 32u;
-      if (body_len <= (unsigned)kDecStage) {
+      const unsigned meta_len = (h.body - 32u + 15u) & ~15u;
+      if (meta_len <= (unsigned)kDecStage) {
         const uint4* src = reinterpret_cast<const uint4*>(body);
         uint4* dst = reinterpret_cast<uint4*>(stage);
-        for (unsigned i = lane; i < body_len / 16u; i += 32u) dst[i] = __ldg(src + i);
+        for (unsigned i = lane; i < meta_len / 16u; i += 32u) dst[i] = __ldg(src + i);
         __syncwarp();
         body = stage;
       } else if (lane == 0) {
-        prefetch_l2_bytes(body, body_len);
+        prefetch_l2_bytes(body, meta_len);
       }
       const uint16_t* ent = reinterpret_cast<const uint16_t*>(body);
       const uint16_t* run = ent + h.n_tb;
-      const uint32_t* adc = reinterpret_cast<const uint32_t*>(body + (h.body - 32u));
-      uint32_t* out = W.digits + base;
+      uint2* out = W.runs + base;
       for (int E = 0; E < h.n_tb && !bad; E += 32) {
-        // ---- 32 entries: time bin, run count, first run
+        // ---- 32 entries: time bin, run count, first run; the units' boundaries
         const int e = E + lane, n_ent = min(32, h.n_tb - E);
         int t = 0, nr = 0;
         if (lane < n_ent) {
@@ -149,9 +158,17 @@ __global__ void __launch_bounds__(kDecThreads, 5) k_decode_digits(DevGeom G, Dev
         const int r_end = r_cur + __shfl_sync(FULL, incl, 31);
         t_last = __shfl_sync(FULL, t, n_ent - 1);
         bad = __any_sync(FULL, bad) || r_end > h.n_runs;
+        if (bad) break;
+        if (lane < n_ent) {
+#pragma unroll
+          for (int k = 0; k < 8; k++) {
+            const int bk = bound_of(k, H);
+            if (tp < bk && t >= bk) btab[k] = (uint16_t)rs;
+          }
+        }
         int carry_end = 0, carry_j = -1;
         for (int R = r_cur; R < r_end && !bad; R += 32) {
-          // ---- 32 runs: checks, their entry's time bin, digit offsets
+          // ---- 32 runs: their entry's time bin, checks, first digits, records
           const int ri = R + lane, n_run = min(32, r_end - R);
           int ps = 0, len = 0;
           if (lane < n_run) {
@@ -165,34 +182,15 @@ __global__ void __launch_bounds__(kDecThreads, 5) k_decode_digits(DevGeom G, Dev
           const int pend = __shfl_up_sync(FULL, end, 1), pj = __shfl_up_sync(FULL, j, 1);
           const int prev_end = lane == 0 ? carry_end : pend, prev_j = lane == 0 ? carry_j : pj;
           if (lane < n_run && (len < 1 || end > np || (prev_j == j && ps < prev_end))) bad = true;
-          const int tup_r = __shfl_up_sync(FULL, tr, 1);
-          const int t_prev_run = lane == 0 ? carry_t : tup_r;
           carry_end = __shfl_sync(FULL, end, 31);
           carry_j = __shfl_sync(FULL, j, 31);
-          carry_t = __shfl_sync(FULL, tr, 31);
           const int dinc = warp_incl_scan32(len);
-          const int drel = dinc - len;                       // first digit of run ri, within the chunk
           const int n_rd = __shfl_sync(FULL, dinc, 31);
           bad = __any_sync(FULL, bad) || d_cur + n_rd > h.n_dig;
           if (bad) break;
-          if (lane < n_run) {
-#pragma unroll
-            for (int k = 0; k < 8; k++)
-              if (t_prev_run < bound_of(k, H) && tr >= bound_of(k, H)) btab[k] = (uint16_t)(d_cur + drel);
-          }
-          // ---- the chunk's digits, 32 at a time: run by search, ADC from its word
-          for (int D = 0; D < n_rd; D += 32) {
-            const int dk = D + lane;
-            const int k = warp_search(drel, n_run, dk);
-            const int ps_k = __shfl_sync(FULL, ps, k), rel_k = __shfl_sync(FULL, drel, k);
-            const int t_k = __shfl_sync(FULL, tr, k);
-            if (dk < n_rd) {
-              const unsigned di = (unsigned)(d_cur + dk);
-              const uint32_t wv = adc[di / 3u];
-              const uint32_t q = (wv >> (10u * (di % 3u))) & kAdcMask;
-              out[di] = (uint32_t)(ps_k + dk - rel_k) | ((uint32_t)t_k << 8) | (q << 16);
-            }
-          }
+          if (lane < n_run)
+            out[ri] = make_uint2((uint32_t)ps | ((uint32_t)len << 8) | ((uint32_t)tr << 16),
+                                 (uint32_t)(d_cur + dinc - len));
           d_cur += n_rd;
         }
         r_cur = r_end;
@@ -202,86 +200,79 @@ __global__ void __launch_bounds__(kDecThreads, 5) k_decode_digits(DevGeom G, Dev
     __syncwarp();   // the stage is free again
     if (lane == 0) {
       if (bad) atomicOr(W.err, kErrCorrupt);
-      const uint32_t n = bad ? 0u : (uint32_t)h.n_dig;
-      W.dtab[2ull * w] = make_uint4((uint32_t)base, (uint32_t)(base >> 32), n, 0u);
-      if (bad) W.dtab[2ull * w + 1] = make_uint4(0u, 0u, 0u, 0u);
+      const uint32_t n = bad ? 0u : (uint32_t)h.n_runs;
+      const unsigned long long adc = ok ? o + h.body : 0ull;
+      W.dtab[3ull * w] = make_uint4((uint32_t)base, (uint32_t)(base >> 32), n, 0u);
+      if (bad) W.dtab[3ull * w + 1] = make_uint4(0u, 0u, 0u, 0u);
+      W.dtab[3ull * w + 2] = make_uint4((uint32_t)adc, (uint32_t)(adc >> 32), 0u, 0u);
     }
   }
 }
 
-// Digits of window w's table row before boundary k (k = -1: 0; k = 8: all).
-__device__ __forceinline__ uint32_t tab_count(const uint4& b, uint32_t n, int k) {
+// Run index of window table row b before boundary k (k = -1: 0; k = 8: all n).
+__device__ __forceinline__ uint32_t tab_run(const uint4& b, uint32_t n, int k) {
   if (k < 0) return 0u;
   if (k >= 8) return n;
   const uint32_t word = k < 2 ? b.x : (k < 4 ? b.y : (k < 6 ? b.z : b.w));
   return (k & 1) ? word >> 16 : word & 0xffffu;
 }
 
-// One unit's digit segments: the previous window's halo, the own chunk, the
-// next window's halo.
-struct UnitDesc {
-  unsigned long long seg_start[3];   // global digit index of each segment's first digit
-  int seg_n[3];                      // digits per segment
-  int frs, c;                        // window coordinates (f | r << 16 | s << 24), chunk
-};
-
-// The descriptor of unit u from the decode table (thread 0 only).
-__device__ __forceinline__ void unit_desc(const DevGeom& G, const DevWork& W, unsigned int u, UnitDesc& D) {
-  const unsigned int w = u / kUnitsPerWin;
-  const int c = (int)(u % kUnitsPerWin);
-  const int frs = window_frs(G, w);
-  const int f = frs & 0xffff;
-  const uint4 a = W.dtab[2ull * w], b = W.dtab[2ull * w + 1];
-  const unsigned long long db = a.x | ((unsigned long long)a.y << 32);
-  // own digits: time bins [64c - H, 64c + 64 + H) of the window
-  const uint32_t lo = tab_count(b, a.z, c == 0 ? -1 : 2 * c - 1);
-  const uint32_t hi = tab_count(b, a.z, c == kUnitsPerWin - 1 ? 8 : 2 * c + 2);
-  D.seg_start[1] = db + lo;
-  D.seg_n[1] = (int)(hi > lo ? hi - lo : 0u);
-  D.seg_n[0] = D.seg_n[2] = 0;
-  D.seg_start[0] = D.seg_start[2] = 0;
-  if (c == 0 && f > 0) {          // the previous window's time bins >= 256 - H
-    const uint4 ap = W.dtab[2ull * (w - 1)], bp = W.dtab[2ull * (w - 1) + 1];
-    const uint32_t l0 = tab_count(bp, ap.z, 7);
-    D.seg_start[0] = (ap.x | ((unsigned long long)ap.y << 32)) + l0;
-    D.seg_n[0] = (int)(ap.z > l0 ? ap.z - l0 : 0u);
-  }
-  if (c == kUnitsPerWin - 1 && f + 1 < G.n_frag) {   // the next window's time bins < H
-    const uint4 an = W.dtab[2ull * (w + 1)], bn = W.dtab[2ull * (w + 1) + 1];
-    D.seg_start[2] = an.x | ((unsigned long long)an.y << 32);
-    D.seg_n[2] = (int)tab_count(bn, an.z, 0);
-  }
-  D.frs = frs;
-  D.c = c;
-}
-
-// Unit descriptors, precomputed by k_unit_descs: three 16-byte words per
-// unit, (seg_start[0], seg_start[1]), (seg_start[2], seg_n[0], seg_n[1]),
-// (seg_n[2], frs, c, 0).
+// Unit descriptors, precomputed by k_unit_descs: per segment k (the previous
+// window's halo, the own window, the next window's halo) two 16-byte words
+//   (first run lo, hi, runs, index in the page of the first digit dA)
+//   (first ADC word lo, hi (index into the pages as 32-bit words), ADC words, digits)
+// then (frs, chunk, digits of all segments, ADC words of all segments).
 __global__ void k_unit_descs(DevGeom G, DevWork W, unsigned int n_units) {
   for (unsigned int u = blockIdx.x * blockDim.x + threadIdx.x; u < n_units; u += gridDim.x * blockDim.x) {
-    UnitDesc D;
-    unit_desc(G, W, u, D);
-    uint4* q = W.udesc + 3ull * u;
-    q[0] = make_uint4((uint32_t)D.seg_start[0], (uint32_t)(D.seg_start[0] >> 32), (uint32_t)D.seg_start[1],
-                      (uint32_t)(D.seg_start[1] >> 32));
-    q[1] = make_uint4((uint32_t)D.seg_start[2], (uint32_t)(D.seg_start[2] >> 32), (uint32_t)D.seg_n[0],
-                      (uint32_t)D.seg_n[1]);
-    q[2] = make_uint4((uint32_t)D.seg_n[2], (uint32_t)D.frs, (uint32_t)D.c, 0u);
+    const unsigned int w = u / kUnitsPerWin;
+    const int c = (int)(u % kUnitsPerWin);
+    const int frs = window_frs(G, w);
+    const int f = frs & 0xffff;
+    uint4* q = W.udesc + (unsigned long long)kDescWords * u;
+    uint32_t tot_d = 0, tot_w = 0;
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+      // segment 0: the previous window's time bins >= 256 - H; 1: own time bins
+      // [64c - H, 64c + 64 + H); 2: the next window's time bins < H
+      const bool have = k == 1 || (k == 0 && c == 0 && f > 0) || (k == 2 && c == kUnitsPerWin - 1 && f + 1 < G.n_frag);
+      uint32_t n = 0, dA = 0, nd = 0, nw = 0;
+      unsigned long long start = 0, aw = 0;
+      if (have) {
+        const unsigned long long ws = (unsigned long long)w + k - 1;
+        const uint4 a = W.dtab[3ull * ws], b = W.dtab[3ull * ws + 1], cc = W.dtab[3ull * ws + 2];
+        uint32_t lo, hi;
+        if (k == 0) { lo = tab_run(b, a.z, 7); hi = a.z; }
+        else if (k == 1) {
+          lo = tab_run(b, a.z, c == 0 ? -1 : 2 * c - 1);
+          hi = tab_run(b, a.z, c == kUnitsPerWin - 1 ? 8 : 2 * c + 2);
+        } else { lo = 0; hi = tab_run(b, a.z, 0); }
+        if (hi > lo) {
+          n = hi - lo;
+          start = (a.x | ((unsigned long long)a.y << 32)) + lo;
+          const uint2 r0 = W.runs[start], r1 = W.runs[start + n - 1];
+          dA = r0.y;
+          const uint32_t dB = r1.y + ((r1.x >> 8) & 255u);
+          nd = dB - dA;
+          nw = (dB - 1u) / 3u - dA / 3u + 1u;
+          aw = ((cc.x | ((unsigned long long)cc.y << 32)) >> 2) + dA / 3u;
+        }
+      }
+      q[2 * k] = make_uint4((uint32_t)start, (uint32_t)(start >> 32), n, dA);
+      q[2 * k + 1] = make_uint4((uint32_t)aw, (uint32_t)(aw >> 32), nw, nd);
+      tot_d += nd;
+      tot_w += nw;
+    }
+    q[6] = make_uint4((uint32_t)frs, (uint32_t)c, tot_d, tot_w);
   }
 }
-
-// Digits a thread keeps in registers between the plane build and step 2:
-// units with at most kReg * kThreads digits take the register path.
-constexpr int kReg = 8;
 
 template <int kThreads>
 struct UnitSmem {
-  uint4 dq[3][3];                    // descriptor ring: units u, u + G, u + 2G (G = gridDim.x)
+  uint4 dq[3][kDescWords];           // descriptor ring: units u, u + G, u + 2G (G = gridDim.x)
   unsigned long long sbase;          // the unit's span of the scratch buffer
   uint32_t total;                    // the unit's own peaks
-  uint32_t wtot[2][kThreads / 32];   // per-round warp counts of own peaks (double-buffered)
-  uint32_t wcnt[kReg * (kThreads / 32)];   // register path: own peaks per (round, warp), then their prefix
+  uint32_t wtot[2][kThreads / 32];   // dense path: per-round warp counts of own peaks (double-buffered)
+  uint32_t wcnt[(kDigCap / kThreads) * (kThreads / 32)];   // list path: own peaks per (round, warp)
 };
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
@@ -324,19 +315,6 @@ __device__ __forceinline__ bool ns_drop_plane(const uint16_t* pl, int L, int ps,
     }
   }
   return false;
-}
-
-// L2 prefetch of n digit words from p (widened to whole 16-byte blocks).
-__device__ __forceinline__ void prefetch_l2_span(const uint32_t* p, int n) {
-  const uintptr_t a = reinterpret_cast<uintptr_t>(p) & ~(uintptr_t)15;
-  const uintptr_t b = (reinterpret_cast<uintptr_t>(p + n) + 15) & ~(uintptr_t)15;
-  prefetch_l2_bytes(reinterpret_cast<const void*>(a), (unsigned long long)(b - a));
-}
-
-// Plane row offsets of the three segments: row = t_in + offset.
-template <int H>
-__device__ __forceinline__ int seg_row_offset(int k, int c) {
-  return k == 0 ? H - kFrag : (k == 1 ? H - kChunkT * c : H + kFrag - kChunkT * (kUnitsPerWin - 1));
 }
 
 // Step 3s weights of the 5x5 window of the own peak at plane index L (charges
@@ -387,33 +365,40 @@ __device__ __forceinline__ void split_weights(const uint16_t* pl, int L, int ps,
   }
 }
 
+// Plane row offsets of the three segments: row = t_in + offset.
+template <int H>
+__device__ __forceinline__ int seg_row_offset(int k, int c) {
+  return k == 0 ? H - kFrag : (k == 1 ? H - kChunkT * c : H + kFrag - kChunkT * (kUnitsPerWin - 1));
+}
+
 // Units are taken round-robin (unit blockIdx.x + k gridDim.x).  Their
-// descriptors come from k_unit_descs two units ahead: lanes 0-2 of warp 0
+// descriptors come from k_unit_descs two units ahead: lanes 0-6 of warp 0
 // copy unit u + 2G's into a ring slot (cp.async) while unit u runs, and thread
-// 0 prefetches unit u + G's digits into L2.  Per unit: the plane is built
-// from the digits (strided over the threads), step 2 runs strided too, the own
-// peaks are ranked in canonical order (digit order) by warp ballots and a
-// prefix over (round, warp), and their plane indices listed; the clusters are
-// then built strided over that list.  Units of at most kReg * kThreads digits
-// (the register path) keep each thread's digits as (plane index, row) words
-// in registers between the plane build and step 2, and rank all rounds with
-// one prefix; larger units re-read their digits and rank round by round.
+// 0 prefetches unit u + G's runs and ADC words into L2.  Per unit: the runs
+// are expanded into the plane and the digit list, step 2 runs over the list
+// (or over every pixel: dense path), the own peaks are ranked, and the
+// clusters built from the ranked list.  Shared memory after the plane: the
+// digit list and the list path's own peaks, or the dense path's own peaks.
 template <int kThreads, bool kNs, bool kSplit>
-__global__ void __launch_bounds__(kThreads, 1024 / kThreads)
+__global__ void __launch_bounds__(kThreads, 896 / kThreads)
     k_find_units(DevGeom G, DevParams P, DevWork W, unsigned int n_units) {
   constexpr int kH = unit_halo(kSplit);             // time halo of the plane
   constexpr int kURows = kChunkT + 2 * kH;          // plane rows
+  constexpr int kWarps = kThreads / 32;
+  static_assert(kDigCap / kThreads <= 32, "one own-peak mask bit per list round");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ UnitSmem<kThreads> U;
-  constexpr int kWarps = kThreads / 32;
   const unsigned FULL = 0xffffffffu;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int ps = G.npmax + 2 * kPad;                 // plane row stride in pads
-  uint16_t* plane = reinterpret_cast<uint16_t*>(smem_raw);
   const int plane_bytes = (kURows * ps * 2 + 15) & ~15;
   const int plane_words16 = plane_bytes / 16;
+  uint16_t* plane = reinterpret_cast<uint16_t*>(smem_raw);
   uint4* plane16 = reinterpret_cast<uint4*>(smem_raw);
-  uint16_t* plist = reinterpret_cast<uint16_t*>(smem_raw + plane_bytes);   // own peaks, canonical order
+  uint16_t* dl = reinterpret_cast<uint16_t*>(smem_raw + plane_bytes);   // the digits' plane indices
+  uint16_t* plist_l = dl + kDigCap;                                        // list path: own peaks, canonical order
+  uint16_t* plist_d = dl;                                                  // dense path: the same
+  const uint32_t* pages32 = reinterpret_cast<const uint32_t*>(W.pages);
   for (int i = tid; i < plane_words16; i += kThreads) plane16[i] = make_uint4(0u, 0u, 0u, 0u);
   if (blockIdx.x == 0 && tid == 0) W.ctr[CTR_NWIN] = n_units;
   const int T = G.n_time_bins;
@@ -423,7 +408,8 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads)
 #pragma unroll
     for (int k = 0; k < 2; k++) {
       const unsigned int uk = blockIdx.x + k * Gs;
-      if (lane < 3 && uk < n_units) cp_async16(&U.dq[k][lane], W.udesc + 3ull * uk + lane);
+      if (lane < kDescWords && uk < n_units)
+        cp_async16(&U.dq[k][lane], W.udesc + (unsigned long long)kDescWords * uk + lane);
       cp_async_commit();
     }
   }
@@ -432,190 +418,180 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads)
     if (wid == 0) {
       const unsigned int u2 = u + 2 * Gs;
       const int s2 = slot == 0 ? 2 : slot - 1;        // (slot + 2) % 3
-      if (lane < 3 && u2 < n_units) cp_async16(&U.dq[s2][lane], W.udesc + 3ull * u2 + lane);
+      if (lane < kDescWords && u2 < n_units)
+        cp_async16(&U.dq[s2][lane], W.udesc + (unsigned long long)kDescWords * u2 + lane);
       cp_async_commit();
       cp_async_wait1();                                // units u and u + G have landed
     }
     __syncthreads();
-    const uint4 q0 = U.dq[slot][0], q1 = U.dq[slot][1], q2 = U.dq[slot][2];
-    if (tid == 0 && u + Gs < n_units) {                // unit u + G's digits into L2 meanwhile
-      const int s1 = slot == 2 ? 0 : slot + 1;
-      const uint4 p0 = U.dq[s1][0], p1 = U.dq[s1][1], p2 = U.dq[s1][2];
-      const unsigned long long a0 = p0.x | ((unsigned long long)p0.y << 32);
-      const unsigned long long a1 = p0.z | ((unsigned long long)p0.w << 32);
-      const unsigned long long a2 = p1.x | ((unsigned long long)p1.y << 32);
-      if ((int)p1.z > 0) prefetch_l2_span(W.digits + a0, (int)p1.z);
-      if ((int)p1.w > 0) prefetch_l2_span(W.digits + a1, (int)p1.w);
-      if ((int)p2.x > 0) prefetch_l2_span(W.digits + a2, (int)p2.x);
-    }
-    slot = slot == 2 ? 0 : slot + 1;
-    const int n0 = (int)q1.z, n01 = n0 + (int)q1.w, n_all = n01 + (int)q2.x;
-    const int frs = (int)q2.y, c = (int)q2.z;
-    const unsigned long long st0 = q0.x | ((unsigned long long)q0.y << 32);
-    const unsigned long long st1 = (q0.z | ((unsigned long long)q0.w << 32)) - n0;
-    const unsigned long long st2 = (q1.x | ((unsigned long long)q1.y << 32)) - n01;
-    const int of0 = seg_row_offset<kH>(0, c), of1 = seg_row_offset<kH>(1, c), of2 = seg_row_offset<kH>(2, c);
-    // digit i of the unit -> (its word, its plane row offset)
-    auto digit = [&](int i, int& off) -> uint32_t {
-      const unsigned long long g = i < n0 ? st0 + i : (i < n01 ? st1 + i : st2 + i);
-      off = i < n0 ? of0 : (i < n01 ? of1 : of2);
-      return __ldg(W.digits + g);
-    };
-    uint32_t total;
-    if (n_all <= kReg * kThreads) {
-      // ---- register path: build the plane, keeping (L | row << 16) per digit
-      uint32_t pk[kReg];
+    // ---- the unit's segments
+    unsigned long long rstart[3], aw[3];
+    uint32_t nrun[3], dA[3];
 #pragma unroll
-      for (int k = 0; k < kReg; k++) {
-        pk[k] = FULL;
-        const int i = tid + k * kThreads;
-        if (i < n_all) {
-          int off;
-          const uint32_t d = digit(i, off);
-          const int row = (int)((d >> 8) & 255u) + off;
-          if (row >= 0 && row < kURows) {
-            const int L = row * ps + kPad + (int)(d & 255u);
-            plane[L] = (uint16_t)(d >> 16);
-            pk[k] = (uint32_t)L | ((uint32_t)row << 16);
-          }
+    for (int k = 0; k < 3; k++) {
+      const uint4 a = U.dq[slot][2 * k], b = U.dq[slot][2 * k + 1];
+      rstart[k] = a.x | ((unsigned long long)a.y << 32);
+      nrun[k] = a.z;
+      dA[k] = a.w;
+      aw[k] = b.x | ((unsigned long long)b.y << 32);
+    }
+    const uint4 q6 = U.dq[slot][6];
+    const int frs = (int)q6.x, c = (int)q6.y;
+    const uint32_t n_dig = q6.z;
+    const uint32_t doff1 = U.dq[slot][1].w, doff2 = doff1 + U.dq[slot][3].w;   // list offsets of segments 1, 2
+    const uint32_t roff1 = nrun[0], roff2 = nrun[0] + nrun[1], n_runs = roff2 + nrun[2];
+    if (tid == 0 && u + Gs < n_units) {                // unit u + G's runs and ADC words into L2 meanwhile
+      const int s1 = slot == 2 ? 0 : slot + 1;
+#pragma unroll
+      for (int k = 0; k < 3; k++) {
+        const uint4 a = U.dq[s1][2 * k], b = U.dq[s1][2 * k + 1];
+        if (a.z) {
+          prefetch_l2_range(W.runs + (a.x | ((unsigned long long)a.y << 32)), 8ull * a.z);
+          prefetch_l2_range(pages32 + (b.x | ((unsigned long long)b.y << 32)), 4ull * b.z);
         }
       }
-      __syncthreads();
-      // ---- step 2 (rows 1..68): peaks marked, own ones flagged per round
+    }
+    slot = slot == 2 ? 0 : slot + 1;
+    const bool list = n_dig <= (uint32_t)kDigCap;     // block-uniform
+    // ---- build: one thread per run; its digits go into the plane (and the list)
+    for (uint32_t i = tid; i < n_runs; i += kThreads) {
+      const int k = i < roff1 ? 0 : (i < roff2 ? 1 : 2);
+      const uint32_t ri = i - (k == 0 ? 0u : (k == 1 ? roff1 : roff2));
+      const uint2 rec = __ldg(W.runs + (k == 0 ? rstart[0] : (k == 1 ? rstart[1] : rstart[2])) + ri);
+      const int p0 = (int)(rec.x & 255u), len = (int)((rec.x >> 8) & 255u);
+      const int row = (int)((rec.x >> 16) & 255u) + seg_row_offset<kH>(k, c);
+      if (row < 0 || row >= kURows) continue;          // cannot happen for a decoded page
+      const int L0 = row * ps + kPad + p0;
+      const uint32_t d0 = rec.y;
+      const uint32_t dk = k == 0 ? dA[0] : (k == 1 ? dA[1] : dA[2]);
+      uint32_t sub = d0 % 3u;
+      const uint32_t* src = pages32 + (k == 0 ? aw[0] : (k == 1 ? aw[1] : aw[2])) + (d0 / 3u - dk / 3u);
+      uint32_t word = __ldg(src);
+      if (list) {
+        uint16_t* dst = dl + (k == 0 ? 0u : (k == 1 ? doff1 : doff2)) + (d0 - dk);
+        for (int j = 0; j < len; j++) {
+          if (j > 0 && sub == 0) word = __ldg(++src);
+          plane[L0 + j] = (uint16_t)((word >> (10u * sub)) & kAdcMask);
+          dst[j] = (uint16_t)(L0 + j);
+          sub = sub == 2u ? 0u : sub + 1u;
+        }
+      } else {
+        for (int j = 0; j < len; j++) {
+          if (j > 0 && sub == 0) word = __ldg(++src);
+          plane[L0 + j] = (uint16_t)((word >> (10u * sub)) & kAdcMask);
+          sub = sub == 2u ? 0u : sub + 1u;
+        }
+      }
+    }
+    __syncthreads();   // plane and digit list complete
+    const int qmin = P.q_peak_min;
+    const int test_lo = ps, test_hi = (kURows - 1) * ps;          // rows 1 .. kURows - 2
+    const int own_lo = kH * ps, own_hi = (kH + kChunkT) * ps;     // own rows
+    uint32_t total;
+    if (list) {
+      // ---- step 2 over the digit list: peaks marked, own ones flagged per round
+      const int nr = (int)((n_dig + kThreads - 1) / kThreads);
       uint32_t own = 0;
-#pragma unroll
-      for (int k = 0; k < kReg; k++) {
-        if (pk[k] == FULL) continue;
-        const int L = (int)(pk[k] & 0xffffu), row = (int)(pk[k] >> 16);
-        if (row >= 1 && row <= kURows - 2) {
-          const int q = plane[L];
-          if (q >= P.q_peak_min && peak_test(plane, L, ps, q, P.q_peak_min)) {
-            plane[L] = (uint16_t)(q | kPeakBit);       // only this thread writes this pixel
-            if (row >= kH && row < kH + kChunkT) own |= 1u << k;
+      for (int k = 0; k < nr; k++) {
+        const uint32_t i = tid + (uint32_t)k * kThreads;
+        if (i < n_dig) {
+          const int L = dl[i];
+          if (L >= test_lo && L < test_hi) {
+            const int q = plane[L];                     // only this thread marks this pixel
+            if (q >= qmin && peak_test(plane, L, ps, q, qmin)) {
+              plane[L] = (uint16_t)(q | kPeakBit);
+              if (L >= own_lo && L < own_hi) own |= 1u << k;
+            }
           }
         }
       }
       if (kNs) {
         __syncthreads();   // every step-2 peak marked: step 2b reads the ring
-#pragma unroll
-        for (int k = 0; k < kReg; k++) {
+        for (int k = 0; k < nr; k++) {
           if (!((own >> k) & 1u)) continue;
-          const int L = (int)(pk[k] & 0xffffu);
+          const int L = dl[tid + (uint32_t)k * kThreads];
           if (ns_drop_plane(plane, L, ps, P.ns_min_dip)) {
             plane[L] = (uint16_t)(plane[L] | kDropBit);
             own &= ~(1u << k);
           }
         }
       }
-      // ---- rank: own peaks per (round, warp), one prefix over them in order
-#pragma unroll
-      for (int k = 0; k < kReg; k++) {
+      // ---- rank: own peaks per (round, warp); every warp scans the counts
+      // itself (at most 64) and places its own peaks
+      for (int k = 0; k < nr; k++) {
         const unsigned m = __ballot_sync(FULL, (own >> k) & 1u);
         if (lane == 0) U.wcnt[k * kWarps + wid] = (uint32_t)__popc(m);
       }
       __syncthreads();
-      if (wid == 0) {
-        uint32_t carry = 0;
-#pragma unroll
-        for (int j0 = 0; j0 < kReg * kWarps; j0 += 32) {
-          const uint32_t v = U.wcnt[j0 + lane];
-          const uint32_t inc = (uint32_t)warp_incl_scan32((int)v);
-          U.wcnt[j0 + lane] = carry + inc - v;
-          carry += __shfl_sync(FULL, inc, 31);
+      uint32_t carry = 0;
+      for (int j0 = 0; j0 < nr * kWarps; j0 += 32) {
+        const bool in = j0 + lane < nr * kWarps;
+        const uint32_t v = in ? U.wcnt[j0 + lane] : 0u;
+        const uint32_t inc = (uint32_t)warp_incl_scan32((int)v);
+        const uint32_t excl = carry + inc - v;           // own peaks before (round, warp) j0 + lane
+        // this warp's rounds k with k * kWarps + wid in [j0, j0 + 32)
+        for (int k = (j0 + kWarps - 1 - wid) / kWarps; k < nr && k * kWarps + wid < j0 + 32; k++) {
+          const uint32_t before = __shfl_sync(FULL, excl, k * kWarps + wid - j0);
+          const unsigned m = __ballot_sync(FULL, (own >> k) & 1u);
+          if ((own >> k) & 1u)
+            plist_l[before + (uint32_t)__popc(m & ((1u << lane) - 1u))] = dl[tid + (uint32_t)k * kThreads];
         }
-        if (lane == 0) {
-          const unsigned long long sb = carry ? atomicAdd(&W.ctr[CTR_SCURSOR], (unsigned long long)carry) : 0ull;
-          if (sb + carry > W.cap_cl) atomicOr(W.err, kErrOverflowCl);
-          U.sbase = sb;
-          U.total = carry;
-          W.win_cnt[u] = carry;
-          W.win_soff[u] = (uint32_t)min(sb, (unsigned long long)0xffffffffu);
-        }
+        carry += __shfl_sync(FULL, inc, 31);
       }
-      __syncthreads();
-#pragma unroll
-      for (int k = 0; k < kReg; k++) {
-        const unsigned m = __ballot_sync(FULL, (own >> k) & 1u);
-        if ((own >> k) & 1u)
-          plist[U.wcnt[k * kWarps + wid] + (uint32_t)__popc(m & ((1u << lane) - 1u))] = (uint16_t)(pk[k] & 0xffffu);
+      total = carry;
+      if (tid == 0) {
+        const unsigned long long sb = total ? atomicAdd(&W.ctr[CTR_SCURSOR], (unsigned long long)total) : 0ull;
+        if (sb + total > W.cap_cl) atomicOr(W.err, kErrOverflowCl);
+        U.sbase = sb;
+        W.win_cnt[u] = total;
+        W.win_soff[u] = (uint32_t)min(sb, (unsigned long long)0xffffffffu);
       }
-      total = U.total;
     } else {
-      // ---- build the plane
-      for (int i = tid; i < n_all; i += kThreads) {
-        int off;
-        const uint32_t d = digit(i, off);
-        const int row = (int)((d >> 8) & 255u) + off;
-        if (row >= 0 && row < kURows) plane[row * ps + kPad + (int)(d & 255u)] = (uint16_t)(d >> 16);
+      // ---- dense path: step 2 on every pixel of rows 1 .. kURows - 2
+      const int np = G.npads[(frs >> 16) & 0xff];
+      const int n_test = (kURows - 2) * np;
+      for (int i = tid; i < n_test; i += kThreads) {
+        const int row = 1 + i / np, p = i - (row - 1) * np;
+        const int L = row * ps + kPad + p;
+        const int q = plane[L];
+        if (q >= qmin && peak_test(plane, L, ps, q, qmin)) plane[L] = (uint16_t)(q | kPeakBit);
       }
-      __syncthreads();
-      // ---- step 2 (rows 1..68), peaks marked; without step 2b the own ones are ranked at once
+      __syncthreads();   // every step-2 peak marked
+      const int n_own = kChunkT * np;
+      if (kNs) {
+        for (int i = tid; i < n_own; i += kThreads) {
+          const int row = kH + i / np, p = i - (row - kH) * np;
+          const int L = row * ps + kPad + p;
+          const uint16_t v = plane[L];
+          if ((v & kPeakBit) && ns_drop_plane(plane, L, ps, P.ns_min_dip)) plane[L] = (uint16_t)(v | kDropBit);
+        }
+        __syncthreads();
+      }
+      // ---- rank the own peaks round by round (pixels in canonical order)
       uint32_t running = 0;                             // own peaks listed so far (block-uniform)
       int parity = 0;
-      for (int base = 0; base < n_all; base += kThreads) {
+      for (int base = 0; base < n_own; base += kThreads) {
         const int i = base + tid;
-        bool own = false;
+        bool own_pk = false;
         int L = 0;
-        if (i < n_all) {
-          int off;
-          const uint32_t d = digit(i, off);
-          const int row = (int)((d >> 8) & 255u) + off;
-          if (row >= 1 && row <= kURows - 2) {
-            L = row * ps + kPad + (int)(d & 255u);
-            const int q = plane[L];
-            if (q >= P.q_peak_min && peak_test(plane, L, ps, q, P.q_peak_min)) {
-              plane[L] = (uint16_t)(q | kPeakBit);     // only this thread writes this pixel
-              own = !kNs && row >= kH && row < kH + kChunkT;
-            }
-          }
+        if (i < n_own) {
+          const int row = kH + i / np, p = i - (row - kH) * np;
+          L = row * ps + kPad + p;
+          const uint16_t v = plane[L];
+          own_pk = (v & kPeakBit) && !(v & kDropBit);
         }
-        if (!kNs) {
-          const unsigned m = __ballot_sync(FULL, own);
-          if (lane == 0) U.wtot[parity][wid] = (uint32_t)__popc(m);
-          __syncthreads();
-          uint32_t before = running;
+        const unsigned m = __ballot_sync(FULL, own_pk);
+        if (lane == 0) U.wtot[parity][wid] = (uint32_t)__popc(m);
+        __syncthreads();
+        uint32_t before = running;
 #pragma unroll
-          for (int k = 0; k < kWarps; k++) {
-            const uint32_t v = U.wtot[parity][k];
-            before += k < wid ? v : 0u;
-            running += v;
-          }
-          if (own) plist[before + (uint32_t)__popc(m & ((1u << lane) - 1u))] = (uint16_t)L;
-          parity ^= 1;
+        for (int k = 0; k < kWarps; k++) {
+          const uint32_t v = U.wtot[parity][k];
+          before += k < wid ? v : 0u;
+          running += v;
         }
-      }
-      if (kNs) {
-        __syncthreads();   // every step-2 peak marked: step 2b reads the ring
-        for (int base = 0; base < n_all; base += kThreads) {
-          const int i = base + tid;
-          bool own = false;
-          int L = 0;
-          if (i < n_all) {
-            int off;
-            const uint32_t d = digit(i, off);
-            const int row = (int)((d >> 8) & 255u) + off;
-            if (row >= kH && row < kH + kChunkT) {
-              L = row * ps + kPad + (int)(d & 255u);
-              const uint16_t v = plane[L];
-              if (v & kPeakBit) {
-                if (ns_drop_plane(plane, L, ps, P.ns_min_dip)) plane[L] = (uint16_t)(v | kDropBit);
-                else own = true;
-              }
-            }
-          }
-          const unsigned m = __ballot_sync(FULL, own);
-          if (lane == 0) U.wtot[parity][wid] = (uint32_t)__popc(m);
-          __syncthreads();
-          uint32_t before = running;
-#pragma unroll
-          for (int k = 0; k < kWarps; k++) {
-            const uint32_t v = U.wtot[parity][k];
-            before += k < wid ? v : 0u;
-            running += v;
-          }
-          if (own) plist[before + (uint32_t)__popc(m & ((1u << lane) - 1u))] = (uint16_t)L;
-          parity ^= 1;
-        }
+        if (own_pk) plist_d[before + (uint32_t)__popc(m & ((1u << lane) - 1u))] = (uint16_t)L;
+        parity ^= 1;
       }
       total = running;
       if (tid == 0) {
@@ -629,6 +605,7 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads)
     __syncthreads();   // list complete, every peak marked, span reserved
     // ---- clusters of the own peaks, strided over the list (canonical order)
     if (total) {
+      const uint16_t* plist = list ? plist_l : plist_d;
       const unsigned long long sb = U.sbase;
       const int f = frs & 0xffff, r = (frs >> 16) & 0xff, s = (frs >> 24) & 0xff;
       const int np = G.npads[r], xrow = G.xrow[r];
@@ -665,11 +642,14 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads)
   if (wid == 0) asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
-// Dynamic shared memory of k_find_units: the plane, then the list of a unit's
-// own peaks (at most one per pair of pads of each of its 64 rows).
+// Dynamic shared memory of k_find_units: the plane, then either the digit
+// list and the own peaks of the list path (kDigCap entries each), or the own
+// peaks of the dense path (at most one per pair of pads of each of 64 rows).
 size_t find2_smem_bytes(int npmax, bool split) {
-  return (((size_t)(kChunkT + 2 * unit_halo(split)) * (npmax + 2 * kPad) * 2 + 15) & ~(size_t)15) +
-         (size_t)kChunkT * ((npmax + 1) / 2) * 2;
+  const size_t plane = ((size_t)(kChunkT + 2 * unit_halo(split)) * (npmax + 2 * kPad) * 2 + 15) & ~(size_t)15;
+  const size_t dense_peaks = (size_t)kChunkT * ((npmax + 1) / 2) * 2;
+  const size_t r = std::max(dense_peaks, (size_t)kDigCap * 2 * 2);
+  return plane + ((r + 15) & ~(size_t)15);
 }
 
 template <int kThreads, bool kNs, bool kSplit>
@@ -706,8 +686,8 @@ cudaError_t launch_find2(const DevGeom& G, const DevParams& P, const DevWork& W,
                          const LaunchCfg& L, cudaStream_t st, unsigned long long* unit_scan_state, int* launches) {
   const unsigned gd = (unsigned)std::min<unsigned long long>((n_windows + 7ull) / 8ull, (unsigned long long)n_sm * 8);
   const bool split = P.split_charge != 0;
-  k_decode_digits<<<gd ? gd : 1, kDecThreads, 0, st>>>(G, W, n_windows, unit_halo(split));
-  const unsigned int n_units = n_windows * kUnitsPerWin;
+  k_decode_runs<<<gd ? gd : 1, kDecThreads, 0, st>>>(G, W, n_windows, unit_halo(split));
+  unsigned int n_units = n_windows * kUnitsPerWin;
   {
     const unsigned gdesc = (unsigned)std::min<unsigned long long>((n_units + 255ull) / 256ull, (unsigned long long)n_sm * 8);
     k_unit_descs<<<gdesc ? gdesc : 1, 256, 0, st>>>(G, W, n_units);
@@ -723,15 +703,12 @@ cudaError_t launch_find2(const DevGeom& G, const DevParams& P, const DevWork& W,
   const unsigned gu = (unsigned)std::max<unsigned long long>(
       1ull, std::min<unsigned long long>(n_units, (unsigned long long)n_sm * per_sm));
   {
-    unsigned int nu = n_units;
-    void* args[] = {const_cast<DevGeom*>(&G), const_cast<DevParams*>(&P), const_cast<DevWork*>(&W), &nu};
+    void* args[] = {const_cast<DevGeom*>(&G), const_cast<DevParams*>(&P), const_cast<DevWork*>(&W), &n_units};
     cudaError_t le = cudaLaunchKernel(fn, dim3(gu), dim3(nt), args, sm, st);
     if (le != cudaSuccess) return le;
   }
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  e = launch_scan(reinterpret_cast<uint64_t*>(W.win_cnt), W.ctr + CTR_NWIN, n_units, unit_scan_state,
-                  W.tickets + TK_SCAN_W, W.ctr + CTR_NCL, W.err, n_sm, st);
+  cudaError_t e = launch_scan(reinterpret_cast<uint64_t*>(W.win_cnt), W.ctr + CTR_NWIN, n_units, unit_scan_state,
+                              W.tickets + TK_SCAN_W, W.ctr + CTR_NCL, W.err, n_sm, st);
   if (e != cudaSuccess) return e;
   e = launch_compact(G, W, n_units, kUnitsPerWin, n_sm, st);
   *launches += 5;

@@ -73,7 +73,7 @@ struct Slot {
   // device buffers
   Buf pages, offsets, winstate, cl, clx, cly, clz, clt, rowstart, chrow, up, down, score, edge, jump, chlen, scanv,
       scanst, chainof, clchain, ch_i32, besta, bestb, trk_i32, trackcl, cl2trk, tracks, ctrl, scratch, wincnt, winsoff,
-      candab, candsc, lenhist, evinfo, xs, lp, cmp, cal, dense, digits, dtab;
+      candab, candsc, lenhist, evinfo, xs, lp, cmp, cal, dense, runrec, dtab;
   unsigned long long* h_ctrl = nullptr;   // pinned copy of [ctr | err]
   // batch tables, device (evinfo) and pinned host copy, same layout:
   // u64 base[kMaxBatch], u64 bytes[kMaxBatch], u32 cl_start[kMaxBatch + 1],
@@ -92,7 +92,7 @@ struct Slot {
   bool cmp_done = false;
   size_t cmp_bytes = 0, cal_bytes = 0;
   // capacities
-  uint64_t cap_pages = 0, cap_windows = 0, cap_cl = 0, cap_ch = 0, cap_dig = 0;
+  uint64_t cap_pages = 0, cap_windows = 0, cap_cl = 0, cap_ch = 0, cap_runs = 0;
   // ticket
   bool in_use = false;
   uint64_t ticket = 0;
@@ -235,15 +235,15 @@ static bool two_pass(const tpc_context* ctx) {
 // Units of the two-pass finder per window (its scan and span arrays are sized for them).
 constexpr uint64_t kUnitsPerWindow = 4;
 
-// Digits the two-pass finder's array must hold for pages_bytes of pages: each
-// digit takes 10 of the 32 bits of an ADC word inside its page.
-static uint64_t digit_cap(uint64_t pages_bytes) { return pages_bytes / 4 * 3 + 3; }
+// Pad runs the two-pass finder's array must hold for pages_bytes of pages: a
+// run takes 2 bytes of its page and at least one digit, 10 bits of an ADC word.
+static uint64_t run_cap(uint64_t pages_bytes) { return pages_bytes / 3 + 3; }
 
 static size_t slot_bytes(uint64_t pages, uint64_t windows, uint64_t cap_cl, uint64_t cap_ch, int nsr,
-                         size_t dense = 0, uint64_t cap_dig = 0) {
-  size_t b = dense + pages + 16 + windows * (8 + 8 + 8 * kUnitsPerWindow + 4 * (kUnitsPerWindow + 2) + 32 +
-                                             48 * kUnitsPerWindow) +
-             cap_dig * 4 + cap_cl * (16 + 16 + 16 + 8 + 8 + 8 + 8 + 4 + 8 + 4 + 4 + 4 + 4) +
+                         size_t dense = 0, uint64_t cap_runs = 0) {
+  size_t b = dense + pages + 16 + windows * (8 + 8 + 8 * kUnitsPerWindow + 4 * (kUnitsPerWindow + 2) + 48 +
+                                             112 * kUnitsPerWindow) +
+             cap_runs * 8 + cap_cl * (16 + 16 + 16 + 8 + 8 + 8 + 8 + 4 + 8 + 4 + 4 + 4 + 4) +
              (scan_tiles(cap_cl) + scan_tiles(cap_ch) + scan_tiles(windows * kUnitsPerWindow)) * 8 +
              cap_ch * (14 * 4 + 8 + 16 + sizeof(tpc_track) + 4 * 12) +
              (size_t)(nsr + 1) * 8 + 1024;
@@ -258,11 +258,11 @@ static tpc_status slot_reserve(tpc_context* ctx, Slot& s, uint64_t pages_bytes, 
   // dense-plane finder variant: one ADC per (sector row, time bin, pad)
   const size_t dstride = (size_t)((ctx->geom.npmax + 7) & ~7);
   const size_t want_dense = (ctx->flags & TPC_CTX_DENSE_FINDER) ? (size_t)windows * kFrag * dstride * 2 : 0;
-  const uint64_t want_dig = two_pass(ctx) ? digit_cap(pages_bytes) : 0;
-  size_t cur = slot_bytes(s.cap_pages, s.cap_windows, s.cap_cl, s.cap_ch, nsr, s.dense.bytes, s.cap_dig);
+  const uint64_t want_runs = two_pass(ctx) ? run_cap(pages_bytes) : 0;
+  size_t cur = slot_bytes(s.cap_pages, s.cap_windows, s.cap_cl, s.cap_ch, nsr, s.dense.bytes, s.cap_runs);
   size_t need = slot_bytes(std::max(s.cap_pages, want_pages), std::max(s.cap_windows, windows),
                            std::max(s.cap_cl, cap_cl), std::max(s.cap_ch, cap_ch), nsr,
-                           std::max(s.dense.bytes, want_dense), std::max(s.cap_dig, want_dig));
+                           std::max(s.dense.bytes, want_dense), std::max(s.cap_runs, want_runs));
   if (ctx->used - cur + need > ctx->budget)
     return fail(TPC_E_NOMEM, "timeframe needs " + std::to_string(need) + " device bytes; budget left " +
                                  std::to_string(ctx->budget - ctx->used + cur));
@@ -273,13 +273,13 @@ static tpc_status slot_reserve(tpc_context* ctx, Slot& s, uint64_t pages_bytes, 
     CUDA_TRY(ensure(s.wincnt, windows * kUnitsPerWindow * 8));
     // span starts (one per unit) | light list | heavy list
     CUDA_TRY(ensure(s.winsoff, windows * (kUnitsPerWindow + 2) * 4));
-    // window table rows (2 x 16 bytes), then the units' descriptors (3 x 16 bytes each)
-    CUDA_TRY(ensure(s.dtab, windows * (32 + 48 * kUnitsPerWindow)));
+    // window table rows (3 x 16 bytes), then the units' descriptors (7 x 16 bytes each)
+    CUDA_TRY(ensure(s.dtab, windows * (48 + 112 * kUnitsPerWindow)));
     s.cap_windows = windows;
   }
-  if (want_dig > s.cap_dig) {
-    CUDA_TRY(ensure(s.digits, want_dig * 4));
-    s.cap_dig = want_dig;
+  if (want_runs > s.cap_runs) {
+    CUDA_TRY(ensure(s.runrec, want_runs * 8));
+    s.cap_runs = want_runs;
   }
   if (cap_cl > s.cap_cl) {
     CUDA_TRY(ensure(s.cl, cap_cl * 16));
@@ -311,7 +311,7 @@ static tpc_status slot_reserve(tpc_context* ctx, Slot& s, uint64_t pages_bytes, 
   CUDA_TRY(ensure(s.ctrl, 256));
   CUDA_TRY(ensure(s.lenhist, 512 * 4));
   ctx->used = ctx->used - cur + slot_bytes(s.cap_pages, s.cap_windows, s.cap_cl, s.cap_ch, nsr, s.dense.bytes,
-                                           s.cap_dig);
+                                           s.cap_runs);
   // wire the work-space pointers
   DevWork& W = s.W;
   W.clusters = (tpc_cluster*)s.cl.p;
@@ -326,10 +326,10 @@ static tpc_status slot_reserve(tpc_context* ctx, Slot& s, uint64_t pages_bytes, 
   W.win_soff = (uint32_t*)s.winsoff.p;
   W.light_list = (uint32_t*)s.winsoff.p + kUnitsPerWindow * s.cap_windows;
   W.heavy_list = (uint32_t*)s.winsoff.p + (kUnitsPerWindow + 1) * s.cap_windows;
-  W.digits = (uint32_t*)s.digits.p;
+  W.runs = (uint2*)s.runrec.p;
   W.dtab = (uint4*)s.dtab.p;
-  W.udesc = (uint4*)s.dtab.p + 2 * s.cap_windows;
-  W.cap_dig = s.cap_dig;
+  W.udesc = (uint4*)s.dtab.p + 3 * s.cap_windows;
+  W.cap_runs = s.cap_runs;
   W.up = (int32_t*)s.up.p; W.down = (int32_t*)s.down.p;
   W.score = (int64_t*)s.score.p;
   W.edge_key = (unsigned long long*)s.edge.p;
@@ -369,7 +369,7 @@ static void slot_free(tpc_context* ctx, Slot& s) {
                 &s.down, &s.score, &s.edge, &s.jump, &s.chlen, &s.scanv, &s.scanst, &s.chainof, &s.clchain,
                 &s.ch_i32, &s.besta, &s.bestb, &s.trk_i32, &s.trackcl, &s.cl2trk, &s.tracks, &s.ctrl,
                 &s.scratch, &s.wincnt, &s.winsoff, &s.candab, &s.candsc, &s.lenhist, &s.evinfo, &s.xs, &s.lp, &s.cmp, &s.cal, &s.dense,
-                &s.digits, &s.dtab};
+                &s.runrec, &s.dtab};
   for (Buf* b : all) free_buf(*b);
   for (auto& e : s.ev_stage) if (e) cudaEventDestroy(e);
   if (s.ev_done) cudaEventDestroy(s.ev_done);
@@ -748,16 +748,16 @@ static void reclaim_idle(tpc_context* ctx, const Slot* keep) {
     if (c.in_use || &c == keep || !c.cap_pages && !c.cap_cl) continue;
     cudaStreamSynchronize(c.stream);
     ctx->used -= slot_bytes(c.cap_pages, c.cap_windows, c.cap_cl, c.cap_ch, nsr1 * (int)c.n_events, c.dense.bytes,
-                            c.cap_dig);
+                            c.cap_runs);
     Buf* big[] = {&c.pages, &c.offsets, &c.winstate, &c.cl, &c.clx, &c.cly, &c.clz, &c.clt, &c.up, &c.down,
                   &c.score, &c.edge, &c.jump, &c.chlen, &c.scanv, &c.scanst, &c.chainof, &c.clchain, &c.ch_i32,
                   &c.besta, &c.bestb, &c.trk_i32, &c.trackcl, &c.cl2trk, &c.tracks, &c.scratch, &c.wincnt,
-                  &c.winsoff, &c.candab, &c.candsc, &c.xs, &c.lp, &c.cmp, &c.cal, &c.dense, &c.digits, &c.dtab};
+                  &c.winsoff, &c.candab, &c.candsc, &c.xs, &c.lp, &c.cmp, &c.cal, &c.dense, &c.runrec, &c.dtab};
     for (Buf* b : big) free_buf(*b);
     ctx->used -= c.xs_bytes + c.lp_bytes + c.cmp_bytes + c.cal_bytes;
     c.xs_bytes = c.lp_bytes = c.cmp_bytes = c.cal_bytes = 0;
     c.xs_done = c.lp_done = c.cmp_done = false;
-    c.cap_pages = c.cap_windows = c.cap_cl = c.cap_ch = c.cap_dig = 0;
+    c.cap_pages = c.cap_windows = c.cap_cl = c.cap_ch = c.cap_runs = 0;
   }
 }
 

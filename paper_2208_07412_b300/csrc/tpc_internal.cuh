@@ -100,11 +100,12 @@ struct DevWork {
   uint32_t* win_soff;            // start of each window's span in scratch_cl
   uint32_t* light_list;          // [n_windows] windows of the light path (first CTR_NLIGHT), or null
   uint32_t* heavy_list;          // [n_windows] the other windows (first CTR_NHEAVY)
-  uint32_t* digits;              // two-pass finder: every digit as pad | t_in << 8 | adc << 16, per page spans
-  uint4* dtab;                   // [2 * n_windows] per window: (span start lo, hi, digits, 0) and the digit
-                                 // counts before time bins 3, 61, 67, 125, 131, 189, 195, 253 (u16 pairs)
-  uint64_t cap_dig;              // digits the array holds
-  uint4* udesc;                  // [3 * units] two-pass finder: unit descriptors (k_unit_descs)
+  uint2* runs;                   // two-pass finder: every pad run as (pad | len << 8 | t_in << 16, index of its
+                                 // first digit in the page), one span per page
+  uint4* dtab;                   // [3 * n_windows] per window: (run span start lo, hi, runs, 0), the run
+                                 // indices at the units' time boundaries (8 x u16), (ADC byte offset lo, hi, 0, 0)
+  uint64_t cap_runs;             // runs the array holds
+  uint4* udesc;                  // [7 * units] two-pass finder: unit descriptors (k_unit_descs)
   // CA
   int32_t* up; int32_t* down;
   int64_t* score;
@@ -155,7 +156,7 @@ enum {
   CTR_NCAND = 23,     // merge candidate pairs found
   CTR_NLIGHT = 24,    // windows the light finder path takes
   CTR_NHEAVY = 25,    // windows the block-per-window finder takes
-  CTR_NDIG = 26,      // digits decoded by the two-pass finder (span cursor)
+  CTR_NRUN = 26,      // pad runs decoded by the two-pass finder (span cursor)
   CTR_COUNT = 27
 };
 enum { TK_FIND = 0, TK_SCAN_A = 1, TK_SCAN_B = 2, TK_SCAN_W = 3, TK_FIND2 = 4, TK_LIGHT = 5, TK_UNIT = 6, TK_DEC = 7,
