@@ -27,8 +27,9 @@
 // 15 of the word: what the 5x5 of a cluster reads as "another peak", step 2b as
 // the step-2 peak set and step 3s as the owners) and keeps a per-thread bit
 // mask of its own peaks, which warp ballots and one prefix rank in canonical
-// order.  Units with more digits than the list holds test every pixel of the
-// plane instead.  Clusters are built over the ranked list; each unit reserves
+// order.  Units with more digits than the list holds (4096) test every pixel
+// of the plane instead, and they and units with more own peaks than their list
+// holds (1024) rank the own peaks in pixel order.  Clusters are built over the ranked list; each unit reserves
 // a span of the scratch buffer with one atomic, and the unit-count scan and
 // the compaction of k_find.cu place the spans canonically.
 #include "find_common.cuh"
@@ -38,7 +39,8 @@ namespace tpc {
 constexpr int kChunkT = 64;                          // own time bins of a unit
 constexpr int kUnitsPerWin = kFrag / kChunkT;        // 4
 constexpr int kDecThreads = 256;                     // decode block (8 warps, one page each)
-constexpr int kDigCap = 2048;                        // digits a unit lists for the digit-driven step 2
+constexpr int kDigCap = 4096;                        // digits a unit lists for the digit-driven step 2
+constexpr int kPlistCap = 1024;                      // own peaks the list path ranks (else pixel-order ranking)
 constexpr int kDescWords = 7;                        // 16-byte words of a unit descriptor
 // Time halo of a unit's plane: 3 bins (the 3x3 test of a pixel 2 bins away),
 // 5 with step 3s (the peaks up to 4 bins away).
@@ -271,9 +273,46 @@ struct UnitSmem {
   uint4 dq[3][kDescWords];           // descriptor ring: units u, u + G, u + 2G (G = gridDim.x)
   unsigned long long sbase;          // the unit's span of the scratch buffer
   uint32_t total;                    // the unit's own peaks
-  uint32_t wtot[2][kThreads / 32];   // dense path: per-round warp counts of own peaks (double-buffered)
-  uint32_t wcnt[(kDigCap / kThreads) * (kThreads / 32)];   // list path: own peaks per (round, warp)
+  uint32_t wcnt[2][32 * (kThreads / 32)];   // own peaks per (round, warp) of a batch of at most 32 rounds
 };
+
+// Ranking of own peaks in canonical order.  A batch is up to 32 rounds of
+// kThreads items in canonical order (item tid + k kThreads of round k); bit k
+// of a thread's mask own marks an own peak.  rank_count stores the own peaks
+// per (round, warp); after a barrier, rank_place has every warp scan those
+// counts itself and list its own peaks at base + their rank (item_L(k) gives
+// the plane index of round k's item).  Returns the batch's own peaks.
+template <int kThreads>
+__device__ __forceinline__ void rank_count(uint32_t own, int nr, uint32_t* wcnt) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int k = 0; k < nr; k++) {
+    const unsigned m = __ballot_sync(0xffffffffu, (own >> k) & 1u);
+    if (lane == 0) wcnt[k * (kThreads / 32) + wid] = (uint32_t)__popc(m);
+  }
+}
+
+template <int kThreads, typename ItemL>
+__device__ __forceinline__ uint32_t rank_place(uint32_t own, int nr, const uint32_t* wcnt, uint32_t base,
+                                               uint16_t* plist, ItemL item_L) {
+  constexpr int kWarps = kThreads / 32;
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint32_t carry = 0;
+  for (int j0 = 0; j0 < nr * kWarps; j0 += 32) {
+    const bool in = j0 + lane < nr * kWarps;
+    const uint32_t v = in ? wcnt[j0 + lane] : 0u;
+    const uint32_t inc = (uint32_t)warp_incl_scan32((int)v);
+    const uint32_t excl = base + carry + inc - v;      // own peaks before (round, warp) j0 + lane
+    // this warp's rounds k with k * kWarps + wid in [j0, j0 + 32)
+    for (int k = (j0 + kWarps - 1 - wid) / kWarps; k < nr && k * kWarps + wid < j0 + 32; k++) {
+      const uint32_t before = __shfl_sync(FULL, excl, k * kWarps + wid - j0);
+      const unsigned m = __ballot_sync(FULL, (own >> k) & 1u);
+      if ((own >> k) & 1u) plist[before + (uint32_t)__popc(m & ((1u << lane) - 1u))] = (uint16_t)item_L(k);
+    }
+    carry += __shfl_sync(FULL, inc, 31);
+  }
+  return carry;
+}
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
@@ -384,11 +423,9 @@ __global__ void __launch_bounds__(kThreads, 896 / kThreads)
     k_find_units(DevGeom G, DevParams P, DevWork W, unsigned int n_units) {
   constexpr int kH = unit_halo(kSplit);             // time halo of the plane
   constexpr int kURows = kChunkT + 2 * kH;          // plane rows
-  constexpr int kWarps = kThreads / 32;
   static_assert(kDigCap / kThreads <= 32, "one own-peak mask bit per list round");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ UnitSmem<kThreads> U;
-  const unsigned FULL = 0xffffffffu;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int ps = G.npmax + 2 * kPad;                 // plane row stride in pads
   const int plane_bytes = (kURows * ps * 2 + 15) & ~15;
@@ -453,6 +490,7 @@ __global__ void __launch_bounds__(kThreads, 896 / kThreads)
     }
     slot = slot == 2 ? 0 : slot + 1;
     const bool list = n_dig <= (uint32_t)kDigCap;     // block-uniform
+    bool pixel_rank = !list;                           // rank by pixel order (block-uniform)
     // ---- build: one thread per run; its digits go into the plane (and the list)
     for (uint32_t i = tid; i < n_runs; i += kThreads) {
       const int k = i < roff1 ? 0 : (i < roff2 ? 1 : 2);
@@ -487,7 +525,7 @@ __global__ void __launch_bounds__(kThreads, 896 / kThreads)
     const int qmin = P.q_peak_min;
     const int test_lo = ps, test_hi = (kURows - 1) * ps;          // rows 1 .. kURows - 2
     const int own_lo = kH * ps, own_hi = (kH + kChunkT) * ps;     // own rows
-    uint32_t total;
+    uint32_t total = 0;
     if (list) {
       // ---- step 2 over the digit list: peaks marked, own ones flagged per round
       const int nr = (int)((n_dig + kThreads - 1) / kThreads);
@@ -516,36 +554,18 @@ __global__ void __launch_bounds__(kThreads, 896 / kThreads)
           }
         }
       }
-      // ---- rank: own peaks per (round, warp); every warp scans the counts
-      // itself (at most 64) and places its own peaks
-      for (int k = 0; k < nr; k++) {
-        const unsigned m = __ballot_sync(FULL, (own >> k) & 1u);
-        if (lane == 0) U.wcnt[k * kWarps + wid] = (uint32_t)__popc(m);
-      }
+      // ---- rank: one batch (nr <= 32 rounds), unless the own peaks overflow their list
+      rank_count<kThreads>(own, nr, U.wcnt[0]);
       __syncthreads();
-      uint32_t carry = 0;
-      for (int j0 = 0; j0 < nr * kWarps; j0 += 32) {
-        const bool in = j0 + lane < nr * kWarps;
-        const uint32_t v = in ? U.wcnt[j0 + lane] : 0u;
-        const uint32_t inc = (uint32_t)warp_incl_scan32((int)v);
-        const uint32_t excl = carry + inc - v;           // own peaks before (round, warp) j0 + lane
-        // this warp's rounds k with k * kWarps + wid in [j0, j0 + 32)
-        for (int k = (j0 + kWarps - 1 - wid) / kWarps; k < nr && k * kWarps + wid < j0 + 32; k++) {
-          const uint32_t before = __shfl_sync(FULL, excl, k * kWarps + wid - j0);
-          const unsigned m = __ballot_sync(FULL, (own >> k) & 1u);
-          if ((own >> k) & 1u)
-            plist_l[before + (uint32_t)__popc(m & ((1u << lane) - 1u))] = dl[tid + (uint32_t)k * kThreads];
-        }
-        carry += __shfl_sync(FULL, inc, 31);
-      }
-      total = carry;
-      if (tid == 0) {
-        const unsigned long long sb = total ? atomicAdd(&W.ctr[CTR_SCURSOR], (unsigned long long)total) : 0ull;
-        if (sb + total > W.cap_cl) atomicOr(W.err, kErrOverflowCl);
-        U.sbase = sb;
-        W.win_cnt[u] = total;
-        W.win_soff[u] = (uint32_t)min(sb, (unsigned long long)0xffffffffu);
-      }
+      uint32_t cnt = 0;
+      for (int j = lane; j < nr * (kThreads / 32); j += 32) cnt += U.wcnt[0][j];
+#pragma unroll
+      for (int o = 16; o; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+      if (cnt <= (uint32_t)kPlistCap)
+        total = rank_place<kThreads>(own, nr, U.wcnt[0], 0u, plist_l,
+                                     [&](int k) { return (int)dl[tid + (uint32_t)k * kThreads]; });
+      else
+        pixel_rank = true;   // block-uniform: every warp summed the same counts
     } else {
       // ---- dense path: step 2 on every pixel of rows 1 .. kURows - 2
       const int np = G.npads[(frs >> 16) & 0xff];
@@ -557,55 +577,51 @@ __global__ void __launch_bounds__(kThreads, 896 / kThreads)
         if (q >= qmin && peak_test(plane, L, ps, q, qmin)) plane[L] = (uint16_t)(q | kPeakBit);
       }
       __syncthreads();   // every step-2 peak marked
+    }
+    if (pixel_rank) {
+      // ---- rank the own pixels' peaks (step 2b decided inline; again, with
+      // the same result, for peaks the list path has decided) in batches of 32
+      // rounds of kThreads pixels, canonical order.  The batches alternate
+      // between the two count buffers, starting with the one the list path
+      // did not use, so one barrier per batch suffices.
+      const int np = G.npads[(frs >> 16) & 0xff];
       const int n_own = kChunkT * np;
-      if (kNs) {
-        for (int i = tid; i < n_own; i += kThreads) {
-          const int row = kH + i / np, p = i - (row - kH) * np;
-          const int L = row * ps + kPad + p;
-          const uint16_t v = plane[L];
-          if ((v & kPeakBit) && ns_drop_plane(plane, L, ps, P.ns_min_dip)) plane[L] = (uint16_t)(v | kDropBit);
-        }
-        __syncthreads();
-      }
-      // ---- rank the own peaks round by round (pixels in canonical order)
+      auto pix_L = [&](int i) { const int row = kH + i / np; return row * ps + kPad + (i - (row - kH) * np); };
       uint32_t running = 0;                             // own peaks listed so far (block-uniform)
-      int parity = 0;
-      for (int base = 0; base < n_own; base += kThreads) {
-        const int i = base + tid;
-        bool own_pk = false;
-        int L = 0;
-        if (i < n_own) {
-          const int row = kH + i / np, p = i - (row - kH) * np;
-          L = row * ps + kPad + p;
-          const uint16_t v = plane[L];
-          own_pk = (v & kPeakBit) && !(v & kDropBit);
+      int parity = 1;
+      for (int B = 0; B < n_own; B += 32 * kThreads) {
+        const int nrb = min(32, (n_own - B + kThreads - 1) / kThreads);
+        uint32_t own = 0;
+        for (int k = 0; k < nrb; k++) {
+          const int i = B + k * kThreads + tid;
+          if (i < n_own) {
+            const int L = pix_L(i);
+            const uint16_t v = plane[L];
+            if (v & kPeakBit) {
+              if (kNs && ns_drop_plane(plane, L, ps, P.ns_min_dip)) plane[L] = (uint16_t)(v | kDropBit);
+              else own |= 1u << k;
+            }
+          }
         }
-        const unsigned m = __ballot_sync(FULL, own_pk);
-        if (lane == 0) U.wtot[parity][wid] = (uint32_t)__popc(m);
+        rank_count<kThreads>(own, nrb, U.wcnt[parity]);
         __syncthreads();
-        uint32_t before = running;
-#pragma unroll
-        for (int k = 0; k < kWarps; k++) {
-          const uint32_t v = U.wtot[parity][k];
-          before += k < wid ? v : 0u;
-          running += v;
-        }
-        if (own_pk) plist_d[before + (uint32_t)__popc(m & ((1u << lane) - 1u))] = (uint16_t)L;
+        running += rank_place<kThreads>(own, nrb, U.wcnt[parity], running, plist_d,
+                                        [&](int k) { return pix_L(B + k * kThreads + tid); });
         parity ^= 1;
       }
       total = running;
-      if (tid == 0) {
-        const unsigned long long sb = total ? atomicAdd(&W.ctr[CTR_SCURSOR], (unsigned long long)total) : 0ull;
-        if (sb + total > W.cap_cl) atomicOr(W.err, kErrOverflowCl);
-        U.sbase = sb;
-        W.win_cnt[u] = total;
-        W.win_soff[u] = (uint32_t)min(sb, (unsigned long long)0xffffffffu);
-      }
+    }
+    if (tid == 0) {
+      const unsigned long long sb = total ? atomicAdd(&W.ctr[CTR_SCURSOR], (unsigned long long)total) : 0ull;
+      if (sb + total > W.cap_cl) atomicOr(W.err, kErrOverflowCl);
+      U.sbase = sb;
+      W.win_cnt[u] = total;
+      W.win_soff[u] = (uint32_t)min(sb, (unsigned long long)0xffffffffu);
     }
     __syncthreads();   // list complete, every peak marked, span reserved
     // ---- clusters of the own peaks, strided over the list (canonical order)
     if (total) {
-      const uint16_t* plist = list ? plist_l : plist_d;
+      const uint16_t* plist = pixel_rank ? plist_d : plist_l;
       const unsigned long long sb = U.sbase;
       const int f = frs & 0xffff, r = (frs >> 16) & 0xff, s = (frs >> 24) & 0xff;
       const int np = G.npads[r], xrow = G.xrow[r];
@@ -637,18 +653,25 @@ __global__ void __launch_bounds__(kThreads, 896 / kThreads)
       }
     }
     __syncthreads();
-    for (int i = tid; i < plane_words16; i += kThreads) plane16[i] = make_uint4(0u, 0u, 0u, 0u);
+    // the plane back to zero: only the listed digits' pixels were written on
+    // the list path (the list is intact unless the pixel-order ranking used its room)
+    if (!pixel_rank) {
+      for (uint32_t i = tid; i < n_dig; i += kThreads) plane[dl[i]] = 0;
+    } else {
+      for (int i = tid; i < plane_words16; i += kThreads) plane16[i] = make_uint4(0u, 0u, 0u, 0u);
+    }
   }
   if (wid == 0) asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
 // Dynamic shared memory of k_find_units: the plane, then either the digit
-// list and the own peaks of the list path (kDigCap entries each), or the own
-// peaks of the dense path (at most one per pair of pads of each of 64 rows).
+// list (kDigCap entries) and the own peaks of the list path (kPlistCap), or
+// the own peaks ranked by pixel order (at most one per pair of pads of each of
+// 64 rows).
 size_t find2_smem_bytes(int npmax, bool split) {
   const size_t plane = ((size_t)(kChunkT + 2 * unit_halo(split)) * (npmax + 2 * kPad) * 2 + 15) & ~(size_t)15;
   const size_t dense_peaks = (size_t)kChunkT * ((npmax + 1) / 2) * 2;
-  const size_t r = std::max(dense_peaks, (size_t)kDigCap * 2 * 2);
+  const size_t r = std::max(dense_peaks, (size_t)(kDigCap + kPlistCap) * 2);
   return plane + ((r + 15) & ~(size_t)15);
 }
 
@@ -669,8 +692,12 @@ cudaError_t prepare_find2() {
   for (int nt : {128, 256})
     for (int ns = 0; ns < 2; ns++)
       for (int sp = 0; sp < 2; sp++)
-        if (e == cudaSuccess)
+        if (e == cudaSuccess) {
           e = cudaFuncSetAttribute(units_kernel(nt, ns, sp), cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+          // all of the unified L1 / shared storage as shared memory: seven CTAs of ~32 KB per SM
+          if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(units_kernel(nt, ns, sp), cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        }
   return e;
 }
 
