@@ -477,15 +477,15 @@ __global__ void __launch_bounds__(kThreads, 896 / kThreads)
     const uint32_t n_dig = q6.z;
     const uint32_t doff1 = U.dq[slot][1].w, doff2 = doff1 + U.dq[slot][3].w;   // list offsets of segments 1, 2
     const uint32_t roff1 = nrun[0], roff2 = nrun[0] + nrun[1], n_runs = roff2 + nrun[2];
-    if (tid == 0 && u + Gs < n_units) {                // unit u + G's runs and ADC words into L2 meanwhile
+    if (wid == kThreads / 32 - 1 && lane < 6 && u + Gs < n_units) {
+      // unit u + G's runs (lanes 0-2) and ADC words (lanes 3-5) into L2
+      // meanwhile, one segment per lane of the last warp
       const int s1 = slot == 2 ? 0 : slot + 1;
-#pragma unroll
-      for (int k = 0; k < 3; k++) {
-        const uint4 a = U.dq[s1][2 * k], b = U.dq[s1][2 * k + 1];
-        if (a.z) {
-          prefetch_l2_range(W.runs + (a.x | ((unsigned long long)a.y << 32)), 8ull * a.z);
-          prefetch_l2_range(pages32 + (b.x | ((unsigned long long)b.y << 32)), 4ull * b.z);
-        }
+      const int k = lane % 3;
+      const uint4 a = U.dq[s1][2 * k], b = U.dq[s1][2 * k + 1];
+      if (a.z) {
+        if (lane < 3) prefetch_l2_range(W.runs + (a.x | ((unsigned long long)a.y << 32)), 8ull * a.z);
+        else prefetch_l2_range(pages32 + (b.x | ((unsigned long long)b.y << 32)), 4ull * b.z);
       }
     }
     slot = slot == 2 ? 0 : slot + 1;
