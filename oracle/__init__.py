@@ -122,6 +122,8 @@ def _load():
         L.orc_find_clusters.restype = ctypes.c_int64
         L.orc_peaks_plane.argtypes = [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P]
         L.orc_peaks_plane_ns.argtypes = [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P]
+        L.orc_entropy_encode.argtypes = [ctypes.c_int64, _P, _P, _P, _P, _P, ctypes.c_int64]
+        L.orc_entropy_encode.restype = ctypes.c_int64
         L.orc_cluster_at.argtypes = [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                      ctypes.c_int, ctypes.c_int, _P]
         L.orc_split_share.argtypes = [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -584,3 +586,19 @@ def reconstruct(tf, params: OracleParams | None = None) -> OracleResult:
     fits = fit_all(tf, cl, cl2trk, len(first), params)
     times["fit"] = time.perf_counter() - t
     return OracleResult(cl, up, down, chain, cl2trk, first, ncl, fits, passes, times)
+
+
+def entropy_encode(code_y, code_z, status):
+    """Step 10c: canonical-Huffman stream of the coded clusters' codes.
+    Returns (lengths [2, 256] of the y and z alphabets, bits, words)."""
+    L = _load()
+    cy = np.ascontiguousarray(code_y, np.int8)
+    cz = np.ascontiguousarray(code_z, np.int8)
+    st = np.ascontiguousarray(status, np.uint8)
+    n = len(st)
+    lens = np.zeros(512, np.uint8)
+    nbits = L.orc_entropy_encode(n, cy.ctypes.data, cz.ctypes.data, st.ctypes.data, lens.ctypes.data, None, 0)
+    words = np.zeros(max(1, (nbits + 31) // 32), np.uint32)
+    L.orc_entropy_encode(n, cy.ctypes.data, cz.ctypes.data, st.ctypes.data, lens.ctypes.data,
+                         words.ctypes.data, len(words))
+    return lens.reshape(2, 256), int(nbits), words[: (nbits + 31) // 32]

@@ -1413,6 +1413,124 @@ int64_t orc_compress(const orc_input* in, const orc_params* P, const orc_cmp_par
   return coded;
 }
 
+/* ------------------------------------------------------------ 10c. entropy coding of the codes
+ * The library's definition of a bit stream for the step-10 codes (the size the
+ * step reaches; the paper gives compression as the reason for online
+ * tracking, "Hardware and data flow"):
+ *   - symbols: code + 128 of the y and z codes of the coded clusters
+ *     (status 1), one alphabet of 256 per component;
+ *   - per component, Huffman code lengths from the symbol counts: the leaves
+ *     (symbols with a count) ordered by (count, symbol) form queue A, new
+ *     nodes join queue B in creation order; each merge takes the lighter of
+ *     the two queue heads twice (a leaf before a node of equal weight), and a
+ *     leaf's length is its depth (a single symbol gets length 1).  If a
+ *     length exceeds 24, every count c becomes (c + 1) / 2 and the lengths
+ *     are built again;
+ *   - canonical codewords: symbols ordered by (length, symbol), the first
+ *     gets 0, each next (previous + 1) << (length - previous length);
+ *   - the stream: for each coded cluster in index order its y codeword then
+ *     its z codeword, most significant bit first; stream bit b is bit
+ *     31 - b % 32 of 32-bit word b / 32; the last word is zero-padded. */
+#define ORC_MAX_CODE_LEN 24
+
+/* Huffman lengths of one 256-symbol alphabet (count 0: length 0). */
+static void huff_lengths(const uint64_t* count_in, uint8_t* len) {
+  uint64_t c[256];
+  for (int i = 0; i < 256; i++) c[i] = count_in[i];
+  for (;;) {
+    int leaves[256], n = 0;
+    for (int i = 0; i < 256; i++) { len[i] = 0; if (c[i]) leaves[n++] = i; }
+    if (n == 0) return;
+    if (n == 1) { len[leaves[0]] = 1; return; }
+    /* queue A: leaves by (count, symbol), insertion sort */
+    for (int i = 1; i < n; i++)
+      for (int j = i; j > 0 && (c[leaves[j]] < c[leaves[j - 1]] ||
+                                (c[leaves[j]] == c[leaves[j - 1]] && leaves[j] < leaves[j - 1])); j--) {
+        int t = leaves[j]; leaves[j] = leaves[j - 1]; leaves[j - 1] = t;
+      }
+    /* nodes 0..255 are the leaves (by symbol), 256.. the merged ones */
+    int parent[512];
+    uint64_t w[512];
+    for (int i = 0; i < 512; i++) parent[i] = -1;
+    for (int i = 0; i < 256; i++) w[i] = c[i];
+    int qa = 0, qb = 256, nb = 256;   /* heads of A (index into leaves) and B (node id); next node id */
+    for (int m = 0; m < n - 1; m++) {
+      int pick[2];
+      for (int k = 0; k < 2; k++) {
+        int take_a;
+        if (qa >= n) take_a = 0;
+        else if (qb >= nb) take_a = 1;
+        else take_a = w[leaves[qa]] <= w[qb];
+        pick[k] = take_a ? leaves[qa++] : qb++;
+      }
+      w[nb] = w[pick[0]] + w[pick[1]];
+      parent[pick[0]] = parent[pick[1]] = nb;
+      nb++;
+    }
+    int maxlen = 0;
+    for (int i = 0; i < n; i++) {
+      int d = 0;
+      for (int x = leaves[i]; parent[x] >= 0; x = parent[x]) d++;
+      len[leaves[i]] = (uint8_t)(d > 255 ? 255 : d);
+      if (d > maxlen) maxlen = d;
+    }
+    if (maxlen <= ORC_MAX_CODE_LEN) return;
+    for (int i = 0; i < 256; i++) if (c[i]) c[i] = (c[i] + 1) / 2;
+  }
+}
+
+/* Canonical codewords from the lengths. */
+static void huff_codes(const uint8_t* len, uint32_t* code) {
+  uint32_t next = 0;
+  int prev_len = 0, first = 1;
+  for (int l = 1; l <= ORC_MAX_CODE_LEN; l++)
+    for (int s = 0; s < 256; s++) {
+      if (len[s] != l) continue;
+      if (first) { next = 0; first = 0; }
+      else next = (next + 1) << (l - prev_len);
+      code[s] = next;
+      prev_len = l;
+    }
+}
+
+/* Encode the codes of n clusters.  len_out[512]: the lengths of the y then
+ * the z alphabet; words (may be NULL) receives the stream if it holds
+ * cap_words words.  Returns the stream's length in bits. */
+int64_t orc_entropy_encode(int64_t n, const int8_t* code_y, const int8_t* code_z, const uint8_t* status,
+                           uint8_t* len_out, uint32_t* words, int64_t cap_words) {
+  uint64_t hist[2][256];
+  memset(hist, 0, sizeof(hist));
+  for (int64_t i = 0; i < n; i++) {
+    if (status[i] != 1) continue;
+    hist[0][code_y[i] + 128]++;
+    hist[1][code_z[i] + 128]++;
+  }
+  uint32_t code[2][256];
+  memset(code, 0, sizeof(code));
+  for (int k = 0; k < 2; k++) {
+    huff_lengths(hist[k], len_out + 256 * k);
+    huff_codes(len_out + 256 * k, code[k]);
+  }
+  int64_t nbits = 0;
+  for (int64_t i = 0; i < n; i++)
+    if (status[i] == 1) nbits += len_out[code_y[i] + 128] + len_out[256 + code_z[i] + 128];
+  if (words && (nbits + 31) / 32 <= cap_words) {
+    for (int64_t k = 0; k < (nbits + 31) / 32; k++) words[k] = 0;
+    int64_t b = 0;
+    for (int64_t i = 0; i < n; i++) {
+      if (status[i] != 1) continue;
+      for (int comp = 0; comp < 2; comp++) {
+        const int sym = (comp ? code_z[i] : code_y[i]) + 128;
+        const int l = len_out[256 * comp + sym];
+        const uint32_t cw = code[comp][sym];
+        for (int j = l - 1; j >= 0; j--, b++)
+          if ((cw >> j) & 1u) words[b / 32] |= 1u << (31 - b % 32);
+      }
+    }
+  }
+  return nbits;
+}
+
 /* ------------------------------------------------------------ 11. drift calibration
  * The paper lists calibration among the EPNs' tasks ("Hardware and data flow");
  * this is the library's definition of a drift-velocity / T0 calibration from
