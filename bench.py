@@ -493,7 +493,7 @@ def compression_stats(tpc, R, pages_d, offs_d, tf, reps=5):
     """The optional step 10 (tpc_compress_clusters): time of the call and the
     size of the position information of the clusters on tracks, as the Shannon
     entropy of the residual codes against the 32 bits of the raw (pad_fp,
-    time_fp) pair."""
+    time_fp) pair, and as the stream that step 10c (tpc_entropy_encode) codes."""
     t = R.submit(pages_d, offs_d, tf.n_time_bins)
     R.wait(t)
     n_cl = tpc.tpc_get_counters(R.ctx, t)["clusters"]
@@ -504,6 +504,13 @@ def compression_stats(tpc, R, pages_d, offs_d, tf, reps=5):
         coded, escaped = tpc.tpc_compress_clusters(R.ctx, t)
         times.append(time.perf_counter() - t0)
     cy, cz, st = tpc.tpc_get_compressed(R.ctx, t, n_cl)
+    # step 10c: the codes entropy-coded into a stream (canonical Huffman)
+    tpc.tpc_entropy_encode(R.ctx, t)      # warm-up
+    etimes = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        _, n_bits, _ = tpc.tpc_entropy_encode(R.ctx, t)
+        etimes.append(time.perf_counter() - t0)
     tpc.tpc_release(R.ctx, t)
 
     def entropy(v):
@@ -515,7 +522,11 @@ def compression_stats(tpc, R, pages_d, offs_d, tf, reps=5):
     return {"ms": 1e3 * statistics.median(times), "clusters": int(n_cl), "coded": coded, "escaped": escaped,
             "position_bits_per_coded_cluster": bits, "raw_position_bits": 32,
             "position_compression": 32.0 / bits if bits else None,
-            "timing": f"host wall clock of the call, median of {reps}"}
+            "stream_bits_per_coded_cluster": n_bits / coded if coded else None,
+            "stream_bytes": (n_bits + 7) // 8,
+            "entropy_coding_ms": 1e3 * statistics.median(etimes),
+            "timing": f"host wall clock of the call, median of {reps} (entropy_coding_ms includes the stream's copy "
+                      "to host memory)"}
 
 
 def calibration_stats(tpc, R, pages_d, offs_d, tf, reps=5):

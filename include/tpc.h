@@ -493,6 +493,36 @@ tpc_status tpc_compress_clusters(tpc_context* ctx, uint64_t ticket, const tpc_cm
  * TPC_E_NOTREADY if tpc_compress_clusters has not run on the ticket. */
 tpc_status tpc_get_compressed(tpc_context* ctx, uint64_t ticket, int8_t* code_y, int8_t* code_z, uint8_t* status);
 
+/* Step 10c, optional: entropy coding of the step-10 codes into a bit stream
+ * (the size the compression reaches; the paper gives data reduction as the
+ * reason for online tracking, "Hardware and data flow"; the code is this
+ * library's definition):
+ *   - symbols: code + 128 of the y and of the z codes of the coded clusters
+ *     (status 1), one 256-symbol alphabet per component;
+ *   - per alphabet, Huffman codeword lengths from the symbol counts: the
+ *     symbols with a count, ordered by (count, symbol), form queue A; merged
+ *     nodes join queue B in creation order; each merge takes the lighter of
+ *     the two queue heads twice, a symbol before a node of equal weight; a
+ *     symbol's length is its depth (1 for a lone symbol).  If a length exceeds
+ *     24, every count c becomes (c + 1) / 2 and the lengths are built again;
+ *   - canonical codewords: symbols ordered by (length, symbol), the first
+ *     gets 0, each next (previous + 1) << (its length - previous length);
+ *   - the stream: for each coded cluster in index order its y codeword, then
+ *     its z codeword, most significant bit first; stream bit b is bit
+ *     31 - b % 32 of 32-bit word b / 32; the last word is zero-padded.
+ * code_y, code_z, status: NULL to encode the ticket's step-10 codes (then
+ * tpc_compress_clusters must have run: TPC_E_NOTREADY otherwise), or host
+ * arrays of n_clusters entries each (all three) that replace the ticket's
+ * step-10 codes before encoding (tpc_get_compressed returns them afterwards).
+ * lengths (may be NULL): the 512 codeword lengths, y alphabet then z (0: symbol
+ * unused).  *n_bits (may be NULL): the stream's length.  words (may be NULL:
+ * size query) receives the (n_bits + 31) / 32 stream words; TPC_E_INVAL if
+ * cap_words is smaller.  Runs on the ticket's stream and waits.
+ * Errors: TPC_E_INVAL, TPC_E_NOTREADY, TPC_E_NOTFOUND, TPC_E_NOMEM, TPC_E_CUDA. */
+tpc_status tpc_entropy_encode(tpc_context* ctx, uint64_t ticket, const int8_t* code_y, const int8_t* code_z,
+                              const uint8_t* status, uint8_t* lengths, uint64_t* n_bits, uint32_t* words,
+                              uint64_t cap_words);
+
 /* Step 11, optional: drift-velocity / T0 calibration from the step-8 tracks of
  * a finished ticket holding one collision whose vertex lies on the beam axis
  * at z = 0 (the paper lists calibration among the EPNs' tasks, "Hardware and

@@ -149,3 +149,163 @@ cudaError_t launch_calibrate(const DevParams& P, const DevWork& W, const CalWork
 }
 
 }  // namespace tpc
+
+// ---------------------------------------------------------------------------
+// Optional entropy coding of the step-10 codes (step 10c of the library's
+// definition): per component (y, z) a canonical Huffman code over the 256
+// symbols code + 128 of the coded clusters, lengths limited to 24 bits, and
+// the stream of the coded clusters' codewords in cluster order (y then z,
+// most significant bit first, stream bit b in bit 31 - b % 32 of word b / 32).
+// Tie rules of the code construction: the leaves ordered by (count, symbol)
+// form one queue, the merged nodes a second in creation order, and each merge
+// takes the lighter head twice, a leaf before a node of equal weight; over
+// 24 bits every count c becomes (c + 1) / 2 and the code is built again.
+namespace tpc {
+
+constexpr int kMaxCodeLen = 24;
+
+__global__ void k_ent_hist(DevWork W, CmpWork C, EntWork E) {
+  __shared__ unsigned int h[512];
+  for (int i = threadIdx.x; i < 512; i += blockDim.x) h[i] = 0;
+  __syncthreads();
+  unsigned long long n = W.ctr[CTR_NCL];
+  if (n > W.cap_cl) n = W.cap_cl;
+  for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
+       i += (unsigned long long)gridDim.x * blockDim.x) {
+    if (C.status[i] != 1) continue;
+    atomicAdd(&h[(int)C.code_y[i] + 128], 1u);
+    atomicAdd(&h[256 + (int)C.code_z[i] + 128], 1u);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 512; i += blockDim.x)
+    if (h[i]) atomicAdd(&E.hist[i], (unsigned long long)h[i]);
+}
+
+// One block of 256 threads, one symbol per thread: the leaves sorted by rank,
+// the merges by thread 0, the depths by every leaf walking up, then the
+// canonical codewords by thread 0.
+__global__ void __launch_bounds__(256) k_ent_tables(EntWork E) {
+  __shared__ unsigned long long w[512];
+  __shared__ int leaves[256], parent[512];
+  __shared__ int maxlen;
+  const int s = threadIdx.x;
+  for (int comp = 0; comp < 2; comp++) {
+    unsigned long long c = E.hist[256 * comp + s];
+    int len = 0;
+    while (true) {
+      __syncthreads();
+      // rank of this leaf in (count, symbol) order
+      w[s] = c;
+      parent[s] = parent[256 + s] = -1;
+      if (s == 0) maxlen = 0;
+      const int n = __syncthreads_count(c != 0);
+      if (c) {
+        int rank = 0;
+        for (int j = 0; j < 256; j++) {
+          const unsigned long long cj = w[j];
+          rank += cj != 0 && (cj < c || (cj == c && j < s));
+        }
+        leaves[rank] = s;
+      }
+      __syncthreads();
+      if (s == 0 && n >= 2) {
+        int qa = 0, qb = 256, nb = 256;
+        for (int m = 0; m < n - 1; m++) {
+          int pick[2];
+          for (int k = 0; k < 2; k++) {
+            bool take_a;
+            if (qa >= n) take_a = false;
+            else if (qb >= nb) take_a = true;
+            else take_a = w[leaves[qa]] <= w[qb];
+            pick[k] = take_a ? leaves[qa++] : qb++;
+          }
+          w[nb] = w[pick[0]] + w[pick[1]];
+          parent[pick[0]] = parent[pick[1]] = nb;
+          nb++;
+        }
+      }
+      __syncthreads();
+      len = 0;
+      if (c) {
+        if (n == 1) len = 1;
+        else for (int x = s; parent[x] >= 0; x = parent[x]) len++;
+        atomicMax(&maxlen, len);
+      }
+      __syncthreads();
+      if (maxlen <= kMaxCodeLen) break;   // block-uniform
+      if (c) c = (c + 1) / 2;
+    }
+    E.len[256 * comp + s] = (uint8_t)len;
+    leaves[s] = len;                      // the lengths, for thread 0
+    __syncthreads();
+    if (s == 0) {
+      uint32_t next = 0;
+      int prev = 0;
+      bool first = true;
+      for (int l = 1; l <= kMaxCodeLen; l++)
+        for (int j = 0; j < 256; j++) {
+          if (leaves[j] != l) continue;
+          next = first ? 0u : (next + 1u) << (l - prev);
+          first = false;
+          prev = l;
+          E.code[256 * comp + j] = next;
+        }
+    }
+  }
+}
+
+// Bits of each cluster's codewords (0 unless coded), scanned afterwards.
+__global__ void k_ent_bits(DevWork W, CmpWork C, EntWork E) {
+  unsigned long long n = W.ctr[CTR_NCL];
+  if (n > W.cap_cl) n = W.cap_cl;
+  for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
+       i += (unsigned long long)gridDim.x * blockDim.x)
+    E.bits[i] = C.status[i] == 1 ? (uint64_t)E.len[(int)C.code_y[i] + 128] + E.len[256 + (int)C.code_z[i] + 128] : 0ull;
+}
+
+// Each coded cluster ORs its (at most 48) bits into the zeroed stream at its
+// offset; bits of different clusters never overlap.
+__global__ void k_ent_pack(DevWork W, CmpWork C, EntWork E) {
+  unsigned long long n = W.ctr[CTR_NCL];
+  if (n > W.cap_cl) n = W.cap_cl;
+  for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
+       i += (unsigned long long)gridDim.x * blockDim.x) {
+    if (C.status[i] != 1) continue;
+    const int sy = (int)C.code_y[i] + 128, sz = 256 + (int)C.code_z[i] + 128;
+    const int lz = E.len[sz];
+    int L = E.len[sy] + lz;
+    const unsigned long long v = ((unsigned long long)E.code[sy] << lz) | E.code[sz];
+    unsigned long long b = E.bits[i];
+    while (L > 0) {
+      const unsigned long long wi = b >> 5;
+      const int room = 32 - (int)(b & 31);
+      const int take = min(room, L);
+      const uint32_t part = (uint32_t)((v >> (L - take)) & ((1ull << take) - 1ull));
+      if (wi < E.cap_words) atomicOr(&E.words[wi], part << (room - take));
+      L -= take;
+      b += take;
+    }
+  }
+}
+
+cudaError_t launch_scan(uint64_t* v, const unsigned long long* n_ptr, unsigned long long cap,
+                        unsigned long long* state, unsigned int* ticket, unsigned long long* total, uint32_t* err,
+                        int n_sm, cudaStream_t st);
+
+// Step 10c on the codes in C: histogram, tables, bit offsets, stream.  The
+// caller has zeroed E.hist, E.scan_state, E.ticket and E.words.
+cudaError_t launch_entropy(const DevWork& W, const CmpWork& C, const EntWork& E, int n_sm, cudaStream_t st) {
+  unsigned long long g = (W.cap_cl + 255) / 256;
+  const unsigned long long m = (unsigned long long)n_sm * 8;
+  if (g > m) g = m;
+  const unsigned grid = (unsigned)(g ? g : 1);
+  k_ent_hist<<<grid, 256, 0, st>>>(W, C, E);
+  k_ent_tables<<<1, 256, 0, st>>>(E);
+  k_ent_bits<<<grid, 256, 0, st>>>(W, C, E);
+  cudaError_t e = launch_scan(E.bits, W.ctr + CTR_NCL, W.cap_cl, E.scan_state, E.ticket, E.total, W.err, n_sm, st);
+  if (e != cudaSuccess) return e;
+  k_ent_pack<<<grid, 256, 0, st>>>(W, C, E);
+  return cudaGetLastError();
+}
+
+}  // namespace tpc

@@ -35,6 +35,7 @@ cudaError_t launch_find2(const DevGeom&, const DevParams&, const DevWork&, unsig
 cudaError_t launch_xsec(const DevGeom&, const DevParams&, const DevWork&, const XsWork&, int, cudaStream_t);
 cudaError_t launch_loopers(const DevGeom&, const DevParams&, const DevWork&, const LoopWork&, int, cudaStream_t);
 cudaError_t launch_compress(const DevParams&, const DevWork&, const CmpWork&, int, cudaStream_t);
+cudaError_t launch_entropy(const DevWork&, const CmpWork&, const EntWork&, int, cudaStream_t);
 cudaError_t launch_calibrate(const DevParams&, const DevWork&, const CalWork&, int, cudaStream_t);
 }  // namespace tpc
 
@@ -1278,14 +1279,39 @@ extern "C" tpc_status tpc_get_looper_links(tpc_context* ctx, uint64_t ticket, in
 }
 
 // ------------------------------------------------------------------ step 10
-static CmpWork cmp_work(Slot& s) {
+// The step-10 buffer: codes and status (3 bytes per cluster), counters, then
+// step 10c's work: tables, bits per cluster, scan state, the stream (at most
+// 48 bits per cluster).
+static size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
+static uint64_t ent_cap_words(uint64_t cap_cl) { return cap_cl * 3 / 2 + 4; }
+static size_t cmp_need(uint64_t cap_cl) {
+  const size_t n = al256(cap_cl);
+  return 3 * n + 256 + 8192 + al256(8 * cap_cl) + al256(8 * scan_tiles(cap_cl)) + 256 + al256(4 * ent_cap_words(cap_cl));
+}
+static CmpWork cmp_work(Slot& s, EntWork* E = nullptr) {
   CmpWork C;
   uint8_t* p = (uint8_t*)s.cmp.p;
-  const size_t n = (s.cap_cl + 255) & ~(size_t)255;
+  const size_t n = al256(s.cap_cl);
   C.code_y = (int8_t*)p;
   C.code_z = (int8_t*)(p + n);
   C.status = p + 2 * n;
   C.ctl = (unsigned long long*)(p + 3 * n);
+  if (E) {
+    uint8_t* q = p + 3 * n + 256;
+    E->hist = (unsigned long long*)q;
+    E->len = q + 4096;
+    E->code = (uint32_t*)(q + 4096 + 1024);
+    q += 8192;
+    E->bits = (uint64_t*)q;
+    q += al256(8 * s.cap_cl);
+    E->scan_state = (unsigned long long*)q;
+    q += al256(8 * scan_tiles(s.cap_cl));
+    E->ticket = (unsigned int*)q;
+    E->total = (unsigned long long*)(q + 16);
+    q += 256;
+    E->words = (uint32_t*)q;
+    E->cap_words = ent_cap_words(s.cap_cl);
+  }
   return C;
 }
 
@@ -1299,7 +1325,7 @@ extern "C" tpc_status tpc_compress_clusters(tpc_context* ctx, uint64_t ticket, c
   tpc_status st = done_slot(ctx, ticket, &s);
   if (st) return st;
   CUDA_TRY(cudaSetDevice(ctx->device));
-  const size_t need = 3 * ((s->cap_cl + 255) & ~(size_t)255) + 256;
+  const size_t need = cmp_need(s->cap_cl);
   if (need > s->cmp.bytes) {
     if (ctx->used - s->cmp_bytes + need > ctx->budget) return fail(TPC_E_NOMEM, "tpc_compress_clusters: over the memory budget");
     CUDA_TRY(ensure(s->cmp, need));
@@ -1339,6 +1365,54 @@ extern "C" tpc_status tpc_get_compressed(tpc_context* ctx, uint64_t ticket, int8
     if (status) CUDA_TRY(cudaMemcpyAsync(status, C.status, ncl, cudaMemcpyDeviceToHost, s->stream));
   }
   CUDA_TRY(cudaStreamSynchronize(s->stream));
+  return TPC_OK;
+}
+
+extern "C" tpc_status tpc_entropy_encode(tpc_context* ctx, uint64_t ticket, const int8_t* code_y,
+                                         const int8_t* code_z, const uint8_t* status, uint8_t* lengths,
+                                         uint64_t* n_bits, uint32_t* words, uint64_t cap_words) {
+  if (!ctx) return fail(TPC_E_INVAL, "tpc_entropy_encode: null argument");
+  const bool given = code_y || code_z || status;
+  if (given && !(code_y && code_z && status))
+    return fail(TPC_E_INVAL, "tpc_entropy_encode: give code_y, code_z and status together, or none");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  Slot* s;
+  tpc_status st = done_slot(ctx, ticket, &s);
+  if (st) return st;
+  if (!given && !s->cmp_done) return fail(TPC_E_NOTREADY, "tpc_compress_clusters has not run on this ticket");
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  const size_t need = cmp_need(s->cap_cl);
+  if (need > s->cmp.bytes) {
+    if (ctx->used - s->cmp_bytes + need > ctx->budget) return fail(TPC_E_NOMEM, "tpc_entropy_encode: over the memory budget");
+    CUDA_TRY(ensure(s->cmp, need));
+    ctx->used = ctx->used - s->cmp_bytes + need;
+    s->cmp_bytes = need;
+  }
+  EntWork E;
+  CmpWork C = cmp_work(*s, &E);
+  const uint64_t ncl = n_cl_of(*s);
+  if (given && ncl) {
+    CUDA_TRY(cudaMemcpyAsync(C.code_y, code_y, ncl, cudaMemcpyHostToDevice, s->stream));
+    CUDA_TRY(cudaMemcpyAsync(C.code_z, code_z, ncl, cudaMemcpyHostToDevice, s->stream));
+    CUDA_TRY(cudaMemcpyAsync(C.status, status, ncl, cudaMemcpyHostToDevice, s->stream));
+  }
+  CUDA_TRY(cudaMemsetAsync(E.hist, 0, 4096, s->stream));
+  CUDA_TRY(cudaMemsetAsync(E.scan_state, 0, 8 * scan_tiles(s->cap_cl), s->stream));
+  CUDA_TRY(cudaMemsetAsync(E.ticket, 0, 256, s->stream));
+  CUDA_TRY(cudaMemsetAsync(E.words, 0, 4 * E.cap_words, s->stream));
+  CUDA_TRY(launch_entropy(s->W, C, E, ctx->n_sm, s->stream));
+  unsigned long long total = 0;
+  CUDA_TRY(cudaMemcpyAsync(&total, E.total, 8, cudaMemcpyDeviceToHost, s->stream));
+  if (lengths) CUDA_TRY(cudaMemcpyAsync(lengths, E.len, 512, cudaMemcpyDeviceToHost, s->stream));
+  CUDA_TRY(cudaStreamSynchronize(s->stream));
+  if (given) s->cmp_done = true;
+  if (n_bits) *n_bits = total;
+  const uint64_t nw = (total + 31) / 32;
+  if (words) {
+    if (nw > cap_words) return fail(TPC_E_INVAL, "tpc_entropy_encode: words holds fewer than (n_bits + 31) / 32 words");
+    if (nw) CUDA_TRY(cudaMemcpyAsync(words, E.words, 4 * nw, cudaMemcpyDeviceToHost, s->stream));
+    CUDA_TRY(cudaStreamSynchronize(s->stream));
+  }
   return TPC_OK;
 }
 

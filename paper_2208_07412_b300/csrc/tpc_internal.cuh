@@ -330,6 +330,19 @@ struct CmpWork {
   float step_y, step_z;          // cm
 };
 
+// Work space of the optional entropy coding of the step-10 codes (step 10c).
+struct EntWork {
+  unsigned long long* hist;      // [512] symbol counts, y then z alphabet
+  uint8_t* len;                  // [512] codeword lengths
+  uint32_t* code;                // [512] canonical codewords
+  uint64_t* bits;                // [cap_cl] bits per cluster, scanned in place to stream offsets
+  unsigned long long* scan_state;
+  unsigned int* ticket;          // scan ticket
+  unsigned long long* total;     // stream length in bits
+  uint32_t* words;               // [cap_words] the stream
+  unsigned long long cap_words;
+};
+
 // Work space of the optional drift calibration (step 11).
 struct CalWork {
   float* tv;                     // [cap_ch] vertex time bin per track, -1 if unused

@@ -98,7 +98,7 @@ EXPORTS = ("tpc_params_default", "tpc_create_geometry", "tpc_destroy_geometry", 
            "tpc_get_counters", "tpc_release", "tpc_last_error", "tpc_find_clusters_noalloc",
            "tpc_submit_batch", "tpc_get_batch_info", "tpc_get_event_clusters", "tpc_get_event_tracks",
            "tpc_get_tuning", "tpc_set_tuning", "tpc_autotune", "tpc_merge_sectors", "tpc_get_merged_tracks",
-           "tpc_join_loopers", "tpc_get_looper_links", "tpc_compress_clusters", "tpc_get_compressed", "tpc_calibrate_drift", "tpc_measure_fma_peak")
+           "tpc_join_loopers", "tpc_get_looper_links", "tpc_compress_clusters", "tpc_get_compressed", "tpc_entropy_encode", "tpc_calibrate_drift", "tpc_measure_fma_peak")
 
 _lib = None
 
@@ -152,6 +152,7 @@ def load(build_if_missing: bool = True):
     L.tpc_compress_clusters.argtypes = [_P, _u64, ctypes.POINTER(tpc_cmp_params), ctypes.POINTER(_u64),
                                         ctypes.POINTER(_u64)]
     L.tpc_get_compressed.argtypes = [_P, _u64, _P, _P, _P]
+    L.tpc_entropy_encode.argtypes = [_P, _u64, _P, _P, _P, _P, ctypes.POINTER(_u64), _P, _u64]
     L.tpc_calibrate_drift.argtypes = [_P, _u64, ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_double),
                                       ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                       ctypes.POINTER(_u64)]
@@ -368,6 +369,27 @@ def tpc_get_compressed(ctx, ticket: int, n_clusters: int):
     st = np.zeros(max(n_clusters, 1), np.uint8)
     _check(load().tpc_get_compressed(ctx, ticket, cy.ctypes.data, cz.ctypes.data, st.ctypes.data))
     return cy[:n_clusters], cz[:n_clusters], st[:n_clusters]
+
+
+def tpc_entropy_encode(ctx, ticket: int, codes=None):
+    """Step 10c on a finished ticket: (lengths [2, 256], n_bits, words).
+    codes: None for the ticket's step-10 codes, or (code_y, code_z, status)
+    arrays of n_clusters entries that replace them."""
+    L = load()
+    nb = _u64()
+    lens = np.zeros(512, np.uint8)
+    args = [None, None, None]
+    if codes is not None:
+        args = [np.ascontiguousarray(codes[0], np.int8), np.ascontiguousarray(codes[1], np.int8),
+                np.ascontiguousarray(codes[2], np.uint8)]
+    keep = [a if a is None or len(a) else np.zeros(1, a.dtype) for a in args]   # no clusters: a dummy entry
+    ptrs = [a.ctypes.data if a is not None else None for a in keep]
+    _check(L.tpc_entropy_encode(ctx, ticket, *ptrs, lens.ctypes.data, ctypes.byref(nb), None, 0))
+    n = int(nb.value)
+    words = np.zeros(max(1, (n + 31) // 32), np.uint32)
+    _check(L.tpc_entropy_encode(ctx, ticket, None, None, None, None, ctypes.byref(nb), words.ctypes.data,
+                                len(words)))
+    return lens.reshape(2, 256), n, words[: (n + 31) // 32]
 
 
 def tpc_calibrate_drift(ctx, ticket: int, t0_bins: float, drift_length_cm: float = 250.0):
