@@ -47,15 +47,21 @@ WORKLOADS = {
                          "floor(15000 U^7.82) (mean ~1,700), 5% loopers, same charge/noise/ZS model"),
 }
 REF_SAMPLE_BYTES = 20 << 20
-# ncu counters of one find stage (its kernels summed: decode, find units, scan
-# and compaction for the two-pass finder): DRAM bytes read + written and warp
-# instructions (smsp__inst_executed.sum), from a capture of the current kernels,
-# keyed by (workload, finder, finder threads), with the ZS bytes of the captured case.  The
-# 55,000-bin continuous timeframe (5.7 GB) is beyond a capture's size, so its
-# figures are those of the first 11,000 bins of the same timeframe scaled by
-# the ZS bytes (the stage's traffic and instructions grow with the pages and
-# clusters).  Must be cleared whenever a finder kernel changes.
-FINDER_COUNTERS = {}
+# ncu counters of one find stage (its kernels summed: k_decode_runs,
+# k_unit_descs, k_find_units and k_compact_clusters; the unit-count scan, ~1 %
+# of the stage, is left out): DRAM bytes read + written and warp instructions
+# (smsp__inst_executed.sum), from a metrics-only capture of the current
+# kernels, keyed by (workload, finder, finder threads), with the ZS bytes of the
+# captured case.  The 55,000-bin continuous timeframe (5.7 GB of pages) is
+# beyond a capture's size, so its figures are those of an 11,000-bin
+# continuous timeframe of the same occupancy law (seed 1, 1.17 GB of pages)
+# scaled by the ZS bytes (the stage's traffic and instructions grow with the
+# pages and clusters).  Must be cleared whenever a finder kernel changes.
+FINDER_COUNTERS = {
+    ("full_tpc", "two_pass", 128): {"zs": 70336448, "dram": 210503168 + 36954880, "instr": 396996243},
+    ("continuous_50khz", "two_pass", 128): {"zs": 1173460064, "dram": 3448704256 + 2630252800,
+                                            "instr": 6110698624},
+}
 # Warp-instruction issue peak: 148 SMs x 4 schedulers x 1 instruction per cycle
 # at the 2032 MHz maximum SM clock.
 ISSUE_PEAK = 148 * 4 * 2.032e9
@@ -619,7 +625,7 @@ def noise_suppression_stats(tpc, torch, tf, pages_d, offs_d, tuning, flush, n_cl
             "find_ms_without": fused_ms, "timing": f"find stage, mean of {reps}, L2 flushed"}
 
 
-FINDER_KERNELS = {"two_pass": "find stage: k_decode_digits + k_find_units + k_scan + k_compact_clusters",
+FINDER_KERNELS = {"two_pass": "find stage: k_decode_runs + k_unit_descs + k_find_units + k_scan + k_compact_clusters",
                   "fused": "find stage: k_find_classify + k_find_light + k_find_clusters + k_scan + k_compact_clusters",
                   "dense": "find stage: k_find_clusters (dense-plane decode and find passes) + k_scan + "
                            "k_compact_clusters"}
