@@ -32,6 +32,11 @@ __device__ __forceinline__ long long llabs_(long long v) { return v < 0 ? -v : v
 // iteration order (d ascending, then u ascending, strict <) is the definition's
 // tie rule.
 constexpr int kCaThreads = 128, kCaChunk = 128, kCaStage = 768;
+// Per staged slice, the index of its first cluster at or past each time bin of
+// [tmin - w, tmax + w + 1] (the chunk's candidate range), built while staging:
+// a cluster's candidate range is then two table reads instead of two binary
+// searches.  Ranges longer than the table fall back to the searches.
+constexpr int kCaIdx = 1024;
 static_assert(kCaThreads >= 128 && kCaThreads % 32 == 0, "four warps compute the four slice bounds");
 
 struct Slice {
@@ -78,6 +83,7 @@ __device__ __forceinline__ unsigned lb_slice(const int32_t* t, unsigned n, int v
 __global__ void __launch_bounds__(kCaThreads)
 k_ca_neighbours(DevGeom G, DevParams P, DevWork W) {
   __shared__ int32_t sm_t[2][kCaStage], sm_y[2][kCaStage], sm_z[2][kCaStage];
+  __shared__ uint16_t sm_idx[2][kCaIdx];
   __shared__ unsigned sm_rng[4];
   const unsigned long long n = n_clusters(W);
   const int R = G.n_rows, nsr = G.n_sectors * R;
@@ -120,16 +126,33 @@ k_ca_neighbours(DevGeom G, DevParams P, DevWork W) {
       }
       __syncthreads();
       Slice sl[2];
+      const int tmin = W.cl_t[cs], tmax = W.cl_t[ce - 1];
+      int tlo[2];
+      bool use_idx[2];
 #pragma unroll
       for (int k = 0; k < 2; k++) {
         const unsigned a = sm_rng[2 * k], b = sm_rng[2 * k + 1];
+        const int w = k == 0 ? wd : wu;
         sl[k].base = a;
         sl[k].n = b > a ? b - a : 0;
+        tlo[k] = tmin - w;
+        const int R = tmax + w + 1 - tlo[k];           // table entries 0 .. R
+        use_idx[k] = sl[k].n <= (unsigned)kCaStage && R < kCaIdx;
         if (sl[k].n <= (unsigned)kCaStage) {
-          for (unsigned i = tid; i < sl[k].n; i += blockDim.x) {
-            sm_t[k][i] = W.cl_t[a + i];
-            sm_y[k][i] = W.cl_y[a + i];
-            sm_z[k][i] = W.cl_z[a + i];
+          // element i (and a virtual element n past the range) fills the table
+          // entries of the bins after its predecessor's time bin up to its own
+          for (unsigned i = tid; i <= sl[k].n; i += blockDim.x) {
+            const int ti = i < sl[k].n ? W.cl_t[a + i] : tmax + w + 2;
+            if (i < sl[k].n) {
+              sm_t[k][i] = ti;
+              sm_y[k][i] = W.cl_y[a + i];
+              sm_z[k][i] = W.cl_z[a + i];
+            }
+            if (use_idx[k]) {
+              const int tp = i > 0 ? W.cl_t[a + i - 1] : tlo[k] - 1;
+              const int b1 = min(ti - tlo[k], R);
+              for (int bb = max(tp + 1 - tlo[k], 0); bb <= b1; bb++) sm_idx[k][bb] = (uint16_t)i;
+            }
           }
           sl[k].t = sm_t[k]; sl[k].y = sm_y[k]; sl[k].z = sm_z[k];
         } else {
@@ -141,20 +164,23 @@ k_ca_neighbours(DevGeom G, DevParams P, DevWork W) {
       if (c < ce) {
         const int Yc = W.cl_y[c], Zc = W.cl_z[c];
         const int tc = W.cl_t[c];
-        const unsigned d0 = lb_slice(sl[0].t, sl[0].n, tc - wd);
-        const unsigned u0 = lb_slice(sl[1].t, sl[1].n, tc - wu);
+        // candidate ranges [d0, d1), [u0, u1): the clusters within the time window
+        const unsigned d0 = use_idx[0] ? sm_idx[0][tc - wd - tlo[0]] : lb_slice(sl[0].t, sl[0].n, tc - wd);
+        const unsigned d1 = use_idx[0] ? sm_idx[0][tc + wd + 1 - tlo[0]] : lb_slice(sl[0].t, sl[0].n, tc + wd + 1);
+        const unsigned u0 = use_idx[1] ? sm_idx[1][tc - wu - tlo[1]] : lb_slice(sl[1].t, sl[1].n, tc - wu);
+        const unsigned u1 = use_idx[1] ? sm_idx[1][tc + wu + 1 - tlo[1]] : lb_slice(sl[1].t, sl[1].n, tc + wu + 1);
         // candidates passing the window cuts, in ascending index order
         constexpr int kMaxCand = 8;
         unsigned di[kMaxCand], ui[kMaxCand];
         int nd = 0, nu = 0;
         bool spill = false;
-        for (unsigned i = d0; i < sl[0].n && sl[0].t[i] <= tc + wd; i++) {
+        for (unsigned i = d0; i < d1; i++) {
           if (abs(Yc - sl[0].y[i]) > yld) continue;
           if (abs(Zc - sl[0].z[i]) > zld) continue;
           if (nd < kMaxCand) di[nd] = i; else spill = true;
           nd++;
         }
-        for (unsigned j = u0; nd > 0 && j < sl[1].n && sl[1].t[j] <= tc + wu; j++) {
+        for (unsigned j = u0; nd > 0 && j < u1; j++) {
           if (abs(sl[1].y[j] - Yc) > ylu) continue;
           if (abs(sl[1].z[j] - Zc) > zlu) continue;
           if (nu < kMaxCand) ui[nu] = j; else spill = true;
