@@ -71,6 +71,23 @@ __device__ __forceinline__ unsigned warp_lower_bound(const int32_t* __restrict__
   return m ? min(lo + (unsigned)(__ffs(m) - 1), hi) : hi;
 }
 
+// The same search when the answer is most likely within 512 elements of lo
+// (the chunk after a chunk whose bound was lo): one round probes [lo, lo + 512)
+// at stride 16 and, if the bound lies there, one more finishes it.
+__device__ __forceinline__ unsigned warp_lower_bound_near(const int32_t* __restrict__ t, unsigned lo, unsigned hi, int v) {
+  const unsigned lane = threadIdx.x & 31;
+  if (hi - lo > 512) {
+    const unsigned idx = lo + lane * 16;
+    const bool ge = __ldg(t + idx) >= v;                 // idx < lo + 512 < hi
+    const unsigned m = __ballot_sync(0xffffffffu, ge);
+    if (m == 0) return warp_lower_bound(t, lo + 31 * 16 + 1, hi, v);
+    const unsigned f = (unsigned)(__ffs(m) - 1);
+    if (f == 0) return lo;
+    return warp_lower_bound(t, lo + (f - 1) * 16 + 1, lo + f * 16, v) ;
+  }
+  return warp_lower_bound(t, lo, hi, v);
+}
+
 __device__ __forceinline__ unsigned lb_slice(const int32_t* t, unsigned n, int v) {
   unsigned lo = 0, hi = n;
   while (lo < hi) {
@@ -121,7 +138,10 @@ k_ca_neighbours(DevGeom G, DevParams P, DevWork W) {
         const int tmin = W.cl_t[cs], tmax = W.cl_t[ce - 1];
         const unsigned a = side == 0 ? dlo : ulo, b = side == 0 ? dhi : uhi;
         const int w = side == 0 ? wd : wu;
-        const unsigned bound = warp_lower_bound(W.cl_t, a, b, (q & 1) ? tmax + w + 1 : tmin - w);
+        // the bounds only grow from chunk to chunk: start from the previous one
+        const unsigned a1 = cs == lo ? a : max(a, min(sm_rng[q], b));
+        const unsigned bound = warp_lower_bound_near(W.cl_t, a1, b, (q & 1) ? tmax + w + 1 : tmin - w);
+        __syncwarp();
         if ((tid & 31) == 0) sm_rng[q] = bound;
       }
       __syncthreads();
