@@ -170,11 +170,17 @@ __global__ void k_ent_hist(DevWork W, CmpWork C, EntWork E) {
   __syncthreads();
   unsigned long long n = W.ctr[CTR_NCL];
   if (n > W.cap_cl) n = W.cap_cl;
-  for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
+  // most codes fall in a few bins: lanes holding the same symbol add once
+  // (their leader adds their number), so the shared counters see few atomics
+  const unsigned long long n_pad = (n + 31) & ~31ull;
+  const int lane = threadIdx.x & 31;
+  for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n_pad;
        i += (unsigned long long)gridDim.x * blockDim.x) {
-    if (C.status[i] != 1) continue;
-    atomicAdd(&h[(int)C.code_y[i] + 128], 1u);
-    atomicAdd(&h[256 + (int)C.code_z[i] + 128], 1u);
+    const bool coded = i < n && C.status[i] == 1;
+    const int sy = coded ? (int)C.code_y[i] + 128 : -1, sz = coded ? 256 + (int)C.code_z[i] + 128 : -1;
+    const unsigned my = __match_any_sync(0xffffffffu, sy), mz = __match_any_sync(0xffffffffu, sz);
+    if (coded && (__ffs(my) - 1) == lane) atomicAdd(&h[sy], (unsigned)__popc(my));
+    if (coded && (__ffs(mz) - 1) == lane) atomicAdd(&h[sz], (unsigned)__popc(mz));
   }
   __syncthreads();
   for (int i = threadIdx.x; i < 512; i += blockDim.x)

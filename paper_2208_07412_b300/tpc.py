@@ -371,10 +371,11 @@ def tpc_get_compressed(ctx, ticket: int, n_clusters: int):
     return cy[:n_clusters], cz[:n_clusters], st[:n_clusters]
 
 
-def tpc_entropy_encode(ctx, ticket: int, codes=None):
+def tpc_entropy_encode(ctx, ticket: int, codes=None, fetch: bool = True):
     """Step 10c on a finished ticket: (lengths [2, 256], n_bits, words).
     codes: None for the ticket's step-10 codes, or (code_y, code_z, status)
-    arrays of n_clusters entries that replace them."""
+    arrays of n_clusters entries that replace them.  fetch=False encodes
+    without copying the stream to host memory (words is then None)."""
     L = load()
     nb = _u64()
     lens = np.zeros(512, np.uint8)
@@ -386,6 +387,8 @@ def tpc_entropy_encode(ctx, ticket: int, codes=None):
     ptrs = [a.ctypes.data if a is not None else None for a in keep]
     _check(L.tpc_entropy_encode(ctx, ticket, *ptrs, lens.ctypes.data, ctypes.byref(nb), None, 0))
     n = int(nb.value)
+    if not fetch:
+        return lens.reshape(2, 256), n, None
     words = np.zeros(max(1, (n + 31) // 32), np.uint32)
     _check(L.tpc_entropy_encode(ctx, ticket, None, None, None, None, ctypes.byref(nb), words.ctypes.data,
                                 len(words)))
