@@ -371,9 +371,12 @@ __global__ void k_chain_rows(DevGeom G, DevWork W) {
   const unsigned long long nch = min(W.ctr[CTR_NCH], (unsigned long long)W.cap_ch);
   const int R = G.n_rows;
   const long long nsr = (long long)G.n_sectors * R;
+  const long long NB = 4LL * G.n_frag + 1, nkeys = nsr * NB;
   if (nch == 0) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i <= nsr; i += (long long)gridDim.x * blockDim.x)
       W.ch_row_start[i] = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i <= nkeys; i += (long long)gridDim.x * blockDim.x)
+      W.ch_bucket[i] = 0;
     return;
   }
   for (unsigned long long k = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; k < nch;
@@ -388,6 +391,16 @@ __global__ void k_chain_rows(DevGeom G, DevWork W) {
     for (long long i = prev + 1; i <= sr && i <= nsr; i++) W.ch_row_start[i] = (uint32_t)k;
     if (k == nch - 1)
       for (long long i = sr + 1; i <= nsr; i++) W.ch_row_start[i] = (uint32_t)nch;
+    // the same over (row, 64-bin bucket of the root's time bin) keys, which
+    // follow the chain order too
+    auto key_of = [&](unsigned long long kk, long long srk) {
+      return srk * NB + min((long long)(W.ch_t[kk] >> 6), NB - 1);
+    };
+    const long long key = key_of(k, sr);
+    const long long kprev = k > 0 ? key_of(k - 1, prev) : -1;
+    for (long long i = kprev + 1; i <= key && i <= nkeys; i++) W.ch_bucket[i] = (uint32_t)k;
+    if (k == nch - 1)
+      for (long long i = key + 1; i <= nkeys; i++) W.ch_bucket[i] = (uint32_t)nch;
   }
 }
 

@@ -17,7 +17,7 @@
 
 namespace tpc {
 
-constexpr int kAhead = 8;   // clusters loaded ahead of the one being fitted
+constexpr int kAhead = 4;   // clusters loaded ahead of the one being fitted
 
 template <int kThreads>
 __global__ void __launch_bounds__(kThreads)

@@ -36,14 +36,6 @@ __device__ __forceinline__ bool extrap_res_within(long long x1, long long y1, lo
   r = n / d;
   return true;
 }
-__device__ __forceinline__ unsigned lower_bound_tm(const int32_t* __restrict__ t, unsigned lo, unsigned hi, long long v) {
-  while (lo < hi) {
-    unsigned mid = (lo + hi) >> 1;
-    if ((long long)__ldg(t + mid) < v) lo = mid + 1; else hi = mid;
-  }
-  return lo;
-}
-
 __global__ void k_merge_cand(DevGeom G, DevParams P, DevWork W) {
   const unsigned long long nch = n_chains_m(W);
   const int ngap = P.gap_max - P.gap_min + 1;
@@ -66,8 +58,12 @@ __global__ void k_merge_cand(DevGeom G, DevParams P, DevWork W) {
     const long long tlo = floordiv_ll(zp - MC - 2, 640) - 3;
     const long long thi = floordiv_ll(zp + MC + 2, 640) + 3;
     // the chains whose bottom (root) cluster lies in row rb, by root time bin
-    const unsigned lo = W.ch_row_start[s * R + rb], hi = W.ch_row_start[s * R + rb + 1];
-    for (unsigned kb = lower_bound_tm(W.ch_t, lo, hi, tlo); kb < hi; kb++) {
+    const unsigned hi = W.ch_row_start[s * R + rb + 1];
+    // the first chain at or past time bin tlo: from its 64-bin bucket's first chain
+    const long long NB = 4LL * G.n_frag + 1;
+    unsigned kb0 = W.ch_bucket[(long long)(s * R + rb) * NB + (tlo < 0 ? 0 : min(tlo >> 6, NB - 1))];
+    while (kb0 < hi && (long long)__ldg(W.ch_t + kb0) < tlo) kb0++;
+    for (unsigned kb = kb0; kb < hi; kb++) {
       if ((long long)__ldg(W.ch_t + kb) > thi) break;
       const int b1 = W.ch_root[kb];
       const int b2 = W.ch_b2[kb];

@@ -247,7 +247,7 @@ static size_t slot_bytes(uint64_t pages, uint64_t windows, uint64_t cap_cl, uint
              cap_runs * 8 + cap_cl * (16 + 16 + 16 + 8 + 8 + 8 + 8 + 4 + 8 + 4 + 4 + 4 + 4) +
              (scan_tiles(cap_cl) + scan_tiles(cap_ch) + scan_tiles(windows * kUnitsPerWindow)) * 8 +
              cap_ch * (14 * 4 + 8 + 16 + sizeof(tpc_track) + 4 * 12) +
-             (size_t)(nsr + 1) * 8 + 1024;
+             (size_t)(nsr + 1) * 8 + (size_t)(4 * windows + nsr + 2) * 4 + 1024;
   return b;
 }
 
@@ -307,7 +307,9 @@ static tpc_status slot_reserve(tpc_context* ctx, Slot& s, uint64_t pages_bytes, 
   CUDA_TRY(ensure(s.scanst,
                   (scan_tiles(s.cap_cl) + scan_tiles(s.cap_ch) + scan_tiles(s.cap_windows * kUnitsPerWindow)) * 8));
   CUDA_TRY(ensure(s.rowstart, (size_t)(nsr + 1) * 4));
-  CUDA_TRY(ensure(s.chrow, (size_t)(nsr + 1) * 4));
+  // first chain per row, then per (row, 64-bin time bucket): 4 buckets per
+  // fragment and one past the last, nsr * (4 n_frag + 1) + 1 entries
+  CUDA_TRY(ensure(s.chrow, (size_t)(nsr + 1) * 4 + (size_t)(4 * s.cap_windows + nsr + 2) * 4));
   if (want_dense) CUDA_TRY(ensure(s.dense, want_dense));
   CUDA_TRY(ensure(s.ctrl, 256));
   CUDA_TRY(ensure(s.lenhist, 512 * 4));
@@ -319,6 +321,7 @@ static tpc_status slot_reserve(tpc_context* ctx, Slot& s, uint64_t pages_bytes, 
   W.cl_x = (int32_t*)s.clx.p; W.cl_y = (int32_t*)s.cly.p; W.cl_z = (int32_t*)s.clz.p; W.cl_t = (int32_t*)s.clt.p;
   W.row_start = (uint32_t*)s.rowstart.p;
   W.ch_row_start = (uint32_t*)s.chrow.p;
+  W.ch_bucket = (uint32_t*)s.chrow.p + (nsr + 1);
   W.dense = (ctx->flags & TPC_CTX_DENSE_FINDER) ? (uint16_t*)s.dense.p : nullptr;
   W.dense_stride = (uint32_t)dstride;
   W.win_state = (unsigned long long*)s.winstate.p;

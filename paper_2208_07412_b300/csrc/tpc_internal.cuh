@@ -120,6 +120,8 @@ struct DevWork {
   int32_t* ch_root; int32_t* ch_len; int32_t* ch_b2; int32_t* ch_top; int32_t* ch_top2;
   int32_t* ch_t;                 // t_peak of the chain's root (bottom) cluster
   uint32_t* ch_row_start;        // [n_sectors * n_rows + 1] first chain whose root lies in each row
+  uint32_t* ch_bucket;           // [n_sectors * n_rows * (4 n_frag + 1) + 1] first chain whose root lies in
+                                 // each (row, 64-bin bucket of its time bin) or later
   int32_t* ch_next; int32_t* ch_prev;
   unsigned long long* best_b;
   unsigned long long* best_a;    // [2 * cap_chains]
