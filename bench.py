@@ -554,8 +554,9 @@ def calibration_stats(tpc, R, pages_d, offs_d, tf, reps=5):
 
 def finder_variants(tpc, torch, tf, pages_d, offs_d, flush, main_ms, reps=5):
     """The measured variants of steps 1-4 beside the default two-pass finder
-    (pages decoded into 4-byte digit words in device memory, then each 64-bin
-    time chunk of a window clustered in a small shared plane): the fused
+    (pages decoded into 8-byte pad-run records in device memory, then each
+    64-bin time chunk of a window expanded into a small shared plane and
+    clustered there): the fused
     finder (each window's pages decoded straight into a shared plane of the
     whole window) and the dense-plane finder (a decode pass writes a dense
     (sector row, time bin, pad) ADC plane to device memory, a find pass reads it

@@ -110,9 +110,10 @@ typedef int32_t tpc_status;
 #define TPC_CTX_FUSED_FINDER 8u   /* steps 1-4 as the fused variant: each window's pages decoded straight
                                      into a shared-memory plane of the whole window and clustered there.
                                      Without either flag the two-pass finder runs: every page decoded
-                                     into 4-byte digit words (pad, time bin, ADC) in device memory (about
-                                     1.7x the ZS bytes), then each 64-bin time chunk of a window clustered
-                                     in a small shared plane.  All three give the same clusters
+                                     into 8-byte pad-run records (pad, length, time bin, first digit) in
+                                     device memory (about 1.2x the ZS bytes), then each 64-bin time chunk
+                                     of a window expanded from its runs and the page's ADC words into a
+                                     small shared plane and clustered there.  All three give the same clusters
                                      (split_charge = 1 needs the two-pass finder). */
 
 /* Pipeline stages, in launch order (indices into tpc_get_stage_times). */

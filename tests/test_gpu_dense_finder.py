@@ -1,6 +1,6 @@
 """The finder variants of steps 1-4 against the default two-pass finder
-(pages decoded into digit words in device memory, then each 64-bin time chunk
-of a window clustered in a small shared plane): the fused variant (context
+(pages decoded into pad-run records in device memory, then each 64-bin time
+chunk of a window expanded into a small shared plane and clustered there): the fused variant (context
 flag TPC_CTX_FUSED_FINDER: each window decoded straight into a shared plane of
 the whole window) and the dense-plane variant (TPC_CTX_DENSE_FINDER: pages
 decoded into a dense (sector row, time bin, pad) plane in device memory,
