@@ -677,6 +677,28 @@ def fit_roofline(n_cl_on_tracks, fit_ms, fma_peak):
                          "nominal 148 SMs x 128 lanes x 2 x 2032 MHz"}
 
 
+# ncu --set full counters of k_ca_neighbours (the CA stage's main kernel) on
+# full_tpc, seed 1 (profiles/k_ca_neighbours_full_tpc.md): L2 throughput
+# (lts__throughput, % of peak), L2 sector rate, warp efficiency (threads per
+# warp instruction / 32), issue active.  Must be cleared whenever the kernel
+# changes.
+CA_COUNTERS = {"workload": "full_tpc seed 1", "l2_throughput_pct_of_peak": 7.80, "l2_sectors_per_ns": 54.0,
+               "lts_hit_rate_pct": 53.7, "warp_efficiency": 19.13 / 32, "issue_active_pct": 49.5,
+               "warps_active_pct": 44.7}
+
+
+def ca_roofline(n_cl, ca_ms, hbm):
+    """The CA stage (steps 5-6): irregular, latency-bound.  Algorithmic bytes
+    ~32 per cluster (coordinates in, up / down / score and chain data out) over
+    the stage's CUDA-event time, against the measured HBM rate for scale; with
+    the L2 throughput and warp efficiency of an ncu capture of k_ca_neighbours."""
+    alg = 32 * n_cl
+    achieved = alg / (ca_ms * 1e-3) / 1e9
+    return {"kernel": "CA stage: k_ca_neighbours + edge rows + links + chains", "bound": "latency",
+            "achieved": achieved, "unit": "GB/s", "peak": hbm, "frac": achieved / hbm,
+            "algorithmic_bytes_per_launch": int(alg), "ncu_k_ca_neighbours": CA_COUNTERS}
+
+
 def extra_workload(tpc, torch, local, name, seed, steps, warmup, flush, hbm, peak_kind, fma_peak):
     """A second workload measured like the main one (device-resident pages, L2
     flushed before every step, CUDA events on the library's stream, the
@@ -719,6 +741,7 @@ def extra_workload(tpc, torch, local, name, seed, steps, warmup, flush, hbm, pea
             "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
             "stages_ms": stages, "roofline": roof, "roofline_issue": issue,
             "roofline_fit": fit_roofline(ctr["clusters_on_tracks"], stages["fit"], fma_peak),
+            "roofline_ca": ca_roofline(ctr["clusters"], stages["ca"], hbm),
             "tuning": tuning, "steps": steps, "warmup": warmup,
             "timing": "CUDA events on the library's stream, L2 flushed before every step"}
 
@@ -889,6 +912,7 @@ def run_ours(args, world, rank, local):
             "roofline": roof,
             "roofline_issue": issue,
             "roofline_fit": fit_roofline(ctr["clusters_on_tracks"], stages["fit"], fma_peak),
+            "roofline_ca": ca_roofline(n_cl, stages["ca"], hbm),
             "e2e": {"value": cl_all / e2e_s_max, "unit": "clusters/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h),
                     "path": "submit from pinned host pages, read clusters, tracks and map back into pinned "
