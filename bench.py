@@ -815,8 +815,19 @@ def run_ours(args, world, rank, local):
     cl_all, tr_all, dev_s_max = job_totals(world, n_cl, n_tr, args.steps, sum(step_ms) / 1e3)
     stages = {k: statistics.mean(r[3][k] for r in recs) for k in tpc.STAGES}
     launches = sum(r[2]["kernel_launches"] for r in recs)
+    # the optional steps on the device context's last timeframe, before its
+    # memory goes to the end-to-end contexts below
+    extras = {}
+    if rank == 0 and world == 1 and args.workload in ("full_tpc", "continuous_50khz"):
+        extras["cross_sector"] = cross_sector_timing(tpc, torch, R, pages_d, offs_d, tf)
+        extras["compression"] = compression_stats(tpc, R, pages_d, offs_d, tf)
+    if rank == 0 and world == 1 and args.workload == "full_tpc":   # one collision: its vertex time
+        extras["calibration"] = calibration_stats(tpc, R, pages_d, offs_d, tf)
+    R.close()
 
-    # ---- end to end through the C ABI with host (pinned) buffers
+    # ---- end to end through the C ABI with host (pinned) buffers, on a
+    # context of three slots with the memory left (at 55,000 bins a slot holds
+    # ~95 GB: two fit, and the third submit queues)
     pages_h = torch.from_numpy(tf.pages).pin_memory()
     offs_h = torch.from_numpy(tf.page_offsets.view(np.int64)).pin_memory()
     # results land in pinned host memory, like the inputs
@@ -827,12 +838,18 @@ def run_ours(args, world, rank, local):
     L = tpc.load()
     n = ctypes.c_uint64()
 
+    free_now, _ = torch.cuda.mem_get_info()
+    depth = 3
+    Rp = tpc.Reconstructor.for_timeframe(tf, device=local, flags=flags & ~tpc.TPC_CTX_STAGE_TIMING,
+                                         mem_budget=int(free_now * 0.85), n_slots=depth)
+    tpc.tpc_set_tuning(Rp.ctx, **tuning)
+
     def e2e_step():
-        t = R.submit(pages_h, offs_h, tf.n_time_bins)
-        R.wait(t)
-        L.tpc_get_clusters(R.ctx, t, cl_buf.data_ptr(), max(n_cl, 1), ctypes.byref(n))
-        L.tpc_get_tracks(R.ctx, t, tr_buf.data_ptr(), max(n_tr, 1), ctypes.byref(n), map_buf.data_ptr())
-        tpc.tpc_release(R.ctx, t)
+        t = Rp.submit(pages_h, offs_h, tf.n_time_bins)
+        Rp.wait(t)
+        L.tpc_get_clusters(Rp.ctx, t, cl_buf.data_ptr(), max(n_cl, 1), ctypes.byref(n))
+        L.tpc_get_tracks(Rp.ctx, t, tr_buf.data_ptr(), max(n_tr, 1), ctypes.byref(n), map_buf.data_ptr())
+        tpc.tpc_release(Rp.ctx, t)
 
     for _ in range(max(1, args.warmup)):
         e2e_step()
@@ -845,15 +862,9 @@ def run_ours(args, world, rank, local):
         e2e_t.append(time.perf_counter() - t0)
     e2e_seq_s_max = max_over_ranks(world, sum(e2e_t))
 
-    # ---- end to end, pipelined: three slots, so that the next timeframes'
-    # host->device copies and kernels overlap this one's device->host read-back
-    # (a budget from the memory left: if two slots do not fit, the second
-    # submit queues and the loop degrades to one timeframe at a time)
-    free_now, _ = torch.cuda.mem_get_info()
-    depth = 3
-    Rp = tpc.Reconstructor.for_timeframe(tf, device=local, flags=flags & ~tpc.TPC_CTX_STAGE_TIMING,
-                                         mem_budget=int(free_now * 0.85), n_slots=depth)
-    tpc.tpc_set_tuning(Rp.ctx, **tuning)
+    # ---- end to end, pipelined: the next timeframes submitted before this one
+    # is read back, so that their host->device copies and kernels overlap its
+    # device->host read-back (slots that do not fit the budget queue)
 
     def fetch(t):
         Rp.wait(t)
@@ -916,17 +927,13 @@ def run_ours(args, world, rank, local):
             "e2e": {"value": cl_all / e2e_s_max, "unit": "clusters/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h),
                     "path": "submit from pinned host pages, read clusters, tracks and map back into pinned "
-                            "memory; three slots, the next two timeframes submitted before this one is read back",
+                            "memory; a context of three slots within the memory left (slots that do not fit queue), "
+                            "the next two timeframes submitted before this one is read back",
                     "sequential_value": cl_all / e2e_seq_s_max},
             "clocks": clk.summary(),
             "gpu_launches": int(launches),
         }
-        if world == 1 and args.workload in ("full_tpc", "continuous_50khz"):
-            line["cross_sector"] = cross_sector_timing(tpc, torch, R, pages_d, offs_d, tf)
-            line["compression"] = compression_stats(tpc, R, pages_d, offs_d, tf)
-        if world == 1 and args.workload == "full_tpc":   # one collision: its vertex time
-            line["calibration"] = calibration_stats(tpc, R, pages_d, offs_d, tf)
-        R.close()   # its slot's memory goes to the comparisons below
+        line.update(extras)
         if world == 1 and not (args.no_variants or args.dense_finder or args.fused_finder) and \
                 args.workload in ("full_tpc", "continuous_50khz"):
             line["finder_variants"] = finder_variants(tpc, torch, tf, pages_d, offs_d, flush, stages["find"])
@@ -953,7 +960,6 @@ def run_ours(args, world, rank, local):
             line["cpu_baseline_all_cores"] = {"value": pb["clusters"] / pb["times"][0], "unit": "clusters/s",
                                               "cores": pb["cores"], "kind": "oracle", "sample": pb["sample"]}
         print(json.dumps(line), flush=True)
-    R.close()
 
 
 def main():
