@@ -765,7 +765,7 @@ def run_ours(args, world, rank, local):
     flags = tpc.TPC_CTX_STAGE_TIMING | (tpc.TPC_CTX_NO_GRAPHS if args.no_graphs else 0) | \
         (tpc.TPC_CTX_DENSE_FINDER if args.dense_finder else 0) | (tpc.TPC_CTX_FUSED_FINDER if args.fused_finder else 0)
     # device memory for one slot: the pages, ~150 B per cluster of capacity
-    # (pages/12 clusters) and the rest; the budget is what the GPU has free
+    # (pages/20 clusters) and the rest; the budget is what the GPU has free
     free_b, _ = torch.cuda.mem_get_info()
     budget = int(min(free_b * 0.85, max(16 << 30, 40 * tf.pages.nbytes)))
     R = tpc.Reconstructor.for_timeframe(tf, device=local, stream=stream.cuda_stream,

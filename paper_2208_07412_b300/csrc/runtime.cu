@@ -637,6 +637,14 @@ static uint64_t guaranteed_cap_cl(uint64_t pages_bytes) {
   return pages_bytes / 8 * 3 + 3 + 1024;
 }
 
+// The initial cluster capacity: one cluster per 20 page bytes (generated
+// timeframes hold one per 43-65 bytes); a denser timeframe overflows it, and
+// the pipeline re-runs once with the bound above.  At ~156 bytes of work space
+// per cluster of capacity, a 5.7 GB timeframe's slot needs ~45 GB for it.
+static uint64_t initial_cap_cl(uint64_t pages_bytes) {
+  return std::min(std::max<uint64_t>(65536, pages_bytes / 20), guaranteed_cap_cl(pages_bytes));
+}
+
 // Validation of one descriptor (before any slot is touched).
 static tpc_status check_desc(const tpc_timeframe_desc* tf) {
   if (tf->n_time_bins < 1 || tf->n_time_bins > 65535) return fail(TPC_E_INVAL, "n_time_bins out of range");
@@ -657,9 +665,7 @@ static tpc_status start_timeframe(tpc_context* ctx, Slot* s, const tpc_timeframe
   const unsigned nfrag = (tf->n_time_bins + kFrag - 1) / kFrag;
   const uint64_t nwin = (uint64_t)ctx->geom.n_sectors * ctx->geom.n_rows * nfrag;
   if (nwin > 0xffffffffull) return fail(TPC_E_INVAL, "too many windows");
-  uint64_t cap_cl = std::max<uint64_t>(65536, tf->pages_bytes / 12);
-  cap_cl = std::min(cap_cl, guaranteed_cap_cl(tf->pages_bytes));
-  cap_cl = std::max(cap_cl, s->cap_cl);
+  const uint64_t cap_cl = std::max(initial_cap_cl(tf->pages_bytes), s->cap_cl);
   tpc_status st = slot_reserve(ctx, *s, tf->pages_bytes, nwin, cap_cl, !dev_in);
   if (st) return st;
   s->pages_bytes = tf->pages_bytes;
@@ -700,9 +706,7 @@ static tpc_status start_batch(tpc_context* ctx, Slot* s, const tpc_timeframe_des
   if (nwin > 0xffffffffull) return fail(TPC_E_INVAL, "too many windows");
   if (!s->h_ev) CUDA_TRY(cudaMallocHost((void**)&s->h_ev, kEvBytes));
   CUDA_TRY(ensure(s->evinfo, kEvBytes));
-  uint64_t cap_cl = std::max<uint64_t>(65536, total / 12);
-  cap_cl = std::min(cap_cl, guaranteed_cap_cl(total));
-  cap_cl = std::max(cap_cl, s->cap_cl);
+  const uint64_t cap_cl = std::max(initial_cap_cl(total), s->cap_cl);
   s->n_events = n_events;
   tpc_status st = slot_reserve(ctx, *s, total, nwin, cap_cl, true);
   if (st) { s->n_events = 1; return st; }
