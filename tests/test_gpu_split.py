@@ -84,3 +84,16 @@ def test_other_finders_refuse(lib):
     p.split_charge = 2
     with pytest.raises(lib.TpcError):
         lib.Reconstructor.for_timeframe(tf, params=p)
+
+
+def test_batch_equals_oracle(lib):
+    """Uneven events in one batched run (the (event, sector) axis): each event's
+    clusters and tracks are the oracle's with charge splitting on."""
+    tfs = [tpcgen.generate(tpcgen.single_sector(s, n_tracks=n)) for s, n in [(11, 40), (12, 400), (13, 150)]]
+    with lib.Reconstructor.for_timeframe(tfs[0], params=params(lib)) as R:
+        batch = R.run_batch(tfs)
+    for tf, ev in zip(tfs, batch):
+        orc = oracle.reconstruct(tf, oracle.OracleParams(split_charge=True))
+        assert ev["clusters"].tobytes() == orc.clusters.tobytes()
+        assert np.array_equal(ev["cl2trk"], orc.cl2trk)
+        assert np.array_equal(ev["tracks"]["first_cluster"], orc.track_first)
