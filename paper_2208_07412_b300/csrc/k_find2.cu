@@ -243,7 +243,7 @@ __global__ void k_unit_descs(DevGeom G, DevWork W, unsigned int n_units) {
         const unsigned long long ws = (unsigned long long)w + k - 1;
         const uint4 a = W.dtab[3ull * ws], b = W.dtab[3ull * ws + 1], cc = W.dtab[3ull * ws + 2];
         uint32_t lo, hi;
-        if (k == 0) { lo = tab_run(b, a.z, 7); hi = a.z; }
+        if (k == 0) { lo = tab_run(b, a.z, 2 * kUnitsPerWin - 1); hi = a.z; }
         else if (k == 1) {
           lo = tab_run(b, a.z, c == 0 ? -1 : 2 * c - 1);
           hi = tab_run(b, a.z, c == kUnitsPerWin - 1 ? 8 : 2 * c + 2);
@@ -719,9 +719,9 @@ cudaError_t launch_find2(const DevGeom& G, const DevParams& P, const DevWork& W,
     const unsigned gdesc = (unsigned)std::min<unsigned long long>((n_units + 255ull) / 256ull, (unsigned long long)n_sm * 8);
     k_unit_descs<<<gdesc ? gdesc : 1, 256, 0, st>>>(G, W, n_units);
   }
-  const size_t sm = find2_smem_bytes(G.npmax, split);
   const bool ns = P.ns_min_dip > 0;
   const int nt = L.find_threads == 256 ? 256 : 128;
+  const size_t sm = find2_smem_bytes(G.npmax, split);
   const void* fn = units_kernel(nt, ns, split);
   // CTAs that are all resident at once (each takes every gridDim.x-th unit)
   int per_sm = 0;
