@@ -38,19 +38,29 @@ __device__ __forceinline__ bool parse_header(const uint4* p, uint64_t off, uint6
   return true;
 }
 
-__device__ __forceinline__ int floordiv32(int n, int d) {   // d > 0
-  int q = n / d;
-  if ((n % d) != 0 && n < 0) q -= 1;
+// floor(n / d) for d > 0 and |n / d| < 2^20: a float quotient, corrected
+// exactly in integers (its error is far below one).
+__device__ __forceinline__ int floordiv32(int n, int d) {
+  int q = (int)floorf(__fdividef((float)n, (float)d));
+  while (q * d > n) q--;
+  while ((q + 1) * d <= n) q++;
   return q;
 }
-// min(255, R(num, den)) for 0 <= num, 0 < den < 2^31: a float quotient,
-// corrected exactly in integers (the quotient is at most 256 here).
+// min(255, R(num, den)) for 0 <= num, 0 < den < 2^31: a float quotient f of
+// (2 num + den) / (2 den), whose relative error (operands rounded to float,
+// approximate division) stays below 3e-7, i.e. below 1e-4 for quotients up to
+// 256; its floor is exact unless f lies within 1e-3 of an integer, where the
+// quotient is corrected in 64-bit integers.
 __device__ __forceinline__ int round_half_up_sat255(long long num, long long den) {
-  if (num >= 255LL * den + den / 2 + den) return 255;
   const long long n2 = 2 * num + den, d2 = 2 * den;
-  long long q = (long long)floorf((float)n2 / (float)d2);
-  while (q * d2 > n2) q--;
-  while ((q + 1) * d2 <= n2) q++;
+  const float f = __fdividef((float)n2, (float)d2);
+  if (f >= 256.0f) return 255;
+  long long q = (long long)f;
+  const float fr = f - (float)q;
+  if (fr < 1e-3f || fr > 0.999f) {
+    while (q > 0 && q * d2 > n2) q--;
+    while ((q + 1) * d2 <= n2) q++;
+  }
   return (int)min(q, 255LL);
 }
 
@@ -98,7 +108,9 @@ template <bool kW>
 __device__ __forceinline__ void cluster_record_t(const int (&q)[5][5], const int (&w)[5][5], bool other, int np,
                                                  int T, int s, int r, int f, int tt, int p, int xrow, uint4& rec,
                                                  int4& xyz) {
-  int Q = 0, Sp = 0, St = 0, Spp = 0, Stt = 0;
+  // included weights summed per pad column (cs) and per time row (rs): the
+  // moments are then a few weighted sums of the five of each
+  int cs[5] = {0, 0, 0, 0, 0}, rs[5] = {0, 0, 0, 0, 0};
   bool excl = false, split = false;
 #pragma unroll
   for (int dt = -2; dt <= 2; dt++) {
@@ -114,9 +126,14 @@ __device__ __forceinline__ void cluster_record_t(const int (&q)[5][5], const int
       }
       const int x = kW ? w[dt + 2][dp + 2] : v;
       if (kW) split |= inc && x != v;
-      if (inc) { Q += x; Sp += x * dp; St += x * dt; Spp += x * dp * dp; Stt += x * dt * dt; }
+      const int xi = inc ? x : 0;
+      cs[dp + 2] += xi;
+      rs[dt + 2] += xi;
     }
   }
+  const int Q = cs[0] + cs[1] + cs[2] + cs[3] + cs[4];
+  const int Sp = 2 * (cs[4] - cs[0]) + cs[3] - cs[1], Spp = 4 * (cs[4] + cs[0]) + cs[3] + cs[1];
+  const int St = 2 * (rs[4] - rs[0]) + rs[3] - rs[1], Stt = 4 * (rs[4] + rs[0]) + rs[3] + rs[1];
   const int t_in = tt - kHalo;
   const int t = kFrag * f + t_in;
   const int pad_fp = 256 * p + floordiv32(512 * Sp + Q, 2 * Q);

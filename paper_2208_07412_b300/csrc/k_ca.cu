@@ -102,6 +102,7 @@ k_ca_neighbours(DevGeom G, DevParams P, DevWork W) {
   __shared__ int32_t sm_t[2][kCaStage], sm_y[2][kCaStage], sm_z[2][kCaStage];
   __shared__ uint16_t sm_idx[2][kCaIdx];
   __shared__ unsigned sm_rng[4];
+  __shared__ int sm_tmm[2];                      // the chunk's first and last time bins
   const unsigned long long n = n_clusters(W);
   const int R = G.n_rows, nsr = G.n_sectors * R;
   const int tid = threadIdx.x;
@@ -131,11 +132,17 @@ k_ca_neighbours(DevGeom G, DevParams P, DevWork W) {
     const unsigned ulo = min((unsigned long long)W.row_start[sr + 1], n), uhi = min((unsigned long long)W.row_start[sr + 2], n);
     for (unsigned cs = lo; cs < hi; cs += kCaChunk) {
       const unsigned ce = min(cs + kCaChunk, hi);
+      // this thread's cluster, loaded before the bounds and the staging so
+      // that its latency overlaps theirs
+      const unsigned c = cs + tid;
+      int Yc = 0, Zc = 0, tc = 0;
+      if (c < ce) { Yc = W.cl_y[c]; Zc = W.cl_z[c]; tc = W.cl_t[c]; }
       if (tid < 128) {
         // slices of the neighbour rows that can pair with clusters [cs, ce):
         // warp q computes bound q (row below: 0, 1; row above: 2, 3)
         const int q = tid >> 5, side = q >> 1;
         const int tmin = W.cl_t[cs], tmax = W.cl_t[ce - 1];
+        if (tid == 0) { sm_tmm[0] = tmin; sm_tmm[1] = tmax; }
         const unsigned a = side == 0 ? dlo : ulo, b = side == 0 ? dhi : uhi;
         const int w = side == 0 ? wd : wu;
         // the bounds only grow from chunk to chunk: start from the previous one
@@ -146,7 +153,7 @@ k_ca_neighbours(DevGeom G, DevParams P, DevWork W) {
       }
       __syncthreads();
       Slice sl[2];
-      const int tmin = W.cl_t[cs], tmax = W.cl_t[ce - 1];
+      const int tmin = sm_tmm[0], tmax = sm_tmm[1];
       int tlo[2];
       bool use_idx[2];
 #pragma unroll
@@ -180,10 +187,7 @@ k_ca_neighbours(DevGeom G, DevParams P, DevWork W) {
         }
       }
       __syncthreads();
-      const unsigned c = cs + tid;
       if (c < ce) {
-        const int Yc = W.cl_y[c], Zc = W.cl_z[c];
-        const int tc = W.cl_t[c];
         // candidate ranges [d0, d1), [u0, u1): the clusters within the time window
         const unsigned d0 = use_idx[0] ? sm_idx[0][tc - wd - tlo[0]] : lb_slice(sl[0].t, sl[0].n, tc - wd);
         const unsigned d1 = use_idx[0] ? sm_idx[0][tc + wd + 1 - tlo[0]] : lb_slice(sl[0].t, sl[0].n, tc + wd + 1);

@@ -630,15 +630,16 @@ __global__ void __launch_bounds__(kThreads, 896 / kThreads)
         const int L = plist[j];
         const int row = L / ps, p = L - row * ps - kPad;
         int q[5][5];
-        bool other = false;
+        unsigned ring = 0;                             // the other 24 words ORed: a peak among them?
 #pragma unroll
         for (int dt = 0; dt < 5; dt++)
 #pragma unroll
           for (int dp = 0; dp < 5; dp++) {
             const uint16_t x = plane[L + (dt - 2) * ps + dp - 2];
             q[dt][dp] = x & kAdcMask;
-            if (dt != 2 || dp != 2) other |= (x & kPeakBit) != 0;
+            if (dt != 2 || dp != 2) ring |= x;
           }
+        const bool other = (ring & kPeakBit) != 0;
         uint4 rec;
         int4 xyz;
         if (kSplit) {
