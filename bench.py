@@ -58,9 +58,9 @@ REF_SAMPLE_BYTES = 20 << 20
 # scaled by the ZS bytes (the stage's traffic and instructions grow with the
 # pages and clusters).  Must be cleared whenever a finder kernel changes.
 FINDER_COUNTERS = {
-    ("full_tpc", "two_pass", 128): {"zs": 70336448, "dram": 210503168 + 36954880, "instr": 396996243},
-    ("continuous_50khz", "two_pass", 128): {"zs": 1173460064, "dram": 3448704256 + 2630252800,
-                                            "instr": 6110698624},
+    ("full_tpc", "two_pass", 128): {"zs": 70336448, "dram": 210552320 + 37405440, "instr": 391738998},
+    ("continuous_50khz", "two_pass", 128): {"zs": 1173460064, "dram": 3438739456 + 2626760192,
+                                            "instr": 5978795343},
 }
 # Warp-instruction issue peak: 148 SMs x 4 schedulers x 1 instruction per cycle
 # at the 2032 MHz maximum SM clock.
@@ -410,10 +410,11 @@ def serve_pass(tpc, R, pool, arrivals):
     return lat, time.perf_counter() - t0, ncl
 
 
-def run_serve(args, world, rank, local):
+def serve_measure(args, local):
     """Served vs plain sequential path under Poisson arrivals of timeframes
     mixing pp-like and Pb-Pb-like occupancy, inputs in pinned host memory
-    (each request is copied in when it is admitted)."""
+    (each request is copied in when it is admitted).  Returns the measurement
+    as a dict (the serve workload's line, without the common keys)."""
     import torch
     from paper_2208_07412_b300 import tpc
     torch.cuda.set_device(local)
@@ -454,10 +455,8 @@ def run_serve(args, world, rank, local):
         lat_p, span_p, ncl_p = serve_pass(tpc, Rp, pool, burst)
         lat_s, span_s, ncl_s = serve_pass(tpc, Rs, pool, burst)
     sizes = sorted(tf.pages.nbytes for tf, _, _ in pool)
-    line = {
-        "metric": METRIC, "value": ncl_s / span_s, "unit": "clusters/s", "n_gpus": 1, "steps": n_req,
-        "warmup": len(pool), "ms_per_step": 1e3 * span_s / n_req, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "i64+f32", "data": "synthetic",
+    return {
+        "n_req": n_req, "n_pool": len(pool), "span_s": span_s, "ncl_s": ncl_s,
         "config": {"workload": f"serve: pool of 8 pp-like (1 MHz, Poisson(30) tracks) + 8 Pb-Pb-like (50 kHz, "
                                f"floor(15000 U^7.82)) continuous timeframes of {min(bins)}-{max(bins)} time bins, "
                                f"{sizes[0] / 1e9:.2f}-{sizes[-1] / 1e9:.2f} GB ZS each, {n_req} requests drawn "
@@ -470,10 +469,21 @@ def run_serve(args, world, rank, local):
                        "served_latency_ms_p50": 1e3 * pct(lat_s, 50), "served_latency_ms_p99": 1e3 * pct(lat_s, 99),
                        "plain_latency_ms_p50": 1e3 * pct(lat_p, 50), "plain_latency_ms_p99": 1e3 * pct(lat_p, 99)},
         "poisson_sweep": points,
-        "e2e": {"value": ncl_s / span_s, "unit": "clusters/s",
-                "h2d_bytes_per_step": int(np.mean([pool[i][0].pages.nbytes + pool[i][0].page_offsets.nbytes
-                                                   for i in order])),
-                "d2h_bytes_per_step": 256},
+        "h2d_bytes_per_request": int(np.mean([pool[i][0].pages.nbytes + pool[i][0].page_offsets.nbytes
+                                              for i in order])),
+    }
+
+
+def run_serve(args, world, rank, local):
+    """The serve workload's own line (C5)."""
+    m = serve_measure(args, local)
+    line = {
+        "metric": METRIC, "value": m["ncl_s"] / m["span_s"], "unit": "clusters/s", "n_gpus": 1,
+        "steps": m["n_req"], "warmup": m["n_pool"], "ms_per_step": 1e3 * m["span_s"] / m["n_req"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i64+f32", "data": "synthetic",
+        "config": m["config"], "saturation": m["saturation"], "poisson_sweep": m["poisson_sweep"],
+        "e2e": {"value": m["ncl_s"] / m["span_s"], "unit": "clusters/s",
+                "h2d_bytes_per_step": m["h2d_bytes_per_request"], "d2h_bytes_per_step": 256},
     }
     print(json.dumps(line), flush=True)
 
@@ -682,9 +692,9 @@ def fit_roofline(n_cl_on_tracks, fit_ms, fma_peak):
 # (lts__throughput, % of peak), L2 sector rate, warp efficiency (threads per
 # warp instruction / 32), issue active.  Must be cleared whenever the kernel
 # changes.
-CA_COUNTERS = {"workload": "full_tpc seed 1", "l2_throughput_pct_of_peak": 7.80, "l2_sectors_per_ns": 54.0,
-               "lts_hit_rate_pct": 53.7, "warp_efficiency": 19.13 / 32, "issue_active_pct": 49.5,
-               "warps_active_pct": 44.7}
+CA_COUNTERS = {"workload": "full_tpc seed 1", "l2_throughput_pct_of_peak": 8.07, "l2_sectors_per_ns": 55.5,
+               "lts_hit_rate_pct": 53.6, "warp_efficiency": 19.17 / 32, "issue_active_pct": 51.3,
+               "warps_active_pct": 44.6}
 
 
 def ca_roofline(n_cl, ca_ms, hbm):
@@ -948,6 +958,10 @@ def run_ours(args, world, rank, local):
             line["batched"] = batched_vs_plain(tpc, torch, local,
                                                tuning=tuning if args.workload == "full_tpc"
                                                else line.get("full_tpc", {}).get("tuning"))
+        if world == 1 and not args.no_serve and args.workload == "continuous_50khz" and not args.time_bins:
+            # C5: served vs plain sequential under Poisson arrivals (the serve workload's figures)
+            m = serve_measure(args, local)
+            line["served"] = {k: m[k] for k in ("config", "saturation", "poisson_sweep")}
         if world == 1 and not args.no_cpu_baseline:
             cb = cpu_baseline(tf, 1)
             line["cpu_baseline"] = {"value": cb["clusters"] / cb["times"][0], "unit": "clusters/s", "cores": 1,
@@ -980,6 +994,8 @@ def main():
                     help="where the nvidia-smi clock samples of the timed region are written (default: the temp dir)")
     ap.add_argument("--no-graphs", action="store_true", help="enqueue every kernel instead of graph replay")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain comparison")
+    ap.add_argument("--no-serve", action="store_true",
+                    help="continuous_50khz: skip the served-vs-plain measurement under Poisson arrivals")
     ap.add_argument("--no-extras", action="store_true",
                     help="continuous_50khz: skip the extra full_tpc measurement")
     ap.add_argument("--no-variants", action="store_true", help="skip the fused-vs-dense finder comparison")
