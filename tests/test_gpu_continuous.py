@@ -1,7 +1,8 @@
 """Continuous-readout timeframes at a 50 kHz Pb-Pb-like interaction rate:
 collisions with uniform start times whose drift windows overlap.
 
-A short continuous timeframe is compared with the oracle in full.  The
+A short continuous timeframe is compared with the oracle in full, and so are
+11,000-bin timeframes of seeds 2-4 sector by sector.  The
 full-size one (55,000 time bins, ~2.7e9 digits, ~5.7 GB of ZS pages) runs
 through the CUDA path as the benchmark runs it, and every one of its 36
 sectors is compared element by element with the oracle run on that sector
@@ -75,10 +76,30 @@ def test_continuous_50khz_full_size(lib):
     for k, orc in oracle_sectors(tf, list(range(tf.n_sectors))):
         view = sector_view(gpu, k)
         compare_integer(view, orc)
-        rep = compare_fit(view, orc)
+        rep = compare_fit(view, orc, tf)
         worst = np.maximum(worst, rep["max_rel_par_plain_floor"])
         seen.add(k)
         ncl_sum += len(orc.clusters)
         ntr_sum += len(orc.track_first)
     assert seen == set(range(tf.n_sectors)) and ncl_sum == n_cl and ntr_sum == n_tr
     print("continuous 50 kHz, all sectors: max plain-floor parameter error vs FP64 oracle", worst.tolist())
+
+
+@pytest.mark.parametrize("seed", [2, 3, 4])
+def test_continuous_50khz_other_seeds(lib, seed):
+    """The continuous timeframe's other seeds, at 11,000 time bins of the same
+    collision law (a fifth of the length, the same occupancy): every sector
+    element by element against the oracle, and the properties of the whole."""
+    tf = tpcgen.generate(tpcgen.continuous_tf(seed, n_time_bins=11000))
+    with lib.Reconstructor.for_timeframe(tf, mem_budget=64 << 30) as R:
+        gpu = R.run(tf)
+    check_properties(gpu, tf)
+    assert len(gpu["clusters"]) > 1e7
+    n_cl = n_tr = 0
+    for k, orc in oracle_sectors(tf, list(range(tf.n_sectors))):
+        view = sector_view(gpu, k)
+        compare_integer(view, orc)
+        compare_fit(view, orc, tf)
+        n_cl += len(orc.clusters)
+        n_tr += len(orc.track_first)
+    assert n_cl == len(gpu["clusters"]) and n_tr == len(gpu["tracks"])
