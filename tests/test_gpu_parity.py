@@ -60,6 +60,20 @@ def test_ragged_time_ranges(lib, n_time_bins):
     compare_fit(gpu, orc)
 
 
+def test_maximum_time_range(lib):
+    """The longest timeframe the ABI takes (65,535 bins: 256 fragments, the
+    last one 255 bins long) on one sector, with collisions at its start, middle
+    and end: the largest fragment index and zeta the records and the fit see."""
+    n = 65535
+    tf = tpcgen.generate(tpcgen.single_sector(9, n_time_bins=n, coll_t0=[0.0, 32000.0, n - 500.0],
+                                              coll_ntracks=[60, 60, 60]))
+    orc = oracle.reconstruct(tf)
+    gpu = run_gpu(lib, tf)
+    compare_integer(gpu, orc)
+    compare_fit(gpu, orc)
+    assert int(gpu["clusters"]["t_peak"].max()) >= 65280 and len(gpu["tracks"]) > 30
+
+
 def test_empty_and_noise_only(lib):
     tf = tpcgen.generate(tpcgen.single_sector(6, n_tracks=0))
     orc = oracle.reconstruct(tf)
