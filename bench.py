@@ -47,6 +47,10 @@ WORKLOADS = {
                          "floor(15000 U^7.82) (mean ~1,700), 5% loopers, same charge/noise/ZS model"),
 }
 REF_SAMPLE_BYTES = 20 << 20
+# The CPU baseline of our arm's line: about 320 MB of ZS pages (two whole
+# sectors of the 55,000-bin timeframe, ~10-20 s of single-core oracle work),
+# the reference arm's steps keep the smaller sample above.
+CPU_SAMPLE_BYTES = 320 << 20
 # ncu counters of one find stage (its kernels summed: k_decode_runs,
 # k_unit_descs, k_find_units and k_compact_clusters; the unit-count scan, ~1 %
 # of the stage, is left out): DRAM bytes read + written and warp instructions
@@ -963,12 +967,12 @@ def run_ours(args, world, rank, local):
             m = serve_measure(args, local)
             line["served"] = {k: m[k] for k in ("config", "saturation", "poisson_sweep")}
         if world == 1 and not args.no_cpu_baseline:
-            cb = cpu_baseline(tf, 1)
+            cb = cpu_baseline(tf, 1, CPU_SAMPLE_BYTES)
             line["cpu_baseline"] = {"value": cb["clusters"] / cb["times"][0], "unit": "clusters/s", "cores": 1,
                                     "kind": "oracle", "sample": cb["sample"]}
             pool = OraclePool()
             try:
-                pb = pool.run(tf, REF_SAMPLE_BYTES, 1)
+                pb = pool.run(tf, CPU_SAMPLE_BYTES, 1)
             finally:
                 pool.close()
             line["cpu_baseline_all_cores"] = {"value": pb["clusters"] / pb["times"][0], "unit": "clusters/s",
