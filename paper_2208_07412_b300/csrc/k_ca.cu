@@ -154,7 +154,8 @@ k_ca_neighbours(DevGeom G, DevParams P, DevWork W) {
       __syncthreads();
       Slice sl[2];
       const int tmin = sm_tmm[0], tmax = sm_tmm[1];
-      int tlo[2];
+      int tlo[2], Rk[2];
+      unsigned nst[2];                                   // elements staged per slice (+1: a virtual one)
       bool use_idx[2];
 #pragma unroll
       for (int k = 0; k < 2; k++) {
@@ -163,27 +164,44 @@ k_ca_neighbours(DevGeom G, DevParams P, DevWork W) {
         sl[k].base = a;
         sl[k].n = b > a ? b - a : 0;
         tlo[k] = tmin - w;
-        const int R = tmax + w + 1 - tlo[k];           // table entries 0 .. R
-        use_idx[k] = sl[k].n <= (unsigned)kCaStage && R < kCaIdx;
-        if (sl[k].n <= (unsigned)kCaStage) {
-          // element i (and a virtual element n past the range) fills the table
-          // entries of the bins after its predecessor's time bin up to its own
-          for (unsigned i = tid; i <= sl[k].n; i += blockDim.x) {
-            const int ti = i < sl[k].n ? W.cl_t[a + i] : tmax + w + 2;
-            if (i < sl[k].n) {
-              sm_t[k][i] = ti;
-              sm_y[k][i] = W.cl_y[a + i];
-              sm_z[k][i] = W.cl_z[a + i];
-            }
-            if (use_idx[k]) {
-              const int tp = i > 0 ? W.cl_t[a + i - 1] : tlo[k] - 1;
-              const int b1 = min(ti - tlo[k], R);
-              for (int bb = max(tp + 1 - tlo[k], 0); bb <= b1; bb++) sm_idx[k][bb] = (uint16_t)i;
-            }
-          }
+        Rk[k] = tmax + w + 1 - tlo[k];                    // table entries 0 .. Rk
+        const bool staged = sl[k].n <= (unsigned)kCaStage;
+        use_idx[k] = staged && Rk[k] < kCaIdx;
+        nst[k] = staged ? sl[k].n + 1 : 0u;
+        if (staged) {
           sl[k].t = sm_t[k]; sl[k].y = sm_y[k]; sl[k].z = sm_z[k];
         } else {
           sl[k].t = W.cl_t + a; sl[k].y = W.cl_y + a; sl[k].z = W.cl_z + a;
+        }
+      }
+      // Both slices staged in one loop, so that their loads are in flight
+      // together.  Element i (and a virtual element n past the range) fills the
+      // table entries of the bins after its predecessor's time bin up to its own.
+      const unsigned nloop = max(nst[0], nst[1]);
+      for (unsigned i = tid; i < nloop; i += blockDim.x) {
+        int ti[2], yi[2], zi[2], tp[2];
+#pragma unroll
+        for (int k = 0; k < 2; k++) {
+          const int w = k == 0 ? wd : wu;
+          const unsigned a = sl[k].base;
+          const bool in = i < nst[k], real = in && i < sl[k].n;
+          ti[k] = real ? W.cl_t[a + i] : tmax + w + 2;
+          yi[k] = real ? W.cl_y[a + i] : 0;
+          zi[k] = real ? W.cl_z[a + i] : 0;
+          tp[k] = (in && use_idx[k] && i > 0) ? W.cl_t[a + i - 1] : tlo[k] - 1;
+        }
+#pragma unroll
+        for (int k = 0; k < 2; k++) {
+          if (i >= nst[k]) continue;
+          if (i < sl[k].n) {
+            sm_t[k][i] = ti[k];
+            sm_y[k][i] = yi[k];
+            sm_z[k][i] = zi[k];
+          }
+          if (use_idx[k]) {
+            const int b1 = min(ti[k] - tlo[k], Rk[k]);
+            for (int bb = max(tp[k] + 1 - tlo[k], 0); bb <= b1; bb++) sm_idx[k][bb] = (uint16_t)i;
+          }
         }
       }
       __syncthreads();
