@@ -696,9 +696,9 @@ def fit_roofline(n_cl_on_tracks, fit_ms, fma_peak):
 # (lts__throughput, % of peak), L2 sector rate, warp efficiency (threads per
 # warp instruction / 32), issue active.  Must be cleared whenever the kernel
 # changes.
-CA_COUNTERS = {"workload": "full_tpc seed 1", "l2_throughput_pct_of_peak": 8.07, "l2_sectors_per_ns": 55.5,
-               "lts_hit_rate_pct": 53.6, "warp_efficiency": 19.17 / 32, "issue_active_pct": 51.3,
-               "warps_active_pct": 44.6}
+CA_COUNTERS = {"workload": "full_tpc seed 1", "l2_throughput_pct_of_peak": 8.57, "l2_sectors_per_ns": 59.1,
+               "lts_hit_rate_pct": 53.5, "warp_efficiency": 19.13 / 32, "issue_active_pct": 53.2,
+               "warps_active_pct": 44.9}
 
 
 def ca_roofline(n_cl, ca_ms, hbm):
