@@ -369,13 +369,17 @@ def batched_vs_plain(tpc, torch, local, n_events=64, seed=1000, reps=3, tuning=N
             done, ncl = [], 0
             pending = list(tickets)
             while pending:
-                for t in list(pending):
+                # admission is in submission order: only the oldest 4 can be running
+                progressed = False
+                for t in pending[:4]:
                     if tpc.tpc_poll(R.ctx, t, 0) == tpc.TPC_STATE_DONE:
                         ncl += tpc.tpc_get_counters(R.ctx, t)["clusters"]
                         tpc.tpc_release(R.ctx, t)
                         pending.remove(t)
                         done.append(time.perf_counter() - t0)
-                time.sleep(20e-6)
+                        progressed = True
+                if not progressed:
+                    time.sleep(20e-6)
             return done, ncl
         served_s, (done, ncl_served) = timed(served)
     assert ncl_plain == n_cl == ncl_served, (ncl_plain, n_cl, ncl_served)
@@ -393,10 +397,12 @@ def batched_vs_plain(tpc, torch, local, n_events=64, seed=1000, reps=3, tuning=N
     }
 
 
-def serve_pass(tpc, R, pool, arrivals):
+def serve_pass(tpc, R, pool, arrivals, n_slots):
     """Feed requests (pool index per arrival time, seconds from the start) to a
     context: each is submitted when due; finished ones are released, which
-    admits queued ones.  Returns per-request latency (s) and the makespan."""
+    admits queued ones.  Admission is in arrival order, so only the oldest
+    n_slots requests in flight can be running: only those are polled.  Returns
+    per-request latency (s) and the makespan."""
     t0 = time.perf_counter()
     nxt, inflight, lat, ncl = 0, {}, [], 0
     while nxt < len(arrivals) or inflight:
@@ -405,12 +411,15 @@ def serve_pass(tpc, R, pool, arrivals):
             tf, pages, offs = pool[arrivals[nxt][1]]
             inflight[R.submit(pages, offs, tf.n_time_bins)] = arrivals[nxt][0]
             nxt += 1
-        for t in list(inflight):
+        progressed = False
+        for t in list(inflight)[:n_slots]:
             if tpc.tpc_poll(R.ctx, t, 0) == tpc.TPC_STATE_DONE:
                 ncl += tpc.tpc_get_counters(R.ctx, t)["clusters"]
                 tpc.tpc_release(R.ctx, t)
                 lat.append(time.perf_counter() - t0 - inflight.pop(t))
-        time.sleep(20e-6)
+                progressed = True
+        if not progressed:
+            time.sleep(20e-6)
     return lat, time.perf_counter() - t0, ncl
 
 
@@ -442,22 +451,22 @@ def serve_measure(args, local):
     with tpc.Reconstructor.for_timeframe(pool[0][0], device=local, mem_budget=budget, n_slots=1) as Rp, \
             tpc.Reconstructor.for_timeframe(pool[0][0], device=local, mem_budget=budget, n_slots=4) as Rs:
         burst = [(0.0, int(i)) for i in order]
-        serve_pass(tpc, Rp, pool, burst[:len(pool)])        # warm-up: grow slots, capture graphs
-        serve_pass(tpc, Rs, pool, burst[:len(pool)])
-        lat, span, ncl = serve_pass(tpc, Rp, pool, burst)
+        serve_pass(tpc, Rp, pool, burst[:len(pool)], 1)     # warm-up: grow slots, capture graphs
+        serve_pass(tpc, Rs, pool, burst[:len(pool)], 4)
+        lat, span, ncl = serve_pass(tpc, Rp, pool, burst, 1)
         rate_plain = n_req / span                            # saturation throughput, plain
         for f in args.serve_load:
             lam = f * rate_plain
             gaps = rng.exponential(1.0 / lam, size=n_req)
             arr = [(float(a), int(i)) for a, i in zip(np.cumsum(gaps) - gaps[0], order)]
             row = {"offered_tf_per_s": lam, "load_vs_plain_saturation": f}
-            for name, R in (("plain", Rp), ("served", Rs)):
-                lat, span, ncl = serve_pass(tpc, R, pool, arr)
+            for name, R, ns in (("plain", Rp, 1), ("served", Rs, 4)):
+                lat, span, ncl = serve_pass(tpc, R, pool, arr, ns)
                 row[name] = {"tf_per_s": n_req / span, "clusters_per_s": ncl / span,
                              "latency_ms_p50": 1e3 * pct(lat, 50), "latency_ms_p99": 1e3 * pct(lat, 99)}
             points.append(row)
-        lat_p, span_p, ncl_p = serve_pass(tpc, Rp, pool, burst)
-        lat_s, span_s, ncl_s = serve_pass(tpc, Rs, pool, burst)
+        lat_p, span_p, ncl_p = serve_pass(tpc, Rp, pool, burst, 1)
+        lat_s, span_s, ncl_s = serve_pass(tpc, Rs, pool, burst, 4)
     sizes = sorted(tf.pages.nbytes for tf, _, _ in pool)
     return {
         "n_req": n_req, "n_pool": len(pool), "span_s": span_s, "ncl_s": ncl_s,
