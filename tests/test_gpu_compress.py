@@ -5,8 +5,9 @@ DELTA = 0.1 step of a rounding boundary (a half-integer), and then by one
 step; a status (coded or escaped) only where it lies within DELTA of the
 +-127.5 escape bound.  On full_tpc the differing codes lie at most 1.7e-3 step
 (y) and 3.8e-2 step (zeta: the prediction carries tgl times the arc, up to
-~250 cm) from their boundaries; DELTA leaves a factor 2.6 over the larger and
-still fails any code computed from a wrong prediction."""
+~250 cm) from their boundaries; on 2,000 bins of the continuous timeframe
+(zeta up to 1,000 cm) 5.3e-4 and 9.0e-2 step.  DELTA still fails any code
+computed from a wrong prediction."""
 import numpy as np
 import pytest
 
@@ -28,8 +29,13 @@ def lib():
     return tpc
 
 
-def test_full_tpc_compression_parity(lib):
-    tf = tpcgen.generate(tpcgen.full_tpc(1))
+@pytest.mark.parametrize("make", [lambda: tpcgen.full_tpc(1),
+                                  lambda: tpcgen.continuous_tf(3, n_time_bins=2000, n_sectors=2)],
+                         ids=["full_tpc", "continuous_pileup"])
+def test_compression_parity(lib, make):
+    """full_tpc, and overlapping collisions of the continuous timeframe (2,000
+    bins, two sectors: zeta up to twice full_tpc's)."""
+    tf = tpcgen.generate(make())
     orc = oracle.reconstruct(tf)
     ocy, ocz, ost, qy, qz = oracle.compress(tf, orc, quotients=True)
     with lib.Reconstructor.for_timeframe(tf) as R:

@@ -46,7 +46,8 @@ def same(got, want):
     assert gw.tobytes() == ow.tobytes()
 
 
-@pytest.mark.parametrize("make", [lambda: tpcgen.single_sector(3, n_tracks=300), lambda: tpcgen.full_tpc(2, n_tracks=3000)])
+@pytest.mark.parametrize("make", [lambda: tpcgen.single_sector(3, n_tracks=300), lambda: tpcgen.full_tpc(2, n_tracks=3000),
+                                  lambda: tpcgen.continuous_tf(3, n_time_bins=2000, n_sectors=2)])
 def test_oracle_codes(lib, make):
     tf = tpcgen.generate(make())
     res = oracle.reconstruct(tf)

@@ -57,6 +57,13 @@ def test_dense_sector_unlisted_windows(lib):
     check(lib, tf, 10)
 
 
+def test_continuous_pileup(lib):
+    """Overlapping collisions of the continuous timeframe (2,000 bins, two sectors)."""
+    tf = tpcgen.generate(tpcgen.continuous_tf(3, n_time_bins=2000, n_sectors=2))
+    g = check(lib, tf, 10)
+    assert len(g["clusters"]) < len(oracle.find_clusters(tf))
+
+
 def test_full_tpc_all_finder_variants(lib):
     tf = tpcgen.generate(tpcgen.full_tpc(2, n_tracks=4000))
     g = check(lib, tf, 10)

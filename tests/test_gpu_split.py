@@ -68,6 +68,14 @@ def test_ragged_time_ranges(lib, n_time_bins):
     check(lib, tf)
 
 
+def test_continuous_pileup(lib):
+    """Overlapping collisions of the continuous timeframe (2,000 bins, two
+    sectors): pile-up puts more peaks within four pixels of each other."""
+    tf = tpcgen.generate(tpcgen.continuous_tf(3, n_time_bins=2000, n_sectors=2))
+    _, split = check(lib, tf, fit=True)
+    assert split.mean() > 0.02
+
+
 def test_full_tpc(lib):
     tf = tpcgen.generate(tpcgen.full_tpc(2, n_tracks=4000))
     g, split = check(lib, tf, fit=True)
